@@ -1,0 +1,181 @@
+/*
+ * frr.h -- C ABI of the B300-native rerandomization balance-check library.
+ *
+ * The method is the batched balance check of FastRerandomize (Goldstein,
+ * Jerzak, Kamat, Zhu; arXiv 2501.07642):
+ *   1. regenerate each candidate assignment of n1 treated out of n units from
+ *      its counter-based key (Sec. 2.1, "Key-only storage");
+ *   2. score it by Hotelling's T^2 / the Mahalanobis balance M of the whitened
+ *      covariates (Sec. 2.2, Sec. 2.3 generate_randomizations);
+ *   3. keep the keys whose M lies in the accepted q-quantile, or below a fixed
+ *      threshold (Sec. 2.2 "Choosing stringency");
+ *   4. replay the accepted keys for the randomization test conditional on
+ *      acceptance and its fiducial interval by test inversion (Sec. 2.3
+ *      randomization_test, Sec. 4 "Design-based inference").
+ *
+ * Units of M. Every M crossing this ABI is in T^2 units:
+ *   M = (n1 n0 / n) * sum_j (m1_j - m0_j)^2 = n / (n1 n0) * ||w^T Zc||^2,
+ * where m1, m0 are the treated / control means of the whitened covariates Zc.
+ * The paper's M = Delta^T Delta of Sec. 2.2 equals this value times
+ * (1/n1 + 1/n0); a threshold a_paper converts to a_paper * n1 n0 / n.
+ *
+ * Keys. A key is a 64-bit draw index b under a 64-bit pool seed (two 32-bit
+ * words each, the paper's "two integers" of Sec. 4). Unit i of draw b gets the
+ * 32-bit word r_i = word (i mod 4) of Philox4x32-10 (Salmon et al., SC'11) with
+ * counter (floor(i/4), 0, lo32(b), hi32(b)) and key (lo32(seed), hi32(seed));
+ * the n1 units with the smallest pairs (r_i, i) are treated. With
+ * seed == FRR_EXACT_SEED the draw index is instead a colex rank in
+ * [0, C(n, n1)), i.e. the position of the n-bit mask in increasing integer
+ * order (Sec. 2.3, randomization_type = "exact"); this needs n <= 63.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns frr_status; nothing aborts or throws across the ABI.
+ *   - The caller owns every input and output buffer. Buffers marked "host or
+ *     device" may live in either memory space: the library asks the CUDA
+ *     runtime which one it is and copies as needed. All others are host.
+ *   - frr_init copies X; the context owns its device copies, its scratch and,
+ *     unless the caller passes one, its CUDA stream.
+ *   - A context is not thread-safe: use one per host thread.
+ *   - After FRR_E_CUDA the context is unusable; destroy it.
+ *   - Calls are synchronous with respect to the host: when a call returns,
+ *     its outputs are written.
+ */
+#ifndef FRR_H
+#define FRR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct frr_ctx frr_ctx;
+
+typedef enum {
+    FRR_OK = 0,
+    FRR_E_ARG = -1,        /* invalid argument: n < 2, n1 not in [1, n-1], d < 1, NULL pointer,
+                              non-finite value in X or Y, q not in (0, 1], both or neither of
+                              q / threshold given, unknown option value */
+    FRR_E_DEGENERATE = -2, /* d >= n-1 with whiten = FRR_CHOL, or a Cholesky pivot <= 1e-12 max S_jj */
+    FRR_E_CUDA = -3,       /* a CUDA runtime / driver call failed; the context is unusable */
+    FRR_E_NOMEM = -4,      /* device or pinned-host allocation failed */
+    FRR_E_TIMEOUT = -5,    /* a bounded device-side wait expired */
+    FRR_E_CAPACITY = -6,   /* an output array is smaller than the result (*K_out holds the size needed) */
+    FRR_E_RANGE = -7,      /* first_draw + B overflows 64 bits, or an exact rank >= C(n, n1) */
+    FRR_E_STATE = -8,      /* call out of sequence (e.g. frr_stream_chunk before frr_stream_begin) */
+    FRR_E_UNSUPPORTED = -9 /* shape outside what the compiled kernels cover (n > 2048, exact mode n > 63) */
+} frr_status;
+
+/* precision of the bulk balance evaluation (the accepted set is always decided in FP64 accuracy) */
+enum { FRR_SPLIT_BF16 = 0, /* tcgen05 tensor cores: Zc = hi + lo (two BF16 parts), FP32 accumulate */
+       FRR_F32 = 1 };      /* CUDA-core FP32 SIMT path */
+
+/* whitening rule (Sec. 2.2; App. A "general Sigma_X" remark) */
+enum { FRR_CHOL = 0,  /* S = L L^T, Zc = Xc L^{-T}: Hotelling T^2 (needs d <= n - 2) */
+       FRR_RIDGE = 1, /* S + ridge * (tr S / d) I = L L^T (any d; needs ridge > 0) */
+       FRR_DIAG = 2 };/* L = diag(sqrt(S_jj)): sum of squared standardised mean differences */
+
+#define FRR_EXACT_SEED UINT64_MAX
+
+typedef struct {
+    int precision;      /* FRR_SPLIT_BF16 (default) or FRR_F32 */
+    int whiten;         /* FRR_CHOL (default), FRR_RIDGE or FRR_DIAG */
+    double ridge;       /* ridge weight for FRR_RIDGE, relative to tr(S)/d; default 0.1 */
+    double band_safety; /* multiplier on the error band of the approximate M; default 2.0, must be >= 1 */
+    void* cuda_stream;  /* cudaStream_t to run on; NULL = the context creates its own */
+} frr_opts;
+
+typedef struct {
+    int64_t draws;              /* draws scored by the last frr_select / stream */
+    int64_t candidates;         /* draws re-checked with the FP64-accurate exact-sum recheck */
+    int64_t accepted;           /* accepted draws */
+    double threshold_m64;       /* largest accepted M (T^2 units) */
+    double band_at_threshold;   /* error band of the approximate M at that threshold */
+    double max_rel_err;         /* max |M_approx - M64| / M64 over re-checked draws */
+    double max_err_over_band;   /* max |M_approx - M64| / band over re-checked draws (must stay < 1) */
+    double boundary_gap_rel;    /* (M64[K+1] - M64[K]) / M64[K] among re-checked draws (q mode; NaN if none) */
+    int parity_at_risk;         /* 1 if boundary_gap_rel < 1e-11: the K-th / (K+1)-th order rests on rounding */
+    int band_violations;        /* re-checked draws with |M_approx - M64| > band (must be 0) */
+    double ms_init;             /* wall time of frr_init */
+    double ms_balance;          /* device time of the balance kernels in the last call */
+    double ms_select;           /* device time of the running selection */
+    double ms_recheck;          /* device time of the exact-sum recheck and final ordering */
+} frr_stats;
+
+/* Fills *o with the defaults listed above. */
+void frr_default_opts(frr_opts* o);
+
+/* Prepares an experiment (Sec. 2.2: centre, covariance with the n-1 denominator,
+ * optional ridge, Cholesky factor, whitening Zc = Xc L^{-T}; all in FP64 on the GPU).
+ * X: host, n x d row-major FP64 (rows are units). n1: number of treated units.
+ * opts: NULL for defaults. On success *out owns device memory; release it with
+ * frr_destroy. Supports n <= 2048. */
+frr_status frr_init(frr_ctx** out, const double* X, int64_t n, int64_t d, int64_t n1, const frr_opts* opts);
+
+/* Balance of draws [first_draw, first_draw + B) (Sec. 2.1 batched processing,
+ * Sec. 2.3 Hotelling T^2). M_out: host or device, B floats, approximate M in
+ * T^2 units from the bulk path chosen by opts.precision. */
+frr_status frr_balance(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_t B, float* M_out);
+
+/* Same as frr_balance with seed = FRR_EXACT_SEED: ranks [first_rank, first_rank + B). */
+frr_status frr_balance_exact(frr_ctx* ctx, uint64_t first_rank, uint64_t B, float* M_out);
+
+/* Accepted pool of draws [first_draw, first_draw + B) (Sec. 2.2, 2.3). Exactly one of
+ * q (0 < q <= 1: keep the K = ceil(qB - 1e-9 qB) draws with the smallest
+ * (M, draw index)) and threshold (>= 0: keep every draw with M <= threshold, T^2 units)
+ * is used; pass NAN for the other. keys_out (host or device, cap entries): accepted
+ * draw indices in ascending order; M64_out (host or device, cap entries, may be NULL):
+ * their M in FP64 accuracy. *K_out: number accepted. If K > cap, nothing is written
+ * and FRR_E_CAPACITY is returned with *K_out = K. */
+frr_status frr_select(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_t B, double q,
+                      double threshold, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out);
+
+/* Streaming form of frr_select over B_total draws fed in chunks (Sec. 2.1 batched
+ * processing; bounded memory). The accepted set after frr_stream_end is identical
+ * to one frr_select over the union of the chunks. Chunks may come in any order but
+ * must not overlap; their lengths must add up to B_total before frr_stream_end. */
+frr_status frr_stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold, uint64_t B_total);
+frr_status frr_stream_chunk(frr_ctx* ctx, uint64_t first_draw, uint64_t B_chunk);
+frr_status frr_stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out);
+
+/* Regenerates the assignment of one key (Sec. 2.1 key-only storage).
+ * w_out: host or device, n bytes, 1 = treated, in unit order. */
+frr_status frr_assignment(frr_ctx* ctx, uint64_t seed, uint64_t key, uint8_t* w_out);
+
+/* Regenerates draws [first_draw, first_draw + count). w_out: host or device, count x n bytes. */
+frr_status frr_assignments(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_t count, uint8_t* w_out);
+
+/* M in FP64 accuracy for an explicit list of draws (the same exact-sum recheck that
+ * decides acceptance). draws, M64_out: host or device, count entries. */
+frr_status frr_recheck(frr_ctx* ctx, uint64_t seed, const uint64_t* draws, int64_t count, double* M64_out);
+
+/* Randomization test conditional on acceptance and its inversion (Sec. 2.3
+ * randomization_test; Sec. 4). Sharp null Y(1) = Y(0) + tau; statistic: the two-sided
+ * difference in means. For each tau_g: count_out[g] = #{k : |t_k(tau_g)| >= |t_obs(tau_g)|}
+ * over the K accepted assignments (the observed one included, so p >= 1/K), with
+ * t_k(tau) = a_k - tau b_k, a_k = DiM_{w_k}(Y), b_k = DiM_{w_k}(w_obs);
+ * p_out[g] = count_out[g] / K. The interval is [min, max] of the grid points with
+ * p > alpha (NAN, NAN when none). keys: host or device, K entries; obs_key must be
+ * one of them. Y: host or device, n. tau: host or device, T. p_out, count_out: host or
+ * device, T entries (count_out may be NULL). ci_lo, ci_hi: host, may be NULL. */
+frr_status frr_randtest(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64_t K, uint64_t obs_key,
+                        const double* Y, const double* tau, int64_t T, double alpha,
+                        double* p_out, int64_t* count_out, double* ci_lo, double* ci_hi);
+
+/* Copies the whitened covariates Zc (host, n x d row-major FP64) out of the context. */
+frr_status frr_whitened(const frr_ctx* ctx, double* Zc_out);
+
+/* Statistics of the last call (see frr_stats). */
+frr_status frr_last_stats(const frr_ctx* ctx, frr_stats* out);
+
+/* Static description of a status code. */
+const char* frr_strerror(frr_status status);
+
+/* Releases everything the context owns. NULL is ignored. */
+void frr_destroy(frr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRR_H */

@@ -1,0 +1,354 @@
+// frr_capi.cu -- the extern "C" entry points of include/frr.h: argument checks,
+// context ownership, host/device marshalling. All arithmetic runs in the
+// kernels of the other translation units.
+#include "frr_internal.cuh"
+
+#include <chrono>
+#include <new>
+#include <vector>
+
+namespace frr {
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+frr_status ensure_device(frr_ctx* ctx, void** buf, size_t* cap_bytes, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (*buf != nullptr && *cap_bytes >= bytes) return FRR_OK;
+    if (*buf != nullptr) {
+        FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap_bytes = 0;
+    }
+    const size_t grown = bytes + bytes / 4;
+    cudaError_t e = cudaMalloc(buf, grown);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return FRR_E_NOMEM;
+    }
+    *cap_bytes = grown;
+    return FRR_OK;
+}
+
+frr_status ensure_host_pinned(frr_ctx* ctx, size_t bytes)
+{
+    if (ctx->host_pinned != nullptr && ctx->host_pinned_bytes >= bytes) return FRR_OK;
+    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    ctx->host_pinned = nullptr;
+    ctx->host_pinned_bytes = 0;
+    if (cudaMallocHost(&ctx->host_pinned, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return FRR_E_NOMEM;
+    }
+    ctx->host_pinned_bytes = bytes;
+    return FRR_OK;
+}
+
+frr_status copy_in(frr_ctx* ctx, void* dst_dev, const void* src_any, size_t bytes)
+{
+    if (bytes == 0) return FRR_OK;
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dst_dev, src_any, bytes, cudaMemcpyDefault, ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return FRR_OK;
+}
+
+frr_status copy_out(frr_ctx* ctx, void* dst_any, const void* src_dev, size_t bytes)
+{
+    if (bytes == 0) return FRR_OK;
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dst_any, src_dev, bytes, cudaMemcpyDefault, ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return FRR_OK;
+}
+
+static frr_status check_range(const frr_ctx* ctx, uint64_t seed, uint64_t first, uint64_t B)
+{
+    if (first + B < first) return FRR_E_RANGE;
+    if (seed == FRR_EXACT_SEED) {
+        if (ctx->n > kExactMaxN) return FRR_E_UNSUPPORTED;
+        if (first + B > binom_host((int)ctx->n, (int)ctx->n1)) return FRR_E_RANGE;
+    }
+    return FRR_OK;
+}
+
+static void release(frr_ctx* ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    void* bufs[] = {ctx->Zc64, ctx->Z32, ctx->Zhi, ctx->Zlo, ctx->Q, ctx->Qsum, ctx->qexp, ctx->binom, ctx->Mhat,
+                    ctx->ret_idx[0], ctx->ret_idx[1], ctx->ret_m[0], ctx->ret_m[1], ctx->dev_counters, ctx->M64,
+                    ctx->ukeys, ctx->misc, ctx->misc2};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    for (cudaEvent_t e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    cudaGetLastError();
+    delete ctx;
+}
+
+}  // namespace frr
+
+using namespace frr;
+
+extern "C" {
+
+void frr_default_opts(frr_opts* o)
+{
+    if (!o) return;
+    o->precision = FRR_SPLIT_BF16;
+    o->whiten = FRR_CHOL;
+    o->ridge = 0.1;
+    o->band_safety = 2.0;
+    o->cuda_stream = nullptr;
+}
+
+const char* frr_strerror(frr_status s)
+{
+    switch (s) {
+        case FRR_OK: return "ok";
+        case FRR_E_ARG: return "invalid argument";
+        case FRR_E_DEGENERATE: return "degenerate covariance (d >= n-1 under Cholesky whitening, or a pivot below tolerance)";
+        case FRR_E_CUDA: return "CUDA error (context unusable)";
+        case FRR_E_NOMEM: return "out of memory";
+        case FRR_E_TIMEOUT: return "bounded device wait expired";
+        case FRR_E_CAPACITY: return "output array too small (K_out holds the size needed)";
+        case FRR_E_RANGE: return "draw range out of bounds";
+        case FRR_E_STATE: return "call out of sequence";
+        case FRR_E_UNSUPPORTED: return "shape not covered by the compiled kernels";
+    }
+    return "unknown status";
+}
+
+frr_status frr_init(frr_ctx** out, const double* X, int64_t n, int64_t d, int64_t n1, const frr_opts* opts)
+{
+    if (!out || !X) return FRR_E_ARG;
+    *out = nullptr;
+    if (n < 2 || d < 1 || n1 < 1 || n1 > n - 1) return FRR_E_ARG;
+    if (n > kMaxN) return FRR_E_UNSUPPORTED;
+    frr_opts o;
+    frr_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != FRR_SPLIT_BF16 && o.precision != FRR_F32) return FRR_E_ARG;
+    if (o.whiten != FRR_CHOL && o.whiten != FRR_RIDGE && o.whiten != FRR_DIAG) return FRR_E_ARG;
+    if (o.whiten == FRR_RIDGE && !(o.ridge > 0.0 && isfinite(o.ridge))) return FRR_E_ARG;
+    if (!(o.band_safety >= 1.0 && isfinite(o.band_safety))) return FRR_E_ARG;
+    for (int64_t k = 0; k < n * d; ++k)
+        if (!isfinite(X[k])) return FRR_E_ARG;
+    if (o.whiten == FRR_CHOL && d >= n - 1) return FRR_E_DEGENERATE;
+
+    const auto t0 = std::chrono::steady_clock::now();
+    frr_ctx* ctx = new (std::nothrow) frr_ctx();
+    if (!ctx) return FRR_E_NOMEM;
+    ctx->n = n; ctx->d = d; ctx->n1 = n1; ctx->n0 = n - n1;
+    ctx->opts = o;
+    ctx->c_M = (double)n / ((double)n1 * (double)(n - n1));
+    const int blocks = ceil_div(n, 128);
+    int kb = 1;
+    while (kb < blocks) kb <<= 1;
+    ctx->kb = kb;
+    ctx->kused = 128 * blocks;
+    ctx->kpad = 128 * kb;
+    ctx->dpad32 = 128 * ceil_div(d, 128);
+
+    auto bail = [&](frr_status s) { release(ctx); return s; };
+#define INIT_CUDA(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) { cudaGetLastError(); \
+        return bail(_e == cudaErrorMemoryAllocation ? FRR_E_NOMEM : FRR_E_CUDA); } } while (0)
+    INIT_CUDA(cudaGetDevice(&ctx->device));
+    INIT_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (o.cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(o.cuda_stream);
+    } else {
+        INIT_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    for (cudaEvent_t& e : ctx->ev) INIT_CUDA(cudaEventCreate(&e));
+    const size_t nd = (size_t)n * d;
+    INIT_CUDA(cudaMalloc(&ctx->Zc64, nd * sizeof(double)));
+    INIT_CUDA(cudaMalloc(&ctx->Z32, (size_t)ctx->kpad * ctx->dpad32 * sizeof(float)));
+    INIT_CUDA(cudaMalloc(&ctx->Zhi, (size_t)d * ctx->kpad * sizeof(__nv_bfloat16)));
+    INIT_CUDA(cudaMalloc(&ctx->Zlo, (size_t)d * ctx->kpad * sizeof(__nv_bfloat16)));
+    INIT_CUDA(cudaMalloc(&ctx->Q, (size_t)ctx->kpad * d * sizeof(long long)));
+    INIT_CUDA(cudaMalloc(&ctx->Qsum, (size_t)d * sizeof(long long)));
+    INIT_CUDA(cudaMalloc(&ctx->qexp, (size_t)d * sizeof(int)));
+    INIT_CUDA(cudaMalloc(&ctx->binom, 64 * 64 * sizeof(uint64_t)));
+    INIT_CUDA(cudaMalloc(&ctx->dev_counters, 16 * sizeof(int)));
+    INIT_CUDA(cudaMemsetAsync(ctx->dev_counters, 0, 16 * sizeof(int), ctx->stream));
+#undef INIT_CUDA
+    frr_status s = prep_run(ctx, X);
+    if (s != FRR_OK) return bail(s);
+    ctx->stats.ms_init = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    ctx->stats.boundary_gap_rel = NAN;
+    *out = ctx;
+    return FRR_OK;
+}
+
+void frr_destroy(frr_ctx* ctx) { release(ctx); }
+
+frr_status frr_balance(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_t B, float* M_out)
+{
+    if (!ctx || (!M_out && B > 0)) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    FRR_TRY(check_range(ctx, seed, first_draw, B));
+    if (B == 0) return FRR_OK;
+    const bool exact = (seed == FRR_EXACT_SEED);
+    if (is_device_ptr(M_out)) {
+        FRR_TRY(balance_launch(ctx, seed, exact, first_draw, B, M_out));
+        FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        return FRR_OK;
+    }
+    const uint64_t chunk = 1ull << 22;
+    for (uint64_t off = 0; off < B; off += chunk) {
+        const uint64_t bc = (B - off < chunk) ? (B - off) : chunk;
+        FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->Mhat), &ctx->Mhat_bytes, bc * sizeof(float)));
+        FRR_TRY(balance_launch(ctx, seed, exact, first_draw + off, bc, ctx->Mhat));
+        FRR_TRY(copy_out(ctx, M_out + off, ctx->Mhat, bc * sizeof(float)));
+    }
+    return FRR_OK;
+}
+
+frr_status frr_balance_exact(frr_ctx* ctx, uint64_t first_rank, uint64_t B, float* M_out)
+{
+    return frr_balance(ctx, FRR_EXACT_SEED, first_rank, B, M_out);
+}
+
+static frr_status check_mode(double q, double threshold)
+{
+    const bool hq = !isnan(q), ht = !isnan(threshold);
+    if (hq == ht) return FRR_E_ARG;
+    if (hq && !(q > 0.0 && q <= 1.0)) return FRR_E_ARG;
+    if (ht && !(threshold >= 0.0)) return FRR_E_ARG;
+    return FRR_OK;
+}
+
+frr_status frr_stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold, uint64_t B_total)
+{
+    if (!ctx) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    FRR_TRY(check_mode(q, threshold));
+    if (B_total == 0) return FRR_E_ARG;
+    if (seed == FRR_EXACT_SEED) {
+        if (ctx->n > kExactMaxN) return FRR_E_UNSUPPORTED;
+        if (B_total > binom_host((int)ctx->n, (int)ctx->n1)) return FRR_E_RANGE;
+    }
+    return stream_begin(ctx, seed, q, threshold, B_total);
+}
+
+frr_status frr_stream_chunk(frr_ctx* ctx, uint64_t first_draw, uint64_t B_chunk)
+{
+    if (!ctx) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    if (!ctx->st.active) return FRR_E_STATE;
+    FRR_TRY(check_range(ctx, ctx->st.seed, first_draw, B_chunk));
+    return stream_chunk(ctx, first_draw, B_chunk);
+}
+
+frr_status frr_stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out)
+{
+    if (!ctx || !K_out || cap < 0 || (!keys_out && cap > 0)) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    return stream_end(ctx, keys_out, M64_out, cap, K_out);
+}
+
+frr_status frr_select(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_t B, double q, double threshold,
+                      uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out)
+{
+    if (!ctx || !K_out || cap < 0 || (!keys_out && cap > 0) || B == 0) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    FRR_TRY(check_mode(q, threshold));
+    FRR_TRY(check_range(ctx, seed, first_draw, B));
+    FRR_TRY(stream_begin(ctx, seed, q, threshold, B));
+    frr_status s = stream_chunk(ctx, first_draw, B);
+    if (s != FRR_OK) { ctx->st.active = false; return s; }
+    return stream_end(ctx, keys_out, M64_out, cap, K_out);
+}
+
+frr_status frr_assignments(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_t count, uint8_t* w_out)
+{
+    if (!ctx || (!w_out && count > 0)) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    FRR_TRY(check_range(ctx, seed, first_draw, count));
+    const bool exact = (seed == FRR_EXACT_SEED);
+    const bool dev = count > 0 && is_device_ptr(w_out);
+    const uint64_t chunk = 1ull << 16;
+    const size_t words = 4 * (size_t)ctx->kb;
+    for (uint64_t off = 0; off < count; off += chunk) {
+        const uint64_t c = (count - off < chunk) ? (count - off) : chunk;
+        const size_t rows_bytes = (size_t)c * words * sizeof(uint32_t);
+        FRR_TRY(ensure_device(ctx, &ctx->misc2, &ctx->misc2_bytes, rows_bytes + (dev ? 0 : (size_t)c * ctx->n)));
+        uint32_t* rows = static_cast<uint32_t*>(ctx->misc2);
+        uint8_t* wdst = dev ? w_out + off * ctx->n : reinterpret_cast<uint8_t*>(static_cast<char*>(ctx->misc2) + rows_bytes);
+        FRR_TRY(bits_launch(ctx, seed, exact, first_draw + off, c, nullptr, rows));
+        FRR_TRY(unpack_launch(ctx, rows, c, wdst));
+        if (!dev) FRR_TRY(copy_out(ctx, w_out + off * ctx->n, wdst, (size_t)c * ctx->n));
+    }
+    FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return FRR_OK;
+}
+
+frr_status frr_assignment(frr_ctx* ctx, uint64_t seed, uint64_t key, uint8_t* w_out)
+{
+    return frr_assignments(ctx, seed, key, 1, w_out);
+}
+
+frr_status frr_recheck(frr_ctx* ctx, uint64_t seed, const uint64_t* draws, int64_t count, double* M64_out)
+{
+    if (!ctx || count < 0 || (count > 0 && (!draws || !M64_out))) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    if (count == 0) return FRR_OK;
+    const bool exact = (seed == FRR_EXACT_SEED);
+    FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->ukeys), &ctx->ukeys_bytes, (size_t)count * 8));
+    FRR_TRY(copy_in(ctx, ctx->ukeys, draws, (size_t)count * 8));
+    if (exact) {
+        if (ctx->n > kExactMaxN) return FRR_E_UNSUPPORTED;
+        std::vector<uint64_t> h((size_t)count);
+        FRR_TRY(copy_out(ctx, h.data(), ctx->ukeys, (size_t)count * 8));
+        const uint64_t tot = binom_host((int)ctx->n, (int)ctx->n1);
+        for (uint64_t v : h)
+            if (v >= tot) return FRR_E_RANGE;
+    }
+    FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->M64), &ctx->M64_bytes, (size_t)count * 8));
+    FRR_TRY(recheck_launch(ctx, seed, exact, ctx->ukeys, count, ctx->M64));
+    FRR_TRY(copy_out(ctx, M64_out, ctx->M64, (size_t)count * 8));
+    return FRR_OK;
+}
+
+frr_status frr_randtest(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64_t K, uint64_t obs_key,
+                        const double* Y, const double* tau, int64_t T, double alpha, double* p_out,
+                        int64_t* count_out, double* ci_lo, double* ci_hi)
+{
+    if (!ctx || !keys || K < 1 || !Y || !tau || T < 1 || !p_out || !(alpha >= 0.0 && alpha <= 1.0)) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    if (seed == FRR_EXACT_SEED && ctx->n > kExactMaxN) return FRR_E_UNSUPPORTED;
+    return randtest_run(ctx, seed, keys, K, obs_key, Y, tau, T, alpha, p_out, count_out, ci_lo, ci_hi);
+}
+
+frr_status frr_whitened(const frr_ctx* ctx, double* Zc_out)
+{
+    if (!ctx || !Zc_out) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    if (cudaMemcpy(Zc_out, ctx->Zc64, (size_t)ctx->n * ctx->d * sizeof(double), cudaMemcpyDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return FRR_E_CUDA;
+    }
+    return FRR_OK;
+}
+
+frr_status frr_last_stats(const frr_ctx* ctx, frr_stats* out)
+{
+    if (!ctx || !out) return FRR_E_ARG;
+    *out = ctx->stats;
+    return FRR_OK;
+}
+
+}  // extern "C"

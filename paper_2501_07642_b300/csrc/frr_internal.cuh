@@ -1,0 +1,157 @@
+// frr_internal.cuh -- context layout and helpers shared by the CUDA sources of libfrr.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "../../include/frr.h"
+
+namespace frr {
+
+// Largest n the generation kernels cover: 16 Philox blocks (64 unit words) per lane.
+constexpr int kMaxN = 2048;
+constexpr int kExactMaxN = 63;
+
+// Fixed-point scale for the exact-sum recheck: |Q_ij| <= 2^kQBits, so sums over
+// at most 2^12 units stay below 2^62.
+constexpr int kQBits = 50;
+
+// Fluctuation multiplier of the accumulation term of the error band (number of
+// standard deviations of a partial sum under complete randomization).
+constexpr double kBandLambda = 6.0;
+
+struct BandConsts {
+    // band(M) = safety * (lin * sqrt(M) + quad + rel * M), M in T^2 units
+    double lin = 0.0, quad = 0.0, rel = 0.0;
+};
+
+struct StreamState {
+    bool active = false;
+    bool exact = false;
+    uint64_t seed = 0;
+    bool q_mode = true;
+    double q = NAN, threshold = NAN;
+    uint64_t total = 0, seen = 0;
+    int64_t K = 0;            // target accepted count (q mode)
+    int64_t retained = 0;     // entries in the retained (candidate) set
+    float cut = INFINITY;     // current cut on the approximate M (keep M_hat <= cut)
+};
+
+}  // namespace frr
+
+struct frr_ctx {
+    int64_t n = 0, d = 0, n1 = 0, n0 = 0;
+    frr_opts opts{};
+    int device = 0, num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int kb = 0;                // Philox blocks per lane, power of two: n <= 128 * kb
+    int kused = 0;             // K positions holding units: 128 * ceil(n / 128)
+    int kpad = 0;              // 128 * kb
+    int dpad32 = 0;            // d rounded up to 128 (FP32 SIMT column tiles)
+    double c_M = 0.0;          // n / (n1 n0)
+
+    // device copies (K-order = the order in which the generator emits unit bits)
+    double* Zc64 = nullptr;    // n x d, natural unit order
+    float* Z32 = nullptr;      // kpad x dpad32, K-order rows, zero padding
+    __nv_bfloat16* Zhi = nullptr;  // d x kpad (K-major), K-order columns
+    __nv_bfloat16* Zlo = nullptr;
+    long long* Q = nullptr;    // kpad x d fixed-point Zc, K-order rows
+    long long* Qsum = nullptr; // d
+    int* qexp = nullptr;       // d: Q_ij = Zc_ij * 2^qexp_j (rounded)
+    uint64_t* binom = nullptr; // 64 x 64 binomial table (exact mode)
+
+    frr::BandConsts band32{}, band_tc{};
+
+    // scratch
+    float* Mhat = nullptr;  size_t Mhat_bytes = 0;       // approximate M of a chunk
+    uint64_t* ret_idx[2] = {nullptr, nullptr};           // retained candidates (ping-pong)
+    float* ret_m[2] = {nullptr, nullptr};
+    size_t ret_bytes_idx[2] = {0, 0}, ret_bytes_m[2] = {0, 0};
+    int ret_cur = 0;
+    int* dev_counters = nullptr;  // small device scalars
+    double* M64 = nullptr; size_t M64_bytes = 0;
+    uint64_t* ukeys = nullptr; size_t ukeys_bytes = 0;   // key staging
+    void* misc = nullptr; size_t misc_bytes = 0;          // replay / randtest scratch
+    void* misc2 = nullptr; size_t misc2_bytes = 0;
+    void* host_pinned = nullptr; size_t host_pinned_bytes = 0;
+    cudaEvent_t ev[8] = {};
+
+    frr::StreamState st;
+    frr_stats stats{};
+    bool failed = false;
+};
+
+namespace frr {
+
+// ---- status helpers ------------------------------------------------------
+#define FRR_CUDA_TRY(ctx, expr)                                                   \
+    do {                                                                          \
+        cudaError_t _e = (expr);                                                  \
+        if (_e != cudaSuccess) {                                                  \
+            if ((ctx) != nullptr) (ctx)->failed = true;                           \
+            return (_e == cudaErrorMemoryAllocation) ? FRR_E_NOMEM : FRR_E_CUDA;  \
+        }                                                                         \
+    } while (0)
+
+#define FRR_TRY(expr)                        \
+    do {                                     \
+        frr_status _s = (expr);              \
+        if (_s != FRR_OK) return _s;         \
+    } while (0)
+
+// true if p is device-accessible memory (device or managed); false for pageable / pinned host
+bool is_device_ptr(const void* p);
+
+// grow a device buffer to at least `bytes` (old contents are not kept)
+frr_status ensure_device(frr_ctx* ctx, void** buf, size_t* cap_bytes, size_t bytes);
+
+// pinned host staging of at least `bytes`
+frr_status ensure_host_pinned(frr_ctx* ctx, size_t bytes);
+
+// copies between a caller buffer (host or device) and a device buffer of the context
+frr_status copy_in(frr_ctx* ctx, void* dst_dev, const void* src_any, size_t bytes);
+frr_status copy_out(frr_ctx* ctx, void* dst_any, const void* src_dev, size_t bytes);
+
+// kernel families (defined in their own translation units)
+frr_status prep_run(frr_ctx* ctx, const double* X_host);
+frr_status balance_f32_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
+frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
+frr_status balance_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
+frr_status bits_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t count,
+                       const uint64_t* draws_dev, uint32_t* rows_dev);
+frr_status unpack_launch(frr_ctx* ctx, const uint32_t* rows_dev, uint64_t count, uint8_t* w_dev);
+frr_status recheck_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws_dev, int64_t count,
+                          double* M64_dev);
+frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold, uint64_t total);
+frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B);
+frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out);
+frr_status randtest_run(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64_t K, uint64_t obs_key,
+                        const double* Y, const double* tau, int64_t T, double alpha, double* p_out,
+                        int64_t* count_out, double* ci_lo, double* ci_hi);
+
+inline uint64_t binom_host(int n, int k)
+{
+    if (k < 0 || k > n) return 0;
+    if (k > n - k) k = n - k;
+    unsigned __int128 r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (unsigned)(n - k + i) / (unsigned)i;
+    return (r > (unsigned __int128)UINT64_MAX) ? UINT64_MAX : (uint64_t)r;
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// band of the approximate M of the chosen bulk path
+inline const BandConsts& band_of(const frr_ctx* ctx)
+{
+    return ctx->opts.precision == FRR_F32 ? ctx->band32 : ctx->band_tc;
+}
+
+__host__ __device__ inline double band_value(double lin, double quad, double rel, double safety, double m)
+{
+    return safety * (lin * sqrt(m > 0.0 ? m : 0.0) + quad + rel * m);
+}
+
+}  // namespace frr

@@ -1,0 +1,150 @@
+// frr_randtest.cu -- randomization test conditional on acceptance and its inversion.
+//
+// Sec. 2.3 (randomization_test) and Sec. 4 ("Design-based inference"): the
+// observed statistic is compared with its distribution over the accepted
+// assignments only; p >= 1/K because the observed assignment is one of them.
+// Reading: sharp null Y_i(1) = Y_i(0) + tau, two-sided difference in means.
+// Under that null the adjusted outcome is Y - tau w_obs, and for accepted
+// assignment k
+//   t_k(tau) = DiM_{w_k}(Y - tau w_obs) = a_k - tau b_k,
+//   a_k = DiM_{w_k}(Y),  b_k = DiM_{w_k}(w_obs) = c_k / n1 - (n1 - c_k) / n0,
+// with c_k = |w_k AND w_obs|; for the observed assignment b = 1 exactly. So a_k
+// and b_k are formed once per key and each grid point costs K comparisons.
+// The interval is [min, max] of the grid points with p > alpha.
+#include "frr_internal.cuh"
+#include "frr_gen.cuh"
+
+#include <vector>
+
+namespace frr {
+namespace {
+
+// a_k with the same ascending-unit sums as the plain definition; b_k from popcounts.
+__global__ void k_contrasts(const uint32_t* __restrict__ rows, int words, int64_t K, int64_t obs, int n, int n1,
+                            const double* __restrict__ Y, double* __restrict__ a, double* __restrict__ b)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const uint32_t* row = rows + k * words;
+    const uint32_t* orow = rows + obs * words;
+    double s1 = 0.0, s0 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const int p = kpos_of_unit(i);
+        if ((row[p >> 5] >> (p & 31)) & 1u) s1 = __dadd_rn(s1, Y[i]);
+        else s0 = __dadd_rn(s0, Y[i]);
+    }
+    int c = 0;
+    for (int q = 0; q < words; ++q) c += __popc(row[q] & orow[q]);
+    const int n0 = n - n1;
+    a[k] = __dsub_rn(__ddiv_rn(s1, (double)n1), __ddiv_rn(s0, (double)n0));
+    b[k] = __dsub_rn(__ddiv_rn((double)c, (double)n1), __ddiv_rn((double)(n1 - c), (double)n0));
+}
+
+// one CTA per grid point: count_g = #{k : |a_k - tau b_k| >= |a_obs - tau b_obs|}
+__global__ void k_tau_grid(const double* __restrict__ a, const double* __restrict__ b, int64_t K, int64_t obs,
+                           const double* __restrict__ tau, long long* __restrict__ count, double* __restrict__ p,
+                           long long* __restrict__ near)
+{
+    __shared__ long long sc[32], sn[32];
+    const int g = blockIdx.x;
+    const double t = tau[g];
+    const double tobs = fabs(__dsub_rn(a[obs], __dmul_rn(t, b[obs])));
+    long long cnt = 0, nr = 0;
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
+        const double tk = fabs(__dsub_rn(a[k], __dmul_rn(t, b[k])));
+        cnt += (tk >= tobs) ? 1 : 0;
+        nr += (fabs(tk - tobs) < 1e-12 * (tobs + 1.0)) ? 1 : 0;
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        cnt += __shfl_xor_sync(kFull, cnt, off);
+        nr += __shfl_xor_sync(kFull, nr, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { sc[warp] = cnt; sn[warp] = nr; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long c = 0, m = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { c += sc[w]; m += sn[w]; }
+        count[g] = c;
+        near[g] = m;
+        p[g] = __ddiv_rn((double)c, (double)K);
+    }
+}
+
+__global__ void k_interval(const double* __restrict__ p, const double* __restrict__ tau, int64_t T, double alpha,
+                           double* __restrict__ out)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double lo = NAN, hi = NAN;
+    for (int64_t g = 0; g < T; ++g) {
+        if (p[g] > alpha) {
+            if (isnan(lo) || tau[g] < lo) lo = tau[g];
+            if (isnan(hi) || tau[g] > hi) hi = tau[g];
+        }
+    }
+    out[0] = lo;
+    out[1] = hi;
+}
+
+}  // namespace
+
+frr_status randtest_run(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64_t K, uint64_t obs_key,
+                        const double* Y, const double* tau, int64_t T, double alpha, double* p_out,
+                        int64_t* count_out, double* ci_lo, double* ci_hi)
+{
+    const bool exact = (seed == FRR_EXACT_SEED);
+    const int n = (int)ctx->n;
+    const int words = 4 * ctx->kb;
+    // host copy of the keys to locate the observed one and validate
+    std::vector<uint64_t> hk((size_t)K);
+    FRR_TRY(copy_out(ctx, hk.data(), keys, (size_t)K * sizeof(uint64_t)));
+    int64_t obs = -1;
+    for (int64_t k = 0; k < K; ++k)
+        if (hk[k] == obs_key) { obs = k; break; }
+    if (obs < 0) return FRR_E_ARG;
+    if (exact) {
+        const uint64_t tot = binom_host((int)ctx->n, (int)ctx->n1);
+        for (int64_t k = 0; k < K; ++k)
+            if (hk[k] >= tot) return FRR_E_RANGE;
+    }
+    std::vector<double> hy((size_t)n), ht((size_t)T);
+    FRR_TRY(copy_out(ctx, hy.data(), Y, (size_t)n * sizeof(double)));
+    FRR_TRY(copy_out(ctx, ht.data(), tau, (size_t)T * sizeof(double)));
+    for (double v : hy) if (!isfinite(v)) return FRR_E_ARG;
+    for (double v : ht) if (!isfinite(v)) return FRR_E_ARG;
+
+    // scratch: keys (K), rows (K x words), Y (n), tau (T), a (K), b (K), count (T), near (T), p (T), ci (2)
+    const size_t bytes = (size_t)K * 8 + (size_t)K * words * 4 + 8 + (size_t)n * 8 + (size_t)T * 8 + (size_t)K * 16 +
+                         (size_t)T * 24 + 16 + 64;
+    FRR_TRY(ensure_device(ctx, &ctx->misc, &ctx->misc_bytes, bytes));
+    char* base = static_cast<char*>(ctx->misc);
+    uint64_t* dkeys = reinterpret_cast<uint64_t*>(base);
+    double* dy = reinterpret_cast<double*>(dkeys + K);
+    double* dtau = dy + n;
+    double* da = dtau + T;
+    double* db = da + K;
+    double* dp = db + K;
+    double* dci = dp + T;
+    long long* dcount = reinterpret_cast<long long*>(dci + 2);
+    long long* dnear = dcount + T;
+    uint32_t* rows = reinterpret_cast<uint32_t*>(dnear + T);
+
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dkeys, hk.data(), (size_t)K * 8, cudaMemcpyHostToDevice, ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dy, hy.data(), (size_t)n * 8, cudaMemcpyHostToDevice, ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dtau, ht.data(), (size_t)T * 8, cudaMemcpyHostToDevice, ctx->stream));
+    FRR_TRY(bits_launch(ctx, seed, exact, 0, (uint64_t)K, dkeys, rows));
+    k_contrasts<<<ceil_div(K, 128), 128, 0, ctx->stream>>>(rows, words, K, obs, n, (int)ctx->n1, dy, da, db);
+    k_tau_grid<<<(unsigned)T, 256, 0, ctx->stream>>>(da, db, K, obs, dtau, dcount, dp, dnear);
+    k_interval<<<1, 1, 0, ctx->stream>>>(dp, dtau, T, alpha, dci);
+    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    FRR_TRY(copy_out(ctx, p_out, dp, (size_t)T * sizeof(double)));
+    if (count_out) FRR_TRY(copy_out(ctx, count_out, dcount, (size_t)T * sizeof(long long)));
+    double ci[2];
+    FRR_TRY(copy_out(ctx, ci, dci, 2 * sizeof(double)));
+    if (ci_lo) *ci_lo = ci[0];
+    if (ci_hi) *ci_hi = ci[1];
+    return FRR_OK;
+}
+
+}  // namespace frr

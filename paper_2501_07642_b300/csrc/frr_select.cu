@@ -1,0 +1,637 @@
+// frr_select.cu -- acceptance of the best q fraction (or of M <= a) with an exact
+// answer, plus key replay helpers.
+//
+// Sec. 2.2 keeps the draws in the accepted q-quantile of M (or M <= a); the
+// library breaks ties by the lower draw index. The bulk paths give an
+// approximate M_hat with a per-draw error band |M_hat - M| <= band(M_hat).
+// Selection therefore runs in two stages:
+//   1. streaming filter (one CTA): over the chunk's M_hat plus the retained
+//      set, find the K-th smallest M_hat, form the cut T = U(M_(K)) with
+//      U(m) = m + band(m), and keep every draw whose lower bound
+//      L(m) = m - band(m) is <= T. Any draw among the true K best has
+//      L <= M <= M_(K)(true) <= T, so the retained set always contains them.
+//   2. exact-sum recheck of the retained draws (fixed-point Zc, exact int64
+//      sums, FP64 assembly), then the K smallest (M64, draw index), reported
+//      in ascending draw order.
+#include "frr_internal.cuh"
+#include "frr_gen.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace frr {
+namespace {
+
+// ------------------------------------------------------------------ replay --
+template <int KB>
+__global__ void k_bits(uint64_t seed, int exact, const uint64_t* __restrict__ binom, int n, int n1, uint64_t first,
+                       uint64_t count, const uint64_t* __restrict__ draws, uint32_t* __restrict__ rows)
+{
+    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= count) return;
+    const uint64_t draw = draws ? draws[w] : first + w;
+    warp_draw_bits<KB>(exact != 0, seed, draw, n, n1, binom, rows + w * (4 * KB), lane);
+}
+
+__global__ void k_unpack(const uint32_t* __restrict__ rows, int words, uint64_t count, int n, uint8_t* __restrict__ w)
+{
+    const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= count * (uint64_t)n) return;
+    const uint64_t b = idx / n;
+    const int i = (int)(idx % n);
+    const int p = kpos_of_unit(i);
+    w[idx] = (uint8_t)((rows[b * words + (p >> 5)] >> (p & 31)) & 1u);
+}
+
+// ----------------------------------------------------------------- recheck --
+// Exact treated sums S_T,j = sum_{i in T} Q_ij in int64 for G draws x 128 columns
+// per CTA; S_C,j = S_all,j - S_T,j exactly, so an assignment and its complement
+// swap (S_T, S_C). Per column: Delta_j = S_T 2^-q / n1 - S_C 2^-q / n0 (FP64) and the
+// CTA writes the fixed-order partial sum of Delta_j^2 over its columns.
+constexpr int RG = 8;     // draws per CTA
+constexpr int RCOLS = 128;
+
+template <int KB>
+__global__ void __launch_bounds__(RCOLS)
+k_recheck(const long long* __restrict__ Q, const long long* __restrict__ Qsum, const int* __restrict__ qexp, int d,
+          int kused, int n, int n1, uint64_t seed, int exact, const uint64_t* __restrict__ binom,
+          const uint64_t* __restrict__ draws, int64_t count, double* __restrict__ part, int ncb)
+{
+    constexpr int W = 4 * KB;
+    __shared__ uint32_t rows[RG][W];
+    __shared__ double red[RCOLS / 32][RG];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g0 = (int64_t)blockIdx.x * RG;
+    for (int g = warp; g < RG; g += RCOLS / 32) {
+        if (g0 + g < count) warp_draw_bits<KB>(exact != 0, seed, draws[g0 + g], n, n1, binom, rows[g], lane);
+        else for (int q = lane; q < W; q += 32) rows[g][q] = 0u;
+    }
+    __syncthreads();
+    const int j = blockIdx.y * RCOLS + threadIdx.x;
+    double part_g[RG];
+#pragma unroll
+    for (int g = 0; g < RG; ++g) part_g[g] = 0.0;
+    if (j < d) {
+        long long acc[RG];
+#pragma unroll
+        for (int g = 0; g < RG; ++g) acc[g] = 0;
+        for (int m = 0; m < kused / 32; ++m) {
+            uint32_t bw[RG];
+#pragma unroll
+            for (int g = 0; g < RG; ++g) bw[g] = rows[g][m];
+            const long long* qp = Q + (size_t)(32 * m) * d + j;
+#pragma unroll 8
+            for (int u = 0; u < 32; ++u) {
+                const long long q = qp[(size_t)u * d];
+#pragma unroll
+                for (int g = 0; g < RG; ++g)
+                    if ((bw[g] >> u) & 1u) acc[g] += q;
+            }
+        }
+        const int e = qexp[j];
+        const long long all = Qsum[j];
+        const int n0 = n - n1;
+#pragma unroll
+        for (int g = 0; g < RG; ++g) {
+            const double m1 = __ddiv_rn(ldexp((double)acc[g], -e), (double)n1);
+            const double m0 = __ddiv_rn(ldexp((double)(all - acc[g]), -e), (double)n0);
+            const double dl = __dsub_rn(m1, m0);
+            part_g[g] = __dmul_rn(dl, dl);
+        }
+    }
+    // fixed-order block reduction: warp butterfly, then warps in order
+#pragma unroll
+    for (int g = 0; g < RG; ++g) {
+        double v = part_g[g];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, off));
+        if (lane == 0) red[warp][g] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < RG) {
+        const int g = threadIdx.x;
+        double v = 0.0;
+        for (int w = 0; w < RCOLS / 32; ++w) v = __dadd_rn(v, red[w][g]);
+        if (g0 + g < count) part[(g0 + g) * ncb + blockIdx.y] = v;
+    }
+}
+
+__global__ void k_recheck_sum(const double* __restrict__ part, int ncb, int64_t count, double scale,
+                              double* __restrict__ M64)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= count) return;
+    double s = 0.0;
+    for (int b = 0; b < ncb; ++b) s = __dadd_rn(s, part[c * ncb + b]);
+    M64[c] = __dmul_rn(scale, s);
+}
+
+// ---------------------------------------------------------- stream filter --
+constexpr int SNT = 1024;
+
+struct CutParams {
+    double lin, quad, rel, safety;
+};
+
+__device__ __forceinline__ double lower_bound_m(const CutParams& cp, float v)
+{
+    const double m = (double)v;
+    return m - band_value(cp.lin, cp.quad, cp.rel, cp.safety, m);
+}
+
+// largest non-negative float v with L(v) <= T (L(v) <= 0 <= T near 0, increasing after its minimum)
+__device__ float largest_v_below(const CutParams& cp, double T, uint32_t lo_bits)
+{
+    if (!(T < INFINITY)) return INFINITY;
+    uint32_t lo = lo_bits, hi = 0x7f800000u;  // L(lo) <= T holds; L(inf) > T
+    while (hi - lo > 1) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (lower_bound_m(cp, __uint_as_float(mid)) <= T) lo = mid; else hi = mid;
+    }
+    return __uint_as_float(lo);
+}
+
+__device__ __forceinline__ uint32_t elem_bits(const float* a, int64_t na, const float* b, int64_t e)
+{
+    return __float_as_uint(e < na ? a[e] : b[e - na]);
+}
+
+// Block-wide exclusive scan of one int per thread (SNT threads). Returns the
+// exclusive prefix; *total gets the block sum.
+__device__ int block_scan_excl(int v, int* ws, int* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int s = ws[lane];
+        int si = s;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(kFull, si, off);
+            if (lane >= off) si += y;
+        }
+        ws[lane] = si - s;
+        if (lane == 31) ws[32] = si;
+    }
+    __syncthreads();
+    const int res = ws[warp] + incl - v;
+    *total = ws[32];
+    __syncthreads();
+    return res;
+}
+
+// One CTA. Inputs: chunk M_hat (nc entries, draw = first + e) and the retained
+// set (nr entries). q mode (K > 0): find the K-th smallest M_hat over both,
+// tighten the cut; threshold mode (K == 0): the cut is fixed. Writes the kept
+// entries (retained first, then the chunk, each in input order) and the count.
+__global__ void __launch_bounds__(SNT)
+k_stream_filter(const float* __restrict__ chunk, int64_t nc, uint64_t first, const float* __restrict__ rm_in,
+                const uint64_t* __restrict__ ri_in, int64_t nr, int64_t K, CutParams cp, float* __restrict__ cut_io,
+                float* __restrict__ rm_out, uint64_t* __restrict__ ri_out, int64_t cap_out, long long* __restrict__ count_out)
+{
+    __shared__ unsigned hist[2048];
+    __shared__ int ws[33];
+    __shared__ uint32_t s_prefix;
+    __shared__ long long s_k;
+    __shared__ float s_cut;
+    const int64_t N = nc + nr;
+    // chunk first, retained after: element e < nc is chunk[e]
+    if (K > 0 && N > K) {
+        if (threadIdx.x == 0) { s_prefix = 0; s_k = K; }
+        const int shifts[3] = {21, 10, 0};
+        const int widths[3] = {11, 11, 10};
+        for (int pass = 0; pass < 3; ++pass) {
+            for (int i = threadIdx.x; i < 2048; i += SNT) hist[i] = 0;
+            __syncthreads();
+            const int sh = shifts[pass], wd = widths[pass];
+            const uint32_t prefix = s_prefix;
+            const long long k = s_k;  // read before the barriers below; one thread rewrites it after them
+            const int hsh = sh + wd;  // bits above this pass must match the prefix
+            for (int64_t base = 0; base < N; base += SNT) {
+                const int64_t e = base + threadIdx.x;
+                bool take = false;
+                uint32_t dig = 0;
+                if (e < N) {
+                    const uint32_t b = elem_bits(chunk, nc, rm_in, e);
+                    take = (hsh >= 32) ? true : ((b >> hsh) == prefix);
+                    dig = (b >> sh) & ((1u << wd) - 1u);
+                }
+                const unsigned key = take ? dig : 0xffffffffu;
+                const unsigned peers = __match_any_sync(kFull, key);
+                if (take && (__ffs(peers) - 1) == (threadIdx.x & 31)) atomicAdd(&hist[dig], (unsigned)__popc(peers));
+            }
+            __syncthreads();
+            // locate the bin holding rank s_k (1-based) by a block scan over 2048 bins (2 per thread)
+            const int b0 = 2 * threadIdx.x;
+            const int h0 = (int)hist[b0], h1 = (int)hist[b0 + 1];
+            int tot;
+            const int excl = block_scan_excl(h0 + h1, ws, &tot);
+            if (excl < k && k <= excl + h0) {
+                s_prefix = (prefix << wd) | (uint32_t)b0;
+                s_k = k - excl;
+            } else if (excl + h0 < k && k <= excl + h0 + h1) {
+                s_prefix = (prefix << wd) | (uint32_t)(b0 + 1);
+                s_k = k - excl - h0;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const float mk = __uint_as_float(s_prefix);
+            const double T = (double)mk + band_value(cp.lin, cp.quad, cp.rel, cp.safety, (double)mk);
+            const float c = largest_v_below(cp, T, s_prefix);
+            s_cut = fminf(c, *cut_io);
+            *cut_io = s_cut;
+        }
+    } else if (threadIdx.x == 0) {
+        s_cut = *cut_io;
+    }
+    __syncthreads();
+    const float cut = s_cut;
+    // compaction: retained entries first, then the chunk, each in order
+    long long written = 0;
+    for (int64_t base = 0; base < N; base += SNT) {
+        const int64_t e = base + threadIdx.x;  // e < nr: retained[e]; else chunk[e - nr]
+        int keep = 0;
+        float v = 0.f;
+        uint64_t idx = 0;
+        if (e < N) {
+            if (e < nr) { v = rm_in[e]; idx = ri_in[e]; }
+            else { v = chunk[e - nr]; idx = first + (uint64_t)(e - nr); }
+            keep = (v <= cut) ? 1 : 0;
+        }
+        int tot;
+        const int pos = block_scan_excl(keep, ws, &tot);
+        if (keep && written + pos < cap_out) {
+            rm_out[written + pos] = v;
+            ri_out[written + pos] = idx;
+        }
+        written += tot;
+    }
+    if (threadIdx.x == 0) *count_out = written;
+}
+
+// ---------------------------------------------------------------- ordering --
+// rank_c = #{c' : (M64_c', idx_c') < (M64_c, idx_c)}
+__global__ void k_rank(const double* __restrict__ m, const uint64_t* __restrict__ idx, int64_t r, int* __restrict__ rank)
+{
+    __shared__ double sm[1024];
+    __shared__ uint64_t si[1024];
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double mc = c < r ? m[c] : 0.0;
+    const uint64_t ic = c < r ? idx[c] : 0;
+    int cnt = 0;
+    for (int64_t t0 = 0; t0 < r; t0 += 1024) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < 1024; k += blockDim.x) {
+            if (t0 + k < r) { sm[k] = m[t0 + k]; si[k] = idx[t0 + k]; }
+        }
+        __syncthreads();
+        const int lim = (int)((r - t0) < 1024 ? (r - t0) : 1024);
+        for (int k = 0; k < lim; ++k) cnt += (sm[k] < mc || (sm[k] == mc && si[k] < ic)) ? 1 : 0;
+    }
+    if (c < r) rank[c] = cnt;
+}
+
+// selected (sel[c] != 0) entries go to position #{selected c' : idx_c' < idx_c}
+__global__ void k_place(const double* __restrict__ m, const uint64_t* __restrict__ idx, const int* __restrict__ sel,
+                        int64_t r, uint64_t* __restrict__ keys_out, double* __restrict__ m_out)
+{
+    __shared__ uint64_t si[1024];
+    __shared__ int ss[1024];
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool me = c < r && sel[c];
+    const uint64_t ic = c < r ? idx[c] : 0;
+    int cnt = 0;
+    for (int64_t t0 = 0; t0 < r; t0 += 1024) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < 1024; k += blockDim.x) {
+            if (t0 + k < r) { si[k] = idx[t0 + k]; ss[k] = sel[t0 + k]; }
+        }
+        __syncthreads();
+        const int lim = (int)((r - t0) < 1024 ? (r - t0) : 1024);
+        for (int k = 0; k < lim; ++k) cnt += (ss[k] && si[k] < ic) ? 1 : 0;
+    }
+    if (me) {
+        keys_out[cnt] = ic;
+        m_out[cnt] = m[c];
+    }
+}
+
+__global__ void k_select_flags(const int* __restrict__ rank, const double* __restrict__ m, int64_t r, int64_t K,
+                               int q_mode, double thr, int* __restrict__ sel, double* __restrict__ boundary)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= r) return;
+    sel[c] = q_mode ? (rank[c] < K ? 1 : 0) : (m[c] <= thr ? 1 : 0);
+    if (q_mode) {
+        if (rank[c] == K - 1) boundary[0] = m[c];
+        if (rank[c] == K) boundary[1] = m[c];
+    }
+}
+
+__global__ void k_count_sel(const int* __restrict__ sel, int64_t r, long long* __restrict__ out)
+{
+    __shared__ int ws[33];
+    long long total = 0;
+    for (int64_t base = 0; base < r; base += SNT) {
+        const int64_t e = base + threadIdx.x;
+        int t;
+        block_scan_excl(e < r ? sel[e] : 0, ws, &t);
+        total += t;
+    }
+    if (threadIdx.x == 0) *out = total;
+}
+
+template <int KB>
+frr_status launch_bits_kb(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t count,
+                          const uint64_t* draws, uint32_t* rows)
+{
+    const uint64_t threads = count * 32;
+    k_bits<KB><<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(seed, exact ? 1 : 0, ctx->binom, (int)ctx->n,
+                                                                          (int)ctx->n1, first, count, draws, rows);
+    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    return FRR_OK;
+}
+
+template <int KB>
+frr_status launch_recheck_kb(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws, int64_t count,
+                             double* part, int ncb)
+{
+    dim3 grid((unsigned)((count + RG - 1) / RG), (unsigned)ncb);
+    k_recheck<KB><<<grid, RCOLS, 0, ctx->stream>>>(ctx->Q, ctx->Qsum, ctx->qexp, (int)ctx->d, ctx->kused, (int)ctx->n,
+                                                   (int)ctx->n1, seed, exact ? 1 : 0, ctx->binom, draws, count, part, ncb);
+    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    return FRR_OK;
+}
+
+}  // namespace
+
+frr_status bits_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t count,
+                       const uint64_t* draws, uint32_t* rows)
+{
+    if (count == 0) return FRR_OK;
+    switch (ctx->kb) {
+        case 1: return launch_bits_kb<1>(ctx, seed, exact, first, count, draws, rows);
+        case 2: return launch_bits_kb<2>(ctx, seed, exact, first, count, draws, rows);
+        case 4: return launch_bits_kb<4>(ctx, seed, exact, first, count, draws, rows);
+        case 8: return launch_bits_kb<8>(ctx, seed, exact, first, count, draws, rows);
+        case 16: return launch_bits_kb<16>(ctx, seed, exact, first, count, draws, rows);
+        default: return FRR_E_UNSUPPORTED;
+    }
+}
+
+frr_status unpack_launch(frr_ctx* ctx, const uint32_t* rows, uint64_t count, uint8_t* w)
+{
+    if (count == 0) return FRR_OK;
+    const uint64_t tot = count * (uint64_t)ctx->n;
+    k_unpack<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(rows, 4 * ctx->kb, count, (int)ctx->n, w);
+    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    return FRR_OK;
+}
+
+frr_status recheck_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws, int64_t count, double* M64)
+{
+    if (count <= 0) return FRR_OK;
+    const int ncb = ceil_div(ctx->d, RCOLS);
+    FRR_TRY(ensure_device(ctx, &ctx->misc2, &ctx->misc2_bytes, (size_t)count * ncb * sizeof(double)));
+    double* part = static_cast<double*>(ctx->misc2);
+    frr_status s;
+    switch (ctx->kb) {
+        case 1: s = launch_recheck_kb<1>(ctx, seed, exact, draws, count, part, ncb); break;
+        case 2: s = launch_recheck_kb<2>(ctx, seed, exact, draws, count, part, ncb); break;
+        case 4: s = launch_recheck_kb<4>(ctx, seed, exact, draws, count, part, ncb); break;
+        case 8: s = launch_recheck_kb<8>(ctx, seed, exact, draws, count, part, ncb); break;
+        case 16: s = launch_recheck_kb<16>(ctx, seed, exact, draws, count, part, ncb); break;
+        default: return FRR_E_UNSUPPORTED;
+    }
+    FRR_TRY(s);
+    const double scale = ((double)ctx->n1 * (double)ctx->n0) / (double)ctx->n;
+    k_recheck_sum<<<ceil_div(count, 256), 256, 0, ctx->stream>>>(part, ncb, count, scale, M64);
+    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    return FRR_OK;
+}
+
+frr_status balance_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout)
+{
+    if (ctx->opts.precision == FRR_F32) return balance_f32_launch(ctx, seed, exact, first, B, Mout);
+    return balance_tc_launch(ctx, seed, exact, first, B, Mout);
+}
+
+// ------------------------------------------------------------- streaming --
+namespace {
+constexpr uint64_t kChunkMax = 1ull << 22;
+
+CutParams cut_params(const frr_ctx* ctx)
+{
+    const BandConsts& b = band_of(ctx);
+    return CutParams{b.lin, b.quad, b.rel, ctx->opts.band_safety};
+}
+
+frr_status ensure_retained(frr_ctx* ctx, int which, int64_t entries)
+{
+    FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->ret_idx[which]), &ctx->ret_bytes_idx[which],
+                          (size_t)entries * sizeof(uint64_t)));
+    FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->ret_m[which]), &ctx->ret_bytes_m[which],
+                          (size_t)entries * sizeof(float)));
+    return FRR_OK;
+}
+
+double host_lower_bound(const frr_ctx* ctx, float v)
+{
+    const BandConsts& b = band_of(ctx);
+    return (double)v - band_value(b.lin, b.quad, b.rel, ctx->opts.band_safety, (double)v);
+}
+
+float host_threshold_cut(const frr_ctx* ctx, double a)
+{
+    // largest float v >= 0 with L(v) <= a (same bisection as the device)
+    if (!(a < INFINITY)) return INFINITY;
+    uint32_t lo = 0, hi = 0x7f800000u;
+    float flo; memcpy(&flo, &lo, 4);
+    if (host_lower_bound(ctx, flo) > a) return -1.0f;  // a < L(0): nothing can pass
+    while (hi - lo > 1) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        float f; memcpy(&f, &mid, 4);
+        if (host_lower_bound(ctx, f) <= a) lo = mid; else hi = mid;
+    }
+    float r; memcpy(&r, &lo, 4);
+    return r;
+}
+}  // namespace
+
+frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold, uint64_t total)
+{
+    StreamState& st = ctx->st;
+    st = StreamState{};
+    st.active = true;
+    st.exact = (seed == FRR_EXACT_SEED);
+    st.seed = seed;
+    st.q_mode = !isnan(q);
+    st.q = q;
+    st.threshold = threshold;
+    st.total = total;
+    if (st.q_mode) {
+        const double qb = q * (double)total;
+        double k = ceil(qb - 1e-9 * qb);
+        if (k < 1.0) k = 1.0;
+        if (k > (double)total) k = (double)total;
+        st.K = (int64_t)k;
+        st.cut = INFINITY;
+    } else {
+        st.K = 0;
+        st.cut = host_threshold_cut(ctx, threshold);
+    }
+    st.retained = 0;
+    ctx->ret_cur = 0;
+    const double ms_init = ctx->stats.ms_init;
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->dev_counters + 8, &st.cut, sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->stats.ms_init = ms_init;
+    ctx->stats.boundary_gap_rel = NAN;
+    return FRR_OK;
+}
+
+frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B)
+{
+    StreamState& st = ctx->st;
+    if (!st.active) return FRR_E_STATE;
+    if (B == 0) return FRR_OK;
+    if (st.seen + B > st.total) return FRR_E_RANGE;
+    float* cut_dev = reinterpret_cast<float*>(ctx->dev_counters + 8);
+    long long* count_dev = reinterpret_cast<long long*>(ctx->dev_counters);
+    const CutParams cp = cut_params(ctx);
+    for (uint64_t off = 0; off < B; off += kChunkMax) {
+        const uint64_t bc = std::min<uint64_t>(kChunkMax, B - off);
+        FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->Mhat), &ctx->Mhat_bytes, bc * sizeof(float)));
+        cudaEventRecord(ctx->ev[0], ctx->stream);
+        FRR_TRY(balance_launch(ctx, st.seed, st.exact, first + off, bc, ctx->Mhat));
+        cudaEventRecord(ctx->ev[1], ctx->stream);
+        const int in = ctx->ret_cur, out = 1 - in;
+        // worst case every entry is kept; grow the output side first time it could overflow
+        int64_t cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
+        const int64_t want = std::min<int64_t>(st.retained + (int64_t)bc, std::max<int64_t>(4 * st.K + 65536, 1 << 20));
+        if (cap < want) {
+            FRR_TRY(ensure_retained(ctx, out, want));
+            cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
+        }
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            k_stream_filter<<<1, SNT, 0, ctx->stream>>>(ctx->Mhat, (int64_t)bc, first + off, ctx->ret_m[in],
+                                                       ctx->ret_idx[in], st.retained, st.q_mode ? st.K : 0, cp, cut_dev,
+                                                       ctx->ret_m[out], ctx->ret_idx[out], cap, count_dev);
+            FRR_CUDA_TRY(ctx, cudaGetLastError());
+            long long kept = 0;
+            FRR_CUDA_TRY(ctx, cudaMemcpyAsync(&kept, count_dev, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+            FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            if (kept <= cap) {
+                st.retained = kept;
+                break;
+            }
+            // the cut is monotone, so re-running with a larger output buffer gives the same set
+            FRR_TRY(ensure_retained(ctx, out, kept));
+            cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
+            if (attempt == 1) return FRR_E_CAPACITY;
+        }
+        cudaEventRecord(ctx->ev[2], ctx->stream);
+        FRR_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev[2]));
+        float t1 = 0.f, t2 = 0.f;
+        cudaEventElapsedTime(&t1, ctx->ev[0], ctx->ev[1]);
+        cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
+        ctx->stats.ms_balance += t1;
+        ctx->stats.ms_select += t2;
+        ctx->ret_cur = out;
+    }
+    st.seen += B;
+    ctx->stats.draws += (int64_t)B;
+    return FRR_OK;
+}
+
+frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out)
+{
+    StreamState& st = ctx->st;
+    if (!st.active) return FRR_E_STATE;
+    if (st.seen != st.total) return FRR_E_STATE;
+    const int64_t r = st.retained;
+    const int cur = ctx->ret_cur;
+    cudaEventRecord(ctx->ev[3], ctx->stream);
+    // scratch: M64 (r), M64 out (r), keys out (r), boundary (2 doubles), rank (r), sel (r)
+    const size_t need = (size_t)r * (3 * sizeof(double) + 2 * sizeof(int)) + 2 * sizeof(double);
+    FRR_TRY(ensure_device(ctx, &ctx->misc, &ctx->misc_bytes, need));
+    char* base = static_cast<char*>(ctx->misc);
+    double* m64 = reinterpret_cast<double*>(base);
+    double* mout = m64 + r;
+    uint64_t* kout = reinterpret_cast<uint64_t*>(mout + r);
+    double* boundary = reinterpret_cast<double*>(kout + r);
+    int* rank = reinterpret_cast<int*>(boundary + 2);
+    int* sel = rank + r;
+    long long* nsel_dev = reinterpret_cast<long long*>(ctx->dev_counters + 4);
+    long long nsel = 0;
+    if (r > 0) {
+        FRR_TRY(recheck_launch(ctx, st.seed, st.exact, ctx->ret_idx[cur], r, m64));
+        const double nanv = NAN;
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(boundary, &nanv, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(boundary + 1, &nanv, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        k_rank<<<ceil_div(r, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], r, rank);
+        k_select_flags<<<ceil_div(r, 256), 256, 0, ctx->stream>>>(rank, m64, r, st.K, st.q_mode ? 1 : 0, st.threshold,
+                                                                  sel, boundary);
+        k_count_sel<<<1, SNT, 0, ctx->stream>>>(sel, r, nsel_dev);
+        k_place<<<ceil_div(r, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], sel, r, kout, mout);
+        FRR_CUDA_TRY(ctx, cudaGetLastError());
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(&nsel, nsel_dev, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    cudaEventRecord(ctx->ev[4], ctx->stream);
+    FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ctx->ev[3], ctx->ev[4]);
+    ctx->stats.ms_recheck += t;
+    *K_out = nsel;
+    st.active = false;
+
+    // statistics of the band model over the re-checked draws (host copies of r values)
+    ctx->stats.candidates = r;
+    ctx->stats.accepted = nsel;
+    if (r > 0) {
+        std::vector<double> hm(r), hb(2);
+        std::vector<float> hf(r);
+        std::vector<int> hs(r);
+        FRR_CUDA_TRY(ctx, cudaMemcpy(hm.data(), m64, r * sizeof(double), cudaMemcpyDeviceToHost));
+        FRR_CUDA_TRY(ctx, cudaMemcpy(hf.data(), ctx->ret_m[cur], r * sizeof(float), cudaMemcpyDeviceToHost));
+        FRR_CUDA_TRY(ctx, cudaMemcpy(hs.data(), sel, r * sizeof(int), cudaMemcpyDeviceToHost));
+        FRR_CUDA_TRY(ctx, cudaMemcpy(hb.data(), boundary, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+        const BandConsts& b = band_of(ctx);
+        double mre = 0, meb = 0, thr = -INFINITY;
+        int viol = 0;
+        for (int64_t c = 0; c < r; ++c) {
+            const double err = fabs((double)hf[c] - hm[c]);
+            const double band = band_value(b.lin, b.quad, b.rel, ctx->opts.band_safety, (double)hf[c]);
+            if (hm[c] > 0) mre = std::max(mre, err / hm[c]);
+            if (band > 0) meb = std::max(meb, err / band);
+            if (err > band) ++viol;
+            if (hs[c]) thr = std::max(thr, hm[c]);
+        }
+        ctx->stats.max_rel_err = mre;
+        ctx->stats.max_err_over_band = meb;
+        ctx->stats.band_violations = viol;
+        ctx->stats.threshold_m64 = nsel > 0 ? thr : NAN;
+        ctx->stats.band_at_threshold = nsel > 0 ? band_value(b.lin, b.quad, b.rel, ctx->opts.band_safety, thr) : NAN;
+        if (st.q_mode && !isnan(hb[0]) && !isnan(hb[1])) {
+            ctx->stats.boundary_gap_rel = (hb[1] - hb[0]) / hb[0];
+            ctx->stats.parity_at_risk = ctx->stats.boundary_gap_rel < 1e-11 ? 1 : 0;
+        }
+    }
+    if (nsel > cap) return FRR_E_CAPACITY;
+    if (nsel > 0) {
+        FRR_TRY(copy_out(ctx, keys_out, kout, (size_t)nsel * sizeof(uint64_t)));
+        if (M64_out) FRR_TRY(copy_out(ctx, M64_out, mout, (size_t)nsel * sizeof(double)));
+    }
+    return FRR_OK;
+}
+
+}  // namespace frr
