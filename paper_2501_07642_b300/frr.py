@@ -1,0 +1,255 @@
+"""Thin ctypes binding of libfrr (include/frr.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts numpy
+arrays / torch tensors to pointers, checks status codes and raises
+``FrrError``. If libfrr.so is missing the import fails: there is no fallback.
+
+Host buffers are numpy arrays; device buffers are torch CUDA tensors (their
+``data_ptr()`` is passed through). The function names are those of the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from pathlib import Path
+
+import numpy as np
+
+LIB_PATH = Path(__file__).resolve().parent / "libfrr.so"
+
+FRR_OK = 0
+STATUS = {0: "FRR_OK", -1: "FRR_E_ARG", -2: "FRR_E_DEGENERATE", -3: "FRR_E_CUDA", -4: "FRR_E_NOMEM",
+          -5: "FRR_E_TIMEOUT", -6: "FRR_E_CAPACITY", -7: "FRR_E_RANGE", -8: "FRR_E_STATE",
+          -9: "FRR_E_UNSUPPORTED"}
+FRR_SPLIT_BF16, FRR_F32 = 0, 1
+FRR_CHOL, FRR_RIDGE, FRR_DIAG = 0, 1, 2
+FRR_EXACT_SEED = (1 << 64) - 1
+PRECISION = {"split_bf16": FRR_SPLIT_BF16, "f32": FRR_F32}
+WHITEN = {"chol": FRR_CHOL, "ridge": FRR_RIDGE, "diag": FRR_DIAG}
+
+
+class FrrError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"{where}: {self.name} ({strerror(status)})")
+
+
+class frr_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("whiten", ctypes.c_int), ("ridge", ctypes.c_double),
+                ("band_safety", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
+
+
+class frr_stats(ctypes.Structure):
+    _fields_ = [("draws", ctypes.c_int64), ("candidates", ctypes.c_int64), ("accepted", ctypes.c_int64),
+                ("threshold_m64", ctypes.c_double), ("band_at_threshold", ctypes.c_double),
+                ("max_rel_err", ctypes.c_double), ("max_err_over_band", ctypes.c_double),
+                ("boundary_gap_rel", ctypes.c_double), ("parity_at_risk", ctypes.c_int),
+                ("band_violations", ctypes.c_int), ("ms_init", ctypes.c_double), ("ms_balance", ctypes.c_double),
+                ("ms_select", ctypes.c_double), ("ms_recheck", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise ImportError(f"{LIB_PATH} is not built (python -m paper_2501_07642_b300.build)")
+        L = ctypes.CDLL(str(LIB_PATH))
+        c = ctypes
+        P, U64, I64, D = c.c_void_p, c.c_uint64, c.c_int64, c.c_double
+        sig = {
+            "frr_default_opts": (None, [P]),
+            "frr_strerror": (c.c_char_p, [c.c_int]),
+            "frr_init": (c.c_int, [P, P, I64, I64, I64, P]),
+            "frr_destroy": (None, [P]),
+            "frr_balance": (c.c_int, [P, U64, U64, U64, P]),
+            "frr_balance_exact": (c.c_int, [P, U64, U64, P]),
+            "frr_select": (c.c_int, [P, U64, U64, U64, D, D, P, P, I64, P]),
+            "frr_stream_begin": (c.c_int, [P, U64, D, D, U64]),
+            "frr_stream_chunk": (c.c_int, [P, U64, U64]),
+            "frr_stream_end": (c.c_int, [P, P, P, I64, P]),
+            "frr_assignment": (c.c_int, [P, U64, U64, P]),
+            "frr_assignments": (c.c_int, [P, U64, U64, U64, P]),
+            "frr_recheck": (c.c_int, [P, U64, P, I64, P]),
+            "frr_randtest": (c.c_int, [P, U64, P, I64, U64, P, P, I64, D, P, P, P, P]),
+            "frr_whitened": (c.c_int, [P, P]),
+            "frr_last_stats": (c.c_int, [P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != FRR_OK:
+        raise FrrError(st, where)
+
+
+def strerror(status: int) -> str:
+    return lib().frr_strerror(status).decode()
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)!r}")
+
+
+def frr_default_opts() -> frr_opts:
+    o = frr_opts()
+    lib().frr_default_opts(ctypes.byref(o))
+    return o
+
+
+class Context:
+    """Owns one frr_ctx (frr_init ... frr_destroy)."""
+
+    def __init__(self, X, n1: int, precision: str = "split_bf16", whiten: str = "chol", ridge: float = 0.1,
+                 band_safety: float = 2.0, stream=None):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        n, d = X.shape
+        o = frr_default_opts()
+        o.precision = PRECISION[precision]
+        o.whiten = WHITEN[whiten]
+        o.ridge = float(ridge)
+        o.band_safety = float(band_safety)
+        o.cuda_stream = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        h = ctypes.c_void_p()
+        _check(lib().frr_init(ctypes.byref(h), X.ctypes.data, n, d, int(n1), ctypes.byref(o)), "frr_init")
+        self.handle = h
+        self.n, self.d, self.n1 = n, d, int(n1)
+        self.precision, self.whiten = precision, whiten
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().frr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def frr_init(X, n1: int, **kw) -> Context:
+    return Context(X, n1, **kw)
+
+
+def frr_destroy(ctx: Context):
+    ctx.close()
+
+
+def frr_balance(ctx: Context, seed: int, first_draw: int, B: int, M_out=None):
+    out = np.empty(B, dtype=np.float32) if M_out is None else M_out
+    _check(lib().frr_balance(ctx.handle, seed, first_draw, B, _ptr(out)), "frr_balance")
+    return out
+
+
+def frr_balance_exact(ctx: Context, first_rank: int, B: int, M_out=None):
+    out = np.empty(B, dtype=np.float32) if M_out is None else M_out
+    _check(lib().frr_balance_exact(ctx.handle, first_rank, B, _ptr(out)), "frr_balance_exact")
+    return out
+
+
+def _q_thr(q, threshold):
+    return (math.nan if q is None else float(q)), (math.nan if threshold is None else float(threshold))
+
+
+def frr_select(ctx: Context, seed: int, first_draw: int, B: int, q=None, threshold=None, cap=None,
+               keys_out=None, M64_out=None):
+    """Returns (keys, M64) as numpy arrays (or the given output buffers, trimmed)."""
+    qq, tt = _q_thr(q, threshold)
+    if cap is None:
+        cap = B if keys_out is None else len(keys_out)
+    keys = np.empty(cap, dtype=np.uint64) if keys_out is None else keys_out
+    m64 = np.empty(cap, dtype=np.float64) if M64_out is None else M64_out
+    K = ctypes.c_int64()
+    _check(lib().frr_select(ctx.handle, seed, first_draw, B, qq, tt, _ptr(keys), _ptr(m64), cap, ctypes.byref(K)),
+           "frr_select")
+    return keys[:K.value], m64[:K.value]
+
+
+def frr_stream_begin(ctx: Context, seed: int, B_total: int, q=None, threshold=None):
+    qq, tt = _q_thr(q, threshold)
+    _check(lib().frr_stream_begin(ctx.handle, seed, qq, tt, B_total), "frr_stream_begin")
+
+
+def frr_stream_chunk(ctx: Context, first_draw: int, B_chunk: int):
+    _check(lib().frr_stream_chunk(ctx.handle, first_draw, B_chunk), "frr_stream_chunk")
+
+
+def frr_stream_end(ctx: Context, cap: int):
+    keys = np.empty(cap, dtype=np.uint64)
+    m64 = np.empty(cap, dtype=np.float64)
+    K = ctypes.c_int64()
+    _check(lib().frr_stream_end(ctx.handle, _ptr(keys), _ptr(m64), cap, ctypes.byref(K)), "frr_stream_end")
+    return keys[:K.value], m64[:K.value]
+
+
+def frr_assignment(ctx: Context, seed: int, key: int, w_out=None):
+    w = np.empty(ctx.n, dtype=np.uint8) if w_out is None else w_out
+    _check(lib().frr_assignment(ctx.handle, seed, key, _ptr(w)), "frr_assignment")
+    return w
+
+
+def frr_assignments(ctx: Context, seed: int, first_draw: int, count: int, w_out=None):
+    w = np.empty((count, ctx.n), dtype=np.uint8) if w_out is None else w_out
+    _check(lib().frr_assignments(ctx.handle, seed, first_draw, count, _ptr(w)), "frr_assignments")
+    return w
+
+
+def frr_recheck(ctx: Context, seed: int, draws, M64_out=None):
+    dr = np.ascontiguousarray(draws, dtype=np.uint64) if isinstance(draws, (list, tuple, np.ndarray)) else draws
+    out = np.empty(len(dr), dtype=np.float64) if M64_out is None else M64_out
+    _check(lib().frr_recheck(ctx.handle, seed, _ptr(dr), len(dr), _ptr(out)), "frr_recheck")
+    return out
+
+
+def frr_randtest(ctx: Context, seed: int, keys, obs_key: int, Y, tau, alpha: float = 0.05):
+    """Returns dict(p, count, ci_lo, ci_hi)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64) if isinstance(keys, (list, tuple, np.ndarray)) else keys
+    Y = np.ascontiguousarray(Y, dtype=np.float64) if isinstance(Y, (list, tuple, np.ndarray)) else Y
+    tau = np.ascontiguousarray(tau, dtype=np.float64) if isinstance(tau, (list, tuple, np.ndarray)) else tau
+    T = len(tau)
+    p = np.empty(T, dtype=np.float64)
+    cnt = np.empty(T, dtype=np.int64)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(lib().frr_randtest(ctx.handle, seed, _ptr(keys), len(keys), obs_key, _ptr(Y), _ptr(tau), T, alpha,
+                              _ptr(p), _ptr(cnt), ctypes.byref(lo), ctypes.byref(hi)), "frr_randtest")
+    return {"p": p, "count": cnt, "ci_lo": lo.value, "ci_hi": hi.value}
+
+
+def frr_whitened(ctx: Context):
+    z = np.empty((ctx.n, ctx.d), dtype=np.float64)
+    _check(lib().frr_whitened(ctx.handle, z.ctypes.data), "frr_whitened")
+    return z
+
+
+def frr_last_stats(ctx: Context) -> dict:
+    s = frr_stats()
+    _check(lib().frr_last_stats(ctx.handle, ctypes.byref(s)), "frr_last_stats")
+    return s.as_dict()
