@@ -1,0 +1,311 @@
+"""Benchmark of the balance-check hot path: balance-checked assignments per second.
+
+Workload: n = 1000 units, n1 = 500, d = 1000 covariates (half N(0,1), a quarter
+Bernoulli(0.3), a quarter lognormal(0,1), standardised), ridge-whitened, and one
+step = one accepted pool of B = 200,000 Philox draws at q = 1e-3 (K = 200):
+regenerate every assignment, score it, stream the selection, re-check the
+candidates exactly and return the accepted keys. Inputs are synthetic.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl frr|reference]
+
+``--impl reference`` times the FP64 CPU oracle on this machine's cores on a
+bounded sample of the same workload (the paper ships no reusable reference
+program; the oracle is the reference arm). Under torchrun every rank runs its
+own draw ranges (weak scaling, no collective on the data path); rank 0 prints
+one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "balance-checked assignments/s at n=d=1000; split-BF16 vs FP32 path, same B300"
+WORKLOAD = "precision_n1000_d1000"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return json.loads(p.read_text()), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.tmp.flush()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            for line in Path(self.tmp.name).read_text().splitlines():
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------- CPU oracle --
+def oracle_zc(X):
+    from oracle import oracle as O
+    Zc, *_ = O.prep(X, "ridge", 0.1)
+    return Zc
+
+
+def oracle_rate(Zc, n1, seed, target_s: float, first: int = 0):
+    """Oracle draws/s on a bounded sample sized to take about target_s seconds."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    O.select(Zc, n1, seed, first, 64, q=1e-3)
+    per = (time.perf_counter() - t0) / 64
+    S = int(max(64, min(200_000, target_s / max(per, 1e-7))))
+    t0 = time.perf_counter()
+    O.select(Zc, n1, seed, first + 64, S, q=1e-3)
+    dt = time.perf_counter() - t0
+    return S / dt, S, O.threads()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2501_07642_b300.workloads import workload
+    w = workload(WORKLOAD)
+    Zc = oracle_zc(w.covariates())
+    rates, samples = [], []
+    for i in range(args.warmup + args.steps):
+        r, S, cores = oracle_rate(Zc, w.n1, w.philox_seed, args.ref_step_s, first=i * 1_000_000)
+        if i >= args.warmup:
+            rates.append(r)
+            samples.append(S)
+    value = len(rates) / sum(1.0 / r for r in rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "draws/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(samples) / len(samples) / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": w.n, "n1": w.n1, "d": w.d, "q": w.q, "whiten": "ridge 0.1",
+                       "draws_per_step": int(statistics.median(samples))},
+            "cpu_baseline": {"value": value, "unit": "draws/s", "cores": cores, "kind": "oracle",
+                             "sample": f"FP64 oracle select (M of every draw + sort) on {int(statistics.median(samples))} "
+                                       f"draws per step of the {WORKLOAD} workload"},
+            "e2e": {"value": value, "unit": "draws/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- GPU --
+def run_frr(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2501_07642_b300 import frr
+    from paper_2501_07642_b300.workloads import workload
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    w = workload(WORKLOAD)
+    X = w.covariates()
+    B, q = w.draws, w.q
+    K = math.ceil(q * B - 1e-9 * q * B)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    peaks, peak_kind = _peaks()
+
+    precisions = [p for p in args.precision.split(",") if p]
+    results = {}
+    draw_base = rank * (1 << 40)  # disjoint draw ranges per rank
+    for prec in precisions:
+        try:
+            ctx = frr.Context(X, w.n1, precision=prec, whiten="ridge", ridge=0.1, stream=stream)
+        except frr.FrrError as e:
+            results[prec] = {"error": str(e)}
+            continue
+        keys = torch.empty(K, dtype=torch.int64, device="cuda")
+        m64 = torch.empty(K, dtype=torch.float64, device="cuda")
+        try:
+            frr.frr_select(ctx, w.philox_seed, draw_base, B, q=q, keys_out=keys, M64_out=m64, cap=K)
+        except frr.FrrError as e:
+            results[prec] = {"error": str(e)}
+            ctx.close()
+            continue
+        step_ms, bal_ms = [], []
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            t_wall = time.perf_counter()
+            for i in range(args.warmup + args.steps):
+                with torch.cuda.stream(stream):
+                    flush.zero_()  # L2 flush between steps, outside the timed events
+                    ev0.record(stream)
+                first = draw_base + (i + 1) * B
+                frr.frr_select(ctx, w.philox_seed, first, B, q=q, keys_out=keys, M64_out=m64, cap=K)
+                with torch.cuda.stream(stream):
+                    ev1.record(stream)
+                ev1.synchronize()
+                if i >= args.warmup:
+                    step_ms.append(ev0.elapsed_time(ev1))
+                    bal_ms.append(frr.frr_last_stats(ctx)["ms_balance"])
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t_wall
+        stats = frr.frr_last_stats(ctx)
+        total_ms = sum(step_ms)
+        if ws > 1:
+            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        # end to end through the public API with host buffers: upload X from pinned
+        # memory, prepare, select, read the keys back
+        e2e = None
+        if args.e2e:
+            Xp = torch.from_numpy(X).pin_memory().numpy()
+            hk = np.empty(K, dtype=np.uint64)
+            hm = np.empty(K, dtype=np.float64)
+            e2e_t = []
+            for i in range(max(1, args.e2e_steps) + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                c2 = frr.Context(Xp, w.n1, precision=prec, whiten="ridge", ridge=0.1)
+                frr.frr_select(c2, w.philox_seed, draw_base + (1 << 30) + i * B, B, q=q, keys_out=hk, M64_out=hm, cap=K)
+                c2.close()
+                if i > 0:
+                    e2e_t.append(time.perf_counter() - t0)
+            e2e = {"value": ws * B / statistics.median(e2e_t), "unit": "draws/s",
+                   "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(K * 16),
+                   "includes": "frr_init (X upload, FP64 prep) + frr_select + key read-back"}
+        results[prec] = {"value": ws * B * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+                         "ms_balance": statistics.mean(bal_ms), "clocks": clk.summary(), "stats": stats, "e2e": e2e,
+                         "wall_s": wall}
+        ctx.close()
+
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    ok = [p for p in precisions if "value" in results.get(p, {})]
+    if not ok:
+        print(json.dumps({"metric": METRIC, "error": {p: results[p].get("error") for p in precisions}}))
+        sys.exit(1)
+    prim = ok[0]
+    r = results[prim]
+    n, d, n1 = w.n, w.d, w.n1
+    if prim == "split_bf16":
+        flops = 2.0 * 2.0 * n * d  # two BF16 parts, dense 0/1 x Zc per draw (multiply-add = 2)
+        achieved = flops * B / (r["ms_balance"] / 1e3) / 1e12
+        peak = peaks["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_balance_tc", "peak_source": f"bf16_tflops (burst, {peak_kind})",
+                "flop_per_draw": flops}
+        dtype = "bf16"
+    else:
+        # plain ALU bound: n * d predicated FP32 adds per draw on 148 SMs x 128 lanes at the sampled SM clock
+        adds = float(n) * d
+        mhz = r["clocks"]["sm_mhz"] or peaks.get("sm_max_mhz", 2032.0)
+        peak = 148 * 128 * mhz * 1e6 / 1e12  # T adds/s
+        achieved = adds * B / (r["ms_balance"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_balance_f32",
+                "peak_source": f"148 SMs x 128 FP32 lanes x median sampled SM clock {mhz} MHz",
+                "adds_per_draw": adds}
+        dtype = "f32"
+    cpu = None
+    if args.cpu_baseline:
+        rate, S, cores = oracle_rate(oracle_zc(X), n1, w.philox_seed, args.cpu_s)
+        cpu = {"value": rate, "unit": "draws/s", "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle select (M of every draw + sort) on {S} draws of the {WORKLOAD} workload"}
+    line = {"metric": METRIC, "value": r["value"], "unit": "draws/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "n1": n1, "d": d, "draws_per_step": B, "q": q, "K": K,
+                       "whiten": "ridge 0.1", "path": prim, "l2": "flushed (256 MiB write) between timed steps"},
+            "paths": {p: ({"value": results[p]["value"], "ms_per_step": results[p]["ms_per_step"],
+                           "ms_balance": results[p]["ms_balance"]} if "value" in results[p] else results[p])
+                      for p in precisions},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": 8 * args.steps * ws,
+            "clocks": {k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "selection": {k: r["stats"][k] for k in ("candidates", "accepted", "max_rel_err", "max_err_over_band",
+                                                     "band_violations", "parity_at_risk")}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("frr", "reference"), default="frr")
+    ap.add_argument("--precision", default="split_bf16,f32")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-s", type=float, default=12.0)
+    ap.add_argument("--ref-step-s", type=float, default=8.0)
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_frr(args)
+
+
+if __name__ == "__main__":
+    main()
