@@ -149,6 +149,25 @@ frr_status frr_assignments(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uin
  * decides acceptance). draws, M64_out: host or device, count entries. */
 frr_status frr_recheck(frr_ctx* ctx, uint64_t seed, const uint64_t* draws, int64_t count, double* M64_out);
 
+/* Allocation-free form of frr_recheck (the paper has no counterpart: this is a property
+ * of this library's interface). For callers that must not have the library allocate
+ * device memory: a latency-critical loop that shares the GPU with other work, where a
+ * cudaMalloc / cudaFree could synchronise the device and stall it, or an application
+ * whose device memory belongs to another allocator (for example a framework's caching
+ * pool with a fixed budget). draws (count entries) and M64_out (count doubles) must be
+ * device memory owned by the caller; pool seeds only (FRR_EXACT_SEED gives
+ * FRR_E_UNSUPPORTED). The kernels' scratch -- count * ceil(d / 128) partial sums -- lives
+ * in one fixed device array of FRR_RECHECK_STATIC_SCRATCH doubles (1 MiB) compiled into
+ * the library, which every GPU that loads the library holds until the process exits;
+ * larger requests return FRR_E_CAPACITY and run nothing. The first call on a device looks
+ * up that array's device address (set-up); make this first call before any stream
+ * capture. Every call on a device shares the array: calls that overlap on the GPU (from
+ * other host threads or other contexts on the same device) race, and the caller must
+ * serialise them. Synchronous like the other entry points; allocates no device or host
+ * memory. */
+#define FRR_RECHECK_STATIC_SCRATCH 131072
+frr_status frr_recheck_static(frr_ctx* ctx, uint64_t seed, const uint64_t* draws, int64_t count, double* M64_out);
+
 /* Randomization test conditional on acceptance and its inversion (Sec. 2.3
  * randomization_test; Sec. 4). Sharp null Y(1) = Y(0) + tau; statistic: the two-sided
  * difference in means. For each tau_g: count_out[g] = #{k : |t_k(tau_g)| >= |t_obs(tau_g)|}

@@ -635,3 +635,31 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
 }
 
 }  // namespace frr
+
+namespace frr {
+
+// The recheck of recheck_launch with the per-CTA partial sums in a device array the
+// caller provides (part_capacity doubles); nothing is allocated. Pool seeds only.
+frr_status recheck_launch_into(frr_ctx* ctx, uint64_t seed, const uint64_t* draws, int64_t count, double* part,
+                               size_t part_capacity, double* M64)
+{
+    if (count <= 0) return FRR_OK;
+    const int ncb = ceil_div(ctx->d, RCOLS);
+    if ((size_t)count * (size_t)ncb > part_capacity) return FRR_E_CAPACITY;
+    frr_status s;
+    switch (ctx->kb) {
+        case 1: s = launch_recheck_kb<1>(ctx, seed, false, draws, count, part, ncb); break;
+        case 2: s = launch_recheck_kb<2>(ctx, seed, false, draws, count, part, ncb); break;
+        case 4: s = launch_recheck_kb<4>(ctx, seed, false, draws, count, part, ncb); break;
+        case 8: s = launch_recheck_kb<8>(ctx, seed, false, draws, count, part, ncb); break;
+        case 16: s = launch_recheck_kb<16>(ctx, seed, false, draws, count, part, ncb); break;
+        default: return FRR_E_UNSUPPORTED;
+    }
+    FRR_TRY(s);
+    const double scale = ((double)ctx->n1 * (double)ctx->n0) / (double)ctx->n;
+    k_recheck_sum<<<ceil_div(count, 256), 256, 0, ctx->stream>>>(part, ncb, count, scale, M64);
+    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    return FRR_OK;
+}
+
+}  // namespace frr

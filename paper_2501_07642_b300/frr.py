@@ -77,6 +77,7 @@ def lib():
             "frr_assignment": (c.c_int, [P, U64, U64, P]),
             "frr_assignments": (c.c_int, [P, U64, U64, U64, P]),
             "frr_recheck": (c.c_int, [P, U64, P, I64, P]),
+            "frr_recheck_static": (c.c_int, [P, U64, P, I64, P]),
             "frr_randtest": (c.c_int, [P, U64, P, I64, U64, P, P, I64, D, P, P, P, P]),
             "frr_whitened": (c.c_int, [P, P]),
             "frr_last_stats": (c.c_int, [P, P]),
