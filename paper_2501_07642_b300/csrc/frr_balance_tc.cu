@@ -1,12 +1,479 @@
-// frr_balance_tc.cu -- split-BF16 tensor-core balance check (tcgen05 + TMA + TMEM).
+// frr_balance_tc.cu -- split-BF16 tensor-core balance check (tcgen05 + TMA + TMEM), sm_103a.
+//
+// Hotelling T^2 of each draw (Sec. 2.2, 2.3): s_b = w_b^T Zc, M_b = n/(n1 n0) ||s_b||^2.
+// W is 0/1, exact in BF16; Zc is split into BF16 parts hi = bf16(Zc), lo = bf16(Zc - hi),
+// and both products accumulate into one FP32 accumulator: s = W.hi + W.lo.
+//
+// One persistent CTA per SM walks tiles of 128 consecutive draws. Warp roles:
+//   warps 0-3   epilogue: tcgen05.ld of the accumulator (TMEM lane = draw), sum of
+//               squares over the covariate chunks, M_hat written per draw;
+//   warp 4      TMA producer: Zc hi / lo tiles (256 covariates x 64 K positions, 128B
+//               swizzle) into a 4-stage shared-memory ring;
+//   warp 5      TMEM allocator and MMA issuer (one thread): per covariate chunk of
+//               N <= 256 columns, 2 x 4 tcgen05.mma (M=128, K=16) per 64-wide K block
+//               into one of two TMEM accumulators (2 x 256 columns);
+//   warps 6-7   A producer: expand the draws' bit rows into BF16 0/1 K-major tiles
+//               (128 x 64, 128B swizzle, a 256-entry byte -> 8 x bf16 table);
+//   warps 8-13  generation: Philox + warp select (frr_gen.cuh) of the next tile's
+//               128 draws into a double-buffered bit-row buffer.
+// The assignment matrix exists only as bits and BF16 tiles in shared memory.
+// Every mbarrier wait is bounded (about one second); on expiry the CTA records an
+// error word, drains its own TMA copies, frees TMEM and returns.
 #include "frr_internal.cuh"
+#include "frr_gen.cuh"
+
+#include <cuda.h>
 
 namespace frr {
+namespace {
+
+constexpr int kThreads = 448;
+constexpr int kTileM = 128;          // draws per tile = TMEM lanes
+constexpr int kChunkN = 256;         // covariates per accumulator chunk
+constexpr int kKBlock = 64;          // K positions per stage (128 bytes of BF16)
+constexpr int kStagesA = 3;
+constexpr int kBBytes = kChunkN * kKBlock * 2;   // 32 KiB
+constexpr int kABytes = kTileM * kKBlock * 2;    // 16 KiB
+constexpr int kGenWarps = 6;
+constexpr int kExpWarps = 2;
+constexpr unsigned long long kWaitCycles = 1ull << 31;
+
+// ------------------------------------------------------------- PTX helpers --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 TMEM lanes (this warp's quarter) x 32 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Shared-memory descriptor of a K-major tile with 128-byte swizzle: rows of 128 bytes,
+// 8-row groups 1024 bytes apart (stride byte offset), leading byte offset unused.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+struct TcParams {
+    int n, n1, d, kused, nkb, nchunks;
+    float c_M;
+    uint64_t seed;
+    int exact;
+    const uint64_t* binom;
+    uint64_t first, B, tiles;
+    float* Mout;
+    int* err;
+};
+
+// Bounded wait. Returns false (and raises the CTA abort flag) on expiry or abort.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err, int code)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = clock64();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            atomicCAS(err, 0, code);
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
+
+template <int KB, int SB>
+__global__ void __launch_bounds__(kThreads, 1)
+k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, TcParams P)
+{
+    constexpr int W = 4 * KB;  // bit-row words per draw
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* sB = smem;                                    // SB x 32 KiB
+    unsigned char* sA = sB + SB * kBBytes;                       // kStagesA x 16 KiB
+    uint32_t* sBits = reinterpret_cast<uint32_t*>(sA + kStagesA * kABytes);  // 2 x 128 x W
+    uint4* sLut = reinterpret_cast<uint4*>(sBits + 2 * kTileM * W);          // 256 entries
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sLut + 256);
+    uint64_t* b_full = bar;
+    uint64_t* b_empty = b_full + SB;
+    uint64_t* a_full = b_empty + SB;
+    uint64_t* a_empty = a_full + kStagesA;
+    uint64_t* acc_full = a_empty + kStagesA;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* bits_full = acc_empty + 2;
+    uint64_t* bits_empty = bits_full + 2;
+    uint64_t* mma_done = bits_empty + 2;
+    uint32_t* sTmem = reinterpret_cast<uint32_t*>(mma_done + 1);
+    volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // byte -> 8 BF16 values (bit e -> element e is 1.0 or 0.0)
+    for (int b = tid; b < 256; b += kThreads) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            w[i] = (((b >> (2 * i)) & 1) ? 0x3F80u : 0u) | (((b >> (2 * i + 1)) & 1) ? 0x3F800000u : 0u);
+        sLut[b] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    if (tid == 0) {
+        for (int s = 0; s < SB; ++s) { mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); }
+        for (int s = 0; s < kStagesA; ++s) { mbar_init(&a_full[s], kExpWarps); mbar_init(&a_empty[s], 1); }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&acc_full[s], 1);
+            mbar_init(&acc_empty[s], 4);
+            mbar_init(&bits_full[s], kGenWarps);
+            mbar_init(&bits_empty[s], kExpWarps);
+        }
+        mbar_init(mma_done, 1);
+        *sAbort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        tmem_alloc(sTmem, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *sTmem;
+
+    const uint64_t tiles = P.tiles;
+    const int nkb = P.nkb, nch = P.nchunks;
+
+    if (warp == 4) {
+        // ------------------------------------------------------------ TMA --
+        if (lane == 0) {
+            uint32_t bi = 0;
+            bool ok = true;
+            for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x)
+                for (int c = 0; c < nch && ok; ++c)
+                    for (int kb = 0; kb < nkb && ok; ++kb)
+                        for (int part = 0; part < 2 && ok; ++part, ++bi) {
+                            const int s = bi % SB;
+                            const uint32_t ph = (bi / SB) & 1u;
+                            if (!(ok = wait_bar(&b_empty[s], ph ^ 1u, sAbort, P.err, 1))) break;
+                            mbar_arrive_expect_tx(&b_full[s], kBBytes);
+                            tma_load_2d(sB + s * kBBytes, part ? &map_lo : &map_hi, &b_full[s], kb * kKBlock, c * kChunkN);
+                        }
+            if (!ok) {
+                // drain the copies this thread may still have in flight
+                const uint32_t from = bi > (uint32_t)SB ? bi - SB : 0u;
+                for (uint32_t i = from; i < bi; ++i) {
+                    const unsigned long long t0 = clock64();
+                    while (!mbar_try_wait(&b_full[i % SB], (i / SB) & 1u) && clock64() - t0 < kWaitCycles) {}
+                }
+            }
+        }
+    } else if (warp == 5) {
+        // ------------------------------------------------------------ MMA --
+        if (lane == 0) {
+            uint32_t ai = 0, bi = 0, g = 0;
+            bool ok = true;
+            for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                for (int c = 0; c < nch && ok; ++c, ++g) {
+                    const int buf = g & 1;
+                    if (!(ok = wait_bar(&acc_empty[buf], ((g >> 1) & 1u) ^ 1u, sAbort, P.err, 2))) break;
+                    tc_fence_after();
+                    const int rem = P.d - c * kChunkN;
+                    const int N = rem >= kChunkN ? kChunkN : ((rem + 15) / 16) * 16;
+                    const uint32_t idesc = idesc_bf16(kTileM, N);
+                    const uint32_t dt = tmem_base + (uint32_t)(buf * kChunkN);
+                    for (int kb = 0; kb < nkb && ok; ++kb, ++ai) {
+                        const int sa = ai % kStagesA;
+                        if (!(ok = wait_bar(&a_full[sa], (ai / kStagesA) & 1u, sAbort, P.err, 3))) break;
+                        const uint64_t adesc = sdesc_sw128(smem_u32(sA + sa * kABytes));
+                        for (int part = 0; part < 2; ++part, ++bi) {
+                            const int sb = bi % SB;
+                            if (!(ok = wait_bar(&b_full[sb], (bi / SB) & 1u, sAbort, P.err, 4))) break;
+                            tc_fence_after();
+                            const uint64_t bdesc = sdesc_sw128(smem_u32(sB + sb * kBBytes));
+#pragma unroll
+                            for (int k = 0; k < kKBlock / 16; ++k)
+                                umma_bf16(dt, adesc + 2u * k, bdesc + 2u * k, idesc, (kb | part | k) != 0 ? 1u : 0u);
+                            umma_commit(&b_empty[sb]);
+                        }
+                        if (ok) umma_commit(&a_empty[sa]);
+                    }
+                    if (ok) umma_commit(&acc_full[buf]);
+                }
+            }
+            // every MMA this thread issued has finished before TMEM is released
+            umma_commit(mma_done);
+            const unsigned long long t0 = clock64();
+            while (!mbar_try_wait(mma_done, 0) && clock64() - t0 < kWaitCycles) {}
+        }
+    } else if (warp >= 6 && warp < 6 + kExpWarps) {
+        // ------------------------------------------------- A tile producer --
+        const int et = tid - 6 * 32;  // 0..63
+        uint32_t ai = 0;
+        uint32_t it = 0;
+        bool ok = true;
+        for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
+            const int bb = it & 1;
+            if (!(ok = wait_bar(&bits_full[bb], (it >> 1) & 1u, sAbort, P.err, 5))) break;
+            const uint32_t* bits = sBits + bb * kTileM * W;
+            for (int c = 0; c < nch && ok; ++c)
+                for (int kb = 0; kb < nkb; ++kb, ++ai) {
+                    const int s = ai % kStagesA;
+                    if (!(ok = wait_bar(&a_empty[s], ((ai / kStagesA) & 1u) ^ 1u, sAbort, P.err, 6))) break;
+                    unsigned char* tile = sA + s * kABytes;
+#pragma unroll 4
+                    for (int idx = et; idx < kTileM * 8; idx += 32 * kExpWarps) {
+                        const int r = idx >> 3, q = idx & 7;
+                        const uint32_t word = bits[r * W + 2 * kb + (q >> 2)];
+                        const uint32_t byte = (word >> (8 * (q & 3))) & 0xFFu;
+                        *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((q ^ (r & 7)) << 4)) = sLut[byte];
+                    }
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&a_full[s]);
+                }
+            __syncwarp();
+            if (ok && lane == 0) mbar_arrive(&bits_empty[bb]);
+        }
+    } else if (warp >= 6 + kExpWarps) {
+        // ------------------------------------------------------ generation --
+        const int gw = warp - (6 + kExpWarps);
+        uint32_t it = 0;
+        bool ok = true;
+        for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
+            const int bb = it & 1;
+            if (!(ok = wait_bar(&bits_empty[bb], ((it >> 1) & 1u) ^ 1u, sAbort, P.err, 7))) break;
+            uint32_t* bits = sBits + bb * kTileM * W;
+            for (int r = gw; r < kTileM; r += kGenWarps) {
+                const uint64_t off = t * kTileM + r;
+                uint32_t* row = bits + r * W;
+                if (off < P.B) {
+                    warp_draw_bits<KB>(P.exact != 0, P.seed, P.first + off, P.n, P.n1, P.binom, row, lane);
+                } else {
+                    for (int q = lane; q < W; q += 32) row[q] = 0u;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bits_full[bb]);
+        }
+    } else {
+        // ------------------------------------------------------- epilogue --
+        const int ew = warp;  // 0..3: TMEM lanes 32 ew .. 32 ew + 31
+        uint32_t g = 0;
+        bool ok = true;
+        for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+            float sumsq = 0.f;
+            for (int c = 0; c < nch; ++c, ++g) {
+                const int buf = g & 1;
+                if (!(ok = wait_bar(&acc_full[buf], (g >> 1) & 1u, sAbort, P.err, 8))) break;
+                tc_fence_after();
+                const int rem = P.d - c * kChunkN;
+                const int N = rem >= kChunkN ? kChunkN : rem;
+                const uint32_t taddr = tmem_base + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * kChunkN);
+                for (int c0 = 0; c0 < N; c0 += 32) {
+                    uint32_t v[32];
+                    tmem_ld32(taddr + (uint32_t)c0, v);
+                    tmem_wait_ld();
+                    const int lim = N - c0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float x = __uint_as_float(v[j]);
+                        if (j < lim) sumsq = fmaf(x, x, sumsq);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            }
+            const uint64_t off = t * kTileM + 32 * ew + lane;
+            if (ok && off < P.B) P.Mout[off] = P.c_M * sumsq;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, 512);
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* m, const __nv_bfloat16* base, int kpad, int d)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)d};
+    const cuuint64_t strides[1] = {(cuuint64_t)kpad * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {(cuuint32_t)kKBlock, (cuuint32_t)kChunkN};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t smem_bytes(int KB, int SB)
+{
+    const size_t bars = (size_t)(2 * SB + 2 * kStagesA + 9) * 8 + 16;
+    return 1024 + (size_t)SB * kBBytes + (size_t)kStagesA * kABytes + 2ull * kTileM * 4 * KB * 4 + 256 * 16 + bars;
+}
+
+template <int KB, int SB>
+frr_status launch(frr_ctx* ctx, const CUtensorMap& mh, const CUtensorMap& ml, const TcParams& P)
+{
+    const size_t smem = smem_bytes(KB, SB);
+    FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_balance_tc<KB, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned grid = (unsigned)(P.tiles < (uint64_t)ctx->num_sms ? P.tiles : (uint64_t)ctx->num_sms);
+    k_balance_tc<KB, SB><<<grid, kThreads, smem, ctx->stream>>>(mh, ml, P);
+    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    return FRR_OK;
+}
+
+}  // namespace
 
 frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout)
 {
-    (void)ctx; (void)seed; (void)exact; (void)first; (void)B; (void)Mout;
-    return FRR_E_UNSUPPORTED;
+    if (B == 0) return FRR_OK;
+    static thread_local const frr_ctx* cached_ctx = nullptr;
+    static thread_local const void* cached_hi = nullptr;
+    static thread_local CUtensorMap mh, ml;
+    if (cached_ctx != ctx || cached_hi != ctx->Zhi) {
+        if (!make_map(&mh, ctx->Zhi, ctx->kpad, (int)ctx->d) || !make_map(&ml, ctx->Zlo, ctx->kpad, (int)ctx->d))
+            return FRR_E_CUDA;
+        cached_ctx = ctx;
+        cached_hi = ctx->Zhi;
+    }
+    TcParams P;
+    P.n = (int)ctx->n;
+    P.n1 = (int)ctx->n1;
+    P.d = (int)ctx->d;
+    P.kused = ctx->kused;
+    P.nkb = ctx->kused / kKBlock;
+    P.nchunks = ceil_div(ctx->d, kChunkN);
+    P.c_M = (float)ctx->c_M;
+    P.seed = seed;
+    P.exact = exact ? 1 : 0;
+    P.binom = ctx->binom;
+    P.first = first;
+    P.B = B;
+    P.tiles = (B + kTileM - 1) / kTileM;
+    P.Mout = Mout;
+    P.err = ctx->dev_counters + 12;
+    switch (ctx->kb) {
+        case 1: return launch<1, 4>(ctx, mh, ml, P);
+        case 2: return launch<2, 4>(ctx, mh, ml, P);
+        case 4: return launch<4, 4>(ctx, mh, ml, P);
+        case 8: return launch<8, 4>(ctx, mh, ml, P);
+        case 16: return launch<16, 3>(ctx, mh, ml, P);
+        default: return FRR_E_UNSUPPORTED;
+    }
 }
 
 }  // namespace frr

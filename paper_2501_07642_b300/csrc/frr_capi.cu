@@ -70,6 +70,17 @@ frr_status copy_out(frr_ctx* ctx, void* dst_any, const void* src_dev, size_t byt
     return FRR_OK;
 }
 
+frr_status take_device_error(frr_ctx* ctx)
+{
+    int err = 0;
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(&err, ctx->dev_counters + 12, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (err == 0) return FRR_OK;
+    FRR_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dev_counters + 12, 0, sizeof(int), ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return FRR_E_TIMEOUT;
+}
+
 static frr_status check_range(const frr_ctx* ctx, uint64_t seed, uint64_t first, uint64_t B)
 {
     if (first + B < first) return FRR_E_RANGE;
@@ -205,7 +216,7 @@ frr_status frr_balance(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_
     if (is_device_ptr(M_out)) {
         FRR_TRY(balance_launch(ctx, seed, exact, first_draw, B, M_out));
         FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-        return FRR_OK;
+        return take_device_error(ctx);
     }
     const uint64_t chunk = 1ull << 22;
     for (uint64_t off = 0; off < B; off += chunk) {
@@ -213,6 +224,7 @@ frr_status frr_balance(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_
         FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->Mhat), &ctx->Mhat_bytes, bc * sizeof(float)));
         FRR_TRY(balance_launch(ctx, seed, exact, first_draw + off, bc, ctx->Mhat));
         FRR_TRY(copy_out(ctx, M_out + off, ctx->Mhat, bc * sizeof(float)));
+        FRR_TRY(take_device_error(ctx));
     }
     return FRR_OK;
 }

@@ -111,6 +111,9 @@ frr_status ensure_device(frr_ctx* ctx, void** buf, size_t* cap_bytes, size_t byt
 // pinned host staging of at least `bytes`
 frr_status ensure_host_pinned(frr_ctx* ctx, size_t bytes);
 
+// FRR_E_TIMEOUT if a kernel of the context recorded an expired bounded wait (the word is cleared)
+frr_status take_device_error(frr_ctx* ctx);
+
 // copies between a caller buffer (host or device) and a device buffer of the context
 frr_status copy_in(frr_ctx* ctx, void* dst_dev, const void* src_any, size_t bytes);
 frr_status copy_out(frr_ctx* ctx, void* dst_any, const void* src_dev, size_t bytes);

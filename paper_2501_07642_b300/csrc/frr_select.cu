@@ -541,6 +541,7 @@ frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B)
         }
         cudaEventRecord(ctx->ev[2], ctx->stream);
         FRR_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev[2]));
+        FRR_TRY(take_device_error(ctx));
         float t1 = 0.f, t2 = 0.f;
         cudaEventElapsedTime(&t1, ctx->ev[0], ctx->ev[1]);
         cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
