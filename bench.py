@@ -60,7 +60,7 @@ class ClockSampler:
         self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.tmp, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -279,7 +279,7 @@ def run_frr(args):
             "paths": {p: ({"value": results[p]["value"], "ms_per_step": results[p]["ms_per_step"],
                            "ms_balance": results[p]["ms_balance"]} if "value" in results[p] else results[p])
                       for p in precisions},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": 8 * args.steps * ws,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": 13 * args.steps * ws,
             "clocks": {k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "selection": {k: r["stats"][k] for k in ("candidates", "accepted", "max_rel_err", "max_err_over_band",
                                                      "band_violations", "parity_at_risk")}}
@@ -289,7 +289,7 @@ def run_frr(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("frr", "reference"), default="frr")
     ap.add_argument("--precision", default="split_bf16,f32")

@@ -14,8 +14,8 @@
 //               into one of two TMEM accumulators (2 x 256 columns);
 //   warps 6-7   A producer: expand the draws' bit rows into BF16 0/1 K-major tiles
 //               (128 x 64, 128B swizzle, a 256-entry byte -> 8 x bf16 table);
-//   warps 8-13  generation: Philox + warp select (frr_gen.cuh) of the next tile's
-//               128 draws into a double-buffered bit-row buffer.
+//   warps 8..   generation (NG warps): Philox + warp select (frr_gen.cuh) of the
+//               next tile's 128 draws into a double-buffered bit-row buffer.
 // The assignment matrix exists only as bits and BF16 tiles in shared memory.
 // Every mbarrier wait is bounded (about one second); on expiry the CTA records an
 // error word, drains its own TMA copies, frees TMEM and returns.
@@ -27,14 +27,12 @@
 namespace frr {
 namespace {
 
-constexpr int kThreads = 448;
 constexpr int kTileM = 128;          // draws per tile = TMEM lanes
 constexpr int kChunkN = 256;         // covariates per accumulator chunk
 constexpr int kKBlock = 64;          // K positions per stage (128 bytes of BF16)
 constexpr int kStagesA = 3;
 constexpr int kBBytes = kChunkN * kKBlock * 2;   // 32 KiB
 constexpr int kABytes = kTileM * kKBlock * 2;    // 16 KiB
-constexpr int kGenWarps = 6;
 constexpr int kExpWarps = 2;
 constexpr unsigned long long kWaitCycles = 1ull << 31;
 
@@ -174,8 +172,8 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
     }
 }
 
-template <int KB, int SB>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int KB, int SB, int NG>
+__global__ void __launch_bounds__((8 + NG) * 32, 1)
 k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, TcParams P)
 {
     constexpr int W = 4 * KB;  // bit-row words per draw
@@ -201,7 +199,7 @@ k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // byte -> 8 BF16 values (bit e -> element e is 1.0 or 0.0)
-    for (int b = tid; b < 256; b += kThreads) {
+    for (int b = tid; b < 256; b += (8 + NG) * 32) {
         uint32_t w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -214,7 +212,7 @@ k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__
         for (int s = 0; s < 2; ++s) {
             mbar_init(&acc_full[s], 1);
             mbar_init(&acc_empty[s], 4);
-            mbar_init(&bits_full[s], kGenWarps);
+            mbar_init(&bits_full[s], NG);
             mbar_init(&bits_empty[s], kExpWarps);
         }
         mbar_init(mma_done, 1);
@@ -333,7 +331,7 @@ k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__
             const int bb = it & 1;
             if (!(ok = wait_bar(&bits_empty[bb], ((it >> 1) & 1u) ^ 1u, sAbort, P.err, 7))) break;
             uint32_t* bits = sBits + bb * kTileM * W;
-            for (int r = gw; r < kTileM; r += kGenWarps) {
+            for (int r = gw; r < kTileM; r += NG) {
                 const uint64_t off = t * kTileM + r;
                 uint32_t* row = bits + r * W;
                 if (off < P.B) {
@@ -425,13 +423,13 @@ size_t smem_bytes(int KB, int SB)
     return 1024 + (size_t)SB * kBBytes + (size_t)kStagesA * kABytes + 2ull * kTileM * 4 * KB * 4 + 256 * 16 + bars;
 }
 
-template <int KB, int SB>
+template <int KB, int SB, int NG>
 frr_status launch(frr_ctx* ctx, const CUtensorMap& mh, const CUtensorMap& ml, const TcParams& P)
 {
     const size_t smem = smem_bytes(KB, SB);
-    FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_balance_tc<KB, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_balance_tc<KB, SB, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const unsigned grid = (unsigned)(P.tiles < (uint64_t)ctx->num_sms ? P.tiles : (uint64_t)ctx->num_sms);
-    k_balance_tc<KB, SB><<<grid, kThreads, smem, ctx->stream>>>(mh, ml, P);
+    k_balance_tc<KB, SB, NG><<<grid, (8 + NG) * 32, smem, ctx->stream>>>(mh, ml, P);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     return FRR_OK;
 }
@@ -467,11 +465,11 @@ frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t f
     P.Mout = Mout;
     P.err = ctx->dev_counters + 12;
     switch (ctx->kb) {
-        case 1: return launch<1, 4>(ctx, mh, ml, P);
-        case 2: return launch<2, 4>(ctx, mh, ml, P);
-        case 4: return launch<4, 4>(ctx, mh, ml, P);
-        case 8: return launch<8, 4>(ctx, mh, ml, P);
-        case 16: return launch<16, 3>(ctx, mh, ml, P);
+        case 1: return launch<1, 4, 10>(ctx, mh, ml, P);
+        case 2: return launch<2, 4, 10>(ctx, mh, ml, P);
+        case 4: return launch<4, 4, 10>(ctx, mh, ml, P);
+        case 8: return launch<8, 4, 10>(ctx, mh, ml, P);
+        case 16: return launch<16, 3, 6>(ctx, mh, ml, P);
         default: return FRR_E_UNSUPPORTED;
     }
 }

@@ -97,7 +97,7 @@ static void release(frr_ctx* ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void* bufs[] = {ctx->Zc64, ctx->Z32, ctx->Zhi, ctx->Zlo, ctx->Q, ctx->Qsum, ctx->qexp, ctx->binom, ctx->Mhat,
                     ctx->ret_idx[0], ctx->ret_idx[1], ctx->ret_m[0], ctx->ret_m[1], ctx->dev_counters, ctx->M64,
-                    ctx->ukeys, ctx->misc, ctx->misc2};
+                    ctx->ukeys, ctx->misc, ctx->misc2, ctx->sel};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);

@@ -16,6 +16,7 @@
 // same order at init, so no permutation happens per draw.
 #pragma once
 #include <stdint.h>
+#include <type_traits>
 
 namespace frr {
 
@@ -80,33 +81,44 @@ __device__ __forceinline__ void unit_words(uint32_t (&r)[4 * KB], uint64_t seed,
 template <int KB>
 __device__ __forceinline__ int warp_count_le(const uint32_t (&r)[4 * KB], uint32_t t)
 {
-    int c = 0;
+    // four independent partial counts keep the add chains short
+    int c[4] = {0, 0, 0, 0};
 #pragma unroll
-    for (int e = 0; e < 4 * KB; ++e) c += (r[e] <= t) ? 1 : 0;
-    return (int)__reduce_add_sync(kFull, (unsigned)c);
+    for (int e = 0; e < 4 * KB; ++e) c[e & 3] += (r[e] <= t) ? 1 : 0;
+    return (int)__reduce_add_sync(kFull, (unsigned)((c[0] + c[1]) + (c[2] + c[3])));
 }
+
+// Slot mask type: one bit per unit word held by the lane.
+template <int KB>
+using slot_mask_t = typename std::conditional<(4 * KB <= 32), uint32_t, uint64_t>::type;
 
 // Treated flags (bit e = slot e = unit 128(e/4) + 4 lane + e%4) of the n1
 // smallest (r, unit) pairs across the warp. Search for the n1-th smallest
 // value v: interpolation on the empirical CDF (the words are uniform), with a
 // bisection step whenever the bracket fails to halve; it stops early as soon as
 // some t has exactly n1 words <= t. Each step strictly shrinks the bracket, so
-// the loop ends after at most ~70 counts (about 5 on average at n = 1000).
+// the loop ends after at most ~70 counts (about 5 on average at n = 1000). The
+// interpolation only steers the search, so it is done in FP32.
 template <int KB>
-__device__ __forceinline__ uint64_t warp_select_smallest(const uint32_t (&r)[4 * KB], int n, int n1, int lane)
+__device__ __forceinline__ slot_mask_t<KB> warp_select_smallest(const uint32_t (&r)[4 * KB], int n, int n1, int lane)
 {
+    using M = slot_mask_t<KB>;
     long long lo = -1, hi = 0xffffffffll;
     int clo = 0, chi = 128 * KB;
-    long long t = ((long long)n1 << 32) / n;
-    const long long step = (1ll << 32) / n;
+    const float inv_n = 1.0f / (float)n;
+    long long t = (long long)((float)n1 * inv_n * 4294967296.0f);
+    if (t > 0xfffffffell) t = 0xfffffffell;
+    if (t < 0) t = 0;
+    const long long step = (long long)(4294967296.0f * inv_n);
     long long prev_span = hi - lo;
     bool bisect = false;
     for (int it = 0;; ++it) {
-        const int c = warp_count_le<KB>(r, (uint32_t)t);
+        const uint32_t tt = (uint32_t)t;
+        const int c = warp_count_le<KB>(r, tt);
         if (c == n1) {
-            uint64_t m = 0;
+            M m = 0;
 #pragma unroll
-            for (int e = 0; e < 4 * KB; ++e) m |= (uint64_t)(r[e] <= (uint32_t)t) << e;
+            for (int e = 0; e < 4 * KB; ++e) m |= (M)(r[e] <= tt) << e;
             return m;
         }
         if (c > n1) { hi = t; chi = c; } else { lo = t; clo = c; }
@@ -117,8 +129,8 @@ __device__ __forceinline__ uint64_t warp_select_smallest(const uint32_t (&r)[4 *
         } else if (bisect) {
             t = lo + span / 2;
         } else {
-            const long long off = (span * (long long)(n1 - clo) + (chi - clo) / 2) / (chi - clo);
-            t = lo + off;
+            const float frac = (float)(n1 - clo) / (float)(chi - clo);
+            t = lo + (long long)((float)span * frac + 0.5f);
         }
         if (t <= lo) t = lo + 1;
         if (t >= hi) t = hi - 1;
@@ -129,7 +141,7 @@ __device__ __forceinline__ uint64_t warp_select_smallest(const uint32_t (&r)[4 *
     // with the smallest unit indices are treated. Unit order is k, then lane, then c.
     const uint32_t v = (uint32_t)hi;
     const int need = n1 - clo;
-    uint64_t m = 0;
+    M m = 0;
     int base = 0;
 #pragma unroll
     for (int k = 0; k < KB; ++k) {
@@ -147,9 +159,9 @@ __device__ __forceinline__ uint64_t warp_select_smallest(const uint32_t (&r)[4 *
         for (int c = 0; c < 4; ++c) {
             const int e = 4 * k + c;
             if (r[e] < v) {
-                m |= 1ull << e;
+                m |= (M)1 << e;
             } else if (r[e] == v) {
-                if (rank < need) m |= 1ull << e;
+                if (rank < need) m |= (M)1 << e;
                 ++rank;
             }
         }
@@ -160,7 +172,7 @@ __device__ __forceinline__ uint64_t warp_select_smallest(const uint32_t (&r)[4 *
 
 // Writes the draw's bit row (4*KB words, K-order) to row[] (shared or global).
 template <int KB>
-__device__ __forceinline__ void warp_store_bits(uint64_t treated, uint32_t* row, int lane)
+__device__ __forceinline__ void warp_store_bits(slot_mask_t<KB> treated, uint32_t* row, int lane)
 {
     constexpr int W = 4 * KB;
     uint32_t mine[(W + 31) / 32];
@@ -168,7 +180,7 @@ __device__ __forceinline__ void warp_store_bits(uint64_t treated, uint32_t* row,
     for (int q = 0; q < (W + 31) / 32; ++q) mine[q] = 0;
 #pragma unroll
     for (int e = 0; e < W; ++e) {
-        const uint32_t w = __ballot_sync(kFull, (unsigned)((treated >> e) & 1ull));
+        const uint32_t w = __ballot_sync(kFull, (unsigned)((treated >> e) & 1u));
         if (lane == (e & 31)) mine[e >> 5] = w;
     }
 #pragma unroll
@@ -219,7 +231,7 @@ __device__ __forceinline__ void warp_draw_bits(bool exact, uint64_t seed, uint64
     } else {
         uint32_t r[4 * KB];
         unit_words<KB>(r, seed, draw, n, lane);
-        const uint64_t t = warp_select_smallest<KB>(r, n, n1, lane);
+        const slot_mask_t<KB> t = warp_select_smallest<KB>(r, n, n1, lane);
         warp_store_bits<KB>(t, row, lane);
     }
 }

@@ -76,6 +76,7 @@ struct frr_ctx {
     uint64_t* ukeys = nullptr; size_t ukeys_bytes = 0;   // key staging
     void* misc = nullptr; size_t misc_bytes = 0;          // replay / randtest scratch
     void* misc2 = nullptr; size_t misc2_bytes = 0;
+    void* sel = nullptr; size_t sel_bytes = 0;           // device state of the running selection
     void* host_pinned = nullptr; size_t host_pinned_bytes = 0;
     cudaEvent_t ev[8] = {};
 

@@ -152,11 +152,6 @@ __device__ float largest_v_below(const CutParams& cp, double T, uint32_t lo_bits
     return __uint_as_float(lo);
 }
 
-__device__ __forceinline__ uint32_t elem_bits(const float* a, int64_t na, const float* b, int64_t e)
-{
-    return __float_as_uint(e < na ? a[e] : b[e - na]);
-}
-
 // Block-wide exclusive scan of one int per thread (SNT threads). Returns the
 // exclusive prefix; *total gets the block sum.
 __device__ int block_scan_excl(int v, int* ws, int* total)
@@ -188,138 +183,161 @@ __device__ int block_scan_excl(int v, int* ws, int* total)
     return res;
 }
 
-// One CTA. Inputs: chunk M_hat (nc entries, draw = first + e) and the retained
-// set (nr entries). q mode (K > 0): find the K-th smallest M_hat over both,
-// tighten the cut; threshold mode (K == 0): the cut is fixed. Writes the kept
-// entries (retained first, then the chunk, each in input order) and the count.
-__global__ void __launch_bounds__(SNT)
-k_stream_filter(const float* __restrict__ chunk, int64_t nc, uint64_t first, const float* __restrict__ rm_in,
-                const uint64_t* __restrict__ ri_in, int64_t nr, int64_t K, CutParams cp, float* __restrict__ cut_io,
-                float* __restrict__ rm_out, uint64_t* __restrict__ ri_out, int64_t cap_out, long long* __restrict__ count_out)
+// ---- parallel selection of the cut over V = chunk (nc values) + retained (nr values)
+// Two histogram levels on the float bit pattern (M_hat >= 0, so the bit order is the
+// value order): bits [31:20] over all of V, then bits [19:8] inside the bin that holds
+// the K-th smallest. The K-th smallest value lies below the upper edge m_up of the
+// second-level bin, so T = U(m_up) >= U(M_(K)) is a safe cut; it is looser than the
+// exact one by at most 2^-15 relative.
+constexpr int kBins = 4096;
+constexpr int kHistThreads = 256;
+
+struct SelState {
+    unsigned hist[2][kBins];
+    unsigned prefix1, prefix2;
+    long long krem;
+    float cut;
+    long long kept;
+};
+
+__device__ __forceinline__ float elem_value(const float* chunk, int64_t nc, const float* ret, int64_t e)
 {
-    __shared__ unsigned hist[2048];
-    __shared__ int ws[33];
-    __shared__ uint32_t s_prefix;
-    __shared__ long long s_k;
-    __shared__ float s_cut;
+    return e < nc ? chunk[e] : ret[e - nc];
+}
+
+// level 0: bins of bits [31:20] of every value; level 1: bins of bits [19:8] of the
+// values whose bits [31:20] equal st->prefix1
+__global__ void __launch_bounds__(kHistThreads)
+k_sel_hist(const float* __restrict__ chunk, int64_t nc, const float* __restrict__ ret, int64_t nr, int level,
+           SelState* __restrict__ st)
+{
+    __shared__ unsigned h[kBins];
+    for (int i = threadIdx.x; i < kBins; i += kHistThreads) h[i] = 0;
+    __syncthreads();
     const int64_t N = nc + nr;
-    // chunk first, retained after: element e < nc is chunk[e]
-    if (K > 0 && N > K) {
-        if (threadIdx.x == 0) { s_prefix = 0; s_k = K; }
-        const int shifts[3] = {21, 10, 0};
-        const int widths[3] = {11, 11, 10};
-        for (int pass = 0; pass < 3; ++pass) {
-            for (int i = threadIdx.x; i < 2048; i += SNT) hist[i] = 0;
-            __syncthreads();
-            const int sh = shifts[pass], wd = widths[pass];
-            const uint32_t prefix = s_prefix;
-            const long long k = s_k;  // read before the barriers below; one thread rewrites it after them
-            const int hsh = sh + wd;  // bits above this pass must match the prefix
-            for (int64_t base = 0; base < N; base += SNT) {
-                const int64_t e = base + threadIdx.x;
-                bool take = false;
-                uint32_t dig = 0;
-                if (e < N) {
-                    const uint32_t b = elem_bits(chunk, nc, rm_in, e);
-                    take = (hsh >= 32) ? true : ((b >> hsh) == prefix);
-                    dig = (b >> sh) & ((1u << wd) - 1u);
-                }
-                const unsigned key = take ? dig : 0xffffffffu;
-                const unsigned peers = __match_any_sync(kFull, key);
-                if (take && (__ffs(peers) - 1) == (threadIdx.x & 31)) atomicAdd(&hist[dig], (unsigned)__popc(peers));
-            }
-            __syncthreads();
-            // locate the bin holding rank s_k (1-based) by a block scan over 2048 bins (2 per thread)
-            const int b0 = 2 * threadIdx.x;
-            const int h0 = (int)hist[b0], h1 = (int)hist[b0 + 1];
-            int tot;
-            const int excl = block_scan_excl(h0 + h1, ws, &tot);
-            if (excl < k && k <= excl + h0) {
-                s_prefix = (prefix << wd) | (uint32_t)b0;
-                s_k = k - excl;
-            } else if (excl + h0 < k && k <= excl + h0 + h1) {
-                s_prefix = (prefix << wd) | (uint32_t)(b0 + 1);
-                s_k = k - excl - h0;
-            }
-            __syncthreads();
+    const unsigned p1 = st->prefix1;
+    const int64_t stride = (int64_t)gridDim.x * kHistThreads;
+    for (int64_t base = (int64_t)blockIdx.x * kHistThreads; base < N; base += stride) {
+        const int64_t e = base + threadIdx.x;
+        bool take = false;
+        unsigned dig = 0;
+        if (e < N) {
+            const uint32_t b = __float_as_uint(elem_value(chunk, nc, ret, e));
+            if (level == 0) { take = true; dig = b >> 20; }
+            else { take = (b >> 20) == p1; dig = (b >> 8) & (kBins - 1); }
         }
-        if (threadIdx.x == 0) {
-            const float mk = __uint_as_float(s_prefix);
-            const double T = (double)mk + band_value(cp.lin, cp.quad, cp.rel, cp.safety, (double)mk);
-            const float c = largest_v_below(cp, T, s_prefix);
-            s_cut = fminf(c, *cut_io);
-            *cut_io = s_cut;
-        }
-    } else if (threadIdx.x == 0) {
-        s_cut = *cut_io;
+        const unsigned key = take ? dig : 0xffffffffu;
+        const unsigned peers = __match_any_sync(kFull, key);
+        if (take && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&h[dig], (unsigned)__popc(peers));
     }
     __syncthreads();
-    const float cut = s_cut;
-    // compaction: retained entries first, then the chunk, each in order
-    long long written = 0;
-    for (int64_t base = 0; base < N; base += SNT) {
-        const int64_t e = base + threadIdx.x;  // e < nr: retained[e]; else chunk[e - nr]
-        int keep = 0;
+    for (int i = threadIdx.x; i < kBins; i += kHistThreads)
+        if (h[i]) atomicAdd(&st->hist[level][i], h[i]);
+}
+
+// One CTA of SNT threads: the bin of histogram `level` that holds rank st->krem.
+// After level 1 it forms the cut. The other histogram is cleared for reuse.
+__global__ void __launch_bounds__(SNT) k_sel_scan(SelState* __restrict__ st, int level, CutParams cp)
+{
+    __shared__ int ws[33];
+    const unsigned* h = st->hist[level];
+    const int b0 = 4 * threadIdx.x;
+    const int h0 = (int)h[b0], h1 = (int)h[b0 + 1], h2 = (int)h[b0 + 2], h3 = (int)h[b0 + 3];
+    const long long k = st->krem;
+    int tot;
+    const int excl = block_scan_excl(h0 + h1 + h2 + h3, ws, &tot);
+    long long c = excl;
+    const int hs[4] = {h0, h1, h2, h3};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (c < k && k <= c + hs[q]) {
+            if (level == 0) { st->prefix1 = (unsigned)(b0 + q); st->krem = k - c; }
+            else { st->prefix2 = (unsigned)(b0 + q); st->krem = k - c; }
+        }
+        c += hs[q];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBins; i += SNT) st->hist[1 - level][i] = 0;
+    if (level == 1 && threadIdx.x == 0) {
+        const uint32_t up_bits = (st->prefix1 << 20) | (st->prefix2 << 8) | 0xFFu;
+        const float mup = __uint_as_float(up_bits);
+        const double T = (double)mup + band_value(cp.lin, cp.quad, cp.rel, cp.safety, (double)mup);
+        const float v = largest_v_below(cp, T, up_bits);
+        st->cut = fminf(v, st->cut);
+    }
+}
+
+// Keep the retained entries and chunk entries with M_hat <= cut (order not preserved:
+// the final ordering sorts by (M64, draw index)).
+__global__ void __launch_bounds__(kHistThreads)
+k_sel_compact(const float* __restrict__ chunk, int64_t nc, uint64_t first, const float* __restrict__ rm_in,
+              const uint64_t* __restrict__ ri_in, int64_t nr, SelState* __restrict__ st, float* __restrict__ rm_out,
+              uint64_t* __restrict__ ri_out, int64_t cap_out)
+{
+    const float cut = st->cut;
+    const int64_t N = nc + nr;
+    const int64_t stride = (int64_t)gridDim.x * kHistThreads;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * kHistThreads; base < N; base += stride) {
+        const int64_t e = base + threadIdx.x;
         float v = 0.f;
         uint64_t idx = 0;
+        bool keep = false;
         if (e < N) {
             if (e < nr) { v = rm_in[e]; idx = ri_in[e]; }
             else { v = chunk[e - nr]; idx = first + (uint64_t)(e - nr); }
-            keep = (v <= cut) ? 1 : 0;
+            keep = v <= cut;
         }
-        int tot;
-        const int pos = block_scan_excl(keep, ws, &tot);
-        if (keep && written + pos < cap_out) {
-            rm_out[written + pos] = v;
-            ri_out[written + pos] = idx;
+        const unsigned m = __ballot_sync(kFull, keep);
+        if (m == 0) continue;
+        long long pos0 = 0;
+        if (lane == 0) pos0 = (long long)atomicAdd((unsigned long long*)&st->kept, (unsigned long long)__popc(m));
+        pos0 = __shfl_sync(kFull, pos0, 0);
+        if (keep) {
+            const long long pos = pos0 + __popc(m & ((1u << lane) - 1u));
+            if (pos < cap_out) { rm_out[pos] = v; ri_out[pos] = idx; }
         }
-        written += tot;
     }
-    if (threadIdx.x == 0) *count_out = written;
+}
+
+__global__ void k_sel_begin(SelState* __restrict__ st, long long K)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->krem = K;
+        st->kept = 0;
+    }
 }
 
 // ---------------------------------------------------------------- ordering --
-// rank_c = #{c' : (M64_c', idx_c') < (M64_c, idx_c)}
+// rank_c = #{c' : (M64_c', idx_c') < (M64_c, idx_c)}, one warp per entry
 __global__ void k_rank(const double* __restrict__ m, const uint64_t* __restrict__ idx, int64_t r, int* __restrict__ rank)
 {
-    __shared__ double sm[1024];
-    __shared__ uint64_t si[1024];
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const double mc = c < r ? m[c] : 0.0;
-    const uint64_t ic = c < r ? idx[c] : 0;
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= r) return;
+    const double mc = m[c];
+    const uint64_t ic = idx[c];
     int cnt = 0;
-    for (int64_t t0 = 0; t0 < r; t0 += 1024) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < 1024; k += blockDim.x) {
-            if (t0 + k < r) { sm[k] = m[t0 + k]; si[k] = idx[t0 + k]; }
-        }
-        __syncthreads();
-        const int lim = (int)((r - t0) < 1024 ? (r - t0) : 1024);
-        for (int k = 0; k < lim; ++k) cnt += (sm[k] < mc || (sm[k] == mc && si[k] < ic)) ? 1 : 0;
+    for (int64_t k = lane; k < r; k += 32) {
+        const double mk = m[k];
+        cnt += (mk < mc || (mk == mc && idx[k] < ic)) ? 1 : 0;
     }
-    if (c < r) rank[c] = cnt;
+    cnt = (int)__reduce_add_sync(kFull, (unsigned)cnt);
+    if (lane == 0) rank[c] = cnt;
 }
 
-// selected (sel[c] != 0) entries go to position #{selected c' : idx_c' < idx_c}
+// selected (sel[c] != 0) entries go to position #{selected c' : idx_c' < idx_c}, one warp per entry
 __global__ void k_place(const double* __restrict__ m, const uint64_t* __restrict__ idx, const int* __restrict__ sel,
                         int64_t r, uint64_t* __restrict__ keys_out, double* __restrict__ m_out)
 {
-    __shared__ uint64_t si[1024];
-    __shared__ int ss[1024];
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool me = c < r && sel[c];
-    const uint64_t ic = c < r ? idx[c] : 0;
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= r || !sel[c]) return;
+    const uint64_t ic = idx[c];
     int cnt = 0;
-    for (int64_t t0 = 0; t0 < r; t0 += 1024) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < 1024; k += blockDim.x) {
-            if (t0 + k < r) { si[k] = idx[t0 + k]; ss[k] = sel[t0 + k]; }
-        }
-        __syncthreads();
-        const int lim = (int)((r - t0) < 1024 ? (r - t0) : 1024);
-        for (int k = 0; k < lim; ++k) cnt += (ss[k] && si[k] < ic) ? 1 : 0;
-    }
-    if (me) {
+    for (int64_t k = lane; k < r; k += 32) cnt += (sel[k] && idx[k] < ic) ? 1 : 0;
+    cnt = (int)__reduce_add_sync(kFull, (unsigned)cnt);
+    if (lane == 0) {
         keys_out[cnt] = ic;
         m_out[cnt] = m[c];
     }
@@ -492,7 +510,11 @@ frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold,
     st.retained = 0;
     ctx->ret_cur = 0;
     const double ms_init = ctx->stats.ms_init;
-    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->dev_counters + 8, &st.cut, sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    FRR_TRY(ensure_device(ctx, &ctx->sel, &ctx->sel_bytes, sizeof(SelState)));
+    FRR_CUDA_TRY(ctx, cudaMemsetAsync(ctx->sel, 0, sizeof(SelState), ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(&static_cast<SelState*>(ctx->sel)->cut, &st.cut, sizeof(float),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     memset(&ctx->stats, 0, sizeof(ctx->stats));
     ctx->stats.ms_init = ms_init;
     ctx->stats.boundary_gap_rel = NAN;
@@ -505,8 +527,7 @@ frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B)
     if (!st.active) return FRR_E_STATE;
     if (B == 0) return FRR_OK;
     if (st.seen + B > st.total) return FRR_E_RANGE;
-    float* cut_dev = reinterpret_cast<float*>(ctx->dev_counters + 8);
-    long long* count_dev = reinterpret_cast<long long*>(ctx->dev_counters);
+    SelState* sel = static_cast<SelState*>(ctx->sel);
     const CutParams cp = cut_params(ctx);
     for (uint64_t off = 0; off < B; off += kChunkMax) {
         const uint64_t bc = std::min<uint64_t>(kChunkMax, B - off);
@@ -515,29 +536,39 @@ frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B)
         FRR_TRY(balance_launch(ctx, st.seed, st.exact, first + off, bc, ctx->Mhat));
         cudaEventRecord(ctx->ev[1], ctx->stream);
         const int in = ctx->ret_cur, out = 1 - in;
-        // worst case every entry is kept; grow the output side first time it could overflow
+        const int64_t N = st.retained + (int64_t)bc;
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(N, kHistThreads), 4 * ctx->num_sms));
+        k_sel_begin<<<1, 32, 0, ctx->stream>>>(sel, st.K);
+        if (st.q_mode && N > st.K) {
+            k_sel_hist<<<grid, kHistThreads, 0, ctx->stream>>>(ctx->Mhat, (int64_t)bc, ctx->ret_m[in], st.retained, 0, sel);
+            k_sel_scan<<<1, SNT, 0, ctx->stream>>>(sel, 0, cp);
+            k_sel_hist<<<grid, kHistThreads, 0, ctx->stream>>>(ctx->Mhat, (int64_t)bc, ctx->ret_m[in], st.retained, 1, sel);
+            k_sel_scan<<<1, SNT, 0, ctx->stream>>>(sel, 1, cp);
+        }
+        FRR_CUDA_TRY(ctx, cudaGetLastError());
         int64_t cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
-        const int64_t want = std::min<int64_t>(st.retained + (int64_t)bc, std::max<int64_t>(4 * st.K + 65536, 1 << 20));
+        const int64_t want = std::min<int64_t>(N, std::max<int64_t>(4 * st.K + 65536, 1 << 20));
         if (cap < want) {
             FRR_TRY(ensure_retained(ctx, out, want));
             cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
         }
-        for (int attempt = 0; attempt < 2; ++attempt) {
-            k_stream_filter<<<1, SNT, 0, ctx->stream>>>(ctx->Mhat, (int64_t)bc, first + off, ctx->ret_m[in],
-                                                       ctx->ret_idx[in], st.retained, st.q_mode ? st.K : 0, cp, cut_dev,
-                                                       ctx->ret_m[out], ctx->ret_idx[out], cap, count_dev);
+        for (int attempt = 0;; ++attempt) {
+            k_sel_compact<<<grid, kHistThreads, 0, ctx->stream>>>(ctx->Mhat, (int64_t)bc, first + off, ctx->ret_m[in],
+                                                                 ctx->ret_idx[in], st.retained, sel, ctx->ret_m[out],
+                                                                 ctx->ret_idx[out], cap);
             FRR_CUDA_TRY(ctx, cudaGetLastError());
             long long kept = 0;
-            FRR_CUDA_TRY(ctx, cudaMemcpyAsync(&kept, count_dev, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+            FRR_CUDA_TRY(ctx, cudaMemcpyAsync(&kept, &sel->kept, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
             FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
             if (kept <= cap) {
                 st.retained = kept;
                 break;
             }
-            // the cut is monotone, so re-running with a larger output buffer gives the same set
+            if (attempt == 1) return FRR_E_CAPACITY;
+            // the cut stays as computed, so the re-run keeps the same set
             FRR_TRY(ensure_retained(ctx, out, kept));
             cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
-            if (attempt == 1) return FRR_E_CAPACITY;
+            k_sel_begin<<<1, 32, 0, ctx->stream>>>(sel, st.K);
         }
         cudaEventRecord(ctx->ev[2], ctx->stream);
         FRR_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev[2]));
@@ -579,11 +610,11 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
         const double nanv = NAN;
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(boundary, &nanv, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(boundary + 1, &nanv, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-        k_rank<<<ceil_div(r, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], r, rank);
+        k_rank<<<ceil_div(r * 32, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], r, rank);
         k_select_flags<<<ceil_div(r, 256), 256, 0, ctx->stream>>>(rank, m64, r, st.K, st.q_mode ? 1 : 0, st.threshold,
                                                                   sel, boundary);
         k_count_sel<<<1, SNT, 0, ctx->stream>>>(sel, r, nsel_dev);
-        k_place<<<ceil_div(r, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], sel, r, kout, mout);
+        k_place<<<ceil_div(r * 32, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], sel, r, kout, mout);
         FRR_CUDA_TRY(ctx, cudaGetLastError());
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(&nsel, nsel_dev, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
     }
