@@ -12,9 +12,9 @@
 //   warp 5      TMEM allocator and MMA issuer (one thread): per covariate chunk of
 //               N <= 256 columns, 2 x 4 tcgen05.mma (M=128, K=16) per 64-wide K block
 //               into one of two TMEM accumulators (2 x 256 columns);
-//   warps 6-7   A producer: expand the draws' bit rows into BF16 0/1 K-major tiles
-//               (128 x 64, 128B swizzle, a 256-entry byte -> 8 x bf16 table);
-//   warps 8..   generation (NG warps): Philox + warp select (frr_gen.cuh) of the
+//   warps 6-9   A producer: expand the draws' bit rows into BF16 0/1 K-major tiles
+//               (128 x 64, 128B swizzle), one draw row per thread, in registers;
+//   warps 10..  generation (NG warps): Philox + warp select (frr_gen.cuh) of the
 //               next tile's 128 draws into a double-buffered bit-row buffer.
 // The assignment matrix exists only as bits and BF16 tiles in shared memory.
 // Every mbarrier wait is bounded (about one second); on expiry the CTA records an
@@ -33,7 +33,7 @@ constexpr int kKBlock = 64;          // K positions per stage (128 bytes of BF16
 constexpr int kStagesA = 3;
 constexpr int kBBytes = kChunkN * kKBlock * 2;   // 32 KiB
 constexpr int kABytes = kTileM * kKBlock * 2;    // 16 KiB
-constexpr int kExpWarps = 2;
+constexpr int kExpWarps = 4;   // 128 threads: one A-tile row each
 constexpr unsigned long long kWaitCycles = 1ull << 31;
 
 // ------------------------------------------------------------- PTX helpers --
@@ -173,17 +173,18 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
 }
 
 template <int KB, int SB, int NG>
-__global__ void __launch_bounds__((8 + NG) * 32, 1)
+__global__ void __launch_bounds__((6 + kExpWarps + NG) * 32, 1)
 k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, TcParams P)
 {
     constexpr int W = 4 * KB;  // bit-row words per draw
+    constexpr int RS = W + 1;  // odd row stride: the expansion threads read 32 rows without bank conflicts
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* sB = smem;                                    // SB x 32 KiB
     unsigned char* sA = sB + SB * kBBytes;                       // kStagesA x 16 KiB
-    uint32_t* sBits = reinterpret_cast<uint32_t*>(sA + kStagesA * kABytes);  // 2 x 128 x W
-    uint4* sLut = reinterpret_cast<uint4*>(sBits + 2 * kTileM * W);          // 256 entries
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sLut + 256);
+    uint32_t* sBits = reinterpret_cast<uint32_t*>(sA + kStagesA * kABytes);  // 2 x 128 x RS
+    uint64_t* bar = reinterpret_cast<uint64_t*>(
+        (reinterpret_cast<uintptr_t>(sBits + 2 * kTileM * RS) + 7) & ~uintptr_t(7));
     uint64_t* b_full = bar;
     uint64_t* b_empty = b_full + SB;
     uint64_t* a_full = b_empty + SB;
@@ -198,14 +199,6 @@ k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // byte -> 8 BF16 values (bit e -> element e is 1.0 or 0.0)
-    for (int b = tid; b < 256; b += (8 + NG) * 32) {
-        uint32_t w[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            w[i] = (((b >> (2 * i)) & 1) ? 0x3F80u : 0u) | (((b >> (2 * i + 1)) & 1) ? 0x3F800000u : 0u);
-        sLut[b] = make_uint4(w[0], w[1], w[2], w[3]);
-    }
     if (tid == 0) {
         for (int s = 0; s < SB; ++s) { mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); }
         for (int s = 0; s < kStagesA; ++s) { mbar_init(&a_full[s], kExpWarps); mbar_init(&a_empty[s], 1); }
@@ -295,25 +288,35 @@ k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__
         }
     } else if (warp >= 6 && warp < 6 + kExpWarps) {
         // ------------------------------------------------- A tile producer --
-        const int et = tid - 6 * 32;  // 0..63
+        // thread r writes row r (draw r of the tile): the 64 bits of K block kb become
+        // eight 16-byte chunks of BF16 0.0 / 1.0, chunk q stored at (q ^ (r % 8)).
+        const int r = tid - 6 * 32;  // 0..127
         uint32_t ai = 0;
         uint32_t it = 0;
         bool ok = true;
         for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
             const int bb = it & 1;
             if (!(ok = wait_bar(&bits_full[bb], (it >> 1) & 1u, sAbort, P.err, 5))) break;
-            const uint32_t* bits = sBits + bb * kTileM * W;
+            const uint32_t* row = sBits + bb * kTileM * RS + r * RS;
             for (int c = 0; c < nch && ok; ++c)
                 for (int kb = 0; kb < nkb; ++kb, ++ai) {
                     const int s = ai % kStagesA;
                     if (!(ok = wait_bar(&a_empty[s], ((ai / kStagesA) & 1u) ^ 1u, sAbort, P.err, 6))) break;
-                    unsigned char* tile = sA + s * kABytes;
-#pragma unroll 4
-                    for (int idx = et; idx < kTileM * 8; idx += 32 * kExpWarps) {
-                        const int r = idx >> 3, q = idx & 7;
-                        const uint32_t word = bits[r * W + 2 * kb + (q >> 2)];
-                        const uint32_t byte = (word >> (8 * (q & 3))) & 0xFFu;
-                        *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((q ^ (r & 7)) << 4)) = sLut[byte];
+                    unsigned char* dst = sA + s * kABytes + (r >> 3) * 1024 + (r & 7) * 128;
+                    const uint32_t w2[2] = {row[2 * kb], row[2 * kb + 1]};
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const uint32_t x = (w2[q >> 2] >> (8 * (q & 3))) & 0xFFu;
+                        // bit i of a nibble -> byte i (0 or 1); the four shifted copies never overlap
+                        const uint32_t ylo = ((x & 0xFu) * 0x00204081u) & 0x01010101u;
+                        const uint32_t yhi = ((x >> 4) * 0x00204081u) & 0x01010101u;
+                        // bytes -> 16-bit lanes holding 0 or 1, times the BF16 pattern of 1.0
+                        uint4 v;
+                        v.x = __byte_perm(ylo, 0u, 0x4140) * 0x3F80u;
+                        v.y = __byte_perm(ylo, 0u, 0x4342) * 0x3F80u;
+                        v.z = __byte_perm(yhi, 0u, 0x4140) * 0x3F80u;
+                        v.w = __byte_perm(yhi, 0u, 0x4342) * 0x3F80u;
+                        *reinterpret_cast<uint4*>(dst + ((q ^ (r & 7)) << 4)) = v;
                     }
                     fence_async_smem();
                     __syncwarp();
@@ -330,10 +333,10 @@ k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__
         for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
             const int bb = it & 1;
             if (!(ok = wait_bar(&bits_empty[bb], ((it >> 1) & 1u) ^ 1u, sAbort, P.err, 7))) break;
-            uint32_t* bits = sBits + bb * kTileM * W;
+            uint32_t* bits = sBits + bb * kTileM * RS;
             for (int r = gw; r < kTileM; r += NG) {
                 const uint64_t off = t * kTileM + r;
-                uint32_t* row = bits + r * W;
+                uint32_t* row = bits + r * RS;
                 if (off < P.B) {
                     warp_draw_bits<KB>(P.exact != 0, P.seed, P.first + off, P.n, P.n1, P.binom, row, lane);
                 } else {
@@ -420,7 +423,7 @@ bool make_map(CUtensorMap* m, const __nv_bfloat16* base, int kpad, int d)
 size_t smem_bytes(int KB, int SB)
 {
     const size_t bars = (size_t)(2 * SB + 2 * kStagesA + 9) * 8 + 16;
-    return 1024 + (size_t)SB * kBBytes + (size_t)kStagesA * kABytes + 2ull * kTileM * 4 * KB * 4 + 256 * 16 + bars;
+    return 1024 + (size_t)SB * kBBytes + (size_t)kStagesA * kABytes + 2ull * kTileM * (4 * KB + 1) * 4 + 8 + bars;
 }
 
 template <int KB, int SB, int NG>
@@ -429,7 +432,7 @@ frr_status launch(frr_ctx* ctx, const CUtensorMap& mh, const CUtensorMap& ml, co
     const size_t smem = smem_bytes(KB, SB);
     FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_balance_tc<KB, SB, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const unsigned grid = (unsigned)(P.tiles < (uint64_t)ctx->num_sms ? P.tiles : (uint64_t)ctx->num_sms);
-    k_balance_tc<KB, SB, NG><<<grid, (8 + NG) * 32, smem, ctx->stream>>>(mh, ml, P);
+    k_balance_tc<KB, SB, NG><<<grid, (6 + kExpWarps + NG) * 32, smem, ctx->stream>>>(mh, ml, P);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     return FRR_OK;
 }
