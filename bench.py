@@ -184,7 +184,7 @@ def run_frr(args):
             results[prec] = {"error": str(e)}
             ctx.close()
             continue
-        step_ms, bal_ms = [], []
+        step_ms, bal_ms, sel_ms, rck_ms = [], [], [], []
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if ws > 1:
             dist.barrier()
@@ -202,7 +202,10 @@ def run_frr(args):
                 ev1.synchronize()
                 if i >= args.warmup:
                     step_ms.append(ev0.elapsed_time(ev1))
-                    bal_ms.append(frr.frr_last_stats(ctx)["ms_balance"])
+                    stt = frr.frr_last_stats(ctx)
+                    bal_ms.append(stt["ms_balance"])
+                    sel_ms.append(stt["ms_select"])
+                    rck_ms.append(stt["ms_recheck"])
             torch.cuda.synchronize()
             wall = time.perf_counter() - t_wall
         stats = frr.frr_last_stats(ctx)
@@ -231,7 +234,8 @@ def run_frr(args):
                    "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(K * 16),
                    "includes": "frr_init (X upload, FP64 prep) + frr_select + key read-back"}
         results[prec] = {"value": ws * B * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
-                         "ms_balance": statistics.mean(bal_ms), "clocks": clk.summary(), "stats": stats, "e2e": e2e,
+                         "ms_balance": statistics.mean(bal_ms), "ms_select": statistics.mean(sel_ms),
+                         "ms_recheck": statistics.mean(rck_ms), "clocks": clk.summary(), "stats": stats, "e2e": e2e,
                          "wall_s": wall}
         ctx.close()
 
@@ -276,10 +280,10 @@ def run_frr(args):
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "n1": n1, "d": d, "draws_per_step": B, "q": q, "K": K,
                        "whiten": "ridge 0.1", "path": prim, "l2": "flushed (256 MiB write) between timed steps"},
-            "paths": {p: ({"value": results[p]["value"], "ms_per_step": results[p]["ms_per_step"],
-                           "ms_balance": results[p]["ms_balance"]} if "value" in results[p] else results[p])
+            "paths": {p: ({k: results[p][k] for k in ("value", "ms_per_step", "ms_balance", "ms_select", "ms_recheck")}
+                          if "value" in results[p] else results[p])
                       for p in precisions},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": 13 * args.steps * ws,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": 14 * args.steps * ws,
             "clocks": {k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "selection": {k: r["stats"][k] for k in ("candidates", "accepted", "max_rel_err", "max_err_over_band",
                                                      "band_violations", "parity_at_risk")}}

@@ -17,6 +17,8 @@
 #include "frr_gen.cuh"
 
 #include <algorithm>
+#include <cstddef>
+#include <cstring>
 #include <vector>
 
 namespace frr {
@@ -198,7 +200,23 @@ struct SelState {
     long long krem;
     float cut;
     long long kept;
+    // end-of-stream results, read back in one copy (see SelTail)
+    long long nsel;
+    double boundary[2];      // M64 of ranks K-1 and K (q mode)
+    double max_rel, max_over_band, thr;
+    int violations;
 };
+
+static_assert(offsetof(SelState, violations) - offsetof(SelState, nsel) == 48, "SelState tail layout");
+
+// the part of SelState read back by the host at the end of a stream
+struct SelTail {
+    long long nsel;
+    double boundary[2];
+    double max_rel, max_over_band, thr;
+    int violations;
+};
+static_assert(offsetof(SelTail, violations) == 48, "SelTail layout");
 
 __device__ __forceinline__ float elem_value(const float* chunk, int64_t nc, const float* ret, int64_t e)
 {
@@ -368,6 +386,44 @@ __global__ void k_count_sel(const int* __restrict__ sel, int64_t r, long long* _
     if (threadIdx.x == 0) *out = total;
 }
 
+// band statistics of the re-checked draws and the largest accepted M64 (one CTA)
+__global__ void __launch_bounds__(SNT)
+k_sel_stats(const double* __restrict__ m64, const float* __restrict__ mhat, const int* __restrict__ sel, int64_t r,
+            CutParams cp, SelState* __restrict__ st)
+{
+    __shared__ double s_rel[32], s_band[32], s_thr[32];
+    __shared__ int s_viol[32];
+    double mrel = 0.0, mband = 0.0, thr = -INFINITY;
+    int viol = 0;
+    for (int64_t c = threadIdx.x; c < r; c += SNT) {
+        const double a = (double)mhat[c], m = m64[c];
+        const double err = fabs(a - m);
+        const double band = band_value(cp.lin, cp.quad, cp.rel, cp.safety, a);
+        if (m > 0.0) mrel = fmax(mrel, err / m);
+        if (band > 0.0) mband = fmax(mband, err / band);
+        viol += (err > band) ? 1 : 0;
+        if (sel[c]) thr = fmax(thr, m);
+    }
+    for (int off = 16; off >= 1; off >>= 1) {
+        mrel = fmax(mrel, __shfl_xor_sync(kFull, mrel, off));
+        mband = fmax(mband, __shfl_xor_sync(kFull, mband, off));
+        thr = fmax(thr, __shfl_xor_sync(kFull, thr, off));
+        viol += __shfl_xor_sync(kFull, viol, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { s_rel[warp] = mrel; s_band[warp] = mband; s_thr[warp] = thr; s_viol[warp] = viol; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < SNT / 32; ++w) {
+            mrel = fmax(mrel, s_rel[w]); mband = fmax(mband, s_band[w]); thr = fmax(thr, s_thr[w]); viol += s_viol[w];
+        }
+        st->max_rel = mrel;
+        st->max_over_band = mband;
+        st->thr = thr;
+        st->violations = viol;
+    }
+}
+
 template <int KB>
 frr_status launch_bits_kb(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t count,
                           const uint64_t* draws, uint32_t* rows)
@@ -514,7 +570,6 @@ frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold,
     FRR_CUDA_TRY(ctx, cudaMemsetAsync(ctx->sel, 0, sizeof(SelState), ctx->stream));
     FRR_CUDA_TRY(ctx, cudaMemcpyAsync(&static_cast<SelState*>(ctx->sel)->cut, &st.cut, sizeof(float),
                                       cudaMemcpyHostToDevice, ctx->stream));
-    FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     memset(&ctx->stats, 0, sizeof(ctx->stats));
     ctx->stats.ms_init = ms_init;
     ctx->stats.boundary_gap_rel = NAN;
@@ -529,6 +584,7 @@ frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B)
     if (st.seen + B > st.total) return FRR_E_RANGE;
     SelState* sel = static_cast<SelState*>(ctx->sel);
     const CutParams cp = cut_params(ctx);
+    FRR_TRY(ensure_host_pinned(ctx, 256));
     for (uint64_t off = 0; off < B; off += kChunkMax) {
         const uint64_t bc = std::min<uint64_t>(kChunkMax, B - off);
         FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->Mhat), &ctx->Mhat_bytes, bc * sizeof(float)));
@@ -557,9 +613,18 @@ frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B)
                                                                  ctx->ret_idx[in], st.retained, sel, ctx->ret_m[out],
                                                                  ctx->ret_idx[out], cap);
             FRR_CUDA_TRY(ctx, cudaGetLastError());
-            long long kept = 0;
-            FRR_CUDA_TRY(ctx, cudaMemcpyAsync(&kept, &sel->kept, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+            long long* hk = static_cast<long long*>(ctx->host_pinned);
+            FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk, &sel->kept, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+            FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk + 1, ctx->dev_counters + 12, sizeof(int), cudaMemcpyDeviceToHost,
+                                              ctx->stream));
+            cudaEventRecord(ctx->ev[2], ctx->stream);
             FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            const long long kept = hk[0];
+            if (*reinterpret_cast<int*>(hk + 1) != 0) {
+                FRR_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dev_counters + 12, 0, sizeof(int), ctx->stream));
+                FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+                return FRR_E_TIMEOUT;
+            }
             if (kept <= cap) {
                 st.retained = kept;
                 break;
@@ -570,9 +635,6 @@ frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B)
             cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
             k_sel_begin<<<1, 32, 0, ctx->stream>>>(sel, st.K);
         }
-        cudaEventRecord(ctx->ev[2], ctx->stream);
-        FRR_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev[2]));
-        FRR_TRY(take_device_error(ctx));
         float t1 = 0.f, t2 = 0.f;
         cudaEventElapsedTime(&t1, ctx->ev[0], ctx->ev[1]);
         cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
@@ -592,76 +654,62 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
     if (st.seen != st.total) return FRR_E_STATE;
     const int64_t r = st.retained;
     const int cur = ctx->ret_cur;
+    SelState* sel = static_cast<SelState*>(ctx->sel);
+    FRR_TRY(ensure_host_pinned(ctx, 256));
     cudaEventRecord(ctx->ev[3], ctx->stream);
-    // scratch: M64 (r), M64 out (r), keys out (r), boundary (2 doubles), rank (r), sel (r)
-    const size_t need = (size_t)r * (3 * sizeof(double) + 2 * sizeof(int)) + 2 * sizeof(double);
+    // scratch: M64 (r), M64 out (r), keys out (r), rank (r), sel (r)
+    const size_t need = (size_t)r * (3 * sizeof(double) + 2 * sizeof(int)) + 64;
     FRR_TRY(ensure_device(ctx, &ctx->misc, &ctx->misc_bytes, need));
     char* base = static_cast<char*>(ctx->misc);
     double* m64 = reinterpret_cast<double*>(base);
     double* mout = m64 + r;
     uint64_t* kout = reinterpret_cast<uint64_t*>(mout + r);
-    double* boundary = reinterpret_cast<double*>(kout + r);
-    int* rank = reinterpret_cast<int*>(boundary + 2);
-    int* sel = rank + r;
-    long long* nsel_dev = reinterpret_cast<long long*>(ctx->dev_counters + 4);
-    long long nsel = 0;
+    int* rank = reinterpret_cast<int*>(kout + r);
+    int* flags = rank + r;
+    SelTail tail{};
+    tail.boundary[0] = tail.boundary[1] = NAN;
     if (r > 0) {
+        const double nanv[2] = {NAN, NAN};
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(sel->boundary, nanv, sizeof(nanv), cudaMemcpyHostToDevice, ctx->stream));
         FRR_TRY(recheck_launch(ctx, st.seed, st.exact, ctx->ret_idx[cur], r, m64));
-        const double nanv = NAN;
-        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(boundary, &nanv, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(boundary + 1, &nanv, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
         k_rank<<<ceil_div(r * 32, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], r, rank);
         k_select_flags<<<ceil_div(r, 256), 256, 0, ctx->stream>>>(rank, m64, r, st.K, st.q_mode ? 1 : 0, st.threshold,
-                                                                  sel, boundary);
-        k_count_sel<<<1, SNT, 0, ctx->stream>>>(sel, r, nsel_dev);
-        k_place<<<ceil_div(r * 32, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], sel, r, kout, mout);
+                                                                  flags, sel->boundary);
+        k_count_sel<<<1, SNT, 0, ctx->stream>>>(flags, r, &sel->nsel);
+        k_place<<<ceil_div(r * 32, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], flags, r, kout, mout);
+        k_sel_stats<<<1, SNT, 0, ctx->stream>>>(m64, ctx->ret_m[cur], flags, r, cut_params(ctx), sel);
         FRR_CUDA_TRY(ctx, cudaGetLastError());
-        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(&nsel, nsel_dev, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_pinned, &sel->nsel, sizeof(SelTail), cudaMemcpyDeviceToHost,
+                                          ctx->stream));
     }
     cudaEventRecord(ctx->ev[4], ctx->stream);
     FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (r > 0) memcpy(&tail, ctx->host_pinned, sizeof(SelTail));
     float t = 0.f;
     cudaEventElapsedTime(&t, ctx->ev[3], ctx->ev[4]);
     ctx->stats.ms_recheck += t;
+    const long long nsel = tail.nsel;
     *K_out = nsel;
     st.active = false;
 
-    // statistics of the band model over the re-checked draws (host copies of r values)
+    const BandConsts& b = band_of(ctx);
     ctx->stats.candidates = r;
     ctx->stats.accepted = nsel;
-    if (r > 0) {
-        std::vector<double> hm(r), hb(2);
-        std::vector<float> hf(r);
-        std::vector<int> hs(r);
-        FRR_CUDA_TRY(ctx, cudaMemcpy(hm.data(), m64, r * sizeof(double), cudaMemcpyDeviceToHost));
-        FRR_CUDA_TRY(ctx, cudaMemcpy(hf.data(), ctx->ret_m[cur], r * sizeof(float), cudaMemcpyDeviceToHost));
-        FRR_CUDA_TRY(ctx, cudaMemcpy(hs.data(), sel, r * sizeof(int), cudaMemcpyDeviceToHost));
-        FRR_CUDA_TRY(ctx, cudaMemcpy(hb.data(), boundary, 2 * sizeof(double), cudaMemcpyDeviceToHost));
-        const BandConsts& b = band_of(ctx);
-        double mre = 0, meb = 0, thr = -INFINITY;
-        int viol = 0;
-        for (int64_t c = 0; c < r; ++c) {
-            const double err = fabs((double)hf[c] - hm[c]);
-            const double band = band_value(b.lin, b.quad, b.rel, ctx->opts.band_safety, (double)hf[c]);
-            if (hm[c] > 0) mre = std::max(mre, err / hm[c]);
-            if (band > 0) meb = std::max(meb, err / band);
-            if (err > band) ++viol;
-            if (hs[c]) thr = std::max(thr, hm[c]);
-        }
-        ctx->stats.max_rel_err = mre;
-        ctx->stats.max_err_over_band = meb;
-        ctx->stats.band_violations = viol;
-        ctx->stats.threshold_m64 = nsel > 0 ? thr : NAN;
-        ctx->stats.band_at_threshold = nsel > 0 ? band_value(b.lin, b.quad, b.rel, ctx->opts.band_safety, thr) : NAN;
-        if (st.q_mode && !isnan(hb[0]) && !isnan(hb[1])) {
-            ctx->stats.boundary_gap_rel = (hb[1] - hb[0]) / hb[0];
-            ctx->stats.parity_at_risk = ctx->stats.boundary_gap_rel < 1e-11 ? 1 : 0;
-        }
+    ctx->stats.max_rel_err = tail.max_rel;
+    ctx->stats.max_err_over_band = tail.max_over_band;
+    ctx->stats.band_violations = tail.violations;
+    ctx->stats.threshold_m64 = nsel > 0 ? tail.thr : NAN;
+    ctx->stats.band_at_threshold = nsel > 0 ? band_value(b.lin, b.quad, b.rel, ctx->opts.band_safety, tail.thr) : NAN;
+    if (st.q_mode && !isnan(tail.boundary[0]) && !isnan(tail.boundary[1])) {
+        ctx->stats.boundary_gap_rel = (tail.boundary[1] - tail.boundary[0]) / tail.boundary[0];
+        ctx->stats.parity_at_risk = ctx->stats.boundary_gap_rel < 1e-11 ? 1 : 0;
     }
     if (nsel > cap) return FRR_E_CAPACITY;
     if (nsel > 0) {
-        FRR_TRY(copy_out(ctx, keys_out, kout, (size_t)nsel * sizeof(uint64_t)));
-        if (M64_out) FRR_TRY(copy_out(ctx, M64_out, mout, (size_t)nsel * sizeof(double)));
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(keys_out, kout, (size_t)nsel * sizeof(uint64_t), cudaMemcpyDefault, ctx->stream));
+        if (M64_out)
+            FRR_CUDA_TRY(ctx, cudaMemcpyAsync(M64_out, mout, (size_t)nsel * sizeof(double), cudaMemcpyDefault, ctx->stream));
+        FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     }
     return FRR_OK;
 }
