@@ -181,6 +181,47 @@ frr_status frr_randtest(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64
                         const double* Y, const double* tau, int64_t T, double alpha,
                         double* p_out, int64_t* count_out, double* ci_lo, double* ci_hi);
 
+/* One experiment of a batched run (Sec. 2.1 "Batched processing": many independent
+ * rerandomizations evaluated together). Inputs are read; outputs and results are written
+ * by frr_batch_run. Exactly one of q / threshold is used (the other NAN), as in frr_select.
+ * Y == NULL skips the randomization test; otherwise w_obs is the accepted key with the
+ * smallest draw index, as in the paper's usage example, and the test follows frr_randtest. */
+typedef struct {
+    const double* X;           /* host, n x d row-major */
+    int64_t n, d, n1;
+    int whiten;                /* FRR_CHOL, FRR_RIDGE or FRR_DIAG */
+    double ridge;
+    uint64_t seed, first_draw, B;
+    double q, threshold;
+    uint64_t* keys_out;        /* host or device, cap entries (ascending draw index) */
+    double* M64_out;           /* host or device, cap entries, may be NULL */
+    int64_t cap;
+    const double* Y;           /* host or device, n, or NULL */
+    const double* tau;         /* host or device, T */
+    int64_t T;
+    double alpha;
+    double* p_out;             /* host or device, T */
+    int64_t* count_out;        /* host or device, T, may be NULL */
+    double ci_lo, ci_hi;       /* out: interval (NAN if empty) */
+    int64_t K_out;             /* out: accepted count */
+    frr_status status;         /* out: status of this experiment */
+} frr_experiment;
+
+typedef struct {
+    int64_t experiments, draws, failed;
+    double ms_init;            /* wall time of the preparation of all experiments */
+    double ms_balance;         /* device time of the balance evaluation of all experiments */
+    double ms_select;          /* wall time of selection, recheck and tests */
+} frr_batch_stats;
+
+/* Runs E independent experiments (Sec. 2.1 batched processing). With opts->precision =
+ * FRR_SPLIT_BF16 the balance of every draw of every experiment is evaluated by one
+ * persistent tensor-core launch over all experiments (shapes may differ); selection,
+ * recheck and tests follow per experiment. opts: NULL for defaults (its whiten and ridge
+ * are ignored; each experiment carries its own). Returns FRR_OK if every experiment
+ * succeeded, else the first failing status; ex[e].status holds each one. stats may be NULL. */
+frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opts* opts, frr_batch_stats* stats);
+
 /* Copies the whitened covariates Zc (host, n x d row-major FP64) out of the context. */
 frr_status frr_whitened(const frr_ctx* ctx, double* Zc_out);
 

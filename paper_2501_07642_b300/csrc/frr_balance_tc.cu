@@ -24,6 +24,8 @@
 
 #include <cuda.h>
 
+#include "frr_tcexp.cuh"
+
 namespace frr {
 namespace {
 
@@ -144,16 +146,9 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-struct TcParams {
-    int n, n1, d, kused, nkb, nchunks;
-    float c_M;
-    uint64_t seed;
-    int exact;
-    const uint64_t* binom;
-    uint64_t first, B, tiles;
-    float* Mout;
-    int* err;
-};
+}  // namespace
+
+namespace {
 
 // Bounded wait. Returns false (and raises the CTA abort flag) on expiry or abort.
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err, int code)
@@ -172,9 +167,37 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
     }
 }
 
-template <int KB, int SB, int NG>
+// Experiment and local tile index of global tile g: the single experiment `one`, or
+// the entry e of `table` with prefix[e] <= g < prefix[e + 1].
+__device__ __forceinline__ const TcExp* tile_job(const TcExp* one, const TcExp* table, const unsigned long long* prefix,
+                                                 int E, uint64_t g, uint64_t& tl)
+{
+    if (table == nullptr) { tl = g; return one; }
+    int lo = 0, hi = E;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= g) lo = mid; else hi = mid;
+    }
+    tl = g - prefix[lo];
+    return table + lo;
+}
+
+// Bit row of one draw for a run-time number of Philox blocks per lane kb <= KBMAX.
+template <int KBMAX>
+__device__ __forceinline__ void draw_bits_kb(int kb, bool exact, uint64_t seed, uint64_t draw, int n, int n1,
+                                             const uint64_t* binom, uint32_t* row, int lane)
+{
+    if constexpr (KBMAX >= 16) { if (kb == 16) { warp_draw_bits<16>(exact, seed, draw, n, n1, binom, row, lane); return; } }
+    if constexpr (KBMAX >= 8) { if (kb == 8) { warp_draw_bits<8>(exact, seed, draw, n, n1, binom, row, lane); return; } }
+    if constexpr (KBMAX >= 4) { if (kb == 4) { warp_draw_bits<4>(exact, seed, draw, n, n1, binom, row, lane); return; } }
+    if constexpr (KBMAX >= 2) { if (kb == 2) { warp_draw_bits<2>(exact, seed, draw, n, n1, binom, row, lane); return; } }
+    warp_draw_bits<1>(exact, seed, draw, n, n1, binom, row, lane);
+}
+
+template <int KB, int SB, int NG, bool MULTI>
 __global__ void __launch_bounds__((6 + kExpWarps + NG) * 32, 1)
-k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, TcParams P)
+k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
+             const unsigned long long* __restrict__ prefix, int E, unsigned long long tiles, int* err)
 {
     constexpr int W = 4 * KB;  // bit-row words per draw
     constexpr int RS = W + 1;  // odd row stride: the expansion threads read 32 rows without bank conflicts
@@ -221,24 +244,27 @@ k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__
     tc_fence_after();
     const uint32_t tmem_base = *sTmem;
 
-    const uint64_t tiles = P.tiles;
-    const int nkb = P.nkb, nch = P.nchunks;
 
     if (warp == 4) {
         // ------------------------------------------------------------ TMA --
         if (lane == 0) {
             uint32_t bi = 0;
             bool ok = true;
-            for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x)
+            for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                uint64_t tl;
+                const TcExp* x = tile_job(&one, table, prefix, E, t, tl);
+                const int nch = x->nchunks, nkb = x->nkb;
                 for (int c = 0; c < nch && ok; ++c)
                     for (int kb = 0; kb < nkb && ok; ++kb)
                         for (int part = 0; part < 2 && ok; ++part, ++bi) {
                             const int s = bi % SB;
                             const uint32_t ph = (bi / SB) & 1u;
-                            if (!(ok = wait_bar(&b_empty[s], ph ^ 1u, sAbort, P.err, 1))) break;
+                            if (!(ok = wait_bar(&b_empty[s], ph ^ 1u, sAbort, err, 1))) break;
                             mbar_arrive_expect_tx(&b_full[s], kBBytes);
-                            tma_load_2d(sB + s * kBBytes, part ? &map_lo : &map_hi, &b_full[s], kb * kKBlock, c * kChunkN);
+                            tma_load_2d(sB + s * kBBytes, part ? &x->map_lo : &x->map_hi, &b_full[s], kb * kKBlock,
+                                        c * kChunkN);
                         }
+            }
             if (!ok) {
                 // drain the copies this thread may still have in flight
                 const uint32_t from = bi > (uint32_t)SB ? bi - SB : 0u;
@@ -254,21 +280,24 @@ k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__
             uint32_t ai = 0, bi = 0, g = 0;
             bool ok = true;
             for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                uint64_t tl;
+                const TcExp* x = tile_job(&one, table, prefix, E, t, tl);
+                const int nch = x->nchunks, nkb = x->nkb, dd = x->d;
                 for (int c = 0; c < nch && ok; ++c, ++g) {
                     const int buf = g & 1;
-                    if (!(ok = wait_bar(&acc_empty[buf], ((g >> 1) & 1u) ^ 1u, sAbort, P.err, 2))) break;
+                    if (!(ok = wait_bar(&acc_empty[buf], ((g >> 1) & 1u) ^ 1u, sAbort, err, 2))) break;
                     tc_fence_after();
-                    const int rem = P.d - c * kChunkN;
+                    const int rem = dd - c * kChunkN;
                     const int N = rem >= kChunkN ? kChunkN : ((rem + 15) / 16) * 16;
                     const uint32_t idesc = idesc_bf16(kTileM, N);
                     const uint32_t dt = tmem_base + (uint32_t)(buf * kChunkN);
                     for (int kb = 0; kb < nkb && ok; ++kb, ++ai) {
                         const int sa = ai % kStagesA;
-                        if (!(ok = wait_bar(&a_full[sa], (ai / kStagesA) & 1u, sAbort, P.err, 3))) break;
+                        if (!(ok = wait_bar(&a_full[sa], (ai / kStagesA) & 1u, sAbort, err, 3))) break;
                         const uint64_t adesc = sdesc_sw128(smem_u32(sA + sa * kABytes));
                         for (int part = 0; part < 2; ++part, ++bi) {
                             const int sb = bi % SB;
-                            if (!(ok = wait_bar(&b_full[sb], (bi / SB) & 1u, sAbort, P.err, 4))) break;
+                            if (!(ok = wait_bar(&b_full[sb], (bi / SB) & 1u, sAbort, err, 4))) break;
                             tc_fence_after();
                             const uint64_t bdesc = sdesc_sw128(smem_u32(sB + sb * kBBytes));
 #pragma unroll
@@ -295,13 +324,16 @@ k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__
         uint32_t it = 0;
         bool ok = true;
         for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
+            uint64_t tl;
+            const TcExp* x = tile_job(&one, table, prefix, E, t, tl);
+            const int nch = x->nchunks, nkb = x->nkb;
             const int bb = it & 1;
-            if (!(ok = wait_bar(&bits_full[bb], (it >> 1) & 1u, sAbort, P.err, 5))) break;
+            if (!(ok = wait_bar(&bits_full[bb], (it >> 1) & 1u, sAbort, err, 5))) break;
             const uint32_t* row = sBits + bb * kTileM * RS + r * RS;
             for (int c = 0; c < nch && ok; ++c)
                 for (int kb = 0; kb < nkb; ++kb, ++ai) {
                     const int s = ai % kStagesA;
-                    if (!(ok = wait_bar(&a_empty[s], ((ai / kStagesA) & 1u) ^ 1u, sAbort, P.err, 6))) break;
+                    if (!(ok = wait_bar(&a_empty[s], ((ai / kStagesA) & 1u) ^ 1u, sAbort, err, 6))) break;
                     unsigned char* dst = sA + s * kABytes + (r >> 3) * 1024 + (r & 7) * 128;
                     const uint32_t w2[2] = {row[2 * kb], row[2 * kb + 1]};
 #pragma unroll
@@ -331,14 +363,20 @@ k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__
         uint32_t it = 0;
         bool ok = true;
         for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
+            uint64_t tl;
+            const TcExp* x = tile_job(&one, table, prefix, E, t, tl);
             const int bb = it & 1;
-            if (!(ok = wait_bar(&bits_empty[bb], ((it >> 1) & 1u) ^ 1u, sAbort, P.err, 7))) break;
+            if (!(ok = wait_bar(&bits_empty[bb], ((it >> 1) & 1u) ^ 1u, sAbort, err, 7))) break;
             uint32_t* bits = sBits + bb * kTileM * RS;
+            const int kbx = x->kb, nx = x->n, n1x = x->n1, ex = x->exact;
+            const uint64_t sx = x->seed, fx = x->first, Bx = x->B;
+            const uint64_t* bx = x->binom;
             for (int r = gw; r < kTileM; r += NG) {
-                const uint64_t off = t * kTileM + r;
+                const uint64_t off = tl * kTileM + r;
                 uint32_t* row = bits + r * RS;
-                if (off < P.B) {
-                    warp_draw_bits<KB>(P.exact != 0, P.seed, P.first + off, P.n, P.n1, P.binom, row, lane);
+                if (off < Bx) {
+                    if constexpr (MULTI) draw_bits_kb<KB>(kbx, ex != 0, sx, fx + off, nx, n1x, bx, row, lane);
+                    else warp_draw_bits<KB>(ex != 0, sx, fx + off, nx, n1x, bx, row, lane);
                 } else {
                     for (int q = lane; q < W; q += 32) row[q] = 0u;
                 }
@@ -352,12 +390,15 @@ k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__
         uint32_t g = 0;
         bool ok = true;
         for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+            uint64_t tl;
+            const TcExp* x = tile_job(&one, table, prefix, E, t, tl);
+            const int nch = x->nchunks, dd = x->d;
             float sumsq = 0.f;
             for (int c = 0; c < nch; ++c, ++g) {
                 const int buf = g & 1;
-                if (!(ok = wait_bar(&acc_full[buf], (g >> 1) & 1u, sAbort, P.err, 8))) break;
+                if (!(ok = wait_bar(&acc_full[buf], (g >> 1) & 1u, sAbort, err, 8))) break;
                 tc_fence_after();
-                const int rem = P.d - c * kChunkN;
+                const int rem = dd - c * kChunkN;
                 const int N = rem >= kChunkN ? kChunkN : rem;
                 const uint32_t taddr = tmem_base + ((uint32_t)(32 * ew) << 16) + (uint32_t)(buf * kChunkN);
                 for (int c0 = 0; c0 < N; c0 += 32) {
@@ -375,8 +416,8 @@ k_balance_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acc_empty[buf]);
             }
-            const uint64_t off = t * kTileM + 32 * ew + lane;
-            if (ok && off < P.B) P.Mout[off] = P.c_M * sumsq;
+            const uint64_t off = tl * kTileM + 32 * ew + lane;
+            if (ok && off < x->B) x->Mout[off] = x->c_M * sumsq;
         }
     }
 
@@ -427,54 +468,89 @@ size_t smem_bytes(int KB, int SB)
 }
 
 template <int KB, int SB, int NG>
-frr_status launch(frr_ctx* ctx, const CUtensorMap& mh, const CUtensorMap& ml, const TcParams& P)
+frr_status launch(frr_ctx* ctx, cudaStream_t stream, int num_sms, const TcExp& one, const TcExp* table,
+                  const unsigned long long* prefix, int E, unsigned long long tiles, int* err)
 {
     const size_t smem = smem_bytes(KB, SB);
-    FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_balance_tc<KB, SB, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const unsigned grid = (unsigned)(P.tiles < (uint64_t)ctx->num_sms ? P.tiles : (uint64_t)ctx->num_sms);
-    k_balance_tc<KB, SB, NG><<<grid, (6 + kExpWarps + NG) * 32, smem, ctx->stream>>>(mh, ml, P);
+    const unsigned grid = (unsigned)(tiles < (unsigned long long)num_sms ? tiles : (unsigned long long)num_sms);
+    if (table == nullptr) {
+        FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_balance_tc<KB, SB, NG, false>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_balance_tc<KB, SB, NG, false><<<grid, (6 + kExpWarps + NG) * 32, smem, stream>>>(one, table, prefix, E, tiles, err);
+    } else {
+        FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_balance_tc<KB, SB, NG, true>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_balance_tc<KB, SB, NG, true><<<grid, (6 + kExpWarps + NG) * 32, smem, stream>>>(one, table, prefix, E, tiles, err);
+    }
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     return FRR_OK;
 }
 
+frr_status launch_kb(frr_ctx* ctx, int kbmax, cudaStream_t stream, int num_sms, const TcExp& one, const TcExp* table,
+                     const unsigned long long* prefix, int E, unsigned long long tiles, int* err)
+{
+    switch (kbmax) {
+        case 1: return launch<1, 4, 10>(ctx, stream, num_sms, one, table, prefix, E, tiles, err);
+        case 2: return launch<2, 4, 10>(ctx, stream, num_sms, one, table, prefix, E, tiles, err);
+        case 4: return launch<4, 4, 10>(ctx, stream, num_sms, one, table, prefix, E, tiles, err);
+        case 8: return launch<8, 4, 10>(ctx, stream, num_sms, one, table, prefix, E, tiles, err);
+        case 16: return launch<16, 3, 6>(ctx, stream, num_sms, one, table, prefix, E, tiles, err);
+        default: return FRR_E_UNSUPPORTED;
+    }
+}
+
 }  // namespace
+
+// Fills the experiment descriptor of a prepared context for draws [first, first + B).
+frr_status tc_describe(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout, TcExp* x)
+{
+    if (!make_map(&x->map_hi, ctx->Zhi, ctx->kpad, (int)ctx->d) || !make_map(&x->map_lo, ctx->Zlo, ctx->kpad, (int)ctx->d))
+        return FRR_E_CUDA;
+    x->binom = ctx->binom;
+    x->Mout = Mout;
+    x->seed = seed;
+    x->first = first;
+    x->B = B;
+    x->c_M = (float)ctx->c_M;
+    x->n = (int)ctx->n;
+    x->n1 = (int)ctx->n1;
+    x->d = (int)ctx->d;
+    x->kb = ctx->kb;
+    x->nkb = ctx->kused / kKBlock;
+    x->nchunks = ceil_div(ctx->d, kChunkN);
+    x->exact = exact ? 1 : 0;
+    return FRR_OK;
+}
 
 frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout)
 {
     if (B == 0) return FRR_OK;
     static thread_local const frr_ctx* cached_ctx = nullptr;
     static thread_local const void* cached_hi = nullptr;
-    static thread_local CUtensorMap mh, ml;
+    static thread_local TcExp one;
     if (cached_ctx != ctx || cached_hi != ctx->Zhi) {
-        if (!make_map(&mh, ctx->Zhi, ctx->kpad, (int)ctx->d) || !make_map(&ml, ctx->Zlo, ctx->kpad, (int)ctx->d))
-            return FRR_E_CUDA;
+        FRR_TRY(tc_describe(ctx, seed, exact, first, B, Mout, &one));
         cached_ctx = ctx;
         cached_hi = ctx->Zhi;
     }
-    TcParams P;
-    P.n = (int)ctx->n;
-    P.n1 = (int)ctx->n1;
-    P.d = (int)ctx->d;
-    P.kused = ctx->kused;
-    P.nkb = ctx->kused / kKBlock;
-    P.nchunks = ceil_div(ctx->d, kChunkN);
-    P.c_M = (float)ctx->c_M;
-    P.seed = seed;
-    P.exact = exact ? 1 : 0;
-    P.binom = ctx->binom;
-    P.first = first;
-    P.B = B;
-    P.tiles = (B + kTileM - 1) / kTileM;
-    P.Mout = Mout;
-    P.err = ctx->dev_counters + 12;
-    switch (ctx->kb) {
-        case 1: return launch<1, 4, 10>(ctx, mh, ml, P);
-        case 2: return launch<2, 4, 10>(ctx, mh, ml, P);
-        case 4: return launch<4, 4, 10>(ctx, mh, ml, P);
-        case 8: return launch<8, 4, 10>(ctx, mh, ml, P);
-        case 16: return launch<16, 3, 6>(ctx, mh, ml, P);
-        default: return FRR_E_UNSUPPORTED;
-    }
+    one.Mout = Mout;
+    one.seed = seed;
+    one.first = first;
+    one.B = B;
+    one.exact = exact ? 1 : 0;
+    const unsigned long long tiles = (B + kTileM - 1) / kTileM;
+    return launch_kb(ctx, ctx->kb, ctx->stream, ctx->num_sms, one, nullptr, nullptr, 1, tiles, ctx->dev_counters + 12);
+}
+
+// One persistent launch over E experiments: `table` (device, E entries) describes them,
+// `prefix` (device, E + 1 entries) holds the first global tile of each. kbmax bounds their
+// Philox blocks per lane. Errors from bounded waits go to *err (device).
+frr_status balance_tc_batch_launch(frr_ctx* owner, const TcExp* table, const unsigned long long* prefix, int E,
+                                   unsigned long long tiles, int kbmax, int* err)
+{
+    if (tiles == 0) return FRR_OK;
+    TcExp unused{};
+    return launch_kb(owner, kbmax, owner->stream, owner->num_sms, unused, table, prefix, E, tiles, err);
 }
 
 }  // namespace frr

@@ -1,0 +1,179 @@
+// frr_batch.cu -- frr_batch_run: many independent experiments, one balance launch.
+//
+// Sec. 2.1 evaluates candidates in batches to amortise launches and saturate the
+// device. Here the batch is a set of whole experiments of uneven n and d: each is
+// prepared (FP64 init) on its own, then the approximate balance of every draw of every
+// experiment comes from ONE persistent tcgen05 launch whose global tile index space
+// concatenates the experiments' draw tiles (experiment tables in device memory), so
+// small and large experiments share all SMs. Selection, exact recheck and the
+// randomization test then run per experiment on the resulting M_hat arrays.
+#include "frr_internal.cuh"
+
+#include <chrono>
+#include <cuda.h>
+#include <vector>
+
+#include "frr_tcexp.cuh"
+
+namespace frr {
+
+frr_status tc_describe(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout, TcExp* x);
+frr_status balance_tc_batch_launch(frr_ctx* owner, const TcExp* table, const unsigned long long* prefix, int E,
+                                   unsigned long long tiles, int kbmax, int* err);
+
+}  // namespace frr
+
+using namespace frr;
+
+extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opts* opts, frr_batch_stats* stats)
+{
+    if (!ex || E < 1) return FRR_E_ARG;
+    frr_opts base;
+    frr_default_opts(&base);
+    if (opts) base = *opts;
+    if (base.precision != FRR_SPLIT_BF16 && base.precision != FRR_F32) return FRR_E_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<frr_ctx*> ctx((size_t)E, nullptr);
+    frr_status first_err = FRR_OK;
+    auto note = [&](int64_t e, frr_status s) {
+        ex[e].status = s;
+        if (s != FRR_OK && first_err == FRR_OK) first_err = s;
+    };
+    cudaStream_t stream = static_cast<cudaStream_t>(base.cuda_stream);
+    bool own_stream = false;
+    if (!stream) {
+        if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return FRR_E_CUDA; }
+        own_stream = true;
+    }
+    int64_t draws = 0;
+    for (int64_t e = 0; e < E; ++e) {
+        ex[e].K_out = 0;
+        ex[e].ci_lo = ex[e].ci_hi = NAN;
+        const bool hq = !isnan(ex[e].q), ht = !isnan(ex[e].threshold);
+        if (hq == ht || (hq && !(ex[e].q > 0.0 && ex[e].q <= 1.0)) || (ht && !(ex[e].threshold >= 0.0)) || ex[e].B == 0 ||
+            ex[e].first_draw + ex[e].B < ex[e].first_draw) {
+            note(e, FRR_E_ARG);
+            continue;
+        }
+        frr_opts o = base;
+        o.whiten = ex[e].whiten;
+        o.ridge = ex[e].ridge;
+        o.cuda_stream = stream;
+        const frr_status s = frr_init(&ctx[e], ex[e].X, ex[e].n, ex[e].d, ex[e].n1, &o);
+        note(e, s);
+        if (s != FRR_OK) ctx[e] = nullptr;
+        else if (ex[e].seed == FRR_EXACT_SEED &&
+                 (ex[e].n > kExactMaxN || ex[e].first_draw + ex[e].B > binom_host((int)ex[e].n, (int)ex[e].n1))) {
+            note(e, ex[e].n > kExactMaxN ? FRR_E_UNSUPPORTED : FRR_E_RANGE);
+            frr_destroy(ctx[e]);
+            ctx[e] = nullptr;
+        }
+    }
+    const auto t1 = std::chrono::steady_clock::now();
+
+    // approximate M of every draw of every prepared experiment
+    std::vector<int64_t> live;
+    for (int64_t e = 0; e < E; ++e)
+        if (ctx[e]) live.push_back(e);
+    float* mhat = nullptr;
+    TcExp* d_table = nullptr;
+    unsigned long long* d_prefix = nullptr;
+    int* d_err = nullptr;
+    float ms_balance = 0.f;
+    frr_status rc = FRR_OK;
+    if (!live.empty()) {
+        std::vector<size_t> off(live.size() + 1, 0);
+        for (size_t k = 0; k < live.size(); ++k) off[k + 1] = off[k] + ex[live[k]].B;
+        frr_ctx* owner = ctx[live[0]];
+        cudaEvent_t ea, eb;
+        cudaEventCreate(&ea);
+        cudaEventCreate(&eb);
+        if (cudaMalloc(&mhat, off.back() * sizeof(float)) != cudaSuccess) { cudaGetLastError(); rc = FRR_E_NOMEM; }
+        if (rc == FRR_OK && base.precision == FRR_SPLIT_BF16) {
+            std::vector<TcExp> table(live.size());
+            std::vector<unsigned long long> prefix(live.size() + 1, 0);
+            int kbmax = 1;
+            for (size_t k = 0; k < live.size() && rc == FRR_OK; ++k) {
+                const frr_experiment& x = ex[live[k]];
+                rc = tc_describe(ctx[live[k]], x.seed, x.seed == FRR_EXACT_SEED, x.first_draw, x.B, mhat + off[k],
+                                 &table[k]);
+                prefix[k + 1] = prefix[k] + (x.B + 127) / 128;
+                if (ctx[live[k]]->kb > kbmax) kbmax = ctx[live[k]]->kb;
+            }
+            if (rc == FRR_OK &&
+                (cudaMalloc(&d_table, table.size() * sizeof(TcExp)) != cudaSuccess ||
+                 cudaMalloc(&d_prefix, prefix.size() * sizeof(unsigned long long)) != cudaSuccess ||
+                 cudaMalloc(&d_err, sizeof(int)) != cudaSuccess)) {
+                cudaGetLastError();
+                rc = FRR_E_NOMEM;
+            }
+            if (rc == FRR_OK) {
+                cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(TcExp), cudaMemcpyHostToDevice, stream);
+                cudaMemcpyAsync(d_prefix, prefix.data(), prefix.size() * sizeof(unsigned long long),
+                                cudaMemcpyHostToDevice, stream);
+                cudaMemsetAsync(d_err, 0, sizeof(int), stream);
+                cudaEventRecord(ea, stream);
+                rc = balance_tc_batch_launch(owner, d_table, d_prefix, (int)live.size(), prefix.back(), kbmax, d_err);
+                cudaEventRecord(eb, stream);
+                int herr = 0;
+                if (cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+                    cudaStreamSynchronize(stream) != cudaSuccess) {
+                    cudaGetLastError();
+                    rc = FRR_E_CUDA;
+                } else if (herr != 0) {
+                    rc = FRR_E_TIMEOUT;
+                }
+            }
+        } else if (rc == FRR_OK) {
+            cudaEventRecord(ea, stream);
+            for (size_t k = 0; k < live.size() && rc == FRR_OK; ++k) {
+                const frr_experiment& x = ex[live[k]];
+                rc = balance_f32_launch(ctx[live[k]], x.seed, x.seed == FRR_EXACT_SEED, x.first_draw, x.B, mhat + off[k]);
+            }
+            cudaEventRecord(eb, stream);
+            if (cudaStreamSynchronize(stream) != cudaSuccess) { cudaGetLastError(); rc = FRR_E_CUDA; }
+        }
+        cudaEventElapsedTime(&ms_balance, ea, eb);
+        cudaEventDestroy(ea);
+        cudaEventDestroy(eb);
+        for (size_t k = 0; k < live.size(); ++k) {
+            const int64_t e = live[k];
+            frr_experiment& x = ex[e];
+            if (rc != FRR_OK) { note(e, rc); continue; }
+            frr_status s = stream_begin(ctx[e], x.seed, x.q, x.threshold, x.B);
+            if (s == FRR_OK) s = stream_chunk_precomputed(ctx[e], x.first_draw, x.B, mhat + off[k]);
+            int64_t K = 0;
+            if (s == FRR_OK) s = stream_end(ctx[e], x.keys_out, x.M64_out, x.cap, &K);
+            x.K_out = K;
+            if (s == FRR_OK && x.Y != nullptr && K > 0) {
+                uint64_t obs = 0;
+                s = copy_out(ctx[e], &obs, x.keys_out, sizeof(uint64_t));
+                if (s == FRR_OK) {
+                    if (!x.tau || x.T < 1 || !x.p_out || !(x.alpha >= 0.0 && x.alpha <= 1.0)) s = FRR_E_ARG;
+                    else s = randtest_run(ctx[e], x.seed, x.keys_out, K, obs, x.Y, x.tau, x.T, x.alpha, x.p_out,
+                                          x.count_out, &x.ci_lo, &x.ci_hi);
+                }
+            }
+            note(e, s);
+            draws += (int64_t)x.B;
+        }
+    }
+    const auto t2 = std::chrono::steady_clock::now();
+    cudaFree(mhat);
+    cudaFree(d_table);
+    cudaFree(d_prefix);
+    cudaFree(d_err);
+    for (frr_ctx* c : ctx) frr_destroy(c);
+    if (own_stream) cudaStreamDestroy(stream);
+    if (stats) {
+        stats->experiments = E;
+        stats->draws = draws;
+        int64_t failed = 0;
+        for (int64_t e = 0; e < E; ++e) failed += ex[e].status != FRR_OK ? 1 : 0;
+        stats->failed = failed;
+        stats->ms_init = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        stats->ms_balance = ms_balance;
+        stats->ms_select = std::chrono::duration<double, std::milli>(t2 - t1).count() - ms_balance;
+    }
+    return first_err;
+}

@@ -132,6 +132,7 @@ frr_status recheck_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_
 frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold, uint64_t total);
 frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B);
 frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out);
+frr_status stream_chunk_precomputed(frr_ctx* ctx, uint64_t first, uint64_t B, const float* Mhat_dev);
 frr_status randtest_run(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64_t K, uint64_t obs_key,
                         const double* Y, const double* tau, int64_t T, double alpha, double* p_out,
                         int64_t* count_out, double* ci_lo, double* ci_hi);

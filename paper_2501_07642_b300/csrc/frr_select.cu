@@ -576,71 +576,98 @@ frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold,
     return FRR_OK;
 }
 
+// Selection step over the approximate M of draws [first, first + bc) held in Mhat (device).
+frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const float* Mhat)
+{
+    StreamState& st = ctx->st;
+    SelState* sel = static_cast<SelState*>(ctx->sel);
+    const CutParams cp = cut_params(ctx);
+    FRR_TRY(ensure_host_pinned(ctx, 256));
+    const int in = ctx->ret_cur, out = 1 - in;
+    const int64_t N = st.retained + (int64_t)bc;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(N, kHistThreads), 4 * ctx->num_sms));
+    k_sel_begin<<<1, 32, 0, ctx->stream>>>(sel, st.K);
+    if (st.q_mode && N > st.K) {
+        k_sel_hist<<<grid, kHistThreads, 0, ctx->stream>>>(Mhat, (int64_t)bc, ctx->ret_m[in], st.retained, 0, sel);
+        k_sel_scan<<<1, SNT, 0, ctx->stream>>>(sel, 0, cp);
+        k_sel_hist<<<grid, kHistThreads, 0, ctx->stream>>>(Mhat, (int64_t)bc, ctx->ret_m[in], st.retained, 1, sel);
+        k_sel_scan<<<1, SNT, 0, ctx->stream>>>(sel, 1, cp);
+    }
+    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    int64_t cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
+    const int64_t want = std::min<int64_t>(N, std::max<int64_t>(4 * st.K + 65536, 1 << 20));
+    if (cap < want) {
+        FRR_TRY(ensure_retained(ctx, out, want));
+        cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
+    }
+    for (int attempt = 0;; ++attempt) {
+        k_sel_compact<<<grid, kHistThreads, 0, ctx->stream>>>(Mhat, (int64_t)bc, first, ctx->ret_m[in],
+                                                             ctx->ret_idx[in], st.retained, sel, ctx->ret_m[out],
+                                                             ctx->ret_idx[out], cap);
+        FRR_CUDA_TRY(ctx, cudaGetLastError());
+        long long* hk = static_cast<long long*>(ctx->host_pinned);
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk, &sel->kept, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk + 1, ctx->dev_counters + 12, sizeof(int), cudaMemcpyDeviceToHost,
+                                          ctx->stream));
+        cudaEventRecord(ctx->ev[2], ctx->stream);
+        FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        const long long kept = hk[0];
+        if (*reinterpret_cast<int*>(hk + 1) != 0) {
+            FRR_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dev_counters + 12, 0, sizeof(int), ctx->stream));
+            FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            return FRR_E_TIMEOUT;
+        }
+        if (kept <= cap) {
+            st.retained = kept;
+            break;
+        }
+        if (attempt == 1) return FRR_E_CAPACITY;
+        // the cut stays as computed, so the re-run keeps the same set
+        FRR_TRY(ensure_retained(ctx, out, kept));
+        cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
+        k_sel_begin<<<1, 32, 0, ctx->stream>>>(sel, st.K);
+    }
+    ctx->ret_cur = out;
+    return FRR_OK;
+}
+
 frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B)
 {
     StreamState& st = ctx->st;
     if (!st.active) return FRR_E_STATE;
     if (B == 0) return FRR_OK;
     if (st.seen + B > st.total) return FRR_E_RANGE;
-    SelState* sel = static_cast<SelState*>(ctx->sel);
-    const CutParams cp = cut_params(ctx);
-    FRR_TRY(ensure_host_pinned(ctx, 256));
     for (uint64_t off = 0; off < B; off += kChunkMax) {
         const uint64_t bc = std::min<uint64_t>(kChunkMax, B - off);
         FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->Mhat), &ctx->Mhat_bytes, bc * sizeof(float)));
         cudaEventRecord(ctx->ev[0], ctx->stream);
         FRR_TRY(balance_launch(ctx, st.seed, st.exact, first + off, bc, ctx->Mhat));
         cudaEventRecord(ctx->ev[1], ctx->stream);
-        const int in = ctx->ret_cur, out = 1 - in;
-        const int64_t N = st.retained + (int64_t)bc;
-        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(N, kHistThreads), 4 * ctx->num_sms));
-        k_sel_begin<<<1, 32, 0, ctx->stream>>>(sel, st.K);
-        if (st.q_mode && N > st.K) {
-            k_sel_hist<<<grid, kHistThreads, 0, ctx->stream>>>(ctx->Mhat, (int64_t)bc, ctx->ret_m[in], st.retained, 0, sel);
-            k_sel_scan<<<1, SNT, 0, ctx->stream>>>(sel, 0, cp);
-            k_sel_hist<<<grid, kHistThreads, 0, ctx->stream>>>(ctx->Mhat, (int64_t)bc, ctx->ret_m[in], st.retained, 1, sel);
-            k_sel_scan<<<1, SNT, 0, ctx->stream>>>(sel, 1, cp);
-        }
-        FRR_CUDA_TRY(ctx, cudaGetLastError());
-        int64_t cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
-        const int64_t want = std::min<int64_t>(N, std::max<int64_t>(4 * st.K + 65536, 1 << 20));
-        if (cap < want) {
-            FRR_TRY(ensure_retained(ctx, out, want));
-            cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
-        }
-        for (int attempt = 0;; ++attempt) {
-            k_sel_compact<<<grid, kHistThreads, 0, ctx->stream>>>(ctx->Mhat, (int64_t)bc, first + off, ctx->ret_m[in],
-                                                                 ctx->ret_idx[in], st.retained, sel, ctx->ret_m[out],
-                                                                 ctx->ret_idx[out], cap);
-            FRR_CUDA_TRY(ctx, cudaGetLastError());
-            long long* hk = static_cast<long long*>(ctx->host_pinned);
-            FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk, &sel->kept, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
-            FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk + 1, ctx->dev_counters + 12, sizeof(int), cudaMemcpyDeviceToHost,
-                                              ctx->stream));
-            cudaEventRecord(ctx->ev[2], ctx->stream);
-            FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-            const long long kept = hk[0];
-            if (*reinterpret_cast<int*>(hk + 1) != 0) {
-                FRR_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dev_counters + 12, 0, sizeof(int), ctx->stream));
-                FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-                return FRR_E_TIMEOUT;
-            }
-            if (kept <= cap) {
-                st.retained = kept;
-                break;
-            }
-            if (attempt == 1) return FRR_E_CAPACITY;
-            // the cut stays as computed, so the re-run keeps the same set
-            FRR_TRY(ensure_retained(ctx, out, kept));
-            cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
-            k_sel_begin<<<1, 32, 0, ctx->stream>>>(sel, st.K);
-        }
+        FRR_TRY(stream_select_step(ctx, first + off, bc, ctx->Mhat));
         float t1 = 0.f, t2 = 0.f;
         cudaEventElapsedTime(&t1, ctx->ev[0], ctx->ev[1]);
         cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
         ctx->stats.ms_balance += t1;
         ctx->stats.ms_select += t2;
-        ctx->ret_cur = out;
+    }
+    st.seen += B;
+    ctx->stats.draws += (int64_t)B;
+    return FRR_OK;
+}
+
+// Selection over draws whose approximate M was computed elsewhere (the batched launch).
+frr_status stream_chunk_precomputed(frr_ctx* ctx, uint64_t first, uint64_t B, const float* Mhat)
+{
+    StreamState& st = ctx->st;
+    if (!st.active) return FRR_E_STATE;
+    if (st.seen + B > st.total) return FRR_E_RANGE;
+    for (uint64_t off = 0; off < B; off += kChunkMax) {
+        const uint64_t bc = std::min<uint64_t>(kChunkMax, B - off);
+        cudaEventRecord(ctx->ev[1], ctx->stream);
+        FRR_TRY(stream_select_step(ctx, first + off, bc, Mhat + off));
+        float t2 = 0.f;
+        cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
+        ctx->stats.ms_select += t2;
     }
     st.seen += B;
     ctx->stats.draws += (int64_t)B;

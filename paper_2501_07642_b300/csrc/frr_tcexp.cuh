@@ -1,0 +1,19 @@
+// frr_tcexp.cuh -- descriptor of one experiment for the tensor-core balance kernel.
+#pragma once
+#include <cuda.h>
+#include <stdint.h>
+
+namespace frr {
+
+// One experiment as the tensor kernel sees it (also the layout of the device table
+// used by the batched launch). The tensor maps describe its Zc hi / lo arrays.
+struct TcExp {
+    CUtensorMap map_hi, map_lo;
+    const uint64_t* binom;
+    float* Mout;          // approximate M of draw first + i goes to Mout[i]
+    uint64_t seed, first, B;
+    float c_M;
+    int n, n1, d, kb, nkb, nchunks, exact;
+};
+
+}  // namespace frr

@@ -52,6 +52,22 @@ class frr_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class frr_experiment(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int64), ("n1", ctypes.c_int64),
+                ("whiten", ctypes.c_int), ("ridge", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("first_draw", ctypes.c_uint64), ("B", ctypes.c_uint64), ("q", ctypes.c_double),
+                ("threshold", ctypes.c_double), ("keys_out", ctypes.c_void_p), ("M64_out", ctypes.c_void_p),
+                ("cap", ctypes.c_int64), ("Y", ctypes.c_void_p), ("tau", ctypes.c_void_p), ("T", ctypes.c_int64),
+                ("alpha", ctypes.c_double), ("p_out", ctypes.c_void_p), ("count_out", ctypes.c_void_p),
+                ("ci_lo", ctypes.c_double), ("ci_hi", ctypes.c_double), ("K_out", ctypes.c_int64),
+                ("status", ctypes.c_int)]
+
+
+class frr_batch_stats(ctypes.Structure):
+    _fields_ = [("experiments", ctypes.c_int64), ("draws", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("ms_init", ctypes.c_double), ("ms_balance", ctypes.c_double), ("ms_select", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -81,6 +97,7 @@ def lib():
             "frr_randtest": (c.c_int, [P, U64, P, I64, U64, P, P, I64, D, P, P, P, P]),
             "frr_whitened": (c.c_int, [P, P]),
             "frr_last_stats": (c.c_int, [P, P]),
+            "frr_batch_run": (c.c_int, [P, I64, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -254,3 +271,67 @@ def frr_last_stats(ctx: Context) -> dict:
     s = frr_stats()
     _check(lib().frr_last_stats(ctx.handle, ctypes.byref(s)), "frr_last_stats")
     return s.as_dict()
+
+
+def frr_batch_run(experiments, precision: str = "split_bf16", band_safety: float = 2.0, stream=None):
+    """experiments: list of dicts with keys X, n1, seed, B (and optional first_draw, q or
+    threshold, whiten, ridge, Y, tau, alpha). Returns (list of result dicts, stats dict).
+    Outputs are host numpy arrays."""
+    E = len(experiments)
+    arr = (frr_experiment * E)()
+    keep = []
+    outs = []
+    for e, x in enumerate(experiments):
+        X = np.ascontiguousarray(x["X"], dtype=np.float64)
+        keep.append(X)
+        q = x.get("q")
+        thr = x.get("threshold")
+        B = int(x["B"])
+        cap = int(x.get("cap", B))
+        keys = np.zeros(cap, dtype=np.uint64)
+        m64 = np.zeros(cap, dtype=np.float64)
+        o = {"keys": keys, "m64": m64}
+        a = arr[e]
+        a.X = X.ctypes.data
+        a.n, a.d = X.shape
+        a.n1 = int(x["n1"])
+        a.whiten = WHITEN[x.get("whiten", "chol")]
+        a.ridge = float(x.get("ridge", 0.1))
+        a.seed = int(x["seed"])
+        a.first_draw = int(x.get("first_draw", 0))
+        a.B = B
+        a.q = math.nan if q is None else float(q)
+        a.threshold = math.nan if thr is None else float(thr)
+        a.keys_out = keys.ctypes.data
+        a.M64_out = m64.ctypes.data
+        a.cap = cap
+        if x.get("Y") is not None:
+            Y = np.ascontiguousarray(x["Y"], dtype=np.float64)
+            tau = np.ascontiguousarray(x["tau"], dtype=np.float64)
+            p = np.zeros(tau.size)
+            cnt = np.zeros(tau.size, dtype=np.int64)
+            keep += [Y, tau]
+            a.Y, a.tau, a.T = Y.ctypes.data, tau.ctypes.data, tau.size
+            a.alpha = float(x.get("alpha", 0.05))
+            a.p_out, a.count_out = p.ctypes.data, cnt.ctypes.data
+            o.update(p=p, count=cnt)
+        outs.append(o)
+    opts = frr_default_opts()
+    opts.precision = PRECISION[precision]
+    opts.band_safety = float(band_safety)
+    opts.cuda_stream = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    st = frr_batch_stats()
+    rc = lib().frr_batch_run(ctypes.addressof(arr), E, ctypes.byref(opts), ctypes.byref(st))
+    res = []
+    for e in range(E):
+        a = arr[e]
+        o = outs[e]
+        K = a.K_out
+        r = {"status": a.status, "K": K, "keys": o["keys"][:K], "m64": o["m64"][:K], "ci_lo": a.ci_lo,
+             "ci_hi": a.ci_hi}
+        if "p" in o:
+            r.update(p=o["p"], count=o["count"])
+        res.append(r)
+    stats = {k: getattr(st, k) for k, _ in frr_batch_stats._fields_}
+    stats["status"] = rc
+    return res, stats

@@ -1,0 +1,116 @@
+"""GPU parity of the batched driver (one persistent balance launch over many
+experiments of uneven n and d) against the FP64 oracle and the single-experiment path."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2501_07642_b300 import frr
+from paper_2501_07642_b300.workloads import ar1_covariates, batched_workloads, outcome
+
+pytestmark = pytest.mark.gpu
+
+REL_M64 = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2501_07642_b300 import build
+    build.build_library()
+    O.build()
+
+
+MIX = [  # (n, d, whiten, B, q, seed)
+    (50, 10, "chol", 20_000, 0.01, 11),
+    (20, 5, "chol", math.comb(20, 10), 0.05, frr.FRR_EXACT_SEED),
+    (137, 60, "chol", 30_000, 0.01, 12),
+    (300, 299, "ridge", 25_000, 0.02, 13),
+    (513, 100, "chol", 15_000, 0.01, 14),
+    (1000, 257, "chol", 12_000, 0.01, 15),
+    (2000, 33, "chol", 8_000, 0.01, 16),
+    (64, 500, "ridge", 20_000, 0.005, 17),
+]
+
+
+@pytest.mark.parametrize("precision", ["split_bf16", "f32"])
+def test_batch_matches_oracle_and_single_path(precision):
+    exps, Xs = [], []
+    for k, (n, d, wh, B, q, seed) in enumerate(MIX):
+        X = ar1_covariates(n, d, 500 + k, 0.3)
+        Xs.append(X)
+        exps.append(dict(X=X, n1=n // 2, whiten=wh, ridge=0.1, seed=seed, first_draw=0 if seed == frr.FRR_EXACT_SEED
+                         else 1000 * k, B=B, q=q))
+    res, stats = frr.frr_batch_run(exps, precision=precision)
+    assert stats["status"] == 0 and stats["failed"] == 0
+    for k, (x, r) in enumerate(zip(exps, res)):
+        n, d, wh, B, q, seed = MIX[k]
+        assert r["status"] == 0
+        Zc, *_ = O.prep(Xs[k], wh, 0.1)
+        s = None if seed == frr.FRR_EXACT_SEED else seed
+        M = O.balance(Zc, n // 2, s, x["first_draw"], B)
+        wk, wm = O.select_from_M(M, x["first_draw"], q=q)
+        assert np.array_equal(r["keys"], wk), f"experiment {k}"
+        assert np.allclose(r["m64"], wm, rtol=REL_M64, atol=0)
+        with frr.Context(Xs[k], n // 2, precision=precision, whiten=wh) as ctx:
+            sk, sm = frr.frr_select(ctx, seed, x["first_draw"], B, q=q)
+        assert np.array_equal(sk, r["keys"]) and np.array_equal(sm, r["m64"])
+
+
+def test_batch_reports_per_experiment_errors():
+    good = dict(X=ar1_covariates(40, 5, 1, 0.0), n1=20, seed=3, B=2000, q=0.05)
+    bad = dict(X=ar1_covariates(10, 9, 2, 0.0), n1=5, seed=3, B=2000, q=0.05)  # d >= n - 1 under Cholesky
+    res, stats = frr.frr_batch_run([good, bad, good])
+    assert stats["status"] == -2 and stats["failed"] == 1
+    assert res[0]["status"] == 0 and res[2]["status"] == 0 and res[1]["status"] == -2
+    assert np.array_equal(res[0]["keys"], res[2]["keys"]) and res[0]["K"] == 100
+
+
+def test_batched_workload_256_experiments_sampled():
+    """The batched workload: 256 experiments (n log-uniform on [50, 2000], d on
+    [10, 500]), 1e5 draws each, q = 0.01, each followed by its randomization test.
+    Every experiment must accept exactly 1000 keys with FP64-accurate M; for a seeded
+    sample of experiments the oracle re-scores the accepted keys and a sample of the
+    rejected draws, and recomputes the test counts."""
+    wls = batched_workloads(256)
+    exps = []
+    for w in wls:
+        X = w.covariates()
+        exps.append(dict(X=X, n1=w.n1, whiten=w.whiten, ridge=w.ridge, seed=w.philox_seed, B=w.draws, q=w.q))
+    res, stats = frr.frr_batch_run(exps)
+    assert stats["status"] == 0, stats
+    assert all(r["K"] == 1000 for r in res)
+    rng = np.random.default_rng(2024)
+    for e in rng.choice(256, 4, replace=False):
+        w, r = wls[e], res[e]
+        X = exps[e]["X"]
+        Zc, *_ = O.prep(X, w.whiten, w.ridge)
+        got = O.balance_list(Zc, w.n1, w.philox_seed, r["keys"])
+        assert np.allclose(r["m64"], got, rtol=REL_M64, atol=0)
+        kth = max(zip(got, r["keys"].tolist()))
+        acc = set(r["keys"].tolist())
+        sample = np.array([s for s in rng.choice(w.draws, 300, replace=False) if int(s) not in acc], dtype=np.uint64)
+        sm = O.balance_list(Zc, w.n1, w.philox_seed, sample)
+        assert all((m, int(k)) > (kth[0], kth[1]) for m, k in zip(sm, sample))
+
+
+def test_batch_randomization_tests_match_single_path():
+    wls = batched_workloads(6)
+    exps, Ys = [], []
+    for w in wls:
+        X = w.covariates()
+        with frr.Context(X, w.n1, precision="f32", whiten=w.whiten, ridge=w.ridge) as ctx:
+            k0 = frr.frr_select(ctx, w.philox_seed, 0, 20_000, q=w.q)[0][0]
+            w_obs = frr.frr_assignment(ctx, w.philox_seed, int(k0))
+        Y = outcome(X, w_obs, w.tau_true, w.y_seed, w.noise_sd)
+        Ys.append(Y)
+        exps.append(dict(X=X, n1=w.n1, whiten=w.whiten, ridge=w.ridge, seed=w.philox_seed, B=20_000, q=w.q, Y=Y,
+                         tau=w.tau_grid, alpha=0.05))
+    res, stats = frr.frr_batch_run(exps, precision="f32")
+    assert stats["status"] == 0
+    for e, (w, r) in enumerate(zip(wls, res)):
+        W = np.stack([O.assignment(w.philox_seed, int(k), w.n, w.n1) for k in r["keys"]])
+        want = O.randtest(W, W[0], Ys[e], w.tau_grid, 0.05)
+        mismatch = r["count"] != want["count"]
+        assert np.all(want["near_ties"][mismatch] > 0) and mismatch.sum() <= 2
+        assert r["ci_lo"] == want["ci_lo"] and r["ci_hi"] == want["ci_hi"]
