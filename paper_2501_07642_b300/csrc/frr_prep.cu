@@ -70,60 +70,179 @@ __global__ void k_diag(const double* __restrict__ S, int d, int whiten, double r
     scal[1] = mx;
 }
 
-// Column j of the unpivoted Cholesky factor, stored column-major: LT[k * d + i] = L_ik.
-//   L_jj = sqrt(A_jj - sum_{k<j} L_jk^2),  L_ij = (A_ij - sum_{k<j} L_ik L_jk) / L_jj  (i > j).
-// Every thread recomputes the pivot with the same operations, so all agree on it.
-__global__ void k_chol_col(const double* __restrict__ S, const double* __restrict__ Adiag, int d, int j,
-                           double tol_abs, double* __restrict__ LT, int* __restrict__ status)
+
+
+// ---- blocked factorisation with the same operation order --------------------------
+// Panels of kP columns. Every entry of the working matrix receives its subtractions
+// "- L_ik L_jk" (resp. "- L_jk z_ik") one by one in ascending k -- earlier panels through
+// the trailing updates, the current panel inside the panel kernel -- followed by the
+// same square root / division, so the results equal the column-by-column definition
+// bit for bit while the work runs in parallel.
+constexpr int kP = 32;
+
+// Panel [k0, k0 + pw) of the Cholesky factor, in place in A (row-major d x d, lower part:
+// working values, final L on exit). Each CTA factors the pw x pw diagonal block with its
+// first warp (lane r owns row k0 + r), then finishes its own rows below the block.
+__global__ void __launch_bounds__(256)
+k_chol_panel(double* __restrict__ A, int d, int k0, int pw, double tol_abs, int* __restrict__ status)
 {
-    const int i = j + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d) return;
-    double s = Adiag[j];
-    double t = (i == j) ? 0.0 : S[(size_t)j * d + i];
-    for (int k = 0; k < j; ++k) {
-        const double ljk = LT[(size_t)k * d + j];
-        s = __dsub_rn(s, __dmul_rn(ljk, ljk));
-        if (i != j) t = __dsub_rn(t, __dmul_rn(LT[(size_t)k * d + i], ljk));
+    __shared__ double Lb[kP][kP + 1];  // L_{k0+jj, k0+kk}, kk <= jj
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        const int r = k0 + tid;
+        double t[kP];
+#pragma unroll
+        for (int kk = 0; kk < kP; ++kk) t[kk] = (tid < pw && kk <= tid) ? A[(size_t)r * d + k0 + kk] : 0.0;
+#pragma unroll
+        for (int jj = 0; jj < kP; ++jj) {
+            if (jj >= pw) break;
+            if (tid == jj) {
+                double sdiag = t[jj];
+#pragma unroll
+                for (int kk = 0; kk < kP; ++kk)
+                    if (kk < jj) sdiag = __dsub_rn(sdiag, __dmul_rn(t[kk], t[kk]));
+                if (!(sdiag > tol_abs)) atomicExch(status, 1);
+                t[jj] = __dsqrt_rn(sdiag > 0.0 ? sdiag : 1.0);
+#pragma unroll
+                for (int kk = 0; kk < kP; ++kk)
+                    if (kk <= jj) Lb[jj][kk] = t[kk];
+            }
+            __syncwarp();
+            if (tid > jj && tid < pw) {
+                double v = t[jj];
+#pragma unroll
+                for (int kk = 0; kk < kP; ++kk)
+                    if (kk < jj) v = __dsub_rn(v, __dmul_rn(t[kk], Lb[jj][kk]));
+                t[jj] = __ddiv_rn(v, Lb[jj][jj]);
+            }
+            __syncwarp();
+        }
+        if (blockIdx.x == 0 && tid < pw) {
+#pragma unroll
+            for (int kk = 0; kk < kP; ++kk)
+                if (kk <= tid) A[(size_t)r * d + k0 + kk] = t[kk];
+        }
     }
-    if (!(s > tol_abs)) {
-        if (i == j) atomicExch(status, 1);
-        return;
+    __syncthreads();
+    const int r = k0 + pw + blockIdx.x * blockDim.x + tid;
+    if (r >= d) return;
+    double t[kP];
+#pragma unroll
+    for (int kk = 0; kk < kP; ++kk) t[kk] = kk < pw ? A[(size_t)r * d + k0 + kk] : 0.0;
+#pragma unroll
+    for (int jj = 0; jj < kP; ++jj) {
+        if (jj >= pw) break;
+        double v = t[jj];
+#pragma unroll
+        for (int kk = 0; kk < kP; ++kk)
+            if (kk < jj) v = __dsub_rn(v, __dmul_rn(t[kk], Lb[jj][kk]));
+        t[jj] = __ddiv_rn(v, Lb[jj][jj]);
     }
-    const double ljj = __dsqrt_rn(s);
-    LT[(size_t)j * d + i] = (i == j) ? ljj : __ddiv_rn(t, ljj);
+#pragma unroll
+    for (int kk = 0; kk < kP; ++kk)
+        if (kk < pw) A[(size_t)r * d + k0 + kk] = t[kk];
 }
 
-__global__ void k_diag_factor(const double* __restrict__ S, int d, double tol_abs, double* __restrict__ LT,
-                              int* __restrict__ status)
+// Trailing update after panel [k0, k0 + pw): A_ij -= L_ik L_jk for k in the panel (ascending),
+// for k0 + pw <= j <= i < d. 32 x 32 tiles, lower-triangle tiles only.
+__global__ void __launch_bounds__(256)
+k_chol_trailing(double* __restrict__ A, int d, int k0, int pw)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= d) return;
-    const double s = S[(size_t)j * d + j];
-    if (!(s > tol_abs)) { atomicExch(status, 1); return; }
-    LT[(size_t)j * d + j] = __dsqrt_rn(s);
+    const int ti = blockIdx.y, tj = blockIdx.x;
+    if (tj > ti) return;
+    __shared__ double Li[32][kP + 1], Lj[32][kP + 1];
+    const int base = k0 + pw;
+    const int i0 = base + 32 * ti, j0 = base + 32 * tj;
+    for (int e = threadIdx.x; e < 32 * kP; e += blockDim.x) {
+        const int rr = e / kP, kk = e % kP;
+        Li[rr][kk] = (i0 + rr < d && kk < pw) ? A[(size_t)(i0 + rr) * d + k0 + kk] : 0.0;
+        Lj[rr][kk] = (j0 + rr < d && kk < pw) ? A[(size_t)(j0 + rr) * d + k0 + kk] : 0.0;
+    }
+    __syncthreads();
+    const int jj = threadIdx.x & 31;
+    for (int ii = threadIdx.x >> 5; ii < 32; ii += blockDim.x >> 5) {
+        const int i = i0 + ii, j = j0 + jj;
+        if (i >= d || j > i) continue;
+        double v = A[(size_t)i * d + j];
+        for (int kk = 0; kk < pw; ++kk) v = __dsub_rn(v, __dmul_rn(Li[ii][kk], Lj[jj][kk]));
+        A[(size_t)i * d + j] = v;
+    }
 }
 
-// Row i of Zc solves L z = Xc_i^T by forward substitution (ascending k):
-//   z_j = (Xc_ij - sum_{k<j} L_jk z_k) / L_jj.  ZT is column-major (ZT[j * n + i]).
-__global__ void k_forward(const double* __restrict__ Xc, const double* __restrict__ LT, int n, int d,
-                          double* __restrict__ ZT)
+// Panel [k0, k0 + pw) of the forward substitution Zc = Xc L^{-T}, in place in T (n x d
+// row-major: working values, final Zc on exit); one thread per row.
+__global__ void __launch_bounds__(256)
+k_fwd_panel(double* __restrict__ T, const double* __restrict__ L, int n, int d, int k0, int pw)
 {
+    __shared__ double Lb[kP][kP + 1];
+    for (int e = threadIdx.x; e < kP * kP; e += blockDim.x) {
+        const int jj = e / kP, kk = e % kP;
+        Lb[jj][kk] = (jj < pw && kk <= jj) ? L[(size_t)(k0 + jj) * d + k0 + kk] : 0.0;
+    }
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    for (int j = 0; j < d; ++j) {
-        double t = Xc[(size_t)i * d + j];
-        for (int k = 0; k < j; ++k) t = __dsub_rn(t, __dmul_rn(LT[(size_t)k * d + j], ZT[(size_t)k * n + i]));
-        ZT[(size_t)j * n + i] = __ddiv_rn(t, LT[(size_t)j * d + j]);
+    double t[kP];
+#pragma unroll
+    for (int kk = 0; kk < kP; ++kk) t[kk] = kk < pw ? T[(size_t)i * d + k0 + kk] : 0.0;
+#pragma unroll
+    for (int jj = 0; jj < kP; ++jj) {
+        if (jj >= pw) break;
+        double v = t[jj];
+#pragma unroll
+        for (int kk = 0; kk < kP; ++kk)
+            if (kk < jj) v = __dsub_rn(v, __dmul_rn(Lb[jj][kk], t[kk]));
+        t[jj] = __ddiv_rn(v, Lb[jj][jj]);
+    }
+#pragma unroll
+    for (int kk = 0; kk < kP; ++kk)
+        if (kk < pw) T[(size_t)i * d + k0 + kk] = t[kk];
+}
+
+// T_ij -= L_jk z_ik for k in panel [k0, k0 + pw) (ascending), j >= k0 + pw. 32 x 32 tiles.
+__global__ void __launch_bounds__(256)
+k_fwd_trailing(double* __restrict__ T, const double* __restrict__ L, int n, int d, int k0, int pw)
+{
+    __shared__ double Zi[32][kP + 1], Lj[32][kP + 1];
+    const int i0 = 32 * blockIdx.y, j0 = k0 + pw + 32 * blockIdx.x;
+    for (int e = threadIdx.x; e < 32 * kP; e += blockDim.x) {
+        const int rr = e / kP, kk = e % kP;
+        Zi[rr][kk] = (i0 + rr < n && kk < pw) ? T[(size_t)(i0 + rr) * d + k0 + kk] : 0.0;
+        Lj[rr][kk] = (j0 + rr < d && kk < pw) ? L[(size_t)(j0 + rr) * d + k0 + kk] : 0.0;
+    }
+    __syncthreads();
+    const int jj = threadIdx.x & 31;
+    for (int ii = threadIdx.x >> 5; ii < 32; ii += blockDim.x >> 5) {
+        const int i = i0 + ii, j = j0 + jj;
+        if (i >= n || j >= d) continue;
+        double v = T[(size_t)i * d + j];
+        for (int kk = 0; kk < pw; ++kk) v = __dsub_rn(v, __dmul_rn(Lj[jj][kk], Zi[ii][kk]));
+        T[(size_t)i * d + j] = v;
     }
 }
 
-__global__ void k_transpose(const double* __restrict__ ZT, int n, int d, double* __restrict__ Z)
+// A = S with the ridge on the diagonal (lower part is what the factorisation reads)
+__global__ void k_init_A(const double* __restrict__ S, const double* __restrict__ Adiag, int d, double* __restrict__ A)
 {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (size_t)n * d) return;
+    if (idx >= (size_t)d * d) return;
     const int i = (int)(idx / d), j = (int)(idx % d);
-    Z[idx] = ZT[(size_t)j * n + i];
+    A[idx] = (i == j) ? Adiag[i] : S[idx];
 }
+
+// diagonal whitening: L = diag(sqrt(S_jj)) stored row-major (zero elsewhere)
+__global__ void k_diag_L(const double* __restrict__ S, int d, double tol_abs, double* __restrict__ A, int* status)
+{
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)d * d) return;
+    const int i = (int)(idx / d), j = (int)(idx % d);
+    if (i != j) { A[idx] = 0.0; return; }
+    const double s = S[idx];
+    if (!(s > tol_abs)) atomicExch(status, 1);
+    A[idx] = __dsqrt_rn(s > 0.0 ? s : 1.0);
+}
+
+
 
 // qexp_j such that |Zc_ij * 2^qexp_j| <= 2^kQBits for every i
 __global__ void k_qexp(const double* __restrict__ Z, int n, int d, int* __restrict__ qexp)
@@ -175,15 +294,41 @@ __global__ void k_qsum(const long long* __restrict__ Q, int kpad, int d, long lo
 //     one rounding of relative size u per accumulated term.
 // SIMT FP32: u = 2^-24 (round to nearest), one pass.
 // Tensor cores: u = 2^-23 (truncation allowed), two passes (hi and lo terms).
-__global__ void k_band_cols(const double* __restrict__ Z, int n, int d, int n1, int kused,
-                            double* __restrict__ eps32, double* __restrict__ eps_tc)
+__global__ void __launch_bounds__(256)
+k_band_cols(const double* __restrict__ Z, int n, int d, int n1, int kused, double* __restrict__ eps32,
+            double* __restrict__ eps_tc)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= d) return;
+    // one CTA per column; thread t covers K positions [t * per, (t + 1) * per)
+    __shared__ double ws1[8], ws2[8], wacc[8], wr32[8], wrtc[8];
+    const int j = blockIdx.x;
+    const int per = (kused + 255) / 256;
+    const int p0 = threadIdx.x * per;
     const double pi = (double)n1 / n;
     const double vf = pi * (1.0 - pi) * (double)n / (double)(n - 1);
-    double s1 = 0.0, s2 = 0.0, acc = 0.0, r32 = 0.0, rtc = 0.0;
-    for (int p = 0; p < kused; ++p) {
+    double l1 = 0.0, l2 = 0.0;
+    for (int p = p0; p < p0 + per && p < kused; ++p) {
+        const int u = unit_of_kpos(p);
+        if (u < n) {
+            const double z = Z[(size_t)u * d + j];
+            l1 += z;
+            l2 += z * z;
+        }
+    }
+    // exclusive prefix of (l1, l2) over threads
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double i1 = l1, i2 = l2;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double y1 = __shfl_up_sync(kFull, i1, off), y2 = __shfl_up_sync(kFull, i2, off);
+        if (lane >= off) { i1 += y1; i2 += y2; }
+    }
+    if (lane == 31) { ws1[warp] = i1; ws2[warp] = i2; }
+    __syncthreads();
+    double b1 = 0.0, b2 = 0.0;
+    for (int w = 0; w < warp; ++w) { b1 += ws1[w]; b2 += ws2[w]; }
+    double s1 = b1 + i1 - l1, s2 = b2 + i2 - l2;
+    double acc = 0.0, r32 = 0.0, rtc = 0.0;
+    for (int p = p0; p < p0 + per && p < kused; ++p) {
         const int u = unit_of_kpos(p);
         if (u >= n) continue;
         const double z = Z[(size_t)u * d + j];
@@ -195,8 +340,20 @@ __global__ void k_band_cols(const double* __restrict__ Z, int n, int d, int n1, 
         const double lo = (double)__bfloat162float(__double2bfloat16(z - hi));
         rtc += fabs((z - hi) - lo);
     }
-    eps32[j] = r32 + ldexp(acc, -24);
-    eps_tc[j] = rtc + 2.0 * ldexp(acc, -23);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        acc += __shfl_xor_sync(kFull, acc, off);
+        r32 += __shfl_xor_sync(kFull, r32, off);
+        rtc += __shfl_xor_sync(kFull, rtc, off);
+    }
+    if (lane == 0) { wacc[warp] = acc; wr32[warp] = r32; wrtc[warp] = rtc; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, R32 = 0.0, RTC = 0.0;
+        for (int w = 0; w < 8; ++w) { A += wacc[w]; R32 += wr32[w]; RTC += wrtc[w]; }
+        eps32[j] = R32 + ldexp(A, -24);
+        eps_tc[j] = RTC + 2.0 * ldexp(A, -23);
+    }
 }
 
 BandConsts band_from_eps(const std::vector<double>& eps, double c_M, int64_t d)
@@ -220,7 +377,7 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
     const int n = (int)ctx->n, d = (int)ctx->d;
     cudaStream_t s = ctx->stream;
     const size_t nd = (size_t)n * d;
-    double *X = nullptr, *xbar = nullptr, *Xc = nullptr, *S = nullptr, *Adiag = nullptr, *LT = nullptr,
+    double *X = nullptr, *xbar = nullptr, *Xc = nullptr, *S = nullptr, *Adiag = nullptr, *Lm = nullptr,
            *ZT = nullptr, *scal = nullptr, *eps = nullptr;
     int* status = nullptr;
     frr_status rc = FRR_OK;
@@ -232,13 +389,13 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
     PREP_CHECK(cudaMalloc(&Xc, nd * sizeof(double)));
     PREP_CHECK(cudaMalloc(&S, (size_t)d * d * sizeof(double)));
     PREP_CHECK(cudaMalloc(&Adiag, d * sizeof(double)));
-    PREP_CHECK(cudaMalloc(&LT, (size_t)d * d * sizeof(double)));
+    PREP_CHECK(cudaMalloc(&Lm, (size_t)d * d * sizeof(double)));
     PREP_CHECK(cudaMalloc(&ZT, nd * sizeof(double)));
     PREP_CHECK(cudaMalloc(&scal, 4 * sizeof(double)));
     PREP_CHECK(cudaMalloc(&eps, 2 * (size_t)d * sizeof(double)));
     PREP_CHECK(cudaMalloc(&status, sizeof(int)));
     PREP_CHECK(cudaMemsetAsync(status, 0, sizeof(int), s));
-    PREP_CHECK(cudaMemsetAsync(LT, 0, (size_t)d * d * sizeof(double), s));
+    PREP_CHECK(cudaMemsetAsync(Lm, 0, (size_t)d * d * sizeof(double), s));
     PREP_CHECK(cudaMemcpyAsync(X, X_host, nd * sizeof(double), cudaMemcpyHostToDevice, s));
 
     k_colmean<<<ceil_div(d, 128), 128, 0, s>>>(X, n, d, xbar);
@@ -254,11 +411,20 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
         PREP_CHECK(cudaMemcpyAsync(sc, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         PREP_CHECK(cudaStreamSynchronize(s));
         const double tol_abs = 1e-12 * sc[1];
+        const size_t dd = (size_t)d * d;
         if (ctx->opts.whiten == FRR_DIAG) {
-            k_diag_factor<<<ceil_div(d, 128), 128, 0, s>>>(S, d, tol_abs, LT, status);
+            k_diag_L<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(S, d, tol_abs, Lm, status);
         } else {
-            for (int j = 0; j < d; ++j)
-                k_chol_col<<<ceil_div(d - j, 128), 128, 0, s>>>(S, Adiag, d, j, tol_abs, LT, status);
+            k_init_A<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(S, Adiag, d, Lm);
+            for (int k0 = 0; k0 < d; k0 += kP) {
+                const int pw = (d - k0) < kP ? (d - k0) : kP;
+                const int below = d - k0 - pw;
+                k_chol_panel<<<below > 0 ? ceil_div(below, 256) : 1, 256, 0, s>>>(Lm, d, k0, pw, tol_abs, status);
+                if (below > 0) {
+                    const int tiles = ceil_div(below, 32);
+                    k_chol_trailing<<<dim3(tiles, tiles), 256, 0, s>>>(Lm, d, k0, pw);
+                }
+            }
         }
         PREP_CHECK(cudaGetLastError());
         int st = 0;
@@ -266,8 +432,15 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
         PREP_CHECK(cudaStreamSynchronize(s));
         if (st != 0) { rc = FRR_E_DEGENERATE; goto cleanup; }
     }
-    k_forward<<<ceil_div(n, 32), 32, 0, s>>>(Xc, LT, n, d, ZT);
-    k_transpose<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(ZT, n, d, ctx->Zc64);
+    // forward substitution in place on a copy of Xc (ZT holds n x d row-major here)
+    PREP_CHECK(cudaMemcpyAsync(ZT, Xc, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    for (int k0 = 0; k0 < d; k0 += kP) {
+        const int pw = (d - k0) < kP ? (d - k0) : kP;
+        k_fwd_panel<<<ceil_div(n, 256), 256, 0, s>>>(ZT, Lm, n, d, k0, pw);
+        const int right = d - k0 - pw;
+        if (right > 0) k_fwd_trailing<<<dim3(ceil_div(right, 32), ceil_div(n, 32)), 256, 0, s>>>(ZT, Lm, n, d, k0, pw);
+    }
+    PREP_CHECK(cudaMemcpyAsync(ctx->Zc64, ZT, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
     k_qexp<<<ceil_div(d, 128), 128, 0, s>>>(ctx->Zc64, n, d, ctx->qexp);
     {
         const size_t tot = (size_t)ctx->kpad * ctx->dpad32;
@@ -277,7 +450,7 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
                                                               ctx->Z32, ctx->Zhi, ctx->Zlo, ctx->Q);
     }
     k_qsum<<<ceil_div(d, 128), 128, 0, s>>>(ctx->Q, ctx->kpad, d, ctx->Qsum);
-    k_band_cols<<<ceil_div(d, 128), 128, 0, s>>>(ctx->Zc64, n, d, (int)ctx->n1, ctx->kused, eps, eps + d);
+    k_band_cols<<<d, 256, 0, s>>>(ctx->Zc64, n, d, (int)ctx->n1, ctx->kused, eps, eps + d);
     PREP_CHECK(cudaGetLastError());
     {
         std::vector<double> e32(d), etc(d);
@@ -297,7 +470,7 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
 
 cleanup:
 #undef PREP_CHECK
-    cudaFree(X); cudaFree(xbar); cudaFree(Xc); cudaFree(S); cudaFree(Adiag); cudaFree(LT);
+    cudaFree(X); cudaFree(xbar); cudaFree(Xc); cudaFree(S); cudaFree(Adiag); cudaFree(Lm);
     cudaFree(ZT); cudaFree(scal); cudaFree(eps); cudaFree(status);
     return rc;
 }
