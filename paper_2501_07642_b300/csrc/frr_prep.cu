@@ -81,9 +81,10 @@ __global__ void k_diag(const double* __restrict__ S, int d, int whiten, double r
 constexpr int kP = 32;
 
 // Panel [k0, k0 + pw) of the Cholesky factor, in place in A (row-major d x d, lower part:
-// working values, final L on exit). Each CTA factors the pw x pw diagonal block with its
-// first warp (lane r owns row k0 + r), then finishes its own rows below the block.
-__global__ void __launch_bounds__(256)
+// working values, final L on exit). Each CTA (one warp, so that the rows spread over many
+// SMs: FP64 throughput per SM is low) factors the pw x pw diagonal block (lane r owns row
+// k0 + r), then finishes its own 32 rows below the block.
+__global__ void __launch_bounds__(32)
 k_chol_panel(double* __restrict__ A, int d, int k0, int pw, double tol_abs, int* __restrict__ status)
 {
     __shared__ double Lb[kP][kP + 1];  // L_{k0+jj, k0+kk}, kk <= jj
@@ -170,8 +171,8 @@ k_chol_trailing(double* __restrict__ A, int d, int k0, int pw)
 }
 
 // Panel [k0, k0 + pw) of the forward substitution Zc = Xc L^{-T}, in place in T (n x d
-// row-major: working values, final Zc on exit); one thread per row.
-__global__ void __launch_bounds__(256)
+// row-major: working values, final Zc on exit); one thread per row, one warp per CTA.
+__global__ void __launch_bounds__(32)
 k_fwd_panel(double* __restrict__ T, const double* __restrict__ L, int n, int d, int k0, int pw)
 {
     __shared__ double Lb[kP][kP + 1];
@@ -384,16 +385,16 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
     auto fail = [&](cudaError_t e) { ctx->failed = true; rc = (e == cudaErrorMemoryAllocation) ? FRR_E_NOMEM : FRR_E_CUDA; };
 #define PREP_CHECK(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) { fail(_e); goto cleanup; } } while (0)
 
-    PREP_CHECK(cudaMalloc(&X, nd * sizeof(double)));
-    PREP_CHECK(cudaMalloc(&xbar, d * sizeof(double)));
-    PREP_CHECK(cudaMalloc(&Xc, nd * sizeof(double)));
-    PREP_CHECK(cudaMalloc(&S, (size_t)d * d * sizeof(double)));
-    PREP_CHECK(cudaMalloc(&Adiag, d * sizeof(double)));
-    PREP_CHECK(cudaMalloc(&Lm, (size_t)d * d * sizeof(double)));
-    PREP_CHECK(cudaMalloc(&ZT, nd * sizeof(double)));
-    PREP_CHECK(cudaMalloc(&scal, 4 * sizeof(double)));
-    PREP_CHECK(cudaMalloc(&eps, 2 * (size_t)d * sizeof(double)));
-    PREP_CHECK(cudaMalloc(&status, sizeof(int)));
+    PREP_CHECK(cudaMallocAsync(&X, nd * sizeof(double), s));
+    PREP_CHECK(cudaMallocAsync(&xbar, d * sizeof(double), s));
+    PREP_CHECK(cudaMallocAsync(&Xc, nd * sizeof(double), s));
+    PREP_CHECK(cudaMallocAsync(&S, (size_t)d * d * sizeof(double), s));
+    PREP_CHECK(cudaMallocAsync(&Adiag, d * sizeof(double), s));
+    PREP_CHECK(cudaMallocAsync(&Lm, (size_t)d * d * sizeof(double), s));
+    PREP_CHECK(cudaMallocAsync(&ZT, nd * sizeof(double), s));
+    PREP_CHECK(cudaMallocAsync(&scal, 4 * sizeof(double), s));
+    PREP_CHECK(cudaMallocAsync(&eps, 2 * (size_t)d * sizeof(double), s));
+    PREP_CHECK(cudaMallocAsync(&status, sizeof(int), s));
     PREP_CHECK(cudaMemsetAsync(status, 0, sizeof(int), s));
     PREP_CHECK(cudaMemsetAsync(Lm, 0, (size_t)d * d * sizeof(double), s));
     PREP_CHECK(cudaMemcpyAsync(X, X_host, nd * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -419,7 +420,7 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
             for (int k0 = 0; k0 < d; k0 += kP) {
                 const int pw = (d - k0) < kP ? (d - k0) : kP;
                 const int below = d - k0 - pw;
-                k_chol_panel<<<below > 0 ? ceil_div(below, 256) : 1, 256, 0, s>>>(Lm, d, k0, pw, tol_abs, status);
+                k_chol_panel<<<below > 0 ? ceil_div(below, 32) : 1, 32, 0, s>>>(Lm, d, k0, pw, tol_abs, status);
                 if (below > 0) {
                     const int tiles = ceil_div(below, 32);
                     k_chol_trailing<<<dim3(tiles, tiles), 256, 0, s>>>(Lm, d, k0, pw);
@@ -436,7 +437,7 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
     PREP_CHECK(cudaMemcpyAsync(ZT, Xc, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
     for (int k0 = 0; k0 < d; k0 += kP) {
         const int pw = (d - k0) < kP ? (d - k0) : kP;
-        k_fwd_panel<<<ceil_div(n, 256), 256, 0, s>>>(ZT, Lm, n, d, k0, pw);
+        k_fwd_panel<<<ceil_div(n, 32), 32, 0, s>>>(ZT, Lm, n, d, k0, pw);
         const int right = d - k0 - pw;
         if (right > 0) k_fwd_trailing<<<dim3(ceil_div(right, 32), ceil_div(n, 32)), 256, 0, s>>>(ZT, Lm, n, d, k0, pw);
     }
@@ -470,8 +471,10 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
 
 cleanup:
 #undef PREP_CHECK
-    cudaFree(X); cudaFree(xbar); cudaFree(Xc); cudaFree(S); cudaFree(Adiag); cudaFree(Lm);
-    cudaFree(ZT); cudaFree(scal); cudaFree(eps); cudaFree(status);
+    // stream-ordered release: no device-wide synchronisation
+    for (void* p : {(void*)X, (void*)xbar, (void*)Xc, (void*)S, (void*)Adiag, (void*)Lm, (void*)ZT, (void*)scal,
+                    (void*)eps, (void*)status})
+        if (p) cudaFreeAsync(p, s);
     return rc;
 }
 

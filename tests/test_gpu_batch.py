@@ -114,3 +114,18 @@ def test_batch_randomization_tests_match_single_path():
         mismatch = r["count"] != want["count"]
         assert np.all(want["near_ties"][mismatch] > 0) and mismatch.sum() <= 2
         assert r["ci_lo"] == want["ci_lo"] and r["ci_hi"] == want["ci_hi"]
+
+
+def test_two_shards_on_one_gpu_merge_to_the_single_pool():
+    from paper_2501_07642_b300.distributed import global_k, merge_accepted, shard, shard_q
+    X = ar1_covariates(200, 100, 77, 0.5)
+    B, q, seed = 100_000, 0.01, 21
+    K = global_k(q, B)
+    with frr.Context(X, 100, precision="split_bf16", whiten="chol") as ctx:
+        want = frr.frr_select(ctx, seed, 500, B, q=q)
+        parts = []
+        for r in range(2):
+            off, cnt = shard(B, r, 2)
+            parts.append(frr.frr_select(ctx, seed, 500 + off, cnt, q=shard_q(K, cnt)))
+    keys, m = merge_accepted(parts, K)
+    assert np.array_equal(keys, want[0]) and np.array_equal(m, want[1])
