@@ -105,11 +105,11 @@ __device__ __forceinline__ slot_mask_t<KB> warp_select_smallest(const uint32_t (
     using M = slot_mask_t<KB>;
     long long lo = -1, hi = 0xffffffffll;
     int clo = 0, chi = 128 * KB;
-    const float inv_n = 1.0f / (float)n;
-    long long t = (long long)((float)n1 * inv_n * 4294967296.0f);
-    if (t > 0xfffffffell) t = 0xfffffffell;
-    if (t < 0) t = 0;
-    const long long step = (long long)(4294967296.0f * inv_n);
+    // Only 32-bit integer <-> float conversions here: the 64-bit ones execute on the
+    // (narrow) FP64 unit, which every generating warp would share.
+    const float inv_n = __fdividef(1.0f, (float)n);
+    long long t = (long long)__float2uint_rz(fminf((float)n1 * inv_n * 4294967296.0f, 4294967040.0f));
+    const long long step = (long long)__float2uint_rz(4294967296.0f * inv_n);
     long long prev_span = hi - lo;
     bool bisect = false;
     for (int it = 0;; ++it) {
@@ -129,8 +129,9 @@ __device__ __forceinline__ slot_mask_t<KB> warp_select_smallest(const uint32_t (
         } else if (bisect) {
             t = lo + span / 2;
         } else {
-            const float frac = (float)(n1 - clo) / (float)(chi - clo);
-            t = lo + (long long)((float)span * frac + 0.5f);
+            const float frac = __fdividef((float)(n1 - clo), (float)(chi - clo));
+            const uint32_t span32 = span > 0xffffffffll ? 0xffffffffu : (uint32_t)span;
+            t = lo + (long long)__float2uint_rz(__uint2float_rz(span32) * frac + 0.5f);
         }
         if (t <= lo) t = lo + 1;
         if (t >= hi) t = hi - 1;
