@@ -145,6 +145,13 @@ frr_status frr_assignment(frr_ctx* ctx, uint64_t seed, uint64_t key, uint8_t* w_
 /* Regenerates draws [first_draw, first_draw + count). w_out: host or device, count x n bytes. */
 frr_status frr_assignments(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_t count, uint8_t* w_out);
 
+/* The second half of the key -> assignment mapping on caller-supplied unit words:
+ * units whose (word, index) pairs are the n1 smallest are treated, ties in the word
+ * broken by the lower unit index (the same warp selection the draws use; this entry
+ * point exists to verify it, e.g. on words with ties). words: host or device, n
+ * 32-bit words in unit order; w_out: host or device, n bytes. */
+frr_status frr_assignment_from_words(frr_ctx* ctx, const uint32_t* words, uint8_t* w_out);
+
 /* M in FP64 accuracy for an explicit list of draws (the same exact-sum recheck that
  * decides acceptance). draws, M64_out: host or device, count entries. */
 frr_status frr_recheck(frr_ctx* ctx, uint64_t seed, const uint64_t* draws, int64_t count, double* M64_out);

@@ -313,6 +313,22 @@ frr_status frr_assignment(frr_ctx* ctx, uint64_t seed, uint64_t key, uint8_t* w_
     return frr_assignments(ctx, seed, key, 1, w_out);
 }
 
+frr_status frr_assignment_from_words(frr_ctx* ctx, const uint32_t* words, uint8_t* w_out)
+{
+    if (!ctx || !words || !w_out) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    const size_t wbytes = (size_t)ctx->n * sizeof(uint32_t), rbytes = (size_t)4 * ctx->kb * sizeof(uint32_t);
+    FRR_TRY(ensure_device(ctx, &ctx->misc2, &ctx->misc2_bytes, wbytes + rbytes + (size_t)ctx->n + 64));
+    uint32_t* dwords = static_cast<uint32_t*>(ctx->misc2);
+    uint32_t* row = dwords + ctx->n;
+    uint8_t* dw = reinterpret_cast<uint8_t*>(row + 4 * ctx->kb);
+    FRR_TRY(copy_in(ctx, dwords, words, wbytes));
+    FRR_TRY(words_select_launch(ctx, dwords, row));
+    FRR_TRY(unpack_launch(ctx, row, 1, dw));
+    FRR_TRY(copy_out(ctx, w_out, dw, (size_t)ctx->n));
+    return FRR_OK;
+}
+
 frr_status frr_recheck(frr_ctx* ctx, uint64_t seed, const uint64_t* draws, int64_t count, double* M64_out)
 {
     if (!ctx || count < 0 || (count > 0 && (!draws || !M64_out))) return FRR_E_ARG;

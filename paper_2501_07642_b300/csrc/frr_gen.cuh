@@ -81,11 +81,15 @@ __device__ __forceinline__ void unit_words(uint32_t (&r)[4 * KB], uint64_t seed,
 template <int KB>
 __device__ __forceinline__ int warp_count_le(const uint32_t (&r)[4 * KB], uint32_t t)
 {
-    // four independent partial counts keep the add chains short
-    int c[4] = {0, 0, 0, 0};
+    // r <= t exactly when t - r does not borrow: the carry of each subtraction is
+    // added to the count (two integer instructions per word)
+    uint32_t c = 0;
 #pragma unroll
-    for (int e = 0; e < 4 * KB; ++e) c[e & 3] += (r[e] <= t) ? 1 : 0;
-    return (int)__reduce_add_sync(kFull, (unsigned)((c[0] + c[1]) + (c[2] + c[3])));
+    for (int e = 0; e < 4 * KB; ++e) {
+        uint32_t scratch;
+        asm("sub.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %1, 0;" : "=r"(scratch), "+r"(c) : "r"(t), "r"(r[e]));
+    }
+    return (int)__reduce_add_sync(kFull, c);
 }
 
 // Slot mask type: one bit per unit word held by the lane.
@@ -99,8 +103,17 @@ using slot_mask_t = typename std::conditional<(4 * KB <= 32), uint32_t, uint64_t
 // some t has exactly n1 words <= t. Each step strictly shrinks the bracket, so
 // the loop ends after at most ~70 counts (about 5 on average at n = 1000). The
 // interpolation only steers the search, so it is done in FP32.
+// Outcome of the selection: normally a value t with exactly n1 words <= t (treated =
+// r <= t); when the n1-th and (n1+1)-th words are equal, a per-slot mask instead.
 template <int KB>
-__device__ __forceinline__ slot_mask_t<KB> warp_select_smallest(const uint32_t (&r)[4 * KB], int n, int n1, int lane)
+struct SelectOutcome {
+    uint32_t t;
+    bool tie;
+    slot_mask_t<KB> mask;
+};
+
+template <int KB>
+__device__ __forceinline__ SelectOutcome<KB> warp_select_smallest(const uint32_t (&r)[4 * KB], int n, int n1, int lane)
 {
     using M = slot_mask_t<KB>;
     long long lo = -1, hi = 0xffffffffll;
@@ -115,12 +128,7 @@ __device__ __forceinline__ slot_mask_t<KB> warp_select_smallest(const uint32_t (
     for (int it = 0;; ++it) {
         const uint32_t tt = (uint32_t)t;
         const int c = warp_count_le<KB>(r, tt);
-        if (c == n1) {
-            M m = 0;
-#pragma unroll
-            for (int e = 0; e < 4 * KB; ++e) m |= (M)(r[e] <= tt) << e;
-            return m;
-        }
+        if (c == n1) return SelectOutcome<KB>{tt, false, 0};
         if (c > n1) { hi = t; chi = c; } else { lo = t; clo = c; }
         const long long span = hi - lo;
         if (span <= 1) break;
@@ -168,25 +176,22 @@ __device__ __forceinline__ slot_mask_t<KB> warp_select_smallest(const uint32_t (
         }
         base += __shfl_sync(kFull, incl, 31);
     }
-    return m;
+    return SelectOutcome<KB>{0u, true, m};
 }
 
-// Writes the draw's bit row (4*KB words, K-order) to row[] (shared or global).
+// Writes the draw's bit row (4*KB words, K-order) to row[] (shared or global). Word e
+// is the warp ballot of slot e; every lane stores the same value (one transaction).
 template <int KB>
-__device__ __forceinline__ void warp_store_bits(slot_mask_t<KB> treated, uint32_t* row, int lane)
+__device__ __forceinline__ void warp_store_bits(const SelectOutcome<KB>& sel, const uint32_t (&r)[4 * KB], uint32_t* row)
 {
     constexpr int W = 4 * KB;
-    uint32_t mine[(W + 31) / 32];
+    if (!sel.tie) {
 #pragma unroll
-    for (int q = 0; q < (W + 31) / 32; ++q) mine[q] = 0;
+        for (int e = 0; e < W; ++e) row[e] = __ballot_sync(kFull, r[e] <= sel.t);
+    } else {
 #pragma unroll
-    for (int e = 0; e < W; ++e) {
-        const uint32_t w = __ballot_sync(kFull, (unsigned)((treated >> e) & 1u));
-        if (lane == (e & 31)) mine[e >> 5] = w;
+        for (int e = 0; e < W; ++e) row[e] = __ballot_sync(kFull, (unsigned)((sel.mask >> e) & 1u));
     }
-#pragma unroll
-    for (int q = 0; q < (W + 31) / 32; ++q)
-        if (lane + 32 * q < W) row[lane + 32 * q] = mine[q];
 }
 
 // Colex unranking (combinatorial number system): rank = sum_m C(c_m, m) with
@@ -232,8 +237,8 @@ __device__ __forceinline__ void warp_draw_bits(bool exact, uint64_t seed, uint64
     } else {
         uint32_t r[4 * KB];
         unit_words<KB>(r, seed, draw, n, lane);
-        const slot_mask_t<KB> t = warp_select_smallest<KB>(r, n, n1, lane);
-        warp_store_bits<KB>(t, row, lane);
+        const SelectOutcome<KB> sel = warp_select_smallest<KB>(r, n, n1, lane);
+        warp_store_bits<KB>(sel, r, row);
     }
 }
 

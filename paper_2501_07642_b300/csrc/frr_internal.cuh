@@ -126,6 +126,7 @@ frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t f
 frr_status balance_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
 frr_status bits_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t count,
                        const uint64_t* draws_dev, uint32_t* rows_dev);
+frr_status words_select_launch(frr_ctx* ctx, const uint32_t* words_dev, uint32_t* row_dev);
 frr_status unpack_launch(frr_ctx* ctx, const uint32_t* rows_dev, uint64_t count, uint8_t* w_dev);
 frr_status recheck_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws_dev, int64_t count,
                           double* M64_dev);

@@ -36,6 +36,23 @@ __global__ void k_bits(uint64_t seed, int exact, const uint64_t* __restrict__ bi
     warp_draw_bits<KB>(exact != 0, seed, draw, n, n1, binom, rows + w * (4 * KB), lane);
 }
 
+// Selection on caller-supplied unit words (word of unit i at words[i]); one warp.
+template <int KB>
+__global__ void k_words_select(const uint32_t* __restrict__ words, int n, int n1, uint32_t* __restrict__ row)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t r[4 * KB];
+#pragma unroll
+    for (int k = 0; k < KB; ++k)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int u = 128 * k + 4 * lane + c;
+            r[4 * k + c] = u < n ? words[u] : 0xffffffffu;
+        }
+    const SelectOutcome<KB> sel = warp_select_smallest<KB>(r, n, n1, lane);
+    warp_store_bits<KB>(sel, r, row);
+}
+
 __global__ void k_unpack(const uint32_t* __restrict__ rows, int words, uint64_t count, int n, uint8_t* __restrict__ w)
 {
     const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -460,6 +477,21 @@ frr_status bits_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, 
         case 16: return launch_bits_kb<16>(ctx, seed, exact, first, count, draws, rows);
         default: return FRR_E_UNSUPPORTED;
     }
+}
+
+frr_status words_select_launch(frr_ctx* ctx, const uint32_t* words, uint32_t* row)
+{
+    const int n = (int)ctx->n, n1 = (int)ctx->n1;
+    switch (ctx->kb) {
+        case 1: k_words_select<1><<<1, 32, 0, ctx->stream>>>(words, n, n1, row); break;
+        case 2: k_words_select<2><<<1, 32, 0, ctx->stream>>>(words, n, n1, row); break;
+        case 4: k_words_select<4><<<1, 32, 0, ctx->stream>>>(words, n, n1, row); break;
+        case 8: k_words_select<8><<<1, 32, 0, ctx->stream>>>(words, n, n1, row); break;
+        case 16: k_words_select<16><<<1, 32, 0, ctx->stream>>>(words, n, n1, row); break;
+        default: return FRR_E_UNSUPPORTED;
+    }
+    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    return FRR_OK;
 }
 
 frr_status unpack_launch(frr_ctx* ctx, const uint32_t* rows, uint64_t count, uint8_t* w)

@@ -93,6 +93,7 @@ def lib():
             "frr_assignment": (c.c_int, [P, U64, U64, P]),
             "frr_assignments": (c.c_int, [P, U64, U64, U64, P]),
             "frr_recheck": (c.c_int, [P, U64, P, I64, P]),
+            "frr_assignment_from_words": (c.c_int, [P, P, P]),
             "frr_recheck_static": (c.c_int, [P, U64, P, I64, P]),
             "frr_randtest": (c.c_int, [P, U64, P, I64, U64, P, P, I64, D, P, P, P, P]),
             "frr_whitened": (c.c_int, [P, P]),
@@ -237,6 +238,13 @@ def frr_assignment(ctx: Context, seed: int, key: int, w_out=None):
 def frr_assignments(ctx: Context, seed: int, first_draw: int, count: int, w_out=None):
     w = np.empty((count, ctx.n), dtype=np.uint8) if w_out is None else w_out
     _check(lib().frr_assignments(ctx.handle, seed, first_draw, count, _ptr(w)), "frr_assignments")
+    return w
+
+
+def frr_assignment_from_words(ctx: Context, words, w_out=None):
+    wd = np.ascontiguousarray(words, dtype=np.uint32) if isinstance(words, (list, tuple, np.ndarray)) else words
+    w = np.empty(ctx.n, dtype=np.uint8) if w_out is None else w_out
+    _check(lib().frr_assignment_from_words(ctx.handle, _ptr(wd), _ptr(w)), "frr_assignment_from_words")
     return w
 
 

@@ -309,3 +309,25 @@ def test_randtest_exact_workload():
     want = O.randtest(W, W[0], Y, w.tau_grid, 0.05)
     _check_counts(got, want)
     assert got["ci_lo"] == want["ci_lo"] and got["ci_hi"] == want["ci_hi"]
+
+
+@pytest.mark.parametrize("n,n1", [(20, 10), (100, 50), (129, 1), (1000, 500), (2000, 1999), (2048, 1024)])
+def test_warp_select_with_ties_matches_library_sort(n, n1):
+    """Words with heavy ties (few distinct values) and ties exactly at the n1 boundary:
+    the treated set is the n1 smallest (word, unit) pairs."""
+    X = ar1_covariates(n, 1, 3, 0.0)
+    rng = np.random.default_rng(n + n1)
+    cases = [rng.integers(0, 4, n, dtype=np.uint64).astype(np.uint32),                 # 4 distinct values
+             np.full(n, 0xffffffff, dtype=np.uint32),                                   # all equal, maximal
+             rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)]
+    w = cases[2].copy()
+    srt = np.sort(w)
+    w[w == srt[n1]] = srt[n1 - 1]                                                       # tie across the boundary
+    cases.append(w)
+    with _ctx(X, n1, whiten="diag") as ctx:
+        for words in cases:
+            got = frr.frr_assignment_from_words(ctx, words)
+            order = np.lexsort((np.arange(n), words.astype(np.int64)))
+            want = np.zeros(n, dtype=np.uint8)
+            want[order[:n1]] = 1
+            assert np.array_equal(got, want)
