@@ -36,7 +36,7 @@ def build_library(force: bool = False, verbose: bool = False) -> Path:
     if not force and not _stale():
         return LIB
     tmp = LIB.with_suffix(f".{os.getpid()}.tmp.so")
-    cmd = [NVCC, *ARCH, *FLAGS, *map(str, sources()), "-o", str(tmp), "-lcuda"]
+    cmd = [NVCC, *ARCH, *FLAGS, *map(str, sources()), "-o", str(tmp)]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)

@@ -97,7 +97,7 @@ static void release(frr_ctx* ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void* bufs[] = {ctx->Zc64, ctx->Z32, ctx->Zhi, ctx->Zlo, ctx->Q, ctx->Qsum, ctx->qexp, ctx->binom, ctx->Mhat,
                     ctx->ret_idx[0], ctx->ret_idx[1], ctx->ret_m[0], ctx->ret_m[1], ctx->dev_counters, ctx->M64,
-                    ctx->ukeys, ctx->misc, ctx->misc2, ctx->sel};
+                    ctx->ukeys, ctx->misc, ctx->misc2, ctx->sel, ctx->Zq};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
@@ -193,6 +193,7 @@ frr_status frr_init(frr_ctx** out, const double* X, int64_t n, int64_t d, int64_
     INIT_CUDA(cudaMalloc(&ctx->Qsum, (size_t)d * sizeof(long long)));
     INIT_CUDA(cudaMalloc(&ctx->qexp, (size_t)d * sizeof(int)));
     INIT_CUDA(cudaMalloc(&ctx->binom, 64 * 64 * sizeof(uint64_t)));
+    INIT_CUDA(cudaMalloc(&ctx->Zq, (size_t)7 * d * ctx->kpad * sizeof(__nv_bfloat16)));
     INIT_CUDA(cudaMalloc(&ctx->dev_counters, 16 * sizeof(int)));
     INIT_CUDA(cudaMemsetAsync(ctx->dev_counters, 0, 16 * sizeof(int), ctx->stream));
 #undef INIT_CUDA

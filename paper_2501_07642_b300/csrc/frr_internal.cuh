@@ -1,6 +1,7 @@
 // frr_internal.cuh -- context layout and helpers shared by the CUDA sources of libfrr.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -62,6 +63,9 @@ struct frr_ctx {
     long long* Qsum = nullptr; // d
     int* qexp = nullptr;       // d: Q_ij = Zc_ij * 2^qexp_j (rounded)
     uint64_t* binom = nullptr; // 64 x 64 binomial table (exact mode)
+    __nv_bfloat16* Zq = nullptr;   // 7 x d x kpad: balanced base-256 digit planes of Q (exact recheck)
+    CUtensorMap qmap{};            // tensor map over Zq (rows 7d, columns kpad)
+    bool qmap_ready = false;
 
     frr::BandConsts band32{}, band_tc{};
 
@@ -130,6 +134,9 @@ frr_status words_select_launch(frr_ctx* ctx, const uint32_t* words_dev, uint32_t
 frr_status unpack_launch(frr_ctx* ctx, const uint32_t* rows_dev, uint64_t count, uint8_t* w_dev);
 frr_status recheck_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws_dev, int64_t count,
                           double* M64_dev);
+frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws_dev, int64_t count,
+                             double* M64_dev);
+frr_status recheck_sum_launch(frr_ctx* ctx, const double* part, int ncb, int64_t count, double* M64_dev);
 frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold, uint64_t total);
 frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B);
 frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out);

@@ -4,9 +4,10 @@
 // loop sharing the GPU with other work (cudaMalloc / cudaFree may synchronise the
 // device and stall it), or an application whose device memory is owned by another
 // allocator, such as a framework's caching pool with a fixed budget. For them this
-// entry point runs the same recheck kernels as frr_recheck on caller-owned device
-// buffers, with the only scratch it needs -- the per-CTA partial sums -- in one
-// fixed array compiled into the library.
+// entry point computes the same exact treated sums as frr_recheck -- with the int64
+// CUDA-core form of the recheck, which needs no bit-row buffer -- on caller-owned device
+// buffers, with the only scratch it needs (the per-CTA partial sums) in one fixed array
+// compiled into the library.
 #include "frr_internal.cuh"
 
 #include <mutex>

@@ -277,6 +277,22 @@ __global__ void k_derive(const double* __restrict__ Z, int n, int d, int kpad, i
     }
 }
 
+// Balanced base-256 digits of Q: Q = sum_{k<7} q_k 256^k with q_k in [-128, 127], plane k
+// stored K-major as BF16 (integers of this size are exact): Zq[(k d + j) kpad + p].
+__global__ void k_digits(const long long* __restrict__ Q, int kpad, int d, __nv_bfloat16* __restrict__ Zq)
+{
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)kpad * d) return;
+    const int j = (int)(idx / kpad), p = (int)(idx % kpad);
+    long long v = Q[(size_t)p * d + j];
+    for (int k = 0; k < 7; ++k) {
+        int q = (int)(v & 0xFF);
+        if (q >= 128) q -= 256;
+        v = (v - q) >> 8;
+        Zq[((size_t)k * d + j) * kpad + p] = __float2bfloat16_rn((float)q);
+    }
+}
+
 __global__ void k_qsum(const long long* __restrict__ Q, int kpad, int d, long long* __restrict__ Qsum)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -451,6 +467,7 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
                                                               ctx->Z32, ctx->Zhi, ctx->Zlo, ctx->Q);
     }
     k_qsum<<<ceil_div(d, 128), 128, 0, s>>>(ctx->Q, ctx->kpad, d, ctx->Qsum);
+    k_digits<<<(unsigned)(((size_t)ctx->kpad * d + 255) / 256), 256, 0, s>>>(ctx->Q, ctx->kpad, d, ctx->Zq);
     k_band_cols<<<d, 256, 0, s>>>(ctx->Zc64, n, d, (int)ctx->n1, ctx->kused, eps, eps + d);
     PREP_CHECK(cudaGetLastError());
     {

@@ -1,0 +1,218 @@
+// frr_recheck_tc.cu -- exact-sum recheck of candidate draws on the tensor cores.
+//
+// The accepted set is decided on M computed from exact treated sums S_T,j =
+// sum_{i in T} Q_ij of the fixed-point covariates Q = round(Zc 2^qexp) (|Q| <= 2^50).
+// Q is written in balanced base-256 digits, Q = sum_{k<7} q_k 256^k with q_k in
+// [-128, 127], each digit plane stored in BF16 (exact). For a 0/1 assignment row w,
+// D_k = sum_i w_i q_k(i) is an integer of magnitude below 2^18, so the tensor cores'
+// FP32 accumulation of the digit products is exact, and S_T = sum_k D_k 256^k is
+// rebuilt exactly in int64 (Horner). The epilogue then forms, per column,
+// Delta_j = S_T 2^-q / n1 - (S_all - S_T) 2^-q / n0 in FP64 -- an assignment and its
+// complement swap S_T and S_C exactly -- and the CTA's partial sum of Delta_j^2.
+//
+// One CTA per (128 candidates, 64 columns): 7 accumulators of 64 columns in TMEM.
+// Warps 0-3 epilogue, warp 4 TMA (7 digit tiles per K block), warp 5 MMA, warps 6-9
+// expand the candidates' bit rows (computed beforehand) into BF16 0/1 A tiles.
+#include "frr_internal.cuh"
+#include "frr_gen.cuh"
+#include "frr_tc_ptx.cuh"
+
+namespace frr {
+using namespace tc;
+namespace {
+
+constexpr int kM = 128, kN = 64, kPlanes = 7, kKB = 64;
+constexpr int kStB = 3, kStA = 2;
+constexpr int kPlaneBytes = kN * kKB * 2;          // 8 KiB
+constexpr int kBBytes = kPlanes * kPlaneBytes;     // 56 KiB
+constexpr int kABytes = kM * kKB * 2;              // 16 KiB
+constexpr int kThreads = 320;
+
+size_t rc_smem_bytes() { return 1024 + (size_t)kStB * kBBytes + (size_t)kStA * kABytes + 16 * 8 + 16; }
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restrict__ rows, int W, int64_t C, int nkb,
+             int d, int n, int n1, const long long* __restrict__ Qsum, const int* __restrict__ qexp,
+             double* __restrict__ part, int ncb, int* err)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* sB = smem;
+    unsigned char* sA = sB + kStB * kBBytes;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sA + kStA * kABytes);
+    uint64_t* b_full = bar;
+    uint64_t* b_empty = b_full + kStB;
+    uint64_t* a_full = b_empty + kStB;
+    uint64_t* a_empty = a_full + kStA;
+    uint64_t* acc_full = a_empty + kStA;
+    uint64_t* mma_done = acc_full + 1;
+    uint32_t* sTmem = reinterpret_cast<uint32_t*>(mma_done + 1);
+    volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t tile = blockIdx.x;
+    const int chunk = blockIdx.y;
+    if (tid == 0) {
+        for (int s = 0; s < kStB; ++s) { mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); }
+        for (int s = 0; s < kStA; ++s) { mbar_init(&a_full[s], 4); mbar_init(&a_empty[s], 1); }
+        mbar_init(acc_full, 1);
+        mbar_init(mma_done, 1);
+        *sAbort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        tmem_alloc(sTmem, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *sTmem;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            int kb = 0;
+            bool ok = true;
+            for (; kb < nkb && ok; ++kb) {
+                const int s = kb % kStB;
+                if (!(ok = wait_bar(&b_empty[s], ((kb / kStB) & 1u) ^ 1u, sAbort, err, 11))) break;
+                mbar_arrive_expect_tx(&b_full[s], kBBytes);
+                for (int pl = 0; pl < kPlanes; ++pl)
+                    tma_load_2d(sB + s * kBBytes + pl * kPlaneBytes, &map_q, &b_full[s], kb * kKB, pl * d + chunk * kN);
+            }
+            if (!ok) {
+                const int from = kb > kStB ? kb - kStB : 0;
+                for (int i = from; i < kb; ++i) {
+                    const unsigned long long t0 = clock64();
+                    while (!mbar_try_wait(&b_full[i % kStB], (i / kStB) & 1u) && clock64() - t0 < kWaitCycles) {}
+                }
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            bool ok = true;
+            const uint32_t idesc = idesc_bf16(kM, kN);
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+                const int sa = kb % kStA, sb = kb % kStB;
+                if (!(ok = wait_bar(&a_full[sa], (kb / kStA) & 1u, sAbort, err, 12))) break;
+                if (!(ok = wait_bar(&b_full[sb], (kb / kStB) & 1u, sAbort, err, 13))) break;
+                tc_fence_after();
+                const uint64_t adesc = sdesc_sw128(smem_u32(sA + sa * kABytes));
+#pragma unroll
+                for (int pl = 0; pl < kPlanes; ++pl) {
+                    const uint64_t bdesc = sdesc_sw128(smem_u32(sB + sb * kBBytes + pl * kPlaneBytes));
+#pragma unroll
+                    for (int k = 0; k < kKB / 16; ++k)
+                        umma_bf16(tmem_base + (uint32_t)(pl * kN), adesc + 2u * k, bdesc + 2u * k, idesc,
+                                  (kb | k) != 0 ? 1u : 0u);
+                }
+                umma_commit(&b_empty[sb]);
+                umma_commit(&a_empty[sa]);
+            }
+            if (ok) umma_commit(acc_full);
+            umma_commit(mma_done);
+            const unsigned long long t0 = clock64();
+            while (!mbar_try_wait(mma_done, 0) && clock64() - t0 < kWaitCycles) {}
+        }
+    } else if (warp >= 6) {
+        const int r = tid - 6 * 32;  // row (candidate) of the A tile
+        const int64_t cand = tile * kM + r;
+        const uint32_t* rw = rows + (cand < C ? cand : 0) * (int64_t)W;
+        bool ok = true;
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int s = kb % kStA;
+            if (!(ok = wait_bar(&a_empty[s], ((kb / kStA) & 1u) ^ 1u, sAbort, err, 14))) break;
+            unsigned char* dst = sA + s * kABytes + (r >> 3) * 1024 + (r & 7) * 128;
+            const uint32_t w2[2] = {cand < C ? rw[2 * kb] : 0u, cand < C ? rw[2 * kb + 1] : 0u};
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const uint32_t x = (w2[q >> 2] >> (8 * (q & 3))) & 0xFFu;
+                const uint32_t ylo = ((x & 0xFu) * 0x00204081u) & 0x01010101u;
+                const uint32_t yhi = ((x >> 4) * 0x00204081u) & 0x01010101u;
+                uint4 v;
+                v.x = __byte_perm(ylo, 0u, 0x4140) * 0x3F80u;
+                v.y = __byte_perm(ylo, 0u, 0x4342) * 0x3F80u;
+                v.z = __byte_perm(yhi, 0u, 0x4140) * 0x3F80u;
+                v.w = __byte_perm(yhi, 0u, 0x4342) * 0x3F80u;
+                *reinterpret_cast<uint4*>(dst + ((q ^ (r & 7)) << 4)) = v;
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_full[s]);
+        }
+    } else {
+        // epilogue: lane = candidate row 32 * warp + lane
+        const int row = 32 * warp + lane;
+        const int64_t cand = tile * kM + row;
+        bool ok = wait_bar(acc_full, 0u, sAbort, err, 15);
+        double psum = 0.0;
+        if (ok) {
+            tc_fence_after();
+            const uint32_t taddr = tmem_base + ((uint32_t)(32 * warp) << 16);
+            const int n0 = n - n1;
+            for (int c0 = 0; c0 < kN; c0 += 32) {
+                long long S[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) S[j] = 0;
+                for (int pl = kPlanes - 1; pl >= 0; --pl) {
+                    uint32_t v[32];
+                    tmem_ld32(taddr + (uint32_t)(pl * kN + c0), v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) S[j] = S[j] * 256 + (long long)__float2int_rn(__uint_as_float(v[j]));
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = chunk * kN + c0 + j;
+                    if (col < d) {
+                        const int e = qexp[col];
+                        const double m1 = __ddiv_rn(ldexp((double)S[j], -e), (double)n1);
+                        const double m0 = __ddiv_rn(ldexp((double)(Qsum[col] - S[j]), -e), (double)n0);
+                        const double dl = __dsub_rn(m1, m0);
+                        psum = __dadd_rn(psum, __dmul_rn(dl, dl));
+                    }
+                }
+            }
+        }
+        if (ok && cand < C) part[cand * ncb + chunk] = psum;
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, 512);
+    }
+}
+
+}  // namespace
+
+// Exact-sum recheck of `count` draws (device list) on the tensor cores; M64 on the device.
+frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws, int64_t count,
+                             double* M64)
+{
+    if (count <= 0) return FRR_OK;
+    const int W = 4 * ctx->kb;
+    const int ncb = ceil_div(ctx->d, kN);
+    const size_t rows_bytes = (size_t)count * W * sizeof(uint32_t);
+    const size_t part_bytes = (size_t)count * ncb * sizeof(double);
+    FRR_TRY(ensure_device(ctx, &ctx->misc2, &ctx->misc2_bytes, rows_bytes + part_bytes + 256));
+    uint32_t* rows = static_cast<uint32_t*>(ctx->misc2);
+    double* part = reinterpret_cast<double*>(static_cast<char*>(ctx->misc2) + ((rows_bytes + 255) & ~size_t(255)));
+    FRR_TRY(bits_launch(ctx, seed, exact, 0, (uint64_t)count, draws, rows));
+    if (!ctx->qmap_ready) {
+        if (!make_map_bf16(&ctx->qmap, ctx->Zq, (uint64_t)ctx->kpad, (uint64_t)kPlanes * ctx->d, kKB, kN))
+            return FRR_E_CUDA;
+        ctx->qmap_ready = true;
+    }
+    const size_t smem = rc_smem_bytes();
+    FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_recheck_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)((count + kM - 1) / kM), (unsigned)ncb);
+    k_recheck_tc<<<grid, kThreads, smem, ctx->stream>>>(ctx->qmap, rows, W, count, ctx->kused / kKB, (int)ctx->d,
+                                                       (int)ctx->n, (int)ctx->n1, ctx->Qsum, ctx->qexp, part, ncb,
+                                                       ctx->dev_counters + 12);
+    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    return recheck_sum_launch(ctx, part, ncb, count, M64);
+}
+
+}  // namespace frr

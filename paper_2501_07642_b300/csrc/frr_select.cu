@@ -503,26 +503,18 @@ frr_status unpack_launch(frr_ctx* ctx, const uint32_t* rows, uint64_t count, uin
     return FRR_OK;
 }
 
-frr_status recheck_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws, int64_t count, double* M64)
+frr_status recheck_sum_launch(frr_ctx* ctx, const double* part, int ncb, int64_t count, double* M64)
 {
-    if (count <= 0) return FRR_OK;
-    const int ncb = ceil_div(ctx->d, RCOLS);
-    FRR_TRY(ensure_device(ctx, &ctx->misc2, &ctx->misc2_bytes, (size_t)count * ncb * sizeof(double)));
-    double* part = static_cast<double*>(ctx->misc2);
-    frr_status s;
-    switch (ctx->kb) {
-        case 1: s = launch_recheck_kb<1>(ctx, seed, exact, draws, count, part, ncb); break;
-        case 2: s = launch_recheck_kb<2>(ctx, seed, exact, draws, count, part, ncb); break;
-        case 4: s = launch_recheck_kb<4>(ctx, seed, exact, draws, count, part, ncb); break;
-        case 8: s = launch_recheck_kb<8>(ctx, seed, exact, draws, count, part, ncb); break;
-        case 16: s = launch_recheck_kb<16>(ctx, seed, exact, draws, count, part, ncb); break;
-        default: return FRR_E_UNSUPPORTED;
-    }
-    FRR_TRY(s);
     const double scale = ((double)ctx->n1 * (double)ctx->n0) / (double)ctx->n;
     k_recheck_sum<<<ceil_div(count, 256), 256, 0, ctx->stream>>>(part, ncb, count, scale, M64);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     return FRR_OK;
+}
+
+// The recheck of the selection path and of frr_recheck: the tensor-core digit-plane kernel.
+frr_status recheck_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws, int64_t count, double* M64)
+{
+    return recheck_tc_launch(ctx, seed, exact, draws, count, M64);
 }
 
 frr_status balance_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout)
@@ -740,10 +732,20 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
         FRR_CUDA_TRY(ctx, cudaGetLastError());
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_pinned, &sel->nsel, sizeof(SelTail), cudaMemcpyDeviceToHost,
                                           ctx->stream));
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(static_cast<char*>(ctx->host_pinned) + 128, ctx->dev_counters + 12, sizeof(int),
+                                          cudaMemcpyDeviceToHost, ctx->stream));
     }
     cudaEventRecord(ctx->ev[4], ctx->stream);
     FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    if (r > 0) memcpy(&tail, ctx->host_pinned, sizeof(SelTail));
+    if (r > 0) {
+        memcpy(&tail, ctx->host_pinned, sizeof(SelTail));
+        if (*reinterpret_cast<int*>(static_cast<char*>(ctx->host_pinned) + 128) != 0) {
+            FRR_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dev_counters + 12, 0, sizeof(int), ctx->stream));
+            FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            st.active = false;
+            return FRR_E_TIMEOUT;
+        }
+    }
     float t = 0.f;
     cudaEventElapsedTime(&t, ctx->ev[3], ctx->ev[4]);
     ctx->stats.ms_recheck += t;
@@ -777,8 +779,9 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
 
 namespace frr {
 
-// The recheck of recheck_launch with the per-CTA partial sums in a device array the
-// caller provides (part_capacity doubles); nothing is allocated. Pool seeds only.
+// The int64 CUDA-core form of the recheck (the same exact treated sums as the tensor-core
+// form behind recheck_launch) with the per-CTA partial sums in a device array the caller
+// provides (part_capacity doubles); nothing is allocated. Pool seeds only.
 frr_status recheck_launch_into(frr_ctx* ctx, uint64_t seed, const uint64_t* draws, int64_t count, double* part,
                                size_t part_capacity, double* M64)
 {
