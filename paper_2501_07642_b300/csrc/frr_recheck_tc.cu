@@ -149,7 +149,10 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
         if (ok) {
             tc_fence_after();
             const uint32_t taddr = tmem_base + ((uint32_t)(32 * warp) << 16);
-            const int n0 = n - n1;
+            // Delta_j = 2^-q_j (S_T r1 - S_C r0) with r1 = 1/n1, r0 = 1/n0: when n1 = n0 both use
+            // the same reciprocal, so swapping S_T and S_C negates Delta_j exactly. Few FP64
+            // operations per column: B300's FP64 unit is narrow.
+            const double r1 = 1.0 / (double)n1, r0 = 1.0 / (double)(n - n1);
             for (int c0 = 0; c0 < kN; c0 += 32) {
                 long long S[32];
 #pragma unroll
@@ -165,10 +168,10 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
                 for (int j = 0; j < 32; ++j) {
                     const int col = chunk * kN + c0 + j;
                     if (col < d) {
-                        const int e = qexp[col];
-                        const double m1 = __ddiv_rn(ldexp((double)S[j], -e), (double)n1);
-                        const double m0 = __ddiv_rn(ldexp((double)(Qsum[col] - S[j]), -e), (double)n0);
-                        const double dl = __dsub_rn(m1, m0);
+                        const double scale = __longlong_as_double((long long)(1023 - qexp[col]) << 52);  // 2^-q_j
+                        const double a = __dmul_rn((double)S[j], r1);
+                        const double b = __dmul_rn((double)(Qsum[col] - S[j]), r0);
+                        const double dl = __dmul_rn(__dsub_rn(a, b), scale);
                         psum = __dadd_rn(psum, __dmul_rn(dl, dl));
                     }
                 }

@@ -159,16 +159,20 @@ __device__ __forceinline__ double lower_bound_m(const CutParams& cp, float v)
     return m - band_value(cp.lin, cp.quad, cp.rel, cp.safety, m);
 }
 
-// largest non-negative float v with L(v) <= T (L(v) <= 0 <= T near 0, increasing after its minimum)
+// largest non-negative float v with L(v) <= T, where L(v) = v - s (lin sqrt(v) + quad + rel v)
+// is <= 0 near 0 and increasing after its minimum. With x = sqrt(v), L(v) = T is the
+// quadratic (1 - s rel) x^2 - s lin x - (s quad + T) = 0; its root gives v, and the float
+// result is stepped down until L(v) <= T holds and up while the next float still satisfies it.
 __device__ float largest_v_below(const CutParams& cp, double T, uint32_t lo_bits)
 {
     if (!(T < INFINITY)) return INFINITY;
-    uint32_t lo = lo_bits, hi = 0x7f800000u;  // L(lo) <= T holds; L(inf) > T
-    while (hi - lo > 1) {
-        const uint32_t mid = lo + (hi - lo) / 2;
-        if (lower_bound_m(cp, __uint_as_float(mid)) <= T) lo = mid; else hi = mid;
-    }
-    return __uint_as_float(lo);
+    const double A = 1.0 - cp.safety * cp.rel, Bq = cp.safety * cp.lin, Cq = cp.safety * cp.quad + T;
+    const double x = (Bq + sqrt(Bq * Bq + 4.0 * A * Cq)) / (2.0 * A);
+    uint32_t v = __float_as_uint((float)(x * x));
+    if (v < lo_bits) v = lo_bits;                 // L(lo) <= T holds by construction
+    for (int i = 0; i < 64 && v > lo_bits && lower_bound_m(cp, __uint_as_float(v)) > T; ++i) --v;
+    for (int i = 0; i < 64 && v < 0x7f7fffffu && lower_bound_m(cp, __uint_as_float(v + 1)) <= T; ++i) ++v;
+    return __uint_as_float(v);
 }
 
 // Block-wide exclusive scan of one int per thread (SNT threads). Returns the
@@ -413,13 +417,14 @@ k_sel_stats(const double* __restrict__ m64, const float* __restrict__ mhat, cons
     double mrel = 0.0, mband = 0.0, thr = -INFINITY;
     int viol = 0;
     for (int64_t c = threadIdx.x; c < r; c += SNT) {
-        const double a = (double)mhat[c], m = m64[c];
-        const double err = fabs(a - m);
-        const double band = band_value(cp.lin, cp.quad, cp.rel, cp.safety, a);
-        if (m > 0.0) mrel = fmax(mrel, err / m);
-        if (band > 0.0) mband = fmax(mband, err / band);
+        // diagnostics only: FP32 is enough (and cheap on B300)
+        const float a = mhat[c], m = (float)m64[c];
+        const float err = fabsf(a - m);
+        const float band = (float)cp.safety * ((float)cp.lin * sqrtf(fmaxf(a, 0.f)) + (float)cp.quad + (float)cp.rel * a);
+        if (m > 0.f) mrel = fmax(mrel, (double)__fdividef(err, m));
+        if (band > 0.f) mband = fmax(mband, (double)__fdividef(err, band));
         viol += (err > band) ? 1 : 0;
-        if (sel[c]) thr = fmax(thr, m);
+        if (sel[c]) thr = fmax(thr, m64[c]);
     }
     for (int off = 16; off >= 1; off >>= 1) {
         mrel = fmax(mrel, __shfl_xor_sync(kFull, mrel, off));
