@@ -17,6 +17,7 @@ one JSON line.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -256,7 +257,7 @@ def run_frr(args):
         achieved = flops * B / (r["ms_balance"] / 1e3) / 1e12
         peak = peaks["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_balance_tc", "peak_source": f"bf16_tflops (burst, {peak_kind})",
+                "traffic": tc_traffic(B), "kernel": "k_balance_tc", "peak_source": f"bf16_tflops (burst, {peak_kind})",
                 "flop_per_draw": flops}
         dtype = "bf16"
     else:
@@ -288,6 +289,24 @@ def run_frr(args):
             "selection": {k: r["stats"][k] for k in ("candidates", "accepted", "max_rel_err", "max_err_over_band",
                                                      "band_violations", "parity_at_risk")}}
     print(json.dumps(line), flush=True)
+
+
+
+def tc_traffic(B):
+    """DRAM bytes per k_balance_tc launch from the committed ncu summary, or None when the
+    kernel's sources changed since the capture or the launch size differs."""
+    md = ROOT / "profiles" / "k_balance_tc_precision_n1000_d1000.md"
+    try:
+        text = md.read_text()
+        rec = json.loads(text[text.rindex("```json") + 7:text.rindex("```")])
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update((ROOT / f).read_bytes())
+        if h.hexdigest() != rec["source_sha256"] or int(rec["draws_per_launch"]) != int(B):
+            return None
+        return int(rec["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 def main():
