@@ -13,7 +13,7 @@
  * Pins: each function is checked by tests/test_oracle_pins.py against values
  * fixed by the paper or by mathematics (Philox known-answer vectors, brute-force
  * enumeration, E[M] = d, affine invariance, complement symmetry, the d = 1 closed
- * form, the d = n-1 degeneracy, textbook exact randomization p-values, the
+ * form, the d = n-1 degeneracy, ranks against the enumeration order, textbook exact randomization p-values, the
  * accepted-count and minimum-p numbers printed in Sec. 2.2). No function is
  * "parity unpinned".
  */
@@ -143,6 +143,43 @@ int64_t oracle_enum_masks(int64_t n, int64_t n1, uint64_t first_rank, int64_t co
         v = next_mask(v);
     }
     return written;
+}
+
+/* Position of a mask in that order, by the combinatorial number system (Knuth,
+ * TAOCP Vol. 4A, Sec. 7.2.1.3): with the set positions c_1 < ... < c_n1, the rank
+ * is sum_i C(c_i, i). Enumerating in increasing integer order is colexicographic
+ * order, whose ranks are exactly these sums. */
+static uint64_t binom_exact(int64_t a, int64_t b)
+{
+    if (b < 0 || b > a) return 0;
+    if (b > a - b) b = a - b;
+    unsigned __int128 r = 1;
+    for (int64_t i = 1; i <= b; ++i) r = r * (unsigned __int128)(a - b + i) / (unsigned __int128)i;
+    return (uint64_t)r;
+}
+
+uint64_t oracle_rank_of_mask(uint64_t mask)
+{
+    uint64_t rank = 0;
+    int64_t i = 0;
+    for (int64_t c = 0; c < 64; ++c)
+        if ((mask >> c) & 1u) rank += binom_exact(c, ++i);
+    return rank;
+}
+
+/* Inverse of oracle_rank_of_mask: for i = n1 down to 1 take the largest c with
+ * C(c, i) <= remaining rank. */
+uint64_t oracle_mask_of_rank(int64_t n, int64_t n1, uint64_t rank)
+{
+    uint64_t mask = 0;
+    int64_t c = n - 1;
+    for (int64_t i = n1; i >= 1; --i) {
+        while (binom_exact(c, i) > rank) --c;
+        mask |= 1ull << c;
+        rank -= binom_exact(c, i);
+        --c;
+    }
+    return mask;
 }
 
 static void mask_to_w(uint64_t mask, int64_t n, uint8_t* w)
@@ -319,9 +356,7 @@ void oracle_balance_list(const double* Zc, int64_t n, int64_t d, int64_t n1, int
 #endif
         for (int64_t b = 0; b < count; ++b) {
             if (exact) {
-                uint64_t m;
-                oracle_enum_masks(n, n1, draws[b], 1, &m);
-                mask_to_w(m, n, w);
+                mask_to_w(oracle_mask_of_rank(n, n1, draws[b]), n, w);
             } else {
                 assignment_with_scratch(seed, draws[b], n, n1, w, r, pairs);
             }

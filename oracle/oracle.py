@@ -56,6 +56,10 @@ def lib():
                                         c.c_uint64, c.c_int64, P, c.c_int]
         _lib.oracle_balance_list.argtypes = [P, c.c_int64, c.c_int64, c.c_int64, c.c_int, c.c_uint64,
                                              P, c.c_int64, P, c.c_int]
+        _lib.oracle_rank_of_mask.argtypes = [c.c_uint64]
+        _lib.oracle_rank_of_mask.restype = c.c_uint64
+        _lib.oracle_mask_of_rank.argtypes = [c.c_int64, c.c_int64, c.c_uint64]
+        _lib.oracle_mask_of_rank.restype = c.c_uint64
         _lib.oracle_k_from_q.argtypes = [c.c_double, c.c_int64]
         _lib.oracle_k_from_q.restype = c.c_int64
         _lib.oracle_select_from_M.argtypes = [P, c.c_uint64, c.c_int64, c.c_double, c.c_double, P, P, c.c_int64]
@@ -107,6 +111,16 @@ def enum_masks(n: int, n1: int, first: int = 0, count: int | None = None) -> np.
     if got < 0:
         raise ValueError("exact enumeration needs 1 <= n1 <= n <= 63")
     return out[:got]
+
+
+def rank_of_mask(mask: int) -> int:
+    """Colex rank (position in the enumeration order) of an n1-subset mask."""
+    return int(lib().oracle_rank_of_mask(int(mask)))
+
+
+def mask_of_rank(n: int, n1: int, rank: int) -> int:
+    """The n1-subset mask at colex rank `rank` (n <= 63)."""
+    return int(lib().oracle_mask_of_rank(n, n1, int(rank)))
 
 
 def masks_to_w(masks: np.ndarray, n: int) -> np.ndarray:

@@ -31,12 +31,22 @@ k_balance_f32(const float* __restrict__ Z32, int dpad32, int kused, int n, int n
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t tile_off = (uint64_t)blockIdx.x * TD;
-    for (int t = warp; t < TD; t += NT / 32) {
-        uint32_t* row = bits + t * RS;
-        if (tile_off + t < B) {
-            warp_draw_bits<KB>(exact != 0, seed, first + tile_off + t, n, n1, binom, row, lane);
-        } else {
-            for (int q = lane; q < W; q += 32) row[q] = 0u;
+    if (exact) {
+        // exact enumeration: one colex rank per thread
+        static_assert(NT >= TD, "one thread per draw");
+        if (threadIdx.x < TD) {
+            uint32_t* row = bits + threadIdx.x * RS;
+            if (tile_off + threadIdx.x < B) lane_exact_row(first + tile_off + threadIdx.x, n, n1, binom, row, W);
+            else for (int q = 0; q < W; ++q) row[q] = 0u;
+        }
+    } else {
+        for (int t = warp; t < TD; t += NT / 32) {
+            uint32_t* row = bits + t * RS;
+            if (tile_off + t < B) {
+                warp_draw_bits<KB>(false, seed, first + tile_off + t, n, n1, binom, row, lane);
+            } else {
+                for (int q = lane; q < W; q += 32) row[q] = 0u;
+            }
         }
     }
     __syncthreads();

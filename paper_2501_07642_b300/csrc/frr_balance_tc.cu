@@ -237,6 +237,7 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
     } else if (warp >= 6 + kExpWarps) {
         // ------------------------------------------------------ generation --
         const int gw = warp - (6 + kExpWarps);
+        static_assert(NG * 32 >= kTileM, "exact mode gives every row of a tile its own lane");
         uint32_t it = 0;
         bool ok = true;
         for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
@@ -248,14 +249,25 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
             const int kbx = x->kb, nx = x->n, n1x = x->n1, ex = x->exact;
             const uint64_t sx = x->seed, fx = x->first, Bx = x->B;
             const uint64_t* bx = x->binom;
-            for (int r = gw; r < kTileM; r += NG) {
-                const uint64_t off = tl * kTileM + r;
-                uint32_t* row = bits + r * RS;
-                if (off < Bx) {
-                    if constexpr (MULTI) draw_bits_kb<KB>(kbx, ex != 0, sx, fx + off, nx, n1x, bx, row, lane);
-                    else warp_draw_bits<KB>(ex != 0, sx, fx + off, nx, n1x, bx, row, lane);
-                } else {
-                    for (int q = lane; q < W; q += 32) row[q] = 0u;
+            if (ex) {
+                // exact enumeration: lane j of this warp unranks row gw + NG j on its own
+                const int r = gw + NG * lane;
+                if (r < kTileM) {
+                    const uint64_t off = tl * kTileM + r;
+                    uint32_t* row = bits + r * RS;
+                    if (off < Bx) lane_exact_row(fx + off, nx, n1x, bx, row, 4 * kbx);
+                    else for (int q = 0; q < 4 * kbx; ++q) row[q] = 0u;
+                }
+            } else {
+                for (int r = gw; r < kTileM; r += NG) {
+                    const uint64_t off = tl * kTileM + r;
+                    uint32_t* row = bits + r * RS;
+                    if (off < Bx) {
+                        if constexpr (MULTI) draw_bits_kb<KB>(kbx, false, sx, fx + off, nx, n1x, bx, row, lane);
+                        else warp_draw_bits<KB>(false, sx, fx + off, nx, n1x, bx, row, lane);
+                    } else {
+                        for (int q = lane; q < W; q += 32) row[q] = 0u;
+                    }
                 }
             }
             __syncwarp();

@@ -224,6 +224,30 @@ __device__ __forceinline__ void warp_store_mask_bits(uint64_t mask, uint32_t* ro
     for (int q = lane; q < words; q += 32) row[q] = (q < 4) ? mine : 0u;
 }
 
+// Word c (c < 4) of the K-order bit row of an n <= 63 mask: bit l is unit 4l + c.
+// The stride-4 bits are gathered by halving the gaps four times.
+__device__ __forceinline__ uint32_t kword_of_mask(uint64_t mask, int c)
+{
+    uint64_t x = (mask >> c) & 0x1111111111111111ull;
+    x = (x | (x >> 3)) & 0x0303030303030303ull;
+    x = (x | (x >> 6)) & 0x000F000F000F000Full;
+    x = (x | (x >> 12)) & 0x000000FF000000FFull;
+    x = (x | (x >> 24)) & 0x000000000000FFFFull;
+    return (uint32_t)x;
+}
+
+// Exact enumeration with one rank per lane (no warp collectives): the lane unranks its
+// own colex rank and writes that draw's row (words 0..3 from the mask, the rest zero).
+__device__ __forceinline__ void lane_exact_row(uint64_t rank, int n, int n1, const uint64_t* binom, uint32_t* row,
+                                               int words)
+{
+    const uint64_t m = unrank_colex(rank, n, n1, binom);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (c < words) row[c] = kword_of_mask(m, c);
+    for (int q = 4; q < words; ++q) row[q] = 0u;
+}
+
 // One draw -> its bit row. 4 * KB words are written.
 template <int KB>
 __device__ __forceinline__ void warp_draw_bits(bool exact, uint64_t seed, uint64_t draw, int n, int n1,

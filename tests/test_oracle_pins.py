@@ -91,6 +91,36 @@ def test_enumeration_visits_every_subset_once_in_increasing_order(oracle, n, n1)
         assert np.array_equal(oracle.enum_masks(n, n1, first=7, count=3), masks[7:10])
 
 
+@pytest.mark.parametrize("n,n1", [(1, 1), (10, 1), (10, 9), (12, 3), (16, 8)])
+def test_rank_and_unrank_follow_the_enumeration_order(oracle, n, n1):
+    # the brute-force order (sorted integer masks) fixes every rank
+    ref = sorted(sum(1 << i for i in c) for c in itertools.combinations(range(n), n1))
+    assert [oracle.mask_of_rank(n, n1, r) for r in range(len(ref))] == ref
+    assert [oracle.rank_of_mask(m) for m in ref] == list(range(len(ref)))
+
+
+def test_unrank_at_the_largest_supported_n(oracle):
+    n, n1 = 63, 31
+    N = math.comb(n, n1)
+    assert oracle.mask_of_rank(n, n1, 0) == (1 << n1) - 1
+    assert oracle.mask_of_rank(n, n1, N - 1) == ((1 << n) - 1) ^ ((1 << (n - n1)) - 1)
+    rng = np.random.default_rng(3)
+    for r in rng.integers(0, N, size=200, dtype=np.uint64):
+        m = oracle.mask_of_rank(n, n1, int(r))
+        assert bin(m).count("1") == n1 and m < (1 << n)
+        assert oracle.rank_of_mask(m) == int(r)
+
+
+@pytest.mark.parametrize("n", [10, 16])
+def test_complement_reverses_the_rank_when_groups_are_equal(oracle, n):
+    # with n1 = n / 2 the complement of rank r sits at rank C(n, n1) - 1 - r (brute force)
+    n1 = n // 2
+    masks = oracle.enum_masks(n, n1)
+    full = (1 << n) - 1
+    N = masks.size
+    assert all(oracle.rank_of_mask(full ^ int(masks[r])) == N - 1 - r for r in range(N))
+
+
 # ----------------------------------------------------------------- prep ----
 @pytest.mark.parametrize("whiten,ridge", [("chol", 0.0), ("ridge", 0.1), ("diag", 0.0)])
 def test_prep_against_library_routines(oracle, whiten, ridge):
