@@ -229,6 +229,51 @@ typedef struct {
  * succeeded, else the first failing status; ex[e].status holds each one. stats may be NULL. */
 frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opts* opts, frr_batch_stats* stats);
 
+/* ---- planning diagnostics (Sec. 2.2 "Choosing stringency"; App. A-D) -------------------
+ * Host-only scalar math; needs no context and no GPU. k = 1/n_T + 1/n_C and
+ * sigma_prog^2 = R2 / (1 - R2) sigma^2. Inputs set to NaN switch their group of outputs off;
+ * outputs that were not computed are NaN. */
+typedef struct {
+    int64_t n_T, n_C;    /* group sizes, >= 1 */
+    int64_t d;           /* covariates, >= 1 */
+    double R2;           /* share of outcome variance explained by the covariates, [0, 1) */
+    double sigma;        /* residual standard deviation, > 0 */
+    double q;            /* acceptance probability (0, 1] for the ex-ante outputs, or NaN */
+    double M_obs;        /* an observed imbalance M >= 0 for the realised outputs, or NaN */
+    double tau;          /* effect size of interest for power and q*, or NaN */
+    double alpha;        /* two-sided size, (0, 1); read only when tau is given */
+    double power;        /* target power, (0, 1); read only when tau is given */
+} frr_diag_in;
+
+typedef struct {
+    double k;                /* 1/n_T + 1/n_C */
+    double sigma2_prog;      /* R2 / (1 - R2) sigma^2 */
+    double rmse_complete;    /* ex-ante RMSE under complete randomization, sqrt(k (sigma^2 + sigma2_prog)) (App. B) */
+    /* from M_obs (App. A) */
+    double rmse_realised;    /* typical orientation: sqrt(sigma^2 k + sigma2_prog M / d) */
+    double rmse_cs_bound;    /* Cauchy-Schwarz upper bound: sqrt(sigma^2 k + sigma2_prog M) */
+    /* at q (Sec. 2.2, App. C) */
+    double c_q;              /* chi2_d quantile at q (inf at q = 1) */
+    double a_q;              /* implied threshold on M, k c_q */
+    double v_a;              /* shrinkage factor P(chi2_{d+2} <= c_q) / q */
+    double rmse_accept;      /* ex-ante RMSE given acceptance, sqrt(k (sigma^2 + v_a sigma2_prog)) */
+    double rmse_reduction;   /* 1 - rmse_accept / rmse_complete */
+    double expected_M;       /* E[M | accept] = k d v_a */
+    double power_at_q;       /* two-sided normal-approximation power at tau (needs tau) */
+    /* inversion for tau, alpha, power (App. D) */
+    double snr_needed;       /* z_{1-alpha/2} + z_{power} */
+    double q_star;           /* largest q with rmse_accept(q) <= |tau| / snr_needed; 0 below the double range */
+    double log10_q_star;     /* log10 of q_star, finite even where q_star underflows */
+    double c_star;           /* chi-square cut at q_star */
+    double v_star;           /* v_a at q_star */
+    double draws_per_accept; /* 1 / q_star */
+    int32_t q_star_status;   /* 0 found by the line search, 1 q = 1 already meets the target,
+                                2 unreachable (sigma^2 k alone exceeds the target), -1 not asked */
+} frr_diag_out;
+
+/* Fills *out from *in. FRR_E_ARG for a NULL pointer or an input outside the ranges above. */
+frr_status frr_diagnose(const frr_diag_in* in, frr_diag_out* out);
+
 /* Copies the whitened covariates Zc (host, n x d row-major FP64) out of the context. */
 frr_status frr_whitened(const frr_ctx* ctx, double* Zc_out);
 

@@ -68,6 +68,22 @@ class frr_batch_stats(ctypes.Structure):
                 ("ms_init", ctypes.c_double), ("ms_balance", ctypes.c_double), ("ms_select", ctypes.c_double)]
 
 
+class frr_diag_in(ctypes.Structure):
+    _fields_ = [("n_T", ctypes.c_int64), ("n_C", ctypes.c_int64), ("d", ctypes.c_int64), ("R2", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("q", ctypes.c_double), ("M_obs", ctypes.c_double),
+                ("tau", ctypes.c_double), ("alpha", ctypes.c_double), ("power", ctypes.c_double)]
+
+
+class frr_diag_out(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in (
+        "k", "sigma2_prog", "rmse_complete", "rmse_realised", "rmse_cs_bound", "c_q", "a_q", "v_a",
+        "rmse_accept", "rmse_reduction", "expected_M", "power_at_q", "snr_needed", "q_star", "log10_q_star",
+        "c_star", "v_star", "draws_per_accept")] + [("q_star_status", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -99,6 +115,7 @@ def lib():
             "frr_whitened": (c.c_int, [P, P]),
             "frr_last_stats": (c.c_int, [P, P]),
             "frr_batch_run": (c.c_int, [P, I64, P, P]),
+            "frr_diagnose": (c.c_int, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -343,3 +360,16 @@ def frr_batch_run(experiments, precision: str = "split_bf16", band_safety: float
     stats = {k: getattr(st, k) for k, _ in frr_batch_stats._fields_}
     stats["status"] = rc
     return res, stats
+
+
+def frr_diagnose(n_T: int, n_C: int, d: int, R2: float, sigma: float = 1.0, q=None, M_obs=None, tau=None,
+                 alpha: float = 0.05, power: float = 0.8) -> dict:
+    """Planning diagnostics (realised RMSE from M_obs, ex-ante RMSE at q, q* for tau).
+    Host-only; needs no context and no GPU. Outputs that were not asked for are NaN."""
+    nan = math.nan
+    a = frr_diag_in(int(n_T), int(n_C), int(d), float(R2), float(sigma), nan if q is None else float(q),
+                    nan if M_obs is None else float(M_obs), nan if tau is None else float(tau), float(alpha),
+                    float(power))
+    o = frr_diag_out()
+    _check(lib().frr_diagnose(ctypes.byref(a), ctypes.byref(o)), "frr_diagnose")
+    return o.as_dict()
