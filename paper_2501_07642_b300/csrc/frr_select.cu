@@ -5,14 +5,15 @@
 // library breaks ties by the lower draw index. The bulk paths give an
 // approximate M_hat with a per-draw error band |M_hat - M| <= band(M_hat).
 // Selection therefore runs in two stages:
-//   1. streaming filter (one CTA): over the chunk's M_hat plus the retained
-//      set, find the K-th smallest M_hat, form the cut T = U(M_(K)) with
+//   1. streaming filter: over the chunk's M_hat plus the retained set, bound
+//      the K-th smallest M_hat from above by two grid-wide histogram levels on
+//      its float bits (m_up >= M_(K)), form the cut T = U(m_up) with
 //      U(m) = m + band(m), and keep every draw whose lower bound
 //      L(m) = m - band(m) is <= T. Any draw among the true K best has
 //      L <= M <= M_(K)(true) <= T, so the retained set always contains them.
-//   2. exact-sum recheck of the retained draws (fixed-point Zc, exact int64
-//      sums, FP64 assembly), then the K smallest (M64, draw index), reported
-//      in ascending draw order.
+//   2. exact-sum recheck of the retained draws (fixed-point Zc, exact integer
+//      sums on the tensor cores, FP64 assembly), then the K smallest
+//      (M64, draw index), reported in ascending draw order.
 #include "frr_internal.cuh"
 #include "frr_gen.cuh"
 
@@ -555,7 +556,7 @@ double host_lower_bound(const frr_ctx* ctx, float v)
 
 float host_threshold_cut(const frr_ctx* ctx, double a)
 {
-    // largest float v >= 0 with L(v) <= a (same bisection as the device)
+    // largest float v >= 0 with L(v) <= a; {v : L(v) <= a} is an interval [0, v*] for a >= L(0)
     if (!(a < INFINITY)) return INFINITY;
     uint32_t lo = 0, hi = 0x7f800000u;
     float flo; memcpy(&flo, &lo, 4);
