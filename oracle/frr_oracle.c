@@ -480,6 +480,48 @@ int oracle_randtest(const uint8_t* W /* K x n accepted assignments */, int64_t K
     return 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Pairwise distances (Sec. 4, fast_distance): D_ij = sqrt(sum_k (x_ik - y_jk)^2) */
+/* for rows x_i of X (n x d) and y_j of Y (m x d), FP32 inputs taken exactly in  */
+/* FP64, differences squared and summed in ascending k. squared != 0 returns the */
+/* sum itself. Y == NULL means Y = X.                                           */
+/* ------------------------------------------------------------------------- */
+void oracle_distance(const float* X, int64_t n, const float* Y, int64_t m, int64_t d, int squared, double* D)
+{
+    if (Y == NULL) { Y = X; m = n; }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < m; ++j) {
+            double acc = 0.0;
+            for (int64_t k = 0; k < d; ++k) {
+                const double t = (double)X[i * d + k] - (double)Y[j * d + k];
+                acc += t * t;
+            }
+            D[i * m + j] = squared ? acc : sqrt(acc);
+        }
+}
+
+/* Entries (i, j) listed in pairs (count of them), same definition. */
+void oracle_distance_pairs(const float* X, const float* Y, int64_t d, const int64_t* ij, int64_t count, int squared,
+                           double* out)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t e = 0; e < count; ++e) {
+        const float* x = X + ij[2 * e] * d;
+        const float* y = Y + ij[2 * e + 1] * d;
+        double acc = 0.0;
+        for (int64_t k = 0; k < d; ++k) {
+            const double t = (double)x[k] - (double)y[k];
+            acc += t * t;
+        }
+        out[e] = squared ? acc : sqrt(acc);
+    }
+}
+
 int oracle_openmp_threads(void)
 {
 #ifdef _OPENMP

@@ -60,6 +60,8 @@ def lib():
         _lib.oracle_rank_of_mask.restype = c.c_uint64
         _lib.oracle_mask_of_rank.argtypes = [c.c_int64, c.c_int64, c.c_uint64]
         _lib.oracle_mask_of_rank.restype = c.c_uint64
+        _lib.oracle_distance.argtypes = [P, c.c_int64, P, c.c_int64, c.c_int64, c.c_int, P]
+        _lib.oracle_distance_pairs.argtypes = [P, P, c.c_int64, P, c.c_int64, c.c_int, P]
         _lib.oracle_k_from_q.argtypes = [c.c_double, c.c_int64]
         _lib.oracle_k_from_q.restype = c.c_int64
         _lib.oracle_select_from_M.argtypes = [P, c.c_uint64, c.c_int64, c.c_double, c.c_double, P, P, c.c_int64]
@@ -218,3 +220,24 @@ def randtest(W: np.ndarray, w_obs: np.ndarray, Y: np.ndarray, tau, alpha: float 
 
 def threads() -> int:
     return int(lib().oracle_openmp_threads())
+
+
+def distance(X: np.ndarray, Y: np.ndarray | None = None, squared: bool = False) -> np.ndarray:
+    """FP64 pairwise Euclidean distances between the rows of FP32 X (n x d) and Y (m x d)."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    n, d = X.shape
+    Yc = None if Y is None else np.ascontiguousarray(Y, dtype=np.float32)
+    m = n if Yc is None else Yc.shape[0]
+    out = np.zeros((n, m))
+    lib().oracle_distance(_p(X), n, None if Yc is None else _p(Yc), m, d, int(squared), _p(out))
+    return out
+
+
+def distance_pairs(X: np.ndarray, Y: np.ndarray, ij: np.ndarray, squared: bool = False) -> np.ndarray:
+    """FP64 distances of the listed (i, j) pairs (an array of shape (count, 2))."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Y = np.ascontiguousarray(Y, dtype=np.float32)
+    ij = np.ascontiguousarray(ij, dtype=np.int64)
+    out = np.zeros(ij.shape[0])
+    lib().oracle_distance_pairs(_p(X), _p(Y), X.shape[1], _p(ij), ij.shape[0], int(squared), _p(out))
+    return out

@@ -352,3 +352,40 @@ def test_randtest_interval_is_grid_points_with_p_above_alpha(oracle):
     assert res["ci_lo"] <= oracle.dim(y, w_obs) <= res["ci_hi"]
     res2 = oracle.randtest(W, w_obs, y, np.array([100.0]), alpha=0.05)
     assert math.isnan(res2["ci_lo"]) and math.isnan(res2["ci_hi"])
+
+
+# -------------------------------------------------------------- distances ----
+def test_distance_matches_library_cdist(oracle):
+    from scipy.spatial.distance import cdist
+    rng = np.random.default_rng(21)
+    X = rng.standard_normal((37, 19)).astype(np.float32)
+    Y = (rng.standard_normal((23, 19)) * 3 + 1).astype(np.float32)
+    want = cdist(X.astype(np.float64), Y.astype(np.float64))
+    assert np.allclose(oracle.distance(X, Y), want, rtol=1e-13, atol=0)
+    assert np.allclose(oracle.distance(X, Y, squared=True), want ** 2, rtol=1e-12, atol=0)
+
+
+def test_distance_self_is_symmetric_with_zero_diagonal(oracle):
+    X = np.random.default_rng(22).standard_normal((30, 7)).astype(np.float32)
+    D = oracle.distance(X)
+    assert np.array_equal(D, D.T) and np.all(np.diag(D) == 0.0)
+
+
+def test_distance_closed_forms(oracle):
+    # points on two axes: |a e1 - b e2| = sqrt(a^2 + b^2); integer shifts leave distances unchanged
+    X = np.zeros((3, 4), dtype=np.float32)
+    Y = np.zeros((2, 4), dtype=np.float32)
+    X[:, 0] = [3, 5, 8]
+    Y[:, 1] = [4, 12]
+    D = oracle.distance(X, Y)
+    assert np.array_equal(D, np.sqrt(np.array([[9 + 16, 9 + 144], [25 + 16, 25 + 144], [64 + 16, 64 + 144]])))
+    assert np.array_equal(oracle.distance(X + 7, Y + 7), D)
+
+
+def test_distance_pairs_are_entries_of_the_matrix(oracle):
+    rng = np.random.default_rng(23)
+    X = rng.standard_normal((11, 5)).astype(np.float32)
+    Y = rng.standard_normal((13, 5)).astype(np.float32)
+    ij = np.stack([rng.integers(0, 11, 40), rng.integers(0, 13, 40)], axis=1)
+    D = oracle.distance(X, Y)
+    assert np.array_equal(oracle.distance_pairs(X, Y, ij), D[ij[:, 0], ij[:, 1]])
