@@ -366,8 +366,14 @@ frr_status launch_kb(frr_ctx* ctx, int kbmax, cudaStream_t stream, int num_sms, 
 // Fills the experiment descriptor of a prepared context for draws [first, first + B).
 frr_status tc_describe(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout, TcExp* x)
 {
-    if (!make_map(&x->map_hi, ctx->Zhi, ctx->kpad, (int)ctx->d) || !make_map(&x->map_lo, ctx->Zlo, ctx->kpad, (int)ctx->d))
-        return FRR_E_CUDA;
+    if (!ctx->maps_ready) {
+        if (!make_map(&ctx->map_hi, ctx->Zhi, ctx->kpad, (int)ctx->d) ||
+            !make_map(&ctx->map_lo, ctx->Zlo, ctx->kpad, (int)ctx->d))
+            return FRR_E_CUDA;
+        ctx->maps_ready = true;
+    }
+    x->map_hi = ctx->map_hi;
+    x->map_lo = ctx->map_lo;
     x->binom = ctx->binom;
     x->Mout = Mout;
     x->seed = seed;
@@ -387,19 +393,8 @@ frr_status tc_describe(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, 
 frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout)
 {
     if (B == 0) return FRR_OK;
-    static thread_local const frr_ctx* cached_ctx = nullptr;
-    static thread_local const void* cached_hi = nullptr;
-    static thread_local TcExp one;
-    if (cached_ctx != ctx || cached_hi != ctx->Zhi) {
-        FRR_TRY(tc_describe(ctx, seed, exact, first, B, Mout, &one));
-        cached_ctx = ctx;
-        cached_hi = ctx->Zhi;
-    }
-    one.Mout = Mout;
-    one.seed = seed;
-    one.first = first;
-    one.B = B;
-    one.exact = exact ? 1 : 0;
+    TcExp one;
+    FRR_TRY(tc_describe(ctx, seed, exact, first, B, Mout, &one));
     const unsigned long long tiles = (B + kTileM - 1) / kTileM;
     return launch_kb(ctx, ctx->kb, ctx->stream, ctx->num_sms, one, nullptr, nullptr, 1, tiles, ctx->dev_counters + 12);
 }

@@ -66,6 +66,8 @@ struct frr_ctx {
     __nv_bfloat16* Zq = nullptr;   // 7 x d x kpad: balanced base-256 digit planes of Q (exact recheck)
     CUtensorMap qmap{};            // tensor map over Zq (rows 7d, columns kpad)
     bool qmap_ready = false;
+    CUtensorMap map_hi{}, map_lo{};  // tensor maps over Zhi / Zlo (balance kernel B operand)
+    bool maps_ready = false;
 
     frr::BandConsts band32{}, band_tc{};
 

@@ -116,6 +116,7 @@ def lib():
             "frr_last_stats": (c.c_int, [P, P]),
             "frr_batch_run": (c.c_int, [P, I64, P, P]),
             "frr_diagnose": (c.c_int, [P, P]),
+            "frr_fast_distance": (c.c_int, [P, I64, P, I64, I64, c.c_int, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -373,3 +374,26 @@ def frr_diagnose(n_T: int, n_C: int, d: int, R2: float, sigma: float = 1.0, q=No
     o = frr_diag_out()
     _check(lib().frr_diagnose(ctypes.byref(a), ctypes.byref(o)), "frr_diagnose")
     return o.as_dict()
+
+
+def frr_fast_distance(X, Y=None, squared: bool = False, D_out=None, stream=None):
+    """Pairwise Euclidean distances between the rows of X (n x d) and Y (m x d), FP32.
+    X, Y, D_out: numpy arrays (host) or torch CUDA tensors (device). Returns D_out, or a
+    new host array when D_out is None."""
+    def _f32(a):
+        if hasattr(a, "data_ptr"):
+            if a.dtype.__str__() != "torch.float32":
+                raise TypeError("device inputs must be float32 tensors")
+            return a
+        return np.ascontiguousarray(a, dtype=np.float32)
+    Xc = _f32(X)
+    n, d = Xc.shape
+    Yc = None if Y is None else _f32(Y)
+    if Yc is not None and Yc.shape[1] != d:
+        raise ValueError("X and Y need the same number of columns")
+    m = n if Yc is None else Yc.shape[0]
+    out = np.empty((n, m), dtype=np.float32) if D_out is None else D_out
+    st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(lib().frr_fast_distance(_ptr(Xc), n, _ptr(Yc), m, d, int(bool(squared)), _ptr(out), st),
+           "frr_fast_distance")
+    return out

@@ -80,3 +80,16 @@ def test_null_context_is_rejected(frr):
     assert L.frr_stream_chunk(None, 0, 1) == -1
     assert L.frr_last_stats(None, None) == -1
     L.frr_destroy(None)  # ignored
+
+
+def test_fast_distance_rejects_bad_arguments_without_a_gpu(frr):
+    L = frr.lib()
+    X = np.zeros((4, 3), dtype=np.float32)
+    D = np.zeros((4, 4), dtype=np.float32)
+    st = frr.STATUS
+    assert st[L.frr_fast_distance(None, 4, None, 0, 3, 0, D.ctypes.data, None)] == "FRR_E_ARG"
+    assert st[L.frr_fast_distance(X.ctypes.data, 4, None, 0, 3, 0, None, None)] == "FRR_E_ARG"
+    assert st[L.frr_fast_distance(X.ctypes.data, 0, None, 0, 3, 0, D.ctypes.data, None)] == "FRR_E_ARG"
+    assert st[L.frr_fast_distance(X.ctypes.data, 4, None, 0, 0, 0, D.ctypes.data, None)] == "FRR_E_ARG"
+    assert st[L.frr_fast_distance(X.ctypes.data, 4, X.ctypes.data, 0, 3, 0, D.ctypes.data, None)] == "FRR_E_ARG"
+    assert st[L.frr_fast_distance(X.ctypes.data, 1 << 31, None, 0, 3, 0, D.ctypes.data, None)] == "FRR_E_UNSUPPORTED"
