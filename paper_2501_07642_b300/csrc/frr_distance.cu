@@ -8,7 +8,9 @@
 //   A row i = [x_h | x_h | x_l],   B row j = [y_h | y_l | y_h],   A_i . B_j = x.y - x_l y_l - e,
 // with |x - x_h - x_l| <= 2^-18 |x| per element. Squared norms come from the FP32 values
 // (summed in FP64). The epilogue reads the accumulator from TMEM, adds the norms, clamps
-// at 0, takes the square root (unless the squared distance was asked for) and stores.
+// at 0, takes the square root (unless the squared distance was asked for) and stages
+// 32 x 32 blocks in shared memory for TMA stores (direct stores when the output rows are
+// not 16-byte aligned).
 //
 // k_distance_tc: one persistent CTA per SM over 128 x 256 output tiles (grouped by
 // bands of tile rows so that the B rows stay in L2). Warp roles:
@@ -22,6 +24,7 @@
 #include "frr_internal.cuh"
 
 #include <cuda.h>
+#include <string.h>
 
 #include "frr_tc_ptx.cuh"
 
@@ -39,7 +42,8 @@ constexpr int kDStageBytes = kDABytes + kDBBytes;
 constexpr int kDEpiWarps = 8;
 constexpr int kDThreads = (kDEpiWarps + 2) * 32;
 constexpr int kDGroup = 8;                     // tile rows per band of the tile order
-constexpr size_t kDSmem = 1024 + (size_t)kDStages * kDStageBytes + 256;
+constexpr int kDOutBytes = 32 * 32 * 4;        // per epilogue warp: 32 rows x 32 columns staged for a TMA store
+constexpr size_t kDSmem = 1024 + (size_t)kDStages * kDStageBytes + (size_t)kDEpiWarps * kDOutBytes + 256;
 
 // Split rows of V (rows x d FP32) into the K-major BF16 operand (rows x 3 dp) and the
 // squared norms. layout 0: [h | h | l] (A side), layout 1: [h | l | h] (B side).
@@ -87,12 +91,13 @@ __device__ __forceinline__ void dist_tile_of(uint64_t t, int ntn, int ntm, int& 
 
 __global__ void __launch_bounds__(kDThreads, 1)
 k_distance_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-              const float* __restrict__ nx, const float* __restrict__ ny, int n, int m, int nkb, int squared,
-              int vec4, float* __restrict__ D, int* err)
+              const __grid_constant__ CUtensorMap mapD, const float* __restrict__ nx, const float* __restrict__ ny,
+              int n, int m, int nkb, int squared, int tma_out, int vec4, float* __restrict__ D, int* err)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kDStages * kDStageBytes);
+    float* sOut = reinterpret_cast<float*>(smem + kDStages * kDStageBytes);   // kDEpiWarps x 32 x 32, 128B-swizzled
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kDStages * kDStageBytes + kDEpiWarps * kDOutBytes);
     uint64_t* full = bar;
     uint64_t* empty = full + kDStages;
     uint64_t* acc_full = empty + kDStages;
@@ -185,25 +190,49 @@ k_distance_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             const int buf = g & 1;
             if (!(ok = wait_bar(&acc_full[buf], (g >> 1) & 1u, sAbort, err, 14))) break;
             tc_fence_after();
-            const int row = tm * kDM + 32 * quarter + lane;
+            const int row0 = tm * kDM + 32 * quarter;
+            const int row = row0 + lane;
             const float nrow = row < n ? nx[row] : 0.0f;
             float* drow = D + (size_t)(row < n ? row : 0) * (size_t)m;
+            float* sbuf = sOut + warp * (kDOutBytes / 4);
             for (int c0 = half * (kDN / 2); c0 < (half + 1) * (kDN / 2); c0 += 32) {
                 const int col0 = tn * kDN + c0;
                 uint32_t v[32];
                 __syncwarp();
                 tmem_ld32(tmem_base + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(buf * kDN + c0), v);
                 tmem_wait_ld();
-                if (row < n && col0 < m) {
-                    float out[32];
+                if (row0 >= n || col0 >= m) continue;   // warp-uniform: nothing of this chunk is stored
+                // the norms of the 32 columns (padded with zeros past m), as 8 broadcast loads
+                float ncol[32];
+                const float4* ny4 = reinterpret_cast<const float4*>(ny + col0);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = col0 + j;
-                        const float ncol = col < m ? __ldg(ny + col) : 0.0f;
-                        float d2 = fmaf(-2.0f, __uint_as_float(v[j]), nrow + ncol);
-                        d2 = fmaxf(d2, 0.0f);
-                        out[j] = squared ? d2 : sqrtf(d2);
+                for (int q = 0; q < 8; ++q) {
+                    const float4 t4 = __ldg(ny4 + q);
+                    ncol[4 * q] = t4.x; ncol[4 * q + 1] = t4.y; ncol[4 * q + 2] = t4.z; ncol[4 * q + 3] = t4.w;
+                }
+                float out[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    float d2 = fmaf(-2.0f, __uint_as_float(v[j]), nrow + ncol[j]);
+                    d2 = fmaxf(d2, 0.0f);
+                    out[j] = squared ? d2 : sqrtf(d2);
+                }
+                if (tma_out) {
+                    // stage row `lane` (16-byte chunk q at q ^ (lane % 8), the 128-byte swizzle)
+                    // and let one TMA store write the 32 x 32 block, clipped to n x m
+                    if (lane == 0) bulk_wait_read();
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        *reinterpret_cast<float4*>(sbuf + lane * 32 + 4 * (q ^ (lane & 7))) =
+                            make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(&mapD, sbuf, col0, row0);
+                        bulk_commit();
                     }
+                } else if (row < n) {
                     if (vec4 && col0 + 32 <= m) {
 #pragma unroll
                         for (int j = 0; j < 32; j += 4)
@@ -222,6 +251,7 @@ k_distance_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         }
     }
 
+    if (warp < kDEpiWarps && lane == 0) bulk_wait_all();
     tc_fence_before();
     __syncthreads();
     if (warp == kDEpiWarps + 1) {
@@ -298,7 +328,9 @@ extern "C" frr_status frr_fast_distance(const float* X, int64_t n, const float* 
     FRR_TRY(dist_alloc(A, (size_t)n * kp * 2, s));
     FRR_TRY(dist_alloc(B, (size_t)m * kp * 2, s));
     FRR_TRY(dist_alloc(nX, (size_t)n * sizeof(float), s));
-    FRR_TRY(dist_alloc(nY, (size_t)m * sizeof(float), s));
+    const int64_t mpad = (m + kDN - 1) / kDN * kDN;   // column norms padded with zeros to whole tiles
+    FRR_TRY(dist_alloc(nY, (size_t)mpad * sizeof(float), s));
+    DIST_CUDA(cudaMemsetAsync(nY.p, 0, (size_t)mpad * sizeof(float), s));
     FRR_TRY(dist_alloc(errb, sizeof(int), s));
     float* Dw = D_out;
     const bool dev_out = is_device_ptr(D_out);
@@ -314,17 +346,19 @@ extern "C" frr_status frr_fast_distance(const float* X, int64_t n, const float* 
                                            static_cast<float*>(nY.p));
     DIST_CUDA(cudaGetLastError());
 
-    CUtensorMap mapA, mapB;
+    CUtensorMap mapA, mapB, mapD;
     if (!make_map_bf16(&mapA, A.p, (uint64_t)kp, (uint64_t)n, kDK, kDM)) return FRR_E_CUDA;
     if (!make_map_bf16(&mapB, B.p, (uint64_t)kp, (uint64_t)m, kDK, kDN)) return FRR_E_CUDA;
     DIST_CUDA(cudaFuncSetAttribute(k_distance_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDSmem));
     const uint64_t tiles = (uint64_t)((n + kDM - 1) / kDM) * (uint64_t)((m + kDN - 1) / kDN);
     const unsigned grid = (unsigned)(tiles < (uint64_t)sms ? tiles : (uint64_t)sms);
-    // 16-byte row stores need m % 4 == 0 and a 16-byte aligned output
+    // 16-byte row stores, and TMA stores, need m % 4 == 0 and a 16-byte aligned output
     const int vec4 = ((m & 3) == 0 && (reinterpret_cast<uintptr_t>(Dw) & 15u) == 0) ? 1 : 0;
-    k_distance_tc<<<grid, kDThreads, kDSmem, s>>>(mapA, mapB, static_cast<const float*>(nX.p),
+    const int tma_out = vec4 && make_map_f32(&mapD, Dw, (uint64_t)m, (uint64_t)n, 32, 32) ? 1 : 0;
+    if (!tma_out) memset(&mapD, 0, sizeof(mapD));
+    k_distance_tc<<<grid, kDThreads, kDSmem, s>>>(mapA, mapB, mapD, static_cast<const float*>(nX.p),
                                                   static_cast<const float*>(nY.p), (int)n, (int)m, (int)(kp / kDK),
-                                                  squared ? 1 : 0, vec4, Dw, static_cast<int*>(errb.p));
+                                                  squared ? 1 : 0, tma_out, vec4, Dw, static_cast<int*>(errb.p));
     DIST_CUDA(cudaGetLastError());
     if (!dev_out)
         DIST_CUDA(cudaMemcpyAsync(D_out, Dw, (size_t)n * m * sizeof(float), cudaMemcpyDeviceToHost, s));

@@ -38,7 +38,9 @@ def _check(X, Y, D, squared):
     return err.max()
 
 
-@pytest.mark.parametrize("n,m,d", [(300, 517, 77), (128, 256, 64), (1, 1, 1), (129, 257, 130), (513, 3, 1000)])
+# m % 4 == 0 takes the TMA-store epilogue, other m the direct stores
+@pytest.mark.parametrize("n,m,d", [(300, 516, 77), (300, 517, 77), (128, 256, 64), (1, 1, 1), (1, 4, 3),
+                                   (129, 260, 130), (129, 257, 130), (513, 3, 1000), (257, 1028, 200)])
 @pytest.mark.parametrize("squared", [False, True])
 def test_ragged_shapes_against_oracle(n, m, d, squared):
     rng = np.random.default_rng(n * 7 + m + d)
