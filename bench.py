@@ -31,6 +31,10 @@ from pathlib import Path
 import numpy as np
 
 ROOT = Path(__file__).resolve().parent
+# library kernels per frr_select step of the precision workload (one chunk, retained set
+# <= 2048): k_balance_tc, k_sel_begin, k_sel_hist x2, k_sel_scan x2, k_sel_compact, k_bits,
+# k_recheck_tc, k_recheck_sum, k_rank, k_sel_finish
+LAUNCHES_PER_STEP = 12
 sys.path.insert(0, str(ROOT))
 
 METRIC = "balance-checked assignments/s at n=d=1000; split-BF16 vs FP32 path, same B300"
@@ -271,6 +275,7 @@ def run_frr(args):
                 "peak_source": f"148 SMs x 128 FP32 lanes x median sampled SM clock {mhz} MHz",
                 "adds_per_draw": adds}
         dtype = "f32"
+    dist_line = distance_bench(peaks["bf16_tflops"]) if args.distance else None
     cpu = None
     if args.cpu_baseline:
         rate, S, cores = oracle_rate(oracle_zc(X), n1, w.philox_seed, args.cpu_s)
@@ -284,12 +289,49 @@ def run_frr(args):
             "paths": {p: ({k: results[p][k] for k in ("value", "ms_per_step", "ms_balance", "ms_select", "ms_recheck")}
                           if "value" in results[p] else results[p])
                       for p in precisions},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": 14 * args.steps * ws,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": LAUNCHES_PER_STEP * args.steps * ws,
             "clocks": {k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "selection": {k: r["stats"][k] for k in ("candidates", "accepted", "max_rel_err", "max_err_over_band",
-                                                     "band_violations", "parity_at_risk")}}
+                                                     "band_violations", "parity_at_risk")},
+            "fast_distance": dist_line}
     print(json.dumps(line), flush=True)
 
+
+
+def distance_bench(peak_tflops: float, n: int = 16384, d: int = 768, reps: int = 5) -> dict:
+    """fast_distance on n x n pairs of d-dimensional FP32 rows (device in / out), one call =
+    operand split, norms and the tensor-core kernel; median of `reps` calls after 2 warm-ups."""
+    import torch
+
+    from paper_2501_07642_b300 import frr
+
+    g = torch.Generator(device="cuda").manual_seed(768)
+    X = torch.randn((n, d), device="cuda", generator=g)
+    Y = torch.randn((n, d), device="cuda", generator=g)
+    D = torch.empty((n, n), device="cuda")
+    for _ in range(2):
+        frr.frr_fast_distance(X, Y, D_out=D)
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        frr.frr_fast_distance(X, Y, D_out=D)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    dp = 64 * ((d + 63) // 64)
+    executed = 2.0 * n * n * 3 * dp  # three BF16 products per FP32 product (split operands)
+    del X, Y, D
+    torch.cuda.empty_cache()
+    return {"workload": f"embedding_n{n}_m{n}_d{d}", "ms_per_call": ms,
+            "pairs_per_s": n * n / (ms / 1e3),
+            "roofline": {"bound": "tensor", "achieved": executed / (ms / 1e3) / 1e12, "peak": peak_tflops,
+                         "unit": "TFLOP/s", "frac": executed / (ms / 1e3) / 1e12 / peak_tflops,
+                         "flop_per_pair": 2.0 * 3 * dp, "note": "whole call (split + norms + kernel)"},
+            "fp32_equivalent_tflops": 2.0 * n * n * d / (ms / 1e3) / 1e12,
+            "output_gbs": n * n * 4 / (ms / 1e3) / 1e9}
 
 
 def tc_traffic(B):
@@ -321,6 +363,7 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-distance", dest="distance", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

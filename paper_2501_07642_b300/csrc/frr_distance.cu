@@ -7,7 +7,7 @@
 // up to 64):
 //   A row i = [x_h | x_h | x_l],   B row j = [y_h | y_l | y_h],   A_i . B_j = x.y - x_l y_l - e,
 // with |x - x_h - x_l| <= 2^-18 |x| per element. Squared norms come from the FP32 values
-// (summed in FP64). The epilogue reads the accumulator from TMEM, adds the norms, clamps
+// (a compensated sum, about as accurate as twice the FP32 precision). The epilogue reads the accumulator from TMEM, adds the norms, clamps
 // at 0, takes the square root (unless the squared distance was asked for) and stages
 // 32 x 32 blocks in shared memory for TMA stores (direct stores when the output rows are
 // not 16-byte aligned).
@@ -26,6 +26,9 @@
 #include <cuda.h>
 #include <string.h>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "frr_tc_ptx.cuh"
 
 namespace frr {
@@ -41,40 +44,58 @@ constexpr int kDBBytes = kDN * kDK * 2;        // 32 KiB
 constexpr int kDStageBytes = kDABytes + kDBBytes;
 constexpr int kDEpiWarps = 8;
 constexpr int kDThreads = (kDEpiWarps + 2) * 32;
-constexpr int kDGroup = 8;                     // tile rows per band of the tile order
+constexpr int kDGroup = 32;                    // tile rows per band of the tile order (4096 rows of X)
 constexpr int kDOutBytes = 32 * 32 * 4;        // per epilogue warp: 32 rows x 32 columns staged for a TMA store
 constexpr size_t kDSmem = 1024 + (size_t)kDStages * kDStageBytes + (size_t)kDEpiWarps * kDOutBytes + 256;
 
-// Split rows of V (rows x d FP32) into the K-major BF16 operand (rows x 3 dp) and the
-// squared norms. layout 0: [h | h | l] (A side), layout 1: [h | l | h] (B side).
-__global__ void k_dist_prep(const float* __restrict__ V, int64_t rows, int d, int dp, int layout,
-                            __nv_bfloat16* __restrict__ out, float* __restrict__ norm2)
+// Error-free transformations (Knuth's TwoSum; the FMA product error), used for the
+// squared norms in the manner of Ogita, Rump and Oishi's Dot2 (SIAM J. Sci. Comput. 26,
+// 2005): the sum of squares is carried as an unevaluated pair (s, c), about as accurate as
+// a sum in twice the FP32 precision, and rounded once at the end.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
-    const int64_t r = blockIdx.x;
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Split rows of V (rows x d FP32) into the K-major BF16 operand (rows x 3 dp) and the
+// squared norms; one warp per row. layout 0: [h | h | l] (A side), layout 1: [h | l | h]
+// (B side).
+__global__ void __launch_bounds__(256) k_dist_prep(const float* __restrict__ V, int64_t rows, int d, int dp,
+                                                   int layout, __nv_bfloat16* __restrict__ out,
+                                                   float* __restrict__ norm2)
+{
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (r >= rows) return;
     const float* v = V + r * (int64_t)d;
     __nv_bfloat16* o = out + r * (int64_t)(3 * dp);
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < dp; k += blockDim.x) {
+    float s = 0.f, c = 0.f;
+    for (int k = lane; k < dp; k += 32) {
         const float x = k < d ? v[k] : 0.0f;
         const __nv_bfloat16 h = __float2bfloat16_rn(x);
         const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
         o[k] = h;
         o[dp + k] = layout == 0 ? h : l;
         o[2 * dp + k] = layout == 0 ? l : h;
-        acc = fma((double)x, (double)x, acc);
+        const float p = x * x;
+        const float pe = fmaf(x, x, -p);
+        float t, q;
+        two_sum(s, p, t, q);
+        s = t;
+        c += q + pe;
     }
-    // block sum of the squares (fixed order: warp butterflies, then warps in order)
-    __shared__ double part[32];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
-        norm2[r] = (float)s;
+    for (int off = 16; off > 0; off >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s, off);
+        const float co = __shfl_xor_sync(0xffffffffu, c, off);
+        float t, q;
+        two_sum(s, so, t, q);
+        s = t;
+        c += co + q;
     }
+    if (lane == 0) norm2[r] = s + c;
 }
 
 __device__ __forceinline__ void dist_tile_of(uint64_t t, int ntn, int ntm, int& tm, int& tn)
@@ -273,10 +294,35 @@ struct DevBuf {
     ~DevBuf() { if (p) cudaFreeAsync(p, s); }
 };
 
-frr_status dist_alloc(DevBuf& b, size_t bytes, cudaStream_t s)
+// The operand temporaries come from a pool per device that keeps its memory after the
+// call (release threshold: never), so repeated calls do not map and unmap it again.
+cudaMemPool_t dist_pool(int dev)
+{
+    static std::mutex mu;
+    static std::unordered_map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pool;
+    return pool;
+}
+
+frr_status dist_alloc(DevBuf& b, size_t bytes, cudaStream_t s, cudaMemPool_t pool = nullptr)
 {
     b.s = s;
-    const cudaError_t e = cudaMallocAsync(&b.p, bytes ? bytes : 16, s);
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&b.p, bytes ? bytes : 16, pool, s)
+                               : cudaMallocAsync(&b.p, bytes ? bytes : 16, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
@@ -325,8 +371,10 @@ extern "C" frr_status frr_fast_distance(const float* X, int64_t n, const float* 
         DIST_CUDA(cudaMemcpyAsync(yin.p, Y, (size_t)m * d * sizeof(float), cudaMemcpyHostToDevice, s));
         Yd = static_cast<const float*>(yin.p);
     }
-    FRR_TRY(dist_alloc(A, (size_t)n * kp * 2, s));
-    FRR_TRY(dist_alloc(B, (size_t)m * kp * 2, s));
+    cudaMemPool_t pool = dist_pool(dev);
+    if (pool == nullptr) return FRR_E_CUDA;
+    FRR_TRY(dist_alloc(A, (size_t)n * kp * 2, s, pool));
+    FRR_TRY(dist_alloc(B, (size_t)m * kp * 2, s, pool));
     FRR_TRY(dist_alloc(nX, (size_t)n * sizeof(float), s));
     const int64_t mpad = (m + kDN - 1) / kDN * kDN;   // column norms padded with zeros to whole tiles
     FRR_TRY(dist_alloc(nY, (size_t)mpad * sizeof(float), s));
@@ -340,10 +388,10 @@ extern "C" frr_status frr_fast_distance(const float* X, int64_t n, const float* 
     }
     DIST_CUDA(cudaMemsetAsync(errb.p, 0, sizeof(int), s));
 
-    k_dist_prep<<<(unsigned)n, 256, 0, s>>>(Xd, n, (int)d, dp, 0, static_cast<__nv_bfloat16*>(A.p),
-                                           static_cast<float*>(nX.p));
-    k_dist_prep<<<(unsigned)m, 256, 0, s>>>(Yd, m, (int)d, dp, 1, static_cast<__nv_bfloat16*>(B.p),
-                                           static_cast<float*>(nY.p));
+    k_dist_prep<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(Xd, n, (int)d, dp, 0, static_cast<__nv_bfloat16*>(A.p),
+                                                       static_cast<float*>(nX.p));
+    k_dist_prep<<<(unsigned)((m + 7) / 8), 256, 0, s>>>(Yd, m, (int)d, dp, 1, static_cast<__nv_bfloat16*>(B.p),
+                                                       static_cast<float*>(nY.p));
     DIST_CUDA(cudaGetLastError());
 
     CUtensorMap mapA, mapB, mapD;

@@ -138,7 +138,9 @@ frr_status recheck_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_
                           double* M64_dev);
 frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws_dev, int64_t count,
                              double* M64_dev);
-frr_status recheck_sum_launch(frr_ctx* ctx, const double* part, int ncb, int64_t count, double* M64_dev);
+// M64 = scale * (sum over the ncb column-block partial sums of each draw) / denom
+frr_status recheck_sum_launch(frr_ctx* ctx, const double* part, int ncb, int64_t count, double* M64_dev, double scale,
+                              double denom);
 frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold, uint64_t total);
 frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B);
 frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out);

@@ -6,9 +6,10 @@
 // [-128, 127], each digit plane stored in BF16 (exact). For a 0/1 assignment row w,
 // D_k = sum_i w_i q_k(i) is an integer of magnitude below 2^18, so the tensor cores'
 // FP32 accumulation of the digit products is exact, and S_T = sum_k D_k 256^k is
-// rebuilt exactly in int64 (Horner). The epilogue then forms, per column,
-// Delta_j = S_T 2^-q / n1 - (S_all - S_T) 2^-q / n0 in FP64 -- an assignment and its
-// complement swap S_T and S_C exactly -- and the CTA's partial sum of Delta_j^2.
+// rebuilt exactly in int64 (Horner). The epilogue then forms, per column, the exact
+// 128-bit integer N_j = S_T n - S_all n1 = n1 n0 Delta_j 2^q_j (an assignment and its
+// complement give -N_j when n1 = n0), rounds N_j 2^-q_j once to FP64 and adds its square
+// to the CTA's partial sum; M64 = sum / (n n1 n0).
 //
 // One CTA per (128 candidates, 64 columns): 7 accumulators of 64 columns in TMEM.
 // Warps 0-3 epilogue, warp 4 TMA (7 digit tiles per K block), warp 5 MMA, warps 6-9
@@ -27,6 +28,45 @@ constexpr int kPlaneBytes = kN * kKB * 2;          // 8 KiB
 constexpr int kBBytes = kPlanes * kPlaneBytes;     // 56 KiB
 constexpr int kABytes = kM * kKB * 2;              // 16 KiB
 constexpr int kThreads = 320;
+
+// Exact conversion of an integer-valued FP32 accumulator with |x| < 2^22: adding
+// 1.5 * 2^23 places the integer in the low mantissa bits.
+__device__ __forceinline__ int acc_to_int(float x) { return __float_as_int(__fadd_rn(x, 12582912.0f)) - 0x4B400000; }
+
+// The signed 128-bit integer (hi, lo) times 2^-q as the nearest FP64 value (ties to even),
+// built with integer instructions: normalise, keep 53 bits, round on the rest.
+__device__ __forceinline__ double i128_to_double_scaled(long long hi, unsigned long long lo, int q)
+{
+    const bool neg = hi < 0;
+    unsigned long long h = (unsigned long long)hi;
+    if (neg) {
+        lo = ~lo + 1ull;
+        h = ~h + (lo == 0ull ? 1ull : 0ull);
+    }
+    if (h == 0ull && lo == 0ull) return 0.0;
+    const int lz = h ? __clzll((long long)h) : 64 + __clzll((long long)lo);
+    if (lz >= 64) {
+        h = lo << (lz - 64);
+        lo = 0ull;
+    } else if (lz > 0) {
+        h = (h << lz) | (lo >> (64 - lz));
+        lo <<= lz;
+    }
+    unsigned long long m = h >> 11;                 // 53 bits, the leading one at bit 52
+    const bool round_bit = ((h >> 10) & 1ull) != 0ull;
+    const bool sticky = (h & 0x3FFull) != 0ull || lo != 0ull;
+    int e = 127 - lz;                               // value = m 2^(e - 52)
+    if (round_bit && (sticky || (m & 1ull))) {
+        ++m;
+        if (m >> 53) {
+            m >>= 1;
+            ++e;
+        }
+    }
+    const unsigned long long bits = ((unsigned long long)(e - q + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull) |
+                                    (neg ? 0x8000000000000000ull : 0ull);
+    return __longlong_as_double((long long)bits);
+}
 
 size_t rc_smem_bytes() { return 1024 + (size_t)kStB * kBBytes + (size_t)kStA * kABytes + 16 * 8 + 16; }
 
@@ -149,10 +189,10 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
         if (ok) {
             tc_fence_after();
             const uint32_t taddr = tmem_base + ((uint32_t)(32 * warp) << 16);
-            // Delta_j = 2^-q_j (S_T r1 - S_C r0) with r1 = 1/n1, r0 = 1/n0: when n1 = n0 both use
-            // the same reciprocal, so swapping S_T and S_C negates Delta_j exactly. Few FP64
-            // operations per column: B300's FP64 unit is narrow.
-            const double r1 = 1.0 / (double)n1, r0 = 1.0 / (double)(n - n1);
+            // n1 n0 Delta_j 2^q_j = S_T n0 - S_C n1 = S_T n - S_all n1 =: N_j, an exact 128-bit
+            // integer; when n1 = n0 the complement (S_T -> S_all - S_T) gives exactly -N_j.
+            // N_j 2^-q_j is rounded once to FP64 with integer instructions and squared into
+            // the partial sum: one FP64 operation per column (B300's FP64 unit is narrow).
             for (int c0 = 0; c0 < kN; c0 += 32) {
                 long long S[32];
 #pragma unroll
@@ -162,17 +202,21 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
                     tmem_ld32(taddr + (uint32_t)(pl * kN + c0), v);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) S[j] = S[j] * 256 + (long long)__float2int_rn(__uint_as_float(v[j]));
+                    for (int j = 0; j < 32; ++j) S[j] = S[j] * 256 + (long long)acc_to_int(__uint_as_float(v[j]));
                 }
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int col = chunk * kN + c0 + j;
                     if (col < d) {
-                        const double scale = __longlong_as_double((long long)(1023 - qexp[col]) << 52);  // 2^-q_j
-                        const double a = __dmul_rn((double)S[j], r1);
-                        const double b = __dmul_rn((double)(Qsum[col] - S[j]), r0);
-                        const double dl = __dmul_rn(__dsub_rn(a, b), scale);
-                        psum = __dadd_rn(psum, __dmul_rn(dl, dl));
+                        const long long Q = Qsum[col];
+                        const unsigned long long a_lo = (unsigned long long)S[j] * (unsigned long long)n;
+                        const long long a_hi = __mul64hi(S[j], (long long)n);
+                        const unsigned long long b_lo = (unsigned long long)Q * (unsigned long long)n1;
+                        const long long b_hi = __mul64hi(Q, (long long)n1);
+                        const unsigned long long lo = a_lo - b_lo;
+                        const long long hi = a_hi - b_hi - (a_lo < b_lo ? 1ll : 0ll);
+                        const double x = i128_to_double_scaled(hi, lo, qexp[col]);
+                        psum = __fma_rn(x, x, psum);
                     }
                 }
             }
@@ -215,7 +259,8 @@ frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint
                                                        (int)ctx->n, (int)ctx->n1, ctx->Qsum, ctx->qexp, part, ncb,
                                                        ctx->dev_counters + 12);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
-    return recheck_sum_launch(ctx, part, ncb, count, M64);
+    // the partial sums hold (N_j 2^-q_j)^2 = (n1 n0 Delta_j)^2, and M = (n1 n0 / n) sum Delta_j^2
+    return recheck_sum_launch(ctx, part, ncb, count, M64, 1.0, (double)ctx->n * (double)ctx->n1 * (double)ctx->n0);
 }
 
 }  // namespace frr

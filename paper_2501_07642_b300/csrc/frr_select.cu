@@ -137,14 +137,15 @@ k_recheck(const long long* __restrict__ Q, const long long* __restrict__ Qsum, c
     }
 }
 
-__global__ void k_recheck_sum(const double* __restrict__ part, int ncb, int64_t count, double scale,
+// M64 = scale * (sum of the column-block partial sums, in block order) / denom
+__global__ void k_recheck_sum(const double* __restrict__ part, int ncb, int64_t count, double scale, double denom,
                               double* __restrict__ M64)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= count) return;
     double s = 0.0;
     for (int b = 0; b < ncb; ++b) s = __dadd_rn(s, part[c * ncb + b]);
-    M64[c] = __dmul_rn(scale, s);
+    M64[c] = __ddiv_rn(__dmul_rn(scale, s), denom);
 }
 
 // ---------------------------------------------------------- stream filter --
@@ -349,17 +350,19 @@ __global__ void k_sel_begin(SelState* __restrict__ st, long long K)
 }
 
 // ---------------------------------------------------------------- ordering --
-// rank_c = #{c' : (M64_c', idx_c') < (M64_c, idx_c)}, one warp per entry
+// rank_c = #{c' : (M64_c', idx_c') < (M64_c, idx_c)}, one warp per entry. M64 >= 0, so
+// the order of the values is the order of their bit patterns as integers (no FP64 compares).
 __global__ void k_rank(const double* __restrict__ m, const uint64_t* __restrict__ idx, int64_t r, int* __restrict__ rank)
 {
     const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (c >= r) return;
-    const double mc = m[c];
+    const long long* mb = reinterpret_cast<const long long*>(m);
+    const long long mc = mb[c];
     const uint64_t ic = idx[c];
     int cnt = 0;
     for (int64_t k = lane; k < r; k += 32) {
-        const double mk = m[k];
+        const long long mk = mb[k];
         cnt += (mk < mc || (mk == mc && idx[k] < ic)) ? 1 : 0;
     }
     cnt = (int)__reduce_add_sync(kFull, (unsigned)cnt);
@@ -447,6 +450,79 @@ k_sel_stats(const double* __restrict__ m64, const float* __restrict__ mhat, cons
     }
 }
 
+// Retained sets up to this size are selected, placed and summarised by one CTA
+// (k_sel_finish, after the multi-CTA k_rank) with the entries in shared memory; larger
+// ones use the separate kernels above.
+constexpr int kTailMax = 2048;
+
+// One CTA, r <= kTailMax: the results of k_select_flags, k_count_sel, k_place and
+// k_sel_stats in a single launch.
+__global__ void __launch_bounds__(SNT)
+k_sel_finish(const double* __restrict__ m64, const uint64_t* __restrict__ idx, const int* __restrict__ rank,
+             const float* __restrict__ mhat, int r, long long K, int q_mode, double thr_a, CutParams cp,
+             uint64_t* __restrict__ keys_out, double* __restrict__ m_out, SelState* __restrict__ st)
+{
+    __shared__ uint64_t si[kTailMax];
+    __shared__ unsigned char ssel[kTailMax];
+    __shared__ double s_thr[32];
+    __shared__ float s_rel[32], s_band[32];
+    __shared__ int s_viol[32], s_n[32];
+    float mrel = 0.f, mband = 0.f;
+    double thr = -INFINITY;
+    int viol = 0, nsel = 0;
+    for (int c = threadIdx.x; c < r; c += SNT) {
+        const double mc = m64[c];
+        const int rk = rank[c];
+        si[c] = idx[c];
+        const int sel = q_mode ? (rk < K ? 1 : 0) : (mc <= thr_a ? 1 : 0);
+        ssel[c] = (unsigned char)sel;
+        if (q_mode) {
+            if (rk == K - 1) st->boundary[0] = mc;
+            if (rk == K) st->boundary[1] = mc;
+        }
+        nsel += sel;
+        if (sel) thr = fmax(thr, mc);
+        // diagnostics only: FP32 is enough (and cheap on B300)
+        const float a = mhat[c], m = (float)mc;
+        const float err = fabsf(a - m);
+        const float band = (float)cp.safety * ((float)cp.lin * sqrtf(fmaxf(a, 0.f)) + (float)cp.quad + (float)cp.rel * a);
+        if (m > 0.f) mrel = fmaxf(mrel, __fdividef(err, m));
+        if (band > 0.f) mband = fmaxf(mband, __fdividef(err, band));
+        viol += (err > band) ? 1 : 0;
+    }
+    __syncthreads();
+    // selected entries in ascending draw index: position = #{selected k : idx_k < idx_c}
+    for (int c = threadIdx.x; c < r; c += SNT) {
+        if (!ssel[c]) continue;
+        const uint64_t ic = si[c];
+        int pos = 0;
+        for (int k = 0; k < r; ++k) pos += (ssel[k] && si[k] < ic) ? 1 : 0;
+        keys_out[pos] = ic;
+        m_out[pos] = m64[c];
+    }
+    for (int off = 16; off >= 1; off >>= 1) {
+        mrel = fmaxf(mrel, __shfl_xor_sync(kFull, mrel, off));
+        mband = fmaxf(mband, __shfl_xor_sync(kFull, mband, off));
+        thr = fmax(thr, __shfl_xor_sync(kFull, thr, off));
+        viol += __shfl_xor_sync(kFull, viol, off);
+        nsel += __shfl_xor_sync(kFull, nsel, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { s_rel[warp] = mrel; s_band[warp] = mband; s_thr[warp] = thr; s_viol[warp] = viol; s_n[warp] = nsel; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < SNT / 32; ++w) {
+            mrel = fmaxf(mrel, s_rel[w]); mband = fmaxf(mband, s_band[w]); thr = fmax(thr, s_thr[w]);
+            viol += s_viol[w]; nsel += s_n[w];
+        }
+        st->nsel = nsel;
+        st->max_rel = mrel;
+        st->max_over_band = mband;
+        st->thr = thr;
+        st->violations = viol;
+    }
+}
+
 template <int KB>
 frr_status launch_bits_kb(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t count,
                           const uint64_t* draws, uint32_t* rows)
@@ -509,10 +585,10 @@ frr_status unpack_launch(frr_ctx* ctx, const uint32_t* rows, uint64_t count, uin
     return FRR_OK;
 }
 
-frr_status recheck_sum_launch(frr_ctx* ctx, const double* part, int ncb, int64_t count, double* M64)
+frr_status recheck_sum_launch(frr_ctx* ctx, const double* part, int ncb, int64_t count, double* M64, double scale,
+                              double denom)
 {
-    const double scale = ((double)ctx->n1 * (double)ctx->n0) / (double)ctx->n;
-    k_recheck_sum<<<ceil_div(count, 256), 256, 0, ctx->stream>>>(part, ncb, count, scale, M64);
+    k_recheck_sum<<<ceil_div(count, 256), 256, 0, ctx->stream>>>(part, ncb, count, scale, denom, M64);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     return FRR_OK;
 }
@@ -730,11 +806,16 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(sel->boundary, nanv, sizeof(nanv), cudaMemcpyHostToDevice, ctx->stream));
         FRR_TRY(recheck_launch(ctx, st.seed, st.exact, ctx->ret_idx[cur], r, m64));
         k_rank<<<ceil_div(r * 32, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], r, rank);
-        k_select_flags<<<ceil_div(r, 256), 256, 0, ctx->stream>>>(rank, m64, r, st.K, st.q_mode ? 1 : 0, st.threshold,
-                                                                  flags, sel->boundary);
-        k_count_sel<<<1, SNT, 0, ctx->stream>>>(flags, r, &sel->nsel);
-        k_place<<<ceil_div(r * 32, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], flags, r, kout, mout);
-        k_sel_stats<<<1, SNT, 0, ctx->stream>>>(m64, ctx->ret_m[cur], flags, r, cut_params(ctx), sel);
+        if (r <= kTailMax) {
+            k_sel_finish<<<1, SNT, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], rank, ctx->ret_m[cur], (int)r, st.K,
+                                                     st.q_mode ? 1 : 0, st.threshold, cut_params(ctx), kout, mout, sel);
+        } else {
+            k_select_flags<<<ceil_div(r, 256), 256, 0, ctx->stream>>>(rank, m64, r, st.K, st.q_mode ? 1 : 0,
+                                                                      st.threshold, flags, sel->boundary);
+            k_count_sel<<<1, SNT, 0, ctx->stream>>>(flags, r, &sel->nsel);
+            k_place<<<ceil_div(r * 32, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], flags, r, kout, mout);
+            k_sel_stats<<<1, SNT, 0, ctx->stream>>>(m64, ctx->ret_m[cur], flags, r, cut_params(ctx), sel);
+        }
         FRR_CUDA_TRY(ctx, cudaGetLastError());
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_pinned, &sel->nsel, sizeof(SelTail), cudaMemcpyDeviceToHost,
                                           ctx->stream));
@@ -805,7 +886,7 @@ frr_status recheck_launch_into(frr_ctx* ctx, uint64_t seed, const uint64_t* draw
     }
     FRR_TRY(s);
     const double scale = ((double)ctx->n1 * (double)ctx->n0) / (double)ctx->n;
-    k_recheck_sum<<<ceil_div(count, 256), 256, 0, ctx->stream>>>(part, ncb, count, scale, M64);
+    k_recheck_sum<<<ceil_div(count, 256), 256, 0, ctx->stream>>>(part, ncb, count, scale, 1.0, M64);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     return FRR_OK;
 }
