@@ -88,6 +88,8 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
     uint64_t* mma_done = acc_full + 1;
     uint32_t* sTmem = reinterpret_cast<uint32_t*>(mma_done + 1);
     volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
+    __shared__ long long sQsum[kN];
+    __shared__ int sQexp[kN];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t tile = blockIdx.x;
@@ -159,11 +161,15 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
         const int64_t cand = tile * kM + r;
         const uint32_t* rw = rows + (cand < C ? cand : 0) * (int64_t)W;
         bool ok = true;
+        // the row words of the next K block are loaded while this one is expanded
+        uint2 nxt = make_uint2(0u, 0u);
+        if (cand < C && nkb > 0) nxt = *reinterpret_cast<const uint2*>(rw);
         for (int kb = 0; kb < nkb && ok; ++kb) {
             const int s = kb % kStA;
+            const uint32_t w2[2] = {nxt.x, nxt.y};
+            if (cand < C && kb + 1 < nkb) nxt = *reinterpret_cast<const uint2*>(rw + 2 * (kb + 1));
             if (!(ok = wait_bar(&a_empty[s], ((kb / kStA) & 1u) ^ 1u, sAbort, err, 14))) break;
             unsigned char* dst = sA + s * kABytes + (r >> 3) * 1024 + (r & 7) * 128;
-            const uint32_t w2[2] = {cand < C ? rw[2 * kb] : 0u, cand < C ? rw[2 * kb + 1] : 0u};
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const uint32_t x = (w2[q >> 2] >> (8 * (q & 3))) & 0xFFu;
@@ -184,6 +190,13 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
         // epilogue: lane = candidate row 32 * warp + lane
         const int row = 32 * warp + lane;
         const int64_t cand = tile * kM + row;
+        // the chunk's column sums and scales, staged while the MMAs run
+        for (int t = row; t < kN; t += 128) {
+            const int col = chunk * kN + t;
+            sQsum[t] = col < d ? Qsum[col] : 0ll;
+            sQexp[t] = col < d ? qexp[col] : 0;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
         bool ok = wait_bar(acc_full, 0u, sAbort, err, 15);
         double psum = 0.0;
         if (ok) {
@@ -208,14 +221,14 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
                 for (int j = 0; j < 32; ++j) {
                     const int col = chunk * kN + c0 + j;
                     if (col < d) {
-                        const long long Q = Qsum[col];
+                        const long long Q = sQsum[c0 + j];
                         const unsigned long long a_lo = (unsigned long long)S[j] * (unsigned long long)n;
                         const long long a_hi = __mul64hi(S[j], (long long)n);
                         const unsigned long long b_lo = (unsigned long long)Q * (unsigned long long)n1;
                         const long long b_hi = __mul64hi(Q, (long long)n1);
                         const unsigned long long lo = a_lo - b_lo;
                         const long long hi = a_hi - b_hi - (a_lo < b_lo ? 1ll : 0ll);
-                        const double x = i128_to_double_scaled(hi, lo, qexp[col]);
+                        const double x = i128_to_double_scaled(hi, lo, sQexp[c0 + j]);
                         psum = __fma_rn(x, x, psum);
                     }
                 }

@@ -369,16 +369,28 @@ __global__ void k_rank(const double* __restrict__ m, const uint64_t* __restrict_
     if (lane == 0) rank[c] = cnt;
 }
 
-// selected (sel[c] != 0) entries go to position #{selected c' : idx_c' < idx_c}, one warp per entry
-__global__ void k_place(const double* __restrict__ m, const uint64_t* __restrict__ idx, const int* __restrict__ sel,
-                        int64_t r, uint64_t* __restrict__ keys_out, double* __restrict__ m_out)
+// Selection of entry c from its rank (q mode: rank < K) or its M64 (threshold mode:
+// M64 <= a); thr_bits is the bit pattern of a >= 0 (M64 >= 0 orders like its bits) or -1.
+__device__ __forceinline__ bool entry_selected(int q_mode, int rank, long long K, long long mbits, long long thr_bits)
+{
+    return q_mode ? (rank < K) : (mbits <= thr_bits);
+}
+
+// Selected entries go to position #{selected c' : idx_c' < idx_c}, one warp per entry
+// (the selection is re-derived from the ranks, so no flag array is needed).
+__global__ void k_place_sel(const double* __restrict__ m, const uint64_t* __restrict__ idx, const int* __restrict__ rank,
+                            int64_t r, long long K, int q_mode, long long thr_bits, uint64_t* __restrict__ keys_out,
+                            double* __restrict__ m_out)
 {
     const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (c >= r || !sel[c]) return;
+    if (c >= r) return;
+    const long long* mb = reinterpret_cast<const long long*>(m);
+    if (!entry_selected(q_mode, rank[c], K, mb[c], thr_bits)) return;
     const uint64_t ic = idx[c];
     int cnt = 0;
-    for (int64_t k = lane; k < r; k += 32) cnt += (sel[k] && idx[k] < ic) ? 1 : 0;
+    for (int64_t k = lane; k < r; k += 32)
+        cnt += (entry_selected(q_mode, rank[k], K, mb[k], thr_bits) && idx[k] < ic) ? 1 : 0;
     cnt = (int)__reduce_add_sync(kFull, (unsigned)cnt);
     if (lane == 0) {
         keys_out[cnt] = ic;
@@ -386,124 +398,44 @@ __global__ void k_place(const double* __restrict__ m, const uint64_t* __restrict
     }
 }
 
-__global__ void k_select_flags(const int* __restrict__ rank, const double* __restrict__ m, int64_t r, int64_t K,
-                               int q_mode, double thr, int* __restrict__ sel, double* __restrict__ boundary)
-{
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= r) return;
-    sel[c] = q_mode ? (rank[c] < K ? 1 : 0) : (m[c] <= thr ? 1 : 0);
-    if (q_mode) {
-        if (rank[c] == K - 1) boundary[0] = m[c];
-        if (rank[c] == K) boundary[1] = m[c];
-    }
-}
-
-__global__ void k_count_sel(const int* __restrict__ sel, int64_t r, long long* __restrict__ out)
-{
-    __shared__ int ws[33];
-    long long total = 0;
-    for (int64_t base = 0; base < r; base += SNT) {
-        const int64_t e = base + threadIdx.x;
-        int t;
-        block_scan_excl(e < r ? sel[e] : 0, ws, &t);
-        total += t;
-    }
-    if (threadIdx.x == 0) *out = total;
-}
-
-// band statistics of the re-checked draws and the largest accepted M64 (one CTA)
+// One CTA: accepted count, the M64 of ranks K-1 and K, the largest accepted M64 and the
+// band statistics of the re-checked draws (the SelTail fields).
 __global__ void __launch_bounds__(SNT)
-k_sel_stats(const double* __restrict__ m64, const float* __restrict__ mhat, const int* __restrict__ sel, int64_t r,
-            CutParams cp, SelState* __restrict__ st)
+k_sel_summary(const double* __restrict__ m64, const int* __restrict__ rank, const float* __restrict__ mhat, int64_t r,
+              long long K, int q_mode, long long thr_bits, CutParams cp, SelState* __restrict__ st)
 {
-    __shared__ double s_rel[32], s_band[32], s_thr[32];
-    __shared__ int s_viol[32];
-    double mrel = 0.0, mband = 0.0, thr = -INFINITY;
-    int viol = 0;
-    for (int64_t c = threadIdx.x; c < r; c += SNT) {
-        // diagnostics only: FP32 is enough (and cheap on B300)
-        const float a = mhat[c], m = (float)m64[c];
-        const float err = fabsf(a - m);
-        const float band = (float)cp.safety * ((float)cp.lin * sqrtf(fmaxf(a, 0.f)) + (float)cp.quad + (float)cp.rel * a);
-        if (m > 0.f) mrel = fmax(mrel, (double)__fdividef(err, m));
-        if (band > 0.f) mband = fmax(mband, (double)__fdividef(err, band));
-        viol += (err > band) ? 1 : 0;
-        if (sel[c]) thr = fmax(thr, m64[c]);
-    }
-    for (int off = 16; off >= 1; off >>= 1) {
-        mrel = fmax(mrel, __shfl_xor_sync(kFull, mrel, off));
-        mband = fmax(mband, __shfl_xor_sync(kFull, mband, off));
-        thr = fmax(thr, __shfl_xor_sync(kFull, thr, off));
-        viol += __shfl_xor_sync(kFull, viol, off);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) { s_rel[warp] = mrel; s_band[warp] = mband; s_thr[warp] = thr; s_viol[warp] = viol; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < SNT / 32; ++w) {
-            mrel = fmax(mrel, s_rel[w]); mband = fmax(mband, s_band[w]); thr = fmax(thr, s_thr[w]); viol += s_viol[w];
-        }
-        st->max_rel = mrel;
-        st->max_over_band = mband;
-        st->thr = thr;
-        st->violations = viol;
-    }
-}
-
-// Retained sets up to this size are selected, placed and summarised by one CTA
-// (k_sel_finish, after the multi-CTA k_rank) with the entries in shared memory; larger
-// ones use the separate kernels above.
-constexpr int kTailMax = 2048;
-
-// One CTA, r <= kTailMax: the results of k_select_flags, k_count_sel, k_place and
-// k_sel_stats in a single launch.
-__global__ void __launch_bounds__(SNT)
-k_sel_finish(const double* __restrict__ m64, const uint64_t* __restrict__ idx, const int* __restrict__ rank,
-             const float* __restrict__ mhat, int r, long long K, int q_mode, double thr_a, CutParams cp,
-             uint64_t* __restrict__ keys_out, double* __restrict__ m_out, SelState* __restrict__ st)
-{
-    __shared__ uint64_t si[kTailMax];
-    __shared__ unsigned char ssel[kTailMax];
-    __shared__ double s_thr[32];
+    __shared__ long long s_thr[32];
     __shared__ float s_rel[32], s_band[32];
     __shared__ int s_viol[32], s_n[32];
+    const long long* mb = reinterpret_cast<const long long*>(m64);
     float mrel = 0.f, mband = 0.f;
-    double thr = -INFINITY;
+    long long thr = -1;
     int viol = 0, nsel = 0;
-    for (int c = threadIdx.x; c < r; c += SNT) {
-        const double mc = m64[c];
+    for (int64_t c = threadIdx.x; c < r; c += SNT) {
         const int rk = rank[c];
-        si[c] = idx[c];
-        const int sel = q_mode ? (rk < K ? 1 : 0) : (mc <= thr_a ? 1 : 0);
-        ssel[c] = (unsigned char)sel;
+        const long long bits = mb[c];
+        const bool sel = entry_selected(q_mode, rk, K, bits, thr_bits);
         if (q_mode) {
-            if (rk == K - 1) st->boundary[0] = mc;
-            if (rk == K) st->boundary[1] = mc;
+            if (rk == K - 1) st->boundary[0] = m64[c];
+            if (rk == K) st->boundary[1] = m64[c];
         }
-        nsel += sel;
-        if (sel) thr = fmax(thr, mc);
+        if (sel) {
+            ++nsel;
+            thr = bits > thr ? bits : thr;
+        }
         // diagnostics only: FP32 is enough (and cheap on B300)
-        const float a = mhat[c], m = (float)mc;
-        const float err = fabsf(a - m);
+        const float a = mhat[c], mf = (float)m64[c];
+        const float err = fabsf(a - mf);
         const float band = (float)cp.safety * ((float)cp.lin * sqrtf(fmaxf(a, 0.f)) + (float)cp.quad + (float)cp.rel * a);
-        if (m > 0.f) mrel = fmaxf(mrel, __fdividef(err, m));
+        if (mf > 0.f) mrel = fmaxf(mrel, __fdividef(err, mf));
         if (band > 0.f) mband = fmaxf(mband, __fdividef(err, band));
         viol += (err > band) ? 1 : 0;
-    }
-    __syncthreads();
-    // selected entries in ascending draw index: position = #{selected k : idx_k < idx_c}
-    for (int c = threadIdx.x; c < r; c += SNT) {
-        if (!ssel[c]) continue;
-        const uint64_t ic = si[c];
-        int pos = 0;
-        for (int k = 0; k < r; ++k) pos += (ssel[k] && si[k] < ic) ? 1 : 0;
-        keys_out[pos] = ic;
-        m_out[pos] = m64[c];
     }
     for (int off = 16; off >= 1; off >>= 1) {
         mrel = fmaxf(mrel, __shfl_xor_sync(kFull, mrel, off));
         mband = fmaxf(mband, __shfl_xor_sync(kFull, mband, off));
-        thr = fmax(thr, __shfl_xor_sync(kFull, thr, off));
+        const long long o = __shfl_xor_sync(kFull, thr, off);
+        thr = o > thr ? o : thr;
         viol += __shfl_xor_sync(kFull, viol, off);
         nsel += __shfl_xor_sync(kFull, nsel, off);
     }
@@ -512,13 +444,13 @@ k_sel_finish(const double* __restrict__ m64, const uint64_t* __restrict__ idx, c
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < SNT / 32; ++w) {
-            mrel = fmaxf(mrel, s_rel[w]); mband = fmaxf(mband, s_band[w]); thr = fmax(thr, s_thr[w]);
+            mrel = fmaxf(mrel, s_rel[w]); mband = fmaxf(mband, s_band[w]); thr = s_thr[w] > thr ? s_thr[w] : thr;
             viol += s_viol[w]; nsel += s_n[w];
         }
         st->nsel = nsel;
         st->max_rel = mrel;
         st->max_over_band = mband;
-        st->thr = thr;
+        st->thr = thr >= 0 ? __longlong_as_double(thr) : -INFINITY;
         st->violations = viol;
     }
 }
@@ -790,32 +722,28 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
     SelState* sel = static_cast<SelState*>(ctx->sel);
     FRR_TRY(ensure_host_pinned(ctx, 256));
     cudaEventRecord(ctx->ev[3], ctx->stream);
-    // scratch: M64 (r), M64 out (r), keys out (r), rank (r), sel (r)
-    const size_t need = (size_t)r * (3 * sizeof(double) + 2 * sizeof(int)) + 64;
+    // scratch: M64 (r), M64 out (r), keys out (r), rank (r)
+    const size_t need = (size_t)r * (3 * sizeof(double) + sizeof(int)) + 64;
     FRR_TRY(ensure_device(ctx, &ctx->misc, &ctx->misc_bytes, need));
     char* base = static_cast<char*>(ctx->misc);
     double* m64 = reinterpret_cast<double*>(base);
     double* mout = m64 + r;
     uint64_t* kout = reinterpret_cast<uint64_t*>(mout + r);
     int* rank = reinterpret_cast<int*>(kout + r);
-    int* flags = rank + r;
     SelTail tail{};
     tail.boundary[0] = tail.boundary[1] = NAN;
     if (r > 0) {
         const double nanv[2] = {NAN, NAN};
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(sel->boundary, nanv, sizeof(nanv), cudaMemcpyHostToDevice, ctx->stream));
         FRR_TRY(recheck_launch(ctx, st.seed, st.exact, ctx->ret_idx[cur], r, m64));
+        // threshold mode: M64 <= a compares as bit patterns (M64 >= 0); a < 0 accepts nothing
+        long long thr_bits = -1;
+        if (!st.q_mode && st.threshold >= 0.0) memcpy(&thr_bits, &st.threshold, sizeof(thr_bits));
         k_rank<<<ceil_div(r * 32, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], r, rank);
-        if (r <= kTailMax) {
-            k_sel_finish<<<1, SNT, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], rank, ctx->ret_m[cur], (int)r, st.K,
-                                                     st.q_mode ? 1 : 0, st.threshold, cut_params(ctx), kout, mout, sel);
-        } else {
-            k_select_flags<<<ceil_div(r, 256), 256, 0, ctx->stream>>>(rank, m64, r, st.K, st.q_mode ? 1 : 0,
-                                                                      st.threshold, flags, sel->boundary);
-            k_count_sel<<<1, SNT, 0, ctx->stream>>>(flags, r, &sel->nsel);
-            k_place<<<ceil_div(r * 32, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], flags, r, kout, mout);
-            k_sel_stats<<<1, SNT, 0, ctx->stream>>>(m64, ctx->ret_m[cur], flags, r, cut_params(ctx), sel);
-        }
+        k_place_sel<<<ceil_div(r * 32, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], rank, r, st.K,
+                                                                   st.q_mode ? 1 : 0, thr_bits, kout, mout);
+        k_sel_summary<<<1, SNT, 0, ctx->stream>>>(m64, rank, ctx->ret_m[cur], r, st.K, st.q_mode ? 1 : 0, thr_bits,
+                                                  cut_params(ctx), sel);
         FRR_CUDA_TRY(ctx, cudaGetLastError());
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_pinned, &sel->nsel, sizeof(SelTail), cudaMemcpyDeviceToHost,
                                           ctx->stream));
