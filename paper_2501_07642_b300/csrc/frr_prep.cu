@@ -87,34 +87,37 @@ constexpr int kP = 32;
 __global__ void __launch_bounds__(32)
 k_chol_panel(double* __restrict__ A, int d, int k0, int pw, double tol_abs, int* __restrict__ status)
 {
+    // Right-looking inside the panel: as soon as column kk is final, every later entry of
+    // the row subtracts its kk-th term. Each entry still receives its subtractions in
+    // ascending kk (the same operations as the column-by-column definition), but the long
+    // dependent chains overlap: B300's FP64 latency (about 64 cycles an add, several
+    // hundred a division) otherwise dominates.
     __shared__ double Lb[kP][kP + 1];  // L_{k0+jj, k0+kk}, kk <= jj
     const int tid = threadIdx.x;
-    if (tid < 32) {
+    {
         const int r = k0 + tid;
         double t[kP];
 #pragma unroll
         for (int kk = 0; kk < kP; ++kk) t[kk] = (tid < pw && kk <= tid) ? A[(size_t)r * d + k0 + kk] : 0.0;
+        // t[tid] is the pivot candidate of row tid (its diagonal), t[kk < tid] the row's entries
 #pragma unroll
         for (int jj = 0; jj < kP; ++jj) {
             if (jj >= pw) break;
             if (tid == jj) {
-                double sdiag = t[jj];
-#pragma unroll
-                for (int kk = 0; kk < kP; ++kk)
-                    if (kk < jj) sdiag = __dsub_rn(sdiag, __dmul_rn(t[kk], t[kk]));
-                if (!(sdiag > tol_abs)) atomicExch(status, 1);
-                t[jj] = __dsqrt_rn(sdiag > 0.0 ? sdiag : 1.0);
-#pragma unroll
-                for (int kk = 0; kk < kP; ++kk)
-                    if (kk <= jj) Lb[jj][kk] = t[kk];
+                if (!(t[jj] > tol_abs)) atomicExch(status, 1);
+                t[jj] = __dsqrt_rn(t[jj] > 0.0 ? t[jj] : 1.0);
+                Lb[jj][jj] = t[jj];
             }
             __syncwarp();
+            if (tid > jj && tid < pw) t[jj] = __ddiv_rn(t[jj], Lb[jj][jj]);
+            if (tid >= jj && tid < pw) Lb[tid][jj] = t[jj];
+            __syncwarp();
+            // row tid: subtract the jj-th term from its later entries (kk in (jj, tid]) --
+            // the diagonal entry subtracts its square
             if (tid > jj && tid < pw) {
-                double v = t[jj];
 #pragma unroll
                 for (int kk = 0; kk < kP; ++kk)
-                    if (kk < jj) v = __dsub_rn(v, __dmul_rn(t[kk], Lb[jj][kk]));
-                t[jj] = __ddiv_rn(v, Lb[jj][jj]);
+                    if (kk > jj && kk <= tid) t[kk] = __dsub_rn(t[kk], __dmul_rn(t[jj], Lb[kk][jj]));
             }
             __syncwarp();
         }
@@ -133,11 +136,10 @@ k_chol_panel(double* __restrict__ A, int d, int k0, int pw, double tol_abs, int*
 #pragma unroll
     for (int jj = 0; jj < kP; ++jj) {
         if (jj >= pw) break;
-        double v = t[jj];
+        t[jj] = __ddiv_rn(t[jj], Lb[jj][jj]);
 #pragma unroll
         for (int kk = 0; kk < kP; ++kk)
-            if (kk < jj) v = __dsub_rn(v, __dmul_rn(t[kk], Lb[jj][kk]));
-        t[jj] = __ddiv_rn(v, Lb[jj][jj]);
+            if (kk > jj && kk < pw) t[kk] = __dsub_rn(t[kk], __dmul_rn(t[jj], Lb[kk][jj]));
     }
 #pragma unroll
     for (int kk = 0; kk < kP; ++kk)
