@@ -264,7 +264,7 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
                     uint32_t* row = bits + r * RS;
                     if (off < Bx) {
                         if constexpr (MULTI) draw_bits_kb<KB>(kbx, false, sx, fx + off, nx, n1x, bx, row, lane);
-                        else warp_draw_bits<KB>(false, sx, fx + off, nx, n1x, bx, row, lane);
+                        else warp_draw_bits_rk<KB>(one.rk, fx + off, nx, n1x, row, lane);
                     } else {
                         for (int q = lane; q < W; q += 32) row[q] = 0u;
                     }
@@ -377,6 +377,7 @@ frr_status tc_describe(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, 
     x->binom = ctx->binom;
     x->Mout = Mout;
     x->seed = seed;
+    philox_round_keys(seed, x->rk);
     x->first = first;
     x->B = B;
     x->c_M = (float)ctx->c_M;

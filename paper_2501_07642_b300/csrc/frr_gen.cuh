@@ -58,6 +58,57 @@ __device__ __forceinline__ void philox4x32_10(uint32_t& x0, uint32_t& x1, uint32
     }
 }
 
+// Round keys of Philox4x32-10 for a seed: rk[2 r], rk[2 r + 1] = (lo, hi of the seed) +
+// r (0x9E3779B9, 0xBB67AE85), r < 10.
+__host__ __device__ __forceinline__ void philox_round_keys(uint64_t seed, uint32_t (&rk)[20])
+{
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = k0;
+        rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// The same rounds as philox4x32_10 with the round keys read from rk (kernel-parameter
+// space when rk points there, so that the XORs take them as constant operands).
+__device__ __forceinline__ void philox4x32_10_rk(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3,
+                                                 const uint32_t* rk)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t a_lo = x0 * 0xD2511F53u;
+        const uint32_t a_hi = __umulhi(x0, 0xD2511F53u);
+        const uint32_t b_lo = x2 * 0xCD9E8D57u;
+        const uint32_t b_hi = __umulhi(x2, 0xCD9E8D57u);
+        const uint32_t y0 = b_hi ^ x1 ^ rk[2 * round];
+        const uint32_t y2 = a_hi ^ x3 ^ rk[2 * round + 1];
+        x0 = y0;
+        x1 = b_lo;
+        x2 = y2;
+        x3 = a_lo;
+    }
+}
+
+template <int KB>
+__device__ __forceinline__ void unit_words_rk(uint32_t (&r)[4 * KB], const uint32_t* rk, uint64_t draw, int n,
+                                              int lane)
+{
+    const uint32_t d0 = (uint32_t)draw, d1 = (uint32_t)(draw >> 32);
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+        const int j = 32 * k + lane;
+        uint32_t x0 = (uint32_t)j, x1 = 0u, x2 = d0, x3 = d1;
+        if (4 * j < n) philox4x32_10_rk(x0, x1, x2, x3, rk);
+        const int u = 4 * j;
+        r[4 * k + 0] = (u + 0 < n) ? x0 : 0xffffffffu;
+        r[4 * k + 1] = (u + 1 < n) ? x1 : 0xffffffffu;
+        r[4 * k + 2] = (u + 2 < n) ? x2 : 0xffffffffu;
+        r[4 * k + 3] = (u + 3 < n) ? x3 : 0xffffffffu;
+    }
+}
+
 // The 4*KB unit words of this lane for draw `draw`; units >= n get 0xffffffff
 // (they sort after every real unit because their index is larger).
 template <int KB>
@@ -246,6 +297,16 @@ __device__ __forceinline__ void lane_exact_row(uint64_t rank, int n, int n1, con
     for (int c = 0; c < 4; ++c)
         if (c < words) row[c] = kword_of_mask(m, c);
     for (int q = 4; q < words; ++q) row[q] = 0u;
+}
+
+// A Philox draw -> its bit row, with precomputed round keys (see unit_words_rk).
+template <int KB>
+__device__ __forceinline__ void warp_draw_bits_rk(const uint32_t* rk, uint64_t draw, int n, int n1, uint32_t* row,
+                                                  int lane)
+{
+    uint32_t r[4 * KB];
+    unit_words_rk<KB>(r, rk, draw, n, lane);
+    warp_store_bits<KB>(warp_select_smallest<KB>(r, n, n1, lane), r, row);
 }
 
 // One draw -> its bit row. 4 * KB words are written.

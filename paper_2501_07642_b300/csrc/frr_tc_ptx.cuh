@@ -149,7 +149,6 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
             atomicCAS(err, 0, code);
             return false;
         }
-        __nanosleep(64);
     }
 }
 

@@ -12,6 +12,7 @@ struct TcExp {
     const uint64_t* binom;
     float* Mout;          // approximate M of draw first + i goes to Mout[i]
     uint64_t seed, first, B;
+    uint32_t rk[20];      // Philox round keys of the seed (philox_round_keys)
     float c_M;
     int n, n1, d, kb, nkb, nchunks, exact;
 };

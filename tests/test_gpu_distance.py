@@ -89,3 +89,26 @@ def test_embedding_workload_sampled():
     want2 = O.distance_pairs(X, Y, ij, squared=True)
     scale = (X[ij[:, 0]].astype(np.float64) ** 2).sum(1) + (Y[ij[:, 1]].astype(np.float64) ** 2).sum(1)
     assert (np.abs(got ** 2 - want2) / scale).max() <= _bound(d)
+
+
+def test_large_magnitudes_long_rows_and_mixed_buffers():
+    import torch
+    rng = np.random.default_rng(2048)
+    X = (rng.standard_normal((150, 2048)) * 3e3 + 1e3).astype(np.float32)
+    Y = (rng.standard_normal((70, 2048)) * 3e3).astype(np.float32)
+    Dd = torch.empty((150, 70), dtype=torch.float32, device="cuda")
+    frr.frr_fast_distance(X, Y, D_out=Dd)          # host inputs, device output
+    _check(X, Y, Dd.cpu().numpy(), False)
+    D2 = frr.frr_fast_distance(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), squared=True)  # device in, host out
+    _check(X, Y, D2, True)
+
+
+def test_duplicate_rows_give_near_zero_distances():
+    rng = np.random.default_rng(4)
+    base = rng.standard_normal((40, 300)).astype(np.float32)
+    X = np.concatenate([base, base[::-1]])
+    D2 = frr.frr_fast_distance(X, None, squared=True)
+    nrm = (X.astype(np.float64) ** 2).sum(1)
+    for i in range(40):
+        j = 79 - i                                   # the duplicate of row i
+        assert D2[i, j] >= 0.0 and D2[i, j] <= _bound(300) * 2 * nrm[i]
