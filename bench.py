@@ -126,6 +126,28 @@ def oracle_rate(Zc, n1, seed, target_s: float, first: int = 0):
     return S / dt, S, O.threads()
 
 
+def oracle_rate_1t(Zc, n1, seed, target_s: float, first: int = 0):
+    """The same oracle selection on one host thread (balance with threads=1, then the sort)."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    O.select_from_M(O.balance(Zc, n1, seed, first, 16, threads=1), first, q=1e-3)
+    per = (time.perf_counter() - t0) / 16
+    S = int(max(16, min(50_000, target_s / max(per, 1e-7))))
+    t0 = time.perf_counter()
+    O.select_from_M(O.balance(Zc, n1, seed, first + 16, S, threads=1), first + 16, q=1e-3)
+    return S / (time.perf_counter() - t0), S
+
+
+def cpu_model() -> str:
+    try:
+        for line in Path("/proc/cpuinfo").read_text().splitlines():
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -239,6 +261,8 @@ def run_frr(args):
                    "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(K * 16),
                    "includes": "frr_init (X upload, FP64 prep) + frr_select + key read-back"}
         results[prec] = {"value": ws * B * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+                         "ms_per_step_median": statistics.median(step_ms), "ms_per_step_min": min(step_ms),
+                         "ms_per_step_max": max(step_ms),
                          "ms_balance": statistics.mean(bal_ms), "ms_select": statistics.mean(sel_ms),
                          "ms_recheck": statistics.mean(rck_ms), "clocks": clk.summary(), "stats": stats, "e2e": e2e,
                          "wall_s": wall}
@@ -278,15 +302,20 @@ def run_frr(args):
     dist_line = distance_bench(peaks["bf16_tflops"]) if args.distance else None
     cpu = None
     if args.cpu_baseline:
-        rate, S, cores = oracle_rate(oracle_zc(X), n1, w.philox_seed, args.cpu_s)
+        Zc = oracle_zc(X)
+        rate, S, cores = oracle_rate(Zc, n1, w.philox_seed, args.cpu_s)
+        rate1, S1 = oracle_rate_1t(Zc, n1, w.philox_seed, args.cpu_s / 4, first=10_000_000)
         cpu = {"value": rate, "unit": "draws/s", "cores": cores, "kind": "oracle",
-               "sample": f"FP64 oracle select (M of every draw + sort) on {S} draws of the {WORKLOAD} workload"}
+               "sample": f"FP64 oracle select (M of every draw + sort) on {S} draws of the {WORKLOAD} workload",
+               "single_thread": {"value": rate1, "sample": f"{S1} draws on one thread"},
+               "cpu_model": cpu_model(), "nproc": os.cpu_count()}
     line = {"metric": METRIC, "value": r["value"], "unit": "draws/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "n1": n1, "d": d, "draws_per_step": B, "q": q, "K": K,
                        "whiten": "ridge 0.1", "path": prim, "l2": "flushed (256 MiB write) between timed steps"},
-            "paths": {p: ({k: results[p][k] for k in ("value", "ms_per_step", "ms_balance", "ms_select", "ms_recheck")}
+            "paths": {p: ({k: results[p][k] for k in ("value", "ms_per_step", "ms_per_step_median", "ms_per_step_min",
+                                                       "ms_per_step_max", "ms_balance", "ms_select", "ms_recheck")}
                           if "value" in results[p] else results[p])
                       for p in precisions},
             "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": LAUNCHES_PER_STEP * args.steps * ws,

@@ -13,7 +13,8 @@
 //               N <= 256 columns, 2 x 4 tcgen05.mma (M=128, K=16) per 64-wide K block
 //               into one of two TMEM accumulators (2 x 256 columns);
 //   warps 6-9   A producer: expand the draws' bit rows into BF16 0/1 K-major tiles
-//               (128 x 64, 128B swizzle), one draw row per thread, in registers;
+//               (128 x 64, 128B swizzle), one draw row per thread, through a 256-entry
+//               byte table in shared memory;
 //   warps 10..  generation (NG warps): Philox + warp select (frr_gen.cuh) of the
 //               next tile's 128 draws into a double-buffered bit-row buffer.
 // The assignment matrix exists only as bits and BF16 tiles in shared memory.
@@ -98,6 +99,12 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
     volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ uint4 sLut8[256];   // byte -> eight BF16 values 0.0 / 1.0 (bit i -> value i)
+    if (tid < 256) {
+        uint32_t h[8];
+        for (int i = 0; i < 8; ++i) h[i] = ((tid >> i) & 1) ? 0x3F80u : 0u;
+        sLut8[tid] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+    }
 
     if (tid == 0) {
         for (int s = 0; s < SB; ++s) { mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); }
@@ -195,7 +202,8 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
     } else if (warp >= 6 && warp < 6 + kExpWarps) {
         // ------------------------------------------------- A tile producer --
         // thread r writes row r (draw r of the tile): the 64 bits of K block kb become
-        // eight 16-byte chunks of BF16 0.0 / 1.0, chunk q stored at (q ^ (r % 8)).
+        // eight 16-byte chunks of BF16 0.0 / 1.0 (one byte-table entry each), chunk q
+        // stored at (q ^ (r % 8)).
         const int r = tid - 6 * 32;  // 0..127
         uint32_t ai = 0;
         uint32_t it = 0;
@@ -216,16 +224,7 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const uint32_t x = (w2[q >> 2] >> (8 * (q & 3))) & 0xFFu;
-                        // bit i of a nibble -> byte i (0 or 1); the four shifted copies never overlap
-                        const uint32_t ylo = ((x & 0xFu) * 0x00204081u) & 0x01010101u;
-                        const uint32_t yhi = ((x >> 4) * 0x00204081u) & 0x01010101u;
-                        // bytes -> 16-bit lanes holding 0 or 1, times the BF16 pattern of 1.0
-                        uint4 v;
-                        v.x = __byte_perm(ylo, 0u, 0x4140) * 0x3F80u;
-                        v.y = __byte_perm(ylo, 0u, 0x4342) * 0x3F80u;
-                        v.z = __byte_perm(yhi, 0u, 0x4140) * 0x3F80u;
-                        v.w = __byte_perm(yhi, 0u, 0x4342) * 0x3F80u;
-                        *reinterpret_cast<uint4*>(dst + ((q ^ (r & 7)) << 4)) = v;
+                        *reinterpret_cast<uint4*>(dst + ((q ^ (r & 7)) << 4)) = sLut8[x];
                     }
                     fence_async_smem();
                     __syncwarp();

@@ -13,7 +13,8 @@
 //
 // One CTA per (128 candidates, 64 columns): 7 accumulators of 64 columns in TMEM.
 // Warps 0-3 epilogue, warp 4 TMA (7 digit tiles per K block), warp 5 MMA, warps 6-9
-// expand the candidates' bit rows (computed beforehand) into BF16 0/1 A tiles.
+// expand the candidates' bit rows (computed beforehand) into BF16 0/1 A tiles through a
+// 256-entry byte table in shared memory.
 #include "frr_internal.cuh"
 #include "frr_gen.cuh"
 #include "frr_tc_ptx.cuh"
@@ -90,8 +91,14 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
     volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
     __shared__ long long sQsum[kN];
     __shared__ int sQexp[kN];
+    __shared__ uint4 sLut8[256];   // byte -> eight BF16 values 0.0 / 1.0 (bit i -> value i)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid < 256) {
+        uint32_t h[8];
+        for (int i = 0; i < 8; ++i) h[i] = ((tid >> i) & 1) ? 0x3F80u : 0u;
+        sLut8[tid] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+    }
     const int64_t tile = blockIdx.x;
     const int chunk = blockIdx.y;
     if (tid == 0) {
@@ -173,14 +180,7 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const uint32_t x = (w2[q >> 2] >> (8 * (q & 3))) & 0xFFu;
-                const uint32_t ylo = ((x & 0xFu) * 0x00204081u) & 0x01010101u;
-                const uint32_t yhi = ((x >> 4) * 0x00204081u) & 0x01010101u;
-                uint4 v;
-                v.x = __byte_perm(ylo, 0u, 0x4140) * 0x3F80u;
-                v.y = __byte_perm(ylo, 0u, 0x4342) * 0x3F80u;
-                v.z = __byte_perm(yhi, 0u, 0x4140) * 0x3F80u;
-                v.w = __byte_perm(yhi, 0u, 0x4342) * 0x3F80u;
-                *reinterpret_cast<uint4*>(dst + ((q ^ (r & 7)) << 4)) = v;
+                *reinterpret_cast<uint4*>(dst + ((q ^ (r & 7)) << 4)) = sLut8[x];
             }
             fence_async_smem();
             __syncwarp();
