@@ -281,6 +281,7 @@ frr_status frr_select(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_t
     FRR_TRY(check_mode(q, threshold));
     FRR_TRY(check_range(ctx, seed, first_draw, B));
     FRR_TRY(stream_begin(ctx, seed, q, threshold, B));
+    ctx->st.defer_count = true;  // one call: the recheck may read the candidate count on the device
     frr_status s = stream_chunk(ctx, first_draw, B);
     if (s != FRR_OK) { ctx->st.active = false; return s; }
     return stream_end(ctx, keys_out, M64_out, cap, K_out);

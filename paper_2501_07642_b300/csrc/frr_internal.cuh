@@ -36,7 +36,10 @@ struct StreamState {
     double q = NAN, threshold = NAN;
     uint64_t total = 0, seen = 0;
     int64_t K = 0;            // target accepted count (q mode)
-    int64_t retained = 0;     // entries in the retained (candidate) set
+    int64_t retained = 0;     // entries in the retained (candidate) set; -1: only on the device
+    int64_t retained_bound = 0;  // upper bound of the retained count when it is only on the device
+    bool defer_count = false; // the last chunk leaves the retained count on the device (no read-back)
+    bool times_pending = false;  // that chunk's event times are read after the final synchronisation
     float cut = INFINITY;     // current cut on the approximate M (keep M_hat <= cut)
 };
 
@@ -130,17 +133,18 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host);
 frr_status balance_f32_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
 frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
 frr_status balance_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
+// count_dev: when given, the count is read on the device and `count` only bounds it
 frr_status bits_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t count,
-                       const uint64_t* draws_dev, uint32_t* rows_dev);
+                       const uint64_t* draws_dev, uint32_t* rows_dev, const long long* count_dev = nullptr);
 frr_status words_select_launch(frr_ctx* ctx, const uint32_t* words_dev, uint32_t* row_dev);
 frr_status unpack_launch(frr_ctx* ctx, const uint32_t* rows_dev, uint64_t count, uint8_t* w_dev);
 frr_status recheck_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws_dev, int64_t count,
-                          double* M64_dev);
+                          double* M64_dev, const long long* count_dev = nullptr);
 frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws_dev, int64_t count,
-                             double* M64_dev);
+                             double* M64_dev, const long long* count_dev = nullptr);
 // M64 = scale * (sum over the ncb column-block partial sums of each draw) / denom
 frr_status recheck_sum_launch(frr_ctx* ctx, const double* part, int ncb, int64_t count, double* M64_dev, double scale,
-                              double denom);
+                              double denom, const long long* count_dev = nullptr);
 frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold, uint64_t total);
 frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B);
 frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out);

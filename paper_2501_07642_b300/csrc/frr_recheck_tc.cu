@@ -11,11 +11,14 @@
 // complement give -N_j when n1 = n0), rounds N_j 2^-q_j once to FP64 and adds its square
 // to the CTA's partial sum; M64 = sum / (n n1 n0).
 //
-// One CTA per (128 candidates, 64 columns): 7 accumulators of 64 columns in TMEM.
+// Work items of (128 candidates, 64 columns), 7 accumulators of 64 columns in TMEM each,
+// taken by persistent CTAs (one per SM at most).
 // Warps 0-3 epilogue, warp 4 TMA (7 digit tiles per K block), warp 5 MMA, warps 6-9
 // expand the candidates' bit rows (computed beforehand) into BF16 0/1 A tiles through a
 // 256-entry byte table in shared memory.
 #include "frr_internal.cuh"
+
+#include <algorithm>
 #include "frr_gen.cuh"
 #include "frr_tc_ptx.cuh"
 
@@ -71,10 +74,14 @@ __device__ __forceinline__ double i128_to_double_scaled(long long hi, unsigned l
 
 size_t rc_smem_bytes() { return 1024 + (size_t)kStB * kBBytes + (size_t)kStA * kABytes + 16 * 8 + 16; }
 
+// Persistent: CTA b takes work items b, b + gridDim.x, ... of (column chunk, candidate
+// tile), item i -> chunk i / T, tile i % T with T = ceil(C / 128) tiles (consecutive items
+// share a chunk's digit tiles in L2). C is read from C_dev when given (a count the host
+// has not read back), else C_host.
 __global__ void __launch_bounds__(kThreads, 1)
-k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restrict__ rows, int W, int64_t C, int nkb,
-             int d, int n, int n1, const long long* __restrict__ Qsum, const int* __restrict__ qexp,
-             double* __restrict__ part, int ncb, int* err)
+k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restrict__ rows, int W, int64_t C_host,
+             const long long* __restrict__ C_dev, int nkb, int d, int n, int n1, const long long* __restrict__ Qsum,
+             const int* __restrict__ qexp, double* __restrict__ part, int ncb, int* err)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -86,7 +93,8 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
     uint64_t* a_full = b_empty + kStB;
     uint64_t* a_empty = a_full + kStA;
     uint64_t* acc_full = a_empty + kStA;
-    uint64_t* mma_done = acc_full + 1;
+    uint64_t* acc_empty = acc_full + 1;
+    uint64_t* mma_done = acc_empty + 1;
     uint32_t* sTmem = reinterpret_cast<uint32_t*>(mma_done + 1);
     volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
     __shared__ long long sQsum[kN];
@@ -99,12 +107,14 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
         for (int i = 0; i < 8; ++i) h[i] = ((tid >> i) & 1) ? 0x3F80u : 0u;
         sLut8[tid] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
     }
-    const int64_t tile = blockIdx.x;
-    const int chunk = blockIdx.y;
+    const int64_t C = C_dev ? (int64_t)*C_dev : C_host;
+    const int64_t T = (C + kM - 1) / kM;
+    const int64_t items = T * ncb;
     if (tid == 0) {
         for (int s = 0; s < kStB; ++s) { mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); }
         for (int s = 0; s < kStA; ++s) { mbar_init(&a_full[s], 4); mbar_init(&a_empty[s], 1); }
         mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 4);
         mbar_init(mma_done, 1);
         *sAbort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -120,18 +130,23 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
 
     if (warp == 4) {
         if (lane == 0) {
-            int kb = 0;
+            uint32_t bi = 0;
             bool ok = true;
-            for (; kb < nkb && ok; ++kb) {
-                const int s = kb % kStB;
-                if (!(ok = wait_bar(&b_empty[s], ((kb / kStB) & 1u) ^ 1u, sAbort, err, 11))) break;
-                mbar_arrive_expect_tx(&b_full[s], kBBytes);
-                for (int pl = 0; pl < kPlanes; ++pl)
-                    tma_load_2d(sB + s * kBBytes + pl * kPlaneBytes, &map_q, &b_full[s], kb * kKB, pl * d + chunk * kN);
+            for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
+                const int chunk = (int)(item / T);
+                for (int kb = 0; kb < nkb; ++kb, ++bi) {
+                    const int s = bi % kStB;
+                    if (!(ok = wait_bar(&b_empty[s], ((bi / kStB) & 1u) ^ 1u, sAbort, err, 11))) break;
+                    mbar_arrive_expect_tx(&b_full[s], kBBytes);
+                    for (int pl = 0; pl < kPlanes; ++pl)
+                        tma_load_2d(sB + s * kBBytes + pl * kPlaneBytes, &map_q, &b_full[s], kb * kKB,
+                                    pl * d + chunk * kN);
+                }
             }
             if (!ok) {
-                const int from = kb > kStB ? kb - kStB : 0;
-                for (int i = from; i < kb; ++i) {
+                // drain the copies this thread may still have in flight
+                const uint32_t from = bi > (uint32_t)kStB ? bi - kStB : 0u;
+                for (uint32_t i = from; i < bi; ++i) {
                     const unsigned long long t0 = clock64();
                     while (!mbar_try_wait(&b_full[i % kStB], (i / kStB) & 1u) && clock64() - t0 < kWaitCycles) {}
                 }
@@ -140,67 +155,80 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
     } else if (warp == 5) {
         if (lane == 0) {
             bool ok = true;
+            uint32_t ai = 0, bi = 0, it = 0;
             const uint32_t idesc = idesc_bf16(kM, kN);
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-                const int sa = kb % kStA, sb = kb % kStB;
-                if (!(ok = wait_bar(&a_full[sa], (kb / kStA) & 1u, sAbort, err, 12))) break;
-                if (!(ok = wait_bar(&b_full[sb], (kb / kStB) & 1u, sAbort, err, 13))) break;
+            for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
+                if (!(ok = wait_bar(acc_empty, (it & 1u) ^ 1u, sAbort, err, 16))) break;
                 tc_fence_after();
-                const uint64_t adesc = sdesc_sw128(smem_u32(sA + sa * kABytes));
+                for (int kb = 0; kb < nkb && ok; ++kb, ++ai, ++bi) {
+                    const int sa = ai % kStA, sb = bi % kStB;
+                    if (!(ok = wait_bar(&a_full[sa], (ai / kStA) & 1u, sAbort, err, 12))) break;
+                    if (!(ok = wait_bar(&b_full[sb], (bi / kStB) & 1u, sAbort, err, 13))) break;
+                    tc_fence_after();
+                    const uint64_t adesc = sdesc_sw128(smem_u32(sA + sa * kABytes));
 #pragma unroll
-                for (int pl = 0; pl < kPlanes; ++pl) {
-                    const uint64_t bdesc = sdesc_sw128(smem_u32(sB + sb * kBBytes + pl * kPlaneBytes));
+                    for (int pl = 0; pl < kPlanes; ++pl) {
+                        const uint64_t bdesc = sdesc_sw128(smem_u32(sB + sb * kBBytes + pl * kPlaneBytes));
 #pragma unroll
-                    for (int k = 0; k < kKB / 16; ++k)
-                        umma_bf16(tmem_base + (uint32_t)(pl * kN), adesc + 2u * k, bdesc + 2u * k, idesc,
-                                  (kb | k) != 0 ? 1u : 0u);
+                        for (int k = 0; k < kKB / 16; ++k)
+                            umma_bf16(tmem_base + (uint32_t)(pl * kN), adesc + 2u * k, bdesc + 2u * k, idesc,
+                                      (kb | k) != 0 ? 1u : 0u);
+                    }
+                    umma_commit(&b_empty[sb]);
+                    umma_commit(&a_empty[sa]);
                 }
-                umma_commit(&b_empty[sb]);
-                umma_commit(&a_empty[sa]);
+                if (ok) umma_commit(acc_full);
             }
-            if (ok) umma_commit(acc_full);
+            // every MMA this thread issued has finished before TMEM is released
             umma_commit(mma_done);
             const unsigned long long t0 = clock64();
             while (!mbar_try_wait(mma_done, 0) && clock64() - t0 < kWaitCycles) {}
         }
     } else if (warp >= 6) {
         const int r = tid - 6 * 32;  // row (candidate) of the A tile
-        const int64_t cand = tile * kM + r;
-        const uint32_t* rw = rows + (cand < C ? cand : 0) * (int64_t)W;
+        uint32_t ai = 0;
         bool ok = true;
-        // the row words of the next K block are loaded while this one is expanded
-        uint2 nxt = make_uint2(0u, 0u);
-        if (cand < C && nkb > 0) nxt = *reinterpret_cast<const uint2*>(rw);
-        for (int kb = 0; kb < nkb && ok; ++kb) {
-            const int s = kb % kStA;
-            const uint32_t w2[2] = {nxt.x, nxt.y};
-            if (cand < C && kb + 1 < nkb) nxt = *reinterpret_cast<const uint2*>(rw + 2 * (kb + 1));
-            if (!(ok = wait_bar(&a_empty[s], ((kb / kStA) & 1u) ^ 1u, sAbort, err, 14))) break;
-            unsigned char* dst = sA + s * kABytes + (r >> 3) * 1024 + (r & 7) * 128;
+        for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
+            const int64_t cand = (item % T) * kM + r;
+            const uint32_t* rw = rows + (cand < C ? cand : 0) * (int64_t)W;
+            // the row words of the next K block are loaded while this one is expanded
+            uint2 nxt = make_uint2(0u, 0u);
+            if (cand < C && nkb > 0) nxt = *reinterpret_cast<const uint2*>(rw);
+            for (int kb = 0; kb < nkb && ok; ++kb, ++ai) {
+                const int s = ai % kStA;
+                const uint32_t w2[2] = {nxt.x, nxt.y};
+                if (cand < C && kb + 1 < nkb) nxt = *reinterpret_cast<const uint2*>(rw + 2 * (kb + 1));
+                if (!(ok = wait_bar(&a_empty[s], ((ai / kStA) & 1u) ^ 1u, sAbort, err, 14))) break;
+                unsigned char* dst = sA + s * kABytes + (r >> 3) * 1024 + (r & 7) * 128;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const uint32_t x = (w2[q >> 2] >> (8 * (q & 3))) & 0xFFu;
-                *reinterpret_cast<uint4*>(dst + ((q ^ (r & 7)) << 4)) = sLut8[x];
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t x = (w2[q >> 2] >> (8 * (q & 3))) & 0xFFu;
+                    *reinterpret_cast<uint4*>(dst + ((q ^ (r & 7)) << 4)) = sLut8[x];
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&a_full[s]);
             }
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&a_full[s]);
         }
     } else {
         // epilogue: lane = candidate row 32 * warp + lane
         const int row = 32 * warp + lane;
-        const int64_t cand = tile * kM + row;
-        // the chunk's column sums and scales, staged while the MMAs run
-        for (int t = row; t < kN; t += 128) {
-            const int col = chunk * kN + t;
-            sQsum[t] = col < d ? Qsum[col] : 0ll;
-            sQexp[t] = col < d ? qexp[col] : 0;
-        }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        bool ok = wait_bar(acc_full, 0u, sAbort, err, 15);
-        double psum = 0.0;
-        if (ok) {
+        uint32_t it = 0;
+        bool ok = true;
+        for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
+            const int chunk = (int)(item / T);
+            const int64_t cand = (item % T) * kM + row;
+            // the chunk's column sums and scales (the previous item's readers are done first)
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            for (int t = row; t < kN; t += 128) {
+                const int col = chunk * kN + t;
+                sQsum[t] = col < d ? Qsum[col] : 0ll;
+                sQexp[t] = col < d ? qexp[col] : 0;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (!(ok = wait_bar(acc_full, it & 1u, sAbort, err, 15))) break;
             tc_fence_after();
+            double psum = 0.0;
             const uint32_t taddr = tmem_base + ((uint32_t)(32 * warp) << 16);
             // n1 n0 Delta_j 2^q_j = S_T n0 - S_C n1 = S_T n - S_all n1 =: N_j, an exact 128-bit
             // integer; when n1 = n0 the complement (S_T -> S_all - S_T) gives exactly -N_j.
@@ -233,8 +261,11 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
+            if (cand < C) part[cand * ncb + chunk] = psum;
         }
-        if (ok && cand < C) part[cand * ncb + chunk] = psum;
     }
 
     tc_fence_before();
@@ -248,8 +279,9 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
 }  // namespace
 
 // Exact-sum recheck of `count` draws (device list) on the tensor cores; M64 on the device.
+// With count_dev the number of draws is read on the device and `count` only bounds it.
 frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws, int64_t count,
-                             double* M64)
+                             double* M64, const long long* count_dev)
 {
     if (count <= 0) return FRR_OK;
     const int W = 4 * ctx->kb;
@@ -259,7 +291,7 @@ frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint
     FRR_TRY(ensure_device(ctx, &ctx->misc2, &ctx->misc2_bytes, rows_bytes + part_bytes + 256));
     uint32_t* rows = static_cast<uint32_t*>(ctx->misc2);
     double* part = reinterpret_cast<double*>(static_cast<char*>(ctx->misc2) + ((rows_bytes + 255) & ~size_t(255)));
-    FRR_TRY(bits_launch(ctx, seed, exact, 0, (uint64_t)count, draws, rows));
+    FRR_TRY(bits_launch(ctx, seed, exact, 0, (uint64_t)count, draws, rows, count_dev));
     if (!ctx->qmap_ready) {
         if (!make_map_bf16(&ctx->qmap, ctx->Zq, (uint64_t)ctx->kpad, (uint64_t)kPlanes * ctx->d, kKB, kN))
             return FRR_E_CUDA;
@@ -267,13 +299,15 @@ frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint
     }
     const size_t smem = rc_smem_bytes();
     FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_recheck_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)((count + kM - 1) / kM), (unsigned)ncb);
-    k_recheck_tc<<<grid, kThreads, smem, ctx->stream>>>(ctx->qmap, rows, W, count, ctx->kused / kKB, (int)ctx->d,
-                                                       (int)ctx->n, (int)ctx->n1, ctx->Qsum, ctx->qexp, part, ncb,
-                                                       ctx->dev_counters + 12);
+    const int64_t items = (int64_t)((count + kM - 1) / kM) * ncb;
+    const unsigned grid = (unsigned)std::min<int64_t>(items, ctx->num_sms);
+    k_recheck_tc<<<grid, kThreads, smem, ctx->stream>>>(ctx->qmap, rows, W, count, count_dev, ctx->kused / kKB,
+                                                       (int)ctx->d, (int)ctx->n, (int)ctx->n1, ctx->Qsum, ctx->qexp,
+                                                       part, ncb, ctx->dev_counters + 12);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     // the partial sums hold (N_j 2^-q_j)^2 = (n1 n0 Delta_j)^2, and M = (n1 n0 / n) sum Delta_j^2
-    return recheck_sum_launch(ctx, part, ncb, count, M64, 1.0, (double)ctx->n * (double)ctx->n1 * (double)ctx->n0);
+    return recheck_sum_launch(ctx, part, ncb, count, M64, 1.0, (double)ctx->n * (double)ctx->n1 * (double)ctx->n0,
+                              count_dev);
 }
 
 }  // namespace frr

@@ -26,15 +26,20 @@ namespace frr {
 namespace {
 
 // ------------------------------------------------------------------ replay --
+// One warp per draw, grid-stride; the count is read from count_dev when given (a count
+// the host has not read back), else it is `count`.
 template <int KB>
 __global__ void k_bits(uint64_t seed, int exact, const uint64_t* __restrict__ binom, int n, int n1, uint64_t first,
-                       uint64_t count, const uint64_t* __restrict__ draws, uint32_t* __restrict__ rows)
+                       uint64_t count, const long long* __restrict__ count_dev, const uint64_t* __restrict__ draws,
+                       uint32_t* __restrict__ rows)
 {
-    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t cnt = count_dev ? (uint64_t)*count_dev : count;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (w >= count) return;
-    const uint64_t draw = draws ? draws[w] : first + w;
-    warp_draw_bits<KB>(exact != 0, seed, draw, n, n1, binom, rows + w * (4 * KB), lane);
+    for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < cnt; w += nw) {
+        const uint64_t draw = draws ? draws[w] : first + w;
+        warp_draw_bits<KB>(exact != 0, seed, draw, n, n1, binom, rows + w * (4 * KB), lane);
+    }
 }
 
 // Selection on caller-supplied unit words (word of unit i at words[i]); one warp.
@@ -138,14 +143,16 @@ k_recheck(const long long* __restrict__ Q, const long long* __restrict__ Qsum, c
 }
 
 // M64 = scale * (sum of the column-block partial sums, in block order) / denom
-__global__ void k_recheck_sum(const double* __restrict__ part, int ncb, int64_t count, double scale, double denom,
+__global__ void k_recheck_sum(const double* __restrict__ part, int ncb, int64_t count,
+                              const long long* __restrict__ count_dev, double scale, double denom,
                               double* __restrict__ M64)
 {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= count) return;
-    double s = 0.0;
-    for (int b = 0; b < ncb; ++b) s = __dadd_rn(s, part[c * ncb + b]);
-    M64[c] = __ddiv_rn(__dmul_rn(scale, s), denom);
+    const int64_t cnt = count_dev ? *count_dev : count;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cnt; c += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < ncb; ++b) s = __dadd_rn(s, part[c * ncb + b]);
+        M64[c] = __ddiv_rn(__dmul_rn(scale, s), denom);
+    }
 }
 
 // ---------------------------------------------------------- stream filter --
@@ -231,6 +238,7 @@ struct SelState {
 };
 
 static_assert(offsetof(SelState, violations) - offsetof(SelState, nsel) == 48, "SelState tail layout");
+static_assert(offsetof(SelState, nsel) - offsetof(SelState, kept) == sizeof(long long), "kept precedes the tail");
 
 // the part of SelState read back by the host at the end of a stream
 struct SelTail {
@@ -352,21 +360,24 @@ __global__ void k_sel_begin(SelState* __restrict__ st, long long K)
 // ---------------------------------------------------------------- ordering --
 // rank_c = #{c' : (M64_c', idx_c') < (M64_c, idx_c)}, one warp per entry. M64 >= 0, so
 // the order of the values is the order of their bit patterns as integers (no FP64 compares).
-__global__ void k_rank(const double* __restrict__ m, const uint64_t* __restrict__ idx, int64_t r, int* __restrict__ rank)
+__global__ void k_rank(const double* __restrict__ m, const uint64_t* __restrict__ idx, int64_t r_host,
+                       const long long* __restrict__ r_dev, int* __restrict__ rank)
 {
-    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t r = r_dev ? *r_dev : r_host;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (c >= r) return;
     const long long* mb = reinterpret_cast<const long long*>(m);
-    const long long mc = mb[c];
-    const uint64_t ic = idx[c];
-    int cnt = 0;
-    for (int64_t k = lane; k < r; k += 32) {
-        const long long mk = mb[k];
-        cnt += (mk < mc || (mk == mc && idx[k] < ic)) ? 1 : 0;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < r; c += nw) {
+        const long long mc = mb[c];
+        const uint64_t ic = idx[c];
+        int cnt = 0;
+        for (int64_t k = lane; k < r; k += 32) {
+            const long long mk = mb[k];
+            cnt += (mk < mc || (mk == mc && idx[k] < ic)) ? 1 : 0;
+        }
+        cnt = (int)__reduce_add_sync(kFull, (unsigned)cnt);
+        if (lane == 0) rank[c] = cnt;
     }
-    cnt = (int)__reduce_add_sync(kFull, (unsigned)cnt);
-    if (lane == 0) rank[c] = cnt;
 }
 
 // Selection of entry c from its rank (q mode: rank < K) or its M64 (threshold mode:
@@ -379,31 +390,35 @@ __device__ __forceinline__ bool entry_selected(int q_mode, int rank, long long K
 // Selected entries go to position #{selected c' : idx_c' < idx_c}, one warp per entry
 // (the selection is re-derived from the ranks, so no flag array is needed).
 __global__ void k_place_sel(const double* __restrict__ m, const uint64_t* __restrict__ idx, const int* __restrict__ rank,
-                            int64_t r, long long K, int q_mode, long long thr_bits, uint64_t* __restrict__ keys_out,
-                            double* __restrict__ m_out)
+                            int64_t r_host, const long long* __restrict__ r_dev, long long K, int q_mode,
+                            long long thr_bits, uint64_t* __restrict__ keys_out, double* __restrict__ m_out)
 {
-    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t r = r_dev ? *r_dev : r_host;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (c >= r) return;
     const long long* mb = reinterpret_cast<const long long*>(m);
-    if (!entry_selected(q_mode, rank[c], K, mb[c], thr_bits)) return;
-    const uint64_t ic = idx[c];
-    int cnt = 0;
-    for (int64_t k = lane; k < r; k += 32)
-        cnt += (entry_selected(q_mode, rank[k], K, mb[k], thr_bits) && idx[k] < ic) ? 1 : 0;
-    cnt = (int)__reduce_add_sync(kFull, (unsigned)cnt);
-    if (lane == 0) {
-        keys_out[cnt] = ic;
-        m_out[cnt] = m[c];
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < r; c += nw) {
+        if (!entry_selected(q_mode, rank[c], K, mb[c], thr_bits)) continue;
+        const uint64_t ic = idx[c];
+        int cnt = 0;
+        for (int64_t k = lane; k < r; k += 32)
+            cnt += (entry_selected(q_mode, rank[k], K, mb[k], thr_bits) && idx[k] < ic) ? 1 : 0;
+        cnt = (int)__reduce_add_sync(kFull, (unsigned)cnt);
+        if (lane == 0) {
+            keys_out[cnt] = ic;
+            m_out[cnt] = m[c];
+        }
     }
 }
 
 // One CTA: accepted count, the M64 of ranks K-1 and K, the largest accepted M64 and the
 // band statistics of the re-checked draws (the SelTail fields).
 __global__ void __launch_bounds__(SNT)
-k_sel_summary(const double* __restrict__ m64, const int* __restrict__ rank, const float* __restrict__ mhat, int64_t r,
-              long long K, int q_mode, long long thr_bits, CutParams cp, SelState* __restrict__ st)
+k_sel_summary(const double* __restrict__ m64, const int* __restrict__ rank, const float* __restrict__ mhat, int64_t r_host,
+              const long long* __restrict__ r_dev, long long K, int q_mode, long long thr_bits, CutParams cp,
+              SelState* __restrict__ st)
 {
+    const int64_t r = r_dev ? *r_dev : r_host;
     __shared__ long long s_thr[32];
     __shared__ float s_rel[32], s_band[32];
     __shared__ int s_viol[32], s_n[32];
@@ -455,13 +470,21 @@ k_sel_summary(const double* __restrict__ m64, const int* __restrict__ rank, cons
     }
 }
 
+// grid of a grid-stride warp-per-item kernel: enough 256-thread CTAs for `count` warps,
+// at most 16 per SM
+unsigned warp_grid(const frr_ctx* ctx, uint64_t count)
+{
+    const uint64_t want = (count * 32 + 255) / 256;
+    const uint64_t cap = (uint64_t)ctx->num_sms * 16;
+    return (unsigned)std::max<uint64_t>(1, std::min(want, cap));
+}
+
 template <int KB>
 frr_status launch_bits_kb(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t count,
-                          const uint64_t* draws, uint32_t* rows)
+                          const long long* count_dev, const uint64_t* draws, uint32_t* rows)
 {
-    const uint64_t threads = count * 32;
-    k_bits<KB><<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(seed, exact ? 1 : 0, ctx->binom, (int)ctx->n,
-                                                                          (int)ctx->n1, first, count, draws, rows);
+    k_bits<KB><<<warp_grid(ctx, count), 256, 0, ctx->stream>>>(seed, exact ? 1 : 0, ctx->binom, (int)ctx->n,
+                                                              (int)ctx->n1, first, count, count_dev, draws, rows);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     return FRR_OK;
 }
@@ -480,15 +503,15 @@ frr_status launch_recheck_kb(frr_ctx* ctx, uint64_t seed, bool exact, const uint
 }  // namespace
 
 frr_status bits_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t count,
-                       const uint64_t* draws, uint32_t* rows)
+                       const uint64_t* draws, uint32_t* rows, const long long* count_dev)
 {
     if (count == 0) return FRR_OK;
     switch (ctx->kb) {
-        case 1: return launch_bits_kb<1>(ctx, seed, exact, first, count, draws, rows);
-        case 2: return launch_bits_kb<2>(ctx, seed, exact, first, count, draws, rows);
-        case 4: return launch_bits_kb<4>(ctx, seed, exact, first, count, draws, rows);
-        case 8: return launch_bits_kb<8>(ctx, seed, exact, first, count, draws, rows);
-        case 16: return launch_bits_kb<16>(ctx, seed, exact, first, count, draws, rows);
+        case 1: return launch_bits_kb<1>(ctx, seed, exact, first, count, count_dev, draws, rows);
+        case 2: return launch_bits_kb<2>(ctx, seed, exact, first, count, count_dev, draws, rows);
+        case 4: return launch_bits_kb<4>(ctx, seed, exact, first, count, count_dev, draws, rows);
+        case 8: return launch_bits_kb<8>(ctx, seed, exact, first, count, count_dev, draws, rows);
+        case 16: return launch_bits_kb<16>(ctx, seed, exact, first, count, count_dev, draws, rows);
         default: return FRR_E_UNSUPPORTED;
     }
 }
@@ -518,17 +541,19 @@ frr_status unpack_launch(frr_ctx* ctx, const uint32_t* rows, uint64_t count, uin
 }
 
 frr_status recheck_sum_launch(frr_ctx* ctx, const double* part, int ncb, int64_t count, double* M64, double scale,
-                              double denom)
+                              double denom, const long long* count_dev)
 {
-    k_recheck_sum<<<ceil_div(count, 256), 256, 0, ctx->stream>>>(part, ncb, count, scale, denom, M64);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(count, 256), 4 * ctx->num_sms));
+    k_recheck_sum<<<grid, 256, 0, ctx->stream>>>(part, ncb, count, count_dev, scale, denom, M64);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     return FRR_OK;
 }
 
 // The recheck of the selection path and of frr_recheck: the tensor-core digit-plane kernel.
-frr_status recheck_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws, int64_t count, double* M64)
+frr_status recheck_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws, int64_t count, double* M64,
+                          const long long* count_dev)
 {
-    return recheck_tc_launch(ctx, seed, exact, draws, count, M64);
+    return recheck_tc_launch(ctx, seed, exact, draws, count, M64, count_dev);
 }
 
 frr_status balance_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout)
@@ -615,7 +640,7 @@ frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold,
 }
 
 // Selection step over the approximate M of draws [first, first + bc) held in Mhat (device).
-frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const float* Mhat)
+frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const float* Mhat, bool last)
 {
     StreamState& st = ctx->st;
     SelState* sel = static_cast<SelState*>(ctx->sel);
@@ -633,10 +658,24 @@ frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const f
     }
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     int64_t cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
-    const int64_t want = std::min<int64_t>(N, std::max<int64_t>(4 * st.K + 65536, 1 << 20));
+    // the last chunk of a deferred-count stream keeps every entry it could keep (capacity N),
+    // so the count need not be read back before the recheck
+    const bool defer = last && st.defer_count && N <= (int64_t)(1 << 20);
+    const int64_t want = defer ? N : std::min<int64_t>(N, std::max<int64_t>(4 * st.K + 65536, 1 << 20));
     if (cap < want) {
         FRR_TRY(ensure_retained(ctx, out, want));
         cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
+    }
+    if (defer) {
+        k_sel_compact<<<grid, kHistThreads, 0, ctx->stream>>>(Mhat, (int64_t)bc, first, ctx->ret_m[in],
+                                                             ctx->ret_idx[in], st.retained, sel, ctx->ret_m[out],
+                                                             ctx->ret_idx[out], cap);
+        FRR_CUDA_TRY(ctx, cudaGetLastError());
+        cudaEventRecord(ctx->ev[2], ctx->stream);
+        st.retained = -1;
+        st.retained_bound = N;
+        ctx->ret_cur = out;
+        return FRR_OK;
     }
     for (int attempt = 0;; ++attempt) {
         k_sel_compact<<<grid, kHistThreads, 0, ctx->stream>>>(Mhat, (int64_t)bc, first, ctx->ret_m[in],
@@ -681,7 +720,11 @@ frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B)
         cudaEventRecord(ctx->ev[0], ctx->stream);
         FRR_TRY(balance_launch(ctx, st.seed, st.exact, first + off, bc, ctx->Mhat));
         cudaEventRecord(ctx->ev[1], ctx->stream);
-        FRR_TRY(stream_select_step(ctx, first + off, bc, ctx->Mhat));
+        FRR_TRY(stream_select_step(ctx, first + off, bc, ctx->Mhat, st.seen + off + bc == st.total));
+        if (st.retained < 0) {
+            st.times_pending = true;  // nothing was synchronised: read the events in stream_end
+            continue;
+        }
         float t1 = 0.f, t2 = 0.f;
         cudaEventElapsedTime(&t1, ctx->ev[0], ctx->ev[1]);
         cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
@@ -702,7 +745,7 @@ frr_status stream_chunk_precomputed(frr_ctx* ctx, uint64_t first, uint64_t B, co
     for (uint64_t off = 0; off < B; off += kChunkMax) {
         const uint64_t bc = std::min<uint64_t>(kChunkMax, B - off);
         cudaEventRecord(ctx->ev[1], ctx->stream);
-        FRR_TRY(stream_select_step(ctx, first + off, bc, Mhat + off));
+        FRR_TRY(stream_select_step(ctx, first + off, bc, Mhat + off, st.seen + off + bc == st.total));
         float t2 = 0.f;
         cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
         ctx->stats.ms_select += t2;
@@ -717,49 +760,65 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
     StreamState& st = ctx->st;
     if (!st.active) return FRR_E_STATE;
     if (st.seen != st.total) return FRR_E_STATE;
-    const int64_t r = st.retained;
+    // the retained count is either known on the host, or (deferred) only on the device,
+    // bounded by retained_bound: the kernels below then read it there
+    const bool dev_count = st.retained < 0;
+    const int64_t rb = dev_count ? st.retained_bound : st.retained;
     const int cur = ctx->ret_cur;
     SelState* sel = static_cast<SelState*>(ctx->sel);
+    const long long* r_dev = dev_count ? &sel->kept : nullptr;
     FRR_TRY(ensure_host_pinned(ctx, 256));
     cudaEventRecord(ctx->ev[3], ctx->stream);
     // scratch: M64 (r), M64 out (r), keys out (r), rank (r)
-    const size_t need = (size_t)r * (3 * sizeof(double) + sizeof(int)) + 64;
+    const size_t need = (size_t)rb * (3 * sizeof(double) + sizeof(int)) + 64;
     FRR_TRY(ensure_device(ctx, &ctx->misc, &ctx->misc_bytes, need));
     char* base = static_cast<char*>(ctx->misc);
     double* m64 = reinterpret_cast<double*>(base);
-    double* mout = m64 + r;
-    uint64_t* kout = reinterpret_cast<uint64_t*>(mout + r);
-    int* rank = reinterpret_cast<int*>(kout + r);
+    double* mout = m64 + rb;
+    uint64_t* kout = reinterpret_cast<uint64_t*>(mout + rb);
+    int* rank = reinterpret_cast<int*>(kout + rb);
+    char* hp = static_cast<char*>(ctx->host_pinned);
     SelTail tail{};
     tail.boundary[0] = tail.boundary[1] = NAN;
-    if (r > 0) {
+    if (rb > 0) {
         const double nanv[2] = {NAN, NAN};
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(sel->boundary, nanv, sizeof(nanv), cudaMemcpyHostToDevice, ctx->stream));
-        FRR_TRY(recheck_launch(ctx, st.seed, st.exact, ctx->ret_idx[cur], r, m64));
+        FRR_TRY(recheck_launch(ctx, st.seed, st.exact, ctx->ret_idx[cur], rb, m64, r_dev));
         // threshold mode: M64 <= a compares as bit patterns (M64 >= 0); a < 0 accepts nothing
         long long thr_bits = -1;
         if (!st.q_mode && st.threshold >= 0.0) memcpy(&thr_bits, &st.threshold, sizeof(thr_bits));
-        k_rank<<<ceil_div(r * 32, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], r, rank);
-        k_place_sel<<<ceil_div(r * 32, 256), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], rank, r, st.K,
-                                                                   st.q_mode ? 1 : 0, thr_bits, kout, mout);
-        k_sel_summary<<<1, SNT, 0, ctx->stream>>>(m64, rank, ctx->ret_m[cur], r, st.K, st.q_mode ? 1 : 0, thr_bits,
-                                                  cut_params(ctx), sel);
+        k_rank<<<warp_grid(ctx, rb), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], rb, r_dev, rank);
+        k_place_sel<<<warp_grid(ctx, rb), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], rank, rb, r_dev, st.K,
+                                                                st.q_mode ? 1 : 0, thr_bits, kout, mout);
+        k_sel_summary<<<1, SNT, 0, ctx->stream>>>(m64, rank, ctx->ret_m[cur], rb, r_dev, st.K, st.q_mode ? 1 : 0,
+                                                  thr_bits, cut_params(ctx), sel);
         FRR_CUDA_TRY(ctx, cudaGetLastError());
-        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_pinned, &sel->nsel, sizeof(SelTail), cudaMemcpyDeviceToHost,
+        // kept (the retained count) and the SelTail fields, in one copy
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hp, &sel->kept, sizeof(long long) + sizeof(SelTail), cudaMemcpyDeviceToHost,
                                           ctx->stream));
-        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(static_cast<char*>(ctx->host_pinned) + 128, ctx->dev_counters + 12, sizeof(int),
-                                          cudaMemcpyDeviceToHost, ctx->stream));
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hp + 128, ctx->dev_counters + 12, sizeof(int), cudaMemcpyDeviceToHost,
+                                          ctx->stream));
     }
     cudaEventRecord(ctx->ev[4], ctx->stream);
     FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    if (r > 0) {
-        memcpy(&tail, ctx->host_pinned, sizeof(SelTail));
-        if (*reinterpret_cast<int*>(static_cast<char*>(ctx->host_pinned) + 128) != 0) {
+    int64_t r = rb;
+    if (rb > 0) {
+        if (dev_count) memcpy(&r, hp, sizeof(long long));
+        memcpy(&tail, hp + sizeof(long long), sizeof(SelTail));
+        if (*reinterpret_cast<int*>(hp + 128) != 0) {
             FRR_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dev_counters + 12, 0, sizeof(int), ctx->stream));
             FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
             st.active = false;
             return FRR_E_TIMEOUT;
         }
+    }
+    if (st.times_pending) {
+        float t1 = 0.f, t2 = 0.f;
+        cudaEventElapsedTime(&t1, ctx->ev[0], ctx->ev[1]);
+        cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
+        ctx->stats.ms_balance += t1;
+        ctx->stats.ms_select += t2;
+        st.times_pending = false;
     }
     float t = 0.f;
     cudaEventElapsedTime(&t, ctx->ev[3], ctx->ev[4]);
@@ -767,6 +826,7 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
     const long long nsel = tail.nsel;
     *K_out = nsel;
     st.active = false;
+    st.retained = r;
 
     const BandConsts& b = band_of(ctx);
     ctx->stats.candidates = r;
@@ -814,7 +874,7 @@ frr_status recheck_launch_into(frr_ctx* ctx, uint64_t seed, const uint64_t* draw
     }
     FRR_TRY(s);
     const double scale = ((double)ctx->n1 * (double)ctx->n0) / (double)ctx->n;
-    k_recheck_sum<<<ceil_div(count, 256), 256, 0, ctx->stream>>>(part, ncb, count, scale, 1.0, M64);
+    k_recheck_sum<<<ceil_div(count, 256), 256, 0, ctx->stream>>>(part, ncb, count, nullptr, scale, 1.0, M64);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     return FRR_OK;
 }
