@@ -3,6 +3,9 @@
 // kernels of the other translation units.
 #include "frr_internal.cuh"
 
+#include <mutex>
+#include <unordered_map>
+
 #include <chrono>
 #include <new>
 #include <vector>
@@ -91,13 +94,35 @@ static frr_status check_range(const frr_ctx* ctx, uint64_t seed, uint64_t first,
     return FRR_OK;
 }
 
+cudaMemPool_t temp_pool(int device)
+{
+    static std::mutex mu;
+    static std::unordered_map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(device);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    uint64_t keep = 256ull << 20;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[device] = pool;
+    return pool;
+}
+
 static void release(frr_ctx* ctx)
 {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    void* bufs[] = {ctx->Zc64, ctx->Z32, ctx->Zhi, ctx->Zlo, ctx->Q, ctx->Qsum, ctx->qexp, ctx->binom, ctx->Mhat,
-                    ctx->ret_idx[0], ctx->ret_idx[1], ctx->ret_m[0], ctx->ret_m[1], ctx->dev_counters, ctx->M64,
-                    ctx->ukeys, ctx->misc, ctx->misc2, ctx->sel, ctx->Zq};
+    // the fixed arrays (Zc64 ... dev_counters) live in ctx->arena
+    void* bufs[] = {ctx->arena, ctx->Mhat, ctx->ret_idx[0], ctx->ret_idx[1], ctx->ret_m[0], ctx->ret_m[1], ctx->M64,
+                    ctx->ukeys, ctx->misc, ctx->misc2, ctx->sel};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
@@ -184,17 +209,36 @@ frr_status frr_init(frr_ctx** out, const double* X, int64_t n, int64_t d, int64_
         ctx->own_stream = true;
     }
     for (cudaEvent_t& e : ctx->ev) INIT_CUDA(cudaEventCreate(&e));
+    // the fixed per-context arrays in one allocation (each part 256-byte aligned): fewer
+    // device-synchronising cudaMalloc / cudaFree calls per context
     const size_t nd = (size_t)n * d;
-    INIT_CUDA(cudaMalloc(&ctx->Zc64, nd * sizeof(double)));
-    INIT_CUDA(cudaMalloc(&ctx->Z32, (size_t)ctx->kpad * ctx->dpad32 * sizeof(float)));
-    INIT_CUDA(cudaMalloc(&ctx->Zhi, (size_t)d * ctx->kpad * sizeof(__nv_bfloat16)));
-    INIT_CUDA(cudaMalloc(&ctx->Zlo, (size_t)d * ctx->kpad * sizeof(__nv_bfloat16)));
-    INIT_CUDA(cudaMalloc(&ctx->Q, (size_t)ctx->kpad * d * sizeof(long long)));
-    INIT_CUDA(cudaMalloc(&ctx->Qsum, (size_t)d * sizeof(long long)));
-    INIT_CUDA(cudaMalloc(&ctx->qexp, (size_t)d * sizeof(int)));
-    INIT_CUDA(cudaMalloc(&ctx->binom, 64 * 64 * sizeof(uint64_t)));
-    INIT_CUDA(cudaMalloc(&ctx->Zq, (size_t)7 * d * ctx->kpad * sizeof(__nv_bfloat16)));
-    INIT_CUDA(cudaMalloc(&ctx->dev_counters, 16 * sizeof(int)));
+    const size_t sizes[10] = {nd * sizeof(double),
+                              (size_t)ctx->kpad * ctx->dpad32 * sizeof(float),
+                              (size_t)d * ctx->kpad * sizeof(__nv_bfloat16),
+                              (size_t)d * ctx->kpad * sizeof(__nv_bfloat16),
+                              (size_t)ctx->kpad * d * sizeof(long long),
+                              (size_t)d * sizeof(long long),
+                              (size_t)d * sizeof(int),
+                              64 * 64 * sizeof(uint64_t),
+                              (size_t)7 * d * ctx->kpad * sizeof(__nv_bfloat16),
+                              16 * sizeof(int)};
+    size_t offs[10], total = 0;
+    for (int i = 0; i < 10; ++i) {
+        offs[i] = total;
+        total += (sizes[i] + 255) & ~size_t(255);
+    }
+    INIT_CUDA(cudaMalloc(&ctx->arena, total));
+    char* a = static_cast<char*>(ctx->arena);
+    ctx->Zc64 = reinterpret_cast<double*>(a + offs[0]);
+    ctx->Z32 = reinterpret_cast<float*>(a + offs[1]);
+    ctx->Zhi = reinterpret_cast<__nv_bfloat16*>(a + offs[2]);
+    ctx->Zlo = reinterpret_cast<__nv_bfloat16*>(a + offs[3]);
+    ctx->Q = reinterpret_cast<long long*>(a + offs[4]);
+    ctx->Qsum = reinterpret_cast<long long*>(a + offs[5]);
+    ctx->qexp = reinterpret_cast<int*>(a + offs[6]);
+    ctx->binom = reinterpret_cast<uint64_t*>(a + offs[7]);
+    ctx->Zq = reinterpret_cast<__nv_bfloat16*>(a + offs[8]);
+    ctx->dev_counters = reinterpret_cast<int*>(a + offs[9]);
     INIT_CUDA(cudaMemsetAsync(ctx->dev_counters, 0, 16 * sizeof(int), ctx->stream));
 #undef INIT_CUDA
     frr_status s = prep_run(ctx, X);

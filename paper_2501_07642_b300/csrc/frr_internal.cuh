@@ -74,6 +74,8 @@ struct frr_ctx {
 
     frr::BandConsts band32{}, band_tc{};
 
+    void* arena = nullptr;     // one allocation holding the fixed per-context arrays above
+
     // scratch
     float* Mhat = nullptr;  size_t Mhat_bytes = 0;       // approximate M of a chunk
     uint64_t* ret_idx[2] = {nullptr, nullptr};           // retained candidates (ping-pong)
@@ -114,6 +116,10 @@ namespace frr {
 
 // true if p is device-accessible memory (device or managed); false for pageable / pinned host
 bool is_device_ptr(const void* p);
+
+// stream-ordered memory pool of the library for short-lived temporaries on `device`; it keeps
+// up to 256 MiB reserved between calls instead of returning it at every synchronisation
+cudaMemPool_t temp_pool(int device);
 
 // grow a device buffer to at least `bytes` (old contents are not kept)
 frr_status ensure_device(frr_ctx* ctx, void** buf, size_t* cap_bytes, size_t bytes);

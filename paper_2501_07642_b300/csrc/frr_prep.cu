@@ -403,16 +403,18 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
     auto fail = [&](cudaError_t e) { ctx->failed = true; rc = (e == cudaErrorMemoryAllocation) ? FRR_E_NOMEM : FRR_E_CUDA; };
 #define PREP_CHECK(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) { fail(_e); goto cleanup; } } while (0)
 
-    PREP_CHECK(cudaMallocAsync(&X, nd * sizeof(double), s));
-    PREP_CHECK(cudaMallocAsync(&xbar, d * sizeof(double), s));
-    PREP_CHECK(cudaMallocAsync(&Xc, nd * sizeof(double), s));
-    PREP_CHECK(cudaMallocAsync(&S, (size_t)d * d * sizeof(double), s));
-    PREP_CHECK(cudaMallocAsync(&Adiag, d * sizeof(double), s));
-    PREP_CHECK(cudaMallocAsync(&Lm, (size_t)d * d * sizeof(double), s));
-    PREP_CHECK(cudaMallocAsync(&ZT, nd * sizeof(double), s));
-    PREP_CHECK(cudaMallocAsync(&scal, 4 * sizeof(double), s));
-    PREP_CHECK(cudaMallocAsync(&eps, 2 * (size_t)d * sizeof(double), s));
-    PREP_CHECK(cudaMallocAsync(&status, sizeof(int), s));
+    cudaMemPool_t pool = temp_pool(ctx->device);
+    if (pool == nullptr) return FRR_E_CUDA;
+    PREP_CHECK(cudaMallocFromPoolAsync(&X, nd * sizeof(double), pool, s));
+    PREP_CHECK(cudaMallocFromPoolAsync(&xbar, d * sizeof(double), pool, s));
+    PREP_CHECK(cudaMallocFromPoolAsync(&Xc, nd * sizeof(double), pool, s));
+    PREP_CHECK(cudaMallocFromPoolAsync(&S, (size_t)d * d * sizeof(double), pool, s));
+    PREP_CHECK(cudaMallocFromPoolAsync(&Adiag, d * sizeof(double), pool, s));
+    PREP_CHECK(cudaMallocFromPoolAsync(&Lm, (size_t)d * d * sizeof(double), pool, s));
+    PREP_CHECK(cudaMallocFromPoolAsync(&ZT, nd * sizeof(double), pool, s));
+    PREP_CHECK(cudaMallocFromPoolAsync(&scal, 4 * sizeof(double), pool, s));
+    PREP_CHECK(cudaMallocFromPoolAsync(&eps, 2 * (size_t)d * sizeof(double), pool, s));
+    PREP_CHECK(cudaMallocFromPoolAsync(&status, sizeof(int), pool, s));
     PREP_CHECK(cudaMemsetAsync(status, 0, sizeof(int), s));
     PREP_CHECK(cudaMemsetAsync(Lm, 0, (size_t)d * d * sizeof(double), s));
     PREP_CHECK(cudaMemcpyAsync(X, X_host, nd * sizeof(double), cudaMemcpyHostToDevice, s));
