@@ -401,13 +401,15 @@ frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t f
 
 // One persistent launch over E experiments: `table` (device, E entries) describes them,
 // `prefix` (device, E + 1 entries) holds the first global tile of each. kbmax bounds their
-// Philox blocks per lane. Errors from bounded waits go to *err (device).
-frr_status balance_tc_batch_launch(frr_ctx* owner, const TcExp* table, const unsigned long long* prefix, int E,
-                                   unsigned long long tiles, int kbmax, int* err)
+// Philox blocks per lane; the launch goes to `stream`. Errors from bounded waits go to *err
+// (device).
+frr_status balance_tc_batch_launch(frr_ctx* owner, cudaStream_t stream, const TcExp* table,
+                                   const unsigned long long* prefix, int E, unsigned long long tiles, int kbmax,
+                                   int* err)
 {
     if (tiles == 0) return FRR_OK;
     TcExp unused{};
-    return launch_kb(owner, kbmax, owner->stream, owner->num_sms, unused, table, prefix, E, tiles, err);
+    return launch_kb(owner, kbmax, stream, owner->num_sms, unused, table, prefix, E, tiles, err);
 }
 
 }  // namespace frr

@@ -6,11 +6,15 @@
 // experiment comes from ONE persistent tcgen05 launch whose global tile index space
 // concatenates the experiments' draw tiles (experiment tables in device memory), so
 // small and large experiments share all SMs. Selection, exact recheck and the
-// randomization test then run per experiment on the resulting M_hat arrays.
+// randomization test then run per experiment on the resulting M_hat arrays. Preparation
+// and the per-experiment stages run on several host threads, one stream each, so that the
+// small kernels of different experiments run concurrently.
 #include "frr_internal.cuh"
 
+#include <algorithm>
 #include <chrono>
 #include <cuda.h>
+#include <thread>
 #include <vector>
 
 #include "frr_tcexp.cuh"
@@ -18,12 +22,30 @@
 namespace frr {
 
 frr_status tc_describe(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout, TcExp* x);
-frr_status balance_tc_batch_launch(frr_ctx* owner, const TcExp* table, const unsigned long long* prefix, int E,
-                                   unsigned long long tiles, int kbmax, int* err);
+frr_status balance_tc_batch_launch(frr_ctx* owner, cudaStream_t stream, const TcExp* table,
+                                   const unsigned long long* prefix, int E, unsigned long long tiles, int kbmax,
+                                   int* err);
 
 }  // namespace frr
 
 using namespace frr;
+
+namespace {
+
+// host worker threads of the batched driver (each owns one stream)
+constexpr int kWorkers = 8;
+
+template <typename F>
+void run_workers(int nw, F&& f)
+{
+    std::vector<std::thread> th;
+    th.reserve((size_t)nw);
+    for (int w = 1; w < nw; ++w) th.emplace_back(f, w);
+    f(0);
+    for (auto& t : th) t.join();
+}
+
+}  // namespace
 
 extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opts* opts, frr_batch_stats* stats)
 {
@@ -46,29 +68,47 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
         own_stream = true;
     }
     int64_t draws = 0;
-    for (int64_t e = 0; e < E; ++e) {
-        ex[e].K_out = 0;
-        ex[e].ci_lo = ex[e].ci_hi = NAN;
-        const bool hq = !isnan(ex[e].q), ht = !isnan(ex[e].threshold);
-        if (hq == ht || (hq && !(ex[e].q > 0.0 && ex[e].q <= 1.0)) || (ht && !(ex[e].threshold >= 0.0)) || ex[e].B == 0 ||
-            ex[e].first_draw + ex[e].B < ex[e].first_draw) {
-            note(e, FRR_E_ARG);
-            continue;
+    // Preparation (FP64, latency-bound on B300) of several experiments at once: worker
+    // threads, each with its own stream, so that their small kernels share the SMs (the
+    // contexts allocate stream-ordered from a pool, so the threads do not synchronise the
+    // device through allocations).
+    const int nw = (int)std::min<int64_t>(kWorkers, E);
+    std::vector<cudaStream_t> ws((size_t)nw, nullptr);
+    for (int w = 0; w < nw; ++w)
+        if (cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            ws[w] = stream;
         }
-        frr_opts o = base;
-        o.whiten = ex[e].whiten;
-        o.ridge = ex[e].ridge;
-        o.cuda_stream = stream;
-        const frr_status s = frr_init(&ctx[e], ex[e].X, ex[e].n, ex[e].d, ex[e].n1, &o);
-        note(e, s);
-        if (s != FRR_OK) ctx[e] = nullptr;
-        else if (ex[e].seed == FRR_EXACT_SEED &&
-                 (ex[e].n > kExactMaxN || ex[e].first_draw + ex[e].B > binom_host((int)ex[e].n, (int)ex[e].n1))) {
-            note(e, ex[e].n > kExactMaxN ? FRR_E_UNSUPPORTED : FRR_E_RANGE);
-            frr_destroy(ctx[e]);
-            ctx[e] = nullptr;
+    std::vector<frr_status> st_init((size_t)E, FRR_OK);
+    auto prepare = [&](int w) {
+        for (int64_t e = w; e < E; e += nw) {
+            ex[e].K_out = 0;
+            ex[e].ci_lo = ex[e].ci_hi = NAN;
+            const bool hq = !isnan(ex[e].q), ht = !isnan(ex[e].threshold);
+            if (hq == ht || (hq && !(ex[e].q > 0.0 && ex[e].q <= 1.0)) || (ht && !(ex[e].threshold >= 0.0)) ||
+                ex[e].B == 0 || ex[e].first_draw + ex[e].B < ex[e].first_draw) {
+                st_init[e] = FRR_E_ARG;
+                continue;
+            }
+            frr_opts o = base;
+            o.whiten = ex[e].whiten;
+            o.ridge = ex[e].ridge;
+            o.cuda_stream = ws[w];
+            frr_status s = frr_init(&ctx[e], ex[e].X, ex[e].n, ex[e].d, ex[e].n1, &o);
+            if (s != FRR_OK) {
+                ctx[e] = nullptr;
+            } else if (ex[e].seed == FRR_EXACT_SEED &&
+                       (ex[e].n > kExactMaxN || ex[e].first_draw + ex[e].B > binom_host((int)ex[e].n, (int)ex[e].n1))) {
+                s = ex[e].n > kExactMaxN ? FRR_E_UNSUPPORTED : FRR_E_RANGE;
+                frr_destroy(ctx[e]);
+                ctx[e] = nullptr;
+            }
+            st_init[e] = s;
         }
-    }
+        if (cudaStreamSynchronize(ws[w]) != cudaSuccess) cudaGetLastError();
+    };
+    run_workers(nw, prepare);
+    for (int64_t e = 0; e < E; ++e) note(e, st_init[e]);
     const auto t1 = std::chrono::steady_clock::now();
 
     // approximate M of every draw of every prepared experiment
@@ -113,7 +153,8 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
                                 cudaMemcpyHostToDevice, stream);
                 cudaMemsetAsync(d_err, 0, sizeof(int), stream);
                 cudaEventRecord(ea, stream);
-                rc = balance_tc_batch_launch(owner, d_table, d_prefix, (int)live.size(), prefix.back(), kbmax, d_err);
+                rc = balance_tc_batch_launch(owner, stream, d_table, d_prefix, (int)live.size(), prefix.back(), kbmax,
+                                             d_err);
                 cudaEventRecord(eb, stream);
                 int herr = 0;
                 if (cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
@@ -126,36 +167,48 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             }
         } else if (rc == FRR_OK) {
             cudaEventRecord(ea, stream);
+            // FP32: one launch per experiment, on its context's stream
             for (size_t k = 0; k < live.size() && rc == FRR_OK; ++k) {
                 const frr_experiment& x = ex[live[k]];
                 rc = balance_f32_launch(ctx[live[k]], x.seed, x.seed == FRR_EXACT_SEED, x.first_draw, x.B, mhat + off[k]);
             }
+            for (cudaStream_t w : ws)
+                if (cudaStreamSynchronize(w) != cudaSuccess) { cudaGetLastError(); rc = FRR_E_CUDA; }
             cudaEventRecord(eb, stream);
             if (cudaStreamSynchronize(stream) != cudaSuccess) { cudaGetLastError(); rc = FRR_E_CUDA; }
         }
         cudaEventElapsedTime(&ms_balance, ea, eb);
         cudaEventDestroy(ea);
         cudaEventDestroy(eb);
-        for (size_t k = 0; k < live.size(); ++k) {
-            const int64_t e = live[k];
-            frr_experiment& x = ex[e];
-            if (rc != FRR_OK) { note(e, rc); continue; }
-            frr_status s = stream_begin(ctx[e], x.seed, x.q, x.threshold, x.B);
-            if (s == FRR_OK) s = stream_chunk_precomputed(ctx[e], x.first_draw, x.B, mhat + off[k]);
-            int64_t K = 0;
-            if (s == FRR_OK) s = stream_end(ctx[e], x.keys_out, x.M64_out, x.cap, &K);
-            x.K_out = K;
-            if (s == FRR_OK && x.Y != nullptr && K > 0) {
-                uint64_t obs = 0;
-                s = copy_out(ctx[e], &obs, x.keys_out, sizeof(uint64_t));
-                if (s == FRR_OK) {
-                    if (!x.tau || x.T < 1 || !x.p_out || !(x.alpha >= 0.0 && x.alpha <= 1.0)) s = FRR_E_ARG;
-                    else s = randtest_run(ctx[e], x.seed, x.keys_out, K, obs, x.Y, x.tau, x.T, x.alpha, x.p_out,
-                                          x.count_out, &x.ci_lo, &x.ci_hi);
+        // selection, recheck and tests per experiment, on the workers' streams (each context
+        // is used by one thread only)
+        std::vector<frr_status> st_sel(live.size(), FRR_OK);
+        auto finish = [&](int w) {
+            for (size_t k = (size_t)w; k < live.size(); k += (size_t)nw) {
+                const int64_t e = live[k];
+                frr_experiment& x = ex[e];
+                if (rc != FRR_OK) { st_sel[k] = rc; continue; }
+                frr_status s = stream_begin(ctx[e], x.seed, x.q, x.threshold, x.B);
+                if (s == FRR_OK) s = stream_chunk_precomputed(ctx[e], x.first_draw, x.B, mhat + off[k]);
+                int64_t K = 0;
+                if (s == FRR_OK) s = stream_end(ctx[e], x.keys_out, x.M64_out, x.cap, &K);
+                x.K_out = K;
+                if (s == FRR_OK && x.Y != nullptr && K > 0) {
+                    uint64_t obs = 0;
+                    s = copy_out(ctx[e], &obs, x.keys_out, sizeof(uint64_t));
+                    if (s == FRR_OK) {
+                        if (!x.tau || x.T < 1 || !x.p_out || !(x.alpha >= 0.0 && x.alpha <= 1.0)) s = FRR_E_ARG;
+                        else s = randtest_run(ctx[e], x.seed, x.keys_out, K, obs, x.Y, x.tau, x.T, x.alpha, x.p_out,
+                                              x.count_out, &x.ci_lo, &x.ci_hi);
+                    }
                 }
+                st_sel[k] = s;
             }
-            note(e, s);
-            draws += (int64_t)x.B;
+        };
+        run_workers(nw, finish);
+        for (size_t k = 0; k < live.size(); ++k) {
+            note(live[k], st_sel[k]);
+            draws += (int64_t)ex[live[k]].B;
         }
     }
     const auto t2 = std::chrono::steady_clock::now();
@@ -164,6 +217,8 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
     cudaFree(d_prefix);
     cudaFree(d_err);
     for (frr_ctx* c : ctx) frr_destroy(c);
+    for (cudaStream_t w : ws)
+        if (w != stream) cudaStreamDestroy(w);
     if (own_stream) cudaStreamDestroy(stream);
     if (stats) {
         stats->experiments = E;

@@ -24,16 +24,18 @@ bool is_device_ptr(const void* p)
 
 frr_status ensure_device(frr_ctx* ctx, void** buf, size_t* cap_bytes, size_t bytes)
 {
+    // stream-ordered allocations from the library pool: no device-wide synchronisation
     if (bytes == 0) bytes = 16;
     if (*buf != nullptr && *cap_bytes >= bytes) return FRR_OK;
     if (*buf != nullptr) {
-        FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-        cudaFree(*buf);
+        cudaFreeAsync(*buf, ctx->stream);
         *buf = nullptr;
         *cap_bytes = 0;
     }
+    cudaMemPool_t pool = temp_pool(ctx->device);
+    if (pool == nullptr) return FRR_E_CUDA;
     const size_t grown = bytes + bytes / 4;
-    cudaError_t e = cudaMalloc(buf, grown);
+    cudaError_t e = cudaMallocFromPoolAsync(buf, grown, pool, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *buf = nullptr;
@@ -120,11 +122,13 @@ static void release(frr_ctx* ctx)
 {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    // the fixed arrays (Zc64 ... dev_counters) live in ctx->arena
+    // the fixed arrays (Zc64 ... dev_counters) live in ctx->arena; all of these come from the
+    // library pool and go back to it in stream order
     void* bufs[] = {ctx->arena, ctx->Mhat, ctx->ret_idx[0], ctx->ret_idx[1], ctx->ret_m[0], ctx->ret_m[1], ctx->M64,
                     ctx->ukeys, ctx->misc, ctx->misc2, ctx->sel};
     for (void* b : bufs)
-        if (b) cudaFree(b);
+        if (b) cudaFreeAsync(b, ctx->stream ? ctx->stream : 0);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     for (cudaEvent_t e : ctx->ev)
         if (e) cudaEventDestroy(e);
@@ -227,7 +231,9 @@ frr_status frr_init(frr_ctx** out, const double* X, int64_t n, int64_t d, int64_
         offs[i] = total;
         total += (sizes[i] + 255) & ~size_t(255);
     }
-    INIT_CUDA(cudaMalloc(&ctx->arena, total));
+    cudaMemPool_t pool = temp_pool(ctx->device);
+    if (pool == nullptr) return bail(FRR_E_CUDA);
+    INIT_CUDA(cudaMallocFromPoolAsync(&ctx->arena, total, pool, ctx->stream));
     char* a = static_cast<char*>(ctx->arena);
     ctx->Zc64 = reinterpret_cast<double*>(a + offs[0]);
     ctx->Z32 = reinterpret_cast<float*>(a + offs[1]);
