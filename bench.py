@@ -300,6 +300,7 @@ def run_frr(args):
                 "adds_per_draw": adds}
         dtype = "f32"
     dist_line = distance_bench(peaks["bf16_tflops"]) if args.distance else None
+    batch_line = batched_bench() if args.batched else None
     cpu = None
     if args.cpu_baseline:
         Zc = oracle_zc(X)
@@ -322,7 +323,7 @@ def run_frr(args):
             "clocks": {k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "selection": {k: r["stats"][k] for k in ("candidates", "accepted", "max_rel_err", "max_err_over_band",
                                                      "band_violations", "parity_at_risk")},
-            "fast_distance": dist_line}
+            "fast_distance": dist_line, "batched": batch_line}
     print(json.dumps(line), flush=True)
 
 
@@ -363,6 +364,29 @@ def distance_bench(peak_tflops: float, n: int = 16384, d: int = 768, reps: int =
             "output_gbs": n * n * 4 / (ms / 1e3) / 1e9}
 
 
+def batched_bench(reps: int = 3) -> dict:
+    """frr_batch_run over the 256-experiment batched workload (n log-uniform on [50, 2000],
+    d on [10, 500], 1e5 draws and q = 0.01 each): preparation, one persistent balance launch
+    and per-experiment selection; host covariates, host results; median of `reps` runs."""
+    from paper_2501_07642_b300 import frr
+    from paper_2501_07642_b300.workloads import batched_workloads
+
+    ws = batched_workloads(256)
+    exps = [dict(X=w.covariates(), n1=w.n1, whiten=w.whiten, ridge=w.ridge, seed=w.philox_seed, B=w.draws, q=w.q,
+                 cap=2048) for w in ws]
+    frr.frr_batch_run(exps[:8])
+    runs = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        _, st = frr.frr_batch_run(exps)
+        runs.append((time.perf_counter() - t0, st))
+    runs.sort(key=lambda r: r[0])
+    dt, st = runs[len(runs) // 2]
+    return {"workload": "batched_256", "experiments": 256, "draws": int(st["draws"]), "s_per_batch": dt,
+            "draws_per_s": st["draws"] / dt, "ms_prep": st["ms_init"], "ms_balance": st["ms_balance"],
+            "ms_select": st["ms_select"], "note": "wall time of frr_batch_run with host inputs and outputs"}
+
+
 def tc_traffic(B):
     """DRAM bytes per k_balance_tc launch from the committed ncu summary, or None when the
     kernel's sources changed since the capture or the launch size differs."""
@@ -393,6 +417,7 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-distance", dest="distance", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

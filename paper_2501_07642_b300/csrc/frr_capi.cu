@@ -132,6 +132,7 @@ static void release(frr_ctx* ctx)
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     for (cudaEvent_t e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     cudaGetLastError();
     delete ctx;
@@ -213,6 +214,7 @@ frr_status frr_init(frr_ctx** out, const double* X, int64_t n, int64_t d, int64_
         ctx->own_stream = true;
     }
     for (cudaEvent_t& e : ctx->ev) INIT_CUDA(cudaEventCreate(&e));
+    INIT_CUDA(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
     // the fixed per-context arrays in one allocation (each part 256-byte aligned): fewer
     // device-synchronising cudaMalloc / cudaFree calls per context
     const size_t nd = (size_t)n * d;

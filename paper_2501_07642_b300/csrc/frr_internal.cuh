@@ -51,6 +51,7 @@ struct frr_ctx {
     int device = 0, num_sms = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t aux = nullptr;  // second stream of the prep (forward substitution beside Cholesky)
     int kb = 0;                // Philox blocks per lane, power of two: n <= 128 * kb
     int kused = 0;             // K positions holding units: 128 * ceil(n / 128)
     int kpad = 0;              // 128 * kb

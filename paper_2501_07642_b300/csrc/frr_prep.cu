@@ -433,33 +433,51 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
         PREP_CHECK(cudaStreamSynchronize(s));
         const double tol_abs = 1e-12 * sc[1];
         const size_t dd = (size_t)d * d;
+        // forward substitution in place on a copy of Xc (ZT holds n x d row-major here)
+        PREP_CHECK(cudaMemcpyAsync(ZT, Xc, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
         if (ctx->opts.whiten == FRR_DIAG) {
             k_diag_L<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(S, d, tol_abs, Lm, status);
-        } else {
-            k_init_A<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(S, Adiag, d, Lm);
             for (int k0 = 0; k0 < d; k0 += kP) {
+                const int pw = (d - k0) < kP ? (d - k0) : kP;
+                k_fwd_panel<<<ceil_div(n, 32), 32, 0, s>>>(ZT, Lm, n, d, k0, pw);
+                const int right = d - k0 - pw;
+                if (right > 0)
+                    k_fwd_trailing<<<dim3(ceil_div(right, 32), ceil_div(n, 32)), 256, 0, s>>>(ZT, Lm, n, d, k0, pw);
+            }
+        } else {
+            // Both factorisations are chains of latency-bound panels. Step p of the forward
+            // substitution needs only column panel p of L, which is final once Cholesky panel
+            // p is done (later trailing updates touch columns to its right), so it runs on a
+            // second stream, one panel behind: the two chains overlap.
+            k_init_A<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(S, Adiag, d, Lm);
+            const int np = ceil_div(d, kP);
+            std::vector<cudaEvent_t> evs((size_t)np + 2, nullptr);
+            for (auto& e : evs) PREP_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            PREP_CHECK(cudaEventRecord(evs[np], s));
+            PREP_CHECK(cudaStreamWaitEvent(ctx->aux, evs[np], 0));
+            for (int p = 0, k0 = 0; k0 < d; ++p, k0 += kP) {
                 const int pw = (d - k0) < kP ? (d - k0) : kP;
                 const int below = d - k0 - pw;
                 k_chol_panel<<<below > 0 ? ceil_div(below, 32) : 1, 32, 0, s>>>(Lm, d, k0, pw, tol_abs, status);
+                PREP_CHECK(cudaEventRecord(evs[p], s));
+                PREP_CHECK(cudaStreamWaitEvent(ctx->aux, evs[p], 0));
+                k_fwd_panel<<<ceil_div(n, 32), 32, 0, ctx->aux>>>(ZT, Lm, n, d, k0, pw);
                 if (below > 0) {
                     const int tiles = ceil_div(below, 32);
                     k_chol_trailing<<<dim3(tiles, tiles), 256, 0, s>>>(Lm, d, k0, pw);
+                    k_fwd_trailing<<<dim3(ceil_div(below, 32), ceil_div(n, 32)), 256, 0, ctx->aux>>>(ZT, Lm, n, d, k0,
+                                                                                                  pw);
                 }
             }
+            PREP_CHECK(cudaEventRecord(evs[np + 1], ctx->aux));
+            PREP_CHECK(cudaStreamWaitEvent(s, evs[np + 1], 0));
+            for (auto& e : evs) cudaEventDestroy(e);
         }
         PREP_CHECK(cudaGetLastError());
         int st = 0;
         PREP_CHECK(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
         PREP_CHECK(cudaStreamSynchronize(s));
         if (st != 0) { rc = FRR_E_DEGENERATE; goto cleanup; }
-    }
-    // forward substitution in place on a copy of Xc (ZT holds n x d row-major here)
-    PREP_CHECK(cudaMemcpyAsync(ZT, Xc, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    for (int k0 = 0; k0 < d; k0 += kP) {
-        const int pw = (d - k0) < kP ? (d - k0) : kP;
-        k_fwd_panel<<<ceil_div(n, 32), 32, 0, s>>>(ZT, Lm, n, d, k0, pw);
-        const int right = d - k0 - pw;
-        if (right > 0) k_fwd_trailing<<<dim3(ceil_div(right, 32), ceil_div(n, 32)), 256, 0, s>>>(ZT, Lm, n, d, k0, pw);
     }
     PREP_CHECK(cudaMemcpyAsync(ctx->Zc64, ZT, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
     k_qexp<<<ceil_div(d, 128), 128, 0, s>>>(ctx->Zc64, n, d, ctx->qexp);
