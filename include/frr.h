@@ -63,7 +63,8 @@ typedef enum {
     FRR_E_CAPACITY = -6,   /* an output array is smaller than the result (*K_out holds the size needed) */
     FRR_E_RANGE = -7,      /* first_draw + B overflows 64 bits, or an exact rank >= C(n, n1) */
     FRR_E_STATE = -8,      /* call out of sequence (e.g. frr_stream_chunk before frr_stream_begin) */
-    FRR_E_UNSUPPORTED = -9 /* shape outside what the compiled kernels cover (n > 2048, exact mode n > 63) */
+    FRR_E_UNSUPPORTED = -9, /* shape outside what the compiled kernels cover (n > 2048, exact mode n > 63) */
+    FRR_E_MISMATCH = -10    /* two configurations of a kernel disagreed on the same input (internal error) */
 } frr_status;
 
 /* precision of the bulk balance evaluation (the accepted set is always decided in FP64 accuracy) */
@@ -83,6 +84,8 @@ typedef struct {
     double ridge;       /* ridge weight for FRR_RIDGE, relative to tr(S)/d; default 0.1 */
     double band_safety; /* multiplier on the error band of the approximate M; default 2.0, must be >= 1 */
     void* cuda_stream;  /* cudaStream_t to run on; NULL = the context creates its own */
+    int autotune;       /* frr_batch_run only: 1 = time the split-BF16 kernel configurations on a
+                           probe of the batch before its launch (see frr_autotune); default 0 */
 } frr_opts;
 
 typedef struct {
@@ -119,6 +122,31 @@ frr_status frr_balance(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_
 
 /* Same as frr_balance with seed = FRR_EXACT_SEED: ranks [first_rank, first_rank + B). */
 frr_status frr_balance_exact(frr_ctx* ctx, uint64_t first_rank, uint64_t B, float* M_out);
+
+/* ---- kernel autotuning --------------------------------------------------------------
+ * The split-BF16 balance kernel (Sec. 2.1 batched processing) is compiled in several
+ * configurations for each number of Philox blocks per lane kb (n <= 128 kb): the number of
+ * generating warps per CTA, which sets how many per-draw selections run concurrently on an
+ * SM, and the depth of the covariate-tile pipeline in shared memory. All produce
+ * bit-identical M_hat. Without tuning a built-in choice per kb is used. */
+#define FRR_TUNE_MAX 8
+typedef struct {
+    int kb;                  /* Philox blocks per lane of the shape class */
+    int chunks;              /* covariate chunks of 256 columns, ceil(d / 256) */
+    int candidates;          /* configurations timed (entries used below) */
+    int chosen;              /* index of the fastest, now used for this shape class */
+    int ng[FRR_TUNE_MAX];    /* generating warps per CTA */
+    int sb[FRR_TUNE_MAX];    /* covariate-tile stages in shared memory */
+    float ms[FRR_TUNE_MAX];  /* fastest timed launch of each on the probe (device ms) */
+} frr_tune_result;
+
+/* Times every configuration compiled for this context's kb on B_probe draws of a fixed
+ * probe seed (0: 8 tiles of 128 draws per SM; at most 2^24), checks that each reproduces
+ * the first one's M_hat bit for bit (else FRR_E_MISMATCH), and makes the fastest the
+ * configuration of every later split-BF16 launch of this shape class (device, kb,
+ * ceil(d / 256)) in this process, for any context. The context's scratch buffer for
+ * M_hat is reused; no other state changes. FRR_E_UNSUPPORTED for an FP32 context. */
+frr_status frr_autotune(frr_ctx* ctx, uint64_t B_probe, frr_tune_result* out);
 
 /* Accepted pool of draws [first_draw, first_draw + B) (Sec. 2.2, 2.3). Exactly one of
  * q (0 < q <= 1: keep the K = ceil(qB - 1e-9 qB) draws with the smallest

@@ -25,6 +25,13 @@
 
 #include <cuda.h>
 
+#include <array>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "frr_tcexp.cuh"
 #include "frr_tc_ptx.cuh"
 
@@ -347,17 +354,104 @@ frr_status launch(frr_ctx* ctx, cudaStream_t stream, int num_sms, const TcExp& o
     return FRR_OK;
 }
 
-frr_status launch_kb(frr_ctx* ctx, int kbmax, cudaStream_t stream, int num_sms, const TcExp& one, const TcExp* table,
-                     const unsigned long long* prefix, int E, unsigned long long tiles, int* err)
+// ---- compiled configurations and their tuning ------------------------------------------
+// (KB, SB, NG): Philox blocks per lane of the generating warps, B-operand stages, and
+// generating warps per CTA, i.e. how many draws each SM selects concurrently. A CTA has
+// 10 + NG warps (at most 32), and the register file gives each thread at most
+// 65536 / (32 (10 + NG)) registers, so long draws (large KB) get fewer generating warps.
+// Every configuration issues the same MMA sequence for a draw, so all of them produce
+// bit-identical M_hat; they differ only in speed, which depends on n (generation cost per
+// draw) and d (tensor work per draw).
+struct TcCfg {
+    int kb, sb, ng;
+};
+constexpr TcCfg kCfg[] = {
+    {1, 4, 10}, {1, 4, 14}, {1, 4, 18}, {1, 4, 22},
+    {2, 4, 10}, {2, 4, 14}, {2, 4, 18}, {2, 4, 22},
+    {4, 4, 10}, {4, 4, 14}, {4, 4, 18}, {4, 4, 22},
+    {8, 4, 8},  {8, 4, 10}, {8, 4, 12},
+    {16, 3, 4}, {16, 3, 6},
+};
+constexpr int kNumCfg = (int)(sizeof(kCfg) / sizeof(kCfg[0]));
+
+using LaunchFn = frr_status (*)(frr_ctx*, cudaStream_t, int, const TcExp&, const TcExp*, const unsigned long long*, int,
+                                unsigned long long, int*);
+
+template <size_t... I>
+constexpr std::array<LaunchFn, sizeof...(I)> launch_table(std::index_sequence<I...>)
 {
-    switch (kbmax) {
-        case 1: return launch<1, 4, 10>(ctx, stream, num_sms, one, table, prefix, E, tiles, err);
-        case 2: return launch<2, 4, 10>(ctx, stream, num_sms, one, table, prefix, E, tiles, err);
-        case 4: return launch<4, 4, 10>(ctx, stream, num_sms, one, table, prefix, E, tiles, err);
-        case 8: return launch<8, 4, 10>(ctx, stream, num_sms, one, table, prefix, E, tiles, err);
-        case 16: return launch<16, 3, 6>(ctx, stream, num_sms, one, table, prefix, E, tiles, err);
-        default: return FRR_E_UNSUPPORTED;
+    return {{&launch<kCfg[I].kb, kCfg[I].sb, kCfg[I].ng>...}};
+}
+constexpr std::array<LaunchFn, kNumCfg> kLaunch = launch_table(std::make_index_sequence<kNumCfg>{});
+
+// built-in choice per KB (measured on B300 with d up to 1000), used until a shape class is tuned
+int default_cfg(int kb)
+{
+    switch (kb) {
+        case 1: return 3;
+        case 2: return 7;
+        case 4: return 11;
+        case 8: return 13;
+        case 16: return 16;
+        default: return -1;
     }
+}
+
+std::mutex g_tune_mu;
+std::map<std::array<int, 4>, int> g_tuned;  // (device, KB, covariate chunks, batched) -> configuration
+
+int chosen_cfg(int device, int kb, int nch, bool multi)
+{
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        const auto it = g_tuned.find({device, kb, nch, multi ? 1 : 0});
+        if (it != g_tuned.end()) return it->second;
+    }
+    return default_cfg(kb);
+}
+
+void remember_cfg(int device, int kb, int nch, bool multi, int cfg)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[{device, kb, nch, multi ? 1 : 0}] = cfg;
+}
+
+frr_status launch_cfg(int cfg, frr_ctx* ctx, cudaStream_t stream, int num_sms, const TcExp& one, const TcExp* table,
+                      const unsigned long long* prefix, int E, unsigned long long tiles, int* err)
+{
+    if (cfg < 0 || cfg >= kNumCfg) return FRR_E_UNSUPPORTED;
+    return kLaunch[(size_t)cfg](ctx, stream, num_sms, one, table, prefix, E, tiles, err);
+}
+
+// Times configuration `cfg` (one warm-up launch, then the fastest of `reps`); run(cfg)
+// enqueues one launch on `stream`.
+template <typename Run>
+frr_status time_cfg(frr_ctx* ctx, cudaStream_t stream, int cfg, int reps, Run&& run, float* ms_out)
+{
+    cudaEvent_t e0, e1;
+    FRR_CUDA_TRY(ctx, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        FRR_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    frr_status s = run(cfg);
+    float best = INFINITY;
+    for (int r = 0; r < reps && s == FRR_OK; ++r) {
+        cudaEventRecord(e0, stream);
+        s = run(cfg);
+        cudaEventRecord(e1, stream);
+        if (s == FRR_OK && cudaEventSynchronize(e1) != cudaSuccess) s = FRR_E_CUDA;
+        float ms = 0.f;
+        if (s == FRR_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == FRR_E_CUDA) {
+        cudaGetLastError();
+        ctx->failed = true;
+    }
+    *ms_out = best;
+    return s;
 }
 
 }  // namespace
@@ -396,20 +490,96 @@ frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t f
     TcExp one;
     FRR_TRY(tc_describe(ctx, seed, exact, first, B, Mout, &one));
     const unsigned long long tiles = (B + kTileM - 1) / kTileM;
-    return launch_kb(ctx, ctx->kb, ctx->stream, ctx->num_sms, one, nullptr, nullptr, 1, tiles, ctx->dev_counters + 12);
+    const int cfg = chosen_cfg(ctx->device, ctx->kb, one.nchunks, false);
+    return launch_cfg(cfg, ctx, ctx->stream, ctx->num_sms, one, nullptr, nullptr, 1, tiles, ctx->dev_counters + 12);
 }
 
 // One persistent launch over E experiments: `table` (device, E entries) describes them,
 // `prefix` (device, E + 1 entries) holds the first global tile of each. kbmax bounds their
-// Philox blocks per lane; the launch goes to `stream`. Errors from bounded waits go to *err
-// (device).
+// Philox blocks per lane and nchmax their covariate chunks; the launch goes to `stream`.
+// Errors from bounded waits go to *err (device).
 frr_status balance_tc_batch_launch(frr_ctx* owner, cudaStream_t stream, const TcExp* table,
                                    const unsigned long long* prefix, int E, unsigned long long tiles, int kbmax,
-                                   int* err)
+                                   int nchmax, int* err)
 {
     if (tiles == 0) return FRR_OK;
     TcExp unused{};
-    return launch_kb(owner, kbmax, stream, owner->num_sms, unused, table, prefix, E, tiles, err);
+    const int cfg = chosen_cfg(owner->device, kbmax, nchmax, true);
+    return launch_cfg(cfg, owner, stream, owner->num_sms, unused, table, prefix, E, tiles, err);
+}
+
+// Times every configuration for kbmax on a (probe) batch described like the launch above
+// and makes the fastest the choice for batches of this shape class.
+frr_status balance_tc_batch_tune(frr_ctx* owner, cudaStream_t stream, const TcExp* table,
+                                 const unsigned long long* prefix, int E, unsigned long long tiles, int kbmax,
+                                 int nchmax, int* err)
+{
+    if (tiles == 0) return FRR_OK;
+    TcExp unused{};
+    int best = -1;
+    float best_ms = INFINITY;
+    for (int c = 0; c < kNumCfg; ++c) {
+        if (kCfg[c].kb != kbmax) continue;
+        float ms = INFINITY;
+        FRR_TRY(time_cfg(owner, stream, c, 2,
+                         [&](int cfg) {
+                             return launch_cfg(cfg, owner, stream, owner->num_sms, unused, table, prefix, E, tiles,
+                                               err);
+                         },
+                         &ms));
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    if (best < 0) return FRR_E_UNSUPPORTED;
+    remember_cfg(owner->device, kbmax, nchmax, true, best);
+    return FRR_OK;
 }
 
 }  // namespace frr
+
+using namespace frr;
+
+extern "C" frr_status frr_autotune(frr_ctx* ctx, uint64_t B_probe, frr_tune_result* out)
+{
+    if (!ctx || !out || B_probe > (1ull << 24)) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    if (ctx->opts.precision != FRR_SPLIT_BF16) return FRR_E_UNSUPPORTED;
+    if (B_probe == 0) B_probe = 8ull * kTileM * (uint64_t)ctx->num_sms;
+    std::memset(out, 0, sizeof(*out));
+    const size_t bytes = (size_t)B_probe * sizeof(float);
+    FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->Mhat), &ctx->Mhat_bytes, 2 * bytes));
+    float* ref = ctx->Mhat;
+    float* cmp = ctx->Mhat + B_probe;
+    TcExp one;
+    constexpr uint64_t kProbeSeed = 0x7E57C0DEull;
+    FRR_TRY(tc_describe(ctx, kProbeSeed, false, 0, B_probe, ref, &one));
+    const unsigned long long tiles = (B_probe + kTileM - 1) / kTileM;
+    std::vector<float> h_ref(B_probe), h_cmp(B_probe);
+    out->kb = ctx->kb;
+    out->chunks = one.nchunks;
+    int best = -1, best_i = -1;
+    float best_ms = INFINITY;
+    for (int c = 0; c < kNumCfg; ++c) {
+        if (kCfg[c].kb != ctx->kb || out->candidates >= FRR_TUNE_MAX) continue;
+        const int i = out->candidates++;
+        one.Mout = (i == 0) ? ref : cmp;
+        float ms = INFINITY;
+        FRR_TRY(time_cfg(ctx, ctx->stream, c, 3,
+                         [&](int cfg) {
+                             return launch_cfg(cfg, ctx, ctx->stream, ctx->num_sms, one, nullptr, nullptr, 1, tiles,
+                                               ctx->dev_counters + 12);
+                         },
+                         &ms));
+        FRR_TRY(take_device_error(ctx));
+        // every configuration must reproduce the first one's M_hat bit for bit
+        FRR_TRY(copy_out(ctx, i == 0 ? h_ref.data() : h_cmp.data(), one.Mout, bytes));
+        if (i > 0 && std::memcmp(h_ref.data(), h_cmp.data(), bytes) != 0) return FRR_E_MISMATCH;
+        out->ng[i] = kCfg[c].ng;
+        out->sb[i] = kCfg[c].sb;
+        out->ms[i] = ms;
+        if (ms < best_ms) { best_ms = ms; best = c; best_i = i; }
+    }
+    if (best < 0) return FRR_E_UNSUPPORTED;
+    out->chosen = best_i;
+    remember_cfg(ctx->device, ctx->kb, one.nchunks, false, best);
+    return FRR_OK;
+}

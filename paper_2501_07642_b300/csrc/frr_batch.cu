@@ -24,7 +24,10 @@ namespace frr {
 frr_status tc_describe(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout, TcExp* x);
 frr_status balance_tc_batch_launch(frr_ctx* owner, cudaStream_t stream, const TcExp* table,
                                    const unsigned long long* prefix, int E, unsigned long long tiles, int kbmax,
-                                   int* err);
+                                   int nchmax, int* err);
+frr_status balance_tc_batch_tune(frr_ctx* owner, cudaStream_t stream, const TcExp* table,
+                                 const unsigned long long* prefix, int E, unsigned long long tiles, int kbmax,
+                                 int nchmax, int* err);
 
 }  // namespace frr
 
@@ -54,6 +57,7 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
     frr_default_opts(&base);
     if (opts) base = *opts;
     if (base.precision != FRR_SPLIT_BF16 && base.precision != FRR_F32) return FRR_E_ARG;
+    if (base.autotune != 0 && base.autotune != 1) return FRR_E_ARG;
     const auto t0 = std::chrono::steady_clock::now();
     std::vector<frr_ctx*> ctx((size_t)E, nullptr);
     frr_status first_err = FRR_OK;
@@ -132,13 +136,27 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
         if (rc == FRR_OK && base.precision == FRR_SPLIT_BF16) {
             std::vector<TcExp> table(live.size());
             std::vector<unsigned long long> prefix(live.size() + 1, 0);
-            int kbmax = 1;
+            int kbmax = 1, nchmax = 1;
             for (size_t k = 0; k < live.size() && rc == FRR_OK; ++k) {
                 const frr_experiment& x = ex[live[k]];
                 rc = tc_describe(ctx[live[k]], x.seed, x.seed == FRR_EXACT_SEED, x.first_draw, x.B, mhat + off[k],
                                  &table[k]);
                 prefix[k + 1] = prefix[k] + (x.B + 127) / 128;
                 if (ctx[live[k]]->kb > kbmax) kbmax = ctx[live[k]]->kb;
+                if (table[k].nchunks > nchmax) nchmax = table[k].nchunks;
+            }
+            // probe batch for the tuner: every experiment with about 1/16 of its draws
+            std::vector<TcExp> probe;
+            std::vector<unsigned long long> probe_prefix;
+            if (rc == FRR_OK && base.autotune) {
+                probe = table;
+                probe_prefix.assign(live.size() + 1, 0);
+                for (size_t k = 0; k < live.size(); ++k) {
+                    const uint64_t tiles_k = (probe[k].B + 127) / 128;
+                    const uint64_t pt = std::max<uint64_t>(1, tiles_k / 16);
+                    probe[k].B = std::min<uint64_t>(probe[k].B, pt * 128);
+                    probe_prefix[k + 1] = probe_prefix[k] + pt;
+                }
             }
             if (rc == FRR_OK &&
                 (cudaMalloc(&d_table, table.size() * sizeof(TcExp)) != cudaSuccess ||
@@ -147,6 +165,22 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
                 cudaGetLastError();
                 rc = FRR_E_NOMEM;
             }
+            if (rc == FRR_OK && base.autotune) {
+                cudaMemcpyAsync(d_table, probe.data(), probe.size() * sizeof(TcExp), cudaMemcpyHostToDevice, stream);
+                cudaMemcpyAsync(d_prefix, probe_prefix.data(), probe_prefix.size() * sizeof(unsigned long long),
+                                cudaMemcpyHostToDevice, stream);
+                cudaMemsetAsync(d_err, 0, sizeof(int), stream);
+                rc = balance_tc_batch_tune(owner, stream, d_table, d_prefix, (int)live.size(), probe_prefix.back(),
+                                           kbmax, nchmax, d_err);
+                int herr = 0;
+                if (rc == FRR_OK && (cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+                                     cudaStreamSynchronize(stream) != cudaSuccess)) {
+                    cudaGetLastError();
+                    rc = FRR_E_CUDA;
+                } else if (rc == FRR_OK && herr != 0) {
+                    rc = FRR_E_TIMEOUT;
+                }
+            }
             if (rc == FRR_OK) {
                 cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(TcExp), cudaMemcpyHostToDevice, stream);
                 cudaMemcpyAsync(d_prefix, prefix.data(), prefix.size() * sizeof(unsigned long long),
@@ -154,7 +188,7 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
                 cudaMemsetAsync(d_err, 0, sizeof(int), stream);
                 cudaEventRecord(ea, stream);
                 rc = balance_tc_batch_launch(owner, stream, d_table, d_prefix, (int)live.size(), prefix.back(), kbmax,
-                                             d_err);
+                                             nchmax, d_err);
                 cudaEventRecord(eb, stream);
                 int herr = 0;
                 if (cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
@@ -187,7 +221,12 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             for (size_t k = (size_t)w; k < live.size(); k += (size_t)nw) {
                 const int64_t e = live[k];
                 frr_experiment& x = ex[e];
-                if (rc != FRR_OK) { st_sel[k] = rc; continue; }
+                if (rc != FRR_OK) {
+                    st_sel[k] = rc;
+                    frr_destroy(ctx[e]);
+                    ctx[e] = nullptr;
+                    continue;
+                }
                 frr_status s = stream_begin(ctx[e], x.seed, x.q, x.threshold, x.B);
                 if (s == FRR_OK) s = stream_chunk_precomputed(ctx[e], x.first_draw, x.B, mhat + off[k]);
                 int64_t K = 0;
@@ -203,6 +242,9 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
                     }
                 }
                 st_sel[k] = s;
+                // released here, in parallel, rather than one by one at the end
+                frr_destroy(ctx[e]);
+                ctx[e] = nullptr;
             }
         };
         run_workers(nw, finish);

@@ -152,6 +152,7 @@ void frr_default_opts(frr_opts* o)
     o->ridge = 0.1;
     o->band_safety = 2.0;
     o->cuda_stream = nullptr;
+    o->autotune = 0;
 }
 
 const char* frr_strerror(frr_status s)
@@ -167,6 +168,7 @@ const char* frr_strerror(frr_status s)
         case FRR_E_RANGE: return "draw range out of bounds";
         case FRR_E_STATE: return "call out of sequence";
         case FRR_E_UNSUPPORTED: return "shape not covered by the compiled kernels";
+        case FRR_E_MISMATCH: return "two kernel configurations disagreed on the same input";
     }
     return "unknown status";
 }

@@ -80,70 +80,142 @@ __global__ void k_diag(const double* __restrict__ S, int d, int whiten, double r
 // bit for bit while the work runs in parallel.
 constexpr int kP = 32;
 
-// Panel [k0, k0 + pw) of the Cholesky factor, in place in A (row-major d x d, lower part:
-// working values, final L on exit). Each CTA (one warp, so that the rows spread over many
-// SMs: FP64 throughput per SM is low) factors the pw x pw diagonal block (lane r owns row
-// k0 + r), then finishes its own 32 rows below the block.
-__global__ void __launch_bounds__(32)
-k_chol_panel(double* __restrict__ A, int d, int k0, int pw, double tol_abs, int* __restrict__ status)
+// The panel kernels work on groups of 32 rows with lane = row; the pw <= 32 panel columns are
+// spread over kPW warps (warp w owns columns w, w + kPW, ...), so that the independent updates
+// of a step run on several warps at once: B300 issues a warp's FP64 instructions about one per
+// 64 cycles, so one warp per row group (all 32 columns in one thread) is issue-bound. Each
+// step publishes the finished column through shared memory; the owner of the next column
+// updates and finishes that column first (look-ahead), then the other owned columns follow.
+constexpr int kPW = 8;
+constexpr int kPC = kP / kPW;  // columns per warp
+
+// RN(a / b) from y = RN(1 / b) by Markstein's method (P. Markstein, IBM J. Res. Dev. 34(1),
+// 1990): from a quotient within one ulp of a / b, q + (a - b q) y rounded once (FMA, with the
+// residual a - b q exact) is the correctly rounded quotient; one correction step from RN(a y)
+// supplies such a quotient. The intermediate values must neither underflow nor overflow, so
+// operands outside a safe exponent range (zero and subnormals included) use the division
+// operator. Five dependent FP64 operations instead of a division.
+__device__ __forceinline__ double div_rn_recip(double a, double b, double y)
 {
-    // Right-looking inside the panel: as soon as column kk is final, every later entry of
-    // the row subtracts its kk-th term. Each entry still receives its subtractions in
-    // ascending kk (the same operations as the column-by-column definition), but the long
-    // dependent chains overlap: B300's FP64 latency (about 64 cycles an add, several
-    // hundred a division) otherwise dominates.
-    __shared__ double Lb[kP][kP + 1];  // L_{k0+jj, k0+kk}, kk <= jj
-    const int tid = threadIdx.x;
-    {
-        const int r = k0 + tid;
-        double t[kP];
+    const int ea = (__double2hiint(a) >> 20) & 0x7ff, eb = (__double2hiint(b) >> 20) & 0x7ff;
+    if (ea < 1023 - 900 || ea > 1023 + 900 || eb < 1023 - 400 || eb > 1023 + 400) return __ddiv_rn(a, b);
+    const double q0 = __dmul_rn(a, y);
+    const double r0 = __fma_rn(-q0, b, a);
+    const double q1 = __fma_rn(r0, y, q0);
+    const double r1 = __fma_rn(-q1, b, a);
+    return __fma_rn(r1, y, q1);
+}
+
+// Right-looking elimination of one 32-row group (lane = row, t[c] = column w + kPW c) against a
+// finished lower-triangular pw x pw block: for jj ascending, t_jj /= L_jj,jj, then
+// t_kk -= L_kk,jj t_jj for jj < kk < pw. Every entry gets its subtractions in ascending jj and
+// then its division, as in the column-by-column definition. Lc[jj][kk] = L_{kk,jj} (kk >= jj),
+// Ld / Yd the diagonal and its reciprocals, Zs[jj][lane] the exchange of finished columns.
+__device__ __forceinline__ void eliminate_rows(double (&t)[kPC], int pw, const double (*Lc)[kP + 1],
+                                               const double* Ld, const double* Yd, double (*Zs)[32], int w, int lane)
+{
+    if (w == 0) {
+        t[0] = div_rn_recip(t[0], Ld[0], Yd[0]);
+        Zs[0][lane] = t[0];
+    }
+    for (int jj = 0; jj < pw; ++jj) {
+        __syncthreads();
+        const double z = Zs[jj][lane];
+        const int nxt = jj + 1;
+        if (nxt < pw && w == nxt % kPW) {
 #pragma unroll
-        for (int kk = 0; kk < kP; ++kk) t[kk] = (tid < pw && kk <= tid) ? A[(size_t)r * d + k0 + kk] : 0.0;
-        // t[tid] is the pivot candidate of row tid (its diagonal), t[kk < tid] the row's entries
-#pragma unroll
-        for (int jj = 0; jj < kP; ++jj) {
-            if (jj >= pw) break;
-            if (tid == jj) {
-                if (!(t[jj] > tol_abs)) atomicExch(status, 1);
-                t[jj] = __dsqrt_rn(t[jj] > 0.0 ? t[jj] : 1.0);
-                Lb[jj][jj] = t[jj];
-            }
-            __syncwarp();
-            if (tid > jj && tid < pw) t[jj] = __ddiv_rn(t[jj], Lb[jj][jj]);
-            if (tid >= jj && tid < pw) Lb[tid][jj] = t[jj];
-            __syncwarp();
-            // row tid: subtract the jj-th term from its later entries (kk in (jj, tid]) --
-            // the diagonal entry subtracts its square
-            if (tid > jj && tid < pw) {
-#pragma unroll
-                for (int kk = 0; kk < kP; ++kk)
-                    if (kk > jj && kk <= tid) t[kk] = __dsub_rn(t[kk], __dmul_rn(t[jj], Lb[kk][jj]));
-            }
-            __syncwarp();
+            for (int c = 0; c < kPC; ++c)
+                if (w + kPW * c == nxt) {
+                    t[c] = div_rn_recip(__dsub_rn(t[c], __dmul_rn(Lc[jj][nxt], z)), Ld[nxt], Yd[nxt]);
+                    Zs[nxt][lane] = t[c];
+                }
         }
-        if (blockIdx.x == 0 && tid < pw) {
 #pragma unroll
-            for (int kk = 0; kk < kP; ++kk)
-                if (kk <= tid) A[(size_t)r * d + k0 + kk] = t[kk];
+        for (int c = 0; c < kPC; ++c) {
+            const int kk = w + kPW * c;
+            if (kk > nxt && kk < pw) t[c] = __dsub_rn(t[c], __dmul_rn(Lc[jj][kk], z));
+        }
+    }
+}
+
+// Panel [k0, k0 + pw) of the Cholesky factor, in place in A (row-major d x d, lower part:
+// working values, final L on exit). Every CTA factors the pw x pw diagonal block (lane = row
+// of the block) and then finishes its own 32 rows below it; CTA 0 writes the block back.
+__global__ void __launch_bounds__(kP * kPW)
+k_chol_panel(double* __restrict__ A, int d, int k0, int pw, const double* __restrict__ scal, int* __restrict__ status)
+{
+    const double tol_abs = __dmul_rn(1e-12, scal[1]);  // pivot tolerance relative to max S_jj
+    __shared__ double Lc[kP][kP + 1];  // Lc[jj][r] = L_{k0+r, k0+jj}, r >= jj
+    __shared__ double Zs[kP][32];
+    __shared__ double Ld[kP], Yd[kP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double t[kPC];
+    {
+        // ---- diagonal block, right-looking: at step jj the pivot becomes L_jj,jj, the rows
+        // below divide by it, and every later entry (kk, r) with jj < kk <= r subtracts
+        // L_r,jj L_kk,jj (the diagonal entry subtracts a square)
+        const int r = lane;
+#pragma unroll
+        for (int c = 0; c < kPC; ++c) {
+            const int kk = w + kPW * c;
+            t[c] = (r < pw && kk <= r) ? A[(size_t)(k0 + r) * d + k0 + kk] : 0.0;
+        }
+        // finish column j held in tc by its owner warp: pivot on lane j, division below it
+        auto finish_col = [&](double& tc, int j) {
+            double piv = 0.0;
+            if (lane == j) {
+                if (!(tc > tol_abs)) atomicExch(status, 1);
+                piv = __dsqrt_rn(tc > 0.0 ? tc : 1.0);
+                Ld[j] = piv;
+            }
+            piv = __shfl_sync(0xffffffffu, piv, j);
+            if (lane == j) tc = piv;
+            else if (lane > j && lane < pw) tc = __ddiv_rn(tc, piv);
+            if (lane >= j && lane < pw) Lc[j][lane] = tc;
+        };
+        if (w == 0) finish_col(t[0], 0);
+        for (int jj = 0; jj < pw; ++jj) {
+            __syncthreads();
+            const double lrj = (r >= jj && r < pw) ? Lc[jj][r] : 0.0;
+            const int nxt = jj + 1;
+            if (nxt < pw && w == nxt % kPW) {
+#pragma unroll
+                for (int c = 0; c < kPC; ++c)
+                    if (w + kPW * c == nxt) {
+                        if (r >= nxt && r < pw) t[c] = __dsub_rn(t[c], __dmul_rn(lrj, Lc[jj][nxt]));
+                        finish_col(t[c], nxt);
+                    }
+            }
+#pragma unroll
+            for (int c = 0; c < kPC; ++c) {
+                const int kk = w + kPW * c;
+                if (kk > nxt && kk < pw && r >= kk && r < pw) t[c] = __dsub_rn(t[c], __dmul_rn(lrj, Lc[jj][kk]));
+            }
+        }
+        if (blockIdx.x == 0) {
+#pragma unroll
+            for (int c = 0; c < kPC; ++c) {
+                const int kk = w + kPW * c;
+                if (r < pw && kk <= r) A[(size_t)(k0 + r) * d + k0 + kk] = t[c];
+            }
         }
     }
     __syncthreads();
-    const int r = k0 + pw + blockIdx.x * blockDim.x + tid;
-    if (r >= d) return;
-    double t[kP];
+    if (threadIdx.x < pw) Yd[threadIdx.x] = __ddiv_rn(1.0, Ld[threadIdx.x]);
+    // ---- this CTA's 32 rows below the block
+    const int r = k0 + pw + blockIdx.x * 32 + lane;
 #pragma unroll
-    for (int kk = 0; kk < kP; ++kk) t[kk] = kk < pw ? A[(size_t)r * d + k0 + kk] : 0.0;
-#pragma unroll
-    for (int jj = 0; jj < kP; ++jj) {
-        if (jj >= pw) break;
-        t[jj] = __ddiv_rn(t[jj], Lb[jj][jj]);
-#pragma unroll
-        for (int kk = 0; kk < kP; ++kk)
-            if (kk > jj && kk < pw) t[kk] = __dsub_rn(t[kk], __dmul_rn(t[jj], Lb[kk][jj]));
+    for (int c = 0; c < kPC; ++c) {
+        const int kk = w + kPW * c;
+        t[c] = (r < d && kk < pw) ? A[(size_t)r * d + k0 + kk] : 0.0;
     }
+    __syncthreads();
+    eliminate_rows(t, pw, Lc, Ld, Yd, Zs, w, lane);
 #pragma unroll
-    for (int kk = 0; kk < kP; ++kk)
-        if (kk < pw) A[(size_t)r * d + k0 + kk] = t[kk];
+    for (int c = 0; c < kPC; ++c) {
+        const int kk = w + kPW * c;
+        if (r < d && kk < pw) A[(size_t)r * d + k0 + kk] = t[c];
+    }
 }
 
 // Trailing update after panel [k0, k0 + pw): A_ij -= L_ik L_jk for k in the panel (ascending),
@@ -173,33 +245,39 @@ k_chol_trailing(double* __restrict__ A, int d, int k0, int pw)
 }
 
 // Panel [k0, k0 + pw) of the forward substitution Zc = Xc L^{-T}, in place in T (n x d
-// row-major: working values, final Zc on exit); one thread per row, one warp per CTA.
-__global__ void __launch_bounds__(32)
+// row-major: working values, final Zc on exit): 32 rows per CTA, eliminated against the
+// panel's diagonal block of L (z_ij = (t_ij - sum_{k<j} L_jk z_ik) / L_jj, subtractions in
+// ascending k).
+__global__ void __launch_bounds__(kP * kPW)
 k_fwd_panel(double* __restrict__ T, const double* __restrict__ L, int n, int d, int k0, int pw)
 {
-    __shared__ double Lb[kP][kP + 1];
+    __shared__ double Lc[kP][kP + 1];  // Lc[jj][kk] = L_{k0+kk, k0+jj}, kk >= jj
+    __shared__ double Zs[kP][32];
+    __shared__ double Ld[kP], Yd[kP];
     for (int e = threadIdx.x; e < kP * kP; e += blockDim.x) {
         const int jj = e / kP, kk = e % kP;
-        Lb[jj][kk] = (jj < pw && kk <= jj) ? L[(size_t)(k0 + jj) * d + k0 + kk] : 0.0;
+        Lc[jj][kk] = (kk < pw && kk >= jj) ? L[(size_t)(k0 + kk) * d + k0 + jj] : 0.0;
+    }
+    if (threadIdx.x < pw) {
+        const double l = L[(size_t)(k0 + threadIdx.x) * d + k0 + threadIdx.x];
+        Ld[threadIdx.x] = l;
+        Yd[threadIdx.x] = __ddiv_rn(1.0, l);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    double t[kPC];
+#pragma unroll
+    for (int c = 0; c < kPC; ++c) {
+        const int kk = w + kPW * c;
+        t[c] = (i < n && kk < pw) ? T[(size_t)i * d + k0 + kk] : 0.0;
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double t[kP];
+    eliminate_rows(t, pw, Lc, Ld, Yd, Zs, w, lane);
 #pragma unroll
-    for (int kk = 0; kk < kP; ++kk) t[kk] = kk < pw ? T[(size_t)i * d + k0 + kk] : 0.0;
-#pragma unroll
-    for (int jj = 0; jj < kP; ++jj) {
-        if (jj >= pw) break;
-        double v = t[jj];
-#pragma unroll
-        for (int kk = 0; kk < kP; ++kk)
-            if (kk < jj) v = __dsub_rn(v, __dmul_rn(Lb[jj][kk], t[kk]));
-        t[jj] = __ddiv_rn(v, Lb[jj][jj]);
+    for (int c = 0; c < kPC; ++c) {
+        const int kk = w + kPW * c;
+        if (i < n && kk < pw) T[(size_t)i * d + k0 + kk] = t[c];
     }
-#pragma unroll
-    for (int kk = 0; kk < kP; ++kk)
-        if (kk < pw) T[(size_t)i * d + k0 + kk] = t[kk];
 }
 
 // T_ij -= L_jk z_ik for k in panel [k0, k0 + pw) (ascending), j >= k0 + pw. 32 x 32 tiles.
@@ -234,8 +312,10 @@ __global__ void k_init_A(const double* __restrict__ S, const double* __restrict_
 }
 
 // diagonal whitening: L = diag(sqrt(S_jj)) stored row-major (zero elsewhere)
-__global__ void k_diag_L(const double* __restrict__ S, int d, double tol_abs, double* __restrict__ A, int* status)
+__global__ void k_diag_L(const double* __restrict__ S, int d, const double* __restrict__ scal, double* __restrict__ A,
+                         int* status)
 {
+    const double tol_abs = __dmul_rn(1e-12, scal[1]);
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)d * d) return;
     const int i = (int)(idx / d), j = (int)(idx % d);
@@ -391,6 +471,20 @@ BandConsts band_from_eps(const std::vector<double>& eps, double c_M, int64_t d)
 
 }  // namespace
 
+// C(c, m) for c, m < 64 at [c * 64 + m] (Pascal's rule; every entry fits in 64 bits), built once
+const uint64_t* binom_table()
+{
+    static const std::vector<uint64_t> tab = [] {
+        std::vector<uint64_t> t(64 * 64, 0);
+        for (int c = 0; c < 64; ++c) {
+            t[(size_t)c * 64] = 1;
+            for (int m = 1; m <= c; ++m) t[(size_t)c * 64 + m] = t[(size_t)(c - 1) * 64 + m - 1] + t[(size_t)(c - 1) * 64 + m];
+        }
+        return t;
+    }();
+    return tab.data();
+}
+
 frr_status prep_run(frr_ctx* ctx, const double* X_host)
 {
     const int n = (int)ctx->n, d = (int)ctx->d;
@@ -428,18 +522,17 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
     k_diag<<<1, 1, 0, s>>>(S, d, ctx->opts.whiten, ctx->opts.ridge, Adiag, scal);
     PREP_CHECK(cudaGetLastError());
     {
-        double sc[2];
-        PREP_CHECK(cudaMemcpyAsync(sc, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        PREP_CHECK(cudaStreamSynchronize(s));
-        const double tol_abs = 1e-12 * sc[1];
+        // The pivot tolerance is read on the device (scal[1] = max S_jj), and a failed pivot is
+        // only flagged (the factorisation goes on with a unit pivot, so every later value stays
+        // finite): the host learns both at the single synchronisation at the end.
         const size_t dd = (size_t)d * d;
         // forward substitution in place on a copy of Xc (ZT holds n x d row-major here)
         PREP_CHECK(cudaMemcpyAsync(ZT, Xc, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
         if (ctx->opts.whiten == FRR_DIAG) {
-            k_diag_L<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(S, d, tol_abs, Lm, status);
+            k_diag_L<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(S, d, scal, Lm, status);
             for (int k0 = 0; k0 < d; k0 += kP) {
                 const int pw = (d - k0) < kP ? (d - k0) : kP;
-                k_fwd_panel<<<ceil_div(n, 32), 32, 0, s>>>(ZT, Lm, n, d, k0, pw);
+                k_fwd_panel<<<ceil_div(n, 32), kP * kPW, 0, s>>>(ZT, Lm, n, d, k0, pw);
                 const int right = d - k0 - pw;
                 if (right > 0)
                     k_fwd_trailing<<<dim3(ceil_div(right, 32), ceil_div(n, 32)), 256, 0, s>>>(ZT, Lm, n, d, k0, pw);
@@ -458,10 +551,10 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
             for (int p = 0, k0 = 0; k0 < d; ++p, k0 += kP) {
                 const int pw = (d - k0) < kP ? (d - k0) : kP;
                 const int below = d - k0 - pw;
-                k_chol_panel<<<below > 0 ? ceil_div(below, 32) : 1, 32, 0, s>>>(Lm, d, k0, pw, tol_abs, status);
+                k_chol_panel<<<below > 0 ? ceil_div(below, 32) : 1, kP * kPW, 0, s>>>(Lm, d, k0, pw, scal, status);
                 PREP_CHECK(cudaEventRecord(evs[p], s));
                 PREP_CHECK(cudaStreamWaitEvent(ctx->aux, evs[p], 0));
-                k_fwd_panel<<<ceil_div(n, 32), 32, 0, ctx->aux>>>(ZT, Lm, n, d, k0, pw);
+                k_fwd_panel<<<ceil_div(n, 32), kP * kPW, 0, ctx->aux>>>(ZT, Lm, n, d, k0, pw);
                 if (below > 0) {
                     const int tiles = ceil_div(below, 32);
                     k_chol_trailing<<<dim3(tiles, tiles), 256, 0, s>>>(Lm, d, k0, pw);
@@ -474,10 +567,6 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
             for (auto& e : evs) cudaEventDestroy(e);
         }
         PREP_CHECK(cudaGetLastError());
-        int st = 0;
-        PREP_CHECK(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-        PREP_CHECK(cudaStreamSynchronize(s));
-        if (st != 0) { rc = FRR_E_DEGENERATE; goto cleanup; }
     }
     PREP_CHECK(cudaMemcpyAsync(ctx->Zc64, ZT, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
     k_qexp<<<ceil_div(d, 128), 128, 0, s>>>(ctx->Zc64, n, d, ctx->qexp);
@@ -492,20 +581,21 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host)
     k_digits<<<(unsigned)(((size_t)ctx->kpad * d + 255) / 256), 256, 0, s>>>(ctx->Q, ctx->kpad, d, ctx->Zq);
     k_band_cols<<<d, 256, 0, s>>>(ctx->Zc64, n, d, (int)ctx->n1, ctx->kused, eps, eps + d);
     PREP_CHECK(cudaGetLastError());
+    // binomial table for exact enumeration (only shapes that allow it read it); the host
+    // table is static, so the copy needs no synchronisation
+    if (n <= kExactMaxN)
+        PREP_CHECK(cudaMemcpyAsync(ctx->binom, binom_table(), 64 * 64 * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
     {
+        // the single synchronisation of the preparation: pivot status and band inputs
         std::vector<double> e32(d), etc(d);
+        int st = 0;
+        PREP_CHECK(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
         PREP_CHECK(cudaMemcpyAsync(e32.data(), eps, d * sizeof(double), cudaMemcpyDeviceToHost, s));
         PREP_CHECK(cudaMemcpyAsync(etc.data(), eps + d, d * sizeof(double), cudaMemcpyDeviceToHost, s));
         PREP_CHECK(cudaStreamSynchronize(s));
+        if (st != 0) { rc = FRR_E_DEGENERATE; goto cleanup; }
         ctx->band32 = band_from_eps(e32, ctx->c_M, d);
         ctx->band_tc = band_from_eps(etc, ctx->c_M, d);
-    }
-    {
-        std::vector<uint64_t> tab(64 * 64);
-        for (int c = 0; c < 64; ++c)
-            for (int m = 0; m < 64; ++m) tab[c * 64 + m] = binom_host(c, m);
-        PREP_CHECK(cudaMemcpyAsync(ctx->binom, tab.data(), tab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
-        PREP_CHECK(cudaStreamSynchronize(s));
     }
 
 cleanup:

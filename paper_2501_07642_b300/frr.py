@@ -20,7 +20,7 @@ LIB_PATH = Path(__file__).resolve().parent / "libfrr.so"
 FRR_OK = 0
 STATUS = {0: "FRR_OK", -1: "FRR_E_ARG", -2: "FRR_E_DEGENERATE", -3: "FRR_E_CUDA", -4: "FRR_E_NOMEM",
           -5: "FRR_E_TIMEOUT", -6: "FRR_E_CAPACITY", -7: "FRR_E_RANGE", -8: "FRR_E_STATE",
-          -9: "FRR_E_UNSUPPORTED"}
+          -9: "FRR_E_UNSUPPORTED", -10: "FRR_E_MISMATCH"}
 FRR_SPLIT_BF16, FRR_F32 = 0, 1
 FRR_CHOL, FRR_RIDGE, FRR_DIAG = 0, 1, 2
 FRR_EXACT_SEED = (1 << 64) - 1
@@ -37,7 +37,7 @@ class FrrError(RuntimeError):
 
 class frr_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("whiten", ctypes.c_int), ("ridge", ctypes.c_double),
-                ("band_safety", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
+                ("band_safety", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("autotune", ctypes.c_int)]
 
 
 class frr_stats(ctypes.Structure):
@@ -61,6 +61,14 @@ class frr_experiment(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("p_out", ctypes.c_void_p), ("count_out", ctypes.c_void_p),
                 ("ci_lo", ctypes.c_double), ("ci_hi", ctypes.c_double), ("K_out", ctypes.c_int64),
                 ("status", ctypes.c_int)]
+
+
+TUNE_MAX = 8
+
+
+class frr_tune_result(ctypes.Structure):
+    _fields_ = [("kb", ctypes.c_int), ("chunks", ctypes.c_int), ("candidates", ctypes.c_int), ("chosen", ctypes.c_int),
+                ("ng", ctypes.c_int * TUNE_MAX), ("sb", ctypes.c_int * TUNE_MAX), ("ms", ctypes.c_float * TUNE_MAX)]
 
 
 class frr_batch_stats(ctypes.Structure):
@@ -115,6 +123,7 @@ def lib():
             "frr_whitened": (c.c_int, [P, P]),
             "frr_last_stats": (c.c_int, [P, P]),
             "frr_batch_run": (c.c_int, [P, I64, P, P]),
+            "frr_autotune": (c.c_int, [P, U64, P]),
             "frr_diagnose": (c.c_int, [P, P]),
             "frr_fast_distance": (c.c_int, [P, I64, P, I64, I64, c.c_int, P, P]),
         }
@@ -299,10 +308,22 @@ def frr_last_stats(ctx: Context) -> dict:
     return s.as_dict()
 
 
-def frr_batch_run(experiments, precision: str = "split_bf16", band_safety: float = 2.0, stream=None):
+def frr_autotune(ctx: Context, B_probe: int = 0) -> dict:
+    """Times the compiled configurations of the split-BF16 balance kernel for this context's
+    shape class and makes the fastest the one used from now on (process-wide)."""
+    r = frr_tune_result()
+    _check(lib().frr_autotune(ctx.handle, int(B_probe), ctypes.byref(r)), "frr_autotune")
+    c = r.candidates
+    return {"kb": r.kb, "chunks": r.chunks, "chosen": r.chosen, "ng": list(r.ng[:c]), "sb": list(r.sb[:c]),
+            "ms": list(r.ms[:c])}
+
+
+def frr_batch_run(experiments, precision: str = "split_bf16", band_safety: float = 2.0, stream=None,
+                  autotune: bool = False):
     """experiments: list of dicts with keys X, n1, seed, B (and optional first_draw, q or
     threshold, whiten, ridge, Y, tau, alpha). Returns (list of result dicts, stats dict).
-    Outputs are host numpy arrays."""
+    Outputs are host numpy arrays. autotune: time the kernel configurations on a probe of
+    the batch first (cached per shape class)."""
     E = len(experiments)
     arr = (frr_experiment * E)()
     keep = []
@@ -346,6 +367,7 @@ def frr_batch_run(experiments, precision: str = "split_bf16", band_safety: float
     opts.precision = PRECISION[precision]
     opts.band_safety = float(band_safety)
     opts.cuda_stream = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    opts.autotune = 1 if autotune else 0
     st = frr_batch_stats()
     rc = lib().frr_batch_run(ctypes.addressof(arr), E, ctypes.byref(opts), ctypes.byref(st))
     res = []

@@ -79,7 +79,22 @@ def test_null_context_is_rejected(frr):
     assert L.frr_select(None, 1, 0, 10, 0.1, math.nan, None, None, 0, ctypes.byref(K)) == -1
     assert L.frr_stream_chunk(None, 0, 1) == -1
     assert L.frr_last_stats(None, None) == -1
+    r = frr.frr_tune_result()
+    assert L.frr_autotune(None, 0, ctypes.byref(r)) == -1
+    assert L.frr_autotune(None, 0, None) == -1
     L.frr_destroy(None)  # ignored
+
+
+def test_batch_rejects_bad_options_without_a_gpu(frr):
+    L = frr.lib()
+    ex = (frr.frr_experiment * 1)()
+    o = frr.frr_default_opts()
+    assert o.autotune == 0
+    o.autotune = 2
+    st = frr.frr_batch_stats()
+    assert L.frr_batch_run(ctypes.addressof(ex), 1, ctypes.byref(o), ctypes.byref(st)) == -1
+    assert L.frr_batch_run(None, 1, None, None) == -1
+    assert L.frr_batch_run(ctypes.addressof(ex), 0, None, None) == -1
 
 
 def test_fast_distance_rejects_bad_arguments_without_a_gpu(frr):

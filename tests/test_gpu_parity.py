@@ -80,7 +80,28 @@ def test_whitened_covariates_bit_exact(n, d, whiten):
     with _ctx(X, n // 2, whiten=whiten) as ctx:
         got = frr.frr_whitened(ctx)
     want, *_ = O.prep(X, whiten, 0.1)
-    assert np.array_equal(got, want)
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
+@pytest.mark.parametrize("case", ["wide_scales", "zero_column", "tiny_and_huge"])
+def test_whitened_covariates_bit_exact_extreme_magnitudes(case):
+    """Bit patterns (signed zeros included) at magnitudes that reach the divisions' safe-range
+    edges: columns scaled by powers of two far from 1, and an exactly constant column whose
+    whitened entries are exact zeros."""
+    n, d = 90, 40
+    X = ar1_covariates(n, d, 77, 0.4)
+    if case == "wide_scales":
+        X = X * np.exp2(np.linspace(-240, 240, d))[None, :]
+    elif case == "zero_column":
+        X[:, 3] = 2.5
+        X[:, 17] = 0.0
+    else:
+        X[:, : d // 2] *= 2.0 ** -300
+        X[:, d // 2:] *= 2.0 ** 300
+    with _ctx(X, n // 2, whiten="ridge") as ctx:
+        got = frr.frr_whitened(ctx)
+    want, *_ = O.prep(X, "ridge", 0.1)
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
 
 
 def test_whitened_precision_workload_bit_exact():
@@ -89,7 +110,7 @@ def test_whitened_precision_workload_bit_exact():
     with _ctx(X, w.n1, whiten="ridge") as ctx:
         got = frr.frr_whitened(ctx)
     want, *_ = O.prep(X, "ridge", 0.1)
-    assert np.array_equal(got, want)
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
 
 
 # ---------------------------------------------------------------- balance ----
