@@ -84,7 +84,9 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             ws[w] = stream;
         }
     std::vector<frr_status> st_init((size_t)E, FRR_OK);
-    auto prepare = [&](int w) {
+    // argument checks and context creation on the worker threads (each context later runs
+    // its selection on the stream of the worker that created it)
+    auto create = [&](int w) {
         for (int64_t e = w; e < E; e += nw) {
             ex[e].K_out = 0;
             ex[e].ci_lo = ex[e].ci_hi = NAN;
@@ -98,20 +100,47 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             o.whiten = ex[e].whiten;
             o.ridge = ex[e].ridge;
             o.cuda_stream = ws[w];
-            frr_status s = frr_init(&ctx[e], ex[e].X, ex[e].n, ex[e].d, ex[e].n1, &o);
-            if (s != FRR_OK) {
-                ctx[e] = nullptr;
-            } else if (ex[e].seed == FRR_EXACT_SEED &&
-                       (ex[e].n > kExactMaxN || ex[e].first_draw + ex[e].B > binom_host((int)ex[e].n, (int)ex[e].n1))) {
-                s = ex[e].n > kExactMaxN ? FRR_E_UNSUPPORTED : FRR_E_RANGE;
-                frr_destroy(ctx[e]);
-                ctx[e] = nullptr;
+            frr_status s = check_init_args(ex[e].X, ex[e].n, ex[e].d, ex[e].n1, o);
+            if (s == FRR_OK && ex[e].seed == FRR_EXACT_SEED) {
+                if (ex[e].n > kExactMaxN) s = FRR_E_UNSUPPORTED;
+                else if (ex[e].first_draw + ex[e].B > binom_host((int)ex[e].n, (int)ex[e].n1)) s = FRR_E_RANGE;
             }
+            if (s == FRR_OK) s = ctx_create(&ctx[e], ex[e].n, ex[e].d, ex[e].n1, o, false);
             st_init[e] = s;
         }
+        // the contexts' arrays come from stream-ordered allocations on this worker's stream
         if (cudaStreamSynchronize(ws[w]) != cudaSuccess) cudaGetLastError();
     };
-    run_workers(nw, prepare);
+    run_workers(nw, create);
+    {
+        // one preparation of every created context: each launch covers all of them
+        std::vector<frr_ctx*> pc;
+        std::vector<const double*> px;
+        std::vector<int64_t> pe;
+        for (int64_t e = 0; e < E; ++e)
+            if (ctx[e]) {
+                pc.push_back(ctx[e]);
+                px.push_back(ex[e].X);
+                pe.push_back(e);
+            }
+        if (!pc.empty()) {
+            cudaStream_t paux = nullptr;
+            std::vector<frr_status> pst(pc.size(), FRR_E_CUDA);
+            if (cudaStreamCreateWithFlags(&paux, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+            } else {
+                prep_run_batch(pc.data(), px.data(), (int)pc.size(), stream, paux, pst.data());
+                cudaStreamDestroy(paux);
+            }
+            for (size_t k = 0; k < pc.size(); ++k) {
+                st_init[(size_t)pe[k]] = pst[k];
+                if (pst[k] != FRR_OK) {
+                    ctx_release(ctx[(size_t)pe[k]]);
+                    ctx[(size_t)pe[k]] = nullptr;
+                }
+            }
+        }
+    }
     for (int64_t e = 0; e < E; ++e) note(e, st_init[e]);
     const auto t1 = std::chrono::steady_clock::now();
 
@@ -221,12 +250,7 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             for (size_t k = (size_t)w; k < live.size(); k += (size_t)nw) {
                 const int64_t e = live[k];
                 frr_experiment& x = ex[e];
-                if (rc != FRR_OK) {
-                    st_sel[k] = rc;
-                    frr_destroy(ctx[e]);
-                    ctx[e] = nullptr;
-                    continue;
-                }
+                if (rc != FRR_OK) { st_sel[k] = rc; continue; }
                 frr_status s = stream_begin(ctx[e], x.seed, x.q, x.threshold, x.B);
                 if (s == FRR_OK) s = stream_chunk_precomputed(ctx[e], x.first_draw, x.B, mhat + off[k]);
                 int64_t K = 0;
@@ -242,9 +266,6 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
                     }
                 }
                 st_sel[k] = s;
-                // released here, in parallel, rather than one by one at the end
-                frr_destroy(ctx[e]);
-                ctx[e] = nullptr;
             }
         };
         run_workers(nw, finish);

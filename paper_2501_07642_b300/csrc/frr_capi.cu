@@ -112,7 +112,7 @@ cudaMemPool_t temp_pool(int device)
         cudaGetLastError();
         return nullptr;
     }
-    uint64_t keep = 256ull << 20;
+    uint64_t keep = 2ull << 30;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     pools[device] = pool;
     return pool;
@@ -137,6 +137,100 @@ static void release(frr_ctx* ctx)
     cudaGetLastError();
     delete ctx;
 }
+
+// Argument checks of frr_init (also applied to every experiment of frr_batch_run).
+frr_status check_init_args(const double* X, int64_t n, int64_t d, int64_t n1, const frr_opts& o)
+{
+    if (!X) return FRR_E_ARG;
+    if (n < 2 || d < 1 || n1 < 1 || n1 > n - 1) return FRR_E_ARG;
+    if (n > kMaxN) return FRR_E_UNSUPPORTED;
+    if (o.precision != FRR_SPLIT_BF16 && o.precision != FRR_F32) return FRR_E_ARG;
+    if (o.whiten != FRR_CHOL && o.whiten != FRR_RIDGE && o.whiten != FRR_DIAG) return FRR_E_ARG;
+    if (o.whiten == FRR_RIDGE && !(o.ridge > 0.0 && isfinite(o.ridge))) return FRR_E_ARG;
+    if (!(o.band_safety >= 1.0 && isfinite(o.band_safety))) return FRR_E_ARG;
+    // non-finite entries have an all-ones exponent field; branch-free so that it vectorises
+    const uint64_t* bits = reinterpret_cast<const uint64_t*>(X);
+    const uint64_t em = 0x7ff0000000000000ull;
+    uint64_t bad = 0;
+    for (int64_t k = 0; k < n * d; ++k) bad |= (uint64_t)((bits[k] & em) == em);
+    if (bad) return FRR_E_ARG;
+    if (o.whiten == FRR_CHOL && d >= n - 1) return FRR_E_DEGENERATE;
+    return FRR_OK;
+}
+
+// A context for an (n, d, n1) experiment with checked options: streams, events and the fixed
+// arrays allocated, nothing prepared yet. with_aux: also the second stream of the preparation
+// (the batched driver prepares on streams of its own).
+frr_status ctx_create(frr_ctx** out, int64_t n, int64_t d, int64_t n1, const frr_opts& o, bool with_aux)
+{
+    *out = nullptr;
+    frr_ctx* ctx = new (std::nothrow) frr_ctx();
+    if (!ctx) return FRR_E_NOMEM;
+    ctx->n = n; ctx->d = d; ctx->n1 = n1; ctx->n0 = n - n1;
+    ctx->opts = o;
+    ctx->c_M = (double)n / ((double)n1 * (double)(n - n1));
+    const int blocks = ceil_div(n, 128);
+    int kb = 1;
+    while (kb < blocks) kb <<= 1;
+    ctx->kb = kb;
+    ctx->kused = 128 * blocks;
+    ctx->kpad = 128 * kb;
+    ctx->dpad32 = 128 * ceil_div(d, 128);
+    ctx->stats.boundary_gap_rel = NAN;
+
+    auto bail = [&](frr_status s) { release(ctx); return s; };
+#define INIT_CUDA(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) { cudaGetLastError(); \
+        return bail(_e == cudaErrorMemoryAllocation ? FRR_E_NOMEM : FRR_E_CUDA); } } while (0)
+    INIT_CUDA(cudaGetDevice(&ctx->device));
+    INIT_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (o.cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(o.cuda_stream);
+    } else {
+        INIT_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    for (cudaEvent_t& e : ctx->ev) INIT_CUDA(cudaEventCreate(&e));
+    if (with_aux) INIT_CUDA(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+    {
+        // the fixed per-context arrays in one allocation (each part 256-byte aligned)
+        const size_t nd = (size_t)n * d;
+        const size_t sizes[10] = {nd * sizeof(double),
+                                  (size_t)ctx->kpad * ctx->dpad32 * sizeof(float),
+                                  (size_t)d * ctx->kpad * sizeof(__nv_bfloat16),
+                                  (size_t)d * ctx->kpad * sizeof(__nv_bfloat16),
+                                  (size_t)ctx->kpad * d * sizeof(long long),
+                                  (size_t)d * sizeof(long long),
+                                  (size_t)d * sizeof(int),
+                                  64 * 64 * sizeof(uint64_t),
+                                  (size_t)7 * d * ctx->kpad * sizeof(__nv_bfloat16),
+                                  16 * sizeof(int)};
+        size_t offs[10], total = 0;
+        for (int i = 0; i < 10; ++i) {
+            offs[i] = total;
+            total += (sizes[i] + 255) & ~size_t(255);
+        }
+        cudaMemPool_t pool = temp_pool(ctx->device);
+        if (pool == nullptr) return bail(FRR_E_CUDA);
+        INIT_CUDA(cudaMallocFromPoolAsync(&ctx->arena, total, pool, ctx->stream));
+        char* a = static_cast<char*>(ctx->arena);
+        ctx->Zc64 = reinterpret_cast<double*>(a + offs[0]);
+        ctx->Z32 = reinterpret_cast<float*>(a + offs[1]);
+        ctx->Zhi = reinterpret_cast<__nv_bfloat16*>(a + offs[2]);
+        ctx->Zlo = reinterpret_cast<__nv_bfloat16*>(a + offs[3]);
+        ctx->Q = reinterpret_cast<long long*>(a + offs[4]);
+        ctx->Qsum = reinterpret_cast<long long*>(a + offs[5]);
+        ctx->qexp = reinterpret_cast<int*>(a + offs[6]);
+        ctx->binom = reinterpret_cast<uint64_t*>(a + offs[7]);
+        ctx->Zq = reinterpret_cast<__nv_bfloat16*>(a + offs[8]);
+        ctx->dev_counters = reinterpret_cast<int*>(a + offs[9]);
+        INIT_CUDA(cudaMemsetAsync(ctx->dev_counters, 0, 16 * sizeof(int), ctx->stream));
+    }
+#undef INIT_CUDA
+    *out = ctx;
+    return FRR_OK;
+}
+
+void ctx_release(frr_ctx* ctx) { release(ctx); }
 
 }  // namespace frr
 
@@ -177,84 +271,19 @@ frr_status frr_init(frr_ctx** out, const double* X, int64_t n, int64_t d, int64_
 {
     if (!out || !X) return FRR_E_ARG;
     *out = nullptr;
-    if (n < 2 || d < 1 || n1 < 1 || n1 > n - 1) return FRR_E_ARG;
-    if (n > kMaxN) return FRR_E_UNSUPPORTED;
     frr_opts o;
     frr_default_opts(&o);
     if (opts) o = *opts;
-    if (o.precision != FRR_SPLIT_BF16 && o.precision != FRR_F32) return FRR_E_ARG;
-    if (o.whiten != FRR_CHOL && o.whiten != FRR_RIDGE && o.whiten != FRR_DIAG) return FRR_E_ARG;
-    if (o.whiten == FRR_RIDGE && !(o.ridge > 0.0 && isfinite(o.ridge))) return FRR_E_ARG;
-    if (!(o.band_safety >= 1.0 && isfinite(o.band_safety))) return FRR_E_ARG;
-    for (int64_t k = 0; k < n * d; ++k)
-        if (!isfinite(X[k])) return FRR_E_ARG;
-    if (o.whiten == FRR_CHOL && d >= n - 1) return FRR_E_DEGENERATE;
-
+    FRR_TRY(check_init_args(X, n, d, n1, o));
     const auto t0 = std::chrono::steady_clock::now();
-    frr_ctx* ctx = new (std::nothrow) frr_ctx();
-    if (!ctx) return FRR_E_NOMEM;
-    ctx->n = n; ctx->d = d; ctx->n1 = n1; ctx->n0 = n - n1;
-    ctx->opts = o;
-    ctx->c_M = (double)n / ((double)n1 * (double)(n - n1));
-    const int blocks = ceil_div(n, 128);
-    int kb = 1;
-    while (kb < blocks) kb <<= 1;
-    ctx->kb = kb;
-    ctx->kused = 128 * blocks;
-    ctx->kpad = 128 * kb;
-    ctx->dpad32 = 128 * ceil_div(d, 128);
-
-    auto bail = [&](frr_status s) { release(ctx); return s; };
-#define INIT_CUDA(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) { cudaGetLastError(); \
-        return bail(_e == cudaErrorMemoryAllocation ? FRR_E_NOMEM : FRR_E_CUDA); } } while (0)
-    INIT_CUDA(cudaGetDevice(&ctx->device));
-    INIT_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    if (o.cuda_stream) {
-        ctx->stream = static_cast<cudaStream_t>(o.cuda_stream);
-    } else {
-        INIT_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
-        ctx->own_stream = true;
+    frr_ctx* ctx = nullptr;
+    FRR_TRY(ctx_create(&ctx, n, d, n1, o, true));
+    const frr_status s = prep_run(ctx, X);
+    if (s != FRR_OK) {
+        release(ctx);
+        return s;
     }
-    for (cudaEvent_t& e : ctx->ev) INIT_CUDA(cudaEventCreate(&e));
-    INIT_CUDA(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
-    // the fixed per-context arrays in one allocation (each part 256-byte aligned): fewer
-    // device-synchronising cudaMalloc / cudaFree calls per context
-    const size_t nd = (size_t)n * d;
-    const size_t sizes[10] = {nd * sizeof(double),
-                              (size_t)ctx->kpad * ctx->dpad32 * sizeof(float),
-                              (size_t)d * ctx->kpad * sizeof(__nv_bfloat16),
-                              (size_t)d * ctx->kpad * sizeof(__nv_bfloat16),
-                              (size_t)ctx->kpad * d * sizeof(long long),
-                              (size_t)d * sizeof(long long),
-                              (size_t)d * sizeof(int),
-                              64 * 64 * sizeof(uint64_t),
-                              (size_t)7 * d * ctx->kpad * sizeof(__nv_bfloat16),
-                              16 * sizeof(int)};
-    size_t offs[10], total = 0;
-    for (int i = 0; i < 10; ++i) {
-        offs[i] = total;
-        total += (sizes[i] + 255) & ~size_t(255);
-    }
-    cudaMemPool_t pool = temp_pool(ctx->device);
-    if (pool == nullptr) return bail(FRR_E_CUDA);
-    INIT_CUDA(cudaMallocFromPoolAsync(&ctx->arena, total, pool, ctx->stream));
-    char* a = static_cast<char*>(ctx->arena);
-    ctx->Zc64 = reinterpret_cast<double*>(a + offs[0]);
-    ctx->Z32 = reinterpret_cast<float*>(a + offs[1]);
-    ctx->Zhi = reinterpret_cast<__nv_bfloat16*>(a + offs[2]);
-    ctx->Zlo = reinterpret_cast<__nv_bfloat16*>(a + offs[3]);
-    ctx->Q = reinterpret_cast<long long*>(a + offs[4]);
-    ctx->Qsum = reinterpret_cast<long long*>(a + offs[5]);
-    ctx->qexp = reinterpret_cast<int*>(a + offs[6]);
-    ctx->binom = reinterpret_cast<uint64_t*>(a + offs[7]);
-    ctx->Zq = reinterpret_cast<__nv_bfloat16*>(a + offs[8]);
-    ctx->dev_counters = reinterpret_cast<int*>(a + offs[9]);
-    INIT_CUDA(cudaMemsetAsync(ctx->dev_counters, 0, 16 * sizeof(int), ctx->stream));
-#undef INIT_CUDA
-    frr_status s = prep_run(ctx, X);
-    if (s != FRR_OK) return bail(s);
     ctx->stats.ms_init = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    ctx->stats.boundary_gap_rel = NAN;
     *out = ctx;
     return FRR_OK;
 }

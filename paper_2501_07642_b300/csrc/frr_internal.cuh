@@ -119,7 +119,8 @@ namespace frr {
 bool is_device_ptr(const void* p);
 
 // stream-ordered memory pool of the library for short-lived temporaries on `device`; it keeps
-// up to 256 MiB reserved between calls instead of returning it at every synchronisation
+// up to 2 GiB reserved between calls instead of returning it at every synchronisation (a
+// 256-experiment batch prepares with about 1.2 GB of temporaries)
 cudaMemPool_t temp_pool(int device);
 
 // grow a device buffer to at least `bytes` (old contents are not kept)
@@ -136,7 +137,15 @@ frr_status copy_in(frr_ctx* ctx, void* dst_dev, const void* src_any, size_t byte
 frr_status copy_out(frr_ctx* ctx, void* dst_any, const void* src_dev, size_t bytes);
 
 // kernel families (defined in their own translation units)
+frr_status check_init_args(const double* X, int64_t n, int64_t d, int64_t n1, const frr_opts& o);
+frr_status ctx_create(frr_ctx** out, int64_t n, int64_t d, int64_t n1, const frr_opts& o, bool with_aux);
+void ctx_release(frr_ctx* ctx);
 frr_status prep_run(frr_ctx* ctx, const double* X_host);
+// prepares E contexts (created, arrays allocated) together on streams s and aux; st_out[e]
+// receives each one's status (FRR_E_DEGENERATE for a failed pivot); the return value is a
+// CUDA failure common to all, else FRR_OK
+frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int E, cudaStream_t s, cudaStream_t aux,
+                          frr_status* st_out);
 frr_status balance_f32_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
 frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
 frr_status balance_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);

@@ -1,4 +1,4 @@
-// frr_prep.cu -- FP64 preparation of an experiment on the GPU (runs once per frr_init).
+// frr_prep.cu -- FP64 preparation of experiments on the GPU (frr_init, frr_batch_run).
 //
 // Sec. 2.2 works with covariates that are centred and whitened so that the
 // Mahalanobis distance is Euclidean (App. A, remark on general Sigma_X):
@@ -14,63 +14,134 @@
 //   Zhi, Zlo : BF16 hi/lo split (Zc ~ hi + lo) for the tensor-core path,
 //   Q    : fixed-point Zc * 2^qexp_j (int64) for the exact-sum recheck,
 //   band : per-column error-band terms of both bulk paths.
+//
+// Any number of experiments of different shapes is prepared together: each kernel
+// launch covers the blocks of every experiment (a table of experiment descriptors and,
+// per launch, the prefix sums of their block counts), so a batch costs about as many
+// launches as one experiment and its many small, latency-bound steps share the SMs.
 #include "frr_internal.cuh"
 #include "frr_gen.cuh"
 
+#include <algorithm>
 #include <vector>
 
 namespace frr {
+
+// One experiment's preparation as the kernels see it (device pointers).
+struct PrepJob {
+    int n, d, n1, whiten, kpad, dpad32, kused;
+    double ridge;
+    // temporaries
+    double *X, *xbar, *Xc, *S, *Adiag, *Lm, *ZT, *scal, *eps;
+    int* status;
+    // outputs (the context's arrays)
+    double* Zc64;
+    float* Z32;
+    __nv_bfloat16 *Zhi, *Zlo, *Zq;
+    long long *Q, *Qsum;
+    int* qexp;
+};
+
 namespace {
 
-__global__ void k_colmean(const double* __restrict__ X, int n, int d, double* __restrict__ xbar)
+#define PJ_ARGS const PrepJob* __restrict__ jobs, const unsigned* __restrict__ prefix, int E
+
+// The job owning this block and the block's index within the job: prefix[e] is the first
+// block of job e (jobs with no blocks have prefix[e] == prefix[e + 1]).
+__device__ __forceinline__ const PrepJob& job_of(PJ_ARGS, unsigned& local)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= d) return;
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s = __dadd_rn(s, X[(size_t)i * d + j]);
-    xbar[j] = __ddiv_rn(s, (double)n);
+    const unsigned b = blockIdx.x;
+    int lo = 0, hi = E;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= b) lo = mid; else hi = mid;
+    }
+    local = b - prefix[lo];
+    return jobs[lo];
 }
 
-__global__ void k_center(const double* __restrict__ X, const double* __restrict__ xbar, int n, int d,
-                         double* __restrict__ Xc)
+__global__ void k_colmean(PJ_ARGS)
 {
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (size_t)n * d) return;
-    Xc[idx] = __dsub_rn(X[idx], xbar[idx % d]);
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int n = J.n, d = J.d;
+    const int j = lb * blockDim.x + threadIdx.x;
+    if (j >= d) return;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s = __dadd_rn(s, J.X[(size_t)i * d + j]);
+    J.xbar[j] = __ddiv_rn(s, (double)n);
+}
+
+__global__ void k_center(PJ_ARGS)
+{
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const size_t idx = (size_t)lb * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)J.n * J.d) return;
+    const double v = __dsub_rn(J.X[idx], J.xbar[idx % J.d]);
+    J.Xc[idx] = v;
+    J.ZT[idx] = v;  // the forward substitution works in place on a copy of Xc
 }
 
 // S_jk = sum_i Xc_ij Xc_ik / (n - 1) for k >= j, mirrored (the product is commutative,
-// so both halves are the value a separate (k, j) computation would give).
-__global__ void k_cov(const double* __restrict__ Xc, int n, int d, double* __restrict__ S)
+// so both halves are the value a separate (k, j) computation would give). 32 x 8 threads
+// per block, blocks row-major over (ceil(d / 32), ceil(d / 8)).
+__global__ void k_cov(PJ_ARGS)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int n = J.n, d = J.d;
+    const unsigned gx = (unsigned)((d + 31) / 32);
+    const int k = (int)(lb % gx) * 32 + threadIdx.x;
+    const int j = (int)(lb / gx) * 8 + threadIdx.y;
     if (j >= d || k >= d || k < j) return;
+    const double* Xc = J.Xc;
     double s = 0.0;
     for (int i = 0; i < n; ++i) s = __dadd_rn(s, __dmul_rn(Xc[(size_t)i * d + j], Xc[(size_t)i * d + k]));
     const double v = __ddiv_rn(s, (double)(n - 1));
-    S[(size_t)j * d + k] = v;
-    S[(size_t)k * d + j] = v;
+    J.S[(size_t)j * d + k] = v;
+    J.S[(size_t)k * d + j] = v;
 }
 
-// trace, max diagonal, and the diagonal of S_lambda (ridge added)
-__global__ void k_diag(const double* __restrict__ S, int d, int whiten, double ridge, double* __restrict__ Adiag,
-                       double* __restrict__ scal /* [0]=trace [1]=maxdiag */)
+// trace, max diagonal, and the diagonal of S_lambda (ridge added); one thread per job
+__global__ void k_diag(PJ_ARGS)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    if (threadIdx.x != 0) return;
+    const int d = J.d;
     double tr = 0.0, mx = 0.0;
     for (int j = 0; j < d; ++j) {
-        const double s = S[(size_t)j * d + j];
+        const double s = J.S[(size_t)j * d + j];
         tr = __dadd_rn(tr, s);
         if (s > mx) mx = s;
     }
-    const double add = (whiten == FRR_RIDGE) ? __dmul_rn(ridge, __ddiv_rn(tr, (double)d)) : 0.0;
-    for (int j = 0; j < d; ++j) Adiag[j] = __dadd_rn(S[(size_t)j * d + j], add);
-    scal[0] = tr;
-    scal[1] = mx;
+    const double add = (J.whiten == FRR_RIDGE) ? __dmul_rn(J.ridge, __ddiv_rn(tr, (double)d)) : 0.0;
+    for (int j = 0; j < d; ++j) J.Adiag[j] = __dadd_rn(J.S[(size_t)j * d + j], add);
+    J.scal[0] = tr;
+    J.scal[1] = mx;
 }
 
-
+// Working matrix of the factorisation: A = S with the ridge on the diagonal (the lower part
+// is what the factorisation reads), or for diagonal whitening L = diag(sqrt(S_jj)) itself.
+__global__ void k_init_L(PJ_ARGS)
+{
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int d = J.d;
+    const size_t idx = (size_t)lb * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)d * d) return;
+    const int i = (int)(idx / d), j = (int)(idx % d);
+    if (J.whiten != FRR_DIAG) {
+        J.Lm[idx] = (i == j) ? J.Adiag[i] : J.S[idx];
+        return;
+    }
+    if (i != j) { J.Lm[idx] = 0.0; return; }
+    const double tol_abs = __dmul_rn(1e-12, J.scal[1]);  // pivot tolerance relative to max S_jj
+    const double s = J.S[idx];
+    if (!(s > tol_abs)) atomicExch(J.status, 1);
+    J.Lm[idx] = __dsqrt_rn(s > 0.0 ? s : 1.0);
+}
 
 // ---- blocked factorisation with the same operation order --------------------------
 // Panels of kP columns. Every entry of the working matrix receives its subtractions
@@ -138,72 +209,92 @@ __device__ __forceinline__ void eliminate_rows(double (&t)[kPC], int pw, const d
     }
 }
 
-// Panel [k0, k0 + pw) of the Cholesky factor, in place in A (row-major d x d, lower part:
-// working values, final L on exit). Every CTA factors the pw x pw diagonal block (lane = row
-// of the block) and then finishes its own 32 rows below it; CTA 0 writes the block back.
-__global__ void __launch_bounds__(kP * kPW)
-k_chol_panel(double* __restrict__ A, int d, int k0, int pw, const double* __restrict__ scal, int* __restrict__ status)
+// Diagonal block of panel p (columns [32 p, 32 p + pw)) of the Cholesky factor, in place in
+// Lm (row-major d x d, lower part: working values, final L on exit); one block per job, lane =
+// row of the block. Right-looking: at step jj the pivot becomes L_jj,jj, the rows below divide
+// by it, and every later entry (kk, r) with jj < kk <= r subtracts L_r,jj L_kk,jj (the
+// diagonal entry subtracts a square). The rows below the block follow in k_chol_below, which
+// reads the finished block (a separate launch: blocks of one launch may start after others
+// have finished, so the block must not be overwritten while other blocks may still read it).
+__global__ void __launch_bounds__(kP * kPW) k_chol_diag(PJ_ARGS, int p)
 {
-    const double tol_abs = __dmul_rn(1e-12, scal[1]);  // pivot tolerance relative to max S_jj
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int d = J.d, k0 = kP * p;
+    const int pw = (d - k0) < kP ? (d - k0) : kP;
+    double* __restrict__ A = J.Lm;
+    const double tol_abs = __dmul_rn(1e-12, J.scal[1]);  // pivot tolerance relative to max S_jj
     __shared__ double Lc[kP][kP + 1];  // Lc[jj][r] = L_{k0+r, k0+jj}, r >= jj
-    __shared__ double Zs[kP][32];
-    __shared__ double Ld[kP], Yd[kP];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int r = lane;
     double t[kPC];
-    {
-        // ---- diagonal block, right-looking: at step jj the pivot becomes L_jj,jj, the rows
-        // below divide by it, and every later entry (kk, r) with jj < kk <= r subtracts
-        // L_r,jj L_kk,jj (the diagonal entry subtracts a square)
-        const int r = lane;
+#pragma unroll
+    for (int c = 0; c < kPC; ++c) {
+        const int kk = w + kPW * c;
+        t[c] = (r < pw && kk <= r) ? A[(size_t)(k0 + r) * d + k0 + kk] : 0.0;
+    }
+    // finish column j held in tc by its owner warp: pivot on lane j, division below it
+    auto finish_col = [&](double& tc, int j) {
+        double piv = 0.0;
+        if (lane == j) {
+            if (!(tc > tol_abs)) atomicExch(J.status, 1);
+            piv = __dsqrt_rn(tc > 0.0 ? tc : 1.0);
+        }
+        piv = __shfl_sync(0xffffffffu, piv, j);
+        if (lane == j) tc = piv;
+        else if (lane > j && lane < pw) tc = __ddiv_rn(tc, piv);
+        if (lane >= j && lane < pw) Lc[j][lane] = tc;
+    };
+    if (w == 0) finish_col(t[0], 0);
+    for (int jj = 0; jj < pw; ++jj) {
+        __syncthreads();
+        const double lrj = (r >= jj && r < pw) ? Lc[jj][r] : 0.0;
+        const int nxt = jj + 1;
+        if (nxt < pw && w == nxt % kPW) {
+#pragma unroll
+            for (int c = 0; c < kPC; ++c)
+                if (w + kPW * c == nxt) {
+                    if (r >= nxt && r < pw) t[c] = __dsub_rn(t[c], __dmul_rn(lrj, Lc[jj][nxt]));
+                    finish_col(t[c], nxt);
+                }
+        }
 #pragma unroll
         for (int c = 0; c < kPC; ++c) {
             const int kk = w + kPW * c;
-            t[c] = (r < pw && kk <= r) ? A[(size_t)(k0 + r) * d + k0 + kk] : 0.0;
-        }
-        // finish column j held in tc by its owner warp: pivot on lane j, division below it
-        auto finish_col = [&](double& tc, int j) {
-            double piv = 0.0;
-            if (lane == j) {
-                if (!(tc > tol_abs)) atomicExch(status, 1);
-                piv = __dsqrt_rn(tc > 0.0 ? tc : 1.0);
-                Ld[j] = piv;
-            }
-            piv = __shfl_sync(0xffffffffu, piv, j);
-            if (lane == j) tc = piv;
-            else if (lane > j && lane < pw) tc = __ddiv_rn(tc, piv);
-            if (lane >= j && lane < pw) Lc[j][lane] = tc;
-        };
-        if (w == 0) finish_col(t[0], 0);
-        for (int jj = 0; jj < pw; ++jj) {
-            __syncthreads();
-            const double lrj = (r >= jj && r < pw) ? Lc[jj][r] : 0.0;
-            const int nxt = jj + 1;
-            if (nxt < pw && w == nxt % kPW) {
-#pragma unroll
-                for (int c = 0; c < kPC; ++c)
-                    if (w + kPW * c == nxt) {
-                        if (r >= nxt && r < pw) t[c] = __dsub_rn(t[c], __dmul_rn(lrj, Lc[jj][nxt]));
-                        finish_col(t[c], nxt);
-                    }
-            }
-#pragma unroll
-            for (int c = 0; c < kPC; ++c) {
-                const int kk = w + kPW * c;
-                if (kk > nxt && kk < pw && r >= kk && r < pw) t[c] = __dsub_rn(t[c], __dmul_rn(lrj, Lc[jj][kk]));
-            }
-        }
-        if (blockIdx.x == 0) {
-#pragma unroll
-            for (int c = 0; c < kPC; ++c) {
-                const int kk = w + kPW * c;
-                if (r < pw && kk <= r) A[(size_t)(k0 + r) * d + k0 + kk] = t[c];
-            }
+            if (kk > nxt && kk < pw && r >= kk && r < pw) t[c] = __dsub_rn(t[c], __dmul_rn(lrj, Lc[jj][kk]));
         }
     }
-    __syncthreads();
-    if (threadIdx.x < pw) Yd[threadIdx.x] = __ddiv_rn(1.0, Ld[threadIdx.x]);
-    // ---- this CTA's 32 rows below the block
-    const int r = k0 + pw + blockIdx.x * 32 + lane;
+#pragma unroll
+    for (int c = 0; c < kPC; ++c) {
+        const int kk = w + kPW * c;
+        if (r < pw && kk <= r) A[(size_t)(k0 + r) * d + k0 + kk] = t[c];
+    }
+}
+
+// Rows below the diagonal block of panel p, 32 per block: L_r,jj = (A_r,jj - sum_{k<jj}
+// L_r,k L_jj,k) / L_jj,jj over the panel's columns, against the finished diagonal block.
+__global__ void __launch_bounds__(kP * kPW) k_chol_below(PJ_ARGS, int p)
+{
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int d = J.d, k0 = kP * p;
+    const int pw = (d - k0) < kP ? (d - k0) : kP;
+    double* __restrict__ A = J.Lm;
+    __shared__ double Lc[kP][kP + 1];  // Lc[jj][kk] = L_{k0+kk, k0+jj}, kk >= jj
+    __shared__ double Zs[kP][32];
+    __shared__ double Ld[kP], Yd[kP];
+    for (int e = threadIdx.x; e < kP * kP; e += blockDim.x) {
+        const int jj = e / kP, kk = e % kP;
+        Lc[jj][kk] = (kk < pw && kk >= jj) ? A[(size_t)(k0 + kk) * d + k0 + jj] : 0.0;
+    }
+    if (threadIdx.x < pw) {
+        const double l = A[(size_t)(k0 + threadIdx.x) * d + k0 + threadIdx.x];
+        Ld[threadIdx.x] = l;
+        Yd[threadIdx.x] = __ddiv_rn(1.0, l);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int r = k0 + pw + (int)lb * 32 + lane;
+    double t[kPC];
 #pragma unroll
     for (int c = 0; c < kPC; ++c) {
         const int kk = w + kPW * c;
@@ -218,13 +309,20 @@ k_chol_panel(double* __restrict__ A, int d, int k0, int pw, const double* __rest
     }
 }
 
-// Trailing update after panel [k0, k0 + pw): A_ij -= L_ik L_jk for k in the panel (ascending),
-// for k0 + pw <= j <= i < d. 32 x 32 tiles, lower-triangle tiles only.
-__global__ void __launch_bounds__(256)
-k_chol_trailing(double* __restrict__ A, int d, int k0, int pw)
+// Trailing update after panel p: A_ij -= L_ik L_jk for k in the panel (ascending), for
+// k0 + pw <= j <= i < d. 32 x 32 tiles, lower-triangle tiles only: local block b is tile
+// (ti, tj) with b = ti (ti + 1) / 2 + tj, tj <= ti.
+__global__ void __launch_bounds__(256) k_chol_trailing(PJ_ARGS, int p)
 {
-    const int ti = blockIdx.y, tj = blockIdx.x;
-    if (tj > ti) return;
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int d = J.d, k0 = kP * p;
+    const int pw = (d - k0) < kP ? (d - k0) : kP;
+    double* __restrict__ A = J.Lm;
+    int ti = (int)((sqrtf(8.0f * (float)lb + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= (int)lb) ++ti;
+    while (ti * (ti + 1) / 2 > (int)lb) --ti;
+    const int tj = (int)lb - ti * (ti + 1) / 2;
     __shared__ double Li[32][kP + 1], Lj[32][kP + 1];
     const int base = k0 + pw;
     const int i0 = base + 32 * ti, j0 = base + 32 * tj;
@@ -244,13 +342,17 @@ k_chol_trailing(double* __restrict__ A, int d, int k0, int pw)
     }
 }
 
-// Panel [k0, k0 + pw) of the forward substitution Zc = Xc L^{-T}, in place in T (n x d
-// row-major: working values, final Zc on exit): 32 rows per CTA, eliminated against the
-// panel's diagonal block of L (z_ij = (t_ij - sum_{k<j} L_jk z_ik) / L_jj, subtractions in
-// ascending k).
-__global__ void __launch_bounds__(kP * kPW)
-k_fwd_panel(double* __restrict__ T, const double* __restrict__ L, int n, int d, int k0, int pw)
+// Panel p of the forward substitution Zc = Xc L^{-T}, in place in ZT (n x d row-major:
+// working values, final Zc on exit): 32 rows per block, eliminated against the panel's
+// diagonal block of L (z_ij = (t_ij - sum_{k<j} L_jk z_ik) / L_jj, subtractions in ascending k).
+__global__ void __launch_bounds__(kP * kPW) k_fwd_panel(PJ_ARGS, int p)
 {
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int n = J.n, d = J.d, k0 = kP * p;
+    const int pw = (d - k0) < kP ? (d - k0) : kP;
+    const double* __restrict__ L = J.Lm;
+    double* __restrict__ T = J.ZT;
     __shared__ double Lc[kP][kP + 1];  // Lc[jj][kk] = L_{k0+kk, k0+jj}, kk >= jj
     __shared__ double Zs[kP][32];
     __shared__ double Ld[kP], Yd[kP];
@@ -264,7 +366,7 @@ k_fwd_panel(double* __restrict__ T, const double* __restrict__ L, int n, int d, 
         Yd[threadIdx.x] = __ddiv_rn(1.0, l);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int i = blockIdx.x * 32 + lane;
+    const int i = (int)lb * 32 + lane;
     double t[kPC];
 #pragma unroll
     for (int c = 0; c < kPC; ++c) {
@@ -280,12 +382,19 @@ k_fwd_panel(double* __restrict__ T, const double* __restrict__ L, int n, int d, 
     }
 }
 
-// T_ij -= L_jk z_ik for k in panel [k0, k0 + pw) (ascending), j >= k0 + pw. 32 x 32 tiles.
-__global__ void __launch_bounds__(256)
-k_fwd_trailing(double* __restrict__ T, const double* __restrict__ L, int n, int d, int k0, int pw)
+// T_ij -= L_jk z_ik for k in panel p (ascending), j >= k0 + pw. 32 x 32 tiles, local block
+// b = (row tile) * (column tiles) + (column tile).
+__global__ void __launch_bounds__(256) k_fwd_trailing(PJ_ARGS, int p)
 {
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int n = J.n, d = J.d, k0 = kP * p;
+    const int pw = (d - k0) < kP ? (d - k0) : kP;
+    const double* __restrict__ L = J.Lm;
+    double* __restrict__ T = J.ZT;
+    const unsigned gx = (unsigned)((d - k0 - pw + 31) / 32);
     __shared__ double Zi[32][kP + 1], Lj[32][kP + 1];
-    const int i0 = 32 * blockIdx.y, j0 = k0 + pw + 32 * blockIdx.x;
+    const int i0 = 32 * (int)(lb / gx), j0 = k0 + pw + 32 * (int)(lb % gx);
     for (int e = threadIdx.x; e < 32 * kP; e += blockDim.x) {
         const int rr = e / kP, kk = e % kP;
         Zi[rr][kk] = (i0 + rr < n && kk < pw) ? T[(size_t)(i0 + rr) * d + k0 + kk] : 0.0;
@@ -302,86 +411,80 @@ k_fwd_trailing(double* __restrict__ T, const double* __restrict__ L, int n, int 
     }
 }
 
-// A = S with the ridge on the diagonal (lower part is what the factorisation reads)
-__global__ void k_init_A(const double* __restrict__ S, const double* __restrict__ Adiag, int d, double* __restrict__ A)
+__global__ void k_copy_zc(PJ_ARGS)
 {
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (size_t)d * d) return;
-    const int i = (int)(idx / d), j = (int)(idx % d);
-    A[idx] = (i == j) ? Adiag[i] : S[idx];
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const size_t idx = (size_t)lb * blockDim.x + threadIdx.x;
+    if (idx < (size_t)J.n * J.d) J.Zc64[idx] = J.ZT[idx];
 }
-
-// diagonal whitening: L = diag(sqrt(S_jj)) stored row-major (zero elsewhere)
-__global__ void k_diag_L(const double* __restrict__ S, int d, const double* __restrict__ scal, double* __restrict__ A,
-                         int* status)
-{
-    const double tol_abs = __dmul_rn(1e-12, scal[1]);
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (size_t)d * d) return;
-    const int i = (int)(idx / d), j = (int)(idx % d);
-    if (i != j) { A[idx] = 0.0; return; }
-    const double s = S[idx];
-    if (!(s > tol_abs)) atomicExch(status, 1);
-    A[idx] = __dsqrt_rn(s > 0.0 ? s : 1.0);
-}
-
-
 
 // qexp_j such that |Zc_ij * 2^qexp_j| <= 2^kQBits for every i
-__global__ void k_qexp(const double* __restrict__ Z, int n, int d, int* __restrict__ qexp)
+__global__ void k_qexp(PJ_ARGS)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int n = J.n, d = J.d;
+    const int j = lb * blockDim.x + threadIdx.x;
     if (j >= d) return;
     double mx = 0.0;
-    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(Z[(size_t)i * d + j]));
+    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(J.Zc64[(size_t)i * d + j]));
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e with f in [0.5, 1): mx < 2^e
-    qexp[j] = (mx > 0.0) ? (kQBits - e) : 0;
+    J.qexp[j] = (mx > 0.0) ? (kQBits - e) : 0;
 }
 
-// K-order derived arrays (p = K position, u = unit at p).
-__global__ void k_derive(const double* __restrict__ Z, int n, int d, int kpad, int dpad32,
-                         const int* __restrict__ qexp, float* __restrict__ Z32, __nv_bfloat16* __restrict__ Zhi,
-                         __nv_bfloat16* __restrict__ Zlo, long long* __restrict__ Q)
+// K-order derived arrays (p = K position, u = unit at p); every element of Z32, Zhi, Zlo and
+// Q is written (zero at padding positions).
+__global__ void k_derive(PJ_ARGS)
 {
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int n = J.n, d = J.d, kpad = J.kpad, dpad32 = J.dpad32;
+    const size_t idx = (size_t)lb * blockDim.x + threadIdx.x;
     if (idx >= (size_t)kpad * dpad32) return;
     const int p = (int)(idx / dpad32), j = (int)(idx % dpad32);
     const int u = unit_of_kpos(p);
-    const double z = (u < n && j < d) ? Z[(size_t)u * d + j] : 0.0;
-    Z32[idx] = (float)z;
+    const double z = (u < n && j < d) ? J.Zc64[(size_t)u * d + j] : 0.0;
+    J.Z32[idx] = (float)z;
     if (j < d) {
         const __nv_bfloat16 hi = __double2bfloat16(z);
         const __nv_bfloat16 lo = __double2bfloat16(z - (double)__bfloat162float(hi));
-        Zhi[(size_t)j * kpad + p] = hi;
-        Zlo[(size_t)j * kpad + p] = lo;
-        Q[(size_t)p * d + j] = llrint(ldexp(z, qexp[j]));
+        J.Zhi[(size_t)j * kpad + p] = hi;
+        J.Zlo[(size_t)j * kpad + p] = lo;
+        J.Q[(size_t)p * d + j] = llrint(ldexp(z, J.qexp[j]));
     }
 }
 
 // Balanced base-256 digits of Q: Q = sum_{k<7} q_k 256^k with q_k in [-128, 127], plane k
 // stored K-major as BF16 (integers of this size are exact): Zq[(k d + j) kpad + p].
-__global__ void k_digits(const long long* __restrict__ Q, int kpad, int d, __nv_bfloat16* __restrict__ Zq)
+__global__ void k_digits(PJ_ARGS)
 {
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int d = J.d, kpad = J.kpad;
+    const size_t idx = (size_t)lb * blockDim.x + threadIdx.x;
     if (idx >= (size_t)kpad * d) return;
     const int j = (int)(idx / kpad), p = (int)(idx % kpad);
-    long long v = Q[(size_t)p * d + j];
+    long long v = J.Q[(size_t)p * d + j];
     for (int k = 0; k < 7; ++k) {
         int q = (int)(v & 0xFF);
         if (q >= 128) q -= 256;
         v = (v - q) >> 8;
-        Zq[((size_t)k * d + j) * kpad + p] = __float2bfloat16_rn((float)q);
+        J.Zq[((size_t)k * d + j) * kpad + p] = __float2bfloat16_rn((float)q);
     }
 }
 
-__global__ void k_qsum(const long long* __restrict__ Q, int kpad, int d, long long* __restrict__ Qsum)
+__global__ void k_qsum(PJ_ARGS)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int d = J.d, kpad = J.kpad;
+    const int j = lb * blockDim.x + threadIdx.x;
     if (j >= d) return;
     long long s = 0;
-    for (int p = 0; p < kpad; ++p) s += Q[(size_t)p * d + j];
-    Qsum[j] = s;
+    for (int p = 0; p < kpad; ++p) s += J.Q[(size_t)p * d + j];
+    J.Qsum[j] = s;
 }
 
 // Per-column error terms of the bulk paths, bounding |s_hat_j - s_j| for the
@@ -393,16 +496,19 @@ __global__ void k_qsum(const long long* __restrict__ Q, int kpad, int d, long lo
 //     one rounding of relative size u per accumulated term.
 // SIMT FP32: u = 2^-24 (round to nearest), one pass.
 // Tensor cores: u = 2^-23 (truncation allowed), two passes (hi and lo terms).
-__global__ void __launch_bounds__(256)
-k_band_cols(const double* __restrict__ Z, int n, int d, int n1, int kused, double* __restrict__ eps32,
-            double* __restrict__ eps_tc)
+// One block per column; eps[j] and eps[d + j] receive the two paths' terms.
+__global__ void __launch_bounds__(256) k_band_cols(PJ_ARGS)
 {
-    // one CTA per column; thread t covers K positions [t * per, (t + 1) * per)
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int n = J.n, d = J.d, kused = J.kused;
+    const double* __restrict__ Z = J.Zc64;
+    // thread t covers K positions [t * per, (t + 1) * per)
     __shared__ double ws1[8], ws2[8], wacc[8], wr32[8], wrtc[8];
-    const int j = blockIdx.x;
+    const int j = (int)lb;
     const int per = (kused + 255) / 256;
     const int p0 = threadIdx.x * per;
-    const double pi = (double)n1 / n;
+    const double pi = (double)J.n1 / n;
     const double vf = pi * (1.0 - pi) * (double)n / (double)(n - 1);
     double l1 = 0.0, l2 = 0.0;
     for (int p = p0; p < p0 + per && p < kused; ++p) {
@@ -450,15 +556,15 @@ k_band_cols(const double* __restrict__ Z, int n, int d, int n1, int kused, doubl
     if (threadIdx.x == 0) {
         double A = 0.0, R32 = 0.0, RTC = 0.0;
         for (int w = 0; w < 8; ++w) { A += wacc[w]; R32 += wr32[w]; RTC += wrtc[w]; }
-        eps32[j] = R32 + ldexp(A, -24);
-        eps_tc[j] = RTC + 2.0 * ldexp(A, -23);
+        J.eps[j] = R32 + ldexp(A, -24);
+        J.eps[d + j] = RTC + 2.0 * ldexp(A, -23);
     }
 }
 
-BandConsts band_from_eps(const std::vector<double>& eps, double c_M, int64_t d)
+BandConsts band_from_eps(const double* eps, double c_M, int64_t d)
 {
     double ss = 0.0;
-    for (double e : eps) ss += e * e;
+    for (int64_t j = 0; j < d; ++j) ss += eps[j] * eps[j];
     const double en = sqrt(ss);
     const double u = ldexp(1.0, -24);
     const double g = (double)(d + 2) * u / (1.0 - (double)(d + 2) * u);
@@ -469,8 +575,6 @@ BandConsts band_from_eps(const std::vector<double>& eps, double c_M, int64_t d)
     return b;
 }
 
-}  // namespace
-
 // C(c, m) for c, m < 64 at [c * 64 + m] (Pascal's rule; every entry fits in 64 bits), built once
 const uint64_t* binom_table()
 {
@@ -478,133 +582,251 @@ const uint64_t* binom_table()
         std::vector<uint64_t> t(64 * 64, 0);
         for (int c = 0; c < 64; ++c) {
             t[(size_t)c * 64] = 1;
-            for (int m = 1; m <= c; ++m) t[(size_t)c * 64 + m] = t[(size_t)(c - 1) * 64 + m - 1] + t[(size_t)(c - 1) * 64 + m];
+            for (int m = 1; m <= c; ++m)
+                t[(size_t)c * 64 + m] = t[(size_t)(c - 1) * 64 + m - 1] + t[(size_t)(c - 1) * 64 + m];
         }
         return t;
     }();
     return tab.data();
 }
 
-frr_status prep_run(frr_ctx* ctx, const double* X_host)
-{
-    const int n = (int)ctx->n, d = (int)ctx->d;
-    cudaStream_t s = ctx->stream;
-    const size_t nd = (size_t)n * d;
-    double *X = nullptr, *xbar = nullptr, *Xc = nullptr, *S = nullptr, *Adiag = nullptr, *Lm = nullptr,
-           *ZT = nullptr, *scal = nullptr, *eps = nullptr;
-    int* status = nullptr;
-    frr_status rc = FRR_OK;
-    auto fail = [&](cudaError_t e) { ctx->failed = true; rc = (e == cudaErrorMemoryAllocation) ? FRR_E_NOMEM : FRR_E_CUDA; };
-#define PREP_CHECK(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) { fail(_e); goto cleanup; } } while (0)
-
-    cudaMemPool_t pool = temp_pool(ctx->device);
-    if (pool == nullptr) return FRR_E_CUDA;
-    PREP_CHECK(cudaMallocFromPoolAsync(&X, nd * sizeof(double), pool, s));
-    PREP_CHECK(cudaMallocFromPoolAsync(&xbar, d * sizeof(double), pool, s));
-    PREP_CHECK(cudaMallocFromPoolAsync(&Xc, nd * sizeof(double), pool, s));
-    PREP_CHECK(cudaMallocFromPoolAsync(&S, (size_t)d * d * sizeof(double), pool, s));
-    PREP_CHECK(cudaMallocFromPoolAsync(&Adiag, d * sizeof(double), pool, s));
-    PREP_CHECK(cudaMallocFromPoolAsync(&Lm, (size_t)d * d * sizeof(double), pool, s));
-    PREP_CHECK(cudaMallocFromPoolAsync(&ZT, nd * sizeof(double), pool, s));
-    PREP_CHECK(cudaMallocFromPoolAsync(&scal, 4 * sizeof(double), pool, s));
-    PREP_CHECK(cudaMallocFromPoolAsync(&eps, 2 * (size_t)d * sizeof(double), pool, s));
-    PREP_CHECK(cudaMallocFromPoolAsync(&status, sizeof(int), pool, s));
-    PREP_CHECK(cudaMemsetAsync(status, 0, sizeof(int), s));
-    PREP_CHECK(cudaMemsetAsync(Lm, 0, (size_t)d * d * sizeof(double), s));
-    PREP_CHECK(cudaMemcpyAsync(X, X_host, nd * sizeof(double), cudaMemcpyHostToDevice, s));
-
-    k_colmean<<<ceil_div(d, 128), 128, 0, s>>>(X, n, d, xbar);
-    k_center<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(X, xbar, n, d, Xc);
+// Block counts of the launches of one job (0: the job has no work in that launch).
+struct JobBlocks {
+    static unsigned colmean(const PrepJob& j) { return (unsigned)ceil_div(j.d, 128); }
+    static unsigned center(const PrepJob& j) { return (unsigned)(((size_t)j.n * j.d + 255) / 256); }
+    static unsigned cov(const PrepJob& j) { return (unsigned)(ceil_div(j.d, 32) * ceil_div(j.d, 8)); }
+    static unsigned one(const PrepJob&) { return 1u; }
+    static unsigned init_L(const PrepJob& j) { return (unsigned)(((size_t)j.d * j.d + 255) / 256); }
+    static unsigned chol_diag(const PrepJob& j, int p)
     {
-        dim3 blk(32, 8), grd(ceil_div(d, 32), ceil_div(d, 8));
-        k_cov<<<grd, blk, 0, s>>>(Xc, n, d, S);
+        return (j.whiten == FRR_DIAG || kP * p >= j.d) ? 0u : 1u;
     }
-    k_diag<<<1, 1, 0, s>>>(S, d, ctx->opts.whiten, ctx->opts.ridge, Adiag, scal);
-    PREP_CHECK(cudaGetLastError());
+    static unsigned chol_below(const PrepJob& j, int p)
     {
-        // The pivot tolerance is read on the device (scal[1] = max S_jj), and a failed pivot is
-        // only flagged (the factorisation goes on with a unit pivot, so every later value stays
-        // finite): the host learns both at the single synchronisation at the end.
-        const size_t dd = (size_t)d * d;
-        // forward substitution in place on a copy of Xc (ZT holds n x d row-major here)
-        PREP_CHECK(cudaMemcpyAsync(ZT, Xc, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        if (ctx->opts.whiten == FRR_DIAG) {
-            k_diag_L<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(S, d, scal, Lm, status);
-            for (int k0 = 0; k0 < d; k0 += kP) {
-                const int pw = (d - k0) < kP ? (d - k0) : kP;
-                k_fwd_panel<<<ceil_div(n, 32), kP * kPW, 0, s>>>(ZT, Lm, n, d, k0, pw);
-                const int right = d - k0 - pw;
-                if (right > 0)
-                    k_fwd_trailing<<<dim3(ceil_div(right, 32), ceil_div(n, 32)), 256, 0, s>>>(ZT, Lm, n, d, k0, pw);
-            }
-        } else {
-            // Both factorisations are chains of latency-bound panels. Step p of the forward
-            // substitution needs only column panel p of L, which is final once Cholesky panel
-            // p is done (later trailing updates touch columns to its right), so it runs on a
-            // second stream, one panel behind: the two chains overlap.
-            k_init_A<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(S, Adiag, d, Lm);
-            const int np = ceil_div(d, kP);
-            std::vector<cudaEvent_t> evs((size_t)np + 2, nullptr);
-            for (auto& e : evs) PREP_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-            PREP_CHECK(cudaEventRecord(evs[np], s));
-            PREP_CHECK(cudaStreamWaitEvent(ctx->aux, evs[np], 0));
-            for (int p = 0, k0 = 0; k0 < d; ++p, k0 += kP) {
-                const int pw = (d - k0) < kP ? (d - k0) : kP;
-                const int below = d - k0 - pw;
-                k_chol_panel<<<below > 0 ? ceil_div(below, 32) : 1, kP * kPW, 0, s>>>(Lm, d, k0, pw, scal, status);
-                PREP_CHECK(cudaEventRecord(evs[p], s));
-                PREP_CHECK(cudaStreamWaitEvent(ctx->aux, evs[p], 0));
-                k_fwd_panel<<<ceil_div(n, 32), kP * kPW, 0, ctx->aux>>>(ZT, Lm, n, d, k0, pw);
-                if (below > 0) {
-                    const int tiles = ceil_div(below, 32);
-                    k_chol_trailing<<<dim3(tiles, tiles), 256, 0, s>>>(Lm, d, k0, pw);
-                    k_fwd_trailing<<<dim3(ceil_div(below, 32), ceil_div(n, 32)), 256, 0, ctx->aux>>>(ZT, Lm, n, d, k0,
-                                                                                                  pw);
-                }
-            }
-            PREP_CHECK(cudaEventRecord(evs[np + 1], ctx->aux));
-            PREP_CHECK(cudaStreamWaitEvent(s, evs[np + 1], 0));
-            for (auto& e : evs) cudaEventDestroy(e);
+        const int k0 = kP * p;
+        if (j.whiten == FRR_DIAG || k0 >= j.d) return 0u;
+        const int pw = std::min(kP, j.d - k0), below = j.d - k0 - pw;
+        return below > 0 ? (unsigned)ceil_div(below, 32) : 0u;
+    }
+    static unsigned chol_trailing(const PrepJob& j, int p)
+    {
+        const int k0 = kP * p;
+        if (j.whiten == FRR_DIAG || k0 >= j.d) return 0u;
+        const int pw = std::min(kP, j.d - k0), below = j.d - k0 - pw;
+        const unsigned t = below > 0 ? (unsigned)ceil_div(below, 32) : 0u;
+        return t * (t + 1) / 2;
+    }
+    static unsigned fwd_panel(const PrepJob& j, int p) { return kP * p < j.d ? (unsigned)ceil_div(j.n, 32) : 0u; }
+    static unsigned fwd_trailing(const PrepJob& j, int p)
+    {
+        const int k0 = kP * p;
+        if (k0 >= j.d) return 0u;
+        const int pw = std::min(kP, j.d - k0), below = j.d - k0 - pw;
+        return below > 0 ? (unsigned)(ceil_div(below, 32) * ceil_div(j.n, 32)) : 0u;
+    }
+    static unsigned derive(const PrepJob& j) { return (unsigned)(((size_t)j.kpad * j.dpad32 + 255) / 256); }
+    static unsigned digits(const PrepJob& j) { return (unsigned)(((size_t)j.kpad * j.d + 255) / 256); }
+    static unsigned band(const PrepJob& j) { return (unsigned)j.d; }
+};
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int E, cudaStream_t s,
+                          cudaStream_t aux, frr_status* st_out)
+{
+    if (E < 1) return FRR_OK;
+    const int device = ctxs[0]->device;
+    cudaMemPool_t pool = temp_pool(device);
+    if (pool == nullptr) return FRR_E_CUDA;
+
+    // ---- one temporary allocation: per-job arrays, status words, job table, prefixes
+    std::vector<PrepJob> jobs((size_t)E);
+    std::vector<size_t> joff((size_t)E);
+    size_t bytes = 0;
+    int max_panels = 0;
+    for (int e = 0; e < E; ++e) {
+        const frr_ctx* c = ctxs[e];
+        const size_t n = (size_t)c->n, d = (size_t)c->d;
+        joff[(size_t)e] = bytes;
+        bytes += 3 * align256(n * d * 8) + 2 * align256(d * d * 8) + 2 * align256(d * 8) + align256(4 * 8) +
+                 align256(2 * d * 8);
+        max_panels = std::max(max_panels, ceil_div(c->d, kP));
+    }
+    const size_t status_off = bytes;
+    bytes += align256((size_t)E * sizeof(int));
+    const size_t table_off = bytes;
+    bytes += align256((size_t)E * sizeof(PrepJob));
+    // prefix arrays of every launch, in launch order
+    std::vector<unsigned> pref;
+    std::vector<size_t> pref_at;
+    auto add_launch = [&](auto count) {
+        pref_at.push_back(pref.size());
+        unsigned acc = 0;
+        for (int e = 0; e < E; ++e) {
+            pref.push_back(acc);
+            acc += count(jobs[(size_t)e]);
         }
+        pref.push_back(acc);
+    };
+    char* base = nullptr;
+    {
+        // fill the job table (pointers relative to the future base; fixed up below)
+        for (int e = 0; e < E; ++e) {
+            const frr_ctx* c = ctxs[e];
+            PrepJob& J = jobs[(size_t)e];
+            J.n = (int)c->n; J.d = (int)c->d; J.n1 = (int)c->n1; J.whiten = c->opts.whiten;
+            J.kpad = c->kpad; J.dpad32 = c->dpad32; J.kused = c->kused; J.ridge = c->opts.ridge;
+            J.Zc64 = c->Zc64; J.Z32 = c->Z32; J.Zhi = c->Zhi; J.Zlo = c->Zlo; J.Zq = c->Zq;
+            J.Q = c->Q; J.Qsum = c->Qsum; J.qexp = c->qexp;
+        }
+    }
+    add_launch(JobBlocks::colmean);
+    add_launch(JobBlocks::center);
+    add_launch(JobBlocks::cov);
+    add_launch(JobBlocks::one);
+    add_launch(JobBlocks::init_L);
+    for (int p = 0; p < max_panels; ++p) {
+        add_launch([p](const PrepJob& j) { return JobBlocks::chol_diag(j, p); });
+        add_launch([p](const PrepJob& j) { return JobBlocks::chol_below(j, p); });
+        add_launch([p](const PrepJob& j) { return JobBlocks::fwd_panel(j, p); });
+        add_launch([p](const PrepJob& j) { return JobBlocks::chol_trailing(j, p); });
+        add_launch([p](const PrepJob& j) { return JobBlocks::fwd_trailing(j, p); });
+    }
+    add_launch(JobBlocks::center);  // Zc copy
+    add_launch(JobBlocks::colmean); // qexp
+    add_launch(JobBlocks::derive);
+    add_launch(JobBlocks::colmean); // qsum
+    add_launch(JobBlocks::digits);
+    add_launch(JobBlocks::band);
+    const size_t pref_off = bytes;
+    bytes += align256(pref.size() * sizeof(unsigned));
+
+    frr_status rc = FRR_OK;
+    std::vector<cudaEvent_t> evs;
+    std::vector<int> h_status((size_t)E, 0);
+    std::vector<std::vector<double>> h_eps((size_t)E);
+    auto fail = [&](cudaError_t e) {
+        cudaGetLastError();
+        rc = (e == cudaErrorMemoryAllocation) ? FRR_E_NOMEM : FRR_E_CUDA;
+    };
+#define PREP_CHECK(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) { fail(_e); goto cleanup; } } while (0)
+    PREP_CHECK(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&base), bytes, pool, s));
+    for (int e = 0; e < E; ++e) {
+        PrepJob& J = jobs[(size_t)e];
+        const size_t n = (size_t)J.n, d = (size_t)J.d;
+        char* q = base + joff[(size_t)e];
+        auto take = [&](size_t b) { char* r = q; q += align256(b); return reinterpret_cast<double*>(r); };
+        J.X = take(n * d * 8); J.Xc = take(n * d * 8); J.ZT = take(n * d * 8);
+        J.S = take(d * d * 8); J.Lm = take(d * d * 8);
+        J.xbar = take(d * 8); J.Adiag = take(d * 8); J.scal = take(4 * 8); J.eps = take(2 * d * 8);
+        J.status = reinterpret_cast<int*>(base + status_off) + e;
+        h_eps[(size_t)e].resize(2 * d);
+    }
+    PREP_CHECK(cudaMemsetAsync(base + status_off, 0, (size_t)E * sizeof(int), s));
+    for (int e = 0; e < E; ++e)
+        PREP_CHECK(cudaMemcpyAsync(jobs[(size_t)e].X, X_host[e], (size_t)jobs[(size_t)e].n * jobs[(size_t)e].d * 8,
+                                   cudaMemcpyHostToDevice, s));
+    PREP_CHECK(cudaMemcpyAsync(base + table_off, jobs.data(), (size_t)E * sizeof(PrepJob), cudaMemcpyHostToDevice, s));
+    PREP_CHECK(cudaMemcpyAsync(base + pref_off, pref.data(), pref.size() * sizeof(unsigned), cudaMemcpyHostToDevice,
+                               s));
+    {
+        const PrepJob* dj = reinterpret_cast<const PrepJob*>(base + table_off);
+        const unsigned* dp = reinterpret_cast<const unsigned*>(base + pref_off);
+        size_t li = 0;
+        // blocks of launch li, and its prefix array on the device
+        auto total = [&](size_t l) { return pref[pref_at[l] + (size_t)E]; };
+        auto P = [&](size_t l) { return dp + pref_at[l]; };
+        if (unsigned g = total(li)) k_colmean<<<g, 128, 0, s>>>(dj, P(li), E);
+        ++li;
+        if (unsigned g = total(li)) k_center<<<g, 256, 0, s>>>(dj, P(li), E);
+        ++li;
+        if (unsigned g = total(li)) k_cov<<<g, dim3(32, 8), 0, s>>>(dj, P(li), E);
+        ++li;
+        if (unsigned g = total(li)) k_diag<<<g, 32, 0, s>>>(dj, P(li), E);
+        ++li;
+        if (unsigned g = total(li)) k_init_L<<<g, 256, 0, s>>>(dj, P(li), E);
+        ++li;
+        PREP_CHECK(cudaGetLastError());
+        // Both factorisations are chains of latency-bound panels. Step p of the forward
+        // substitution needs only column panel p of L, which is final once Cholesky panel
+        // p is done (later trailing updates touch columns to its right), so it runs on the
+        // second stream, one panel behind: the two chains overlap.
+        evs.assign((size_t)max_panels + 2, nullptr);
+        for (auto& ev : evs) PREP_CHECK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        PREP_CHECK(cudaEventRecord(evs[(size_t)max_panels], s));
+        PREP_CHECK(cudaStreamWaitEvent(aux, evs[(size_t)max_panels], 0));
+        for (int p = 0; p < max_panels; ++p) {
+            const size_t ld = li, lp = li + 1, lf = li + 2, lt = li + 3, lft = li + 4;
+            li += 5;
+            if (unsigned g = total(ld)) k_chol_diag<<<g, kP * kPW, 0, s>>>(dj, P(ld), E, p);
+            if (unsigned g = total(lp)) k_chol_below<<<g, kP * kPW, 0, s>>>(dj, P(lp), E, p);
+            PREP_CHECK(cudaEventRecord(evs[(size_t)p], s));
+            PREP_CHECK(cudaStreamWaitEvent(aux, evs[(size_t)p], 0));
+            if (unsigned g = total(lf)) k_fwd_panel<<<g, kP * kPW, 0, aux>>>(dj, P(lf), E, p);
+            if (unsigned g = total(lt)) k_chol_trailing<<<g, 256, 0, s>>>(dj, P(lt), E, p);
+            if (unsigned g = total(lft)) k_fwd_trailing<<<g, 256, 0, aux>>>(dj, P(lft), E, p);
+        }
+        PREP_CHECK(cudaEventRecord(evs[(size_t)max_panels + 1], aux));
+        PREP_CHECK(cudaStreamWaitEvent(s, evs[(size_t)max_panels + 1], 0));
+        if (unsigned g = total(li)) k_copy_zc<<<g, 256, 0, s>>>(dj, P(li), E);
+        ++li;
+        if (unsigned g = total(li)) k_qexp<<<g, 128, 0, s>>>(dj, P(li), E);
+        ++li;
+        if (unsigned g = total(li)) k_derive<<<g, 256, 0, s>>>(dj, P(li), E);
+        ++li;
+        if (unsigned g = total(li)) k_qsum<<<g, 128, 0, s>>>(dj, P(li), E);
+        ++li;
+        if (unsigned g = total(li)) k_digits<<<g, 256, 0, s>>>(dj, P(li), E);
+        ++li;
+        if (unsigned g = total(li)) k_band_cols<<<g, 256, 0, s>>>(dj, P(li), E);
+        ++li;
         PREP_CHECK(cudaGetLastError());
     }
-    PREP_CHECK(cudaMemcpyAsync(ctx->Zc64, ZT, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    k_qexp<<<ceil_div(d, 128), 128, 0, s>>>(ctx->Zc64, n, d, ctx->qexp);
-    {
-        const size_t tot = (size_t)ctx->kpad * ctx->dpad32;
-        PREP_CHECK(cudaMemsetAsync(ctx->Zhi, 0, (size_t)d * ctx->kpad * sizeof(__nv_bfloat16), s));
-        PREP_CHECK(cudaMemsetAsync(ctx->Zlo, 0, (size_t)d * ctx->kpad * sizeof(__nv_bfloat16), s));
-        k_derive<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ctx->Zc64, n, d, ctx->kpad, ctx->dpad32, ctx->qexp,
-                                                              ctx->Z32, ctx->Zhi, ctx->Zlo, ctx->Q);
-    }
-    k_qsum<<<ceil_div(d, 128), 128, 0, s>>>(ctx->Q, ctx->kpad, d, ctx->Qsum);
-    k_digits<<<(unsigned)(((size_t)ctx->kpad * d + 255) / 256), 256, 0, s>>>(ctx->Q, ctx->kpad, d, ctx->Zq);
-    k_band_cols<<<d, 256, 0, s>>>(ctx->Zc64, n, d, (int)ctx->n1, ctx->kused, eps, eps + d);
-    PREP_CHECK(cudaGetLastError());
-    // binomial table for exact enumeration (only shapes that allow it read it); the host
-    // table is static, so the copy needs no synchronisation
-    if (n <= kExactMaxN)
-        PREP_CHECK(cudaMemcpyAsync(ctx->binom, binom_table(), 64 * 64 * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
-    {
-        // the single synchronisation of the preparation: pivot status and band inputs
-        std::vector<double> e32(d), etc(d);
-        int st = 0;
-        PREP_CHECK(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-        PREP_CHECK(cudaMemcpyAsync(e32.data(), eps, d * sizeof(double), cudaMemcpyDeviceToHost, s));
-        PREP_CHECK(cudaMemcpyAsync(etc.data(), eps + d, d * sizeof(double), cudaMemcpyDeviceToHost, s));
-        PREP_CHECK(cudaStreamSynchronize(s));
-        if (st != 0) { rc = FRR_E_DEGENERATE; goto cleanup; }
-        ctx->band32 = band_from_eps(e32, ctx->c_M, d);
-        ctx->band_tc = band_from_eps(etc, ctx->c_M, d);
+    // binomial tables for exact enumeration (only shapes that allow it read them); the host
+    // table is static, so the copies need no synchronisation
+    for (int e = 0; e < E; ++e)
+        if (ctxs[e]->n <= kExactMaxN)
+            PREP_CHECK(cudaMemcpyAsync(ctxs[e]->binom, binom_table(), 64 * 64 * sizeof(uint64_t),
+                                       cudaMemcpyHostToDevice, s));
+    // the single synchronisation of the preparation: pivot status and band inputs
+    PREP_CHECK(cudaMemcpyAsync(h_status.data(), base + status_off, (size_t)E * sizeof(int), cudaMemcpyDeviceToHost, s));
+    for (int e = 0; e < E; ++e)
+        PREP_CHECK(cudaMemcpyAsync(h_eps[(size_t)e].data(), jobs[(size_t)e].eps, h_eps[(size_t)e].size() * 8,
+                                   cudaMemcpyDeviceToHost, s));
+    PREP_CHECK(cudaStreamSynchronize(s));
+    for (int e = 0; e < E; ++e) {
+        frr_ctx* c = ctxs[e];
+        if (h_status[(size_t)e] != 0) {
+            st_out[e] = FRR_E_DEGENERATE;
+            continue;
+        }
+        c->band32 = band_from_eps(h_eps[(size_t)e].data(), c->c_M, c->d);
+        c->band_tc = band_from_eps(h_eps[(size_t)e].data() + c->d, c->c_M, c->d);
+        st_out[e] = FRR_OK;
     }
 
 cleanup:
 #undef PREP_CHECK
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
     // stream-ordered release: no device-wide synchronisation
-    for (void* p : {(void*)X, (void*)xbar, (void*)Xc, (void*)S, (void*)Adiag, (void*)Lm, (void*)ZT, (void*)scal,
-                    (void*)eps, (void*)status})
-        if (p) cudaFreeAsync(p, s);
+    if (base) cudaFreeAsync(base, s);
+    if (rc != FRR_OK)
+        for (int e = 0; e < E; ++e) st_out[e] = rc;
     return rc;
+}
+
+frr_status prep_run(frr_ctx* ctx, const double* X_host)
+{
+    frr_status st = FRR_OK;
+    const frr_status rc = prep_run_batch(&ctx, &X_host, 1, ctx->stream, ctx->aux, &st);
+    if (rc != FRR_OK) {
+        ctx->failed = true;
+        return rc;
+    }
+    return st;
 }
 
 }  // namespace frr
