@@ -300,7 +300,7 @@ def run_frr(args):
                 "adds_per_draw": adds}
         dtype = "f32"
     dist_line = distance_bench(peaks["bf16_tflops"]) if args.distance else None
-    batch_line = batched_bench() if args.batched else None
+    batch_line = batched_bench(args.batched_reps) if args.batched else None
     cpu = None
     if args.cpu_baseline:
         Zc = oracle_zc(X)
@@ -366,25 +366,34 @@ def distance_bench(peak_tflops: float, n: int = 16384, d: int = 768, reps: int =
 
 def batched_bench(reps: int = 3) -> dict:
     """frr_batch_run over the 256-experiment batched workload (n log-uniform on [50, 2000],
-    d on [10, 500], 1e5 draws and q = 0.01 each): preparation, one persistent balance launch
-    and per-experiment selection; host covariates, host results; median of `reps` runs."""
+    d on [10, 500], 1e5 draws and q = 0.01 each, then each experiment's randomization test
+    over its 201-point tau grid): batched preparation, one persistent balance launch per
+    class of n (autotuned, replayed as one CUDA graph), per-experiment selection and test;
+    host covariates and outcomes, host results; median of `reps` runs after one warm-up run
+    (which also tunes)."""
     from paper_2501_07642_b300 import frr
-    from paper_2501_07642_b300.workloads import batched_workloads
+    from paper_2501_07642_b300.workloads import batched_workloads, outcome
 
     ws = batched_workloads(256)
-    exps = [dict(X=w.covariates(), n1=w.n1, whiten=w.whiten, ridge=w.ridge, seed=w.philox_seed, B=w.draws, q=w.q,
-                 cap=2048) for w in ws]
-    frr.frr_batch_run(exps[:8])
+    exps = []
+    for w in ws:
+        X = w.covariates()
+        # outcome with no treatment effect (the test's w_obs is the first accepted key)
+        Y = outcome(X, np.zeros(w.n), 0.0, w.y_seed)
+        exps.append(dict(X=X, n1=w.n1, whiten=w.whiten, ridge=w.ridge, seed=w.philox_seed, B=w.draws, q=w.q,
+                         cap=2048, Y=Y, tau=w.tau_grid, alpha=0.05))
+    frr.frr_batch_run(exps, autotune=True)
     runs = []
     for _ in range(reps):
         t0 = time.perf_counter()
-        _, st = frr.frr_batch_run(exps)
+        _, st = frr.frr_batch_run(exps, autotune=True)
         runs.append((time.perf_counter() - t0, st))
     runs.sort(key=lambda r: r[0])
     dt, st = runs[len(runs) // 2]
     return {"workload": "batched_256", "experiments": 256, "draws": int(st["draws"]), "s_per_batch": dt,
             "draws_per_s": st["draws"] / dt, "ms_prep": st["ms_init"], "ms_balance": st["ms_balance"],
-            "ms_select": st["ms_select"], "note": "wall time of frr_batch_run with host inputs and outputs"}
+            "ms_select_and_tests": st["ms_select"], "randomization_tests": "201-point tau grid per experiment",
+            "note": "wall time of frr_batch_run with host inputs and outputs"}
 
 
 def tc_traffic(B):
@@ -418,9 +427,15 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-distance", dest="distance", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the 256-experiment batched leg and print its record (for profiling)")
+    ap.add_argument("--batched-reps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.batched_only:
+        print(json.dumps({"batched": batched_bench(args.batched_reps)}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -249,10 +249,14 @@ typedef struct {
     double ms_select;          /* wall time of selection, recheck and tests */
 } frr_batch_stats;
 
-/* Runs E independent experiments (Sec. 2.1 batched processing). With opts->precision =
- * FRR_SPLIT_BF16 the balance of every draw of every experiment is evaluated by one
- * persistent tensor-core launch over all experiments (shapes may differ); selection,
- * recheck and tests follow per experiment. opts: NULL for defaults (its whiten and ridge
+/* Runs E independent experiments (Sec. 2.1 batched processing). All experiments are
+ * prepared together (each preparation kernel covers every experiment). With
+ * opts->precision = FRR_SPLIT_BF16 the balance of every draw of every experiment is
+ * evaluated by one persistent tensor-core launch per class of n (Philox blocks per lane),
+ * each over all experiments of its class (shapes may differ), the launches replayed as one
+ * CUDA graph; opts->autotune = 1 times the kernel configurations of each class first.
+ * Selection, recheck and tests follow per experiment. Results equal those of frr_init +
+ * frr_select (+ frr_randtest) per experiment. opts: NULL for defaults (its whiten and ridge
  * are ignored; each experiment carries its own). Returns FRR_OK if every experiment
  * succeeded, else the first failing status; ex[e].status holds each one. stats may be NULL. */
 frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opts* opts, frr_batch_stats* stats);

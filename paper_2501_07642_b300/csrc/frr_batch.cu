@@ -1,14 +1,18 @@
-// frr_batch.cu -- frr_batch_run: many independent experiments, one balance launch.
+// frr_batch.cu -- frr_batch_run: many independent experiments, few launches.
 //
 // Sec. 2.1 evaluates candidates in batches to amortise launches and saturate the
-// device. Here the batch is a set of whole experiments of uneven n and d: each is
-// prepared (FP64 init) on its own, then the approximate balance of every draw of every
-// experiment comes from ONE persistent tcgen05 launch whose global tile index space
-// concatenates the experiments' draw tiles (experiment tables in device memory), so
-// small and large experiments share all SMs. Selection, exact recheck and the
-// randomization test then run per experiment on the resulting M_hat arrays. Preparation
-// and the per-experiment stages run on several host threads, one stream each, so that the
-// small kernels of different experiments run concurrently.
+// device. Here the batch is a set of whole experiments of uneven n and d:
+//   1. contexts are created (argument checks, fixed arrays) on a few host threads;
+//   2. all experiments are prepared together (FP64 init): every preparation kernel covers
+//      the blocks of every experiment (frr_prep.cu), one synchronisation at the end;
+//   3. the approximate balance of every draw of every experiment comes from one persistent
+//      tcgen05 launch per class of Philox blocks per lane (experiment tables in device
+//      memory, so small and large experiments share all SMs), the launches captured as
+//      parallel branches of one CUDA graph; the kernel configuration of each class is the
+//      built-in or autotuned one;
+//   4. selection, exact recheck and the randomization test run per experiment on the
+//      resulting M_hat arrays, on the host threads, one stream each, so that the small
+//      kernels of different experiments run concurrently.
 #include "frr_internal.cuh"
 
 #include <algorithm>
@@ -35,8 +39,10 @@ using namespace frr;
 
 namespace {
 
-// host worker threads of the batched driver (each owns one stream)
-constexpr int kWorkers = 8;
+// host worker threads of the batched driver (each owns one stream); more threads were slower
+// on B300 hosts (8: +5-15 %, 16 and 32: +25-45 % per batch), the CUDA driver serialising
+// their API calls
+constexpr int kWorkers = 4;
 
 template <typename F>
 void run_workers(int nw, F&& f)
@@ -163,71 +169,135 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
         cudaEventCreate(&eb);
         if (cudaMalloc(&mhat, off.back() * sizeof(float)) != cudaSuccess) { cudaGetLastError(); rc = FRR_E_NOMEM; }
         if (rc == FRR_OK && base.precision == FRR_SPLIT_BF16) {
-            std::vector<TcExp> table(live.size());
-            std::vector<unsigned long long> prefix(live.size() + 1, 0);
-            int kbmax = 1, nchmax = 1;
+            // Experiments are grouped by Philox blocks per lane (kb): each group runs in a
+            // persistent launch of the kernel configuration compiled (and tuned) for its kb, so
+            // short experiments get many generating warps instead of the register budget of the
+            // longest one. The group launches are captured as parallel branches of one CUDA
+            // graph; a group's CTAs start on the SMs that the previous group's tail frees.
+            std::vector<TcExp> desc(live.size());
             for (size_t k = 0; k < live.size() && rc == FRR_OK; ++k) {
                 const frr_experiment& x = ex[live[k]];
                 rc = tc_describe(ctx[live[k]], x.seed, x.seed == FRR_EXACT_SEED, x.first_draw, x.B, mhat + off[k],
-                                 &table[k]);
-                prefix[k + 1] = prefix[k] + (x.B + 127) / 128;
-                if (ctx[live[k]]->kb > kbmax) kbmax = ctx[live[k]]->kb;
-                if (table[k].nchunks > nchmax) nchmax = table[k].nchunks;
+                                 &desc[k]);
             }
-            // probe batch for the tuner: every experiment with about 1/16 of its draws
-            std::vector<TcExp> probe;
-            std::vector<unsigned long long> probe_prefix;
-            if (rc == FRR_OK && base.autotune) {
-                probe = table;
-                probe_prefix.assign(live.size() + 1, 0);
+            struct Group {
+                int kb = 0, nch = 1;
+                size_t t0 = 0, cnt = 0;          // slice of the concatenated tables
+                size_t p0 = 0, pp0 = 0;          // slices of the concatenated prefix arrays
+                unsigned long long tiles = 0, probe_tiles = 0;
+            };
+            std::vector<Group> groups;
+            std::vector<TcExp> table, probe;
+            std::vector<unsigned long long> prefix, probe_prefix;
+            for (int kb = 16; kb >= 1 && rc == FRR_OK; kb >>= 1) {
+                Group g;
+                g.kb = kb;
+                g.t0 = table.size();
+                g.p0 = prefix.size();
+                g.pp0 = probe_prefix.size();
+                prefix.push_back(0);
+                probe_prefix.push_back(0);
                 for (size_t k = 0; k < live.size(); ++k) {
-                    const uint64_t tiles_k = (probe[k].B + 127) / 128;
-                    const uint64_t pt = std::max<uint64_t>(1, tiles_k / 16);
-                    probe[k].B = std::min<uint64_t>(probe[k].B, pt * 128);
-                    probe_prefix[k + 1] = probe_prefix[k] + pt;
+                    if (ctx[live[k]]->kb != kb) continue;
+                    table.push_back(desc[k]);
+                    const uint64_t tk = (desc[k].B + 127) / 128;
+                    g.tiles += tk;
+                    prefix.push_back(g.tiles);
+                    g.nch = std::max(g.nch, desc[k].nchunks);
+                    // probe for the tuner: about 1/16 of each experiment's tiles
+                    TcExp pr = desc[k];
+                    const uint64_t pt = std::max<uint64_t>(1, tk / 16);
+                    pr.B = std::min<uint64_t>(pr.B, pt * 128);
+                    probe.push_back(pr);
+                    g.probe_tiles += pt;
+                    probe_prefix.push_back(g.probe_tiles);
                 }
+                g.cnt = table.size() - g.t0;
+                if (g.cnt == 0) {
+                    prefix.resize(g.p0);
+                    probe_prefix.resize(g.pp0);
+                    continue;
+                }
+                groups.push_back(g);
             }
-            if (rc == FRR_OK &&
-                (cudaMalloc(&d_table, table.size() * sizeof(TcExp)) != cudaSuccess ||
-                 cudaMalloc(&d_prefix, prefix.size() * sizeof(unsigned long long)) != cudaSuccess ||
-                 cudaMalloc(&d_err, sizeof(int)) != cudaSuccess)) {
+            // one device block: tables, probe tables, prefixes, probe prefixes, error word
+            const size_t tb = table.size() * sizeof(TcExp);
+            const size_t pb = prefix.size() * sizeof(unsigned long long);
+            const size_t ppb = probe_prefix.size() * sizeof(unsigned long long);
+            char* dbuf = nullptr;
+            if (rc == FRR_OK && cudaMalloc(&dbuf, 2 * tb + pb + ppb + 256) != cudaSuccess) {
                 cudaGetLastError();
                 rc = FRR_E_NOMEM;
             }
-            if (rc == FRR_OK && base.autotune) {
-                cudaMemcpyAsync(d_table, probe.data(), probe.size() * sizeof(TcExp), cudaMemcpyHostToDevice, stream);
-                cudaMemcpyAsync(d_prefix, probe_prefix.data(), probe_prefix.size() * sizeof(unsigned long long),
-                                cudaMemcpyHostToDevice, stream);
-                cudaMemsetAsync(d_err, 0, sizeof(int), stream);
-                rc = balance_tc_batch_tune(owner, stream, d_table, d_prefix, (int)live.size(), probe_prefix.back(),
-                                           kbmax, nchmax, d_err);
-                int herr = 0;
-                if (rc == FRR_OK && (cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-                                     cudaStreamSynchronize(stream) != cudaSuccess)) {
-                    cudaGetLastError();
-                    rc = FRR_E_CUDA;
-                } else if (rc == FRR_OK && herr != 0) {
-                    rc = FRR_E_TIMEOUT;
-                }
-            }
             if (rc == FRR_OK) {
-                cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(TcExp), cudaMemcpyHostToDevice, stream);
-                cudaMemcpyAsync(d_prefix, prefix.data(), prefix.size() * sizeof(unsigned long long),
-                                cudaMemcpyHostToDevice, stream);
+                d_table = reinterpret_cast<TcExp*>(dbuf);
+                TcExp* d_probe = reinterpret_cast<TcExp*>(dbuf + tb);
+                d_prefix = reinterpret_cast<unsigned long long*>(dbuf + 2 * tb);
+                unsigned long long* d_pprefix = reinterpret_cast<unsigned long long*>(dbuf + 2 * tb + pb);
+                d_err = reinterpret_cast<int*>(dbuf + 2 * tb + pb + ppb);
+                cudaMemcpyAsync(d_table, table.data(), tb, cudaMemcpyHostToDevice, stream);
+                cudaMemcpyAsync(d_probe, probe.data(), tb, cudaMemcpyHostToDevice, stream);
+                cudaMemcpyAsync(d_prefix, prefix.data(), pb, cudaMemcpyHostToDevice, stream);
+                cudaMemcpyAsync(d_pprefix, probe_prefix.data(), ppb, cudaMemcpyHostToDevice, stream);
                 cudaMemsetAsync(d_err, 0, sizeof(int), stream);
-                cudaEventRecord(ea, stream);
-                rc = balance_tc_batch_launch(owner, stream, d_table, d_prefix, (int)live.size(), prefix.back(), kbmax,
-                                             nchmax, d_err);
-                cudaEventRecord(eb, stream);
-                int herr = 0;
-                if (cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-                    cudaStreamSynchronize(stream) != cudaSuccess) {
-                    cudaGetLastError();
-                    rc = FRR_E_CUDA;
-                } else if (herr != 0) {
-                    rc = FRR_E_TIMEOUT;
+                for (const Group& g : groups) {
+                    if (!base.autotune || rc != FRR_OK) break;
+                    rc = balance_tc_batch_tune(owner, stream, d_probe + g.t0, d_pprefix + g.pp0, (int)g.cnt,
+                                               g.probe_tiles, g.kb, g.nch, d_err);
                 }
+                // the launches of all groups as one graph: a fork from `stream`, one branch per
+                // group on its own capture stream, joined back into `stream`
+                std::vector<cudaStream_t> gs(groups.size(), nullptr);
+                std::vector<cudaEvent_t> gev(groups.size() + 1, nullptr);
+                cudaGraph_t graph = nullptr;
+                cudaGraphExec_t exec = nullptr;
+                bool ok = rc == FRR_OK;
+                for (size_t i = 0; i < groups.size() && ok; ++i)
+                    ok = cudaStreamCreateWithFlags(&gs[i], cudaStreamNonBlocking) == cudaSuccess;
+                for (size_t i = 0; i < gev.size() && ok; ++i)
+                    ok = cudaEventCreateWithFlags(&gev[i], cudaEventDisableTiming) == cudaSuccess;
+                if (ok && cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+                    bool cap = cudaEventRecord(gev[0], stream) == cudaSuccess;
+                    for (size_t i = 0; i < groups.size() && cap; ++i) {
+                        const Group& g = groups[i];
+                        cap = cudaStreamWaitEvent(gs[i], gev[0], 0) == cudaSuccess &&
+                              balance_tc_batch_launch(owner, gs[i], d_table + g.t0, d_prefix + g.p0, (int)g.cnt,
+                                                      g.tiles, g.kb, g.nch, d_err) == FRR_OK &&
+                              cudaEventRecord(gev[i + 1], gs[i]) == cudaSuccess &&
+                              cudaStreamWaitEvent(stream, gev[i + 1], 0) == cudaSuccess;
+                    }
+                    const bool ended = cudaStreamEndCapture(stream, &graph) == cudaSuccess;
+                    ok = cap && ended && graph != nullptr &&
+                         cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+                } else {
+                    ok = false;
+                }
+                if (ok) {
+                    cudaEventRecord(ea, stream);
+                    ok = cudaGraphLaunch(exec, stream) == cudaSuccess;
+                    cudaEventRecord(eb, stream);
+                }
+                int herr = 0;
+                if (rc == FRR_OK) {
+                    if (!ok || cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+                        cudaStreamSynchronize(stream) != cudaSuccess) {
+                        cudaGetLastError();
+                        rc = FRR_E_CUDA;
+                    } else if (herr != 0) {
+                        rc = FRR_E_TIMEOUT;
+                    }
+                }
+                if (exec) cudaGraphExecDestroy(exec);
+                if (graph) cudaGraphDestroy(graph);
+                for (cudaEvent_t ev : gev)
+                    if (ev) cudaEventDestroy(ev);
+                for (cudaStream_t st : gs)
+                    if (st) cudaStreamDestroy(st);
+                cudaGetLastError();
             }
+            d_prefix = nullptr;  // parts of dbuf
+            d_err = nullptr;
+            d_table = reinterpret_cast<TcExp*>(dbuf);
         } else if (rc == FRR_OK) {
             cudaEventRecord(ea, stream);
             // FP32: one launch per experiment, on its context's stream
@@ -252,6 +322,9 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
                 frr_experiment& x = ex[e];
                 if (rc != FRR_OK) { st_sel[k] = rc; continue; }
                 frr_status s = stream_begin(ctx[e], x.seed, x.q, x.threshold, x.B);
+                // one chunk: the recheck may read the candidate count on the device (no read-back
+                // between the selection and the recheck)
+                ctx[e]->st.defer_count = true;
                 if (s == FRR_OK) s = stream_chunk_precomputed(ctx[e], x.first_draw, x.B, mhat + off[k]);
                 int64_t K = 0;
                 if (s == FRR_OK) s = stream_end(ctx[e], x.keys_out, x.M64_out, x.cap, &K);

@@ -19,22 +19,35 @@
 namespace frr {
 namespace {
 
-// a_k with the same ascending-unit sums as the plain definition; b_k from popcounts.
+// a_k and b_k, one warp per key: lane l sums the treated and control outcomes of units
+// l, l + 32, ... and the warp adds the lane sums in a fixed tree. (A single thread summing
+// n units in order is a chain of n dependent FP64 additions, about 64 cycles each on B300.
+// The different summation order changes a_k only in its last bits, so a comparison
+// |t_k| >= |t_obs| can differ from an in-order evaluation only at numerical near-ties,
+// which the tests allow and the oracle flags.) b_k from popcounts.
 __global__ void k_contrasts(const uint32_t* __restrict__ rows, int words, int64_t K, int64_t obs, int n, int n1,
                             const double* __restrict__ Y, double* __restrict__ a, double* __restrict__ b)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (k >= K) return;
     const uint32_t* row = rows + k * words;
     const uint32_t* orow = rows + obs * words;
     double s1 = 0.0, s0 = 0.0;
-    for (int i = 0; i < n; ++i) {
+    for (int i = lane; i < n; i += 32) {
         const int p = kpos_of_unit(i);
         if ((row[p >> 5] >> (p & 31)) & 1u) s1 = __dadd_rn(s1, Y[i]);
         else s0 = __dadd_rn(s0, Y[i]);
     }
     int c = 0;
-    for (int q = 0; q < words; ++q) c += __popc(row[q] & orow[q]);
+    for (int q = lane; q < words; q += 32) c += __popc(row[q] & orow[q]);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        s1 = __dadd_rn(s1, __shfl_xor_sync(kFull, s1, off));
+        s0 = __dadd_rn(s0, __shfl_xor_sync(kFull, s0, off));
+        c += __shfl_xor_sync(kFull, c, off);
+    }
+    if (lane != 0) return;
     const int n0 = n - n1;
     a[k] = __dsub_rn(__ddiv_rn(s1, (double)n1), __ddiv_rn(s0, (double)n0));
     b[k] = __dsub_rn(__ddiv_rn((double)c, (double)n1), __ddiv_rn((double)(n1 - c), (double)n0));
@@ -72,19 +85,27 @@ __global__ void k_tau_grid(const double* __restrict__ a, const double* __restric
     }
 }
 
+// [min, max] of the grid points with p > alpha; one warp (the FP64 comparisons of a single
+// thread over T points form a long dependent chain on B300's narrow FP64 unit)
 __global__ void k_interval(const double* __restrict__ p, const double* __restrict__ tau, int64_t T, double alpha,
                            double* __restrict__ out)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    double lo = NAN, hi = NAN;
-    for (int64_t g = 0; g < T; ++g) {
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t g = threadIdx.x; g < T; g += 32)
         if (p[g] > alpha) {
-            if (isnan(lo) || tau[g] < lo) lo = tau[g];
-            if (isnan(hi) || tau[g] > hi) hi = tau[g];
+            lo = fmin(lo, tau[g]);
+            hi = fmax(hi, tau[g]);
         }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(kFull, lo, off));
+        hi = fmax(hi, __shfl_xor_sync(kFull, hi, off));
     }
-    out[0] = lo;
-    out[1] = hi;
+    if (threadIdx.x == 0) {
+        out[0] = (lo == INFINITY) ? NAN : lo;
+        out[1] = (hi == -INFINITY) ? NAN : hi;
+    }
 }
 
 }  // namespace
@@ -134,9 +155,9 @@ frr_status randtest_run(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64
     FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dy, hy.data(), (size_t)n * 8, cudaMemcpyHostToDevice, ctx->stream));
     FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dtau, ht.data(), (size_t)T * 8, cudaMemcpyHostToDevice, ctx->stream));
     FRR_TRY(bits_launch(ctx, seed, exact, 0, (uint64_t)K, dkeys, rows));
-    k_contrasts<<<ceil_div(K, 128), 128, 0, ctx->stream>>>(rows, words, K, obs, n, (int)ctx->n1, dy, da, db);
+    k_contrasts<<<ceil_div(K, 4), 128, 0, ctx->stream>>>(rows, words, K, obs, n, (int)ctx->n1, dy, da, db);
     k_tau_grid<<<(unsigned)T, 256, 0, ctx->stream>>>(da, db, K, obs, dtau, dcount, dp, dnear);
-    k_interval<<<1, 1, 0, ctx->stream>>>(dp, dtau, T, alpha, dci);
+    k_interval<<<1, 32, 0, ctx->stream>>>(dp, dtau, T, alpha, dci);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     FRR_TRY(copy_out(ctx, p_out, dp, (size_t)T * sizeof(double)));
     if (count_out) FRR_TRY(copy_out(ctx, count_out, dcount, (size_t)T * sizeof(long long)));

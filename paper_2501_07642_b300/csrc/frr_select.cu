@@ -744,8 +744,13 @@ frr_status stream_chunk_precomputed(frr_ctx* ctx, uint64_t first, uint64_t B, co
     if (st.seen + B > st.total) return FRR_E_RANGE;
     for (uint64_t off = 0; off < B; off += kChunkMax) {
         const uint64_t bc = std::min<uint64_t>(kChunkMax, B - off);
+        cudaEventRecord(ctx->ev[0], ctx->stream);  // no balance here: an empty interval
         cudaEventRecord(ctx->ev[1], ctx->stream);
         FRR_TRY(stream_select_step(ctx, first + off, bc, Mhat + off, st.seen + off + bc == st.total));
+        if (st.retained < 0) {
+            st.times_pending = true;  // nothing was synchronised: read the events in stream_end
+            continue;
+        }
         float t2 = 0.f;
         cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
         ctx->stats.ms_select += t2;
