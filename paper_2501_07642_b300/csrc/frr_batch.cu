@@ -331,7 +331,8 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
                 x.K_out = K;
                 if (s == FRR_OK && x.Y != nullptr && K > 0) {
                     uint64_t obs = 0;
-                    s = copy_out(ctx[e], &obs, x.keys_out, sizeof(uint64_t));
+                    if (is_device_ptr(x.keys_out)) s = copy_out(ctx[e], &obs, x.keys_out, sizeof(uint64_t));
+                    else obs = x.keys_out[0];
                     if (s == FRR_OK) {
                         if (!x.tau || x.T < 1 || !x.p_out || !(x.alpha >= 0.0 && x.alpha <= 1.0)) s = FRR_E_ARG;
                         else s = randtest_run(ctx[e], x.seed, x.keys_out, K, obs, x.Y, x.tau, x.T, x.alpha, x.p_out,

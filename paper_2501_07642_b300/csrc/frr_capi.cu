@@ -45,17 +45,53 @@ frr_status ensure_device(frr_ctx* ctx, void** buf, size_t* cap_bytes, size_t byt
     return FRR_OK;
 }
 
+// Pinned host blocks are kept by the library between contexts (power-of-two sizes from
+// 4 KiB): cudaMallocHost is slow and cudaFreeHost synchronises the device, which a batch of
+// many short-lived contexts would otherwise pay once per context.
+namespace {
+std::mutex g_pinned_mu;
+std::unordered_map<size_t, std::vector<void*>> g_pinned_free;
+
+size_t pinned_class(size_t bytes)
+{
+    size_t c = 4096;
+    while (c < bytes) c <<= 1;
+    return c;
+}
+}  // namespace
+
+void pinned_put(void* p, size_t cap)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    g_pinned_free[cap].push_back(p);
+}
+
 frr_status ensure_host_pinned(frr_ctx* ctx, size_t bytes)
 {
     if (ctx->host_pinned != nullptr && ctx->host_pinned_bytes >= bytes) return FRR_OK;
-    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    // the old block may still be the target of a copy in flight on this stream
+    if (ctx->host_pinned) {
+        FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        pinned_put(ctx->host_pinned, ctx->host_pinned_bytes);
+    }
     ctx->host_pinned = nullptr;
     ctx->host_pinned_bytes = 0;
-    if (cudaMallocHost(&ctx->host_pinned, bytes) != cudaSuccess) {
+    const size_t cap = pinned_class(bytes);
+    {
+        std::lock_guard<std::mutex> lock(g_pinned_mu);
+        auto it = g_pinned_free.find(cap);
+        if (it != g_pinned_free.end() && !it->second.empty()) {
+            ctx->host_pinned = it->second.back();
+            it->second.pop_back();
+        }
+    }
+    if (ctx->host_pinned == nullptr && cudaMallocHost(&ctx->host_pinned, cap) != cudaSuccess) {
         cudaGetLastError();
+        ctx->host_pinned = nullptr;
         return FRR_E_NOMEM;
     }
-    ctx->host_pinned_bytes = bytes;
+    ctx->host_pinned_bytes = cap;
     return FRR_OK;
 }
 
@@ -129,7 +165,7 @@ static void release(frr_ctx* ctx)
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, ctx->stream ? ctx->stream : 0);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    pinned_put(ctx->host_pinned, ctx->host_pinned_bytes);
     for (cudaEvent_t e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);

@@ -14,6 +14,7 @@
 #include "frr_internal.cuh"
 #include "frr_gen.cuh"
 
+#include <cstring>
 #include <vector>
 
 namespace frr {
@@ -117,9 +118,30 @@ frr_status randtest_run(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64
     const bool exact = (seed == FRR_EXACT_SEED);
     const int n = (int)ctx->n;
     const int words = 4 * ctx->kb;
-    // host copy of the keys to locate the observed one and validate
-    std::vector<uint64_t> hk((size_t)K);
-    FRR_TRY(copy_out(ctx, hk.data(), keys, (size_t)K * sizeof(uint64_t)));
+    // host views of the inputs: host memory is read in place; device inputs are copied
+    // back together (one synchronisation)
+    const bool keys_dev = is_device_ptr(keys), y_dev = is_device_ptr(Y), tau_dev = is_device_ptr(tau);
+    std::vector<uint64_t> hk_buf;
+    std::vector<double> hy_buf, ht_buf;
+    const uint64_t* hk = keys;
+    const double* hy = Y;
+    const double* ht = tau;
+    if (keys_dev) {
+        hk_buf.resize((size_t)K);
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk_buf.data(), keys, (size_t)K * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        hk = hk_buf.data();
+    }
+    if (y_dev) {
+        hy_buf.resize((size_t)n);
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hy_buf.data(), Y, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        hy = hy_buf.data();
+    }
+    if (tau_dev) {
+        ht_buf.resize((size_t)T);
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(ht_buf.data(), tau, (size_t)T * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        ht = ht_buf.data();
+    }
+    if (keys_dev || y_dev || tau_dev) FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     int64_t obs = -1;
     for (int64_t k = 0; k < K; ++k)
         if (hk[k] == obs_key) { obs = k; break; }
@@ -129,16 +151,15 @@ frr_status randtest_run(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64
         for (int64_t k = 0; k < K; ++k)
             if (hk[k] >= tot) return FRR_E_RANGE;
     }
-    std::vector<double> hy((size_t)n), ht((size_t)T);
-    FRR_TRY(copy_out(ctx, hy.data(), Y, (size_t)n * sizeof(double)));
-    FRR_TRY(copy_out(ctx, ht.data(), tau, (size_t)T * sizeof(double)));
-    for (double v : hy) if (!isfinite(v)) return FRR_E_ARG;
-    for (double v : ht) if (!isfinite(v)) return FRR_E_ARG;
+    for (int i = 0; i < n; ++i) if (!isfinite(hy[i])) return FRR_E_ARG;
+    for (int64_t g = 0; g < T; ++g) if (!isfinite(ht[g])) return FRR_E_ARG;
 
     // scratch: keys (K), rows (K x words), Y (n), tau (T), a (K), b (K), count (T), near (T), p (T), ci (2)
     const size_t bytes = (size_t)K * 8 + (size_t)K * words * 4 + 8 + (size_t)n * 8 + (size_t)T * 8 + (size_t)K * 16 +
                          (size_t)T * 24 + 16 + 64;
     FRR_TRY(ensure_device(ctx, &ctx->misc, &ctx->misc_bytes, bytes));
+    // pinned staging of the host outputs: p (T), count (T), ci (2)
+    FRR_TRY(ensure_host_pinned(ctx, (size_t)T * 16 + 16));
     char* base = static_cast<char*>(ctx->misc);
     uint64_t* dkeys = reinterpret_cast<uint64_t*>(base);
     double* dy = reinterpret_cast<double*>(dkeys + K);
@@ -151,20 +172,32 @@ frr_status randtest_run(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64
     long long* dnear = dcount + T;
     uint32_t* rows = reinterpret_cast<uint32_t*>(dnear + T);
 
-    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dkeys, hk.data(), (size_t)K * 8, cudaMemcpyHostToDevice, ctx->stream));
-    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dy, hy.data(), (size_t)n * 8, cudaMemcpyHostToDevice, ctx->stream));
-    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dtau, ht.data(), (size_t)T * 8, cudaMemcpyHostToDevice, ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dkeys, keys, (size_t)K * 8, cudaMemcpyDefault, ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dy, Y, (size_t)n * 8, cudaMemcpyDefault, ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dtau, tau, (size_t)T * 8, cudaMemcpyDefault, ctx->stream));
     FRR_TRY(bits_launch(ctx, seed, exact, 0, (uint64_t)K, dkeys, rows));
     k_contrasts<<<ceil_div(K, 4), 128, 0, ctx->stream>>>(rows, words, K, obs, n, (int)ctx->n1, dy, da, db);
     k_tau_grid<<<(unsigned)T, 256, 0, ctx->stream>>>(da, db, K, obs, dtau, dcount, dp, dnear);
     k_interval<<<1, 32, 0, ctx->stream>>>(dp, dtau, T, alpha, dci);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
-    FRR_TRY(copy_out(ctx, p_out, dp, (size_t)T * sizeof(double)));
-    if (count_out) FRR_TRY(copy_out(ctx, count_out, dcount, (size_t)T * sizeof(long long)));
-    double ci[2];
-    FRR_TRY(copy_out(ctx, ci, dci, 2 * sizeof(double)));
-    if (ci_lo) *ci_lo = ci[0];
-    if (ci_hi) *ci_hi = ci[1];
+    // outputs: device ones copied on the stream, host ones through the pinned staging; one
+    // synchronisation for all
+    double* sp = static_cast<double*>(ctx->host_pinned);
+    long long* scount = reinterpret_cast<long long*>(sp + T);
+    double* sci = reinterpret_cast<double*>(scount + T);
+    const bool p_dev = is_device_ptr(p_out);
+    const bool c_dev = count_out != nullptr && is_device_ptr(count_out);
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(p_dev ? (void*)p_out : (void*)sp, dp, (size_t)T * 8,
+                                      p_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if (count_out)
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(c_dev ? (void*)count_out : (void*)scount, dcount, (size_t)T * 8,
+                                          c_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(sci, dci, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!p_dev) memcpy(p_out, sp, (size_t)T * 8);
+    if (count_out && !c_dev) memcpy(count_out, scount, (size_t)T * 8);
+    if (ci_lo) *ci_lo = sci[0];
+    if (ci_hi) *ci_hi = sci[1];
     return FRR_OK;
 }
 

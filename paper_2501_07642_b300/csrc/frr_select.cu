@@ -772,7 +772,16 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
     const int cur = ctx->ret_cur;
     SelState* sel = static_cast<SelState*>(ctx->sel);
     const long long* r_dev = dev_count ? &sel->kept : nullptr;
-    FRR_TRY(ensure_host_pinned(ctx, 256));
+    // Where the accepted keys go. q mode accepts exactly K draws, so when K fits the
+    // placement kernel writes them straight into device outputs; host outputs are copied
+    // into pinned memory together with the summary (the first min(cap, r) entries hold them
+    // whenever they fit). Either way one synchronisation serves the call.
+    const bool host_keys = cap > 0 && !is_device_ptr(keys_out);
+    const bool host_m = M64_out != nullptr && cap > 0 && !is_device_ptr(M64_out);
+    const bool direct = st.q_mode && st.K <= cap && !host_keys && !host_m;
+    const int64_t stage_n = std::min<int64_t>(cap, rb);
+    const bool stage = !direct && (host_keys || host_m) && stage_n > 0;
+    FRR_TRY(ensure_host_pinned(ctx, 256 + (stage ? (size_t)stage_n * 16 : 0)));
     cudaEventRecord(ctx->ev[3], ctx->stream);
     // scratch: M64 (r), M64 out (r), keys out (r), rank (r)
     const size_t need = (size_t)rb * (3 * sizeof(double) + sizeof(int)) + 64;
@@ -783,6 +792,10 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
     uint64_t* kout = reinterpret_cast<uint64_t*>(mout + rb);
     int* rank = reinterpret_cast<int*>(kout + rb);
     char* hp = static_cast<char*>(ctx->host_pinned);
+    uint64_t* hk = reinterpret_cast<uint64_t*>(hp + 256);
+    double* hm = reinterpret_cast<double*>(hk + stage_n);
+    uint64_t* place_k = direct ? keys_out : kout;
+    double* place_m = (direct && M64_out) ? M64_out : mout;
     SelTail tail{};
     tail.boundary[0] = tail.boundary[1] = NAN;
     if (rb > 0) {
@@ -794,7 +807,7 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
         if (!st.q_mode && st.threshold >= 0.0) memcpy(&thr_bits, &st.threshold, sizeof(thr_bits));
         k_rank<<<warp_grid(ctx, rb), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], rb, r_dev, rank);
         k_place_sel<<<warp_grid(ctx, rb), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], rank, rb, r_dev, st.K,
-                                                                st.q_mode ? 1 : 0, thr_bits, kout, mout);
+                                                                st.q_mode ? 1 : 0, thr_bits, place_k, place_m);
         k_sel_summary<<<1, SNT, 0, ctx->stream>>>(m64, rank, ctx->ret_m[cur], rb, r_dev, st.K, st.q_mode ? 1 : 0,
                                                   thr_bits, cut_params(ctx), sel);
         FRR_CUDA_TRY(ctx, cudaGetLastError());
@@ -803,6 +816,12 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
                                           ctx->stream));
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hp + 128, ctx->dev_counters + 12, sizeof(int), cudaMemcpyDeviceToHost,
                                           ctx->stream));
+        if (stage) {
+            if (host_keys)
+                FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk, kout, (size_t)stage_n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+            if (host_m)
+                FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hm, mout, (size_t)stage_n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        }
     }
     cudaEventRecord(ctx->ev[4], ctx->stream);
     FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -846,11 +865,25 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
         ctx->stats.parity_at_risk = ctx->stats.boundary_gap_rel < 1e-11 ? 1 : 0;
     }
     if (nsel > cap) return FRR_E_CAPACITY;
-    if (nsel > 0) {
-        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(keys_out, kout, (size_t)nsel * sizeof(uint64_t), cudaMemcpyDefault, ctx->stream));
-        if (M64_out)
-            FRR_CUDA_TRY(ctx, cudaMemcpyAsync(M64_out, mout, (size_t)nsel * sizeof(double), cudaMemcpyDefault, ctx->stream));
-        FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (nsel > 0 && !direct) {
+        bool device_copies = false;
+        if (host_keys) {
+            memcpy(keys_out, hk, (size_t)nsel * sizeof(uint64_t));
+        } else {
+            FRR_CUDA_TRY(ctx, cudaMemcpyAsync(keys_out, kout, (size_t)nsel * sizeof(uint64_t), cudaMemcpyDefault,
+                                              ctx->stream));
+            device_copies = true;
+        }
+        if (M64_out) {
+            if (host_m) {
+                memcpy(M64_out, hm, (size_t)nsel * sizeof(double));
+            } else {
+                FRR_CUDA_TRY(ctx, cudaMemcpyAsync(M64_out, mout, (size_t)nsel * sizeof(double), cudaMemcpyDefault,
+                                                  ctx->stream));
+                device_copies = true;
+            }
+        }
+        if (device_copies) FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     }
     return FRR_OK;
 }
