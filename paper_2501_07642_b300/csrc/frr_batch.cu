@@ -39,10 +39,12 @@ using namespace frr;
 
 namespace {
 
-// host worker threads of the batched driver (each owns one stream); more threads were slower
-// on B300 hosts (8: +5-15 %, 16 and 32: +25-45 % per batch), the CUDA driver serialising
-// their API calls
+// host threads that check arguments and create contexts (the scan of X for non-finite values
+// is the larger part); the CUDA calls themselves are issued from one thread, since the driver
+// serialised calls from several (8 threads made a batch 5-15 % slower, 16 and 32 up to 45 %)
 constexpr int kWorkers = 4;
+// streams of the contexts: the selection and test chains of different experiments overlap
+constexpr int kStreams = 8;
 
 template <typename F>
 void run_workers(int nw, F&& f)
@@ -83,15 +85,16 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
     // contexts allocate stream-ordered from a pool, so the threads do not synchronise the
     // device through allocations).
     const int nw = (int)std::min<int64_t>(kWorkers, E);
-    std::vector<cudaStream_t> ws((size_t)nw, nullptr);
-    for (int w = 0; w < nw; ++w)
+    // the contexts' streams, assigned round-robin (experiment e runs on ws[e % ns])
+    const int ns = (int)std::min<int64_t>(kStreams, E);
+    std::vector<cudaStream_t> ws((size_t)ns, nullptr);
+    for (int w = 0; w < ns; ++w)
         if (cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
             ws[w] = stream;
         }
     std::vector<frr_status> st_init((size_t)E, FRR_OK);
-    // argument checks and context creation on the worker threads (each context later runs
-    // its selection on the stream of the worker that created it)
+    // argument checks and context creation on the worker threads
     auto create = [&](int w) {
         for (int64_t e = w; e < E; e += nw) {
             ex[e].K_out = 0;
@@ -105,7 +108,7 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             frr_opts o = base;
             o.whiten = ex[e].whiten;
             o.ridge = ex[e].ridge;
-            o.cuda_stream = ws[w];
+            o.cuda_stream = ws[(size_t)(e % ns)];
             frr_status s = check_init_args(ex[e].X, ex[e].n, ex[e].d, ex[e].n1, o);
             if (s == FRR_OK && ex[e].seed == FRR_EXACT_SEED) {
                 if (ex[e].n > kExactMaxN) s = FRR_E_UNSUPPORTED;
@@ -114,10 +117,11 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             if (s == FRR_OK) s = ctx_create(&ctx[e], ex[e].n, ex[e].d, ex[e].n1, o, false);
             st_init[e] = s;
         }
-        // the contexts' arrays come from stream-ordered allocations on this worker's stream
-        if (cudaStreamSynchronize(ws[w]) != cudaSuccess) cudaGetLastError();
     };
     run_workers(nw, create);
+    // the contexts' arrays come from stream-ordered allocations on their streams
+    for (cudaStream_t w : ws)
+        if (cudaStreamSynchronize(w) != cudaSuccess) cudaGetLastError();
     {
         // one preparation of every created context: each launch covers all of them
         std::vector<frr_ctx*> pc;
@@ -313,36 +317,108 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
         cudaEventElapsedTime(&ms_balance, ea, eb);
         cudaEventDestroy(ea);
         cudaEventDestroy(eb);
-        // selection, recheck and tests per experiment, on the workers' streams (each context
-        // is used by one thread only)
+        // Selection, recheck and tests, issued from this thread. q-mode experiments whose test
+        // inputs are in host memory are pipelined: each one's whole chain is enqueued on its
+        // context's stream without a read-back (q mode accepts exactly K draws, so the test
+        // reads the placed keys on the device), and the results are collected after every
+        // chain is enqueued. The others (threshold mode, device test inputs) run one by one.
         std::vector<frr_status> st_sel(live.size(), FRR_OK);
-        auto finish = [&](int w) {
-            for (size_t k = (size_t)w; k < live.size(); k += (size_t)nw) {
-                const int64_t e = live[k];
-                frr_experiment& x = ex[e];
-                if (rc != FRR_OK) { st_sel[k] = rc; continue; }
-                frr_status s = stream_begin(ctx[e], x.seed, x.q, x.threshold, x.B);
-                // one chunk: the recheck may read the candidate count on the device (no read-back
-                // between the selection and the recheck)
-                ctx[e]->st.defer_count = true;
-                if (s == FRR_OK) s = stream_chunk_precomputed(ctx[e], x.first_draw, x.B, mhat + off[k]);
-                int64_t K = 0;
-                if (s == FRR_OK) s = stream_end(ctx[e], x.keys_out, x.M64_out, x.cap, &K);
-                x.K_out = K;
-                if (s == FRR_OK && x.Y != nullptr && K > 0) {
-                    uint64_t obs = 0;
-                    if (is_device_ptr(x.keys_out)) s = copy_out(ctx[e], &obs, x.keys_out, sizeof(uint64_t));
-                    else obs = x.keys_out[0];
-                    if (s == FRR_OK) {
-                        if (!x.tau || x.T < 1 || !x.p_out || !(x.alpha >= 0.0 && x.alpha <= 1.0)) s = FRR_E_ARG;
-                        else s = randtest_run(ctx[e], x.seed, x.keys_out, K, obs, x.Y, x.tau, x.T, x.alpha, x.p_out,
-                                              x.count_out, &x.ci_lo, &x.ci_hi);
+        auto one_by_one = [&](size_t k) -> frr_status {
+            const int64_t e = live[k];
+            frr_experiment& x = ex[e];
+            frr_status s = stream_begin(ctx[e], x.seed, x.q, x.threshold, x.B);
+            // one chunk: the recheck may read the candidate count on the device
+            ctx[e]->st.defer_count = true;
+            if (s == FRR_OK) s = stream_chunk_precomputed(ctx[e], x.first_draw, x.B, mhat + off[k]);
+            int64_t K = 0;
+            if (s == FRR_OK) s = stream_end(ctx[e], x.keys_out, x.M64_out, x.cap, &K);
+            x.K_out = K;
+            if (s == FRR_OK && x.Y != nullptr && K > 0) {
+                uint64_t obs = 0;
+                if (is_device_ptr(x.keys_out)) s = copy_out(ctx[e], &obs, x.keys_out, sizeof(uint64_t));
+                else obs = x.keys_out[0];
+                if (s == FRR_OK) {
+                    if (!x.tau || x.T < 1 || !x.p_out || !(x.alpha >= 0.0 && x.alpha <= 1.0)) s = FRR_E_ARG;
+                    else s = randtest_run(ctx[e], x.seed, x.keys_out, K, obs, x.Y, x.tau, x.T, x.alpha, x.p_out,
+                                          x.count_out, &x.ci_lo, &x.ci_hi);
+                }
+            }
+            return s;
+        };
+        struct Pending {
+            bool piped = false, test = false, p_dev = false, c_dev = false;
+            size_t off = 0;
+        };
+        std::vector<Pending> pend(live.size());
+        for (size_t k = 0; k < live.size() && rc == FRR_OK; ++k) {
+            const int64_t e = live[k];
+            frr_experiment& x = ex[e];
+            frr_ctx* c = ctx[e];
+            const bool host_test = x.Y == nullptr || (!is_device_ptr(x.Y) && x.tau != nullptr && !is_device_ptr(x.tau));
+            if (isnan(x.q) || !host_test) continue;
+            Pending& P = pend[k];
+            P.piped = true;
+            frr_status s = stream_begin(c, x.seed, x.q, x.threshold, x.B);
+            c->st.defer_count = true;
+            if (s == FRR_OK) s = stream_chunk_precomputed(c, x.first_draw, x.B, mhat + off[k]);
+            size_t extra = 0;
+            if (s == FRR_OK && x.Y != nullptr) {
+                if (!x.tau || x.T < 1 || !x.p_out || !(x.alpha >= 0.0 && x.alpha <= 1.0)) s = FRR_E_ARG;
+                for (int64_t i = 0; i < x.n && s == FRR_OK; ++i)
+                    if (!isfinite(x.Y[i])) s = FRR_E_ARG;
+                for (int64_t g = 0; g < x.T && s == FRR_OK; ++g)
+                    if (!isfinite(x.tau[g])) s = FRR_E_ARG;
+                P.test = s == FRR_OK && c->st.K <= x.cap;  // else FRR_E_CAPACITY from the selection
+                if (P.test) extra = (size_t)x.T * 16 + 16;
+            }
+            if (s == FRR_OK) s = stream_end_enqueue(c, x.keys_out, x.M64_out, x.cap, extra);
+            if (s == FRR_OK && P.test) {
+                const double* dp = nullptr;
+                const long long* dc = nullptr;
+                const double* dci = nullptr;
+                s = randtest_enqueue(c, x.seed, stream_end_keys_dev(c, x.keys_out), c->st.K, 0, x.Y, x.tau, x.T,
+                                     x.alpha, &dp, &dc, &dci);
+                if (s == FRR_OK) {
+                    P.off = stream_end_pinned_used(c);
+                    char* hp = static_cast<char*>(c->host_pinned) + P.off;
+                    P.p_dev = is_device_ptr(x.p_out);
+                    P.c_dev = x.count_out != nullptr && is_device_ptr(x.count_out);
+                    const size_t tb = (size_t)x.T * 8;
+                    if (cudaMemcpyAsync(P.p_dev ? (void*)x.p_out : (void*)hp, dp, tb,
+                                        P.p_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                        (x.count_out && cudaMemcpyAsync(P.c_dev ? (void*)x.count_out : (void*)(hp + tb), dc, tb,
+                                                        P.c_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                                        c->stream) != cudaSuccess) ||
+                        cudaMemcpyAsync(hp + 2 * tb, dci, 16, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) {
+                        cudaGetLastError();
+                        s = FRR_E_CUDA;
                     }
                 }
-                st_sel[k] = s;
             }
-        };
-        run_workers(nw, finish);
+            st_sel[k] = s;
+        }
+        for (size_t k = 0; k < live.size(); ++k) {
+            if (rc != FRR_OK) { st_sel[k] = rc; continue; }
+            if (!pend[k].piped) { st_sel[k] = one_by_one(k); continue; }
+            if (st_sel[k] != FRR_OK) continue;
+            const int64_t e = live[k];
+            frr_experiment& x = ex[e];
+            frr_ctx* c = ctx[e];
+            int64_t K = 0;
+            frr_status s = stream_end_finish(c, x.keys_out, x.M64_out, x.cap, &K);  // synchronises the stream
+            x.K_out = K;
+            if (s == FRR_OK && pend[k].test) {
+                const char* hp = static_cast<const char*>(c->host_pinned) + pend[k].off;
+                const size_t tb = (size_t)x.T * 8;
+                if (!pend[k].p_dev) memcpy(x.p_out, hp, tb);
+                if (x.count_out && !pend[k].c_dev) memcpy(x.count_out, hp + tb, tb);
+                double ci[2];
+                memcpy(ci, hp + 2 * tb, sizeof(ci));
+                x.ci_lo = ci[0];
+                x.ci_hi = ci[1];
+            }
+            st_sel[k] = s;
+        }
         for (size_t k = 0; k < live.size(); ++k) {
             note(live[k], st_sel[k]);
             draws += (int64_t)ex[live[k]].B;

@@ -161,7 +161,7 @@ static void release(frr_ctx* ctx)
     // the fixed arrays (Zc64 ... dev_counters) live in ctx->arena; all of these come from the
     // library pool and go back to it in stream order
     void* bufs[] = {ctx->arena, ctx->Mhat, ctx->ret_idx[0], ctx->ret_idx[1], ctx->ret_m[0], ctx->ret_m[1], ctx->M64,
-                    ctx->ukeys, ctx->misc, ctx->misc2, ctx->sel};
+                    ctx->ukeys, ctx->misc, ctx->misc2, ctx->rt, ctx->sel};
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, ctx->stream ? ctx->stream : 0);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);

@@ -41,6 +41,11 @@ struct StreamState {
     bool defer_count = false; // the last chunk leaves the retained count on the device (no read-back)
     bool times_pending = false;  // that chunk's event times are read after the final synchronisation
     float cut = INFINITY;     // current cut on the approximate M (keep M_hat <= cut)
+    // stream_end_enqueue -> stream_end_finish: where the outputs go
+    bool end_enqueued = false, end_direct = false, end_host_keys = false, end_host_m = false, end_stage = false;
+    bool end_dev_count = false;
+    int64_t end_rb = 0, end_stage_n = 0;
+    size_t end_pinned = 0;    // pinned bytes used by the summary and the staged outputs
 };
 
 }  // namespace frr
@@ -88,6 +93,7 @@ struct frr_ctx {
     uint64_t* ukeys = nullptr; size_t ukeys_bytes = 0;   // key staging
     void* misc = nullptr; size_t misc_bytes = 0;          // replay / randtest scratch
     void* misc2 = nullptr; size_t misc2_bytes = 0;
+    void* rt = nullptr; size_t rt_bytes = 0;             // randomization-test scratch
     void* sel = nullptr; size_t sel_bytes = 0;           // device state of the running selection
     void* host_pinned = nullptr; size_t host_pinned_bytes = 0;
     cudaEvent_t ev[8] = {};
@@ -164,7 +170,22 @@ frr_status recheck_sum_launch(frr_ctx* ctx, const double* part, int ncb, int64_t
 frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold, uint64_t total);
 frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B);
 frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out);
+// stream_end in two halves: the first enqueues the recheck, ordering, placement and read-back
+// copies (reserving extra_pinned bytes of pinned memory after its own for the caller); the
+// second synchronises the stream, reads the summary and writes the outputs
+frr_status stream_end_enqueue(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, size_t extra_pinned);
+frr_status stream_end_finish(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out);
+// after stream_end_enqueue: the device array the accepted keys are placed in (ascending draw
+// index; q mode: exactly K of them), and the first pinned byte free for the caller
+const uint64_t* stream_end_keys_dev(const frr_ctx* ctx, const uint64_t* keys_out);
+size_t stream_end_pinned_used(const frr_ctx* ctx);
 frr_status stream_chunk_precomputed(frr_ctx* ctx, uint64_t first, uint64_t B, const float* Mhat_dev);
+// the test's kernels on ctx->stream for K checked keys (host or device; obs = index of the
+// observed assignment) and checked Y (n), tau (T) (host or device); the results stay on the
+// device: p (T), count (T), ci (2)
+frr_status randtest_enqueue(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64_t K, int64_t obs, const double* Y,
+                            const double* tau, int64_t T, double alpha, const double** dp, const long long** dcount,
+                            const double** dci);
 frr_status randtest_run(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64_t K, uint64_t obs_key,
                         const double* Y, const double* tau, int64_t T, double alpha, double* p_out,
                         int64_t* count_out, double* ci_lo, double* ci_hi);

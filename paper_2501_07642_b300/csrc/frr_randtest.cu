@@ -111,13 +111,48 @@ __global__ void k_interval(const double* __restrict__ p, const double* __restric
 
 }  // namespace
 
+frr_status randtest_enqueue(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64_t K, int64_t obs, const double* Y,
+                            const double* tau, int64_t T, double alpha, const double** dp_out,
+                            const long long** dcount_out, const double** dci_out)
+{
+    const bool exact = (seed == FRR_EXACT_SEED);
+    const int n = (int)ctx->n;
+    const int words = 4 * ctx->kb;
+    // scratch: keys (K), rows (K x words), Y (n), tau (T), a (K), b (K), count (T), near (T), p (T), ci (2)
+    const size_t bytes = (size_t)K * 8 + (size_t)K * words * 4 + 8 + (size_t)n * 8 + (size_t)T * 8 + (size_t)K * 16 +
+                         (size_t)T * 24 + 16 + 64;
+    FRR_TRY(ensure_device(ctx, &ctx->rt, &ctx->rt_bytes, bytes));
+    char* base = static_cast<char*>(ctx->rt);
+    uint64_t* dkeys = reinterpret_cast<uint64_t*>(base);
+    double* dy = reinterpret_cast<double*>(dkeys + K);
+    double* dtau = dy + n;
+    double* da = dtau + T;
+    double* db = da + K;
+    double* dp = db + K;
+    double* dci = dp + T;
+    long long* dcount = reinterpret_cast<long long*>(dci + 2);
+    long long* dnear = dcount + T;
+    uint32_t* rows = reinterpret_cast<uint32_t*>(dnear + T);
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dkeys, keys, (size_t)K * 8, cudaMemcpyDefault, ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dy, Y, (size_t)n * 8, cudaMemcpyDefault, ctx->stream));
+    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dtau, tau, (size_t)T * 8, cudaMemcpyDefault, ctx->stream));
+    FRR_TRY(bits_launch(ctx, seed, exact, 0, (uint64_t)K, dkeys, rows));
+    k_contrasts<<<ceil_div(K, 4), 128, 0, ctx->stream>>>(rows, words, K, obs, n, (int)ctx->n1, dy, da, db);
+    k_tau_grid<<<(unsigned)T, 256, 0, ctx->stream>>>(da, db, K, obs, dtau, dcount, dp, dnear);
+    k_interval<<<1, 32, 0, ctx->stream>>>(dp, dtau, T, alpha, dci);
+    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    *dp_out = dp;
+    *dcount_out = dcount;
+    *dci_out = dci;
+    return FRR_OK;
+}
+
 frr_status randtest_run(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64_t K, uint64_t obs_key,
                         const double* Y, const double* tau, int64_t T, double alpha, double* p_out,
                         int64_t* count_out, double* ci_lo, double* ci_hi)
 {
     const bool exact = (seed == FRR_EXACT_SEED);
     const int n = (int)ctx->n;
-    const int words = 4 * ctx->kb;
     // host views of the inputs: host memory is read in place; device inputs are copied
     // back together (one synchronisation)
     const bool keys_dev = is_device_ptr(keys), y_dev = is_device_ptr(Y), tau_dev = is_device_ptr(tau);
@@ -154,32 +189,12 @@ frr_status randtest_run(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64
     for (int i = 0; i < n; ++i) if (!isfinite(hy[i])) return FRR_E_ARG;
     for (int64_t g = 0; g < T; ++g) if (!isfinite(ht[g])) return FRR_E_ARG;
 
-    // scratch: keys (K), rows (K x words), Y (n), tau (T), a (K), b (K), count (T), near (T), p (T), ci (2)
-    const size_t bytes = (size_t)K * 8 + (size_t)K * words * 4 + 8 + (size_t)n * 8 + (size_t)T * 8 + (size_t)K * 16 +
-                         (size_t)T * 24 + 16 + 64;
-    FRR_TRY(ensure_device(ctx, &ctx->misc, &ctx->misc_bytes, bytes));
     // pinned staging of the host outputs: p (T), count (T), ci (2)
     FRR_TRY(ensure_host_pinned(ctx, (size_t)T * 16 + 16));
-    char* base = static_cast<char*>(ctx->misc);
-    uint64_t* dkeys = reinterpret_cast<uint64_t*>(base);
-    double* dy = reinterpret_cast<double*>(dkeys + K);
-    double* dtau = dy + n;
-    double* da = dtau + T;
-    double* db = da + K;
-    double* dp = db + K;
-    double* dci = dp + T;
-    long long* dcount = reinterpret_cast<long long*>(dci + 2);
-    long long* dnear = dcount + T;
-    uint32_t* rows = reinterpret_cast<uint32_t*>(dnear + T);
-
-    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dkeys, keys, (size_t)K * 8, cudaMemcpyDefault, ctx->stream));
-    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dy, Y, (size_t)n * 8, cudaMemcpyDefault, ctx->stream));
-    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dtau, tau, (size_t)T * 8, cudaMemcpyDefault, ctx->stream));
-    FRR_TRY(bits_launch(ctx, seed, exact, 0, (uint64_t)K, dkeys, rows));
-    k_contrasts<<<ceil_div(K, 4), 128, 0, ctx->stream>>>(rows, words, K, obs, n, (int)ctx->n1, dy, da, db);
-    k_tau_grid<<<(unsigned)T, 256, 0, ctx->stream>>>(da, db, K, obs, dtau, dcount, dp, dnear);
-    k_interval<<<1, 32, 0, ctx->stream>>>(dp, dtau, T, alpha, dci);
-    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    const double* dp = nullptr;
+    const long long* dcount = nullptr;
+    const double* dci = nullptr;
+    FRR_TRY(randtest_enqueue(ctx, seed, keys, K, obs, Y, tau, T, alpha, &dp, &dcount, &dci));
     // outputs: device ones copied on the stream, host ones through the pinned staging; one
     // synchronisation for all
     double* sp = static_cast<double*>(ctx->host_pinned);

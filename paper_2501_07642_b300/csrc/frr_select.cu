@@ -760,10 +760,10 @@ frr_status stream_chunk_precomputed(frr_ctx* ctx, uint64_t first, uint64_t B, co
     return FRR_OK;
 }
 
-frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out)
+frr_status stream_end_enqueue(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, size_t extra_pinned)
 {
     StreamState& st = ctx->st;
-    if (!st.active) return FRR_E_STATE;
+    if (!st.active || st.end_enqueued) return FRR_E_STATE;
     if (st.seen != st.total) return FRR_E_STATE;
     // the retained count is either known on the host, or (deferred) only on the device,
     // bounded by retained_bound: the kernels below then read it there
@@ -781,7 +781,17 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
     const bool direct = st.q_mode && st.K <= cap && !host_keys && !host_m;
     const int64_t stage_n = std::min<int64_t>(cap, rb);
     const bool stage = !direct && (host_keys || host_m) && stage_n > 0;
-    FRR_TRY(ensure_host_pinned(ctx, 256 + (stage ? (size_t)stage_n * 16 : 0)));
+    const size_t used = 256 + (stage ? (size_t)stage_n * 16 : 0);
+    FRR_TRY(ensure_host_pinned(ctx, used + extra_pinned));
+    st.end_enqueued = true;
+    st.end_direct = direct;
+    st.end_host_keys = host_keys;
+    st.end_host_m = host_m;
+    st.end_stage = stage;
+    st.end_dev_count = dev_count;
+    st.end_rb = rb;
+    st.end_stage_n = stage_n;
+    st.end_pinned = used;
     cudaEventRecord(ctx->ev[3], ctx->stream);
     // scratch: M64 (r), M64 out (r), keys out (r), rank (r)
     const size_t need = (size_t)rb * (3 * sizeof(double) + sizeof(int)) + 64;
@@ -796,8 +806,6 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
     double* hm = reinterpret_cast<double*>(hk + stage_n);
     uint64_t* place_k = direct ? keys_out : kout;
     double* place_m = (direct && M64_out) ? M64_out : mout;
-    SelTail tail{};
-    tail.boundary[0] = tail.boundary[1] = NAN;
     if (rb > 0) {
         const double nanv[2] = {NAN, NAN};
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(sel->boundary, nanv, sizeof(nanv), cudaMemcpyHostToDevice, ctx->stream));
@@ -824,10 +832,38 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
         }
     }
     cudaEventRecord(ctx->ev[4], ctx->stream);
+    return FRR_OK;
+}
+
+const uint64_t* stream_end_keys_dev(const frr_ctx* ctx, const uint64_t* keys_out)
+{
+    if (ctx->st.end_direct) return keys_out;
+    const double* m64 = static_cast<const double*>(ctx->misc);
+    return reinterpret_cast<const uint64_t*>(m64 + 2 * ctx->st.end_rb);
+}
+
+size_t stream_end_pinned_used(const frr_ctx* ctx) { return ctx->st.end_pinned; }
+
+frr_status stream_end_finish(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out)
+{
+    StreamState& st = ctx->st;
+    if (!st.active || !st.end_enqueued) return FRR_E_STATE;
+    st.end_enqueued = false;
+    const int64_t rb = st.end_rb;
+    const bool direct = st.end_direct, host_keys = st.end_host_keys, host_m = st.end_host_m;
+    const int64_t stage_n = st.end_stage_n;
+    double* m64 = static_cast<double*>(ctx->misc);
+    double* mout = m64 + rb;
+    uint64_t* kout = reinterpret_cast<uint64_t*>(mout + rb);
+    char* hp = static_cast<char*>(ctx->host_pinned);
+    uint64_t* hk = reinterpret_cast<uint64_t*>(hp + 256);
+    double* hm = reinterpret_cast<double*>(hk + stage_n);
+    SelTail tail{};
+    tail.boundary[0] = tail.boundary[1] = NAN;
     FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     int64_t r = rb;
     if (rb > 0) {
-        if (dev_count) memcpy(&r, hp, sizeof(long long));
+        if (st.end_dev_count) memcpy(&r, hp, sizeof(long long));
         memcpy(&tail, hp + sizeof(long long), sizeof(SelTail));
         if (*reinterpret_cast<int*>(hp + 128) != 0) {
             FRR_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dev_counters + 12, 0, sizeof(int), ctx->stream));
@@ -886,6 +922,12 @@ frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t
         if (device_copies) FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     }
     return FRR_OK;
+}
+
+frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out)
+{
+    FRR_TRY(stream_end_enqueue(ctx, keys_out, M64_out, cap, 0));
+    return stream_end_finish(ctx, keys_out, M64_out, cap, K_out);
 }
 
 }  // namespace frr
