@@ -13,9 +13,10 @@
 //
 // Work items of (128 candidates, 64 columns), 7 accumulators of 64 columns in TMEM each,
 // taken by persistent CTAs (one per SM at most).
-// Warps 0-3 epilogue, warp 4 TMA (7 digit tiles per K block), warp 5 MMA, warps 6-9
-// expand the candidates' bit rows (computed beforehand) into BF16 0/1 A tiles through a
-// 256-entry byte table in shared memory.
+// Warps 0-7 epilogue (warp w: TMEM lanes 32 (w % 4) .., columns 32 (w / 4) .. of the item,
+// so two warps share each row and the integer epilogue runs on twice the warps), warp 8 TMA
+// (7 digit tiles per K block), warp 9 MMA, warps 10-13 expand the candidates' bit rows
+// (computed beforehand) into BF16 0/1 A tiles through a 256-entry byte table in shared memory.
 #include "frr_internal.cuh"
 
 #include <algorithm>
@@ -31,7 +32,10 @@ constexpr int kStB = 3, kStA = 2;
 constexpr int kPlaneBytes = kN * kKB * 2;          // 8 KiB
 constexpr int kBBytes = kPlanes * kPlaneBytes;     // 56 KiB
 constexpr int kABytes = kM * kKB * 2;              // 16 KiB
-constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;   // two per TMEM lane quarter, one per 32-column half of an item
+constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1, kExpWarp0 = kEpiWarps + 2;
+constexpr int kThreads = (kExpWarp0 + 4) * 32;
+static_assert(kN == 64, "two epilogue warps per lane quarter, 32 columns each");
 
 // Exact conversion of an integer-valued FP32 accumulator with |x| < 2^22: adding
 // 1.5 * 2^23 places the integer in the low mantissa bits.
@@ -114,12 +118,12 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
         for (int s = 0; s < kStB; ++s) { mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); }
         for (int s = 0; s < kStA; ++s) { mbar_init(&a_full[s], 4); mbar_init(&a_empty[s], 1); }
         mbar_init(acc_full, 1);
-        mbar_init(acc_empty, 4);
+        mbar_init(acc_empty, kEpiWarps);
         mbar_init(mma_done, 1);
         *sAbort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) {
+    if (warp == kMmaWarp) {
         tmem_alloc(sTmem, 512);
         tmem_relinquish();
     }
@@ -128,7 +132,7 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
     tc_fence_after();
     const uint32_t tmem_base = *sTmem;
 
-    if (warp == 4) {
+    if (warp == kTmaWarp) {
         if (lane == 0) {
             uint32_t bi = 0;
             bool ok = true;
@@ -152,7 +156,7 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
                 }
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == kMmaWarp) {
         if (lane == 0) {
             bool ok = true;
             uint32_t ai = 0, bi = 0, it = 0;
@@ -184,8 +188,8 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
             const unsigned long long t0 = clock64();
             while (!mbar_try_wait(mma_done, 0) && clock64() - t0 < kWaitCycles) {}
         }
-    } else if (warp >= 6) {
-        const int r = tid - 6 * 32;  // row (candidate) of the A tile
+    } else if (warp >= kExpWarp0) {
+        const int r = tid - kExpWarp0 * 32;  // row (candidate) of the A tile
         uint32_t ai = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x) {
@@ -211,30 +215,30 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
             }
         }
     } else {
-        // epilogue: lane = candidate row 32 * warp + lane
-        const int row = 32 * warp + lane;
+        // epilogue: candidate row 32 (warp % 4) + lane, column half warp / 4 of the item
+        const int row = 32 * (warp & 3) + lane, half = warp >> 2;
         uint32_t it = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
             const int chunk = (int)(item / T);
             const int64_t cand = (item % T) * kM + row;
             // the chunk's column sums and scales (the previous item's readers are done first)
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            for (int t = row; t < kN; t += 128) {
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            for (int t = tid; t < kN; t += 32 * kEpiWarps) {
                 const int col = chunk * kN + t;
                 sQsum[t] = col < d ? Qsum[col] : 0ll;
                 sQexp[t] = col < d ? qexp[col] : 0;
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            asm volatile("bar.sync 1, 256;" ::: "memory");
             if (!(ok = wait_bar(acc_full, it & 1u, sAbort, err, 15))) break;
             tc_fence_after();
             double psum = 0.0;
-            const uint32_t taddr = tmem_base + ((uint32_t)(32 * warp) << 16);
+            const uint32_t taddr = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16);
             // n1 n0 Delta_j 2^q_j = S_T n0 - S_C n1 = S_T n - S_all n1 =: N_j, an exact 128-bit
             // integer; when n1 = n0 the complement (S_T -> S_all - S_T) gives exactly -N_j.
             // N_j 2^-q_j is rounded once to FP64 with integer instructions and squared into
             // the partial sum: one FP64 operation per column (B300's FP64 unit is narrow).
-            for (int c0 = 0; c0 < kN; c0 += 32) {
+            for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 32) {
                 long long S[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) S[j] = 0;
@@ -264,13 +268,13 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty);
-            if (cand < C) part[cand * ncb + chunk] = psum;
+            if (cand < C) part[(cand * ncb + chunk) * 2 + half] = psum;
         }
     }
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 5) {
+    if (warp == kMmaWarp) {
         tc_fence_after();
         tmem_dealloc(tmem_base, 512);
     }
@@ -287,7 +291,7 @@ frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint
     const int W = 4 * ctx->kb;
     const int ncb = ceil_div(ctx->d, kN);
     const size_t rows_bytes = (size_t)count * W * sizeof(uint32_t);
-    const size_t part_bytes = (size_t)count * ncb * sizeof(double);
+    const size_t part_bytes = (size_t)count * ncb * 2 * sizeof(double);
     FRR_TRY(ensure_device(ctx, &ctx->misc2, &ctx->misc2_bytes, rows_bytes + part_bytes + 256));
     uint32_t* rows = static_cast<uint32_t*>(ctx->misc2);
     double* part = reinterpret_cast<double*>(static_cast<char*>(ctx->misc2) + ((rows_bytes + 255) & ~size_t(255)));
@@ -306,7 +310,7 @@ frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint
                                                        part, ncb, ctx->dev_counters + 12);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     // the partial sums hold (N_j 2^-q_j)^2 = (n1 n0 Delta_j)^2, and M = (n1 n0 / n) sum Delta_j^2
-    return recheck_sum_launch(ctx, part, ncb, count, M64, 1.0, (double)ctx->n * (double)ctx->n1 * (double)ctx->n0,
+    return recheck_sum_launch(ctx, part, 2 * ncb, count, M64, 1.0, (double)ctx->n * (double)ctx->n1 * (double)ctx->n0,
                               count_dev);
 }
 
