@@ -129,3 +129,81 @@ def test_two_shards_on_one_gpu_merge_to_the_single_pool():
             parts.append(frr.frr_select(ctx, seed, 500 + off, cnt, q=shard_q(K, cnt)))
     keys, m = merge_accepted(parts, K)
     assert np.array_equal(keys, want[0]) and np.array_equal(m, want[1])
+
+
+def test_batch_paths_agree_with_single_calls():
+    """One batch mixing the driver's paths -- q mode with host buffers (chains enqueued
+    without read-backs), q mode with device outputs (keys placed directly), q mode with
+    device test inputs and threshold mode (both one by one) -- against frr_select +
+    frr_randtest on single contexts."""
+    import ctypes
+    import torch
+
+    dev = torch.device("cuda")
+    specs = [("host", 0.01), ("dev_out", 0.01), ("dev_in", 0.02), ("thr", None)]
+    exps = (frr.frr_experiment * len(specs))()
+    keep, want = [], []
+    for k, (kind, q) in enumerate(specs):
+        n, d = (120 + 40 * k, 30 + 11 * k)
+        X = ar1_covariates(n, d, 900 + k, 0.3)
+        Y = np.ascontiguousarray(X[:, 0] + np.random.default_rng(k).standard_normal(n))
+        tau = np.linspace(-1.0, 1.0, 41)
+        seed, first, B = 50 + k, 1000 * k, 12_000
+        with frr.Context(X, n // 2, precision="split_bf16", whiten="chol") as ctx:
+            if q is None:
+                ref_keys, ref_m = frr.frr_select(ctx, seed, first, B, q=0.004)
+                thr = float(ref_m.max())
+                sk, sm = frr.frr_select(ctx, seed, first, B, threshold=thr)
+            else:
+                thr = math.nan
+                sk, sm = frr.frr_select(ctx, seed, first, B, q=q)
+            rt = frr.frr_randtest(ctx, seed, sk, int(sk[0]), Y, tau)
+            p, cnt, lo, hi = rt["p"], rt["count"], rt["ci_lo"], rt["ci_hi"]
+        want.append((sk, sm, p, cnt, lo, hi))
+        a = exps[k]
+        a.X = X.ctypes.data
+        a.n, a.d, a.n1 = n, d, n // 2
+        a.whiten = frr.WHITEN["chol"]
+        a.ridge = 0.1
+        a.seed, a.first_draw, a.B = seed, first, B
+        a.q = math.nan if q is None else q
+        a.threshold = thr
+        cap = 4096
+        a.cap = cap
+        a.T = tau.size
+        a.alpha = 0.05
+        if kind == "dev_out":
+            bufs = dict(keys=torch.zeros(cap, dtype=torch.int64, device=dev), m=torch.zeros(cap, dtype=torch.float64, device=dev),
+                        p=torch.zeros(tau.size, dtype=torch.float64, device=dev),
+                        c=torch.zeros(tau.size, dtype=torch.int64, device=dev))
+            a.keys_out, a.M64_out = bufs["keys"].data_ptr(), bufs["m"].data_ptr()
+            a.p_out, a.count_out = bufs["p"].data_ptr(), bufs["c"].data_ptr()
+            a.Y, a.tau = Y.ctypes.data, tau.ctypes.data
+        else:
+            bufs = dict(keys=np.zeros(cap, dtype=np.uint64), m=np.zeros(cap), p=np.zeros(tau.size),
+                        c=np.zeros(tau.size, dtype=np.int64))
+            a.keys_out, a.M64_out = bufs["keys"].ctypes.data, bufs["m"].ctypes.data
+            a.p_out, a.count_out = bufs["p"].ctypes.data, bufs["c"].ctypes.data
+            if kind == "dev_in":
+                bufs["Yd"] = torch.from_numpy(Y).to(dev)
+                bufs["td"] = torch.from_numpy(tau).to(dev)
+                a.Y, a.tau = bufs["Yd"].data_ptr(), bufs["td"].data_ptr()
+            else:
+                a.Y, a.tau = Y.ctypes.data, tau.ctypes.data
+        keep += [X, Y, tau, bufs]
+    st = frr.frr_batch_stats()
+    opts = frr.frr_default_opts()
+    rc = frr.lib().frr_batch_run(ctypes.addressof(exps), len(specs), ctypes.byref(opts), ctypes.byref(st))
+    torch.cuda.synchronize()
+    assert rc == 0, [exps[k].status for k in range(len(specs))]
+    for k, (kind, q) in enumerate(specs):
+        sk, sm, p, cnt, lo, hi = want[k]
+        a, bufs = exps[k], keep[4 * k + 3]
+        K = a.K_out
+        assert a.status == 0 and K == len(sk), kind
+        get = (lambda t: t.cpu().numpy()) if kind == "dev_out" else (lambda t: t)
+        assert np.array_equal(get(bufs["keys"])[:K].astype(np.uint64), sk), kind
+        assert np.array_equal(get(bufs["m"])[:K], sm), kind
+        assert np.array_equal(get(bufs["p"]), p) and np.array_equal(get(bufs["c"]), cnt), kind
+        same = lambda u, v: u == v or (math.isnan(u) and math.isnan(v))
+        assert same(a.ci_lo, lo) and same(a.ci_hi, hi), kind
