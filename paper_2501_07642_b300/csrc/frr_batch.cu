@@ -94,6 +94,18 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             ws[w] = stream;
         }
     std::vector<frr_status> st_init((size_t)E, FRR_OK);
+    // The covariates go to the device through one pinned staging block (the copy into it is
+    // also the check for non-finite values), so that their upload is DMA from pinned memory
+    // rather than the driver staging pageable memory on the calling thread.
+    std::vector<size_t> xoff((size_t)E + 1, 0);
+    for (int64_t e = 0; e < E; ++e) {
+        const bool sized = ex[e].X && ex[e].n >= 2 && ex[e].n <= kMaxN && ex[e].d >= 1 && ex[e].d <= (1 << 20);
+        xoff[(size_t)e + 1] = xoff[(size_t)e] + (sized ? (size_t)ex[e].n * (size_t)ex[e].d : 0);
+    }
+    size_t stage_cap = 0;
+    double* stage = xoff[(size_t)E] > 0
+                        ? static_cast<double*>(pinned_get(xoff[(size_t)E] * sizeof(double), &stage_cap))
+                        : nullptr;
     // argument checks and context creation on the worker threads
     auto create = [&](int w) {
         for (int64_t e = w; e < E; e += nw) {
@@ -109,7 +121,8 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             o.whiten = ex[e].whiten;
             o.ridge = ex[e].ridge;
             o.cuda_stream = ws[(size_t)(e % ns)];
-            frr_status s = check_init_args(ex[e].X, ex[e].n, ex[e].d, ex[e].n1, o);
+            frr_status s = check_init_args(ex[e].X, ex[e].n, ex[e].d, ex[e].n1, o, stage == nullptr);
+            if (s == FRR_OK && stage) s = stage_finite(ex[e].X, ex[e].n * ex[e].d, stage + xoff[(size_t)e]);
             if (s == FRR_OK && ex[e].seed == FRR_EXACT_SEED) {
                 if (ex[e].n > kExactMaxN) s = FRR_E_UNSUPPORTED;
                 else if (ex[e].first_draw + ex[e].B > binom_host((int)ex[e].n, (int)ex[e].n1)) s = FRR_E_RANGE;
@@ -130,7 +143,7 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
         for (int64_t e = 0; e < E; ++e)
             if (ctx[e]) {
                 pc.push_back(ctx[e]);
-                px.push_back(ex[e].X);
+                px.push_back(stage ? stage + xoff[(size_t)e] : ex[e].X);
                 pe.push_back(e);
             }
         if (!pc.empty()) {
@@ -142,6 +155,10 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
                 prep_run_batch(pc.data(), px.data(), (int)pc.size(), stream, paux, pst.data());
                 cudaStreamDestroy(paux);
             }
+            // (the uploads from the staging block have finished even if the preparation failed)
+            if (cudaStreamSynchronize(stream) != cudaSuccess) cudaGetLastError();
+            pinned_put(stage, stage_cap);
+            stage = nullptr;
             for (size_t k = 0; k < pc.size(); ++k) {
                 st_init[(size_t)pe[k]] = pst[k];
                 if (pst[k] != FRR_OK) {
@@ -151,6 +168,7 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             }
         }
     }
+    pinned_put(stage, stage_cap);  // (when nothing was prepared)
     for (int64_t e = 0; e < E; ++e) note(e, st_init[e]);
     const auto t1 = std::chrono::steady_clock::now();
 

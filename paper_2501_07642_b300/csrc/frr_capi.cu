@@ -45,15 +45,18 @@ frr_status ensure_device(frr_ctx* ctx, void** buf, size_t* cap_bytes, size_t byt
     return FRR_OK;
 }
 
-// Pinned host blocks are kept by the library between contexts (power-of-two sizes from
-// 4 KiB): cudaMallocHost is slow and cudaFreeHost synchronises the device, which a batch of
+// Pinned host blocks are kept by the library between contexts and calls (size classes
+// below): cudaMallocHost is slow and cudaFreeHost synchronises the device, which a batch of
 // many short-lived contexts would otherwise pay once per context.
 namespace {
 std::mutex g_pinned_mu;
 std::unordered_map<size_t, std::vector<void*>> g_pinned_free;
 
+// size classes: powers of two from 4 KiB to 16 MiB, then multiples of 16 MiB
 size_t pinned_class(size_t bytes)
 {
+    const size_t big = size_t(16) << 20;
+    if (bytes > big) return (bytes + big - 1) / big * big;
     size_t c = 4096;
     while (c < bytes) c <<= 1;
     return c;
@@ -65,6 +68,27 @@ void pinned_put(void* p, size_t cap)
     if (!p) return;
     std::lock_guard<std::mutex> lock(g_pinned_mu);
     g_pinned_free[cap].push_back(p);
+}
+
+void* pinned_get(size_t bytes, size_t* cap_out)
+{
+    const size_t cap = pinned_class(bytes);
+    *cap_out = cap;
+    {
+        std::lock_guard<std::mutex> lock(g_pinned_mu);
+        auto it = g_pinned_free.find(cap);
+        if (it != g_pinned_free.end() && !it->second.empty()) {
+            void* p = it->second.back();
+            it->second.pop_back();
+            return p;
+        }
+    }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
 }
 
 frr_status ensure_host_pinned(frr_ctx* ctx, size_t bytes)
@@ -175,7 +199,22 @@ static void release(frr_ctx* ctx)
 }
 
 // Argument checks of frr_init (also applied to every experiment of frr_batch_run).
-frr_status check_init_args(const double* X, int64_t n, int64_t d, int64_t n1, const frr_opts& o)
+// Copies n*d values from X to dst (pinned staging) and checks that they are finite, in one pass.
+frr_status stage_finite(const double* X, int64_t count, double* dst)
+{
+    const uint64_t* bits = reinterpret_cast<const uint64_t*>(X);
+    uint64_t* out = reinterpret_cast<uint64_t*>(dst);
+    const uint64_t em = 0x7ff0000000000000ull;
+    uint64_t bad = 0;
+    for (int64_t k = 0; k < count; ++k) {
+        const uint64_t b = bits[k];
+        out[k] = b;
+        bad |= (uint64_t)((b & em) == em);
+    }
+    return bad ? FRR_E_ARG : FRR_OK;
+}
+
+frr_status check_init_args(const double* X, int64_t n, int64_t d, int64_t n1, const frr_opts& o, bool scan_x)
 {
     if (!X) return FRR_E_ARG;
     if (n < 2 || d < 1 || n1 < 1 || n1 > n - 1) return FRR_E_ARG;
@@ -188,7 +227,8 @@ frr_status check_init_args(const double* X, int64_t n, int64_t d, int64_t n1, co
     const uint64_t* bits = reinterpret_cast<const uint64_t*>(X);
     const uint64_t em = 0x7ff0000000000000ull;
     uint64_t bad = 0;
-    for (int64_t k = 0; k < n * d; ++k) bad |= (uint64_t)((bits[k] & em) == em);
+    if (scan_x)
+        for (int64_t k = 0; k < n * d; ++k) bad |= (uint64_t)((bits[k] & em) == em);
     if (bad) return FRR_E_ARG;
     if (o.whiten == FRR_CHOL && d >= n - 1) return FRR_E_DEGENERATE;
     return FRR_OK;
@@ -310,7 +350,7 @@ frr_status frr_init(frr_ctx** out, const double* X, int64_t n, int64_t d, int64_
     frr_opts o;
     frr_default_opts(&o);
     if (opts) o = *opts;
-    FRR_TRY(check_init_args(X, n, d, n1, o));
+    FRR_TRY(check_init_args(X, n, d, n1, o, true));
     const auto t0 = std::chrono::steady_clock::now();
     frr_ctx* ctx = nullptr;
     FRR_TRY(ctx_create(&ctx, n, d, n1, o, true));

@@ -143,7 +143,12 @@ frr_status copy_in(frr_ctx* ctx, void* dst_dev, const void* src_any, size_t byte
 frr_status copy_out(frr_ctx* ctx, void* dst_any, const void* src_dev, size_t bytes);
 
 // kernel families (defined in their own translation units)
-frr_status check_init_args(const double* X, int64_t n, int64_t d, int64_t n1, const frr_opts& o);
+// scan_x: also reject non-finite entries of X (else the caller checks them, e.g. stage_finite)
+frr_status check_init_args(const double* X, int64_t n, int64_t d, int64_t n1, const frr_opts& o, bool scan_x);
+frr_status stage_finite(const double* X, int64_t count, double* dst);
+// pinned host blocks pooled by the library (size classes: powers of two up to 16 MiB, then multiples of 16 MiB)
+void* pinned_get(size_t bytes, size_t* cap_out);
+void pinned_put(void* p, size_t cap);
 frr_status ctx_create(frr_ctx** out, int64_t n, int64_t d, int64_t n1, const frr_opts& o, bool with_aux);
 void ctx_release(frr_ctx* ctx);
 frr_status prep_run(frr_ctx* ctx, const double* X_host);
