@@ -378,6 +378,7 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             P.piped = true;
             frr_status s = stream_begin(c, x.seed, x.q, x.threshold, x.B);
             c->st.defer_count = true;
+            c->st.timing = false;  // per-experiment phase times are not reported by the batch
             if (s == FRR_OK) s = stream_chunk_precomputed(c, x.first_draw, x.B, mhat + off[k]);
             size_t extra = 0;
             if (s == FRR_OK && x.Y != nullptr) {
@@ -394,8 +395,8 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
                 const double* dp = nullptr;
                 const long long* dc = nullptr;
                 const double* dci = nullptr;
-                s = randtest_enqueue(c, x.seed, stream_end_keys_dev(c, x.keys_out), c->st.K, 0, x.Y, x.tau, x.T,
-                                     x.alpha, &dp, &dc, &dci);
+                s = randtest_enqueue(c, x.seed, stream_end_keys_dev(c, x.keys_out), true, c->st.K, 0, x.Y, x.tau,
+                                     x.T, x.alpha, &dp, &dc, &dci);
                 if (s == FRR_OK) {
                     P.off = stream_end_pinned_used(c);
                     char* hp = static_cast<char*>(c->host_pinned) + P.off;

@@ -40,6 +40,7 @@ struct StreamState {
     int64_t retained_bound = 0;  // upper bound of the retained count when it is only on the device
     bool defer_count = false; // the last chunk leaves the retained count on the device (no read-back)
     bool times_pending = false;  // that chunk's event times are read after the final synchronisation
+    bool timing = true;       // record the per-phase events of frr_stats (off in the batched driver)
     float cut = INFINITY;     // current cut on the approximate M (keep M_hat <= cut)
     // stream_end_enqueue -> stream_end_finish: where the outputs go
     bool end_enqueued = false, end_direct = false, end_host_keys = false, end_host_m = false, end_stage = false;
@@ -185,12 +186,12 @@ frr_status stream_end_finish(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, 
 const uint64_t* stream_end_keys_dev(const frr_ctx* ctx, const uint64_t* keys_out);
 size_t stream_end_pinned_used(const frr_ctx* ctx);
 frr_status stream_chunk_precomputed(frr_ctx* ctx, uint64_t first, uint64_t B, const float* Mhat_dev);
-// the test's kernels on ctx->stream for K checked keys (host or device; obs = index of the
+// the test's kernels on ctx->stream for K checked keys (host, or device when keys_on_device; obs = index of the
 // observed assignment) and checked Y (n), tau (T) (host or device); the results stay on the
 // device: p (T), count (T), ci (2)
-frr_status randtest_enqueue(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64_t K, int64_t obs, const double* Y,
-                            const double* tau, int64_t T, double alpha, const double** dp, const long long** dcount,
-                            const double** dci);
+frr_status randtest_enqueue(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, bool keys_on_device, int64_t K,
+                            int64_t obs, const double* Y, const double* tau, int64_t T, double alpha,
+                            const double** dp, const long long** dcount, const double** dci);
 frr_status randtest_run(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64_t K, uint64_t obs_key,
                         const double* Y, const double* tau, int64_t T, double alpha, double* p_out,
                         int64_t* count_out, double* ci_lo, double* ci_hi);

@@ -111,9 +111,9 @@ __global__ void k_interval(const double* __restrict__ p, const double* __restric
 
 }  // namespace
 
-frr_status randtest_enqueue(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64_t K, int64_t obs, const double* Y,
-                            const double* tau, int64_t T, double alpha, const double** dp_out,
-                            const long long** dcount_out, const double** dci_out)
+frr_status randtest_enqueue(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, bool keys_on_device, int64_t K,
+                            int64_t obs, const double* Y, const double* tau, int64_t T, double alpha,
+                            const double** dp_out, const long long** dcount_out, const double** dci_out)
 {
     const bool exact = (seed == FRR_EXACT_SEED);
     const int n = (int)ctx->n;
@@ -133,10 +133,11 @@ frr_status randtest_enqueue(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, i
     long long* dcount = reinterpret_cast<long long*>(dci + 2);
     long long* dnear = dcount + T;
     uint32_t* rows = reinterpret_cast<uint32_t*>(dnear + T);
-    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dkeys, keys, (size_t)K * 8, cudaMemcpyDefault, ctx->stream));
+    if (!keys_on_device)
+        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dkeys, keys, (size_t)K * 8, cudaMemcpyHostToDevice, ctx->stream));
     FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dy, Y, (size_t)n * 8, cudaMemcpyDefault, ctx->stream));
     FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dtau, tau, (size_t)T * 8, cudaMemcpyDefault, ctx->stream));
-    FRR_TRY(bits_launch(ctx, seed, exact, 0, (uint64_t)K, dkeys, rows));
+    FRR_TRY(bits_launch(ctx, seed, exact, 0, (uint64_t)K, keys_on_device ? keys : dkeys, rows));
     k_contrasts<<<ceil_div(K, 4), 128, 0, ctx->stream>>>(rows, words, K, obs, n, (int)ctx->n1, dy, da, db);
     k_tau_grid<<<(unsigned)T, 256, 0, ctx->stream>>>(da, db, K, obs, dtau, dcount, dp, dnear);
     k_interval<<<1, 32, 0, ctx->stream>>>(dp, dtau, T, alpha, dci);
@@ -194,7 +195,7 @@ frr_status randtest_run(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, int64
     const double* dp = nullptr;
     const long long* dcount = nullptr;
     const double* dci = nullptr;
-    FRR_TRY(randtest_enqueue(ctx, seed, keys, K, obs, Y, tau, T, alpha, &dp, &dcount, &dci));
+    FRR_TRY(randtest_enqueue(ctx, seed, keys, keys_dev, K, obs, Y, tau, T, alpha, &dp, &dcount, &dci));
     // outputs: device ones copied on the stream, host ones through the pinned staging; one
     // synchronisation for all
     double* sp = static_cast<double*>(ctx->host_pinned);

@@ -349,6 +349,24 @@ k_sel_compact(const float* __restrict__ chunk, int64_t nc, uint64_t first, const
     }
 }
 
+// State of a new stream: the level-0 histogram cleared (each scan clears the other level for
+// its next use), the cut, the counters and the end-of-stream fields (boundary M64 = NaN until
+// the summary finds them). One launch instead of a memset and host-to-device copies.
+__global__ void __launch_bounds__(SNT) k_sel_init(SelState* __restrict__ st, float cut)
+{
+    for (int i = threadIdx.x; i < kBins; i += SNT) st->hist[0][i] = 0;
+    if (threadIdx.x == 0) {
+        st->prefix1 = st->prefix2 = 0;
+        st->krem = 0;
+        st->cut = cut;
+        st->kept = 0;
+        st->nsel = 0;
+        st->boundary[0] = st->boundary[1] = __longlong_as_double(0x7FF8000000000000ll);
+        st->max_rel = st->max_over_band = st->thr = 0.0;
+        st->violations = 0;
+    }
+}
+
 __global__ void k_sel_begin(SelState* __restrict__ st, long long K)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -630,9 +648,8 @@ frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold,
     ctx->ret_cur = 0;
     const double ms_init = ctx->stats.ms_init;
     FRR_TRY(ensure_device(ctx, &ctx->sel, &ctx->sel_bytes, sizeof(SelState)));
-    FRR_CUDA_TRY(ctx, cudaMemsetAsync(ctx->sel, 0, sizeof(SelState), ctx->stream));
-    FRR_CUDA_TRY(ctx, cudaMemcpyAsync(&static_cast<SelState*>(ctx->sel)->cut, &st.cut, sizeof(float),
-                                      cudaMemcpyHostToDevice, ctx->stream));
+    k_sel_init<<<1, SNT, 0, ctx->stream>>>(static_cast<SelState*>(ctx->sel), st.cut);
+    FRR_CUDA_TRY(ctx, cudaGetLastError());
     memset(&ctx->stats, 0, sizeof(ctx->stats));
     ctx->stats.ms_init = ms_init;
     ctx->stats.boundary_gap_rel = NAN;
@@ -671,7 +688,7 @@ frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const f
                                                              ctx->ret_idx[in], st.retained, sel, ctx->ret_m[out],
                                                              ctx->ret_idx[out], cap);
         FRR_CUDA_TRY(ctx, cudaGetLastError());
-        cudaEventRecord(ctx->ev[2], ctx->stream);
+        if (st.timing) cudaEventRecord(ctx->ev[2], ctx->stream);
         st.retained = -1;
         st.retained_bound = N;
         ctx->ret_cur = out;
@@ -686,7 +703,7 @@ frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const f
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk, &sel->kept, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk + 1, ctx->dev_counters + 12, sizeof(int), cudaMemcpyDeviceToHost,
                                           ctx->stream));
-        cudaEventRecord(ctx->ev[2], ctx->stream);
+        if (st.timing) cudaEventRecord(ctx->ev[2], ctx->stream);
         FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         const long long kept = hk[0];
         if (*reinterpret_cast<int*>(hk + 1) != 0) {
@@ -717,9 +734,9 @@ frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B)
     for (uint64_t off = 0; off < B; off += kChunkMax) {
         const uint64_t bc = std::min<uint64_t>(kChunkMax, B - off);
         FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->Mhat), &ctx->Mhat_bytes, bc * sizeof(float)));
-        cudaEventRecord(ctx->ev[0], ctx->stream);
+        if (st.timing) cudaEventRecord(ctx->ev[0], ctx->stream);
         FRR_TRY(balance_launch(ctx, st.seed, st.exact, first + off, bc, ctx->Mhat));
-        cudaEventRecord(ctx->ev[1], ctx->stream);
+        if (st.timing) cudaEventRecord(ctx->ev[1], ctx->stream);
         FRR_TRY(stream_select_step(ctx, first + off, bc, ctx->Mhat, st.seen + off + bc == st.total));
         if (st.retained < 0) {
             st.times_pending = true;  // nothing was synchronised: read the events in stream_end
@@ -744,15 +761,15 @@ frr_status stream_chunk_precomputed(frr_ctx* ctx, uint64_t first, uint64_t B, co
     if (st.seen + B > st.total) return FRR_E_RANGE;
     for (uint64_t off = 0; off < B; off += kChunkMax) {
         const uint64_t bc = std::min<uint64_t>(kChunkMax, B - off);
-        cudaEventRecord(ctx->ev[0], ctx->stream);  // no balance here: an empty interval
-        cudaEventRecord(ctx->ev[1], ctx->stream);
+        if (st.timing) cudaEventRecord(ctx->ev[0], ctx->stream);  // no balance here: an empty interval
+        if (st.timing) cudaEventRecord(ctx->ev[1], ctx->stream);
         FRR_TRY(stream_select_step(ctx, first + off, bc, Mhat + off, st.seen + off + bc == st.total));
         if (st.retained < 0) {
-            st.times_pending = true;  // nothing was synchronised: read the events in stream_end
+            st.times_pending = st.timing;  // nothing was synchronised: read the events in stream_end
             continue;
         }
         float t2 = 0.f;
-        cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
+        if (st.timing) cudaEventElapsedTime(&t2, ctx->ev[1], ctx->ev[2]);
         ctx->stats.ms_select += t2;
     }
     st.seen += B;
@@ -792,7 +809,7 @@ frr_status stream_end_enqueue(frr_ctx* ctx, uint64_t* keys_out, double* M64_out,
     st.end_rb = rb;
     st.end_stage_n = stage_n;
     st.end_pinned = used;
-    cudaEventRecord(ctx->ev[3], ctx->stream);
+    if (st.timing) cudaEventRecord(ctx->ev[3], ctx->stream);
     // scratch: M64 (r), M64 out (r), keys out (r), rank (r)
     const size_t need = (size_t)rb * (3 * sizeof(double) + sizeof(int)) + 64;
     FRR_TRY(ensure_device(ctx, &ctx->misc, &ctx->misc_bytes, need));
@@ -807,8 +824,7 @@ frr_status stream_end_enqueue(frr_ctx* ctx, uint64_t* keys_out, double* M64_out,
     uint64_t* place_k = direct ? keys_out : kout;
     double* place_m = (direct && M64_out) ? M64_out : mout;
     if (rb > 0) {
-        const double nanv[2] = {NAN, NAN};
-        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(sel->boundary, nanv, sizeof(nanv), cudaMemcpyHostToDevice, ctx->stream));
+        // (sel->boundary was set to NaN by k_sel_init)
         FRR_TRY(recheck_launch(ctx, st.seed, st.exact, ctx->ret_idx[cur], rb, m64, r_dev));
         // threshold mode: M64 <= a compares as bit patterns (M64 >= 0); a < 0 accepts nothing
         long long thr_bits = -1;
@@ -831,7 +847,7 @@ frr_status stream_end_enqueue(frr_ctx* ctx, uint64_t* keys_out, double* M64_out,
                 FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hm, mout, (size_t)stage_n * 8, cudaMemcpyDeviceToHost, ctx->stream));
         }
     }
-    cudaEventRecord(ctx->ev[4], ctx->stream);
+    if (st.timing) cudaEventRecord(ctx->ev[4], ctx->stream);
     return FRR_OK;
 }
 
@@ -881,7 +897,7 @@ frr_status stream_end_finish(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, 
         st.times_pending = false;
     }
     float t = 0.f;
-    cudaEventElapsedTime(&t, ctx->ev[3], ctx->ev[4]);
+    if (st.timing) cudaEventElapsedTime(&t, ctx->ev[3], ctx->ev[4]);
     ctx->stats.ms_recheck += t;
     const long long nsel = tail.nsel;
     *K_out = nsel;
