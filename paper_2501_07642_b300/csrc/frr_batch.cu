@@ -341,12 +341,12 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
         // reads the placed keys on the device), and the results are collected after every
         // chain is enqueued. The others (threshold mode, device test inputs) run one by one.
         std::vector<frr_status> st_sel(live.size(), FRR_OK);
-        auto one_by_one = [&](size_t k) -> frr_status {
+        auto one_by_one = [&](size_t k, bool defer) -> frr_status {
             const int64_t e = live[k];
             frr_experiment& x = ex[e];
             frr_status s = stream_begin(ctx[e], x.seed, x.q, x.threshold, x.B);
             // one chunk: the recheck may read the candidate count on the device
-            ctx[e]->st.defer_count = true;
+            ctx[e]->st.defer_count = defer;
             if (s == FRR_OK) s = stream_chunk_precomputed(ctx[e], x.first_draw, x.B, mhat + off[k]);
             int64_t K = 0;
             if (s == FRR_OK) s = stream_end(ctx[e], x.keys_out, x.M64_out, x.cap, &K);
@@ -418,7 +418,11 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
         }
         for (size_t k = 0; k < live.size(); ++k) {
             if (rc != FRR_OK) { st_sel[k] = rc; continue; }
-            if (!pend[k].piped) { st_sel[k] = one_by_one(k); continue; }
+            if (!pend[k].piped) {
+                st_sel[k] = one_by_one(k, true);
+                if (st_sel[k] == FRR_E_CAPACITY && ctx[live[k]]->st.overflowed) st_sel[k] = one_by_one(k, false);
+                continue;
+            }
             if (st_sel[k] != FRR_OK) continue;
             const int64_t e = live[k];
             frr_experiment& x = ex[e];
@@ -426,6 +430,11 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             int64_t K = 0;
             frr_status s = stream_end_finish(c, x.keys_out, x.M64_out, x.cap, &K);  // synchronises the stream
             x.K_out = K;
+            if (s == FRR_E_CAPACITY && c->st.overflowed) {
+                // the retained set outgrew its deferred buffer: this experiment again, undeferred
+                st_sel[k] = one_by_one(k, false);
+                continue;
+            }
             if (s == FRR_OK && pend[k].test) {
                 const char* hp = static_cast<const char*>(c->host_pinned) + pend[k].off;
                 const size_t tb = (size_t)x.T * 8;

@@ -439,11 +439,16 @@ frr_status frr_select(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_t
     if (ctx->failed) return FRR_E_CUDA;
     FRR_TRY(check_mode(q, threshold));
     FRR_TRY(check_range(ctx, seed, first_draw, B));
-    FRR_TRY(stream_begin(ctx, seed, q, threshold, B));
-    ctx->st.defer_count = true;  // one call: the recheck may read the candidate count on the device
-    frr_status s = stream_chunk(ctx, first_draw, B);
-    if (s != FRR_OK) { ctx->st.active = false; return s; }
-    return stream_end(ctx, keys_out, M64_out, cap, K_out);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        FRR_TRY(stream_begin(ctx, seed, q, threshold, B));
+        // one call: the recheck may read the candidate count on the device (first attempt)
+        ctx->st.defer_count = attempt == 0;
+        frr_status s = stream_chunk(ctx, first_draw, B);
+        if (s != FRR_OK) { ctx->st.active = false; return s; }
+        s = stream_end(ctx, keys_out, M64_out, cap, K_out);
+        if (!(s == FRR_E_CAPACITY && ctx->st.overflowed)) return s;
+    }
+    return FRR_E_CAPACITY;
 }
 
 frr_status frr_assignments(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_t count, uint8_t* w_out)

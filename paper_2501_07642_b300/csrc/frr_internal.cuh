@@ -41,6 +41,7 @@ struct StreamState {
     bool defer_count = false; // the last chunk leaves the retained count on the device (no read-back)
     bool times_pending = false;  // that chunk's event times are read after the final synchronisation
     bool timing = true;       // record the per-phase events of frr_stats (off in the batched driver)
+    bool overflowed = false;  // stream_end found the deferred retained set larger than its buffer
     float cut = INFINITY;     // current cut on the approximate M (keep M_hat <= cut)
     // stream_end_enqueue -> stream_end_finish: where the outputs go
     bool end_enqueued = false, end_direct = false, end_host_keys = false, end_host_m = false, end_stage = false;

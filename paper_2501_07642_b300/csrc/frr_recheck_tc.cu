@@ -111,7 +111,7 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
         for (int i = 0; i < 8; ++i) h[i] = ((tid >> i) & 1) ? 0x3F80u : 0u;
         sLut8[tid] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
     }
-    const int64_t C = C_dev ? (int64_t)*C_dev : C_host;
+    const int64_t C = C_dev ? std::min<int64_t>((int64_t)*C_dev, C_host) : C_host;  // within the buffers
     const int64_t T = (C + kM - 1) / kM;
     const int64_t items = T * ncb;
     if (tid == 0) {

@@ -33,7 +33,9 @@ __global__ void k_bits(uint64_t seed, int exact, const uint64_t* __restrict__ bi
                        uint64_t count, const long long* __restrict__ count_dev, const uint64_t* __restrict__ draws,
                        uint32_t* __restrict__ rows)
 {
-    const uint64_t cnt = count_dev ? (uint64_t)*count_dev : count;
+    // a device count can exceed the bound when the retained set overflowed its buffer (the
+    // host then redoes the selection); only the entries within the bound exist
+    const uint64_t cnt = count_dev ? std::min<uint64_t>((uint64_t)*count_dev, count) : count;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < cnt; w += nw) {
@@ -147,7 +149,7 @@ __global__ void k_recheck_sum(const double* __restrict__ part, int ncb, int64_t 
                               const long long* __restrict__ count_dev, double scale, double denom,
                               double* __restrict__ M64)
 {
-    const int64_t cnt = count_dev ? *count_dev : count;
+    const int64_t cnt = count_dev ? (*count_dev < count ? *count_dev : count) : count;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cnt; c += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int b = 0; b < ncb; ++b) s = __dadd_rn(s, part[c * ncb + b]);
@@ -381,7 +383,7 @@ __global__ void k_sel_begin(SelState* __restrict__ st, long long K)
 __global__ void k_rank(const double* __restrict__ m, const uint64_t* __restrict__ idx, int64_t r_host,
                        const long long* __restrict__ r_dev, int* __restrict__ rank)
 {
-    const int64_t r = r_dev ? *r_dev : r_host;
+    const int64_t r = r_dev ? (*r_dev < r_host ? *r_dev : r_host) : r_host;  // within the buffers
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
     const long long* mb = reinterpret_cast<const long long*>(m);
@@ -411,7 +413,7 @@ __global__ void k_place_sel(const double* __restrict__ m, const uint64_t* __rest
                             int64_t r_host, const long long* __restrict__ r_dev, long long K, int q_mode,
                             long long thr_bits, uint64_t* __restrict__ keys_out, double* __restrict__ m_out)
 {
-    const int64_t r = r_dev ? *r_dev : r_host;
+    const int64_t r = r_dev ? (*r_dev < r_host ? *r_dev : r_host) : r_host;  // within the buffers
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
     const long long* mb = reinterpret_cast<const long long*>(m);
@@ -436,7 +438,7 @@ k_sel_summary(const double* __restrict__ m64, const int* __restrict__ rank, cons
               const long long* __restrict__ r_dev, long long K, int q_mode, long long thr_bits, CutParams cp,
               SelState* __restrict__ st)
 {
-    const int64_t r = r_dev ? *r_dev : r_host;
+    const int64_t r = r_dev ? (*r_dev < r_host ? *r_dev : r_host) : r_host;  // within the buffers
     __shared__ long long s_thr[32];
     __shared__ float s_rel[32], s_band[32];
     __shared__ int s_viol[32], s_n[32];
@@ -678,7 +680,12 @@ frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const f
     // the last chunk of a deferred-count stream keeps every entry it could keep (capacity N),
     // so the count need not be read back before the recheck
     const bool defer = last && st.defer_count && N <= (int64_t)(1 << 20);
-    const int64_t want = defer ? N : std::min<int64_t>(N, std::max<int64_t>(4 * st.K + 65536, 1 << 20));
+    // Deferred (count not read back): in q mode the retained set is about K plus the draws
+    // inside the band around the cut, so 4 K + 16384 entries hold it; a larger set overflows
+    // the buffer, which stream_end detects (the count is read back there) and the caller then
+    // redoes the selection without deferral. Threshold mode keeps room for every draw.
+    const int64_t want = defer ? (st.q_mode ? std::min<int64_t>(N, 4 * st.K + 16384) : N)
+                               : std::min<int64_t>(N, std::max<int64_t>(4 * st.K + 65536, 1 << 20));
     if (cap < want) {
         FRR_TRY(ensure_retained(ctx, out, want));
         cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
@@ -690,7 +697,7 @@ frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const f
         FRR_CUDA_TRY(ctx, cudaGetLastError());
         if (st.timing) cudaEventRecord(ctx->ev[2], ctx->stream);
         st.retained = -1;
-        st.retained_bound = N;
+        st.retained_bound = std::min<int64_t>(N, cap);
         ctx->ret_cur = out;
         return FRR_OK;
     }
@@ -886,6 +893,12 @@ frr_status stream_end_finish(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, 
             FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
             st.active = false;
             return FRR_E_TIMEOUT;
+        }
+        if (r > rb) {
+            // the deferred retained set outgrew its buffer: nothing written; redo undeferred
+            st.active = false;
+            st.overflowed = true;
+            return FRR_E_CAPACITY;
         }
     }
     if (st.times_pending) {

@@ -207,3 +207,27 @@ def test_batch_paths_agree_with_single_calls():
         assert np.array_equal(get(bufs["p"]), p) and np.array_equal(get(bufs["c"]), cnt), kind
         same = lambda u, v: u == v or (math.isnan(u) and math.isnan(v))
         assert same(a.ci_lo, lo) and same(a.ci_hi, hi), kind
+
+
+@pytest.mark.parametrize("path", ["select", "batch"])
+def test_heavily_tied_pool_overflows_the_deferred_buffer_and_is_redone(path):
+    """One binary covariate: M takes a handful of values, so about a quarter of the draws tie
+    at the smallest M and the retained set (far more than 4 K + 16384 draws) outgrows the
+    buffer of a deferred selection. The selection is redone without deferral and must still
+    return the K draws with the smallest (M, index), as the oracle does."""
+    n, B, q, seed = 40, 200_000, 0.001, 33
+    X = np.zeros((n, 1))
+    X[: n // 2, 0] = 1.0
+    if path == "select":
+        with frr.Context(X, n // 2, whiten="diag") as ctx:
+            keys, m64 = frr.frr_select(ctx, seed, 0, B, q=q)
+    else:
+        res, st = frr.frr_batch_run([dict(X=X, n1=n // 2, whiten="diag", seed=seed, B=B, q=q)])
+        assert st["status"] == 0
+        keys, m64 = res[0]["keys"], res[0]["m64"]
+    Zc, *_ = O.prep(X, "diag", 0.0)
+    M = O.balance(Zc, n // 2, seed, 0, B)
+    wk, wm = O.select_from_M(M, 0, q=q)
+    assert np.sum(M <= wm.max()) > 4 * len(wk) + 16384  # the overflow really happens
+    assert np.array_equal(keys, wk)
+    assert np.allclose(m64, wm, rtol=1e-11, atol=1e-300)
