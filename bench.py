@@ -31,10 +31,10 @@ from pathlib import Path
 import numpy as np
 
 ROOT = Path(__file__).resolve().parent
-# library kernels per frr_select step of the precision workload (one chunk): k_balance_tc,
-# k_sel_begin, k_sel_hist x2, k_sel_scan x2, k_sel_compact, k_bits, k_recheck_tc,
-# k_recheck_sum, k_rank, k_place_sel, k_sel_summary
-LAUNCHES_PER_STEP = 13
+# library kernels per frr_select step of the precision workload (one chunk): k_sel_init,
+# k_balance_tc, k_sel_begin, k_sel_hist x2, k_sel_scan x2, k_sel_compact, k_bits,
+# k_recheck_tc, k_recheck_sum, k_rank, k_place_sel, k_sel_summary
+LAUNCHES_PER_STEP = 14
 sys.path.insert(0, str(ROOT))
 
 METRIC = "balance-checked assignments/s at n=d=1000; split-BF16 vs FP32 path, same B300"
