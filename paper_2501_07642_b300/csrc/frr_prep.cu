@@ -67,8 +67,18 @@ __global__ void k_colmean(PJ_ARGS)
     const int n = J.n, d = J.d;
     const int j = lb * blockDim.x + threadIdx.x;
     if (j >= d) return;
+    // ascending i, as the definition; the loads run ahead of the dependent FP64 additions
+    const double* x = J.X + j;
     double s = 0.0;
-    for (int i = 0; i < n; ++i) s = __dadd_rn(s, J.X[(size_t)i * d + j]);
+    int i = 0;
+    for (; i + 8 <= n; i += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = x[(size_t)(i + u) * d];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s = __dadd_rn(s, v[u]);
+    }
+    for (; i < n; ++i) s = __dadd_rn(s, x[(size_t)i * d]);
     J.xbar[j] = __ddiv_rn(s, (double)n);
 }
 
@@ -103,23 +113,52 @@ __global__ void k_cov(PJ_ARGS)
     J.S[(size_t)k * d + j] = v;
 }
 
-// trace, max diagonal, and the diagonal of S_lambda (ridge added); one thread per job
-__global__ void k_diag(PJ_ARGS)
+// trace, max diagonal, and the diagonal of S_lambda (ridge added); one block per job. The
+// trace is one chain of FP64 additions in ascending j (as the definition); the maximum (of
+// non-negative values: an integer maximum of their bit patterns) and the ridge diagonal are
+// spread over the block.
+__global__ void __launch_bounds__(256) k_diag(PJ_ARGS)
 {
     unsigned lb;
     const PrepJob& J = job_of(jobs, prefix, E, lb);
-    if (threadIdx.x != 0) return;
     const int d = J.d;
-    double tr = 0.0, mx = 0.0;
-    for (int j = 0; j < d; ++j) {
-        const double s = J.S[(size_t)j * d + j];
-        tr = __dadd_rn(tr, s);
-        if (s > mx) mx = s;
+    const double* S = J.S;
+    __shared__ double s_tr;
+    __shared__ unsigned long long s_mx[8];
+    unsigned long long mx = 0ull;  // bits of +0.0
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(S[(size_t)j * d + j]);
+        mx = b > mx ? b : mx;
     }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(kFull, mx, off);
+        mx = o > mx ? o : mx;
+    }
+    if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
+    if (threadIdx.x == 0) {
+        double tr = 0.0;
+        int j = 0;
+        for (; j + 8 <= d; j += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = S[(size_t)(j + u) * d + (j + u)];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) tr = __dadd_rn(tr, v[u]);
+        }
+        for (; j < d; ++j) tr = __dadd_rn(tr, S[(size_t)j * d + j]);
+        s_tr = tr;
+    }
+    __syncthreads();
+    const double tr = s_tr;
     const double add = (J.whiten == FRR_RIDGE) ? __dmul_rn(J.ridge, __ddiv_rn(tr, (double)d)) : 0.0;
-    for (int j = 0; j < d; ++j) J.Adiag[j] = __dadd_rn(J.S[(size_t)j * d + j], add);
-    J.scal[0] = tr;
-    J.scal[1] = mx;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) J.Adiag[j] = __dadd_rn(S[(size_t)j * d + j], add);
+    if (threadIdx.x == 0) {
+        unsigned long long m = s_mx[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = s_mx[w] > m ? s_mx[w] : m;
+        J.scal[0] = tr;
+        J.scal[1] = __longlong_as_double((long long)m);
+    }
 }
 
 // Working matrix of the factorisation: A = S with the ridge on the diagonal (the lower part
@@ -427,8 +466,15 @@ __global__ void k_qexp(PJ_ARGS)
     const int n = J.n, d = J.d;
     const int j = lb * blockDim.x + threadIdx.x;
     if (j >= d) return;
-    double mx = 0.0;
-    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(J.Zc64[(size_t)i * d + j]));
+    // max |Zc_ij| as an integer maximum of the magnitudes' bit patterns (no FP64 compares)
+    const unsigned long long* z = reinterpret_cast<const unsigned long long*>(J.Zc64) + j;
+    unsigned long long mb = 0ull;
+#pragma unroll 8
+    for (int i = 0; i < n; ++i) {
+        const unsigned long long b = z[(size_t)i * d] & 0x7FFFFFFFFFFFFFFFull;
+        mb = b > mb ? b : mb;
+    }
+    const double mx = __longlong_as_double((long long)mb);
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e with f in [0.5, 1): mx < 2^e
     J.qexp[j] = (mx > 0.0) ? (kQBits - e) : 0;
@@ -483,6 +529,7 @@ __global__ void k_qsum(PJ_ARGS)
     const int j = lb * blockDim.x + threadIdx.x;
     if (j >= d) return;
     long long s = 0;
+#pragma unroll 8
     for (int p = 0; p < kpad; ++p) s += J.Q[(size_t)p * d + j];
     J.Qsum[j] = s;
 }
@@ -744,7 +791,7 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         ++li;
         if (unsigned g = total(li)) k_cov<<<g, dim3(32, 8), 0, s>>>(dj, P(li), E);
         ++li;
-        if (unsigned g = total(li)) k_diag<<<g, 32, 0, s>>>(dj, P(li), E);
+        if (unsigned g = total(li)) k_diag<<<g, 256, 0, s>>>(dj, P(li), E);
         ++li;
         if (unsigned g = total(li)) k_init_L<<<g, 256, 0, s>>>(dj, P(li), E);
         ++li;
