@@ -301,6 +301,7 @@ def run_frr(args):
         dtype = "f32"
     dist_line = distance_bench(peaks["bf16_tflops"]) if args.distance else None
     batch_line = batched_bench(args.batched_reps) if args.batched else None
+    stream_line = stream_bench() if args.stream else None
     cpu = None
     if args.cpu_baseline:
         Zc = oracle_zc(X)
@@ -323,7 +324,7 @@ def run_frr(args):
             "clocks": {k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "selection": {k: r["stats"][k] for k in ("candidates", "accepted", "max_rel_err", "max_err_over_band",
                                                      "band_violations", "parity_at_risk")},
-            "fast_distance": dist_line, "batched": batch_line}
+            "fast_distance": dist_line, "batched": batch_line, "stream": stream_line}
     print(json.dumps(line), flush=True)
 
 
@@ -396,6 +397,36 @@ def batched_bench(reps: int = 3) -> dict:
             "note": "wall time of frr_batch_run with host inputs and outputs"}
 
 
+def stream_bench() -> dict:
+    """The streaming workload (stream_n1000_d1000): 1e8 draws in 1e6-draw chunks through
+    frr_stream_begin / frr_stream_chunk / frr_stream_end at q = 1.2e-5 (K = 1200), split BF16;
+    wall time of the whole stream after a two-chunk warm-up stream, device inputs resident."""
+    import torch
+    from paper_2501_07642_b300 import frr
+    from paper_2501_07642_b300.workloads import workload
+
+    w = workload("stream_n1000_d1000")
+    X = w.covariates()
+    K = math.ceil(w.q * w.draws - 1e-9 * w.q * w.draws)
+    with frr.Context(X, w.n1, precision="split_bf16", whiten=w.whiten, ridge=w.ridge) as ctx:
+        frr.frr_stream_begin(ctx, w.philox_seed, 2 * w.chunk, q=w.q)
+        for c in range(2):
+            frr.frr_stream_chunk(ctx, (1 << 40) + c * w.chunk, w.chunk)
+        frr.frr_stream_end(ctx, 4096)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        frr.frr_stream_begin(ctx, w.philox_seed, w.draws, q=w.q)
+        for c in range(w.draws // w.chunk):
+            frr.frr_stream_chunk(ctx, c * w.chunk, w.chunk)
+        keys, _ = frr.frr_stream_end(ctx, 2 * K)
+        dt = time.perf_counter() - t0
+        st = frr.frr_last_stats(ctx)
+    return {"workload": "stream_n1000_d1000", "draws": w.draws, "chunk": w.chunk, "K": int(len(keys)),
+            "s": dt, "draws_per_s": w.draws / dt, "candidates_rechecked": int(st["candidates"]),
+            "ms_balance": st["ms_balance"], "ms_select": st["ms_select"], "ms_recheck": st["ms_recheck"],
+            "note": "wall time of the stream (one read-back per chunk bounds the retained set)"}
+
+
 def tc_traffic(B):
     """DRAM bytes per k_balance_tc launch from the committed ncu summary, or None when the
     kernel's sources changed since the capture or the launch size differs."""
@@ -414,6 +445,7 @@ def tc_traffic(B):
 
 
 def main():
+    global WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
@@ -427,10 +459,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=7)
     ap.add_argument("--no-distance", dest="distance", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-stream", dest="stream", action="store_false")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="workload of the main leg (for profiling other shapes; the headline is the default)")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the 256-experiment batched leg and print its record (for profiling)")
     ap.add_argument("--batched-reps", type=int, default=3)
     args = ap.parse_args()
+    WORKLOAD = args.workload
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.batched_only:
