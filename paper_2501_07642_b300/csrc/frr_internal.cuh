@@ -107,6 +107,31 @@ struct frr_ctx {
 
 namespace frr {
 
+// ---- programmatic dependent launch ------------------------------------------
+// The selection and recheck kernels of one frr_select follow each other on one stream. Launched
+// with launch_pdl, a kernel's blocks may be scheduled while the previous kernel finishes; each
+// such kernel calls pdl_wait() before it touches memory, which returns once the previous
+// kernel has completed and its writes are visible, and pdl_launch_dependents() to let the next
+// kernel be scheduled early. Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream, A... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 // ---- status helpers ------------------------------------------------------
 #define FRR_CUDA_TRY(ctx, expr)                                                   \
     do {                                                                          \

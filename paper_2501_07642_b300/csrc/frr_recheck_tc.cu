@@ -87,6 +87,8 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
              const long long* __restrict__ C_dev, int nkb, int d, int n, int n1, const long long* __restrict__ Qsum,
              const int* __restrict__ qexp, double* __restrict__ part, int ncb, int* err)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* sB = smem;
@@ -305,10 +307,9 @@ frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint
     FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_recheck_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t items = (int64_t)((count + kM - 1) / kM) * ncb;
     const unsigned grid = (unsigned)std::min<int64_t>(items, ctx->num_sms);
-    k_recheck_tc<<<grid, kThreads, smem, ctx->stream>>>(ctx->qmap, rows, W, count, count_dev, ctx->kused / kKB,
-                                                       (int)ctx->d, (int)ctx->n, (int)ctx->n1, ctx->Qsum, ctx->qexp,
-                                                       part, ncb, ctx->dev_counters + 12);
-    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    FRR_CUDA_TRY(ctx, launch_pdl(k_recheck_tc, grid, kThreads, smem, ctx->stream, ctx->qmap, rows, W, count, count_dev,
+                                 ctx->kused / kKB, (int)ctx->d, (int)ctx->n, (int)ctx->n1, ctx->Qsum, ctx->qexp, part,
+                                 ncb, ctx->dev_counters + 12));
     // the partial sums hold (N_j 2^-q_j)^2 = (n1 n0 Delta_j)^2, and M = (n1 n0 / n) sum Delta_j^2
     return recheck_sum_launch(ctx, part, 2 * ncb, count, M64, 1.0, (double)ctx->n * (double)ctx->n1 * (double)ctx->n0,
                               count_dev);

@@ -33,6 +33,8 @@ __global__ void k_bits(uint64_t seed, int exact, const uint64_t* __restrict__ bi
                        uint64_t count, const long long* __restrict__ count_dev, const uint64_t* __restrict__ draws,
                        uint32_t* __restrict__ rows)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     // a device count can exceed the bound when the retained set overflowed its buffer (the
     // host then redoes the selection); only the entries within the bound exist
     const uint64_t cnt = count_dev ? std::min<uint64_t>((uint64_t)*count_dev, count) : count;
@@ -149,6 +151,8 @@ __global__ void k_recheck_sum(const double* __restrict__ part, int ncb, int64_t 
                               const long long* __restrict__ count_dev, double scale, double denom,
                               double* __restrict__ M64)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t cnt = count_dev ? (*count_dev < count ? *count_dev : count) : count;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cnt; c += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
@@ -262,6 +266,8 @@ __global__ void __launch_bounds__(kHistThreads)
 k_sel_hist(const float* __restrict__ chunk, int64_t nc, const float* __restrict__ ret, int64_t nr, int level,
            SelState* __restrict__ st)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ unsigned h[kBins];
     for (int i = threadIdx.x; i < kBins; i += kHistThreads) h[i] = 0;
     __syncthreads();
@@ -290,6 +296,8 @@ k_sel_hist(const float* __restrict__ chunk, int64_t nc, const float* __restrict_
 // After level 1 it forms the cut. The other histogram is cleared for reuse.
 __global__ void __launch_bounds__(SNT) k_sel_scan(SelState* __restrict__ st, int level, CutParams cp)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ int ws[33];
     const unsigned* h = st->hist[level];
     const int b0 = 4 * threadIdx.x;
@@ -325,6 +333,8 @@ k_sel_compact(const float* __restrict__ chunk, int64_t nc, uint64_t first, const
               const uint64_t* __restrict__ ri_in, int64_t nr, SelState* __restrict__ st, float* __restrict__ rm_out,
               uint64_t* __restrict__ ri_out, int64_t cap_out)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     const float cut = st->cut;
     const int64_t N = nc + nr;
     const int64_t stride = (int64_t)gridDim.x * kHistThreads;
@@ -371,6 +381,8 @@ __global__ void __launch_bounds__(SNT) k_sel_init(SelState* __restrict__ st, flo
 
 __global__ void k_sel_begin(SelState* __restrict__ st, long long K)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->krem = K;
         st->kept = 0;
@@ -383,6 +395,8 @@ __global__ void k_sel_begin(SelState* __restrict__ st, long long K)
 __global__ void k_rank(const double* __restrict__ m, const uint64_t* __restrict__ idx, int64_t r_host,
                        const long long* __restrict__ r_dev, int* __restrict__ rank)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t r = r_dev ? (*r_dev < r_host ? *r_dev : r_host) : r_host;  // within the buffers
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -413,6 +427,8 @@ __global__ void k_place_sel(const double* __restrict__ m, const uint64_t* __rest
                             int64_t r_host, const long long* __restrict__ r_dev, long long K, int q_mode,
                             long long thr_bits, uint64_t* __restrict__ keys_out, double* __restrict__ m_out)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t r = r_dev ? (*r_dev < r_host ? *r_dev : r_host) : r_host;  // within the buffers
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -438,6 +454,8 @@ k_sel_summary(const double* __restrict__ m64, const int* __restrict__ rank, cons
               const long long* __restrict__ r_dev, long long K, int q_mode, long long thr_bits, CutParams cp,
               SelState* __restrict__ st)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t r = r_dev ? (*r_dev < r_host ? *r_dev : r_host) : r_host;  // within the buffers
     __shared__ long long s_thr[32];
     __shared__ float s_rel[32], s_band[32];
@@ -503,9 +521,8 @@ template <int KB>
 frr_status launch_bits_kb(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t count,
                           const long long* count_dev, const uint64_t* draws, uint32_t* rows)
 {
-    k_bits<KB><<<warp_grid(ctx, count), 256, 0, ctx->stream>>>(seed, exact ? 1 : 0, ctx->binom, (int)ctx->n,
-                                                              (int)ctx->n1, first, count, count_dev, draws, rows);
-    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    FRR_CUDA_TRY(ctx, launch_pdl(k_bits<KB>, warp_grid(ctx, count), 256, 0, ctx->stream, seed, exact ? 1 : 0, ctx->binom,
+                                 (int)ctx->n, (int)ctx->n1, first, count, count_dev, draws, rows));
     return FRR_OK;
 }
 
@@ -564,7 +581,8 @@ frr_status recheck_sum_launch(frr_ctx* ctx, const double* part, int ncb, int64_t
                               double denom, const long long* count_dev)
 {
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(count, 256), 4 * ctx->num_sms));
-    k_recheck_sum<<<grid, 256, 0, ctx->stream>>>(part, ncb, count, count_dev, scale, denom, M64);
+    FRR_CUDA_TRY(ctx, launch_pdl(k_recheck_sum, grid, 256, 0, ctx->stream, part, ncb, count, count_dev, scale, denom,
+                                 M64));
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     return FRR_OK;
 }
@@ -668,12 +686,14 @@ frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const f
     const int in = ctx->ret_cur, out = 1 - in;
     const int64_t N = st.retained + (int64_t)bc;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(N, kHistThreads), 4 * ctx->num_sms));
-    k_sel_begin<<<1, 32, 0, ctx->stream>>>(sel, st.K);
+    FRR_CUDA_TRY(ctx, launch_pdl(k_sel_begin, 1, 32, 0, ctx->stream, sel, (long long)st.K));
     if (st.q_mode && N > st.K) {
-        k_sel_hist<<<grid, kHistThreads, 0, ctx->stream>>>(Mhat, (int64_t)bc, ctx->ret_m[in], st.retained, 0, sel);
-        k_sel_scan<<<1, SNT, 0, ctx->stream>>>(sel, 0, cp);
-        k_sel_hist<<<grid, kHistThreads, 0, ctx->stream>>>(Mhat, (int64_t)bc, ctx->ret_m[in], st.retained, 1, sel);
-        k_sel_scan<<<1, SNT, 0, ctx->stream>>>(sel, 1, cp);
+        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_hist, grid, kHistThreads, 0, ctx->stream, Mhat, (int64_t)bc, ctx->ret_m[in],
+                                     st.retained, 0, sel));
+        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_scan, 1, SNT, 0, ctx->stream, sel, 0, cp));
+        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_hist, grid, kHistThreads, 0, ctx->stream, Mhat, (int64_t)bc, ctx->ret_m[in],
+                                     st.retained, 1, sel));
+        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_scan, 1, SNT, 0, ctx->stream, sel, 1, cp));
     }
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     int64_t cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
@@ -691,9 +711,9 @@ frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const f
         cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
     }
     if (defer) {
-        k_sel_compact<<<grid, kHistThreads, 0, ctx->stream>>>(Mhat, (int64_t)bc, first, ctx->ret_m[in],
-                                                             ctx->ret_idx[in], st.retained, sel, ctx->ret_m[out],
-                                                             ctx->ret_idx[out], cap);
+        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_compact, grid, kHistThreads, 0, ctx->stream, Mhat, (int64_t)bc, first,
+                                     ctx->ret_m[in], ctx->ret_idx[in], st.retained, sel, ctx->ret_m[out],
+                                     ctx->ret_idx[out], cap));
         FRR_CUDA_TRY(ctx, cudaGetLastError());
         if (st.timing) cudaEventRecord(ctx->ev[2], ctx->stream);
         st.retained = -1;
@@ -702,9 +722,9 @@ frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const f
         return FRR_OK;
     }
     for (int attempt = 0;; ++attempt) {
-        k_sel_compact<<<grid, kHistThreads, 0, ctx->stream>>>(Mhat, (int64_t)bc, first, ctx->ret_m[in],
-                                                             ctx->ret_idx[in], st.retained, sel, ctx->ret_m[out],
-                                                             ctx->ret_idx[out], cap);
+        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_compact, grid, kHistThreads, 0, ctx->stream, Mhat, (int64_t)bc, first,
+                                     ctx->ret_m[in], ctx->ret_idx[in], st.retained, sel, ctx->ret_m[out],
+                                     ctx->ret_idx[out], cap));
         FRR_CUDA_TRY(ctx, cudaGetLastError());
         long long* hk = static_cast<long long*>(ctx->host_pinned);
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk, &sel->kept, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
@@ -836,11 +856,12 @@ frr_status stream_end_enqueue(frr_ctx* ctx, uint64_t* keys_out, double* M64_out,
         // threshold mode: M64 <= a compares as bit patterns (M64 >= 0); a < 0 accepts nothing
         long long thr_bits = -1;
         if (!st.q_mode && st.threshold >= 0.0) memcpy(&thr_bits, &st.threshold, sizeof(thr_bits));
-        k_rank<<<warp_grid(ctx, rb), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], rb, r_dev, rank);
-        k_place_sel<<<warp_grid(ctx, rb), 256, 0, ctx->stream>>>(m64, ctx->ret_idx[cur], rank, rb, r_dev, st.K,
-                                                                st.q_mode ? 1 : 0, thr_bits, place_k, place_m);
-        k_sel_summary<<<1, SNT, 0, ctx->stream>>>(m64, rank, ctx->ret_m[cur], rb, r_dev, st.K, st.q_mode ? 1 : 0,
-                                                  thr_bits, cut_params(ctx), sel);
+        FRR_CUDA_TRY(ctx, launch_pdl(k_rank, warp_grid(ctx, rb), 256, 0, ctx->stream, m64, ctx->ret_idx[cur], rb, r_dev,
+                                     rank));
+        FRR_CUDA_TRY(ctx, launch_pdl(k_place_sel, warp_grid(ctx, rb), 256, 0, ctx->stream, m64, ctx->ret_idx[cur], rank,
+                                     rb, r_dev, (long long)st.K, st.q_mode ? 1 : 0, thr_bits, place_k, place_m));
+        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_summary, 1, SNT, 0, ctx->stream, m64, rank, ctx->ret_m[cur], rb, r_dev,
+                                     (long long)st.K, st.q_mode ? 1 : 0, thr_bits, cut_params(ctx), sel));
         FRR_CUDA_TRY(ctx, cudaGetLastError());
         // kept (the retained count) and the SelTail fields, in one copy
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hp, &sel->kept, sizeof(long long) + sizeof(SelTail), cudaMemcpyDeviceToHost,
