@@ -29,6 +29,8 @@ namespace {
 __global__ void k_contrasts(const uint32_t* __restrict__ rows, int words, int64_t K, int64_t obs, int n, int n1,
                             const double* __restrict__ Y, double* __restrict__ a, double* __restrict__ b)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (k >= K) return;
@@ -59,6 +61,8 @@ __global__ void k_tau_grid(const double* __restrict__ a, const double* __restric
                            const double* __restrict__ tau, long long* __restrict__ count, double* __restrict__ p,
                            long long* __restrict__ near)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     __shared__ long long sc[32], sn[32];
     const int g = blockIdx.x;
     const double t = tau[g];
@@ -91,6 +95,8 @@ __global__ void k_tau_grid(const double* __restrict__ a, const double* __restric
 __global__ void k_interval(const double* __restrict__ p, const double* __restrict__ tau, int64_t T, double alpha,
                            double* __restrict__ out)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     double lo = INFINITY, hi = -INFINITY;
     for (int64_t g = threadIdx.x; g < T; g += 32)
@@ -138,10 +144,12 @@ frr_status randtest_enqueue(frr_ctx* ctx, uint64_t seed, const uint64_t* keys, b
     FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dy, Y, (size_t)n * 8, cudaMemcpyDefault, ctx->stream));
     FRR_CUDA_TRY(ctx, cudaMemcpyAsync(dtau, tau, (size_t)T * 8, cudaMemcpyDefault, ctx->stream));
     FRR_TRY(bits_launch(ctx, seed, exact, 0, (uint64_t)K, keys_on_device ? keys : dkeys, rows));
-    k_contrasts<<<ceil_div(K, 4), 128, 0, ctx->stream>>>(rows, words, K, obs, n, (int)ctx->n1, dy, da, db);
-    k_tau_grid<<<(unsigned)T, 256, 0, ctx->stream>>>(da, db, K, obs, dtau, dcount, dp, dnear);
-    k_interval<<<1, 32, 0, ctx->stream>>>(dp, dtau, T, alpha, dci);
-    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    FRR_CUDA_TRY(ctx, launch_pdl(k_contrasts, ceil_div(K, 4), 128, 0, ctx->stream, (const uint32_t*)rows, words, K, obs,
+                                 n, (int)ctx->n1, (const double*)dy, da, db));
+    FRR_CUDA_TRY(ctx, launch_pdl(k_tau_grid, (unsigned)T, 256, 0, ctx->stream, (const double*)da, (const double*)db, K,
+                                 obs, (const double*)dtau, dcount, dp, dnear));
+    FRR_CUDA_TRY(ctx, launch_pdl(k_interval, 1, 32, 0, ctx->stream, (const double*)dp, (const double*)dtau, T, alpha,
+                                 dci));
     *dp_out = dp;
     *dcount_out = dcount;
     *dci_out = dci;
