@@ -226,6 +226,33 @@ def test_select_threshold_mode():
     assert np.array_equal(k2, wk)
 
 
+@pytest.mark.parametrize("mode", ["q", "threshold"])
+def test_select_into_device_buffers_equals_host_buffers(mode):
+    """Device outputs: in q mode the placement kernel writes the accepted keys straight into
+    them (the count is K); in threshold mode they are copied after the read-back. Both must
+    equal the host-buffer results, and a too-small device buffer must stay untouched."""
+    import torch
+    w = workload("mc_n100_d100")
+    X = w.covariates()
+    with _ctx(X, w.n1, "split_bf16", w.whiten) as ctx:
+        hk, hm = frr.frr_select(ctx, 1, 500, 60_000, q=0.01)
+        kw = dict(q=0.01) if mode == "q" else dict(threshold=float(hm.max()))
+        hk, hm = frr.frr_select(ctx, 1, 500, 60_000, **kw)
+        dk = torch.full((4096,), -1, dtype=torch.int64, device="cuda")
+        dm = torch.full((4096,), -1.0, dtype=torch.float64, device="cuda")
+        k, m = frr.frr_select(ctx, 1, 500, 60_000, keys_out=dk, M64_out=dm, cap=4096, **kw)
+        K = len(hk)
+        assert len(k) == K
+        assert np.array_equal(dk[:K].cpu().numpy().astype(np.uint64), hk)
+        assert np.array_equal(dm[:K].cpu().numpy(), hm)
+        small = torch.full((K - 1,), -1, dtype=torch.int64, device="cuda")
+        smallm = torch.full((K - 1,), -1.0, dtype=torch.float64, device="cuda")
+        with pytest.raises(frr.FrrError) as e:
+            frr.frr_select(ctx, 1, 500, 60_000, keys_out=small, M64_out=smallm, cap=K - 1, **kw)
+        assert e.value.name == "FRR_E_CAPACITY"
+        assert bool((small == -1).all()) and bool((smallm == -1.0).all())
+
+
 def test_stream_in_shuffled_chunks_equals_one_select():
     w = workload("mc_n100_d100")
     X = w.covariates()
