@@ -7,8 +7,11 @@
  * CPU-baseline leg. It shares no code, header or table with the CUDA path.
  *
  * Every routine is the plain definition written out step by step, in FP64,
- * compiled with -ffp-contract=off (no fused multiply-add), with sums taken in
- * ascending index order. There is no blocking, fusion or reordering.
+ * compiled with -ffp-contract=off (no implicit contraction), with sums taken in
+ * ascending index order. The dot products of the preparation (covariance,
+ * Cholesky factor, forward substitution) add each term with one explicit fused
+ * multiply-add, fma() -- a single rounding per term; every other operation is
+ * rounded on its own. There is no blocking, fusion or reordering.
  *
  * Pins: each function is checked by tests/test_oracle_pins.py against values
  * fixed by the paper or by mathematics (Philox known-answer vectors, brute-force
@@ -217,7 +220,7 @@ int oracle_prep(const double* X, int64_t n, int64_t d, int whiten, double ridge,
     for (int64_t j = 0; j < d; ++j)
         for (int64_t k = 0; k < d; ++k) {
             double s = 0.0;
-            for (int64_t i = 0; i < n; ++i) s += Xc[i * d + j] * Xc[i * d + k];
+            for (int64_t i = 0; i < n; ++i) s = fma(Xc[i * d + j], Xc[i * d + k], s);
             S[j * d + k] = s / (double)(n - 1);
         }
 
@@ -243,13 +246,13 @@ int oracle_prep(const double* X, int64_t n, int64_t d, int whiten, double ridge,
         /* column-oriented Cholesky, ascending k */
         for (int64_t j = 0; j < d; ++j) {
             double s = A[j * d + j];
-            for (int64_t k = 0; k < j; ++k) s -= Lw[j * d + k] * Lw[j * d + k];
+            for (int64_t k = 0; k < j; ++k) s = fma(-Lw[j * d + k], Lw[j * d + k], s);
             if (!(s > tol * maxdiag)) { status = -2; free(A); goto done; }
             double ljj = sqrt(s);
             Lw[j * d + j] = ljj;
             for (int64_t i = j + 1; i < d; ++i) {
                 double t = A[i * d + j];
-                for (int64_t k = 0; k < j; ++k) t -= Lw[i * d + k] * Lw[j * d + k];
+                for (int64_t k = 0; k < j; ++k) t = fma(-Lw[i * d + k], Lw[j * d + k], t);
                 Lw[i * d + j] = t / ljj;
             }
         }
@@ -260,7 +263,7 @@ int oracle_prep(const double* X, int64_t n, int64_t d, int whiten, double ridge,
     for (int64_t i = 0; i < n; ++i) {
         for (int64_t j = 0; j < d; ++j) {
             double t = Xc[i * d + j];
-            for (int64_t k = 0; k < j; ++k) t -= Lw[j * d + k] * Zc[i * d + k];
+            for (int64_t k = 0; k < j; ++k) t = fma(-Lw[j * d + k], Zc[i * d + k], t);
             Zc[i * d + j] = t / Lw[j * d + j];
         }
     }

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
 benchmark's CPU-baseline leg, never by the product package. It shares no code
 with the CUDA path and does not import it.
 
-``build()`` compiles frr_oracle.c with gcc (-O2 -ffp-contract=off -fopenmp)
+``build()`` compiles frr_oracle.c with gcc (-O2 -ffp-contract=off -fopenmp, -mfma where available)
 into oracle/_build/libfrr_oracle.so.
 """
 from __future__ import annotations
@@ -25,12 +25,23 @@ _lib = None
 WHITEN = {"chol": 0, "ridge": 1, "diag": 2}
 
 
+def _cpu_has_fma() -> bool:
+    try:
+        with open("/proc/cpuinfo") as f:
+            return any(line.startswith("flags") and " fma " in f" {line.split(':', 1)[1].strip()} " for line in f)
+    except OSError:
+        return False
+
+
 def build(force: bool = False) -> Path:
-    """Compile the oracle shared library (FP64, no FMA contraction, OpenMP)."""
+    """Compile the oracle shared library (FP64, no implicit contraction, OpenMP). The explicit
+    fma() calls of the preparation are correctly rounded either way; with -mfma they compile
+    to the hardware instruction instead of a library call (much faster at n = d = 1000)."""
     _OUT.parent.mkdir(parents=True, exist_ok=True)
     if force or not _OUT.exists() or _OUT.stat().st_mtime < _SRC.stat().st_mtime:
         tmp = _OUT.with_suffix(f".{os.getpid()}.tmp.so")
-        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+        extra = ["-mfma"] if _cpu_has_fma() else []
+        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", *extra,
                         "-fPIC", "-shared", str(_SRC), "-o", str(tmp), "-lm"], check=True)
         os.replace(tmp, _OUT)
     return _OUT

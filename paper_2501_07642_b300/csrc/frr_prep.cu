@@ -4,9 +4,10 @@
 // Mahalanobis distance is Euclidean (App. A, remark on general Sigma_X):
 //   xbar = column means, Xc = X - 1 xbar^T, S = Xc^T Xc / (n - 1),
 //   S_lambda = S (+ ridge * tr(S)/d * I), S_lambda = L L^T, Zc = Xc L^{-T}.
-// Every step uses explicitly rounded FP64 operations (no contraction into
-// FMA) in ascending index order, one dependent chain per output, so the
-// results do not depend on the launch shape.
+// Every step uses explicitly rounded FP64 operations in ascending index order,
+// one dependent chain per output, so the results do not depend on the launch
+// shape; each term of a dot product (covariance, Cholesky factor, forward
+// substitution) is added by one fused multiply-add (one rounding per term).
 //
 // From Zc (natural unit order) the kernels below derive the arrays the
 // balance path reads, all in K-order (see frr_gen.cuh):
@@ -107,7 +108,7 @@ __global__ void k_cov(PJ_ARGS)
     if (j >= d || k >= d || k < j) return;
     const double* Xc = J.Xc;
     double s = 0.0;
-    for (int i = 0; i < n; ++i) s = __dadd_rn(s, __dmul_rn(Xc[(size_t)i * d + j], Xc[(size_t)i * d + k]));
+    for (int i = 0; i < n; ++i) s = __fma_rn(Xc[(size_t)i * d + j], Xc[(size_t)i * d + k], s);
     const double v = __ddiv_rn(s, (double)(n - 1));
     J.S[(size_t)j * d + k] = v;
     J.S[(size_t)k * d + j] = v;
@@ -183,8 +184,8 @@ __global__ void k_init_L(PJ_ARGS)
 }
 
 // ---- blocked factorisation with the same operation order --------------------------
-// Panels of kP columns. Every entry of the working matrix receives its subtractions
-// "- L_ik L_jk" (resp. "- L_jk z_ik") one by one in ascending k -- earlier panels through
+// Panels of kP columns. Every entry of the working matrix receives its fused
+// multiply-subtractions "- L_ik L_jk" (resp. "- L_jk z_ik") one by one in ascending k -- earlier panels through
 // the trailing updates, the current panel inside the panel kernel -- followed by the
 // same square root / division, so the results equal the column-by-column definition
 // bit for bit while the work runs in parallel.
@@ -236,14 +237,14 @@ __device__ __forceinline__ void eliminate_rows(double (&t)[kPC], int pw, const d
 #pragma unroll
             for (int c = 0; c < kPC; ++c)
                 if (w + kPW * c == nxt) {
-                    t[c] = div_rn_recip(__dsub_rn(t[c], __dmul_rn(Lc[jj][nxt], z)), Ld[nxt], Yd[nxt]);
+                    t[c] = div_rn_recip(__fma_rn(-Lc[jj][nxt], z, t[c]), Ld[nxt], Yd[nxt]);
                     Zs[nxt][lane] = t[c];
                 }
         }
 #pragma unroll
         for (int c = 0; c < kPC; ++c) {
             const int kk = w + kPW * c;
-            if (kk > nxt && kk < pw) t[c] = __dsub_rn(t[c], __dmul_rn(Lc[jj][kk], z));
+            if (kk > nxt && kk < pw) t[c] = __fma_rn(-Lc[jj][kk], z, t[c]);
         }
     }
 }
@@ -293,14 +294,14 @@ __global__ void __launch_bounds__(kP * kPW) k_chol_diag(PJ_ARGS, int p)
 #pragma unroll
             for (int c = 0; c < kPC; ++c)
                 if (w + kPW * c == nxt) {
-                    if (r >= nxt && r < pw) t[c] = __dsub_rn(t[c], __dmul_rn(lrj, Lc[jj][nxt]));
+                    if (r >= nxt && r < pw) t[c] = __fma_rn(-lrj, Lc[jj][nxt], t[c]);
                     finish_col(t[c], nxt);
                 }
         }
 #pragma unroll
         for (int c = 0; c < kPC; ++c) {
             const int kk = w + kPW * c;
-            if (kk > nxt && kk < pw && r >= kk && r < pw) t[c] = __dsub_rn(t[c], __dmul_rn(lrj, Lc[jj][kk]));
+            if (kk > nxt && kk < pw && r >= kk && r < pw) t[c] = __fma_rn(-lrj, Lc[jj][kk], t[c]);
         }
     }
 #pragma unroll
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(256) k_chol_trailing(PJ_ARGS, int p)
         const int i = i0 + ii, j = j0 + jj;
         if (i >= d || j > i) continue;
         double v = A[(size_t)i * d + j];
-        for (int kk = 0; kk < pw; ++kk) v = __dsub_rn(v, __dmul_rn(Li[ii][kk], Lj[jj][kk]));
+        for (int kk = 0; kk < pw; ++kk) v = __fma_rn(-Li[ii][kk], Lj[jj][kk], v);
         A[(size_t)i * d + j] = v;
     }
 }
@@ -445,7 +446,7 @@ __global__ void __launch_bounds__(256) k_fwd_trailing(PJ_ARGS, int p)
         const int i = i0 + ii, j = j0 + jj;
         if (i >= n || j >= d) continue;
         double v = T[(size_t)i * d + j];
-        for (int kk = 0; kk < pw; ++kk) v = __dsub_rn(v, __dmul_rn(Lj[jj][kk], Zi[ii][kk]));
+        for (int kk = 0; kk < pw; ++kk) v = __fma_rn(-Lj[jj][kk], Zi[ii][kk], v);
         T[(size_t)i * d + j] = v;
     }
 }
