@@ -64,6 +64,18 @@ def test_batch_reports_per_experiment_errors():
     assert stats["status"] == -2 and stats["failed"] == 1
     assert res[0]["status"] == 0 and res[2]["status"] == 0 and res[1]["status"] == -2
     assert np.array_equal(res[0]["keys"], res[2]["keys"]) and res[0]["K"] == 100
+    # a non-finite covariate (caught while staging the batch's covariates), a degenerate
+    # pivot (a duplicated column: S is singular, found on the device) and an exact-mode rank
+    # range beyond C(n, n1) each fail alone
+    nan_x = ar1_covariates(40, 5, 4, 0.0)
+    nan_x[7, 2] = np.nan
+    dup = ar1_covariates(40, 6, 5, 0.0)
+    dup[:, 3] = dup[:, 1]
+    exact_bad = dict(X=ar1_covariates(12, 3, 6, 0.0), n1=6, seed=frr.FRR_EXACT_SEED, first_draw=900, B=100, q=0.1)
+    res, stats = frr.frr_batch_run([good, dict(good, X=nan_x), dict(good, X=dup), exact_bad, good])
+    assert [r["status"] for r in res] == [0, -1, -2, -7, 0]
+    assert stats["failed"] == 3
+    assert np.array_equal(res[0]["keys"], res[4]["keys"])
 
 
 def test_batched_workload_256_experiments_sampled():
