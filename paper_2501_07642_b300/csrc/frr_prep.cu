@@ -22,6 +22,7 @@
 // launches as one experiment and its many small, latency-bound steps share the SMs.
 #include "frr_internal.cuh"
 #include "frr_gen.cuh"
+#include "frr_tc_ptx.cuh"
 
 #include <algorithm>
 #include <vector>
@@ -47,6 +48,9 @@ namespace {
 
 #define PJ_ARGS const PrepJob* __restrict__ jobs, const unsigned* __restrict__ prefix, int E
 
+// Status bits of a preparation: 1 = non-positive Cholesky pivot, 2 = a bounded wait expired.
+constexpr int kStatusPivot = 1, kStatusTimeout = 2;
+
 // The job owning this block and the block's index within the job: prefix[e] is the first
 // block of job e (jobs with no blocks have prefix[e] == prefix[e + 1]).
 __device__ __forceinline__ const PrepJob& job_of(PJ_ARGS, unsigned& local)
@@ -68,18 +72,23 @@ __global__ void k_colmean(PJ_ARGS)
     const int n = J.n, d = J.d;
     const int j = lb * blockDim.x + threadIdx.x;
     if (j >= d) return;
-    // ascending i, as the definition; the loads run ahead of the dependent FP64 additions
+    // ascending i, as the definition. The chain of dependent FP64 additions sets the time, so
+    // the loads of the next kU rows are issued before the additions of the current kU rows.
+    constexpr int kU = 16;
     const double* x = J.X + j;
-    double s = 0.0;
-    int i = 0;
-    for (; i + 8 <= n; i += 8) {
-        double v[8];
+    double s = 0.0, cur[kU];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = x[(size_t)(i + u) * d];
+    for (int u = 0; u < kU; ++u) cur[u] = (u < n) ? x[(size_t)u * d] : 0.0;
+    for (int i = 0; i < n; i += kU) {
+        double nxt[kU];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) s = __dadd_rn(s, v[u]);
+        for (int u = 0; u < kU; ++u) nxt[u] = (i + kU + u < n) ? x[(size_t)(i + kU + u) * d] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i + u < n) s = __dadd_rn(s, cur[u]);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) cur[u] = nxt[u];
     }
-    for (; i < n; ++i) s = __dadd_rn(s, x[(size_t)i * d]);
     J.xbar[j] = __ddiv_rn(s, (double)n);
 }
 
@@ -179,7 +188,7 @@ __global__ void k_init_L(PJ_ARGS)
     if (i != j) { J.Lm[idx] = 0.0; return; }
     const double tol_abs = __dmul_rn(1e-12, J.scal[1]);  // pivot tolerance relative to max S_jj
     const double s = J.S[idx];
-    if (!(s > tol_abs)) atomicExch(J.status, 1);
+    if (!(s > tol_abs)) atomicOr(J.status, kStatusPivot);
     J.Lm[idx] = __dsqrt_rn(s > 0.0 ? s : 1.0);
 }
 
@@ -191,25 +200,62 @@ __global__ void k_init_L(PJ_ARGS)
 // bit for bit while the work runs in parallel.
 constexpr int kP = 32;
 
-// The panel kernels work on groups of 32 rows with lane = row; the pw <= 32 panel columns are
-// spread over kPW warps (warp w owns columns w, w + kPW, ...), so that the independent updates
-// of a step run on several warps at once: B300 issues a warp's FP64 instructions about one per
-// 64 cycles, so one warp per row group (all 32 columns in one thread) is issue-bound. Each
-// step publishes the finished column through shared memory; the owner of the next column
-// updates and finishes that column first (look-ahead), then the other owned columns follow.
-constexpr int kPW = 8;
-constexpr int kPC = kP / kPW;  // columns per warp
+// The panel kernels work on groups of 32 rows with lane = row, one warp per panel column
+// (kP warps). B300 runs FP64 at about one warp instruction per 19 cycles per SM, shared
+// among the warps that issue it, and at most one per 64 cycles for a single warp; every
+// issued FP64 instruction counts, predicated off or not. So the kernels let a column's
+// dependent chain (its last update, then the square root or division) compete with as few
+// other FP64 instructions as possible: warp w owns column w, applies the updates from
+// columns jj < w as soon as each of them is published (one mbarrier per column, 32 lane
+// arrivals after the lane's store of the finished value), finishes its column and stops.
+// No block-wide barrier holds the warps in lockstep, and finished warps issue nothing.
+constexpr int kPW = kP;  // warps per panel block
+
+// Bounded wait for the publication of one column (phase `parity` of its mbarrier). On expiry
+// the block's abort flag and the timeout bit are raised; later waits of the block return at once.
+__device__ __forceinline__ bool wait_col(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status)
+{
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = clock64();
+    for (;;) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > tc::kWaitCycles) {
+            *abort_flag = 1;
+            atomicOr(status, kStatusTimeout);
+            return false;
+        }
+    }
+}
+
+// Shared state of a panel block: the published columns Zs[jj][lane] with their mbarriers.
+struct PanelSync {
+    double Zs[kP][32];
+    uint64_t bar[kP];
+    int abort_flag;
+};
+
+__device__ __forceinline__ void panel_sync_init(PanelSync& ps)
+{
+    if (threadIdx.x < kP) tc::mbar_init(&ps.bar[threadIdx.x], 32);
+    if (threadIdx.x == 0) ps.abort_flag = 0;
+}
+
+// Publish the finished value of column w for this lane's row (every lane of the warp arrives).
+__device__ __forceinline__ void publish(PanelSync& ps, int w, int lane, double v)
+{
+    ps.Zs[w][lane] = v;
+    tc::mbar_arrive(&ps.bar[w]);
+}
 
 // RN(a / b) from y = RN(1 / b) by Markstein's method (P. Markstein, IBM J. Res. Dev. 34(1),
 // 1990): from a quotient within one ulp of a / b, q + (a - b q) y rounded once (FMA, with the
 // residual a - b q exact) is the correctly rounded quotient; one correction step from RN(a y)
-// supplies such a quotient. The intermediate values must neither underflow nor overflow, so
-// operands outside a safe exponent range (zero and subnormals included) use the division
-// operator. Five dependent FP64 operations instead of a division.
-__device__ __forceinline__ double div_rn_recip(double a, double b, double y)
+// supplies such a quotient. Five dependent FP64 operations instead of a division. The
+// intermediate values must neither underflow nor overflow, and a zero dividend must keep its
+// sign, so the result is correct only when markstein_unsafe(a, b) is false.
+__device__ __forceinline__ double div_markstein(double a, double b, double y)
 {
-    const int ea = (__double2hiint(a) >> 20) & 0x7ff, eb = (__double2hiint(b) >> 20) & 0x7ff;
-    if (ea < 1023 - 900 || ea > 1023 + 900 || eb < 1023 - 400 || eb > 1023 + 400) return __ddiv_rn(a, b);
     const double q0 = __dmul_rn(a, y);
     const double r0 = __fma_rn(-q0, b, a);
     const double q1 = __fma_rn(r0, y, q0);
@@ -217,45 +263,65 @@ __device__ __forceinline__ double div_rn_recip(double a, double b, double y)
     return __fma_rn(r1, y, q1);
 }
 
-// Right-looking elimination of one 32-row group (lane = row, t[c] = column w + kPW c) against a
-// finished lower-triangular pw x pw block: for jj ascending, t_jj /= L_jj,jj, then
-// t_kk -= L_kk,jj t_jj for jj < kk < pw. Every entry gets its subtractions in ascending jj and
-// then its division, as in the column-by-column definition. Lc[jj][kk] = L_{kk,jj} (kk >= jj),
-// Ld / Yd the diagonal and its reciprocals, Zs[jj][lane] the exchange of finished columns.
-__device__ __forceinline__ void eliminate_rows(double (&t)[kPC], int pw, const double (*Lc)[kP + 1],
-                                               const double* Ld, const double* Yd, double (*Zs)[32], int w, int lane)
+// Operands outside the safe exponent range of div_markstein (zero and subnormals included).
+__device__ __forceinline__ bool markstein_unsafe(double a, double b)
 {
-    if (w == 0) {
-        t[0] = div_rn_recip(t[0], Ld[0], Yd[0]);
-        Zs[0][lane] = t[0];
+    const int ea = (__double2hiint(a) >> 20) & 0x7ff, eb = (__double2hiint(b) >> 20) & 0x7ff;
+    return ea < 1023 - 900 || ea > 1023 + 900 || eb < 1023 - 400 || eb > 1023 + 400;
+}
+
+// Column w of one 32-row group (lane = row, t = the working value) eliminated against a
+// finished lower-triangular pw x pw block: t -= L_w,jj z_jj for jj < w ascending, as each
+// z_jj is published (mbarrier phase `parity`), then t /= L_w,w; the result is published as
+// column w. Lc[jj][kk] = L_{kk,jj} (kk >= jj), Ld / Yd the diagonal and its reciprocals.
+// kExact = false divides by div_markstein and ORs markstein_unsafe into `unsafe` for rows
+// that exist (row_ok; padding rows hold zeros and are never stored, and a zero dividend would
+// otherwise send the last row block of every launch down the slow path); kExact = true uses
+// the division operator.
+template <bool kExact>
+__device__ __forceinline__ double eliminate_col(double t, int w, int lane, const double (*Lc)[kP + 1],
+                                                const double* Ld, const double* Yd, PanelSync& ps, uint32_t parity,
+                                                bool row_ok, bool& unsafe, int* status)
+{
+    for (int jj = 0; jj < w; ++jj) {
+        if (!wait_col(&ps.bar[jj], parity, &ps.abort_flag, status)) break;
+        t = __fma_rn(-Lc[jj][w], ps.Zs[jj][lane], t);
     }
-    for (int jj = 0; jj < pw; ++jj) {
-        __syncthreads();
-        const double z = Zs[jj][lane];
-        const int nxt = jj + 1;
-        if (nxt < pw && w == nxt % kPW) {
-#pragma unroll
-            for (int c = 0; c < kPC; ++c)
-                if (w + kPW * c == nxt) {
-                    t[c] = div_rn_recip(__fma_rn(-Lc[jj][nxt], z, t[c]), Ld[nxt], Yd[nxt]);
-                    Zs[nxt][lane] = t[c];
-                }
-        }
-#pragma unroll
-        for (int c = 0; c < kPC; ++c) {
-            const int kk = w + kPW * c;
-            if (kk > nxt && kk < pw) t[c] = __fma_rn(-Lc[jj][kk], z, t[c]);
-        }
+    if (kExact) {
+        t = __ddiv_rn(t, Ld[w]);
+    } else {
+        unsafe |= row_ok && markstein_unsafe(t, Ld[w]);
+        t = div_markstein(t, Ld[w], Yd[w]);
     }
+    publish(ps, w, lane, t);
+    return t;
+}
+
+// The row-panel elimination of a block: the fast pass with div_markstein, and, if any
+// division of the block had operands outside its safe range (rare: zero or extreme values),
+// the whole pass again from the original values with the division operator (the second
+// phase of every column's mbarrier). Every warp of the block calls this (warps w >= pw only
+// take part in the block-wide vote).
+__device__ __forceinline__ double eliminate_panel_rows(double t0, int pw, int w, int lane, const double (*Lc)[kP + 1],
+                                                       const double* Ld, const double* Yd, PanelSync& ps, bool row_ok,
+                                                       int* status)
+{
+    bool unsafe = false;
+    double t = t0;
+    if (w < pw) t = eliminate_col<false>(t0, w, lane, Lc, Ld, Yd, ps, 0u, row_ok, unsafe, status);
+    if (__syncthreads_or(unsafe) && w < pw)
+        t = eliminate_col<true>(t0, w, lane, Lc, Ld, Yd, ps, 1u, row_ok, unsafe, status);
+    return t;
 }
 
 // Diagonal block of panel p (columns [32 p, 32 p + pw)) of the Cholesky factor, in place in
 // Lm (row-major d x d, lower part: working values, final L on exit); one block per job, lane =
-// row of the block. Right-looking: at step jj the pivot becomes L_jj,jj, the rows below divide
-// by it, and every later entry (kk, r) with jj < kk <= r subtracts L_r,jj L_kk,jj (the
-// diagonal entry subtracts a square). The rows below the block follow in k_chol_below, which
-// reads the finished block (a separate launch: blocks of one launch may start after others
-// have finished, so the block must not be overwritten while other blocks may still read it).
+// row of the block, warp w = column w. Column w receives - L_r,jj L_w,jj for jj < w in
+// ascending jj (each as soon as column jj is published), then its pivot L_w,w = sqrt(t_w,w)
+// and the divisions of the rows below it. The rows below the block follow in k_chol_below,
+// which reads the finished block (a separate launch: blocks of one launch may start after
+// others have finished, so the block must not be overwritten while other blocks may still
+// read it).
 __global__ void __launch_bounds__(kP * kPW) k_chol_diag(PJ_ARGS, int p)
 {
     unsigned lb;
@@ -264,51 +330,28 @@ __global__ void __launch_bounds__(kP * kPW) k_chol_diag(PJ_ARGS, int p)
     const int pw = (d - k0) < kP ? (d - k0) : kP;
     double* __restrict__ A = J.Lm;
     const double tol_abs = __dmul_rn(1e-12, J.scal[1]);  // pivot tolerance relative to max S_jj
-    __shared__ double Lc[kP][kP + 1];  // Lc[jj][r] = L_{k0+r, k0+jj}, r >= jj
+    __shared__ PanelSync ps;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r = lane;
-    double t[kPC];
-#pragma unroll
-    for (int c = 0; c < kPC; ++c) {
-        const int kk = w + kPW * c;
-        t[c] = (r < pw && kk <= r) ? A[(size_t)(k0 + r) * d + k0 + kk] : 0.0;
+    double t = (r < pw && w < pw && w <= r) ? A[(size_t)(k0 + r) * d + k0 + w] : 0.0;
+    panel_sync_init(ps);
+    __syncthreads();
+    if (w >= pw) return;
+    for (int jj = 0; jj < w; ++jj) {
+        if (!wait_col(&ps.bar[jj], 0u, &ps.abort_flag, J.status)) break;
+        t = __fma_rn(-ps.Zs[jj][lane], ps.Zs[jj][w], t);
     }
-    // finish column j held in tc by its owner warp: pivot on lane j, division below it
-    auto finish_col = [&](double& tc, int j) {
-        double piv = 0.0;
-        if (lane == j) {
-            if (!(tc > tol_abs)) atomicExch(J.status, 1);
-            piv = __dsqrt_rn(tc > 0.0 ? tc : 1.0);
-        }
-        piv = __shfl_sync(0xffffffffu, piv, j);
-        if (lane == j) tc = piv;
-        else if (lane > j && lane < pw) tc = __ddiv_rn(tc, piv);
-        if (lane >= j && lane < pw) Lc[j][lane] = tc;
-    };
-    if (w == 0) finish_col(t[0], 0);
-    for (int jj = 0; jj < pw; ++jj) {
-        __syncthreads();
-        const double lrj = (r >= jj && r < pw) ? Lc[jj][r] : 0.0;
-        const int nxt = jj + 1;
-        if (nxt < pw && w == nxt % kPW) {
-#pragma unroll
-            for (int c = 0; c < kPC; ++c)
-                if (w + kPW * c == nxt) {
-                    if (r >= nxt && r < pw) t[c] = __fma_rn(-lrj, Lc[jj][nxt], t[c]);
-                    finish_col(t[c], nxt);
-                }
-        }
-#pragma unroll
-        for (int c = 0; c < kPC; ++c) {
-            const int kk = w + kPW * c;
-            if (kk > nxt && kk < pw && r >= kk && r < pw) t[c] = __fma_rn(-lrj, Lc[jj][kk], t[c]);
-        }
+    // pivot on lane w, division below it
+    double piv = 0.0;
+    if (lane == w) {
+        if (!(t > tol_abs)) atomicOr(J.status, kStatusPivot);
+        piv = __dsqrt_rn(t > 0.0 ? t : 1.0);
     }
-#pragma unroll
-    for (int c = 0; c < kPC; ++c) {
-        const int kk = w + kPW * c;
-        if (r < pw && kk <= r) A[(size_t)(k0 + r) * d + k0 + kk] = t[c];
-    }
+    piv = __shfl_sync(0xffffffffu, piv, w);
+    if (lane == w) t = piv;
+    else if (lane > w && lane < pw) t = __ddiv_rn(t, piv);
+    publish(ps, w, lane, (lane >= w && lane < pw) ? t : 0.0);
+    if (r < pw && w <= r) A[(size_t)(k0 + r) * d + k0 + w] = t;
 }
 
 // Rows below the diagonal block of panel p, 32 per block: L_r,jj = (A_r,jj - sum_{k<jj}
@@ -321,10 +364,10 @@ __global__ void __launch_bounds__(kP * kPW) k_chol_below(PJ_ARGS, int p)
     const int pw = (d - k0) < kP ? (d - k0) : kP;
     double* __restrict__ A = J.Lm;
     __shared__ double Lc[kP][kP + 1];  // Lc[jj][kk] = L_{k0+kk, k0+jj}, kk >= jj
-    __shared__ double Zs[kP][32];
     __shared__ double Ld[kP], Yd[kP];
-    for (int e = threadIdx.x; e < kP * kP; e += blockDim.x) {
-        const int jj = e / kP, kk = e % kP;
+    __shared__ PanelSync ps;
+    {
+        const int jj = threadIdx.x / kP, kk = threadIdx.x % kP;
         Lc[jj][kk] = (kk < pw && kk >= jj) ? A[(size_t)(k0 + kk) * d + k0 + jj] : 0.0;
     }
     if (threadIdx.x < pw) {
@@ -334,19 +377,11 @@ __global__ void __launch_bounds__(kP * kPW) k_chol_below(PJ_ARGS, int p)
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r = k0 + pw + (int)lb * 32 + lane;
-    double t[kPC];
-#pragma unroll
-    for (int c = 0; c < kPC; ++c) {
-        const int kk = w + kPW * c;
-        t[c] = (r < d && kk < pw) ? A[(size_t)r * d + k0 + kk] : 0.0;
-    }
+    const double t0 = (r < d && w < pw) ? A[(size_t)r * d + k0 + w] : 0.0;
+    panel_sync_init(ps);
     __syncthreads();
-    eliminate_rows(t, pw, Lc, Ld, Yd, Zs, w, lane);
-#pragma unroll
-    for (int c = 0; c < kPC; ++c) {
-        const int kk = w + kPW * c;
-        if (r < d && kk < pw) A[(size_t)r * d + k0 + kk] = t[c];
-    }
+    const double t = eliminate_panel_rows(t0, pw, w, lane, Lc, Ld, Yd, ps, r < d, J.status);
+    if (r < d && w < pw) A[(size_t)r * d + k0 + w] = t;
 }
 
 // Trailing update after panel p: A_ij -= L_ik L_jk for k in the panel (ascending), for
@@ -394,10 +429,10 @@ __global__ void __launch_bounds__(kP * kPW) k_fwd_panel(PJ_ARGS, int p)
     const double* __restrict__ L = J.Lm;
     double* __restrict__ T = J.ZT;
     __shared__ double Lc[kP][kP + 1];  // Lc[jj][kk] = L_{k0+kk, k0+jj}, kk >= jj
-    __shared__ double Zs[kP][32];
     __shared__ double Ld[kP], Yd[kP];
-    for (int e = threadIdx.x; e < kP * kP; e += blockDim.x) {
-        const int jj = e / kP, kk = e % kP;
+    __shared__ PanelSync ps;
+    {
+        const int jj = threadIdx.x / kP, kk = threadIdx.x % kP;
         Lc[jj][kk] = (kk < pw && kk >= jj) ? L[(size_t)(k0 + kk) * d + k0 + jj] : 0.0;
     }
     if (threadIdx.x < pw) {
@@ -407,19 +442,11 @@ __global__ void __launch_bounds__(kP * kPW) k_fwd_panel(PJ_ARGS, int p)
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = (int)lb * 32 + lane;
-    double t[kPC];
-#pragma unroll
-    for (int c = 0; c < kPC; ++c) {
-        const int kk = w + kPW * c;
-        t[c] = (i < n && kk < pw) ? T[(size_t)i * d + k0 + kk] : 0.0;
-    }
+    const double t0 = (i < n && w < pw) ? T[(size_t)i * d + k0 + w] : 0.0;
+    panel_sync_init(ps);
     __syncthreads();
-    eliminate_rows(t, pw, Lc, Ld, Yd, Zs, w, lane);
-#pragma unroll
-    for (int c = 0; c < kPC; ++c) {
-        const int kk = w + kPW * c;
-        if (i < n && kk < pw) T[(size_t)i * d + k0 + kk] = t[c];
-    }
+    const double t = eliminate_panel_rows(t0, pw, w, lane, Lc, Ld, Yd, ps, i < n, J.status);
+    if (i < n && w < pw) T[(size_t)i * d + k0 + w] = t;
 }
 
 // T_ij -= L_jk z_ik for k in panel p (ascending), j >= k0 + pw. 32 x 32 tiles, local block
@@ -459,22 +486,31 @@ __global__ void k_copy_zc(PJ_ARGS)
     if (idx < (size_t)J.n * J.d) J.Zc64[idx] = J.ZT[idx];
 }
 
-// qexp_j such that |Zc_ij * 2^qexp_j| <= 2^kQBits for every i
-__global__ void k_qexp(PJ_ARGS)
+// qexp_j such that |Zc_ij * 2^qexp_j| <= 2^kQBits for every i. Block (32, kRG): 32 columns,
+// the rows split over kRG thread rows (a maximum does not depend on the order of its operands).
+constexpr int kRG = 16;
+
+__global__ void __launch_bounds__(32 * kRG) k_qexp(PJ_ARGS)
 {
     unsigned lb;
     const PrepJob& J = job_of(jobs, prefix, E, lb);
     const int n = J.n, d = J.d;
-    const int j = lb * blockDim.x + threadIdx.x;
-    if (j >= d) return;
+    const int j = (int)lb * 32 + threadIdx.x;
+    __shared__ unsigned long long part[kRG][32];
     // max |Zc_ij| as an integer maximum of the magnitudes' bit patterns (no FP64 compares)
-    const unsigned long long* z = reinterpret_cast<const unsigned long long*>(J.Zc64) + j;
     unsigned long long mb = 0ull;
+    if (j < d) {
+        const unsigned long long* z = reinterpret_cast<const unsigned long long*>(J.Zc64) + j;
 #pragma unroll 8
-    for (int i = 0; i < n; ++i) {
-        const unsigned long long b = z[(size_t)i * d] & 0x7FFFFFFFFFFFFFFFull;
-        mb = b > mb ? b : mb;
+        for (int i = threadIdx.y; i < n; i += kRG) {
+            const unsigned long long b = z[(size_t)i * d] & 0x7FFFFFFFFFFFFFFFull;
+            mb = b > mb ? b : mb;
+        }
     }
+    part[threadIdx.y][threadIdx.x] = mb;
+    __syncthreads();
+    if (threadIdx.y != 0 || j >= d) return;
+    for (int g = 1; g < kRG; ++g) mb = part[g][threadIdx.x] > mb ? part[g][threadIdx.x] : mb;
     const double mx = __longlong_as_double((long long)mb);
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e with f in [0.5, 1): mx < 2^e
@@ -522,16 +558,24 @@ __global__ void k_digits(PJ_ARGS)
     }
 }
 
-__global__ void k_qsum(PJ_ARGS)
+// Qsum_j = sum_p Q_pj: integer additions, exact in any order, so the K positions are split
+// over kRG thread rows as in k_qexp.
+__global__ void __launch_bounds__(32 * kRG) k_qsum(PJ_ARGS)
 {
     unsigned lb;
     const PrepJob& J = job_of(jobs, prefix, E, lb);
     const int d = J.d, kpad = J.kpad;
-    const int j = lb * blockDim.x + threadIdx.x;
-    if (j >= d) return;
+    const int j = (int)lb * 32 + threadIdx.x;
+    __shared__ long long part[kRG][32];
     long long s = 0;
+    if (j < d) {
 #pragma unroll 8
-    for (int p = 0; p < kpad; ++p) s += J.Q[(size_t)p * d + j];
+        for (int p = threadIdx.y; p < kpad; p += kRG) s += J.Q[(size_t)p * d + j];
+    }
+    part[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y != 0 || j >= d) return;
+    for (int g = 1; g < kRG; ++g) s += part[g][threadIdx.x];
     J.Qsum[j] = s;
 }
 
@@ -641,6 +685,7 @@ const uint64_t* binom_table()
 // Block counts of the launches of one job (0: the job has no work in that launch).
 struct JobBlocks {
     static unsigned colmean(const PrepJob& j) { return (unsigned)ceil_div(j.d, 128); }
+    static unsigned cols32(const PrepJob& j) { return (unsigned)ceil_div(j.d, 32); }
     static unsigned center(const PrepJob& j) { return (unsigned)(((size_t)j.n * j.d + 255) / 256); }
     static unsigned cov(const PrepJob& j) { return (unsigned)(ceil_div(j.d, 32) * ceil_div(j.d, 8)); }
     static unsigned one(const PrepJob&) { return 1u; }
@@ -743,9 +788,9 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         add_launch([p](const PrepJob& j) { return JobBlocks::fwd_trailing(j, p); });
     }
     add_launch(JobBlocks::center);  // Zc copy
-    add_launch(JobBlocks::colmean); // qexp
+    add_launch(JobBlocks::cols32);  // qexp
     add_launch(JobBlocks::derive);
-    add_launch(JobBlocks::colmean); // qsum
+    add_launch(JobBlocks::cols32);  // qsum
     add_launch(JobBlocks::digits);
     add_launch(JobBlocks::band);
     const size_t pref_off = bytes;
@@ -820,11 +865,11 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         PREP_CHECK(cudaStreamWaitEvent(s, evs[(size_t)max_panels + 1], 0));
         if (unsigned g = total(li)) k_copy_zc<<<g, 256, 0, s>>>(dj, P(li), E);
         ++li;
-        if (unsigned g = total(li)) k_qexp<<<g, 128, 0, s>>>(dj, P(li), E);
+        if (unsigned g = total(li)) k_qexp<<<g, dim3(32, kRG), 0, s>>>(dj, P(li), E);
         ++li;
         if (unsigned g = total(li)) k_derive<<<g, 256, 0, s>>>(dj, P(li), E);
         ++li;
-        if (unsigned g = total(li)) k_qsum<<<g, 128, 0, s>>>(dj, P(li), E);
+        if (unsigned g = total(li)) k_qsum<<<g, dim3(32, kRG), 0, s>>>(dj, P(li), E);
         ++li;
         if (unsigned g = total(li)) k_digits<<<g, 256, 0, s>>>(dj, P(li), E);
         ++li;
@@ -847,7 +892,7 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
     for (int e = 0; e < E; ++e) {
         frr_ctx* c = ctxs[e];
         if (h_status[(size_t)e] != 0) {
-            st_out[e] = FRR_E_DEGENERATE;
+            st_out[e] = (h_status[(size_t)e] & kStatusTimeout) ? FRR_E_TIMEOUT : FRR_E_DEGENERATE;
             continue;
         }
         c->band32 = band_from_eps(h_eps[(size_t)e].data(), c->c_M, c->d);

@@ -83,11 +83,12 @@ def test_whitened_covariates_bit_exact(n, d, whiten):
     assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
 
 
-@pytest.mark.parametrize("case", ["wide_scales", "zero_column", "tiny_and_huge"])
+@pytest.mark.parametrize("case", ["wide_scales", "zero_column", "tiny_and_huge", "all_tiny"])
 def test_whitened_covariates_bit_exact_extreme_magnitudes(case):
     """Bit patterns (signed zeros included) at magnitudes that reach the divisions' safe-range
-    edges: columns scaled by powers of two far from 1, and an exactly constant column whose
-    whitened entries are exact zeros."""
+    edges: columns scaled by powers of two far from 1, an exactly constant column whose
+    whitened entries are exact zeros, and covariates so small (2^-500) that the covariances
+    (~2^-1000) and pivots (~2^-500) fall outside the fast division's exponent range."""
     n, d = 90, 40
     X = ar1_covariates(n, d, 77, 0.4)
     if case == "wide_scales":
@@ -95,9 +96,11 @@ def test_whitened_covariates_bit_exact_extreme_magnitudes(case):
     elif case == "zero_column":
         X[:, 3] = 2.5
         X[:, 17] = 0.0
-    else:
+    elif case == "tiny_and_huge":
         X[:, : d // 2] *= 2.0 ** -300
         X[:, d // 2:] *= 2.0 ** 300
+    else:
+        X = X * 2.0 ** -500
     with _ctx(X, n // 2, whiten="ridge") as ctx:
         got = frr.frr_whitened(ctx)
     want, *_ = O.prep(X, "ridge", 0.1)
