@@ -223,15 +223,19 @@ frr_status check_init_args(const double* X, int64_t n, int64_t d, int64_t n1, co
     if (o.whiten != FRR_CHOL && o.whiten != FRR_RIDGE && o.whiten != FRR_DIAG) return FRR_E_ARG;
     if (o.whiten == FRR_RIDGE && !(o.ridge > 0.0 && isfinite(o.ridge))) return FRR_E_ARG;
     if (!(o.band_safety >= 1.0 && isfinite(o.band_safety))) return FRR_E_ARG;
+    if (scan_x && !all_finite(X, n * d)) return FRR_E_ARG;
+    if (o.whiten == FRR_CHOL && d >= n - 1) return FRR_E_DEGENERATE;
+    return FRR_OK;
+}
+
+bool all_finite(const double* X, int64_t count)
+{
     // non-finite entries have an all-ones exponent field; branch-free so that it vectorises
     const uint64_t* bits = reinterpret_cast<const uint64_t*>(X);
     const uint64_t em = 0x7ff0000000000000ull;
     uint64_t bad = 0;
-    if (scan_x)
-        for (int64_t k = 0; k < n * d; ++k) bad |= (uint64_t)((bits[k] & em) == em);
-    if (bad) return FRR_E_ARG;
-    if (o.whiten == FRR_CHOL && d >= n - 1) return FRR_E_DEGENERATE;
-    return FRR_OK;
+    for (int64_t k = 0; k < count; ++k) bad |= (uint64_t)((bits[k] & em) == em);
+    return bad == 0;
 }
 
 // A context for an (n, d, n1) experiment with checked options: streams, events and the fixed
@@ -350,14 +354,34 @@ frr_status frr_init(frr_ctx** out, const double* X, int64_t n, int64_t d, int64_
     frr_opts o;
     frr_default_opts(&o);
     if (opts) o = *opts;
-    FRR_TRY(check_init_args(X, n, d, n1, o, true));
+    // The scan of X for non-finite entries runs on the host while the device prepares (a
+    // non-finite X is still reported as FRR_E_ARG, before any other error, GPU or not).
+    {
+        const frr_status c = check_init_args(X, n, d, n1, o, false);
+        if (c == FRR_E_DEGENERATE) return check_init_args(X, n, d, n1, o, true);
+        if (c != FRR_OK) return c;
+    }
     const auto t0 = std::chrono::steady_clock::now();
     frr_ctx* ctx = nullptr;
-    FRR_TRY(ctx_create(&ctx, n, d, n1, o, true));
-    const frr_status s = prep_run(ctx, X);
-    if (s != FRR_OK) {
+    {
+        const frr_status c = ctx_create(&ctx, n, d, n1, o, true);
+        if (c != FRR_OK) return all_finite(X, n * d) ? c : FRR_E_ARG;
+    }
+    struct Scan {
+        const double* X;
+        int64_t count;
+        bool finite;
+        static void run(void* a)
+        {
+            Scan* sc = static_cast<Scan*>(a);
+            sc->finite = all_finite(sc->X, sc->count);
+        }
+    } scan{X, n * d, true};
+    const frr_status s = prep_run(ctx, X, &Scan::run, &scan);
+    if (s != FRR_OK || !scan.finite) {
         release(ctx);
-        return s;
+        // a failed preparation may have returned before running the scan
+        return (scan.finite && all_finite(X, n * d)) ? s : FRR_E_ARG;
     }
     ctx->stats.ms_init = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = ctx;

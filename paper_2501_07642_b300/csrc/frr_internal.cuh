@@ -172,18 +172,21 @@ frr_status copy_out(frr_ctx* ctx, void* dst_any, const void* src_dev, size_t byt
 // kernel families (defined in their own translation units)
 // scan_x: also reject non-finite entries of X (else the caller checks them, e.g. stage_finite)
 frr_status check_init_args(const double* X, int64_t n, int64_t d, int64_t n1, const frr_opts& o, bool scan_x);
+bool all_finite(const double* X, int64_t count);
 frr_status stage_finite(const double* X, int64_t count, double* dst);
 // pinned host blocks pooled by the library (size classes: powers of two up to 16 MiB, then multiples of 16 MiB)
 void* pinned_get(size_t bytes, size_t* cap_out);
 void pinned_put(void* p, size_t cap);
 frr_status ctx_create(frr_ctx** out, int64_t n, int64_t d, int64_t n1, const frr_opts& o, bool with_aux);
 void ctx_release(frr_ctx* ctx);
-frr_status prep_run(frr_ctx* ctx, const double* X_host);
+// host_work(arg), when given, runs on the host while the device prepares (after every copy
+// and launch is enqueued, before the preparation's single synchronisation)
+frr_status prep_run(frr_ctx* ctx, const double* X_host, void (*host_work)(void*) = nullptr, void* arg = nullptr);
 // prepares E contexts (created, arrays allocated) together on streams s and aux; st_out[e]
-// receives each one's status (FRR_E_DEGENERATE for a failed pivot); the return value is a
-// CUDA failure common to all, else FRR_OK
+// receives each one's status (FRR_E_DEGENERATE for a failed pivot, FRR_E_TIMEOUT for an
+// expired bounded wait); the return value is a CUDA failure common to all, else FRR_OK
 frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int E, cudaStream_t s, cudaStream_t aux,
-                          frr_status* st_out);
+                          frr_status* st_out, void (*host_work)(void*) = nullptr, void* arg = nullptr);
 frr_status balance_f32_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
 frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
 frr_status balance_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
