@@ -254,7 +254,8 @@ typedef struct {
  * opts->precision = FRR_SPLIT_BF16 the balance of every draw of every experiment is
  * evaluated by one persistent tensor-core launch per class of n (Philox blocks per lane),
  * each over all experiments of its class (shapes may differ), the launches replayed as one
- * CUDA graph; opts->autotune = 1 times the kernel configurations of each class first.
+ * CUDA graph; opts->autotune = 1 first times the kernel configurations of each class
+ * not yet timed in this process (the choices are kept process-wide).
  * Selection, recheck and tests follow per experiment. Results equal those of frr_init +
  * frr_select (+ frr_randtest) per experiment. opts: NULL for defaults (its whiten and ridge
  * are ignored; each experiment carries its own). Returns FRR_OK if every experiment

@@ -416,6 +416,12 @@ void remember_cfg(int device, int kb, int nch, bool multi, int cfg)
     g_tuned[{device, kb, nch, multi ? 1 : 0}] = cfg;
 }
 
+bool tuned_already(int device, int kb, int nch, bool multi)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    return g_tuned.count({device, kb, nch, multi ? 1 : 0}) != 0;
+}
+
 frr_status launch_cfg(int cfg, frr_ctx* ctx, cudaStream_t stream, int num_sms, const TcExp& one, const TcExp* table,
                       const unsigned long long* prefix, int E, unsigned long long tiles, int* err)
 {
@@ -515,6 +521,8 @@ frr_status balance_tc_batch_tune(frr_ctx* owner, cudaStream_t stream, const TcEx
                                  int nchmax, int* err)
 {
     if (tiles == 0) return FRR_OK;
+    // a class is timed once per process (frr_autotune re-times a context's class on request)
+    if (tuned_already(owner->device, kbmax, nchmax, true)) return FRR_OK;
     TcExp unused{};
     int best = -1;
     float best_ms = INFINITY;

@@ -49,9 +49,16 @@ constexpr int kStreams = 8;
 template <typename F>
 void run_workers(int nw, F&& f)
 {
+    // the workers use the calling thread's device (a new thread starts on device 0)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
     std::vector<std::thread> th;
     th.reserve((size_t)nw);
-    for (int w = 1; w < nw; ++w) th.emplace_back(f, w);
+    for (int w = 1; w < nw; ++w)
+        th.emplace_back([&f, dev, w] {
+            cudaSetDevice(dev);
+            f(w);
+        });
     f(0);
     for (auto& t : th) t.join();
 }
@@ -379,6 +386,12 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             frr_status s = stream_begin(c, x.seed, x.q, x.threshold, x.B);
             c->st.defer_count = true;
             c->st.timing = false;  // per-experiment phase times are not reported by the batch
+            if (s == FRR_OK) {
+                // the context's pinned block, sized once before anything is in flight on its
+                // (shared) stream: growing it later would wait for the stream
+                const size_t need = stream_end_pinned_bound(c, x.cap) + (x.Y ? (size_t)std::max<int64_t>(x.T, 0) * 16 + 16 : 0);
+                if (need <= (size_t(1) << 20)) s = ensure_host_pinned(c, need);
+            }
             if (s == FRR_OK) s = stream_chunk_precomputed(c, x.first_draw, x.B, mhat + off[k]);
             size_t extra = 0;
             if (s == FRR_OK && x.Y != nullptr) {

@@ -214,6 +214,10 @@ frr_status stream_end_finish(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, 
 // index; q mode: exactly K of them), and the first pinned byte free for the caller
 const uint64_t* stream_end_keys_dev(const frr_ctx* ctx, const uint64_t* keys_out);
 size_t stream_end_pinned_used(const frr_ctx* ctx);
+// after stream_begin: an upper bound of the pinned bytes stream_end_enqueue takes for its own
+// use, when the stream is one deferred chunk into a fresh context (so that the caller can
+// reserve the block before anything is in flight: growing it later synchronises the stream)
+size_t stream_end_pinned_bound(const frr_ctx* ctx, int64_t cap);
 frr_status stream_chunk_precomputed(frr_ctx* ctx, uint64_t first, uint64_t B, const float* Mhat_dev);
 // the test's kernels on ctx->stream for K checked keys (host, or device when keys_on_device; obs = index of the
 // observed assignment) and checked Y (n), tau (T) (host or device); the results stay on the

@@ -888,6 +888,17 @@ const uint64_t* stream_end_keys_dev(const frr_ctx* ctx, const uint64_t* keys_out
 
 size_t stream_end_pinned_used(const frr_ctx* ctx) { return ctx->st.end_pinned; }
 
+size_t stream_end_pinned_bound(const frr_ctx* ctx, int64_t cap)
+{
+    // the staged outputs hold min(cap, retained) entries of 16 bytes; a deferred q-mode
+    // stream retains at most its buffer's capacity, 4 K + 16384 entries grown by a quarter
+    // (ensure_device)
+    const StreamState& st = ctx->st;
+    int64_t rb = (int64_t)st.total;
+    if (st.q_mode) rb = std::min<int64_t>(rb, (4 * st.K + 16384) + (4 * st.K + 16384) / 4 + 1);
+    return 256 + (size_t)std::max<int64_t>(0, std::min<int64_t>(cap, rb)) * 16;
+}
+
 frr_status stream_end_finish(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out)
 {
     StreamState& st = ctx->st;
