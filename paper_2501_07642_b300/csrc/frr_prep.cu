@@ -384,9 +384,32 @@ __global__ void __launch_bounds__(kP * kPW) k_chol_below(PJ_ARGS, int p)
     if (r < d && w < pw) A[(size_t)r * d + k0 + w] = t;
 }
 
+// Look-ahead part of the trailing update after panel p: the diagonal block of panel p + 1
+// (rows and columns [k0 + pw, k0 + pw + pw1)) receives A_ij -= L_ik L_jk for k in panel p
+// (ascending), the operations of k_chol_trailing's tile (0, 0), so that the next diagonal
+// block can be factored while the rest of the trailing update runs. One block (one warp) per
+// row i of the tile, lane = column j <= i.
+__global__ void __launch_bounds__(32) k_chol_lookahead(PJ_ARGS, int p)
+{
+    unsigned lb;
+    const PrepJob& J = job_of(jobs, prefix, E, lb);
+    const int d = J.d, k0 = kP * p;
+    const int pw = (d - k0) < kP ? (d - k0) : kP;
+    const int r0 = k0 + pw;
+    double* __restrict__ A = J.Lm;
+    const int i = r0 + (int)lb, j = r0 + (int)threadIdx.x;
+    if (j > i) return;
+    const double* Li = A + (size_t)i * d + k0;
+    const double* Lj = A + (size_t)j * d + k0;
+    double v = A[(size_t)i * d + j];
+    for (int kk = 0; kk < pw; ++kk) v = __fma_rn(-Li[kk], Lj[kk], v);
+    A[(size_t)i * d + j] = v;
+}
+
 // Trailing update after panel p: A_ij -= L_ik L_jk for k in the panel (ascending), for
-// k0 + pw <= j <= i < d. 32 x 32 tiles, lower-triangle tiles only: local block b is tile
-// (ti, tj) with b = ti (ti + 1) / 2 + tj, tj <= ti.
+// k0 + pw <= j <= i < d. 32 x 32 tiles, lower-triangle tiles only: tile (ti, tj) has index
+// b = ti (ti + 1) / 2 + tj, tj <= ti, and local block lb covers tile b = lb + 1 (tile 0, the
+// next panel's diagonal block, is k_chol_lookahead's).
 __global__ void __launch_bounds__(256) k_chol_trailing(PJ_ARGS, int p)
 {
     unsigned lb;
@@ -394,10 +417,11 @@ __global__ void __launch_bounds__(256) k_chol_trailing(PJ_ARGS, int p)
     const int d = J.d, k0 = kP * p;
     const int pw = (d - k0) < kP ? (d - k0) : kP;
     double* __restrict__ A = J.Lm;
-    int ti = (int)((sqrtf(8.0f * (float)lb + 1.0f) - 1.0f) * 0.5f);
-    while ((ti + 1) * (ti + 2) / 2 <= (int)lb) ++ti;
-    while (ti * (ti + 1) / 2 > (int)lb) --ti;
-    const int tj = (int)lb - ti * (ti + 1) / 2;
+    const unsigned b = lb + 1;
+    int ti = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= (int)b) ++ti;
+    while (ti * (ti + 1) / 2 > (int)b) --ti;
+    const int tj = (int)b - ti * (ti + 1) / 2;
     __shared__ double Li[32][kP + 1], Lj[32][kP + 1];
     const int base = k0 + pw;
     const int i0 = base + 32 * ti, j0 = base + 32 * tj;
@@ -701,13 +725,20 @@ struct JobBlocks {
         const int pw = std::min(kP, j.d - k0), below = j.d - k0 - pw;
         return below > 0 ? (unsigned)ceil_div(below, 32) : 0u;
     }
+    static unsigned chol_lookahead(const PrepJob& j, int p)
+    {
+        const int k0 = kP * p;
+        if (j.whiten == FRR_DIAG || k0 >= j.d) return 0u;
+        const int pw = std::min(kP, j.d - k0), below = j.d - k0 - pw;
+        return (unsigned)std::max(0, std::min(kP, below));
+    }
     static unsigned chol_trailing(const PrepJob& j, int p)
     {
         const int k0 = kP * p;
         if (j.whiten == FRR_DIAG || k0 >= j.d) return 0u;
         const int pw = std::min(kP, j.d - k0), below = j.d - k0 - pw;
         const unsigned t = below > 0 ? (unsigned)ceil_div(below, 32) : 0u;
-        return t * (t + 1) / 2;
+        return t > 0 ? t * (t + 1) / 2 - 1 : 0u;  // every tile but the look-ahead one
     }
     static unsigned fwd_panel(const PrepJob& j, int p) { return kP * p < j.d ? (unsigned)ceil_div(j.n, 32) : 0u; }
     static unsigned fwd_trailing(const PrepJob& j, int p)
@@ -786,6 +817,7 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         add_launch([p](const PrepJob& j) { return JobBlocks::fwd_panel(j, p); });
         add_launch([p](const PrepJob& j) { return JobBlocks::chol_trailing(j, p); });
         add_launch([p](const PrepJob& j) { return JobBlocks::fwd_trailing(j, p); });
+        add_launch([p](const PrepJob& j) { return JobBlocks::chol_lookahead(j, p); });
     }
     add_launch(JobBlocks::center);  // Zc copy
     add_launch(JobBlocks::cols32);  // qexp
@@ -798,6 +830,7 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
 
     frr_status rc = FRR_OK;
     std::vector<cudaEvent_t> evs;
+    cudaStream_t ts = nullptr;  // the Cholesky's trailing updates
     std::vector<int> h_status((size_t)E, 0);
     std::vector<std::vector<double>> h_eps((size_t)E);
     auto fail = [&](cudaError_t e) {
@@ -845,24 +878,37 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         // Both factorisations are chains of latency-bound panels. Step p of the forward
         // substitution needs only column panel p of L, which is final once Cholesky panel
         // p is done (later trailing updates touch columns to its right), so it runs on the
-        // second stream, one panel behind: the two chains overlap.
-        evs.assign((size_t)max_panels + 2, nullptr);
+        // second stream, one panel behind: the two chains overlap. Within the Cholesky, the
+        // next panel's diagonal block gets panel p's update first (k_chol_lookahead) so that
+        // it can be factored while the rest of the trailing update runs on a third stream;
+        // the rows below panel p + 1 wait for that rest.
+        const size_t mp = (size_t)max_panels;
+        evs.assign(2 * mp + 3, nullptr);  // [p]: rows below panel p final; [mp + p]: trailing rest p
         for (auto& ev : evs) PREP_CHECK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        PREP_CHECK(cudaEventRecord(evs[(size_t)max_panels], s));
-        PREP_CHECK(cudaStreamWaitEvent(aux, evs[(size_t)max_panels], 0));
+        PREP_CHECK(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
+        PREP_CHECK(cudaEventRecord(evs[2 * mp], s));
+        PREP_CHECK(cudaStreamWaitEvent(aux, evs[2 * mp], 0));
+        PREP_CHECK(cudaStreamWaitEvent(ts, evs[2 * mp], 0));
         for (int p = 0; p < max_panels; ++p) {
-            const size_t ld = li, lp = li + 1, lf = li + 2, lt = li + 3, lft = li + 4;
-            li += 5;
+            const size_t ld = li, lp = li + 1, lf = li + 2, lt = li + 3, lft = li + 4, la = li + 5;
+            li += 6;
+            const size_t pp = (size_t)p;
             if (unsigned g = total(ld)) k_chol_diag<<<g, kP * kPW, 0, s>>>(dj, P(ld), E, p);
+            if (p > 0) PREP_CHECK(cudaStreamWaitEvent(s, evs[mp + pp - 1], 0));
             if (unsigned g = total(lp)) k_chol_below<<<g, kP * kPW, 0, s>>>(dj, P(lp), E, p);
-            PREP_CHECK(cudaEventRecord(evs[(size_t)p], s));
-            PREP_CHECK(cudaStreamWaitEvent(aux, evs[(size_t)p], 0));
+            PREP_CHECK(cudaEventRecord(evs[pp], s));
+            PREP_CHECK(cudaStreamWaitEvent(aux, evs[pp], 0));
+            PREP_CHECK(cudaStreamWaitEvent(ts, evs[pp], 0));
             if (unsigned g = total(lf)) k_fwd_panel<<<g, kP * kPW, 0, aux>>>(dj, P(lf), E, p);
-            if (unsigned g = total(lt)) k_chol_trailing<<<g, 256, 0, s>>>(dj, P(lt), E, p);
+            if (unsigned g = total(la)) k_chol_lookahead<<<g, 32, 0, s>>>(dj, P(la), E, p);
+            if (unsigned g = total(lt)) k_chol_trailing<<<g, 256, 0, ts>>>(dj, P(lt), E, p);
+            PREP_CHECK(cudaEventRecord(evs[mp + pp], ts));
             if (unsigned g = total(lft)) k_fwd_trailing<<<g, 256, 0, aux>>>(dj, P(lft), E, p);
         }
-        PREP_CHECK(cudaEventRecord(evs[(size_t)max_panels + 1], aux));
-        PREP_CHECK(cudaStreamWaitEvent(s, evs[(size_t)max_panels + 1], 0));
+        PREP_CHECK(cudaEventRecord(evs[2 * mp + 1], aux));
+        PREP_CHECK(cudaStreamWaitEvent(s, evs[2 * mp + 1], 0));
+        PREP_CHECK(cudaEventRecord(evs[2 * mp + 2], ts));
+        PREP_CHECK(cudaStreamWaitEvent(s, evs[2 * mp + 2], 0));
         if (unsigned g = total(li)) k_copy_zc<<<g, 256, 0, s>>>(dj, P(li), E);
         ++li;
         if (unsigned g = total(li)) k_qexp<<<g, dim3(32, kRG), 0, s>>>(dj, P(li), E);
@@ -905,6 +951,13 @@ cleanup:
 #undef PREP_CHECK
     for (cudaEvent_t ev : evs)
         if (ev) cudaEventDestroy(ev);
+    if (ts) cudaStreamDestroy(ts);
+    // after a failure, work may still be in flight on the other streams
+    if (rc != FRR_OK) {
+        cudaStreamSynchronize(aux);
+        if (ts) cudaStreamSynchronize(ts);
+        cudaGetLastError();
+    }
     // stream-ordered release: no device-wide synchronisation
     if (base) cudaFreeAsync(base, s);
     if (rc != FRR_OK)
