@@ -401,8 +401,17 @@ __global__ void __launch_bounds__(32) k_chol_lookahead(PJ_ARGS, int p)
     if (j > i) return;
     const double* Li = A + (size_t)i * d + k0;
     const double* Lj = A + (size_t)j * d + k0;
+    // every operand is loaded before the chain of dependent FMAs starts
+    double li[kP], lj[kP];
+#pragma unroll
+    for (int kk = 0; kk < kP; ++kk) {
+        li[kk] = kk < pw ? Li[kk] : 0.0;
+        lj[kk] = kk < pw ? Lj[kk] : 0.0;
+    }
     double v = A[(size_t)i * d + j];
-    for (int kk = 0; kk < pw; ++kk) v = __fma_rn(-Li[kk], Lj[kk], v);
+#pragma unroll
+    for (int kk = 0; kk < kP; ++kk)
+        if (kk < pw) v = __fma_rn(-li[kk], lj[kk], v);
     A[(size_t)i * d + j] = v;
 }
 
@@ -882,33 +891,33 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         // next panel's diagonal block gets panel p's update first (k_chol_lookahead) so that
         // it can be factored while the rest of the trailing update runs on a third stream;
         // the rows below panel p + 1 wait for that rest.
-        const size_t mp = (size_t)max_panels;
-        evs.assign(2 * mp + 3, nullptr);  // [p]: rows below panel p final; [mp + p]: trailing rest p
+        // Three events serve every dependency: each wait is enqueued right after its record,
+        // and a wait already enqueued is not affected by a later record of the same event.
+        evs.assign(3, nullptr);  // [0]: rows below panel p final; [1]: trailing rest p done; [2]: fork / join
         for (auto& ev : evs) PREP_CHECK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         PREP_CHECK(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
-        PREP_CHECK(cudaEventRecord(evs[2 * mp], s));
-        PREP_CHECK(cudaStreamWaitEvent(aux, evs[2 * mp], 0));
-        PREP_CHECK(cudaStreamWaitEvent(ts, evs[2 * mp], 0));
+        PREP_CHECK(cudaEventRecord(evs[2], s));
+        PREP_CHECK(cudaStreamWaitEvent(aux, evs[2], 0));
+        PREP_CHECK(cudaStreamWaitEvent(ts, evs[2], 0));
         for (int p = 0; p < max_panels; ++p) {
             const size_t ld = li, lp = li + 1, lf = li + 2, lt = li + 3, lft = li + 4, la = li + 5;
             li += 6;
-            const size_t pp = (size_t)p;
             if (unsigned g = total(ld)) k_chol_diag<<<g, kP * kPW, 0, s>>>(dj, P(ld), E, p);
-            if (p > 0) PREP_CHECK(cudaStreamWaitEvent(s, evs[mp + pp - 1], 0));
+            if (p > 0) PREP_CHECK(cudaStreamWaitEvent(s, evs[1], 0));  // trailing rest p - 1
             if (unsigned g = total(lp)) k_chol_below<<<g, kP * kPW, 0, s>>>(dj, P(lp), E, p);
-            PREP_CHECK(cudaEventRecord(evs[pp], s));
-            PREP_CHECK(cudaStreamWaitEvent(aux, evs[pp], 0));
-            PREP_CHECK(cudaStreamWaitEvent(ts, evs[pp], 0));
+            PREP_CHECK(cudaEventRecord(evs[0], s));
+            PREP_CHECK(cudaStreamWaitEvent(aux, evs[0], 0));
+            PREP_CHECK(cudaStreamWaitEvent(ts, evs[0], 0));
             if (unsigned g = total(lf)) k_fwd_panel<<<g, kP * kPW, 0, aux>>>(dj, P(lf), E, p);
             if (unsigned g = total(la)) k_chol_lookahead<<<g, 32, 0, s>>>(dj, P(la), E, p);
             if (unsigned g = total(lt)) k_chol_trailing<<<g, 256, 0, ts>>>(dj, P(lt), E, p);
-            PREP_CHECK(cudaEventRecord(evs[mp + pp], ts));
+            PREP_CHECK(cudaEventRecord(evs[1], ts));
             if (unsigned g = total(lft)) k_fwd_trailing<<<g, 256, 0, aux>>>(dj, P(lft), E, p);
         }
-        PREP_CHECK(cudaEventRecord(evs[2 * mp + 1], aux));
-        PREP_CHECK(cudaStreamWaitEvent(s, evs[2 * mp + 1], 0));
-        PREP_CHECK(cudaEventRecord(evs[2 * mp + 2], ts));
-        PREP_CHECK(cudaStreamWaitEvent(s, evs[2 * mp + 2], 0));
+        PREP_CHECK(cudaEventRecord(evs[2], aux));
+        PREP_CHECK(cudaStreamWaitEvent(s, evs[2], 0));
+        PREP_CHECK(cudaEventRecord(evs[2], ts));
+        PREP_CHECK(cudaStreamWaitEvent(s, evs[2], 0));
         if (unsigned g = total(li)) k_copy_zc<<<g, 256, 0, s>>>(dj, P(li), E);
         ++li;
         if (unsigned g = total(li)) k_qexp<<<g, dim3(32, kRG), 0, s>>>(dj, P(li), E);
