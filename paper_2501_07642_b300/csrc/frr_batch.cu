@@ -39,10 +39,12 @@ using namespace frr;
 
 namespace {
 
-// host threads that check arguments and create contexts (the scan of X for non-finite values
-// is the larger part); the CUDA calls themselves are issued from one thread, since the driver
-// serialised calls from several (8 threads made a batch 5-15 % slower, 16 and 32 up to 45 %)
-constexpr int kWorkers = 4;
+// host threads that check arguments, copy the covariates into the pinned staging block (with
+// the scan for non-finite values: bound by host memory bandwidth) and create contexts; with the
+// 256-experiment workload (226 MB of covariates) 8 of them stage about 6 ms faster than 4. The
+// selection chains are enqueued from one thread: from several, the driver's calls contended
+// (4 threads were 40-60 % slower for that phase)
+constexpr int kWorkers = 8;
 // streams of the contexts: the selection and test chains of different experiments overlap
 constexpr int kStreams = 8;
 

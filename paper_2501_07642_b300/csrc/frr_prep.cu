@@ -65,31 +65,40 @@ __device__ __forceinline__ const PrepJob& job_of(PJ_ARGS, unsigned& local)
     return jobs[lo];
 }
 
-__global__ void k_colmean(PJ_ARGS)
+// Column means: one chain of FP64 additions per column in ascending i, as the definition.
+// The chain (64 cycles per dependent addition) sets the time, so its operands come from
+// shared memory: warps 1..7 copy tiles of kCmRows rows x 32 columns (double-buffered) while
+// warp 0, lane = column, adds the previous tile.
+constexpr int kCmRows = 64;
+
+__global__ void __launch_bounds__(256) k_colmean(PJ_ARGS)
 {
     unsigned lb;
     const PrepJob& J = job_of(jobs, prefix, E, lb);
     const int n = J.n, d = J.d;
-    const int j = lb * blockDim.x + threadIdx.x;
-    if (j >= d) return;
-    // ascending i, as the definition. The chain of dependent FP64 additions sets the time, so
-    // the loads of the next kU rows are issued before the additions of the current kU rows.
-    constexpr int kU = 16;
-    const double* x = J.X + j;
-    double s = 0.0, cur[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) cur[u] = (u < n) ? x[(size_t)u * d] : 0.0;
-    for (int i = 0; i < n; i += kU) {
-        double nxt[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) nxt[u] = (i + kU + u < n) ? x[(size_t)(i + kU + u) * d] : 0.0;
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-            if (i + u < n) s = __dadd_rn(s, cur[u]);
-#pragma unroll
-        for (int u = 0; u < kU; ++u) cur[u] = nxt[u];
+    const int j0 = (int)lb * 32;
+    __shared__ double tile[2][kCmRows][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ntiles = (n + kCmRows - 1) / kCmRows;
+    auto load = [&](int t, int buf) {
+        for (int r = w - 1; r < kCmRows; r += 7) {
+            const int i = t * kCmRows + r, j = j0 + lane;
+            tile[buf][r][lane] = (i < n && j < d) ? J.X[(size_t)i * d + j] : 0.0;
+        }
+    };
+    if (w > 0) load(0, 0);
+    __syncthreads();
+    double s = 0.0;
+    for (int t = 0; t < ntiles; ++t) {
+        if (w > 0) {
+            if (t + 1 < ntiles) load(t + 1, (t + 1) & 1);
+        } else {
+            const int rows = min(kCmRows, n - t * kCmRows);
+            for (int r = 0; r < rows; ++r) s = __dadd_rn(s, tile[t & 1][r][lane]);
+        }
+        __syncthreads();
     }
-    J.xbar[j] = __ddiv_rn(s, (double)n);
+    if (w == 0 && j0 + lane < d) J.xbar[j0 + lane] = __ddiv_rn(s, (double)n);
 }
 
 __global__ void k_center(PJ_ARGS)
@@ -717,7 +726,7 @@ const uint64_t* binom_table()
 
 // Block counts of the launches of one job (0: the job has no work in that launch).
 struct JobBlocks {
-    static unsigned colmean(const PrepJob& j) { return (unsigned)ceil_div(j.d, 128); }
+    static unsigned colmean(const PrepJob& j) { return (unsigned)ceil_div(j.d, 32); }
     static unsigned cols32(const PrepJob& j) { return (unsigned)ceil_div(j.d, 32); }
     static unsigned center(const PrepJob& j) { return (unsigned)(((size_t)j.n * j.d + 255) / 256); }
     static unsigned cov(const PrepJob& j) { return (unsigned)(ceil_div(j.d, 32) * ceil_div(j.d, 8)); }
@@ -873,7 +882,7 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         // blocks of launch li, and its prefix array on the device
         auto total = [&](size_t l) { return pref[pref_at[l] + (size_t)E]; };
         auto P = [&](size_t l) { return dp + pref_at[l]; };
-        if (unsigned g = total(li)) k_colmean<<<g, 128, 0, s>>>(dj, P(li), E);
+        if (unsigned g = total(li)) k_colmean<<<g, 256, 0, s>>>(dj, P(li), E);
         ++li;
         if (unsigned g = total(li)) k_center<<<g, 256, 0, s>>>(dj, P(li), E);
         ++li;
