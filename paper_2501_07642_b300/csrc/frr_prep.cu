@@ -673,7 +673,9 @@ __global__ void __launch_bounds__(256) k_band_cols(PJ_ARGS)
         const double z = Z[(size_t)u * d + j];
         s1 += z;
         s2 += z * z;
-        acc += fabs(pi * s1) + kBandLambda * sqrt(vf * s2) + fabs(z);
+        // the standard-deviation term in FP32 rounded upward (never below the FP64 value beyond
+        // that product's own rounding; FP32 square roots cost no FP64 instructions)
+        acc += fabs(pi * s1) + kBandLambda * (double)__fsqrt_ru(__double2float_ru(vf * s2)) + fabs(z);
         r32 += fabs(z - (double)(float)z);
         const double hi = (double)__bfloat162float(__double2bfloat16(z));
         const double lo = (double)__bfloat162float(__double2bfloat16(z - hi));
