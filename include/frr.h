@@ -246,7 +246,8 @@ typedef struct {
     int64_t experiments, draws, failed;
     double ms_init;            /* wall time of the preparation of all experiments */
     double ms_balance;         /* device time of the balance evaluation of all experiments */
-    double ms_select;          /* wall time of selection, recheck and tests */
+    double ms_select;          /* wall time after the preparation beyond ms_balance: selection, recheck
+                                  and tests (issued while the balance runs) */
 } frr_batch_stats;
 
 /* Runs E independent experiments (Sec. 2.1 batched processing). All experiments are

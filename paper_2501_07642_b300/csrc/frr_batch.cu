@@ -191,6 +191,13 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
     int* d_err = nullptr;
     float ms_balance = 0.f;
     frr_status rc = FRR_OK;
+    // the balance graph and what it uses, kept until the end of the batch (the selection is
+    // issued while the graph runs); bal_err: its error word, read once the selection is issued
+    cudaGraph_t bal_graph = nullptr;
+    cudaGraphExec_t bal_exec = nullptr;
+    std::vector<cudaEvent_t> bal_gev;
+    std::vector<cudaStream_t> bal_gs;
+    const int* bal_err = nullptr;
     if (!live.empty()) {
         std::vector<size_t> off(live.size() + 1, 0);
         for (size_t k = 0; k < live.size(); ++k) off[k + 1] = off[k] + ex[live[k]].B;
@@ -308,22 +315,21 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
                     ok = cudaGraphLaunch(exec, stream) == cudaSuccess;
                     cudaEventRecord(eb, stream);
                 }
-                int herr = 0;
-                if (rc == FRR_OK) {
-                    if (!ok || cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-                        cudaStreamSynchronize(stream) != cudaSuccess) {
-                        cudaGetLastError();
-                        rc = FRR_E_CUDA;
-                    } else if (herr != 0) {
-                        rc = FRR_E_TIMEOUT;
-                    }
+                if (rc == FRR_OK && !ok) {
+                    cudaGetLastError();
+                    rc = FRR_E_CUDA;
                 }
-                if (exec) cudaGraphExecDestroy(exec);
-                if (graph) cudaGraphDestroy(graph);
-                for (cudaEvent_t ev : gev)
-                    if (ev) cudaEventDestroy(ev);
-                for (cudaStream_t st : gs)
-                    if (st) cudaStreamDestroy(st);
+                if (rc == FRR_OK) {
+                    // The experiments' streams wait for the balance on the device, so that this
+                    // thread issues their selection chains while the graph runs.
+                    for (cudaStream_t w : ws)
+                        if (cudaStreamWaitEvent(w, eb, 0) != cudaSuccess) { cudaGetLastError(); rc = FRR_E_CUDA; }
+                    bal_err = d_err;
+                }
+                bal_exec = exec;
+                bal_graph = graph;
+                bal_gev = gev;
+                bal_gs = gs;
                 cudaGetLastError();
             }
             d_prefix = nullptr;  // parts of dbuf
@@ -341,9 +347,6 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             cudaEventRecord(eb, stream);
             if (cudaStreamSynchronize(stream) != cudaSuccess) { cudaGetLastError(); rc = FRR_E_CUDA; }
         }
-        cudaEventElapsedTime(&ms_balance, ea, eb);
-        cudaEventDestroy(ea);
-        cudaEventDestroy(eb);
         // Selection, recheck and tests, issued from this thread. q-mode experiments whose test
         // inputs are in host memory are pipelined: each one's whole chain is enqueued on its
         // context's stream without a read-back (q mode accepts exactly K draws, so the test
@@ -431,6 +434,16 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             }
             st_sel[k] = s;
         }
+        if (bal_err != nullptr && rc == FRR_OK) {
+            int herr = 0;
+            if (cudaMemcpyAsync(&herr, bal_err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+                cudaStreamSynchronize(stream) != cudaSuccess) {
+                cudaGetLastError();
+                rc = FRR_E_CUDA;
+            } else if (herr != 0) {
+                rc = FRR_E_TIMEOUT;  // the selection issued on its output is discarded
+            }
+        }
         for (size_t k = 0; k < live.size(); ++k) {
             if (rc != FRR_OK) { st_sel[k] = rc; continue; }
             if (!pend[k].piped) {
@@ -462,6 +475,16 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
             }
             st_sel[k] = s;
         }
+        if (cudaStreamSynchronize(stream) != cudaSuccess) cudaGetLastError();
+        if (cudaEventElapsedTime(&ms_balance, ea, eb) != cudaSuccess) { cudaGetLastError(); ms_balance = 0.f; }
+        cudaEventDestroy(ea);
+        cudaEventDestroy(eb);
+        if (bal_exec) cudaGraphExecDestroy(bal_exec);
+        if (bal_graph) cudaGraphDestroy(bal_graph);
+        for (cudaEvent_t ev : bal_gev)
+            if (ev) cudaEventDestroy(ev);
+        for (cudaStream_t st : bal_gs)
+            if (st) cudaStreamDestroy(st);
         for (size_t k = 0; k < live.size(); ++k) {
             note(live[k], st_sel[k]);
             draws += (int64_t)ex[live[k]].B;
@@ -484,7 +507,7 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
         stats->failed = failed;
         stats->ms_init = std::chrono::duration<double, std::milli>(t1 - t0).count();
         stats->ms_balance = ms_balance;
-        stats->ms_select = std::chrono::duration<double, std::milli>(t2 - t1).count() - ms_balance;
+        stats->ms_select = std::max(0.0, std::chrono::duration<double, std::milli>(t2 - t1).count() - ms_balance);
     }
     return first_err;
 }
