@@ -1,42 +1,67 @@
 """Builds libfrr.so (the CUDA library behind include/frr.h) in-tree for sm_103a.
 
 ``python -m paper_2501_07642_b300.build`` or ``build_library()``; nvcc
-cross-compiles without a GPU.
+cross-compiles without a GPU. Each translation unit is compiled on its own (in
+parallel, into ``_build/``) and the objects are linked into one shared library.
 """
 from __future__ import annotations
 
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 from pathlib import Path
 
 PKG = Path(__file__).resolve().parent
 ROOT = PKG.parent
 CSRC = PKG / "csrc"
+OBJ = PKG / "_build"
 LIB = PKG / "libfrr.so"
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr",
-         "-I", str(ROOT / "include")]
+CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+          "-I", str(ROOT / "include")]
 
 
 def sources() -> list[Path]:
     return sorted(CSRC.glob("*.cu"))
 
 
-def _stale() -> bool:
-    if not LIB.exists():
+def _headers() -> list[Path]:
+    return list(CSRC.glob("*.cuh")) + [ROOT / "include" / "frr.h", Path(__file__)]
+
+
+def _stale(target: Path, deps: list[Path]) -> bool:
+    if not target.exists():
         return True
-    t = LIB.stat().st_mtime
-    deps = list(CSRC.glob("*")) + [ROOT / "include" / "frr.h", Path(__file__)]
+    t = target.stat().st_mtime
     return any(p.stat().st_mtime > t for p in deps)
 
 
+def _compile(src: Path, verbose: bool) -> Path:
+    obj = OBJ / (src.stem + ".o")
+    if _stale(obj, [src, *_headers()]):
+        tmp = obj.with_suffix(f".{os.getpid()}.tmp.o")
+        cmd = [NVCC, *ARCH, *CFLAGS, "-c", str(src), "-o", str(tmp)]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, obj)
+    return obj
+
+
 def build_library(force: bool = False, verbose: bool = False) -> Path:
-    if not force and not _stale():
+    srcs = sources()
+    if not force and not _stale(LIB, [*srcs, *_headers()]):
         return LIB
+    OBJ.mkdir(exist_ok=True)
+    if force:
+        for o in OBJ.glob("*.o"):
+            o.unlink()
+    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     tmp = LIB.with_suffix(f".{os.getpid()}.tmp.so")
-    cmd = [NVCC, *ARCH, *FLAGS, *map(str, sources()), "-o", str(tmp)]
+    cmd = [NVCC, *ARCH, "-shared", *map(str, objs), "-o", str(tmp)]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)
