@@ -134,11 +134,12 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *sTmem;
-
+    // limit of every bounded wait (shortened only by the failure-path test, see frr_test_wait_expiry)
+    const unsigned long long wlim = one.wait_cycles ? one.wait_cycles : kWaitCycles;
 
     if (warp == 4) {
         // ------------------------------------------------------------ TMA --
-        if (lane == 0) {
+        if (lane == 0 && !one.skip_tma) {
             uint32_t bi = 0;
             bool ok = true;
             for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
@@ -150,7 +151,7 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
                         for (int part = 0; part < 2 && ok; ++part, ++bi) {
                             const int s = bi % SB;
                             const uint32_t ph = (bi / SB) & 1u;
-                            if (!(ok = wait_bar(&b_empty[s], ph ^ 1u, sAbort, err, 1))) break;
+                            if (!(ok = wait_bar(&b_empty[s], ph ^ 1u, sAbort, err, 1, wlim))) break;
                             mbar_arrive_expect_tx(&b_full[s], kBBytes);
                             tma_load_2d(sB + s * kBBytes, part ? &x->map_lo : &x->map_hi, &b_full[s], kb * kKBlock,
                                         c * kChunkN);
@@ -176,7 +177,7 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
                 const int nch = x->nchunks, nkb = x->nkb, dd = x->d;
                 for (int c = 0; c < nch && ok; ++c, ++g) {
                     const int buf = g & 1;
-                    if (!(ok = wait_bar(&acc_empty[buf], ((g >> 1) & 1u) ^ 1u, sAbort, err, 2))) break;
+                    if (!(ok = wait_bar(&acc_empty[buf], ((g >> 1) & 1u) ^ 1u, sAbort, err, 2, wlim))) break;
                     tc_fence_after();
                     const int rem = dd - c * kChunkN;
                     const int N = rem >= kChunkN ? kChunkN : ((rem + 15) / 16) * 16;
@@ -184,11 +185,11 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
                     const uint32_t dt = tmem_base + (uint32_t)(buf * kChunkN);
                     for (int kb = 0; kb < nkb && ok; ++kb, ++ai) {
                         const int sa = ai % kStagesA;
-                        if (!(ok = wait_bar(&a_full[sa], (ai / kStagesA) & 1u, sAbort, err, 3))) break;
+                        if (!(ok = wait_bar(&a_full[sa], (ai / kStagesA) & 1u, sAbort, err, 3, wlim))) break;
                         const uint64_t adesc = sdesc_sw128(smem_u32(sA + sa * kABytes));
                         for (int part = 0; part < 2; ++part, ++bi) {
                             const int sb = bi % SB;
-                            if (!(ok = wait_bar(&b_full[sb], (bi / SB) & 1u, sAbort, err, 4))) break;
+                            if (!(ok = wait_bar(&b_full[sb], (bi / SB) & 1u, sAbort, err, 4, wlim))) break;
                             tc_fence_after();
                             const uint64_t bdesc = sdesc_sw128(smem_u32(sB + sb * kBBytes));
 #pragma unroll
@@ -220,12 +221,12 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
             const TcExp* x = tile_job(&one, table, prefix, E, t, tl);
             const int nch = x->nchunks, nkb = x->nkb;
             const int bb = it & 1;
-            if (!(ok = wait_bar(&bits_full[bb], (it >> 1) & 1u, sAbort, err, 5))) break;
+            if (!(ok = wait_bar(&bits_full[bb], (it >> 1) & 1u, sAbort, err, 5, wlim))) break;
             const uint32_t* row = sBits + bb * kTileM * RS + r * RS;
             for (int c = 0; c < nch && ok; ++c)
                 for (int kb = 0; kb < nkb; ++kb, ++ai) {
                     const int s = ai % kStagesA;
-                    if (!(ok = wait_bar(&a_empty[s], ((ai / kStagesA) & 1u) ^ 1u, sAbort, err, 6))) break;
+                    if (!(ok = wait_bar(&a_empty[s], ((ai / kStagesA) & 1u) ^ 1u, sAbort, err, 6, wlim))) break;
                     unsigned char* dst = sA + s * kABytes + (r >> 3) * 1024 + (r & 7) * 128;
                     const uint32_t w2[2] = {row[2 * kb], row[2 * kb + 1]};
 #pragma unroll
@@ -250,7 +251,7 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
             uint64_t tl;
             const TcExp* x = tile_job(&one, table, prefix, E, t, tl);
             const int bb = it & 1;
-            if (!(ok = wait_bar(&bits_empty[bb], ((it >> 1) & 1u) ^ 1u, sAbort, err, 7))) break;
+            if (!(ok = wait_bar(&bits_empty[bb], ((it >> 1) & 1u) ^ 1u, sAbort, err, 7, wlim))) break;
             uint32_t* bits = sBits + bb * kTileM * RS;
             const int kbx = x->kb, nx = x->n, n1x = x->n1, ex = x->exact;
             const uint64_t sx = x->seed, fx = x->first, Bx = x->B;
@@ -291,7 +292,7 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
             float sumsq = 0.f;
             for (int c = 0; c < nch; ++c, ++g) {
                 const int buf = g & 1;
-                if (!(ok = wait_bar(&acc_full[buf], (g >> 1) & 1u, sAbort, err, 8))) break;
+                if (!(ok = wait_bar(&acc_full[buf], (g >> 1) & 1u, sAbort, err, 8, wlim))) break;
                 tc_fence_after();
                 const int rem = dd - c * kChunkN;
                 const int N = rem >= kChunkN ? kChunkN : rem;
@@ -487,6 +488,8 @@ frr_status tc_describe(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, 
     x->nkb = ctx->kused / kKBlock;
     x->nchunks = ceil_div(ctx->d, kChunkN);
     x->exact = exact ? 1 : 0;
+    x->skip_tma = 0;
+    x->wait_cycles = 0;
     return FRR_OK;
 }
 
@@ -590,4 +593,27 @@ extern "C" frr_status frr_autotune(frr_ctx* ctx, uint64_t B_probe, frr_tune_resu
     out->chosen = best_i;
     remember_cfg(ctx->device, ctx->kb, one.nchunks, false, best);
     return FRR_OK;
+}
+
+extern "C" frr_status frr_test_wait_expiry(frr_ctx* ctx, uint64_t wait_cycles)
+{
+    if (!ctx) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    if (ctx->opts.precision != FRR_SPLIT_BF16) return FRR_E_UNSUPPORTED;
+    if (wait_cycles < 10000) wait_cycles = 10000;
+    if (wait_cycles > kWaitCycles) wait_cycles = kWaitCycles;
+    // one tile of 128 draws per SM; the covariate tiles never arrive, so the first MMA wait
+    // expires, the CTA raises its abort flag and every other role returns through its own
+    // bounded wait; TMEM is released at the kernel's end as on every exit
+    const uint64_t B = (uint64_t)kTileM * (uint64_t)ctx->num_sms;
+    FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->Mhat), &ctx->Mhat_bytes, (size_t)B * sizeof(float)));
+    TcExp one;
+    FRR_TRY(tc_describe(ctx, 1, false, 0, B, ctx->Mhat, &one));
+    one.skip_tma = 1;
+    one.wait_cycles = wait_cycles;
+    const int cfg = chosen_cfg(ctx->device, ctx->kb, one.nchunks, false);
+    FRR_TRY(launch_cfg(cfg, ctx, ctx->stream, ctx->num_sms, one, nullptr, nullptr, 1, (B + kTileM - 1) / kTileM,
+                       ctx->dev_counters + 12));
+    FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return take_device_error(ctx);
 }

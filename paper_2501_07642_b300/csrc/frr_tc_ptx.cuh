@@ -136,15 +136,17 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
 }
 
 
-// Bounded wait. Returns false (and raises the CTA abort flag) on expiry or abort.
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err, int code)
+// Bounded wait: at most `limit` SM clock cycles. Returns false (and raises the CTA abort
+// flag) on expiry or abort.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err, int code,
+                                         unsigned long long limit = kWaitCycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = clock64();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             atomicCAS(err, 0, code);
             return false;
