@@ -43,6 +43,7 @@
 #ifndef FRR_H
 #define FRR_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -148,6 +149,16 @@ typedef struct {
  * M_hat is reused; no other state changes. FRR_E_UNSUPPORTED for an FP32 context. */
 frr_status frr_autotune(frr_ctx* ctx, uint64_t B_probe, frr_tune_result* out);
 
+/* Test of the failure path (the paper has no counterpart; for tests only). Runs one
+ * split-BF16 balance launch of this context (128 draws per SM) in which the producer of the
+ * covariate tiles issues nothing, so the first wait for a tile is never satisfied. Every
+ * bounded wait of that launch gives up after wait_cycles SM clock cycles (clamped to
+ * [1e4, 2^31]; 2^31, about one second, is the limit of every normal launch): the kernel
+ * records which wait expired, releases its tensor memory and returns, and the call returns
+ * FRR_E_TIMEOUT with the recorded error cleared and the context still usable. No other call
+ * is affected. FRR_E_UNSUPPORTED for an FP32 context. */
+frr_status frr_test_wait_expiry(frr_ctx* ctx, uint64_t wait_cycles);
+
 /* Accepted pool of draws [first_draw, first_draw + B) (Sec. 2.2, 2.3). Exactly one of
  * q (0 < q <= 1: keep the K = ceil(qB - 1e-9 qB) draws with the smallest
  * (M, draw index)) and threshold (>= 0: keep every draw with M <= threshold, T^2 units)
@@ -165,6 +176,49 @@ frr_status frr_select(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_t
 frr_status frr_stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold, uint64_t B_total);
 frr_status frr_stream_chunk(frr_ctx* ctx, uint64_t first_draw, uint64_t B_chunk);
 frr_status frr_stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out);
+
+/* ---- stream checkpoints (Sec. 2.1 key-only storage) -----------------------------------
+ * Between two frr_stream_chunk calls a stream is described by its parameters, its current
+ * cut on the approximate M and the retained (draw index, approximate M) pairs -- about K
+ * plus the draws inside the error band, 12 bytes each. frr_stream_save writes that state to
+ * a caller-owned host blob; frr_stream_load restores it into a context prepared from the
+ * same covariates with the same options (in this or another process), after which the
+ * remaining chunks and frr_stream_end give exactly the accepted set of the uninterrupted
+ * stream.
+ *
+ * Blob layout, version 1, little-endian: a 256-byte header -- bytes 0-7 "FRRSTRM\0",
+ * 8-11 version (uint32), 12-15 header size 256 (uint32), 16-39 n, d, n1 (int64), 40-47
+ * precision, whiten (int32), 48-63 ridge, band_safety (double), 64-87 the three error-band
+ * constants of the context (double), 88-111 seed, B_total, draws seen so far (uint64),
+ * 112-119 exact, q_mode (int32), 120-135 q, threshold (double), 136-151 K, retained count r
+ * (int64), 152-155 cut (float), 160-183 the draws / balance / selection statistics (int64,
+ * double, double), 184-247 zero, 248-255 FNV-1a 64-bit checksum of the whole blob with these
+ * 8 bytes taken as zero -- then r draw indices (uint64) and their r approximate M (float).
+ * The blob is 256 + 12 r bytes. */
+typedef struct {
+    int32_t version;
+    int64_t n, d, n1;
+    int32_t precision;
+    uint64_t seed, total, seen;  /* pool seed, B_total, draws streamed so far */
+    double q, threshold;         /* the one not used is NaN */
+    int64_t K;                   /* target accepted count (q mode), 0 in threshold mode */
+    int64_t retained;            /* retained (candidate) pairs stored in the blob */
+} frr_stream_info;
+
+/* Saves the running stream (after frr_stream_begin and any number of chunks). blob: host,
+ * cap bytes; *size_out receives the blob's size. blob == NULL or cap too small: nothing is
+ * written and FRR_E_CAPACITY is returned with *size_out set. FRR_E_STATE when no stream is
+ * running. The stream continues unchanged. */
+frr_status frr_stream_save(frr_ctx* ctx, void* blob, size_t cap, size_t* size_out);
+
+/* Replaces the context's stream state with a saved one (any running stream is dropped).
+ * FRR_E_ARG for a corrupted blob or one saved by a context of another shape, options or
+ * covariates (band constants differ); FRR_E_UNSUPPORTED for an unknown version. */
+frr_status frr_stream_load(frr_ctx* ctx, const void* blob, size_t size);
+
+/* Checks a blob (magic, version, size, checksum) without a context or GPU and describes it.
+ * FRR_E_ARG for a corrupted blob, FRR_E_UNSUPPORTED for an unknown version. */
+frr_status frr_stream_blob_info(const void* blob, size_t size, frr_stream_info* out);
 
 /* Regenerates the assignment of one key (Sec. 2.1 key-only storage).
  * w_out: host or device, n bytes, 1 = treated, in unit order. */
@@ -190,15 +244,19 @@ frr_status frr_recheck(frr_ctx* ctx, uint64_t seed, const uint64_t* draws, int64
  * cudaMalloc / cudaFree could synchronise the device and stall it, or an application
  * whose device memory belongs to another allocator (for example a framework's caching
  * pool with a fixed budget). draws (count entries) and M64_out (count doubles) must be
- * device memory owned by the caller; pool seeds only (FRR_EXACT_SEED gives
- * FRR_E_UNSUPPORTED). The kernels' scratch -- count * ceil(d / 128) partial sums -- lives
- * in one fixed device array of FRR_RECHECK_STATIC_SCRATCH doubles (1 MiB) compiled into
- * the library, which every GPU that loads the library holds until the process exits;
- * larger requests return FRR_E_CAPACITY and run nothing. The first call on a device looks
- * up that array's device address (set-up); make this first call before any stream
- * capture. Every call on a device shares the array: calls that overlap on the GPU (from
- * other host threads or other contexts on the same device) race, and the caller must
- * serialise them. Synchronous like the other entry points; allocates no device or host
+ * device memory of the context's GPU (or managed memory), owned by the caller and 8-byte
+ * aligned; anything else -- host memory, another GPU's memory -- returns FRR_E_ARG and runs
+ * nothing. Pool seeds only (FRR_EXACT_SEED gives FRR_E_UNSUPPORTED); count == 0 returns
+ * FRR_OK without touching the buffers. The kernels' scratch -- count * ceil(d / 128)
+ * partial sums -- lives in one fixed device array of FRR_RECHECK_STATIC_SCRATCH doubles
+ * (1 MiB) compiled into the library, which every GPU that loads the library holds until the
+ * process exits; larger requests return FRR_E_CAPACITY and run nothing. The first call on a
+ * device looks up that array's device address (set-up), and so does the first call after
+ * the device's primary context was destroyed and created again (cudaDeviceReset); make
+ * such a first call before any stream capture. Every call on a device shares the array:
+ * calls that overlap on the GPU (from other host threads or other contexts on the same
+ * device) race, and the caller must serialise them. The call waits for the context's
+ * stream before it returns, like the other entry points; it allocates no device or host
  * memory. */
 #define FRR_RECHECK_STATIC_SCRATCH 131072
 frr_status frr_recheck_static(frr_ctx* ctx, uint64_t seed, const uint64_t* draws, int64_t count, double* M64_out);

@@ -459,6 +459,26 @@ frr_status frr_stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int
     return stream_end(ctx, keys_out, M64_out, cap, K_out);
 }
 
+frr_status frr_stream_save(frr_ctx* ctx, void* blob, size_t cap, size_t* size_out)
+{
+    if (!ctx || !size_out) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    return stream_save(ctx, blob, cap, size_out);
+}
+
+frr_status frr_stream_load(frr_ctx* ctx, const void* blob, size_t size)
+{
+    if (!ctx || !blob) return FRR_E_ARG;
+    if (ctx->failed) return FRR_E_CUDA;
+    return stream_load(ctx, blob, size);
+}
+
+frr_status frr_stream_blob_info(const void* blob, size_t size, frr_stream_info* out)
+{
+    if (!blob || !out) return FRR_E_ARG;
+    return stream_blob_check(blob, size, out);
+}
+
 frr_status frr_select(frr_ctx* ctx, uint64_t seed, uint64_t first_draw, uint64_t B, double q, double threshold,
                       uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out)
 {

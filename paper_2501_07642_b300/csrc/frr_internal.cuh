@@ -205,6 +205,11 @@ frr_status recheck_sum_launch(frr_ctx* ctx, const double* part, int ncb, int64_t
 frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold, uint64_t total);
 frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B);
 frr_status stream_end(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, int64_t cap, int64_t* K_out);
+// checkpoint of a running stream between chunks (layout in include/frr.h, frr_stream_save)
+frr_status stream_save(frr_ctx* ctx, void* blob, size_t cap, size_t* size_out);
+frr_status stream_load(frr_ctx* ctx, const void* blob, size_t size);
+// checks a blob's magic, version, size and checksum; fills *info when given
+frr_status stream_blob_check(const void* blob, size_t size, frr_stream_info* info);
 // stream_end in two halves: the first enqueues the recheck, ordering, placement and read-back
 // copies (reserving extra_pinned bytes of pinned memory after its own for the caller); the
 // second synchronises the stream, reads the summary and writes the outputs

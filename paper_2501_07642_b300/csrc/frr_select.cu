@@ -1021,3 +1021,190 @@ frr_status recheck_launch_into(frr_ctx* ctx, uint64_t seed, const uint64_t* draw
 }
 
 }  // namespace frr
+
+// ------------------------------------------------------ stream checkpoints --
+// A stream between chunks is fully described by its parameters, the cut on the approximate
+// M and the retained set (draw index, approximate M); key-only storage (Sec. 2.1) keeps it
+// small. The blob is a 256-byte header followed by the retained indices (uint64) and their
+// approximate M (float), little-endian; its FNV-1a checksum covers everything else.
+namespace frr {
+namespace {
+
+constexpr char kBlobMagic[8] = {'F', 'R', 'R', 'S', 'T', 'R', 'M', '\0'};
+constexpr uint32_t kBlobVersion = 1;
+constexpr size_t kBlobHeader = 256;
+
+struct BlobHeader {               // 256 bytes
+    char magic[8];
+    uint32_t version, header_bytes;
+    int64_t n, d, n1;
+    int32_t precision, whiten;
+    double ridge, band_safety;
+    double band_lin, band_quad, band_rel;
+    uint64_t seed, total, seen;
+    int32_t exact, q_mode;
+    double q, threshold;
+    int64_t K, retained;
+    float cut;
+    uint32_t pad0;
+    int64_t stat_draws;
+    double stat_ms_balance, stat_ms_select;
+    unsigned char reserved[64];
+    uint64_t checksum;
+};
+static_assert(sizeof(BlobHeader) == kBlobHeader, "stream checkpoint header layout");
+static_assert(offsetof(BlobHeader, checksum) == 248, "stream checkpoint header layout");
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t bytes)
+{
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < bytes; ++i) {
+        h ^= c[i];
+        h *= 0x100000001B3ull;
+    }
+    return h;
+}
+
+uint64_t blob_checksum(const BlobHeader& h, const void* payload, size_t payload_bytes)
+{
+    BlobHeader z = h;
+    z.checksum = 0;
+    const uint64_t h0 = fnv1a(0xCBF29CE484222325ull, &z, sizeof(z));
+    return fnv1a(h0, payload, payload_bytes);
+}
+
+}  // namespace
+
+frr_status stream_blob_check(const void* blob, size_t size, frr_stream_info* info)
+{
+    if (!blob || size < kBlobHeader) return FRR_E_ARG;
+    BlobHeader h;
+    memcpy(&h, blob, sizeof(h));
+    if (memcmp(h.magic, kBlobMagic, sizeof(kBlobMagic)) != 0) return FRR_E_ARG;
+    if (h.version != kBlobVersion || h.header_bytes != kBlobHeader) return FRR_E_UNSUPPORTED;
+    if (h.retained < 0 || h.retained > (int64_t)((size - kBlobHeader) / 12) ||
+        size != kBlobHeader + (size_t)h.retained * 12)
+        return FRR_E_ARG;
+    if (blob_checksum(h, static_cast<const char*>(blob) + kBlobHeader, size - kBlobHeader) != h.checksum)
+        return FRR_E_ARG;
+    if (h.seen > h.total || h.n < 2 || h.d < 1 || h.n1 < 1 || h.n1 > h.n - 1) return FRR_E_ARG;
+    if (info) {
+        info->version = (int32_t)h.version;
+        info->n = h.n;
+        info->d = h.d;
+        info->n1 = h.n1;
+        info->precision = h.precision;
+        info->seed = h.seed;
+        info->total = h.total;
+        info->seen = h.seen;
+        info->q = h.q;
+        info->threshold = h.threshold;
+        info->K = h.K;
+        info->retained = h.retained;
+    }
+    return FRR_OK;
+}
+
+frr_status stream_save(frr_ctx* ctx, void* blob, size_t cap, size_t* size_out)
+{
+    StreamState& st = ctx->st;
+    if (!st.active || st.end_enqueued || st.retained < 0) return FRR_E_STATE;
+    const size_t size = kBlobHeader + (size_t)st.retained * 12;
+    *size_out = size;
+    if (!blob || cap < size) return FRR_E_CAPACITY;
+    BlobHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kBlobMagic, sizeof(kBlobMagic));
+    h.version = kBlobVersion;
+    h.header_bytes = kBlobHeader;
+    h.n = ctx->n;
+    h.d = ctx->d;
+    h.n1 = ctx->n1;
+    h.precision = ctx->opts.precision;
+    h.whiten = ctx->opts.whiten;
+    h.ridge = ctx->opts.ridge;
+    h.band_safety = ctx->opts.band_safety;
+    const BandConsts& b = band_of(ctx);
+    h.band_lin = b.lin;
+    h.band_quad = b.quad;
+    h.band_rel = b.rel;
+    h.seed = st.seed;
+    h.total = st.total;
+    h.seen = st.seen;
+    h.exact = st.exact ? 1 : 0;
+    h.q_mode = st.q_mode ? 1 : 0;
+    h.q = st.q;
+    h.threshold = st.threshold;
+    h.K = st.K;
+    h.retained = st.retained;
+    // the running cut lives on the device (each chunk's scan may tighten it)
+    SelState* sel = static_cast<SelState*>(ctx->sel);
+    float cut = st.cut;
+    FRR_TRY(copy_out(ctx, &cut, &sel->cut, sizeof(float)));
+    h.cut = cut;
+    h.stat_draws = ctx->stats.draws;
+    h.stat_ms_balance = ctx->stats.ms_balance;
+    h.stat_ms_select = ctx->stats.ms_select;
+    char* payload = static_cast<char*>(blob) + kBlobHeader;
+    const int cur = ctx->ret_cur;
+    if (st.retained > 0) {
+        FRR_TRY(copy_out(ctx, payload, ctx->ret_idx[cur], (size_t)st.retained * sizeof(uint64_t)));
+        FRR_TRY(copy_out(ctx, payload + (size_t)st.retained * sizeof(uint64_t), ctx->ret_m[cur],
+                         (size_t)st.retained * sizeof(float)));
+    }
+    h.checksum = blob_checksum(h, payload, size - kBlobHeader);
+    memcpy(blob, &h, sizeof(h));
+    return FRR_OK;
+}
+
+frr_status stream_load(frr_ctx* ctx, const void* blob, size_t size)
+{
+    FRR_TRY(stream_blob_check(blob, size, nullptr));
+    BlobHeader h;
+    memcpy(&h, blob, sizeof(h));
+    // the blob must come from a context that scores draws identically: same shape, options
+    // and (through the covariates) the same error-band constants
+    const BandConsts& b = band_of(ctx);
+    if (h.n != ctx->n || h.d != ctx->d || h.n1 != ctx->n1 || h.precision != ctx->opts.precision ||
+        h.whiten != ctx->opts.whiten || h.band_safety != ctx->opts.band_safety ||
+        (ctx->opts.whiten == FRR_RIDGE && h.ridge != ctx->opts.ridge) || h.band_lin != b.lin || h.band_quad != b.quad ||
+        h.band_rel != b.rel)
+        return FRR_E_ARG;
+    const bool exact = h.exact != 0;
+    if (exact && (ctx->n > kExactMaxN || h.total > binom_host((int)ctx->n, (int)ctx->n1))) return FRR_E_ARG;
+    FRR_TRY(stream_begin(ctx, h.seed, h.q_mode ? h.q : NAN, h.q_mode ? NAN : h.threshold, h.total));
+    StreamState& st = ctx->st;
+    if ((h.q_mode != 0) != st.q_mode || (st.q_mode && st.K != h.K)) {
+        st.active = false;
+        return FRR_E_ARG;
+    }
+    st.seen = h.seen;
+    st.cut = h.cut;
+    const char* payload = static_cast<const char*>(blob) + kBlobHeader;
+    if (h.retained > 0) {
+        frr_status s = ensure_retained(ctx, 0, h.retained);
+        if (s == FRR_OK) s = copy_in(ctx, ctx->ret_idx[0], payload, (size_t)h.retained * sizeof(uint64_t));
+        if (s == FRR_OK)
+            s = copy_in(ctx, ctx->ret_m[0], payload + (size_t)h.retained * sizeof(uint64_t),
+                        (size_t)h.retained * sizeof(float));
+        if (s != FRR_OK) {
+            st.active = false;
+            return s;
+        }
+    }
+    ctx->ret_cur = 0;
+    st.retained = h.retained;
+    // the device-side cut of the restored stream (stream_begin set the fresh one)
+    SelState* sel = static_cast<SelState*>(ctx->sel);
+    frr_status s = copy_in(ctx, &sel->cut, &h.cut, sizeof(float));
+    if (s != FRR_OK) {
+        st.active = false;
+        return s;
+    }
+    ctx->stats.draws = h.stat_draws;
+    ctx->stats.ms_balance = h.stat_ms_balance;
+    ctx->stats.ms_select = h.stat_ms_select;
+    return FRR_OK;
+}
+
+}  // namespace frr

@@ -92,6 +92,16 @@ class frr_diag_out(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class frr_stream_info(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_int32), ("n", ctypes.c_int64), ("d", ctypes.c_int64), ("n1", ctypes.c_int64),
+                ("precision", ctypes.c_int32), ("seed", ctypes.c_uint64), ("total", ctypes.c_uint64),
+                ("seen", ctypes.c_uint64), ("q", ctypes.c_double), ("threshold", ctypes.c_double),
+                ("K", ctypes.c_int64), ("retained", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -124,6 +134,10 @@ def lib():
             "frr_last_stats": (c.c_int, [P, P]),
             "frr_batch_run": (c.c_int, [P, I64, P, P]),
             "frr_autotune": (c.c_int, [P, U64, P]),
+            "frr_test_wait_expiry": (c.c_int, [P, U64]),
+            "frr_stream_save": (c.c_int, [P, P, c.c_size_t, P]),
+            "frr_stream_load": (c.c_int, [P, P, c.c_size_t]),
+            "frr_stream_blob_info": (c.c_int, [P, c.c_size_t, P]),
             "frr_diagnose": (c.c_int, [P, P]),
             "frr_fast_distance": (c.c_int, [P, I64, P, I64, I64, c.c_int, P, P]),
         }
@@ -262,6 +276,27 @@ def frr_assignment(ctx: Context, seed: int, key: int, w_out=None):
     return w
 
 
+def frr_stream_save(ctx: Context) -> bytes:
+    """The running stream's checkpoint blob (layout in include/frr.h)."""
+    size = ctypes.c_size_t()
+    st = lib().frr_stream_save(ctx.handle, None, 0, ctypes.byref(size))
+    if st != -6:
+        _check(st, "frr_stream_save")
+    buf = ctypes.create_string_buffer(size.value)
+    _check(lib().frr_stream_save(ctx.handle, buf, size.value, ctypes.byref(size)), "frr_stream_save")
+    return buf.raw[:size.value]
+
+
+def frr_stream_load(ctx: Context, blob: bytes):
+    _check(lib().frr_stream_load(ctx.handle, blob, len(blob)), "frr_stream_load")
+
+
+def frr_stream_blob_info(blob: bytes) -> dict:
+    info = frr_stream_info()
+    _check(lib().frr_stream_blob_info(blob, len(blob), ctypes.byref(info)), "frr_stream_blob_info")
+    return info.as_dict()
+
+
 def frr_assignments(ctx: Context, seed: int, first_draw: int, count: int, w_out=None):
     w = np.empty((count, ctx.n), dtype=np.uint8) if w_out is None else w_out
     _check(lib().frr_assignments(ctx.handle, seed, first_draw, count, _ptr(w)), "frr_assignments")
@@ -316,6 +351,13 @@ def frr_autotune(ctx: Context, B_probe: int = 0) -> dict:
     c = r.candidates
     return {"kb": r.kb, "chunks": r.chunks, "chosen": r.chosen, "ng": list(r.ng[:c]), "sb": list(r.sb[:c]),
             "ms": list(r.ms[:c])}
+
+
+def frr_test_wait_expiry(ctx: Context, wait_cycles: int) -> int:
+    """Failure-path test: one balance launch whose covariate tiles never arrive, with every
+    bounded wait limited to wait_cycles SM cycles. Returns the raw status (FRR_E_TIMEOUT
+    expected) instead of raising."""
+    return int(lib().frr_test_wait_expiry(ctx.handle, int(wait_cycles)))
 
 
 def frr_batch_run(experiments, precision: str = "split_bf16", band_safety: float = 2.0, stream=None,
