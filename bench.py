@@ -32,9 +32,8 @@ import numpy as np
 
 ROOT = Path(__file__).resolve().parent
 # library kernels per frr_select step of the precision workload (one chunk): k_sel_init,
-# k_balance_tc, k_sel_begin, k_sel_hist x2, k_sel_scan x2, k_sel_compact, k_bits,
-# k_recheck_tc, k_recheck_sum, k_rank, k_place_sel, k_sel_summary
-LAUNCHES_PER_STEP = 14
+# k_balance_tc, k_sel_cut (one 8-CTA cluster), k_bits, k_recheck_tc, k_finish
+LAUNCHES_PER_STEP = 6
 sys.path.insert(0, str(ROOT))
 
 METRIC = "balance-checked assignments/s at n=d=1000; split-BF16 vs FP32 path, same B300"
@@ -65,10 +64,17 @@ class ClockSampler:
         self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.tmp, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        # the first sample marks a running sampler (nvidia-smi takes a moment to start)
+        t0 = time.perf_counter()
+        while self.proc is not None and time.perf_counter() - t0 < 5.0:
+            self.tmp.flush()
+            if Path(self.tmp.name).stat().st_size > 0:
+                break
+            time.sleep(0.02)
         return self
 
     def __exit__(self, *exc):
@@ -218,7 +224,11 @@ def run_frr(args):
         torch.cuda.synchronize()
         with ClockSampler(torch.cuda.current_device()) as clk:
             t_wall = time.perf_counter()
-            for i in range(args.warmup + args.steps):
+            # W warm-up steps, repeated until the clock sampler has seen at least 0.3 s of this
+            # load (the timed steps alone take tens of milliseconds)
+            n_warm = args.warmup
+            i = 0
+            while i < n_warm + args.steps:
                 with torch.cuda.stream(stream):
                     flush.zero_()  # L2 flush between steps, outside the timed events
                     ev0.record(stream)
@@ -227,7 +237,11 @@ def run_frr(args):
                 with torch.cuda.stream(stream):
                     ev1.record(stream)
                 ev1.synchronize()
-                if i >= args.warmup:
+                i += 1
+                if i == n_warm and time.perf_counter() - t_wall < 0.3:
+                    n_warm += 1
+                    continue
+                if i > n_warm:
                     step_ms.append(ev0.elapsed_time(ev1))
                     stt = frr.frr_last_stats(ctx)
                     bal_ms.append(stt["ms_balance"])

@@ -65,7 +65,8 @@ typedef enum {
     FRR_E_RANGE = -7,      /* first_draw + B overflows 64 bits, or an exact rank >= C(n, n1) */
     FRR_E_STATE = -8,      /* call out of sequence (e.g. frr_stream_chunk before frr_stream_begin) */
     FRR_E_UNSUPPORTED = -9, /* shape outside what the compiled kernels cover (n > 2048, exact mode n > 63) */
-    FRR_E_MISMATCH = -10    /* two configurations of a kernel disagreed on the same input (internal error) */
+    FRR_E_MISMATCH = -10    /* internal consistency check failed: two configurations of a kernel disagreed on
+                              the same input, or a q-mode selection did not keep exactly K draws */
 } frr_status;
 
 /* precision of the bulk balance evaluation (the accepted set is always decided in FP64 accuracy) */

@@ -313,7 +313,18 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
                 if (lane == 0) mbar_arrive(&acc_empty[buf]);
             }
             const uint64_t off = tl * kTileM + 32 * ew + lane;
-            if (ok && off < x->B) x->Mout[off] = x->c_M * sumsq;
+            const float mh = x->c_M * sumsq;
+            if (ok && off < x->B) x->Mout[off] = mh;
+            // level-0 histogram of the streaming selection (bits [31:20] of M_hat), one atomic
+            // per distinct bin of the warp
+            unsigned* h0 = x->hist0;
+            if (h0 != nullptr) {
+                const bool take = ok && off < x->B;
+                const unsigned bin = __float_as_uint(mh) >> 20;
+                const unsigned mask = __activemask();
+                const unsigned peers = __match_any_sync(mask, take ? bin : 0xffffffffu);
+                if (take && (__ffs(peers) - 1) == lane) atomicAdd(&h0[bin], (unsigned)__popc(peers));
+            }
         }
     }
 
@@ -490,14 +501,17 @@ frr_status tc_describe(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, 
     x->exact = exact ? 1 : 0;
     x->skip_tma = 0;
     x->wait_cycles = 0;
+    x->hist0 = nullptr;
     return FRR_OK;
 }
 
-frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout)
+frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout,
+                             unsigned* hist0)
 {
     if (B == 0) return FRR_OK;
     TcExp one;
     FRR_TRY(tc_describe(ctx, seed, exact, first, B, Mout, &one));
+    one.hist0 = hist0;
     const unsigned long long tiles = (B + kTileM - 1) / kTileM;
     const int cfg = chosen_cfg(ctx->device, ctx->kb, one.nchunks, false);
     return launch_cfg(cfg, ctx, ctx->stream, ctx->num_sms, one, nullptr, nullptr, 1, tiles, ctx->dev_counters + 12);

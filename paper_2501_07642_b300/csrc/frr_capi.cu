@@ -285,7 +285,7 @@ frr_status ctx_create(frr_ctx** out, int64_t n, int64_t d, int64_t n1, const frr
                                   (size_t)d * sizeof(long long),
                                   (size_t)d * sizeof(int),
                                   64 * 64 * sizeof(uint64_t),
-                                  (size_t)7 * d * ctx->kpad * sizeof(__nv_bfloat16),
+                                  (size_t)kDigitPlanes * d * ctx->kpad * sizeof(__half),
                                   16 * sizeof(int)};
         size_t offs[10], total = 0;
         for (int i = 0; i < 10; ++i) {
@@ -304,7 +304,7 @@ frr_status ctx_create(frr_ctx** out, int64_t n, int64_t d, int64_t n1, const frr
         ctx->Qsum = reinterpret_cast<long long*>(a + offs[5]);
         ctx->qexp = reinterpret_cast<int*>(a + offs[6]);
         ctx->binom = reinterpret_cast<uint64_t*>(a + offs[7]);
-        ctx->Zq = reinterpret_cast<__nv_bfloat16*>(a + offs[8]);
+        ctx->Zq = reinterpret_cast<__half*>(a + offs[8]);
         ctx->dev_counters = reinterpret_cast<int*>(a + offs[9]);
         INIT_CUDA(cudaMemsetAsync(ctx->dev_counters, 0, 16 * sizeof(int), ctx->stream));
     }
@@ -345,7 +345,7 @@ const char* frr_strerror(frr_status s)
         case FRR_E_RANGE: return "draw range out of bounds";
         case FRR_E_STATE: return "call out of sequence";
         case FRR_E_UNSUPPORTED: return "shape not covered by the compiled kernels";
-        case FRR_E_MISMATCH: return "two kernel configurations disagreed on the same input";
+        case FRR_E_MISMATCH: return "internal consistency check failed";
     }
     return "unknown status";
 }

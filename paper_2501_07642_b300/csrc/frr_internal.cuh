@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 #include <math.h>
 
@@ -18,6 +19,15 @@ constexpr int kExactMaxN = 63;
 // Fixed-point scale for the exact-sum recheck: |Q_ij| <= 2^kQBits, so sums over
 // at most 2^12 units stay below 2^62.
 constexpr int kQBits = 50;
+
+// The fixed-point covariates of the exact recheck are written in kDigitPlanes balanced digits
+// of kDigitBits bits, Q = sum_k D_k 2^(kDigitBits k) with D_k in [-2^(kDigitBits-1),
+// 2^(kDigitBits-1)), each plane stored in FP16 (integers up to 2^11 are exact in FP16). Five
+// 11-bit digits cover |Q| <= 2^kQBits; a plane's sum over <= 2048 treated units stays below
+// 2^21 in magnitude, so FP32 accumulation of it is exact.
+constexpr int kDigitPlanes = 5;
+constexpr int kDigitBits = 11;
+static_assert(kDigitPlanes * kDigitBits >= kQBits + 2, "digit planes cover the fixed-point range");
 
 // Fluctuation multiplier of the accumulation term of the error band (number of
 // standard deviations of a partial sum under complete randomization).
@@ -43,6 +53,7 @@ struct StreamState {
     bool timing = true;       // record the per-phase events of frr_stats (off in the batched driver)
     bool overflowed = false;  // stream_end found the deferred retained set larger than its buffer
     float cut = INFINITY;     // current cut on the approximate M (keep M_hat <= cut)
+    int parity = 0;           // histogram set of the next chunk's selection
     // stream_end_enqueue -> stream_end_finish: where the outputs go
     bool end_enqueued = false, end_direct = false, end_host_keys = false, end_host_m = false, end_stage = false;
     bool end_dev_count = false;
@@ -74,8 +85,8 @@ struct frr_ctx {
     long long* Qsum = nullptr; // d
     int* qexp = nullptr;       // d: Q_ij = Zc_ij * 2^qexp_j (rounded)
     uint64_t* binom = nullptr; // 64 x 64 binomial table (exact mode)
-    __nv_bfloat16* Zq = nullptr;   // 7 x d x kpad: balanced base-256 digit planes of Q (exact recheck)
-    CUtensorMap qmap{};            // tensor map over Zq (rows 7d, columns kpad)
+    __half* Zq = nullptr;          // kDigitPlanes x d x kpad: balanced digit planes of Q (exact recheck)
+    CUtensorMap qmap{};            // tensor map over Zq (rows kDigitPlanes d, columns kpad)
     bool qmap_ready = false;
     CUtensorMap map_hi{}, map_lo{};  // tensor maps over Zhi / Zlo (balance kernel B operand)
     bool maps_ready = false;
@@ -188,11 +199,17 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host, void (*host_work)(void*)
 frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int E, cudaStream_t s, cudaStream_t aux,
                           frr_status* st_out, void (*host_work)(void*) = nullptr, void* arg = nullptr);
 frr_status balance_f32_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
-frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
-frr_status balance_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
-// count_dev: when given, the count is read on the device and `count` only bounds it
+// hist0 (split BF16 only, may be NULL): 4096 counters that also receive the level-0 histogram
+// of the scored M_hat (bits [31:20] of each value) for the streaming selection
+frr_status balance_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev,
+                             unsigned* hist0 = nullptr);
+frr_status balance_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev,
+                          unsigned* hist0 = nullptr);
+// count_dev: when given, the count is read on the device and `count` only bounds it; the
+// kernel also zeroes zero[0, nzero) (counters of the kernel launched after it)
 frr_status bits_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t count,
-                       const uint64_t* draws_dev, uint32_t* rows_dev, const long long* count_dev = nullptr);
+                       const uint64_t* draws_dev, uint32_t* rows_dev, const long long* count_dev = nullptr,
+                       int* zero = nullptr, int nzero = 0);
 frr_status words_select_launch(frr_ctx* ctx, const uint32_t* words_dev, uint32_t* row_dev);
 frr_status unpack_launch(frr_ctx* ctx, const uint32_t* rows_dev, uint64_t count, uint8_t* w_dev);
 frr_status recheck_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_t* draws_dev, int64_t count,

@@ -39,7 +39,8 @@ struct PrepJob {
     // outputs (the context's arrays)
     double* Zc64;
     float* Z32;
-    __nv_bfloat16 *Zhi, *Zlo, *Zq;
+    __nv_bfloat16 *Zhi, *Zlo;
+    __half* Zq;
     long long *Q, *Qsum;
     int* qexp;
 };
@@ -581,8 +582,8 @@ __global__ void k_derive(PJ_ARGS)
     }
 }
 
-// Balanced base-256 digits of Q: Q = sum_{k<7} q_k 256^k with q_k in [-128, 127], plane k
-// stored K-major as BF16 (integers of this size are exact): Zq[(k d + j) kpad + p].
+// Balanced base-2048 digits of Q: Q = sum_{k<5} q_k 2048^k with q_k in [-1024, 1023], plane
+// k stored K-major as FP16 (integers of this size are exact): Zq[(k d + j) kpad + p].
 __global__ void k_digits(PJ_ARGS)
 {
     unsigned lb;
@@ -592,11 +593,12 @@ __global__ void k_digits(PJ_ARGS)
     if (idx >= (size_t)kpad * d) return;
     const int j = (int)(idx / kpad), p = (int)(idx % kpad);
     long long v = J.Q[(size_t)p * d + j];
-    for (int k = 0; k < 7; ++k) {
-        int q = (int)(v & 0xFF);
-        if (q >= 128) q -= 256;
-        v = (v - q) >> 8;
-        J.Zq[((size_t)k * d + j) * kpad + p] = __float2bfloat16_rn((float)q);
+    constexpr int base = 1 << kDigitBits, half = base / 2;
+    for (int k = 0; k < kDigitPlanes; ++k) {
+        int q = (int)(v & (base - 1));
+        if (q >= half) q -= base;
+        v = (v - q) >> kDigitBits;
+        J.Zq[((size_t)k * d + j) * kpad + p] = __float2half_rn((float)q);
     }
 }
 

@@ -2,21 +2,23 @@
 //
 // The accepted set is decided on M computed from exact treated sums S_T,j =
 // sum_{i in T} Q_ij of the fixed-point covariates Q = round(Zc 2^qexp) (|Q| <= 2^50).
-// Q is written in balanced base-256 digits, Q = sum_{k<7} q_k 256^k with q_k in
-// [-128, 127], each digit plane stored in BF16 (exact). For a 0/1 assignment row w,
-// D_k = sum_i w_i q_k(i) is an integer of magnitude below 2^18, so the tensor cores'
-// FP32 accumulation of the digit products is exact, and S_T = sum_k D_k 256^k is
-// rebuilt exactly in int64 (Horner). The epilogue then forms, per column, the exact
+// Q is written in balanced base-2048 digits, Q = sum_{k<5} q_k 2048^k with q_k in
+// [-1024, 1023], each digit plane stored in FP16 (exact). For a 0/1 assignment row w
+// (FP16 ones), D_k = sum_i w_i q_k(i) is an integer of magnitude at most 2^21, so the
+// tensor cores' FP32 accumulation of the digit products is exact, and
+// S_T = sum_k D_k 2048^k is rebuilt exactly in int64 (Horner). The epilogue then forms, per column, the exact
 // 128-bit integer N_j = S_T n - S_all n1 = n1 n0 Delta_j 2^q_j (an assignment and its
 // complement give -N_j when n1 = n0), rounds N_j 2^-q_j once to FP64 and adds its square
 // to the CTA's partial sum; M64 = sum / (n n1 n0).
 //
-// Work items of (128 candidates, 64 columns), 7 accumulators of 64 columns in TMEM each,
+// Work items of (128 candidates, 64 columns), 5 accumulators of 64 columns in TMEM each,
 // taken by persistent CTAs (one per SM at most).
 // Warps 0-7 epilogue (warp w: TMEM lanes 32 (w % 4) .., columns 32 (w / 4) .. of the item,
 // so two warps share each row and the integer epilogue runs on twice the warps), warp 8 TMA
-// (7 digit tiles per K block), warp 9 MMA, warps 10-13 expand the candidates' bit rows
-// (computed beforehand) into BF16 0/1 A tiles through a 256-entry byte table in shared memory.
+// (5 digit tiles per K block), warp 9 MMA, warps 10-13 expand the candidates' bit rows
+// (computed beforehand) into FP16 0/1 A tiles through a 256-entry byte table in shared memory.
+// The CTA that finishes the last column chunk of a candidate tile also adds up each
+// candidate's partial sums (in column order) into its M64.
 #include "frr_internal.cuh"
 
 #include <algorithm>
@@ -27,10 +29,10 @@ namespace frr {
 using namespace tc;
 namespace {
 
-constexpr int kM = 128, kN = 64, kPlanes = 7, kKB = 64;
-constexpr int kStB = 3, kStA = 2;
+constexpr int kM = 128, kN = 64, kPlanes = kDigitPlanes, kKB = 64;
+constexpr int kStB = 4, kStA = 2;
 constexpr int kPlaneBytes = kN * kKB * 2;          // 8 KiB
-constexpr int kBBytes = kPlanes * kPlaneBytes;     // 56 KiB
+constexpr int kBBytes = kPlanes * kPlaneBytes;     // 40 KiB
 constexpr int kABytes = kM * kKB * 2;              // 16 KiB
 constexpr int kEpiWarps = 8;   // two per TMEM lane quarter, one per 32-column half of an item
 constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1, kExpWarp0 = kEpiWarps + 2;
@@ -85,7 +87,8 @@ size_t rc_smem_bytes() { return 1024 + (size_t)kStB * kBBytes + (size_t)kStA * k
 __global__ void __launch_bounds__(kThreads, 1)
 k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restrict__ rows, int W, int64_t C_host,
              const long long* __restrict__ C_dev, int nkb, int d, int n, int n1, const long long* __restrict__ Qsum,
-             const int* __restrict__ qexp, double* __restrict__ part, int ncb, int* err)
+             const int* __restrict__ qexp, double* __restrict__ part, int ncb, int* __restrict__ tile_done,
+             double denom, double* __restrict__ M64, int* err)
 {
     pdl_wait();
     pdl_launch_dependents();
@@ -105,12 +108,13 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
     volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
     __shared__ long long sQsum[kN];
     __shared__ int sQexp[kN];
-    __shared__ uint4 sLut8[256];   // byte -> eight BF16 values 0.0 / 1.0 (bit i -> value i)
+    __shared__ int sLast;   // this CTA completed the last column chunk of the item's candidate tile
+    __shared__ uint4 sLut8[256];   // byte -> eight FP16 values 0.0 / 1.0 (bit i -> value i)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid < 256) {
         uint32_t h[8];
-        for (int i = 0; i < 8; ++i) h[i] = ((tid >> i) & 1) ? 0x3F80u : 0u;
+        for (int i = 0; i < 8; ++i) h[i] = ((tid >> i) & 1) ? 0x3C00u : 0u;
         sLut8[tid] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
     }
     const int64_t C = C_dev ? std::min<int64_t>((int64_t)*C_dev, C_host) : C_host;  // within the buffers
@@ -162,7 +166,7 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
         if (lane == 0) {
             bool ok = true;
             uint32_t ai = 0, bi = 0, it = 0;
-            const uint32_t idesc = idesc_bf16(kM, kN);
+            const uint32_t idesc = idesc_f16(kM, kN);
             for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
                 if (!(ok = wait_bar(acc_empty, (it & 1u) ^ 1u, sAbort, err, 16))) break;
                 tc_fence_after();
@@ -249,7 +253,8 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
                     tmem_ld32(taddr + (uint32_t)(pl * kN + c0), v);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) S[j] = S[j] * 256 + (long long)acc_to_int(__uint_as_float(v[j]));
+                    for (int j = 0; j < 32; ++j)
+                        S[j] = S[j] * (1ll << kDigitBits) + (long long)acc_to_int(__uint_as_float(v[j]));
                 }
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
@@ -271,6 +276,30 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty);
             if (cand < C) part[(cand * ncb + chunk) * 2 + half] = psum;
+            // The CTA that completes the last of a tile's ncb column chunks sums each candidate's
+            // 2 ncb partial sums in column order and forms M64 = sum / (n n1 n0): the writers
+            // fence their partial sums before counting, the last one fences after (acquire).
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (tid == 0) {
+                __threadfence();
+                sLast = atomicAdd(&tile_done[item % T], 1) == ncb - 1;
+            }
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (sLast && half == 0 && cand < C) {
+                __threadfence();
+                const double* pc = part + cand * (int64_t)(2 * ncb);
+                double s = 0.0;
+                // eight independent loads in flight, then added in column order
+                for (int b0 = 0; b0 < 2 * ncb; b0 += 8) {
+                    double v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = b0 + u < 2 * ncb ? __ldcg(pc + b0 + u) : 0.0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (b0 + u < 2 * ncb) s = __dadd_rn(s, v[u]);
+                }
+                M64[cand] = __ddiv_rn(__dmul_rn(1.0, s), denom);
+            }
         }
     }
 
@@ -292,14 +321,18 @@ frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint
     if (count <= 0) return FRR_OK;
     const int W = 4 * ctx->kb;
     const int ncb = ceil_div(ctx->d, kN);
-    const size_t rows_bytes = (size_t)count * W * sizeof(uint32_t);
-    const size_t part_bytes = (size_t)count * ncb * 2 * sizeof(double);
-    FRR_TRY(ensure_device(ctx, &ctx->misc2, &ctx->misc2_bytes, rows_bytes + part_bytes + 256));
+    const int64_t tiles = (count + kM - 1) / kM;
+    const size_t rows_bytes = ((size_t)count * W * sizeof(uint32_t) + 255) & ~size_t(255);
+    const size_t part_bytes = ((size_t)count * ncb * 2 * sizeof(double) + 255) & ~size_t(255);
+    const size_t ctr_bytes = (size_t)tiles * sizeof(int);
+    FRR_TRY(ensure_device(ctx, &ctx->misc2, &ctx->misc2_bytes, rows_bytes + part_bytes + ctr_bytes));
     uint32_t* rows = static_cast<uint32_t*>(ctx->misc2);
-    double* part = reinterpret_cast<double*>(static_cast<char*>(ctx->misc2) + ((rows_bytes + 255) & ~size_t(255)));
-    FRR_TRY(bits_launch(ctx, seed, exact, 0, (uint64_t)count, draws, rows, count_dev));
+    double* part = reinterpret_cast<double*>(static_cast<char*>(ctx->misc2) + rows_bytes);
+    int* tile_done = reinterpret_cast<int*>(static_cast<char*>(ctx->misc2) + rows_bytes + part_bytes);
+    // the bit rows, and the per-tile completion counters zeroed before the recheck counts on them
+    FRR_TRY(bits_launch(ctx, seed, exact, 0, (uint64_t)count, draws, rows, count_dev, tile_done, (int)tiles));
     if (!ctx->qmap_ready) {
-        if (!make_map_bf16(&ctx->qmap, ctx->Zq, (uint64_t)ctx->kpad, (uint64_t)kPlanes * ctx->d, kKB, kN))
+        if (!make_map_f16(&ctx->qmap, ctx->Zq, (uint64_t)ctx->kpad, (uint64_t)kPlanes * ctx->d, kKB, kN))
             return FRR_E_CUDA;
         ctx->qmap_ready = true;
     }
@@ -307,12 +340,12 @@ frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint
     FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_recheck_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t items = (int64_t)((count + kM - 1) / kM) * ncb;
     const unsigned grid = (unsigned)std::min<int64_t>(items, ctx->num_sms);
+    // the partial sums hold (N_j 2^-q_j)^2 = (n1 n0 Delta_j)^2, and M = (n1 n0 / n) sum Delta_j^2
+    const double denom = (double)ctx->n * (double)ctx->n1 * (double)ctx->n0;
     FRR_CUDA_TRY(ctx, launch_pdl(k_recheck_tc, grid, kThreads, smem, ctx->stream, ctx->qmap, rows, W, count, count_dev,
                                  ctx->kused / kKB, (int)ctx->d, (int)ctx->n, (int)ctx->n1, ctx->Qsum, ctx->qexp, part,
-                                 ncb, ctx->dev_counters + 12));
-    // the partial sums hold (N_j 2^-q_j)^2 = (n1 n0 Delta_j)^2, and M = (n1 n0 / n) sum Delta_j^2
-    return recheck_sum_launch(ctx, part, 2 * ncb, count, M64, 1.0, (double)ctx->n * (double)ctx->n1 * (double)ctx->n0,
-                              count_dev);
+                                 ncb, tile_done, denom, M64, ctx->dev_counters + 12));
+    return FRR_OK;
 }
 
 }  // namespace frr

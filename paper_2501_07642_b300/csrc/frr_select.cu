@@ -31,10 +31,12 @@ namespace {
 template <int KB>
 __global__ void k_bits(uint64_t seed, int exact, const uint64_t* __restrict__ binom, int n, int n1, uint64_t first,
                        uint64_t count, const long long* __restrict__ count_dev, const uint64_t* __restrict__ draws,
-                       uint32_t* __restrict__ rows)
+                       uint32_t* __restrict__ rows, int* __restrict__ zero, int nzero)
 {
     pdl_wait();
     pdl_launch_dependents();
+    // counters of the kernel that follows (the recheck's per-tile completion counts)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nzero; i += gridDim.x * blockDim.x) zero[i] = 0;
     // a device count can exceed the bound when the retained set overflowed its buffer (the
     // host then redoes the selection); only the entries within the bound exist
     const uint64_t cnt = count_dev ? std::min<uint64_t>((uint64_t)*count_dev, count) : count;
@@ -168,207 +170,280 @@ struct CutParams {
     double lin, quad, rel, safety;
 };
 
-__device__ __forceinline__ double lower_bound_m(const CutParams& cp, float v)
+// A cut for the upper edge m_up of the bin that holds the K-th smallest M_hat: every v with
+// L(v) = v - band(v) <= T, T = U(m_up) = m_up + band(m_up), must be kept. L is increasing
+// beyond its minimum near 0, and with x = sqrt(v), L(v) = T is the quadratic
+// (1 - s rel) x^2 - s lin x - (s quad + T) = 0, band(v) = s (lin sqrt(v) + quad + rel v). The
+// root is evaluated in FP32 with every operation rounded towards the larger result (and
+// the leading coefficient rounded down, which can only enlarge the root), so the value
+// returned is at or above the exact bound: a few more draws may be kept, never fewer.
+__device__ float cut_upper_bound(const CutParams& cp, float mup)
 {
-    const double m = (double)v;
-    return m - band_value(cp.lin, cp.quad, cp.rel, cp.safety, m);
+    if (!(mup < INFINITY)) return INFINITY;
+    const float s = __double2float_ru(cp.safety), lin = __double2float_ru(cp.lin);
+    const float quad = __double2float_ru(cp.quad), rel = __double2float_ru(cp.rel);
+    const float band = __fmul_ru(s, __fadd_ru(__fadd_ru(__fmul_ru(lin, __fsqrt_ru(mup)), quad), __fmul_ru(rel, mup)));
+    const float T = __fadd_ru(mup, band);
+    const float A = __fsub_rd(1.0f, __fmul_ru(s, rel));
+    if (!(A > 0.0f)) return INFINITY;
+    const float Bq = __fmul_ru(s, lin), Cq = __fadd_ru(__fmul_ru(s, quad), T);
+    const float disc = __fadd_ru(__fmul_ru(Bq, Bq), __fmul_ru(__fmul_ru(4.0f, A), Cq));
+    const float x = __fdiv_ru(__fadd_ru(Bq, __fsqrt_ru(disc)), __fmul_rd(2.0f, A));
+    return fmaxf(__fmul_ru(x, x), mup);
 }
 
-// largest non-negative float v with L(v) <= T, where L(v) = v - s (lin sqrt(v) + quad + rel v)
-// is <= 0 near 0 and increasing after its minimum. With x = sqrt(v), L(v) = T is the
-// quadratic (1 - s rel) x^2 - s lin x - (s quad + T) = 0; its root gives v, and the float
-// result is stepped down until L(v) <= T holds and up while the next float still satisfies it.
-__device__ float largest_v_below(const CutParams& cp, double T, uint32_t lo_bits)
-{
-    if (!(T < INFINITY)) return INFINITY;
-    const double A = 1.0 - cp.safety * cp.rel, Bq = cp.safety * cp.lin, Cq = cp.safety * cp.quad + T;
-    const double x = (Bq + sqrt(Bq * Bq + 4.0 * A * Cq)) / (2.0 * A);
-    uint32_t v = __float_as_uint((float)(x * x));
-    if (v < lo_bits) v = lo_bits;                 // L(lo) <= T holds by construction
-    for (int i = 0; i < 64 && v > lo_bits && lower_bound_m(cp, __uint_as_float(v)) > T; ++i) --v;
-    for (int i = 0; i < 64 && v < 0x7f7fffffu && lower_bound_m(cp, __uint_as_float(v + 1)) <= T; ++i) ++v;
-    return __uint_as_float(v);
-}
-
-// Block-wide exclusive scan of one int per thread (SNT threads). Returns the
-// exclusive prefix; *total gets the block sum.
-__device__ int block_scan_excl(int v, int* ws, int* total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = v;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, off);
-        if (lane >= off) incl += y;
-    }
-    if (lane == 31) ws[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        int s = ws[lane];
-        int si = s;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(kFull, si, off);
-            if (lane >= off) si += y;
-        }
-        ws[lane] = si - s;
-        if (lane == 31) ws[32] = si;
-    }
-    __syncthreads();
-    const int res = ws[warp] + incl - v;
-    *total = ws[32];
-    __syncthreads();
-    return res;
-}
-
-// ---- parallel selection of the cut over V = chunk (nc values) + retained (nr values)
+// ---- cut and compaction over V = retained (nr values) + chunk (nc values)
 // Two histogram levels on the float bit pattern (M_hat >= 0, so the bit order is the
 // value order): bits [31:20] over all of V, then bits [19:8] inside the bin that holds
 // the K-th smallest. The K-th smallest value lies below the upper edge m_up of the
 // second-level bin, so T = U(m_up) >= U(M_(K)) is a safe cut; it is looser than the
 // exact one by at most 2^-15 relative.
+// The level-0 counts are kept per stream in one of two histogram sets (parity of the
+// chunk): the split-BF16 balance kernel adds each chunk's values as it scores them (or
+// k_sel_hist0 does), and the compaction of the previous chunk has added the values it
+// kept. k_sel_level1 then finds the level-0 bin of rank K (every CTA reads the 4096 bins)
+// and counts level 1; k_sel_keep forms the cut, compacts, and adds the kept values to the
+// other set, which k_sel_level1 has cleared. Two launches per chunk, all SMs busy.
 constexpr int kBins = 4096;
-constexpr int kHistThreads = 256;
+constexpr int kSelThreads = 512;
+constexpr int kSelUnroll = 4;
 
 struct SelState {
-    unsigned hist[2][kBins];
-    unsigned prefix1, prefix2;
-    long long krem;
+    unsigned hist0[2][kBins];  // level-0 counts, per chunk parity
+    unsigned hist1[2][kBins];  // level-1 counts, per chunk parity
+    unsigned p1;               // level-0 bin of rank K (k_sel_level1 -> k_sel_keep)
+    int pad2;
+    long long krem;            // rank K inside that bin
     float cut;
+    int pad0;
     long long kept;
-    // end-of-stream results, read back in one copy (see SelTail)
+    // end-of-stream results, read back in one copy together with kept (see SelTail)
     long long nsel;
     double boundary[2];      // M64 of ranks K-1 and K (q mode)
     double max_rel, max_over_band, thr;
     int violations;
+    int err;                 // the context's device error word once the selection has run
+    int fin_overflow;        // more retained draws than the one-CTA finish holds: redo
+    int pad1;
 };
 
-static_assert(offsetof(SelState, violations) - offsetof(SelState, nsel) == 48, "SelState tail layout");
-static_assert(offsetof(SelState, nsel) - offsetof(SelState, kept) == sizeof(long long), "kept precedes the tail");
-
-// the part of SelState read back by the host at the end of a stream
+// the part of SelState read back by the host at the end of a stream (after kept)
 struct SelTail {
     long long nsel;
     double boundary[2];
     double max_rel, max_over_band, thr;
     int violations;
+    int err;
+    int fin_overflow;
+    int pad1;
 };
-static_assert(offsetof(SelTail, violations) == 48, "SelTail layout");
+static_assert(offsetof(SelState, nsel) - offsetof(SelState, kept) == sizeof(long long), "kept precedes the tail");
+static_assert(offsetof(SelState, violations) - offsetof(SelState, nsel) == offsetof(SelTail, violations), "tail layout");
+static_assert(offsetof(SelState, fin_overflow) - offsetof(SelState, nsel) == offsetof(SelTail, fin_overflow), "tail layout");
+static_assert(sizeof(SelState) - offsetof(SelState, nsel) == sizeof(SelTail), "tail layout");
 
-__device__ __forceinline__ float elem_value(const float* chunk, int64_t nc, const float* ret, int64_t e)
+__device__ __forceinline__ float sel_elem(const float* ret, int64_t nr, const float* chunk, int64_t e)
 {
-    return e < nc ? chunk[e] : ret[e - nc];
+    return e < nr ? ret[e] : chunk[e - nr];
 }
 
-// level 0: bins of bits [31:20] of every value; level 1: bins of bits [19:8] of the
-// values whose bits [31:20] equal st->prefix1
-__global__ void __launch_bounds__(kHistThreads)
-k_sel_hist(const float* __restrict__ chunk, int64_t nc, const float* __restrict__ ret, int64_t nr, int level,
-           SelState* __restrict__ st)
+// Adds 1 to bin `dig` of h for every lane with take, one atomic per distinct bin of the warp.
+__device__ __forceinline__ void warp_count(unsigned* h, bool take, unsigned dig)
+{
+    const unsigned key = take ? dig : 0xffffffffu;
+    const unsigned peers = __match_any_sync(kFull, key);
+    if (take && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&h[dig], (unsigned)__popc(peers));
+}
+
+// Zeroes a shared histogram, and adds its non-zero bins to a global one afterwards.
+__device__ __forceinline__ void shist_clear(unsigned* h)
+{
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x) h[i] = 0u;
+    __syncthreads();
+}
+__device__ __forceinline__ void shist_flush(const unsigned* h, unsigned* g)
+{
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&g[i], h[i]);
+}
+
+// The bin of the global histogram g that holds rank k (1-based; k <= the total count), and
+// k minus the counts of the bins before it. Every thread of the block gets the answer.
+__device__ void find_bin(const unsigned* __restrict__ g, long long k, unsigned* bin_out, long long* k_out)
+{
+    __shared__ long long s_part[kSelThreads / 32];
+    __shared__ unsigned s_bin;
+    __shared__ long long s_k;
+    constexpr int per = kBins / kSelThreads;  // 8 consecutive bins per thread
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint4 a = *reinterpret_cast<const uint4*>(g + per * tid);
+    const uint4 b = *reinterpret_cast<const uint4*>(g + per * tid + 4);
+    const unsigned c[per] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    long long mine = 0;
+#pragma unroll
+    for (int i = 0; i < per; ++i) mine += c[i];
+    long long incl = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long y = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) s_part[warp] = incl;
+    __syncthreads();
+    long long before = incl - mine;
+    for (int w = 0; w < warp; ++w) before += s_part[w];
+    if (before < k && k <= before + mine) {
+        long long run = before;
+#pragma unroll
+        for (int i = 0; i < per; ++i) {
+            if (run < k && k <= run + (long long)c[i]) {
+                s_bin = (unsigned)(per * tid + i);
+                s_k = k - run;
+            }
+            run += c[i];
+        }
+    }
+    __syncthreads();
+    *bin_out = s_bin;
+    *k_out = s_k;
+    __syncthreads();
+}
+
+// Level-0 counts of the values [0, nc) of a chunk into the global histogram g, for a chunk
+// whose balance kernel did not add them (FP32 path, values computed elsewhere, a restored stream).
+__global__ void __launch_bounds__(kSelThreads)
+k_sel_hist0(const float* __restrict__ vals, int64_t nc, unsigned* __restrict__ g)
 {
     pdl_wait();
     pdl_launch_dependents();
     __shared__ unsigned h[kBins];
-    for (int i = threadIdx.x; i < kBins; i += kHistThreads) h[i] = 0;
-    __syncthreads();
-    const int64_t N = nc + nr;
-    const unsigned p1 = st->prefix1;
-    const int64_t stride = (int64_t)gridDim.x * kHistThreads;
-    for (int64_t base = (int64_t)blockIdx.x * kHistThreads; base < N; base += stride) {
+    shist_clear(h);
+    const int64_t stride = (int64_t)gridDim.x * kSelThreads;
+    for (int64_t base = (int64_t)blockIdx.x * kSelThreads; base < nc; base += stride) {
         const int64_t e = base + threadIdx.x;
-        bool take = false;
-        unsigned dig = 0;
-        if (e < N) {
-            const uint32_t b = __float_as_uint(elem_value(chunk, nc, ret, e));
-            if (level == 0) { take = true; dig = b >> 20; }
-            else { take = (b >> 20) == p1; dig = (b >> 8) & (kBins - 1); }
-        }
-        const unsigned key = take ? dig : 0xffffffffu;
-        const unsigned peers = __match_any_sync(kFull, key);
-        if (take && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&h[dig], (unsigned)__popc(peers));
+        const bool take = e < nc;
+        warp_count(h, take, take ? (__float_as_uint(vals[e]) >> 20) : 0u);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kBins; i += kHistThreads)
-        if (h[i]) atomicAdd(&st->hist[level][i], h[i]);
+    shist_flush(h, g);
 }
 
-// One CTA of SNT threads: the bin of histogram `level` that holds rank st->krem.
-// After level 1 it forms the cut. The other histogram is cleared for reuse.
-__global__ void __launch_bounds__(SNT) k_sel_scan(SelState* __restrict__ st, int level, CutParams cp)
+// Grid of the selection kernels: one slice of V per CTA, at most one CTA per SM.
+__host__ __device__ inline int64_t sel_slice(int64_t N, int grid) { return (N + grid - 1) / grid; }
+
+// Level 1 of the cut (when new_cut) over V; also clears the other parity's histograms and the
+// kept counter for k_sel_keep.
+__global__ void __launch_bounds__(kSelThreads)
+k_sel_level1(const float* __restrict__ ret_m, int64_t nr, const float* __restrict__ chunk, int64_t nc, long long K,
+             int new_cut, int par, SelState* __restrict__ st)
 {
     pdl_wait();
     pdl_launch_dependents();
-    __shared__ int ws[33];
-    const unsigned* h = st->hist[level];
-    const int b0 = 4 * threadIdx.x;
-    const int h0 = (int)h[b0], h1 = (int)h[b0 + 1], h2 = (int)h[b0 + 2], h3 = (int)h[b0 + 3];
-    const long long k = st->krem;
-    int tot;
-    const int excl = block_scan_excl(h0 + h1 + h2 + h3, ws, &tot);
-    long long c = excl;
-    const int hs[4] = {h0, h1, h2, h3};
+    __shared__ unsigned h[kBins];
+    const int tid = threadIdx.x;
+    // the other set was last read by the previous chunk's kernels, which have completed
+    for (int i = blockIdx.x * kSelThreads + tid; i < kBins; i += gridDim.x * kSelThreads) {
+        st->hist0[1 - par][i] = 0u;
+        st->hist1[1 - par][i] = 0u;
+    }
+    if (blockIdx.x == 0 && tid == 0) st->kept = 0;
+    if (!new_cut) return;
+    unsigned p1;
+    long long krem;
+    find_bin(st->hist0[par], K, &p1, &krem);
+    if (blockIdx.x == 0 && tid == 0) {
+        st->p1 = p1;
+        st->krem = krem;
+    }
+    shist_clear(h);
+    const int64_t N = nr + nc, per = sel_slice(N, gridDim.x);
+    const int64_t lo = std::min<int64_t>(N, (int64_t)blockIdx.x * per), hi = std::min<int64_t>(N, lo + per);
+    for (int64_t base = lo; base < hi; base += (int64_t)kSelThreads * kSelUnroll) {
+        float v[kSelUnroll];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (c < k && k <= c + hs[q]) {
-            if (level == 0) { st->prefix1 = (unsigned)(b0 + q); st->krem = k - c; }
-            else { st->prefix2 = (unsigned)(b0 + q); st->krem = k - c; }
+        for (int u = 0; u < kSelUnroll; ++u) {
+            const int64_t e = base + (int64_t)u * kSelThreads + tid;
+            v[u] = e < hi ? sel_elem(ret_m, nr, chunk, e) : 0.f;
         }
-        c += hs[q];
+#pragma unroll
+        for (int u = 0; u < kSelUnroll; ++u) {
+            const int64_t e = base + (int64_t)u * kSelThreads + tid;
+            const uint32_t b = __float_as_uint(v[u]);
+            warp_count(h, e < hi && (b >> 20) == p1, (b >> 8) & (kBins - 1));
+        }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kBins; i += SNT) st->hist[1 - level][i] = 0;
-    if (level == 1 && threadIdx.x == 0) {
-        const uint32_t up_bits = (st->prefix1 << 20) | (st->prefix2 << 8) | 0xFFu;
-        const float mup = __uint_as_float(up_bits);
-        const double T = (double)mup + band_value(cp.lin, cp.quad, cp.rel, cp.safety, (double)mup);
-        const float v = largest_v_below(cp, T, up_bits);
-        st->cut = fminf(v, st->cut);
-    }
+    shist_flush(h, st->hist1[par]);
 }
 
-// Keep the retained entries and chunk entries with M_hat <= cut (order not preserved:
-// the final ordering sorts by (M64, draw index)).
-__global__ void __launch_bounds__(kHistThreads)
-k_sel_compact(const float* __restrict__ chunk, int64_t nc, uint64_t first, const float* __restrict__ rm_in,
-              const uint64_t* __restrict__ ri_in, int64_t nr, SelState* __restrict__ st, float* __restrict__ rm_out,
-              uint64_t* __restrict__ ri_out, int64_t cap_out)
+// The cut (when new_cut: from the level-1 counts, looser than the exact K-th value by at
+// most 2^-15 relative plus the directed rounding of cut_upper_bound, and never looser than
+// the cut so far), then the compaction of the
+// CTA's slice: entries with M_hat <= cut are appended to (m_out, i_out) (order not kept:
+// the final ordering sorts by (M64, draw index)) and counted straight into the other
+// parity's level-0 histogram for the next chunk (the kept entries are few).
+__global__ void __launch_bounds__(kSelThreads)
+k_sel_keep(const float* __restrict__ ret_m, const uint64_t* __restrict__ ret_i, int64_t nr,
+           const float* __restrict__ chunk, int64_t nc, uint64_t first, int new_cut, int par, CutParams cp,
+           SelState* __restrict__ st, float* __restrict__ m_out, uint64_t* __restrict__ i_out, int64_t cap_out)
 {
     pdl_wait();
     pdl_launch_dependents();
-    const float cut = st->cut;
-    const int64_t N = nc + nr;
-    const int64_t stride = (int64_t)gridDim.x * kHistThreads;
-    const int lane = threadIdx.x & 31;
-    for (int64_t base = (int64_t)blockIdx.x * kHistThreads; base < N; base += stride) {
-        const int64_t e = base + threadIdx.x;
-        float v = 0.f;
-        uint64_t idx = 0;
-        bool keep = false;
-        if (e < N) {
-            if (e < nr) { v = rm_in[e]; idx = ri_in[e]; }
-            else { v = chunk[e - nr]; idx = first + (uint64_t)(e - nr); }
-            keep = v <= cut;
+    __shared__ float s_cut;
+    const int tid = threadIdx.x, lane = tid & 31;
+    // every CTA derives the same cut; a CTA that reads the cut after CTA 0 stored the new one
+    // gets the same minimum
+    float cut = st->cut;
+    if (new_cut) {
+        unsigned p2;
+        long long k2;
+        find_bin(st->hist1[par], st->krem, &p2, &k2);
+        if (tid == 0) {
+            const uint32_t up_bits = (st->p1 << 20) | (p2 << 8) | 0xFFu;
+            s_cut = fminf(cut_upper_bound(cp, __uint_as_float(up_bits)), cut);
         }
-        const unsigned m = __ballot_sync(kFull, keep);
-        if (m == 0) continue;
-        long long pos0 = 0;
-        if (lane == 0) pos0 = (long long)atomicAdd((unsigned long long*)&st->kept, (unsigned long long)__popc(m));
-        pos0 = __shfl_sync(kFull, pos0, 0);
-        if (keep) {
-            const long long pos = pos0 + __popc(m & ((1u << lane) - 1u));
-            if (pos < cap_out) { rm_out[pos] = v; ri_out[pos] = idx; }
+        __syncthreads();
+        cut = s_cut;
+        if (blockIdx.x == 0 && tid == 0) st->cut = cut;
+    }
+    unsigned* h_next = st->hist0[1 - par];
+    const int64_t N = nr + nc, per = sel_slice(N, gridDim.x);
+    const int64_t lo = std::min<int64_t>(N, (int64_t)blockIdx.x * per), hi = std::min<int64_t>(N, lo + per);
+    for (int64_t base = lo; base < hi; base += (int64_t)kSelThreads * kSelUnroll) {
+        float v[kSelUnroll];
+#pragma unroll
+        for (int u = 0; u < kSelUnroll; ++u) {
+            const int64_t e = base + (int64_t)u * kSelThreads + tid;
+            v[u] = e < hi ? sel_elem(ret_m, nr, chunk, e) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kSelUnroll; ++u) {
+            const int64_t e = base + (int64_t)u * kSelThreads + tid;
+            const bool keep = e < hi && v[u] <= cut;
+            warp_count(h_next, keep, __float_as_uint(v[u]) >> 20);
+            const unsigned m = __ballot_sync(kFull, keep);
+            if (m == 0) continue;
+            unsigned long long pos0 = 0;
+            if (lane == 0) pos0 = atomicAdd(reinterpret_cast<unsigned long long*>(&st->kept), (unsigned long long)__popc(m));
+            pos0 = __shfl_sync(kFull, pos0, 0);
+            if (keep) {
+                const unsigned long long pos = pos0 + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+                if (pos < (unsigned long long)cap_out) {
+                    m_out[pos] = v[u];
+                    i_out[pos] = e < nr ? ret_i[e] : first + (uint64_t)(e - nr);
+                }
+            }
         }
     }
 }
 
-// State of a new stream: the level-0 histogram cleared (each scan clears the other level for
-// its next use), the cut, the counters and the end-of-stream fields (boundary M64 = NaN until
-// the summary finds them). One launch instead of a memset and host-to-device copies.
-__global__ void __launch_bounds__(SNT) k_sel_init(SelState* __restrict__ st, float cut)
+// State of a new stream: both histogram sets cleared, the cut, the counters and the
+// end-of-stream fields (boundary M64 = NaN until the finish finds them).
+__global__ void __launch_bounds__(kSelThreads) k_sel_init(SelState* __restrict__ st, float cut)
 {
-    for (int i = threadIdx.x; i < kBins; i += SNT) st->hist[0][i] = 0;
-    if (threadIdx.x == 0) {
-        st->prefix1 = st->prefix2 = 0;
+    unsigned* h = &st->hist0[0][0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * kBins; i += gridDim.x * blockDim.x) h[i] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->p1 = 0;
         st->krem = 0;
         st->cut = cut;
         st->kept = 0;
@@ -376,17 +451,299 @@ __global__ void __launch_bounds__(SNT) k_sel_init(SelState* __restrict__ st, flo
         st->boundary[0] = st->boundary[1] = __longlong_as_double(0x7FF8000000000000ll);
         st->max_rel = st->max_over_band = st->thr = 0.0;
         st->violations = 0;
+        st->err = 0;
+        st->fin_overflow = 0;
     }
 }
 
-__global__ void k_sel_begin(SelState* __restrict__ st, long long K)
+// ------------------------------------------------------------- one-CTA finish --
+// The exact M of every retained draw is known (the recheck); what is left is the order.
+// One CTA of 1024 threads holds the r <= kFinMax retained pairs (M64, draw index), one to
+// four per thread. M64 >= 0 orders like its bit pattern, so in q mode the K-th smallest M64
+// is found by a radix select on the 64-bit patterns (8 bits per pass, from the first bit in
+// which the smallest and largest pattern differ); an entry is accepted when its M64 is
+// smaller, or equal and among the first (K minus the smaller ones) of the equal entries in
+// draw order. Threshold mode accepts M64 <= a. Each accepted entry is then placed at the
+// number of accepted entries with a smaller draw index (one warp per entry), and one thread
+// writes the summary the host reads back.
+constexpr int kFinMax = 4096;
+constexpr int kFinThreads = SNT;
+constexpr int kFinPer = kFinMax / kFinThreads;   // entries per thread
+
+__global__ void __launch_bounds__(kFinThreads, 1)
+k_finish(const double* __restrict__ m64, const uint64_t* __restrict__ idx, const float* __restrict__ mhat, int64_t r_host,
+         const long long* __restrict__ r_dev, long long K, int q_mode, long long thr_bits, CutParams cp,
+         const int* __restrict__ err_word, SelState* __restrict__ st, uint64_t* __restrict__ keys_out,
+         double* __restrict__ m_out)
 {
     pdl_wait();
     pdl_launch_dependents();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->krem = K;
-        st->kept = 0;
+    extern __shared__ unsigned long long fin_smem[];
+    __shared__ unsigned hist[256];
+    __shared__ unsigned long long s_red[32][2];
+    __shared__ float s_rel[32], s_band[32];
+    __shared__ int s_viol[32];
+    __shared__ unsigned long long s_prefix;
+    __shared__ long long s_k, s_ntie;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // a device count above the bound belongs to an overflowed buffer: the host redoes the selection
+    const int64_t r = r_dev ? (*r_dev < r_host ? *r_dev : r_host) : r_host;
+    if (r > kFinMax) {
+        if (tid == 0) {
+            st->fin_overflow = 1;
+            st->nsel = 0;
+            st->err = *err_word;
+        }
+        return;
     }
+    if (r <= 0) {
+        if (tid == 0) {
+            const double nan = __longlong_as_double(0x7FF8000000000000ll);
+            st->nsel = 0;
+            st->boundary[0] = st->boundary[1] = nan;
+            st->thr = -INFINITY;
+            st->max_rel = st->max_over_band = 0.0;
+            st->violations = 0;
+            st->fin_overflow = 0;
+            st->err = *err_word;
+        }
+        return;
+    }
+    unsigned long long* sk = fin_smem;             // M64 bit patterns
+    unsigned long long* si = fin_smem + kFinMax;   // draw indices
+    int* sflag = reinterpret_cast<int*>(fin_smem + 2 * kFinMax);  // accepted (1) or not (0)
+    unsigned long long key[kFinPer];
+    unsigned long long lo_key = ~0ull, hi_key = 0ull;
+    float mrel = 0.f, mband = 0.f;
+    int viol = 0;
+#pragma unroll
+    for (int m = 0; m < kFinPer; ++m) {
+        const int c = tid + m * kFinThreads;
+        key[m] = ~0ull;
+        if (c < r) {
+            const double mv = m64[c];
+            key[m] = (unsigned long long)__double_as_longlong(mv);
+            sk[c] = key[m];
+            si[c] = idx[c];
+            lo_key = key[m] < lo_key ? key[m] : lo_key;
+            hi_key = key[m] > hi_key ? key[m] : hi_key;
+            // diagnostics only: FP32 is enough (and cheap on B300)
+            const float a = mhat[c], mf = (float)mv;
+            const float err = fabsf(a - mf);
+            const float band =
+                (float)cp.safety * ((float)cp.lin * sqrtf(fmaxf(a, 0.f)) + (float)cp.quad + (float)cp.rel * a);
+            if (mf > 0.f) mrel = fmaxf(mrel, __fdividef(err, mf));
+            if (band > 0.f) mband = fmaxf(mband, __fdividef(err, band));
+            viol += (err > band) ? 1 : 0;
+        }
+    }
+    for (int off = 16; off >= 1; off >>= 1) {
+        mrel = fmaxf(mrel, __shfl_xor_sync(kFull, mrel, off));
+        mband = fmaxf(mband, __shfl_xor_sync(kFull, mband, off));
+        viol += __shfl_xor_sync(kFull, viol, off);
+        const unsigned long long a = __shfl_xor_sync(kFull, lo_key, off), b = __shfl_xor_sync(kFull, hi_key, off);
+        lo_key = a < lo_key ? a : lo_key;
+        hi_key = b > hi_key ? b : hi_key;
+    }
+    if (lane == 0) {
+        s_rel[warp] = mrel;
+        s_band[warp] = mband;
+        s_viol[warp] = viol;
+        s_red[warp][0] = lo_key;
+        s_red[warp][1] = hi_key;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < kFinThreads / 32; ++w) {
+            lo_key = s_red[w][0] < lo_key ? s_red[w][0] : lo_key;
+            hi_key = s_red[w][1] > hi_key ? s_red[w][1] : hi_key;
+        }
+        s_red[0][0] = lo_key;
+        s_red[0][1] = hi_key;
+    }
+    __syncthreads();
+    lo_key = s_red[0][0];
+    hi_key = s_red[0][1];
+
+    // the accepted set: key < thr, plus the first `need` entries equal to thr in draw order
+    unsigned long long thr;
+    long long need;
+    if (q_mode) {
+        // radix select of the K-th smallest key (K <= r here), from the first differing bit
+        unsigned long long prefix = 0ull;
+        long long k = K < r ? K : r;
+        const int top = (lo_key == hi_key) ? -1 : 63 - __clzll((long long)(lo_key ^ hi_key));
+        prefix = top < 0 ? lo_key : (top >= 63 ? 0ull : (lo_key >> (top + 1)) << (top + 1));
+        for (int shift = top - 7; top >= 0; shift -= 8) {
+            const int sh = shift < 0 ? 0 : shift;
+            const int bits = shift < 0 ? 8 + shift : 8;        // the last pass may take fewer bits
+            const unsigned long long himask = (sh + bits >= 64) ? 0ull : (~0ull << (sh + bits));
+            if (tid < 256) hist[tid] = 0u;
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < kFinPer; ++m) {
+                if (m * kFinThreads >= r) break;  // the same for the whole block
+                const int c = tid + m * kFinThreads;
+                const bool take = c < r && (key[m] & himask) == (prefix & himask);
+                const unsigned d = take ? (unsigned)((key[m] >> sh) & ((1u << bits) - 1u)) : 0u;
+                const unsigned peers = __match_any_sync(kFull, take ? d : 0xffffffffu);
+                if (take && (__ffs(peers) - 1) == lane) atomicAdd(&hist[d], (unsigned)__popc(peers));
+            }
+            __syncthreads();
+            if (warp == 0) {
+                // digit holding rank k: lane l scans bins 8l .. 8l + 7
+                unsigned cnt[8];
+                long long mine = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) { cnt[i] = hist[8 * lane + i]; mine += cnt[i]; }
+                long long incl = mine;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const long long y = __shfl_up_sync(kFull, incl, off);
+                    if (lane >= off) incl += y;
+                }
+                long long run = incl - mine;
+                if (run < k && k <= incl) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        if (run < k && k <= run + (long long)cnt[i]) {
+                            s_prefix = (prefix & himask) | ((unsigned long long)(8 * lane + i) << sh);
+                            s_k = k - run;
+                        }
+                        run += cnt[i];
+                    }
+                }
+            }
+            __syncthreads();
+            prefix = s_prefix;
+            k = s_k;
+            if (shift <= 0) break;
+        }
+        thr = prefix;  // the K-th smallest key; k of the entries equal to it are accepted
+        need = k;
+    } else {
+        thr = thr_bits < 0 ? 0ull : (unsigned long long)thr_bits;
+        need = thr_bits < 0 ? 0 : (long long)kFinMax;  // threshold mode keeps every equal entry
+    }
+    if (tid == 0) s_ntie = 0;
+    __syncthreads();
+    // flags: below the threshold key, or equal to it (ranked among the equal ones below)
+    int below = 0;
+#pragma unroll
+    for (int m = 0; m < kFinPer; ++m) {
+        const int c = tid + m * kFinThreads;
+        if (c < r) {
+            const bool lt = q_mode ? key[m] < thr : (thr_bits >= 0 && key[m] <= thr);
+            sflag[c] = lt ? 1 : 0;
+            if (q_mode && key[m] == thr) atomicAdd(reinterpret_cast<unsigned long long*>(&s_ntie), 1ull);
+            below += lt ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    if (q_mode) {
+        // entries equal to thr: accepted when fewer than `need` equal entries have a smaller
+        // draw index (one warp per equal entry; equal M64 are rare, e.g. complement pairs)
+        for (int c = warp; c < r; c += kFinThreads / 32) {
+            if (sk[c] != thr) continue;
+            const unsigned long long ic = si[c];
+            int before = 0;
+            for (int c2 = lane; c2 < r; c2 += 32) before += (sk[c2] == thr && si[c2] < ic) ? 1 : 0;
+            before = (int)__reduce_add_sync(kFull, (unsigned)before);
+            if (lane == 0 && before < need) sflag[c] = 1;
+        }
+    }
+    // smallest key above the accepted ones (the (K+1)-th M64) and the accepted count
+    unsigned long long above = ~0ull;
+#pragma unroll
+    for (int m = 0; m < kFinPer; ++m) {
+        const int c = tid + m * kFinThreads;
+        if (c < r && key[m] > thr && key[m] < above) above = key[m];
+    }
+    for (int off = 16; off >= 1; off >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(kFull, above, off);
+        above = a < above ? a : above;
+        below += __shfl_xor_sync(kFull, below, off);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        s_red[warp][0] = above;
+        s_red[warp][1] = (unsigned long long)below;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long nb = 0;
+        for (int w = 0; w < kFinThreads / 32; ++w) {
+            above = s_red[w][0] < above ? s_red[w][0] : above;
+            nb += (long long)s_red[w][1];
+        }
+        for (int w = 1; w < kFinThreads / 32; ++w) {
+            mrel = fmaxf(mrel, s_rel[w]);
+            mband = fmaxf(mband, s_band[w]);
+            viol += s_viol[w];
+        }
+        const long long ns = q_mode ? (K < r ? K : r) : nb;
+        const double nan = __longlong_as_double(0x7FF8000000000000ll);
+        st->boundary[0] = (q_mode && K >= 1 && K - 1 < r) ? __longlong_as_double((long long)thr) : nan;
+        // the (K+1)-th M64: another entry equal to thr if there is one, else the next larger key
+        st->boundary[1] = (q_mode && K < r) ? __longlong_as_double((long long)(s_ntie > need ? thr : above)) : nan;
+        if (q_mode) st->thr = ns > 0 ? __longlong_as_double((long long)thr) : -INFINITY;
+        st->nsel = ns;
+        st->max_rel = mrel;
+        st->max_over_band = mband;
+        st->violations = viol;
+        st->fin_overflow = 0;
+    }
+    __syncthreads();
+    // the accepted entries, packed (in any order) into the shared arrays ai / ak
+    __shared__ int s_na;
+    if (tid == 0) s_na = 0;
+    __syncthreads();
+    unsigned long long* ai = fin_smem + 2 * kFinMax + kFinMax / 2;   // packed accepted draw indices
+    unsigned long long* ak = ai + kFinMax;                           // and their M64 bit patterns
+    for (int c0 = 0; c0 < r; c0 += kFinThreads) {
+        const int c = c0 + tid;
+        const bool a = c < r && sflag[c] != 0;
+        const unsigned m = __ballot_sync(kFull, a);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&s_na, __popc(m));
+        base = __shfl_sync(kFull, base, 0);
+        if (a) {
+            const int q = base + __popc(m & ((1u << lane) - 1u));
+            ai[q] = si[c];
+            ak[q] = sk[c];
+        }
+    }
+    __syncthreads();
+    const int na = s_na;
+    // position = accepted entries with a smaller draw index (one warp per accepted entry)
+    unsigned long long best = 0ull;
+    bool any = false;
+    for (int a = warp; a < na; a += kFinThreads / 32) {
+        const unsigned long long ic = ai[a];
+        int pos = 0;
+        for (int b = lane; b < na; b += 32) pos += ai[b] < ic ? 1 : 0;
+        pos = (int)__reduce_add_sync(kFull, (unsigned)pos);
+        if (lane == 0) {
+            keys_out[pos] = ic;
+            m_out[pos] = __longlong_as_double((long long)ak[a]);
+            if (!q_mode && (!any || ak[a] > best)) { best = ak[a]; any = true; }
+        }
+    }
+    if (!q_mode) {
+        // threshold mode: the largest accepted M64
+        __shared__ unsigned long long s_best[32];
+        __shared__ int s_any[32];
+        if (lane == 0) { s_best[warp] = best; s_any[warp] = any ? 1 : 0; }
+        __syncthreads();
+        if (tid == 0) {
+            bool a = false;
+            unsigned long long b = 0ull;
+            for (int w = 0; w < kFinThreads / 32; ++w)
+                if (s_any[w] && (!a || s_best[w] > b)) { b = s_best[w]; a = true; }
+            st->thr = a ? __longlong_as_double((long long)b) : -INFINITY;
+        }
+    }
+    if (tid == 0) st->err = *err_word;
 }
 
 // ---------------------------------------------------------------- ordering --
@@ -448,11 +805,12 @@ __global__ void k_place_sel(const double* __restrict__ m, const uint64_t* __rest
 }
 
 // One CTA: accepted count, the M64 of ranks K-1 and K, the largest accepted M64 and the
-// band statistics of the re-checked draws (the SelTail fields).
+// band statistics of the re-checked draws (the SelTail fields), for retained sets larger than
+// the one-CTA finish holds.
 __global__ void __launch_bounds__(SNT)
 k_sel_summary(const double* __restrict__ m64, const int* __restrict__ rank, const float* __restrict__ mhat, int64_t r_host,
               const long long* __restrict__ r_dev, long long K, int q_mode, long long thr_bits, CutParams cp,
-              SelState* __restrict__ st)
+              const int* __restrict__ err_word, SelState* __restrict__ st)
 {
     pdl_wait();
     pdl_launch_dependents();
@@ -505,6 +863,8 @@ k_sel_summary(const double* __restrict__ m64, const int* __restrict__ rank, cons
         st->max_over_band = mband;
         st->thr = thr >= 0 ? __longlong_as_double(thr) : -INFINITY;
         st->violations = viol;
+        st->fin_overflow = 0;
+        st->err = *err_word;
     }
 }
 
@@ -519,10 +879,10 @@ unsigned warp_grid(const frr_ctx* ctx, uint64_t count)
 
 template <int KB>
 frr_status launch_bits_kb(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t count,
-                          const long long* count_dev, const uint64_t* draws, uint32_t* rows)
+                          const long long* count_dev, const uint64_t* draws, uint32_t* rows, int* zero, int nzero)
 {
     FRR_CUDA_TRY(ctx, launch_pdl(k_bits<KB>, warp_grid(ctx, count), 256, 0, ctx->stream, seed, exact ? 1 : 0, ctx->binom,
-                                 (int)ctx->n, (int)ctx->n1, first, count, count_dev, draws, rows));
+                                 (int)ctx->n, (int)ctx->n1, first, count, count_dev, draws, rows, zero, nzero));
     return FRR_OK;
 }
 
@@ -540,15 +900,15 @@ frr_status launch_recheck_kb(frr_ctx* ctx, uint64_t seed, bool exact, const uint
 }  // namespace
 
 frr_status bits_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t count,
-                       const uint64_t* draws, uint32_t* rows, const long long* count_dev)
+                       const uint64_t* draws, uint32_t* rows, const long long* count_dev, int* zero, int nzero)
 {
     if (count == 0) return FRR_OK;
     switch (ctx->kb) {
-        case 1: return launch_bits_kb<1>(ctx, seed, exact, first, count, count_dev, draws, rows);
-        case 2: return launch_bits_kb<2>(ctx, seed, exact, first, count, count_dev, draws, rows);
-        case 4: return launch_bits_kb<4>(ctx, seed, exact, first, count, count_dev, draws, rows);
-        case 8: return launch_bits_kb<8>(ctx, seed, exact, first, count, count_dev, draws, rows);
-        case 16: return launch_bits_kb<16>(ctx, seed, exact, first, count, count_dev, draws, rows);
+        case 1: return launch_bits_kb<1>(ctx, seed, exact, first, count, count_dev, draws, rows, zero, nzero);
+        case 2: return launch_bits_kb<2>(ctx, seed, exact, first, count, count_dev, draws, rows, zero, nzero);
+        case 4: return launch_bits_kb<4>(ctx, seed, exact, first, count, count_dev, draws, rows, zero, nzero);
+        case 8: return launch_bits_kb<8>(ctx, seed, exact, first, count, count_dev, draws, rows, zero, nzero);
+        case 16: return launch_bits_kb<16>(ctx, seed, exact, first, count, count_dev, draws, rows, zero, nzero);
         default: return FRR_E_UNSUPPORTED;
     }
 }
@@ -594,10 +954,11 @@ frr_status recheck_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint64_
     return recheck_tc_launch(ctx, seed, exact, draws, count, M64, count_dev);
 }
 
-frr_status balance_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout)
+frr_status balance_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout,
+                          unsigned* hist0)
 {
     if (ctx->opts.precision == FRR_F32) return balance_f32_launch(ctx, seed, exact, first, B, Mout);
-    return balance_tc_launch(ctx, seed, exact, first, B, Mout);
+    return balance_tc_launch(ctx, seed, exact, first, B, Mout, hist0);
 }
 
 // ------------------------------------------------------------- streaming --
@@ -668,7 +1029,7 @@ frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold,
     ctx->ret_cur = 0;
     const double ms_init = ctx->stats.ms_init;
     FRR_TRY(ensure_device(ctx, &ctx->sel, &ctx->sel_bytes, sizeof(SelState)));
-    k_sel_init<<<1, SNT, 0, ctx->stream>>>(static_cast<SelState*>(ctx->sel), st.cut);
+    k_sel_init<<<8, kSelThreads, 0, ctx->stream>>>(static_cast<SelState*>(ctx->sel), st.cut);
     FRR_CUDA_TRY(ctx, cudaGetLastError());
     memset(&ctx->stats, 0, sizeof(ctx->stats));
     ctx->stats.ms_init = ms_init;
@@ -676,26 +1037,19 @@ frr_status stream_begin(frr_ctx* ctx, uint64_t seed, double q, double threshold,
     return FRR_OK;
 }
 
-// Selection step over the approximate M of draws [first, first + bc) held in Mhat (device).
-frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const float* Mhat, bool last)
+// Selection step over the approximate M of draws [first, first + bc) held in Mhat (device):
+// k_sel_level1 and k_sel_keep form the cut (q mode) and compact the chunk and the retained set.
+// hist_done: the balance kernel already added the chunk's level-0 counts.
+frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const float* Mhat, bool last, bool hist_done)
 {
     StreamState& st = ctx->st;
     SelState* sel = static_cast<SelState*>(ctx->sel);
     const CutParams cp = cut_params(ctx);
     FRR_TRY(ensure_host_pinned(ctx, 256));
     const int in = ctx->ret_cur, out = 1 - in;
+    const int par = st.parity;
     const int64_t N = st.retained + (int64_t)bc;
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(N, kHistThreads), 4 * ctx->num_sms));
-    FRR_CUDA_TRY(ctx, launch_pdl(k_sel_begin, 1, 32, 0, ctx->stream, sel, (long long)st.K));
-    if (st.q_mode && N > st.K) {
-        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_hist, grid, kHistThreads, 0, ctx->stream, Mhat, (int64_t)bc, ctx->ret_m[in],
-                                     st.retained, 0, sel));
-        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_scan, 1, SNT, 0, ctx->stream, sel, 0, cp));
-        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_hist, grid, kHistThreads, 0, ctx->stream, Mhat, (int64_t)bc, ctx->ret_m[in],
-                                     st.retained, 1, sel));
-        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_scan, 1, SNT, 0, ctx->stream, sel, 1, cp));
-    }
-    FRR_CUDA_TRY(ctx, cudaGetLastError());
+    const int new_cut = (st.q_mode && N > st.K) ? 1 : 0;
     int64_t cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
     // the last chunk of a deferred-count stream keeps every entry it could keep (capacity N),
     // so the count need not be read back before the recheck
@@ -710,22 +1064,36 @@ frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const f
         FRR_TRY(ensure_retained(ctx, out, want));
         cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
     }
-    if (defer) {
-        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_compact, grid, kHistThreads, 0, ctx->stream, Mhat, (int64_t)bc, first,
-                                     ctx->ret_m[in], ctx->ret_idx[in], st.retained, sel, ctx->ret_m[out],
-                                     ctx->ret_idx[out], cap));
+    if (!hist_done && bc > 0) {
+        const unsigned g0 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)bc, kSelThreads),
+                                                                               4 * ctx->num_sms));
+        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_hist0, g0, kSelThreads, 0, ctx->stream, Mhat, (int64_t)bc,
+                                     &sel->hist0[par][0]));
+    }
+    // one slice of V per CTA, at most one CTA per SM
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(N, 2 * kSelThreads), ctx->num_sms));
+    auto select_launch = [&](int fresh_cut) -> frr_status {
+        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_level1, grid, kSelThreads, 0, ctx->stream, (const float*)ctx->ret_m[in],
+                                     st.retained, Mhat, (int64_t)bc, (long long)st.K, fresh_cut, par, sel));
+        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_keep, grid, kSelThreads, 0, ctx->stream, (const float*)ctx->ret_m[in],
+                                     (const uint64_t*)ctx->ret_idx[in], st.retained, Mhat, (int64_t)bc, first, fresh_cut,
+                                     par, cp, sel, ctx->ret_m[out], ctx->ret_idx[out], cap));
         FRR_CUDA_TRY(ctx, cudaGetLastError());
+        return FRR_OK;
+    };
+    if (defer) {
+        FRR_TRY(select_launch(new_cut));
         if (st.timing) cudaEventRecord(ctx->ev[2], ctx->stream);
         st.retained = -1;
         st.retained_bound = std::min<int64_t>(N, cap);
+        st.parity = 1 - par;
         ctx->ret_cur = out;
         return FRR_OK;
     }
     for (int attempt = 0;; ++attempt) {
-        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_compact, grid, kHistThreads, 0, ctx->stream, Mhat, (int64_t)bc, first,
-                                     ctx->ret_m[in], ctx->ret_idx[in], st.retained, sel, ctx->ret_m[out],
-                                     ctx->ret_idx[out], cap));
-        FRR_CUDA_TRY(ctx, cudaGetLastError());
+        // a repeat keeps the cut the first launch stored, so it keeps the same set (and
+        // k_sel_level1 clears the next chunk's counts again before k_sel_keep adds them)
+        FRR_TRY(select_launch(attempt == 0 ? new_cut : 0));
         long long* hk = static_cast<long long*>(ctx->host_pinned);
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk, &sel->kept, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk + 1, ctx->dev_counters + 12, sizeof(int), cudaMemcpyDeviceToHost,
@@ -743,11 +1111,10 @@ frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const f
             break;
         }
         if (attempt == 1) return FRR_E_CAPACITY;
-        // the cut stays as computed, so the re-run keeps the same set
         FRR_TRY(ensure_retained(ctx, out, kept));
         cap = (int64_t)(ctx->ret_bytes_m[out] / sizeof(float));
-        k_sel_begin<<<1, 32, 0, ctx->stream>>>(sel, st.K);
     }
+    st.parity = 1 - par;
     ctx->ret_cur = out;
     return FRR_OK;
 }
@@ -762,9 +1129,13 @@ frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B)
         const uint64_t bc = std::min<uint64_t>(kChunkMax, B - off);
         FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->Mhat), &ctx->Mhat_bytes, bc * sizeof(float)));
         if (st.timing) cudaEventRecord(ctx->ev[0], ctx->stream);
-        FRR_TRY(balance_launch(ctx, st.seed, st.exact, first + off, bc, ctx->Mhat));
+        // the split-BF16 balance kernel also adds the chunk's level-0 counts of the selection
+        SelState* sel = static_cast<SelState*>(ctx->sel);
+        const bool fused = ctx->opts.precision == FRR_SPLIT_BF16;
+        FRR_TRY(balance_launch(ctx, st.seed, st.exact, first + off, bc, ctx->Mhat,
+                               fused ? &sel->hist0[st.parity][0] : nullptr));
         if (st.timing) cudaEventRecord(ctx->ev[1], ctx->stream);
-        FRR_TRY(stream_select_step(ctx, first + off, bc, ctx->Mhat, st.seen + off + bc == st.total));
+        FRR_TRY(stream_select_step(ctx, first + off, bc, ctx->Mhat, st.seen + off + bc == st.total, fused));
         if (st.retained < 0) {
             st.times_pending = true;  // nothing was synchronised: read the events in stream_end
             continue;
@@ -790,7 +1161,7 @@ frr_status stream_chunk_precomputed(frr_ctx* ctx, uint64_t first, uint64_t B, co
         const uint64_t bc = std::min<uint64_t>(kChunkMax, B - off);
         if (st.timing) cudaEventRecord(ctx->ev[0], ctx->stream);  // no balance here: an empty interval
         if (st.timing) cudaEventRecord(ctx->ev[1], ctx->stream);
-        FRR_TRY(stream_select_step(ctx, first + off, bc, Mhat + off, st.seen + off + bc == st.total));
+        FRR_TRY(stream_select_step(ctx, first + off, bc, Mhat + off, st.seen + off + bc == st.total, false));
         if (st.retained < 0) {
             st.times_pending = st.timing;  // nothing was synchronised: read the events in stream_end
             continue;
@@ -851,22 +1222,37 @@ frr_status stream_end_enqueue(frr_ctx* ctx, uint64_t* keys_out, double* M64_out,
     uint64_t* place_k = direct ? keys_out : kout;
     double* place_m = (direct && M64_out) ? M64_out : mout;
     if (rb > 0) {
-        // (sel->boundary was set to NaN by k_sel_init)
         FRR_TRY(recheck_launch(ctx, st.seed, st.exact, ctx->ret_idx[cur], rb, m64, r_dev));
         // threshold mode: M64 <= a compares as bit patterns (M64 >= 0); a < 0 accepts nothing
         long long thr_bits = -1;
         if (!st.q_mode && st.threshold >= 0.0) memcpy(&thr_bits, &st.threshold, sizeof(thr_bits));
-        FRR_CUDA_TRY(ctx, launch_pdl(k_rank, warp_grid(ctx, rb), 256, 0, ctx->stream, m64, ctx->ret_idx[cur], rb, r_dev,
-                                     rank));
-        FRR_CUDA_TRY(ctx, launch_pdl(k_place_sel, warp_grid(ctx, rb), 256, 0, ctx->stream, m64, ctx->ret_idx[cur], rank,
-                                     rb, r_dev, (long long)st.K, st.q_mode ? 1 : 0, thr_bits, place_k, place_m));
-        FRR_CUDA_TRY(ctx, launch_pdl(k_sel_summary, 1, SNT, 0, ctx->stream, m64, rank, ctx->ret_m[cur], rb, r_dev,
-                                     (long long)st.K, st.q_mode ? 1 : 0, thr_bits, cut_params(ctx), sel));
+        // The ordering: one CTA sorts the retained set in shared memory when it holds at most
+        // kFinMax draws -- known on the host, or (deferred count, q mode) expected because it is
+        // about K plus the draws inside the band; a larger deferred set sets fin_overflow and the
+        // caller redoes the selection with the count read back. Otherwise rank and place with
+        // one warp per entry.
+        const bool one_cta = dev_count ? (st.q_mode && st.K <= kFinMax / 4)
+                                       : (rb <= (st.q_mode ? kFinMax : kFinMax / 4) && st.K <= kFinMax / 4);
+        if (one_cta) {
+            // M64 patterns, indices, flags, packed accepted indices and patterns (147 KiB)
+            const size_t smem = (size_t)kFinMax * (4 * sizeof(unsigned long long) + sizeof(int));
+            FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            FRR_CUDA_TRY(ctx, launch_pdl(k_finish, 1, kFinThreads, smem, ctx->stream, (const double*)m64,
+                                         (const uint64_t*)ctx->ret_idx[cur], (const float*)ctx->ret_m[cur], rb, r_dev,
+                                         (long long)st.K, st.q_mode ? 1 : 0, thr_bits, cut_params(ctx),
+                                         (const int*)(ctx->dev_counters + 12), sel, place_k, place_m));
+        } else {
+            FRR_CUDA_TRY(ctx, launch_pdl(k_rank, warp_grid(ctx, rb), 256, 0, ctx->stream, m64, ctx->ret_idx[cur], rb,
+                                         r_dev, rank));
+            FRR_CUDA_TRY(ctx, launch_pdl(k_place_sel, warp_grid(ctx, rb), 256, 0, ctx->stream, m64, ctx->ret_idx[cur],
+                                         rank, rb, r_dev, (long long)st.K, st.q_mode ? 1 : 0, thr_bits, place_k, place_m));
+            FRR_CUDA_TRY(ctx, launch_pdl(k_sel_summary, 1, SNT, 0, ctx->stream, m64, rank, ctx->ret_m[cur], rb, r_dev,
+                                         (long long)st.K, st.q_mode ? 1 : 0, thr_bits, cut_params(ctx),
+                                         (const int*)(ctx->dev_counters + 12), sel));
+        }
         FRR_CUDA_TRY(ctx, cudaGetLastError());
-        // kept (the retained count) and the SelTail fields, in one copy
+        // kept (the retained count) and the SelTail fields (the device error word included), in one copy
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hp, &sel->kept, sizeof(long long) + sizeof(SelTail), cudaMemcpyDeviceToHost,
-                                          ctx->stream));
-        FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hp + 128, ctx->dev_counters + 12, sizeof(int), cudaMemcpyDeviceToHost,
                                           ctx->stream));
         if (stage) {
             if (host_keys)
@@ -920,14 +1306,15 @@ frr_status stream_end_finish(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, 
     if (rb > 0) {
         if (st.end_dev_count) memcpy(&r, hp, sizeof(long long));
         memcpy(&tail, hp + sizeof(long long), sizeof(SelTail));
-        if (*reinterpret_cast<int*>(hp + 128) != 0) {
+        if (tail.err != 0) {
             FRR_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dev_counters + 12, 0, sizeof(int), ctx->stream));
             FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
             st.active = false;
             return FRR_E_TIMEOUT;
         }
-        if (r > rb) {
-            // the deferred retained set outgrew its buffer: nothing written; redo undeferred
+        if (r > rb || tail.fin_overflow) {
+            // the deferred retained set outgrew its buffer (or the one-CTA finish): nothing
+            // written; redo undeferred
             st.active = false;
             st.overflowed = true;
             return FRR_E_CAPACITY;
@@ -948,6 +1335,8 @@ frr_status stream_end_finish(frr_ctx* ctx, uint64_t* keys_out, double* M64_out, 
     *K_out = nsel;
     st.active = false;
     st.retained = r;
+    // q mode accepts exactly min(K, B) draws; anything else is an internal error
+    if (st.q_mode && nsel != std::min<int64_t>(st.K, (int64_t)st.total)) return FRR_E_MISMATCH;
 
     const BandConsts& b = band_of(ctx);
     ctx->stats.candidates = r;
@@ -1194,6 +1583,21 @@ frr_status stream_load(frr_ctx* ctx, const void* blob, size_t size)
     }
     ctx->ret_cur = 0;
     st.retained = h.retained;
+    st.parity = 0;
+    if (h.retained > 0) {
+        // the level-0 counts of the restored retained set (stream_begin cleared both sets)
+        SelState* sl = static_cast<SelState*>(ctx->sel);
+        const unsigned g0 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(h.retained, kSelThreads),
+                                                                               4 * ctx->num_sms));
+        const cudaError_t e = launch_pdl(k_sel_hist0, g0, kSelThreads, 0, ctx->stream, (const float*)ctx->ret_m[0],
+                                         (int64_t)h.retained, &sl->hist0[0][0]);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->failed = true;
+            st.active = false;
+            return FRR_E_CUDA;
+        }
+    }
     // the device-side cut of the restored stream (stream_begin set the fresh one)
     SelState* sel = static_cast<SelState*>(ctx->sel);
     frr_status s = copy_in(ctx, &sel->cut, &h.cut, sizeof(float));

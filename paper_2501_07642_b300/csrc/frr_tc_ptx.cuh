@@ -127,6 +127,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // Shared-memory descriptor of a K-major tile with 128-byte swizzle: rows of 128 bytes,
 // 8-row groups 1024 bytes apart (stride byte offset), leading byte offset unused.
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
@@ -157,6 +163,9 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
 // 2D K-major BF16 tensor map: rows x cols (cols contiguous), box box_cols x box_rows,
 // 128-byte swizzle, zero fill out of bounds.
 bool make_map_bf16(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, uint32_t box_cols, uint32_t box_rows);
+
+// The same for FP16 elements.
+bool make_map_f16(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, uint32_t box_cols, uint32_t box_rows);
 
 // 2D FP32 tensor map (rows x cols, cols contiguous, row stride cols * 4 bytes), box
 // box_cols x box_rows, 128-byte swizzle (box_cols * 4 must be 128).

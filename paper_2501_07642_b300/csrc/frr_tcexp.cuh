@@ -15,6 +15,7 @@ struct TcExp {
     uint32_t rk[20];      // Philox round keys of the seed (philox_round_keys)
     float c_M;
     int n, n1, d, kb, nkb, nchunks, exact;
+    unsigned* hist0;      // NULL, or 4096 counters that also count bits [31:20] of each M_hat
     // failure-path test of the single-experiment launch only (zero otherwise): the covariate
     // tile producer issues nothing, and every bounded wait gives up after wait_cycles cycles
     int skip_tma;
