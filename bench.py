@@ -294,25 +294,31 @@ def run_frr(args):
     prim = ok[0]
     r = results[prim]
     n, d, n1 = w.n, w.d, w.n1
-    if prim == "split_bf16":
-        flops = 2.0 * 2.0 * n * d  # two BF16 parts, dense 0/1 x Zc per draw (multiply-add = 2)
-        achieved = flops * B / (r["ms_balance"] / 1e3) / 1e12
-        peak = peaks["bf16_tflops"]
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": tc_traffic(B), "kernel": "k_balance_tc", "peak_source": f"bf16_tflops (burst, {peak_kind})",
-                "flop_per_draw": flops}
-        dtype = "bf16"
-    else:
-        # plain ALU bound: n * d predicated FP32 adds per draw on 148 SMs x 128 lanes at the sampled SM clock
-        adds = float(n) * d
-        mhz = r["clocks"]["sm_mhz"] or peaks.get("sm_max_mhz", 2032.0)
-        peak = 148 * 128 * mhz * 1e6 / 1e12  # T adds/s
-        achieved = adds * B / (r["ms_balance"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s", "frac": achieved / peak,
+    f32_peak = fp32_lane_peak()
+
+    def roofline(path, res):
+        if path == "split_bf16":
+            flops = 2.0 * 2.0 * n * d  # two BF16 parts, dense 0/1 x Zc per draw (multiply-add = 2)
+            achieved = flops * B / (res["ms_balance"] / 1e3) / 1e12
+            peak = peaks["bf16_tflops"]
+            return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": tc_traffic(B), "kernel": "k_balance_tc",
+                    "peak_source": f"bf16_tflops (burst, {peak_kind})", "flop_per_draw": flops}
+        # FP32 CUDA-core path: the algorithmic work is n1 * d additions per draw (the treated rows;
+        # the kernel executes n * d predicated ones), against the FP32 lane rate measured with a
+        # cuBLAS FP32 GEMM in this run (one lane operation per multiply-add)
+        adds = float(n1) * d
+        achieved = adds * B / (res["ms_balance"] / 1e3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": f32_peak, "unit": "Tadd/s", "frac": achieved / f32_peak,
                 "traffic": None, "kernel": "k_balance_f32",
-                "peak_source": f"148 SMs x 128 FP32 lanes x median sampled SM clock {mhz} MHz",
-                "adds_per_draw": adds}
-        dtype = "f32"
+                "peak_source": "FP32 lane operations/s of a cuBLAS FP32 GEMM (8192^3, TF32 off), measured in this run",
+                "adds_per_draw": adds, "executed_adds_per_draw": float(n) * d,
+                "executed_frac": 2.0 * achieved / f32_peak}
+
+    roof = roofline(prim, r)
+    dtype = "bf16" if prim == "split_bf16" else "f32"
+    for p in ok:
+        results[p]["roofline"] = roofline(p, results[p])
     dist_line = distance_bench(peaks["bf16_tflops"]) if args.distance else None
     batch_line = batched_bench(args.batched_reps) if args.batched else None
     stream_line = stream_bench() if args.stream else None
@@ -331,7 +337,8 @@ def run_frr(args):
             "config": {"workload": WORKLOAD, "n": n, "n1": n1, "d": d, "draws_per_step": B, "q": q, "K": K,
                        "whiten": "ridge 0.1", "path": prim, "l2": "flushed (256 MiB write) between timed steps"},
             "paths": {p: ({k: results[p][k] for k in ("value", "ms_per_step", "ms_per_step_median", "ms_per_step_min",
-                                                       "ms_per_step_max", "ms_balance", "ms_select", "ms_recheck")}
+                                                       "ms_per_step_max", "ms_balance", "ms_select", "ms_recheck",
+                                                       "roofline")}
                           if "value" in results[p] else results[p])
                       for p in precisions},
             "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": LAUNCHES_PER_STEP * args.steps * ws,
@@ -341,6 +348,32 @@ def run_frr(args):
             "fast_distance": dist_line, "batched": batch_line, "stream": stream_line}
     print(json.dumps(line), flush=True)
 
+
+
+def fp32_lane_peak(size: int = 8192, reps: int = 5) -> float:
+    """FP32 lane operations per second (T/s) of this GPU, measured: a cuBLAS FP32 GEMM with TF32
+    off does one FP32 multiply-add per lane operation; best of `reps` after two warm-ups."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        a = torch.randn(size, size, device="cuda")
+        b = torch.randn(size, size, device="cuda")
+        for _ in range(2):
+            torch.mm(a, b)
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.mm(a, b)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b
+        torch.cuda.empty_cache()
+        return float(size) ** 3 / (best / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
 def distance_bench(peak_tflops: float, n: int = 16384, d: int = 768, reps: int = 5) -> dict:

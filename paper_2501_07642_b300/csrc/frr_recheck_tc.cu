@@ -13,10 +13,11 @@
 //
 // Work items of (128 candidates, 64 columns), 5 accumulators of 64 columns in TMEM each,
 // taken by persistent CTAs (one per SM at most).
-// Warps 0-7 epilogue (warp w: TMEM lanes 32 (w % 4) .., columns 32 (w / 4) .. of the item,
-// so two warps share each row and the integer epilogue runs on twice the warps), warp 8 TMA
-// (5 digit tiles per K block), warp 9 MMA, warps 10-13 expand the candidates' bit rows
-// (computed beforehand) into FP16 0/1 A tiles through a 256-entry byte table in shared memory.
+// Warps 0-15 epilogue (warp w: TMEM lanes 32 (w % 4) .., columns 16 (w / 4) .. of the item,
+// so four warps share each row and the integer epilogue runs on 16 warps), warp 16 TMA (5
+// digit tiles per K block, stacked into one 320-row B tile), warp 17 MMA (planes 0-3 in one
+// N = 256 MMA, plane 4 in an N = 64 MMA), warps 18-21 expand the candidates' bit rows
+// (computed beforehand) into FP16 0/1 A tiles with integer arithmetic.
 // The CTA that finishes the last column chunk of a candidate tile also adds up each
 // candidate's partial sums (in column order) into its M64.
 #include "frr_internal.cuh"
@@ -34,10 +35,22 @@ constexpr int kStB = 4, kStA = 2;
 constexpr int kPlaneBytes = kN * kKB * 2;          // 8 KiB
 constexpr int kBBytes = kPlanes * kPlaneBytes;     // 40 KiB
 constexpr int kABytes = kM * kKB * 2;              // 16 KiB
-constexpr int kEpiWarps = 8;   // two per TMEM lane quarter, one per 32-column half of an item
+constexpr int kEpiWarps = 16;  // four per TMEM lane quarter, one per 16-column quarter of an item
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kParts = 4;      // partial sums per (candidate, column chunk): one per column quarter
 constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1, kExpWarp0 = kEpiWarps + 2;
 constexpr int kThreads = (kExpWarp0 + 4) * 32;
-static_assert(kN == 64, "two epilogue warps per lane quarter, 32 columns each");
+static_assert(kN == 64 && kPlanes == 5, "16-column epilogue quarters; planes 0-3 in one N = 256 MMA");
+
+// Eight FP16 values 0.0 / 1.0 from the bits of byte x (bit i -> element i): y * 0x8001 puts
+// bits 0 and 1 of y at positions 0 and 16, and times 0x3C00 (FP16 1.0) makes them halves.
+__device__ __forceinline__ uint4 expand_byte_f16(uint32_t x)
+{
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w[q] = (((x >> (2 * q)) * 0x8001u) & 0x00010001u) * 0x3C00u;
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
 
 // Exact conversion of an integer-valued FP32 accumulator with |x| < 2^22: adding
 // 1.5 * 2^23 places the integer in the low mantissa bits.
@@ -109,14 +122,9 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
     __shared__ long long sQsum[kN];
     __shared__ int sQexp[kN];
     __shared__ int sLast;   // this CTA completed the last column chunk of the item's candidate tile
-    __shared__ uint4 sLut8[256];   // byte -> eight FP16 values 0.0 / 1.0 (bit i -> value i)
+    __shared__ double sSum[kParts - 1][kM];  // quarter sums of the M64 partial sums (last CTA)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid < 256) {
-        uint32_t h[8];
-        for (int i = 0; i < 8; ++i) h[i] = ((tid >> i) & 1) ? 0x3C00u : 0u;
-        sLut8[tid] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
-    }
     const int64_t C = C_dev ? std::min<int64_t>((int64_t)*C_dev, C_host) : C_host;  // within the buffers
     const int64_t T = (C + kM - 1) / kM;
     const int64_t items = T * ncb;
@@ -166,7 +174,9 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
         if (lane == 0) {
             bool ok = true;
             uint32_t ai = 0, bi = 0, it = 0;
-            const uint32_t idesc = idesc_f16(kM, kN);
+            // planes 0-3 (rows 0-255 of the stacked B tile) in one N = 256 MMA, plane 4 in an
+            // N = 64 MMA: the 0/1 A tile is read twice per K step instead of once per plane
+            const uint32_t idesc4 = idesc_f16(kM, 4 * kN), idesc1 = idesc_f16(kM, kN);
             for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
                 if (!(ok = wait_bar(acc_empty, (it & 1u) ^ 1u, sAbort, err, 16))) break;
                 tc_fence_after();
@@ -176,13 +186,13 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
                     if (!(ok = wait_bar(&b_full[sb], (bi / kStB) & 1u, sAbort, err, 13))) break;
                     tc_fence_after();
                     const uint64_t adesc = sdesc_sw128(smem_u32(sA + sa * kABytes));
+                    const uint64_t bdesc4 = sdesc_sw128(smem_u32(sB + sb * kBBytes));
+                    const uint64_t bdesc1 = sdesc_sw128(smem_u32(sB + sb * kBBytes + 4 * kPlaneBytes));
 #pragma unroll
-                    for (int pl = 0; pl < kPlanes; ++pl) {
-                        const uint64_t bdesc = sdesc_sw128(smem_u32(sB + sb * kBBytes + pl * kPlaneBytes));
-#pragma unroll
-                        for (int k = 0; k < kKB / 16; ++k)
-                            umma_bf16(tmem_base + (uint32_t)(pl * kN), adesc + 2u * k, bdesc + 2u * k, idesc,
-                                      (kb | k) != 0 ? 1u : 0u);
+                    for (int k = 0; k < kKB / 16; ++k) {
+                        umma_bf16(tmem_base, adesc + 2u * k, bdesc4 + 2u * k, idesc4, (kb | k) != 0 ? 1u : 0u);
+                        umma_bf16(tmem_base + (uint32_t)(4 * kN), adesc + 2u * k, bdesc1 + 2u * k, idesc1,
+                                  (kb | k) != 0 ? 1u : 0u);
                     }
                     umma_commit(&b_empty[sb]);
                     umma_commit(&a_empty[sa]);
@@ -213,7 +223,7 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const uint32_t x = (w2[q >> 2] >> (8 * (q & 3))) & 0xFFu;
-                    *reinterpret_cast<uint4*>(dst + ((q ^ (r & 7)) << 4)) = sLut8[x];
+                    *reinterpret_cast<uint4*>(dst + ((q ^ (r & 7)) << 4)) = expand_byte_f16(x);
                 }
                 fence_async_smem();
                 __syncwarp();
@@ -221,21 +231,21 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
             }
         }
     } else {
-        // epilogue: candidate row 32 (warp % 4) + lane, column half warp / 4 of the item
-        const int row = 32 * (warp & 3) + lane, half = warp >> 2;
+        // epilogue: candidate row 32 (warp % 4) + lane, column quarter warp / 4 of the item
+        const int row = 32 * (warp & 3) + lane, qtr = warp >> 2;
         uint32_t it = 0;
         bool ok = true;
         for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
             const int chunk = (int)(item / T);
             const int64_t cand = (item % T) * kM + row;
             // the chunk's column sums and scales (the previous item's readers are done first)
-            asm volatile("bar.sync 1, 256;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" :: "n"(kEpiThreads) : "memory");
             for (int t = tid; t < kN; t += 32 * kEpiWarps) {
                 const int col = chunk * kN + t;
                 sQsum[t] = col < d ? Qsum[col] : 0ll;
                 sQexp[t] = col < d ? qexp[col] : 0;
             }
-            asm volatile("bar.sync 1, 256;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" :: "n"(kEpiThreads) : "memory");
             if (!(ok = wait_bar(acc_full, it & 1u, sAbort, err, 15))) break;
             tc_fence_after();
             double psum = 0.0;
@@ -244,20 +254,21 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
             // integer; when n1 = n0 the complement (S_T -> S_all - S_T) gives exactly -N_j.
             // N_j 2^-q_j is rounded once to FP64 with integer instructions and squared into
             // the partial sum: one FP64 operation per column (B300's FP64 unit is narrow).
-            for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 32) {
-                long long S[32];
+            {
+                const int c0 = 16 * qtr;
+                long long S[16];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) S[j] = 0;
+                for (int j = 0; j < 16; ++j) S[j] = 0;
                 for (int pl = kPlanes - 1; pl >= 0; --pl) {
-                    uint32_t v[32];
-                    tmem_ld32(taddr + (uint32_t)(pl * kN + c0), v);
+                    uint32_t v[16];
+                    tmem_ld16(taddr + (uint32_t)(pl * kN + c0), v);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
+                    for (int j = 0; j < 16; ++j)
                         S[j] = S[j] * (1ll << kDigitBits) + (long long)acc_to_int(__uint_as_float(v[j]));
                 }
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
+                for (int j = 0; j < 16; ++j) {
                     const int col = chunk * kN + c0 + j;
                     if (col < d) {
                         const long long Q = sQsum[c0 + j];
@@ -275,30 +286,41 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty);
-            if (cand < C) part[(cand * ncb + chunk) * 2 + half] = psum;
+            if (cand < C) part[(cand * ncb + chunk) * kParts + qtr] = psum;
             // The CTA that completes the last of a tile's ncb column chunks sums each candidate's
             // 2 ncb partial sums in column order and forms M64 = sum / (n n1 n0): the writers
             // fence their partial sums before counting, the last one fences after (acquire).
-            asm volatile("bar.sync 1, 256;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" :: "n"(kEpiThreads) : "memory");
             if (tid == 0) {
                 __threadfence();
                 sLast = atomicAdd(&tile_done[item % T], 1) == ncb - 1;
             }
-            asm volatile("bar.sync 1, 256;" ::: "memory");
-            if (sLast && half == 0 && cand < C) {
+            asm volatile("bar.sync 1, %0;" :: "n"(kEpiThreads) : "memory");
+            if (sLast) {
+                // thread (row, quarter qtr) adds partial sums [qtr ncb, (qtr + 1) ncb) of the row's
+                // 4 ncb in column order, sixteen loads in flight; the quarters are then added in
+                // order, and M64 = sum / (n n1 n0)
                 __threadfence();
-                const double* pc = part + cand * (int64_t)(2 * ncb);
+                const int nparts = kParts * ncb;
+                const double* pc = part + cand * (int64_t)nparts;
                 double s = 0.0;
-                // eight independent loads in flight, then added in column order
-                for (int b0 = 0; b0 < 2 * ncb; b0 += 8) {
-                    double v[8];
+                if (cand < C) {
+                    for (int b0 = qtr * ncb; b0 < (qtr + 1) * ncb; b0 += 16) {
+                        double v[16];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) v[u] = b0 + u < 2 * ncb ? __ldcg(pc + b0 + u) : 0.0;
+                        for (int u = 0; u < 16; ++u) v[u] = b0 + u < (qtr + 1) * ncb ? __ldcg(pc + b0 + u) : 0.0;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        if (b0 + u < 2 * ncb) s = __dadd_rn(s, v[u]);
+                        for (int u = 0; u < 16; ++u)
+                            if (b0 + u < (qtr + 1) * ncb) s = __dadd_rn(s, v[u]);
+                    }
                 }
-                M64[cand] = __ddiv_rn(__dmul_rn(1.0, s), denom);
+                if (qtr > 0) sSum[qtr - 1][row] = s;
+                asm volatile("bar.sync 1, %0;" :: "n"(kEpiThreads) : "memory");
+                if (qtr == 0 && cand < C) {
+#pragma unroll
+                    for (int q = 0; q < kParts - 1; ++q) s = __dadd_rn(s, sSum[q][row]);
+                    M64[cand] = __ddiv_rn(__dmul_rn(1.0, s), denom);
+                }
             }
         }
     }
@@ -323,7 +345,7 @@ frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint
     const int ncb = ceil_div(ctx->d, kN);
     const int64_t tiles = (count + kM - 1) / kM;
     const size_t rows_bytes = ((size_t)count * W * sizeof(uint32_t) + 255) & ~size_t(255);
-    const size_t part_bytes = ((size_t)count * ncb * 2 * sizeof(double) + 255) & ~size_t(255);
+    const size_t part_bytes = ((size_t)count * ncb * kParts * sizeof(double) + 255) & ~size_t(255);
     const size_t ctr_bytes = (size_t)tiles * sizeof(int);
     FRR_TRY(ensure_device(ctx, &ctx->misc2, &ctx->misc2_bytes, rows_bytes + part_bytes + ctr_bytes));
     uint32_t* rows = static_cast<uint32_t*>(ctx->misc2);
