@@ -32,8 +32,8 @@ import numpy as np
 
 ROOT = Path(__file__).resolve().parent
 # library kernels per frr_select step of the precision workload (one chunk): k_sel_init,
-# k_balance_tc, k_sel_cut (one 8-CTA cluster), k_bits, k_recheck_tc, k_finish
-LAUNCHES_PER_STEP = 6
+# k_balance_tc, k_sel_level1, k_sel_keep, k_bits, k_recheck_tc, k_finish
+LAUNCHES_PER_STEP = 7
 sys.path.insert(0, str(ROOT))
 
 METRIC = "balance-checked assignments/s at n=d=1000; split-BF16 vs FP32 path, same B300"
@@ -294,7 +294,7 @@ def run_frr(args):
     prim = ok[0]
     r = results[prim]
     n, d, n1 = w.n, w.d, w.n1
-    f32_peak = fp32_lane_peak()
+    f32_peak = fp32_lane_peak() if "f32" in ok else None
 
     def roofline(path, res):
         if path == "split_bf16":

@@ -110,7 +110,7 @@ template <int KB>
 frr_status launch_kb(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout)
 {
     const size_t smem = 32 * 32 * sizeof(float4) + (size_t)TD * (4 * KB + 1) * sizeof(uint32_t);
-    FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_balance_f32<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FRR_CUDA_TRY(ctx, set_smem_limit(k_balance_f32<KB>, (int)smem, ctx->device));
     const uint64_t tiles = (B + TD - 1) / TD;
     k_balance_f32<KB><<<(unsigned)tiles, NT, smem, ctx->stream>>>(ctx->Z32, ctx->dpad32, ctx->kused, (int)ctx->n,
                                                                   (int)ctx->n1, (float)ctx->c_M, seed, exact ? 1 : 0,

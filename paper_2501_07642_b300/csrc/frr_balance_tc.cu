@@ -354,12 +354,10 @@ frr_status launch(frr_ctx* ctx, cudaStream_t stream, int num_sms, const TcExp& o
     const size_t smem = smem_bytes(KB, SB);
     const unsigned grid = (unsigned)(tiles < (unsigned long long)num_sms ? tiles : (unsigned long long)num_sms);
     if (table == nullptr) {
-        FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_balance_tc<KB, SB, NG, false>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FRR_CUDA_TRY(ctx, set_smem_limit(k_balance_tc<KB, SB, NG, false>, (int)smem, ctx->device));
         k_balance_tc<KB, SB, NG, false><<<grid, (6 + kExpWarps + NG) * 32, smem, stream>>>(one, table, prefix, E, tiles, err);
     } else {
-        FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_balance_tc<KB, SB, NG, true>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FRR_CUDA_TRY(ctx, set_smem_limit(k_balance_tc<KB, SB, NG, true>, (int)smem, ctx->device));
         k_balance_tc<KB, SB, NG, true><<<grid, (6 + kExpWarps + NG) * 32, smem, stream>>>(one, table, prefix, E, tiles, err);
     }
     FRR_CUDA_TRY(ctx, cudaGetLastError());

@@ -4,7 +4,10 @@
 #include "frr_internal.cuh"
 
 #include <mutex>
+#include <string>
 #include <unordered_map>
+
+#include <cstdio>
 
 #include <chrono>
 #include <new>
@@ -20,6 +23,26 @@ bool is_device_ptr(const void* p)
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t set_smem_limit(const void* fn, int bytes, int device)
+{
+    static std::mutex mu;
+    static std::unordered_map<std::string, int> done;
+    char key[64];
+    snprintf(key, sizeof(key), "%p/%d", fn, device);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = done.find(key);
+        if (it != done.end() && it->second >= bytes) return cudaSuccess;
+    }
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(mu);
+        int& v = done[key];
+        if (v < bytes) v = bytes;
+    }
+    return e;
 }
 
 frr_status ensure_device(frr_ctx* ctx, void** buf, size_t* cap_bytes, size_t bytes)

@@ -162,6 +162,15 @@ inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_
 // true if p is device-accessible memory (device or managed); false for pageable / pinned host
 bool is_device_ptr(const void* p);
 
+// cudaFuncSetAttribute(fn, MaxDynamicSharedMemorySize, bytes) once per (kernel, device, size):
+// the attribute belongs to the function, so repeating it at every launch only costs host time
+cudaError_t set_smem_limit(const void* fn, int bytes, int device);
+template <typename... P>
+inline cudaError_t set_smem_limit(void (*kernel)(P...), int bytes, int device)
+{
+    return set_smem_limit(reinterpret_cast<const void*>(kernel), bytes, device);
+}
+
 // stream-ordered memory pool of the library for short-lived temporaries on `device`; it keeps
 // up to 2 GiB reserved between calls instead of returning it at every synchronisation (a
 // 256-experiment batch prepares with about 1.2 GB of temporaries)

@@ -359,7 +359,7 @@ frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint
         ctx->qmap_ready = true;
     }
     const size_t smem = rc_smem_bytes();
-    FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_recheck_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FRR_CUDA_TRY(ctx, set_smem_limit(k_recheck_tc, (int)smem, ctx->device));
     const int64_t items = (int64_t)((count + kM - 1) / kM) * ncb;
     const unsigned grid = (unsigned)std::min<int64_t>(items, ctx->num_sms);
     // the partial sums hold (N_j 2^-q_j)^2 = (n1 n0 Delta_j)^2, and M = (n1 n0 / n) sum Delta_j^2

@@ -1236,7 +1236,7 @@ frr_status stream_end_enqueue(frr_ctx* ctx, uint64_t* keys_out, double* M64_out,
         if (one_cta) {
             // M64 patterns, indices, flags, packed accepted indices and patterns (147 KiB)
             const size_t smem = (size_t)kFinMax * (4 * sizeof(unsigned long long) + sizeof(int));
-            FRR_CUDA_TRY(ctx, cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            FRR_CUDA_TRY(ctx, set_smem_limit(k_finish, (int)smem, ctx->device));
             FRR_CUDA_TRY(ctx, launch_pdl(k_finish, 1, kFinThreads, smem, ctx->stream, (const double*)m64,
                                          (const uint64_t*)ctx->ret_idx[cur], (const float*)ctx->ret_m[cur], rb, r_dev,
                                          (long long)st.K, st.q_mode ? 1 : 0, thr_bits, cut_params(ctx),
