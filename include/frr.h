@@ -371,10 +371,10 @@ frr_status frr_diagnose(const frr_diag_in* in, frr_diag_out* out);
  * D[i * m + j] = ||X_i - Y_j||_2 for the rows of X (n x d) and Y (m x d), row-major FP32,
  * or its square when squared != 0. Y == NULL means Y = X (m is then ignored). X, Y and
  * D_out may each be host or device memory; the call returns when D_out is written. Work
- * runs on cuda_stream (NULL = the default stream). The split operands ((n + m) * 6 dp
- * bytes) come from a memory pool the library keeps per device, which retains its largest
- * footprint for later calls until the process exits; other temporaries (copies of host
- * inputs, a device staging copy of a host D_out) are freed before the call returns.
+ * runs on cuda_stream (NULL = the default stream). Every temporary -- the split operands
+ * ((n + m) * 6 dp bytes), the norms, and for host buffers the device copies of X, Y and D_out
+ * -- comes from a memory pool the library keeps per device, which retains its largest
+ * footprint for later calls until the process exits.
  * The cross term runs on the tensor cores with each value split into two BF16 parts and
  * FP32 accumulation; the squared norms are compensated sums rounded once to FP32.
  * |D^2 - exact| <= (3 * 2^-18 + (3 dp + 4) * 2^-24) (||X_i||^2 + ||Y_j||^2) with dp = d

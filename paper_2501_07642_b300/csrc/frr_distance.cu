@@ -59,32 +59,67 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     e = (a - (s - bb)) + (b - bb);
 }
 
-// Split rows of V (rows x d FP32) into the K-major BF16 operand (rows x 3 dp) and the
-// squared norms; one warp per row. layout 0: [h | h | l] (A side), layout 1: [h | l | h]
-// (B side).
-__global__ void __launch_bounds__(256) k_dist_prep(const float* __restrict__ V, int64_t rows, int d, int dp,
-                                                   int layout, __nv_bfloat16* __restrict__ out,
-                                                   float* __restrict__ norm2)
+// Split rows into the K-major BF16 operands (rows x 3 dp) and the squared norms, one warp
+// per row: rows [0, n) of X into A with layout [h | h | l], rows [0, m) of Y into B with
+// layout [h | l | h]; lane l handles elements 4l + 128 i (four per 16-byte load when the
+// rows are 16-byte aligned). The same launch zeroes the column norms' padding [m, mpad)
+// and the error word, so a call needs no memsets.
+// BF16 parts h = bf16(x), l = bf16(x - h) of four values, packed as two 8-byte words
+__device__ __forceinline__ void split4(const float (&x)[4], uint2& hw, uint2& lw)
 {
-    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    __nv_bfloat16 h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        h[q] = __float2bfloat16_rn(x[q]);
+        l[q] = __float2bfloat16_rn(x[q] - __bfloat162float(h[q]));
+    }
+    memcpy(&hw, h, 8);
+    memcpy(&lw, l, 8);
+}
+
+__global__ void __launch_bounds__(256) k_dist_prep(const float* __restrict__ X, int64_t n, const float* __restrict__ Y,
+                                                   int64_t m, int64_t mpad, int d, int dp, int vec,
+                                                   __nv_bfloat16* __restrict__ A, __nv_bfloat16* __restrict__ B,
+                                                   float* __restrict__ nx, float* __restrict__ ny, int* __restrict__ err)
+{
+    const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (r >= rows) return;
-    const float* v = V + r * (int64_t)d;
-    __nv_bfloat16* o = out + r * (int64_t)(3 * dp);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *err = 0;
+    if (w >= n + m) {
+        // the padding of the column norms, one entry per thread of the trailing blocks
+        const int64_t pidx = m + (w - n - m) * 32 + lane;
+        if (pidx < mpad) ny[pidx] = 0.0f;
+        return;
+    }
+    const bool side_b = w >= n;
+    const int64_t r = side_b ? w - n : w;
+    const float* v = (side_b ? Y : X) + r * (int64_t)d;
+    __nv_bfloat16* o = (side_b ? B : A) + r * (int64_t)(3 * dp);
     float s = 0.f, c = 0.f;
-    for (int k = lane; k < dp; k += 32) {
-        const float x = k < d ? v[k] : 0.0f;
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-        o[k] = h;
-        o[dp + k] = layout == 0 ? h : l;
-        o[2 * dp + k] = layout == 0 ? l : h;
-        const float p = x * x;
-        const float pe = fmaf(x, x, -p);
-        float t, q;
-        two_sum(s, p, t, q);
-        s = t;
-        c += q + pe;
+    for (int k = 4 * lane; k < dp; k += 128) {
+        float x[4];
+        if (vec && k + 4 <= d) {
+            const float4 t = *reinterpret_cast<const float4*>(v + k);
+            x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = k + q < d ? v[k + q] : 0.0f;
+        }
+        // [h | h | l] for X, [h | l | h] for Y
+        uint2 hw, lw;
+        split4(x, hw, lw);
+        *reinterpret_cast<uint2*>(o + k) = hw;
+        *reinterpret_cast<uint2*>(o + dp + k) = side_b ? lw : hw;
+        *reinterpret_cast<uint2*>(o + 2 * dp + k) = side_b ? hw : lw;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float p = x[q] * x[q];
+            const float pe = fmaf(x[q], x[q], -p);
+            float t, e;
+            two_sum(s, p, t, e);
+            s = t;
+            c += e + pe;
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -95,7 +130,7 @@ __global__ void __launch_bounds__(256) k_dist_prep(const float* __restrict__ V, 
         s = t;
         c += co + q;
     }
-    if (lane == 0) norm2[r] = s + c;
+    if (lane == 0) (side_b ? ny : nx)[r] = s + c;
 }
 
 __device__ __forceinline__ void dist_tile_of(uint64_t t, int ntn, int ntm, int& tm, int& tn)
@@ -356,48 +391,53 @@ extern "C" frr_status frr_fast_distance(const float* X, int64_t n, const float* 
 
     const int dp = (int)((d + kDK - 1) / kDK) * kDK;
     const int64_t kp = 3ll * dp;
+    // every temporary comes from the library's per-device pool, which keeps its memory
+    // mapped between calls (a pool that returns it at each synchronisation maps it again on
+    // the next call)
+    cudaMemPool_t pool = dist_pool(dev);
+    if (pool == nullptr) return FRR_E_CUDA;
     DevBuf xin, yin, A, B, nX, nY, Dd, errb;
     const float* Xd = X;
     const float* Yd = Y;
     if (!is_device_ptr(X)) {
-        FRR_TRY(dist_alloc(xin, (size_t)n * d * sizeof(float), s));
+        FRR_TRY(dist_alloc(xin, (size_t)n * d * sizeof(float), s, pool));
         DIST_CUDA(cudaMemcpyAsync(xin.p, X, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, s));
         Xd = static_cast<const float*>(xin.p);
     }
     if (Y == nullptr) {
         Yd = Xd;
     } else if (!is_device_ptr(Y)) {
-        FRR_TRY(dist_alloc(yin, (size_t)m * d * sizeof(float), s));
+        FRR_TRY(dist_alloc(yin, (size_t)m * d * sizeof(float), s, pool));
         DIST_CUDA(cudaMemcpyAsync(yin.p, Y, (size_t)m * d * sizeof(float), cudaMemcpyHostToDevice, s));
         Yd = static_cast<const float*>(yin.p);
     }
-    cudaMemPool_t pool = dist_pool(dev);
-    if (pool == nullptr) return FRR_E_CUDA;
     FRR_TRY(dist_alloc(A, (size_t)n * kp * 2, s, pool));
     FRR_TRY(dist_alloc(B, (size_t)m * kp * 2, s, pool));
-    FRR_TRY(dist_alloc(nX, (size_t)n * sizeof(float), s));
+    FRR_TRY(dist_alloc(nX, (size_t)n * sizeof(float), s, pool));
     const int64_t mpad = (m + kDN - 1) / kDN * kDN;   // column norms padded with zeros to whole tiles
-    FRR_TRY(dist_alloc(nY, (size_t)mpad * sizeof(float), s));
-    DIST_CUDA(cudaMemsetAsync(nY.p, 0, (size_t)mpad * sizeof(float), s));
-    FRR_TRY(dist_alloc(errb, sizeof(int), s));
+    FRR_TRY(dist_alloc(nY, (size_t)mpad * sizeof(float), s, pool));
+    FRR_TRY(dist_alloc(errb, sizeof(int), s, pool));
     float* Dw = D_out;
     const bool dev_out = is_device_ptr(D_out);
     if (!dev_out) {
-        FRR_TRY(dist_alloc(Dd, (size_t)n * m * sizeof(float), s));
+        FRR_TRY(dist_alloc(Dd, (size_t)n * m * sizeof(float), s, pool));
         Dw = static_cast<float*>(Dd.p);
     }
-    DIST_CUDA(cudaMemsetAsync(errb.p, 0, sizeof(int), s));
-
-    k_dist_prep<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(Xd, n, (int)d, dp, 0, static_cast<__nv_bfloat16*>(A.p),
-                                                       static_cast<float*>(nX.p));
-    k_dist_prep<<<(unsigned)((m + 7) / 8), 256, 0, s>>>(Yd, m, (int)d, dp, 1, static_cast<__nv_bfloat16*>(B.p),
-                                                       static_cast<float*>(nY.p));
+    // one launch splits both operands, zeroes the norm padding and the error word
+    const int vec = ((d & 3) == 0 && (reinterpret_cast<uintptr_t>(Xd) & 15u) == 0 &&
+                     (reinterpret_cast<uintptr_t>(Yd) & 15u) == 0) ? 1 : 0;
+    const int64_t prep_warps = n + m + (mpad - m + 31) / 32;
+    k_dist_prep<<<(unsigned)((prep_warps + 7) / 8), 256, 0, s>>>(Xd, n, Yd, m, mpad, (int)d, dp, vec,
+                                                                static_cast<__nv_bfloat16*>(A.p),
+                                                                static_cast<__nv_bfloat16*>(B.p),
+                                                                static_cast<float*>(nX.p), static_cast<float*>(nY.p),
+                                                                static_cast<int*>(errb.p));
     DIST_CUDA(cudaGetLastError());
 
     CUtensorMap mapA, mapB, mapD;
     if (!make_map_bf16(&mapA, A.p, (uint64_t)kp, (uint64_t)n, kDK, kDM)) return FRR_E_CUDA;
     if (!make_map_bf16(&mapB, B.p, (uint64_t)kp, (uint64_t)m, kDK, kDN)) return FRR_E_CUDA;
-    DIST_CUDA(cudaFuncSetAttribute(k_distance_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDSmem));
+    DIST_CUDA(set_smem_limit(k_distance_tc, (int)kDSmem, dev));
     const uint64_t tiles = (uint64_t)((n + kDM - 1) / kDM) * (uint64_t)((m + kDN - 1) / kDN);
     const unsigned grid = (unsigned)(tiles < (uint64_t)sms ? tiles : (uint64_t)sms);
     // 16-byte row stores, and TMA stores, need m % 4 == 0 and a 16-byte aligned output
