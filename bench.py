@@ -49,22 +49,25 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 10 ms while the steps run. The sampler
+    is started (and its first sample awaited) before the warm-up; summary() keeps the samples
+    taken inside [t0, t1] (wall clock), or all of them when none falls inside."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
         self.tmp = None
+        self.window = None
 
     def __enter__(self):
         self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=self.tmp, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -74,8 +77,12 @@ class ClockSampler:
             self.tmp.flush()
             if Path(self.tmp.name).stat().st_size > 0:
                 break
-            time.sleep(0.02)
+            time.sleep(0.01)
         return self
+
+    def mark(self, t0: float, t1: float):
+        """Wall-clock window (time.time()) of the timed steps."""
+        self.window = (t0, t1)
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -87,22 +94,36 @@ class ClockSampler:
         self.tmp.flush()
 
     def summary(self) -> dict:
+        import datetime
         rows = []
         try:
             for line in Path(self.tmp.name).read_text().splitlines():
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
+                if len(parts) >= 10:
                     rows.append(parts)
         finally:
             os.unlink(self.tmp.name)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+
+        def stamp(r):
+            try:
+                return datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                return None
+
+        inside = rows
+        if self.window is not None:
+            lo, hi = self.window
+            w = [r for r in rows if (t := stamp(r)) is not None and lo - 0.005 <= t <= hi + 0.005]
+            if w:
+                inside = w
+        sm = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in inside if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[6 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "samples_in_timed_steps": len(inside) if inside is not rows else 0}
 
 
 def _dist():
@@ -224,11 +245,12 @@ def run_frr(args):
         torch.cuda.synchronize()
         with ClockSampler(torch.cuda.current_device()) as clk:
             t_wall = time.perf_counter()
-            # W warm-up steps, repeated until the clock sampler has seen at least 0.3 s of this
-            # load (the timed steps alone take tens of milliseconds)
             n_warm = args.warmup
             i = 0
+            t_timed0 = None
             while i < n_warm + args.steps:
+                if i == n_warm:
+                    t_timed0 = time.time()
                 with torch.cuda.stream(stream):
                     flush.zero_()  # L2 flush between steps, outside the timed events
                     ev0.record(stream)
@@ -238,9 +260,6 @@ def run_frr(args):
                     ev1.record(stream)
                 ev1.synchronize()
                 i += 1
-                if i == n_warm and time.perf_counter() - t_wall < 0.3:
-                    n_warm += 1
-                    continue
                 if i > n_warm:
                     step_ms.append(ev0.elapsed_time(ev1))
                     stt = frr.frr_last_stats(ctx)
@@ -248,6 +267,7 @@ def run_frr(args):
                     sel_ms.append(stt["ms_select"])
                     rck_ms.append(stt["ms_recheck"])
             torch.cuda.synchronize()
+            clk.mark(t_timed0, time.time())
             wall = time.perf_counter() - t_wall
         stats = frr.frr_last_stats(ctx)
         total_ms = sum(step_ms)
@@ -342,7 +362,7 @@ def run_frr(args):
                           if "value" in results[p] else results[p])
                       for p in precisions},
             "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": LAUNCHES_PER_STEP * args.steps * ws,
-            "clocks": {k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "clocks": {k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples", "samples_in_timed_steps")},
             "selection": {k: r["stats"][k] for k in ("candidates", "accepted", "max_rel_err", "max_err_over_band",
                                                      "band_violations", "parity_at_risk")},
             "fast_distance": dist_line, "batched": batch_line, "stream": stream_line}

@@ -518,6 +518,7 @@ k_finish(const double* __restrict__ m64, const uint64_t* __restrict__ idx, const
     int viol = 0;
 #pragma unroll
     for (int m = 0; m < kFinPer; ++m) {
+        if (m * kFinThreads >= r) break;  // the same for the whole block
         const int c = tid + m * kFinThreads;
         key[m] = ~0ull;
         if (c < r) {
@@ -631,6 +632,7 @@ k_finish(const double* __restrict__ m64, const uint64_t* __restrict__ idx, const
     int below = 0;
 #pragma unroll
     for (int m = 0; m < kFinPer; ++m) {
+        if (m * kFinThreads >= r) break;  // the same for the whole block
         const int c = tid + m * kFinThreads;
         if (c < r) {
             const bool lt = q_mode ? key[m] < thr : (thr_bits >= 0 && key[m] <= thr);
@@ -656,6 +658,7 @@ k_finish(const double* __restrict__ m64, const uint64_t* __restrict__ idx, const
     unsigned long long above = ~0ull;
 #pragma unroll
     for (int m = 0; m < kFinPer; ++m) {
+        if (m * kFinThreads >= r) break;  // the same for the whole block
         const int c = tid + m * kFinThreads;
         if (c < r && key[m] > thr && key[m] < above) above = key[m];
     }
