@@ -16,17 +16,20 @@ namespace frr {
 constexpr int kMaxN = 2048;
 constexpr int kExactMaxN = 63;
 
-// Fixed-point scale for the exact-sum recheck: |Q_ij| <= 2^kQBits, so sums over
-// at most 2^12 units stay below 2^62.
-constexpr int kQBits = 50;
+// Fixed-point scale for the exact-sum recheck: |Q_ij| <= 2^kQBits (the rounding of Zc to Q
+// then moves a column sum by at most n 2^-kQBits times the column's largest magnitude),
+// and sums over at most 2^12 units stay below 2^58.
+constexpr int kQBits = 46;
 
 // The fixed-point covariates of the exact recheck are written in kDigitPlanes balanced digits
 // of kDigitBits bits, Q = sum_k D_k 2^(kDigitBits k) with D_k in [-2^(kDigitBits-1),
-// 2^(kDigitBits-1)), each plane stored in FP16 (integers up to 2^11 are exact in FP16). Five
-// 11-bit digits cover |Q| <= 2^kQBits; a plane's sum over <= 2048 treated units stays below
-// 2^21 in magnitude, so FP32 accumulation of it is exact.
-constexpr int kDigitPlanes = 5;
-constexpr int kDigitBits = 11;
+// 2^(kDigitBits-1)), each plane stored in FP16 (every integer of magnitude <= 2^11 is exact in
+// FP16, so 12-bit balanced digits are). Four 12-bit digits cover |Q| <= 2^kQBits; a plane's
+// sum over <= 2047 treated units stays below 2047 * 2^11 < 2^22 in magnitude, so FP32
+// accumulation of it is exact in any order. Four planes of a 64-column chunk make one
+// 256-row B tile: one N = 256 MMA per K step.
+constexpr int kDigitPlanes = 4;
+constexpr int kDigitBits = 12;
 static_assert(kDigitPlanes * kDigitBits >= kQBits + 2, "digit planes cover the fixed-point range");
 
 // Fluctuation multiplier of the accumulation term of the error band (number of

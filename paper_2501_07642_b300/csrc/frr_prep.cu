@@ -582,7 +582,7 @@ __global__ void k_derive(PJ_ARGS)
     }
 }
 
-// Balanced base-2048 digits of Q: Q = sum_{k<5} q_k 2048^k with q_k in [-1024, 1023], plane
+// Balanced base-4096 digits of Q: Q = sum_{k<4} q_k 4096^k with q_k in [-2048, 2047], plane
 // k stored K-major as FP16 (integers of this size are exact): Zq[(k d + j) kpad + p].
 __global__ void k_digits(PJ_ARGS)
 {

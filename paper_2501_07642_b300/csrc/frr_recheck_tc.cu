@@ -1,23 +1,23 @@
 // frr_recheck_tc.cu -- exact-sum recheck of candidate draws on the tensor cores.
 //
 // The accepted set is decided on M computed from exact treated sums S_T,j =
-// sum_{i in T} Q_ij of the fixed-point covariates Q = round(Zc 2^qexp) (|Q| <= 2^50).
-// Q is written in balanced base-2048 digits, Q = sum_{k<5} q_k 2048^k with q_k in
-// [-1024, 1023], each digit plane stored in FP16 (exact). For a 0/1 assignment row w
-// (FP16 ones), D_k = sum_i w_i q_k(i) is an integer of magnitude at most 2^21, so the
+// sum_{i in T} Q_ij of the fixed-point covariates Q = round(Zc 2^qexp) (|Q| <= 2^46).
+// Q is written in balanced base-4096 digits, Q = sum_{k<4} q_k 4096^k with q_k in
+// [-2048, 2047], each digit plane stored in FP16 (exact). For a 0/1 assignment row w
+// (FP16 ones), D_k = sum_i w_i q_k(i) is an integer of magnitude below 2^22, so the
 // tensor cores' FP32 accumulation of the digit products is exact, and
-// S_T = sum_k D_k 2048^k is rebuilt exactly in int64 (Horner). The epilogue then forms, per column, the exact
+// S_T = sum_k D_k 4096^k is rebuilt exactly in int64 (Horner). The epilogue then forms, per column, the exact
 // 128-bit integer N_j = S_T n - S_all n1 = n1 n0 Delta_j 2^q_j (an assignment and its
 // complement give -N_j when n1 = n0), rounds N_j 2^-q_j once to FP64 and adds its square
 // to the CTA's partial sum; M64 = sum / (n n1 n0).
 //
-// Work items of (128 candidates, 64 columns), 5 accumulators of 64 columns in TMEM each,
+// Work items of (128 candidates, 64 columns), 4 accumulators of 64 columns in TMEM each,
 // taken by persistent CTAs (one per SM at most).
 // Warps 0-15 epilogue (warp w: TMEM lanes 32 (w % 4) .., columns 16 (w / 4) .. of the item,
-// so four warps share each row and the integer epilogue runs on 16 warps), warp 16 TMA (5
-// digit tiles per K block, stacked into one 320-row B tile), warp 17 MMA (planes 0-3 in one
-// N = 256 MMA, plane 4 in an N = 64 MMA), warps 18-21 expand the candidates' bit rows
-// (computed beforehand) into FP16 0/1 A tiles with integer arithmetic.
+// so four warps share each row and the integer epilogue runs on 16 warps), warp 16 TMA (4
+// digit tiles per K block, stacked into one 256-row B tile), warp 17 MMA (all four planes in
+// one N = 256 MMA per K step of 16), warps 18-21 expand the candidates' bit rows (computed
+// beforehand) into FP16 0/1 A tiles with integer arithmetic.
 // The CTA that finishes the last column chunk of a candidate tile also adds up each
 // candidate's partial sums (in column order) into its M64.
 #include "frr_internal.cuh"
@@ -33,14 +33,14 @@ namespace {
 constexpr int kM = 128, kN = 64, kPlanes = kDigitPlanes, kKB = 64;
 constexpr int kStB = 4, kStA = 2;
 constexpr int kPlaneBytes = kN * kKB * 2;          // 8 KiB
-constexpr int kBBytes = kPlanes * kPlaneBytes;     // 40 KiB
+constexpr int kBBytes = kPlanes * kPlaneBytes;     // 32 KiB
 constexpr int kABytes = kM * kKB * 2;              // 16 KiB
 constexpr int kEpiWarps = 16;  // four per TMEM lane quarter, one per 16-column quarter of an item
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kParts = 4;      // partial sums per (candidate, column chunk): one per column quarter
 constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1, kExpWarp0 = kEpiWarps + 2;
 constexpr int kThreads = (kExpWarp0 + 4) * 32;
-static_assert(kN == 64 && kPlanes == 5, "16-column epilogue quarters; planes 0-3 in one N = 256 MMA");
+static_assert(kN == 64 && kPlanes * kN == 256, "16-column epilogue quarters; the four planes in one N = 256 MMA");
 
 // Eight FP16 values 0.0 / 1.0 from the bits of byte x (bit i -> element i): y * 0x8001 puts
 // bits 0 and 1 of y at positions 0 and 16, and times 0x3C00 (FP16 1.0) makes them halves.
@@ -174,9 +174,9 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
         if (lane == 0) {
             bool ok = true;
             uint32_t ai = 0, bi = 0, it = 0;
-            // planes 0-3 (rows 0-255 of the stacked B tile) in one N = 256 MMA, plane 4 in an
-            // N = 64 MMA: the 0/1 A tile is read twice per K step instead of once per plane
-            const uint32_t idesc4 = idesc_f16(kM, 4 * kN), idesc1 = idesc_f16(kM, kN);
+            // the four planes (rows 0-255 of the stacked B tile) in one N = 256 MMA: the 0/1 A
+            // tile is read once per K step
+            const uint32_t idesc4 = idesc_f16(kM, kPlanes * kN);
             for (int64_t item = blockIdx.x; item < items && ok; item += gridDim.x, ++it) {
                 if (!(ok = wait_bar(acc_empty, (it & 1u) ^ 1u, sAbort, err, 16))) break;
                 tc_fence_after();
@@ -187,13 +187,9 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
                     tc_fence_after();
                     const uint64_t adesc = sdesc_sw128(smem_u32(sA + sa * kABytes));
                     const uint64_t bdesc4 = sdesc_sw128(smem_u32(sB + sb * kBBytes));
-                    const uint64_t bdesc1 = sdesc_sw128(smem_u32(sB + sb * kBBytes + 4 * kPlaneBytes));
 #pragma unroll
-                    for (int k = 0; k < kKB / 16; ++k) {
+                    for (int k = 0; k < kKB / 16; ++k)
                         umma_bf16(tmem_base, adesc + 2u * k, bdesc4 + 2u * k, idesc4, (kb | k) != 0 ? 1u : 0u);
-                        umma_bf16(tmem_base + (uint32_t)(4 * kN), adesc + 2u * k, bdesc1 + 2u * k, idesc1,
-                                  (kb | k) != 0 ? 1u : 0u);
-                    }
                     umma_commit(&b_empty[sb]);
                     umma_commit(&a_empty[sa]);
                 }

@@ -250,7 +250,10 @@ def frr_select(ctx: Context, seed: int, first_draw: int, B: int, q=None, thresho
     K = ctypes.c_int64()
     _check(lib().frr_select(ctx.handle, seed, first_draw, B, qq, tt, _ptr(keys), _ptr(m64), cap, ctypes.byref(K)),
            "frr_select")
-    return keys[:K.value], m64[:K.value]
+    k = K.value
+    if k == len(keys) and k == len(m64):
+        return keys, m64  # already exactly K long (slicing a device tensor costs microseconds)
+    return keys[:k], m64[:k]
 
 
 def frr_stream_begin(ctx: Context, seed: int, B_total: int, q=None, threshold=None):

@@ -218,15 +218,26 @@ def test_select_monte_carlo_workload(precision):
 
 
 def test_select_threshold_mode():
+    """Threshold mode (Sec. 2.2 with a fixed acceptance threshold a) accepts the draws with
+    M <= a. Against itself: a = the K-th accepted M64 of q mode gives the same draws. Against
+    the oracle: a lies midway between two consecutive oracle M values, so the two sides agree
+    however the last bits of M round (a threshold equal to some draw's M would not)."""
     w = workload("mc_n100_d100")
     X = w.covariates()
+    B, K = 50_000, 500
+    _, _, M = _oracle_select(X, w.n1, w.whiten, 1, 0, B, q=0.01)
+    Ms = np.sort(M)
+    assert Ms[K] - Ms[K - 1] > 1e-9 * Ms[K]
+    a_mid = float(0.5 * (Ms[K - 1] + Ms[K]))
     with _ctx(X, w.n1, "f32", w.whiten) as ctx:
-        k1, m1 = frr.frr_select(ctx, 1, 0, 50_000, q=0.01)
-        a = float(np.max(m1))
-        k2, m2 = frr.frr_select(ctx, 1, 0, 50_000, threshold=a)
-    assert np.array_equal(k1, k2)
-    wk, _, _ = _oracle_select(X, w.n1, w.whiten, 1, 0, 50_000, threshold=a)
-    assert np.array_equal(k2, wk)
+        k1, m1 = frr.frr_select(ctx, 1, 0, B, q=0.01)
+        k2, m2 = frr.frr_select(ctx, 1, 0, B, threshold=float(np.max(m1)))
+        k3, m3 = frr.frr_select(ctx, 1, 0, B, threshold=a_mid)
+    assert len(k1) == K and np.array_equal(k1, k2)
+    wk, wm = O.select_from_M(M, 0, threshold=a_mid)
+    assert len(wk) == K
+    assert np.array_equal(k3, wk)
+    assert np.allclose(m3, wm, rtol=REL_M64, atol=0)
 
 
 @pytest.mark.parametrize("mode", ["q", "threshold"])
