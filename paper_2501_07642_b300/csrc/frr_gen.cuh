@@ -91,6 +91,27 @@ __device__ __forceinline__ void philox4x32_10_rk(uint32_t& x0, uint32_t& x1, uin
     }
 }
 
+// Words 4k .. 4k + 3 of a lane (units u .. u + 3 of Philox block k): the block's output,
+// with units >= n set to 0xffffffff. Block k of the warp covers units 128k .. 128k + 127, so
+// when all of them exist (a warp-uniform test) no per-word selects are issued (about nine
+// integer instructions per block, on the pipe that generation keeps busiest).
+template <int KB>
+__device__ __forceinline__ void pad_block(uint32_t (&r)[4 * KB], int k, uint32_t x0, uint32_t x1, uint32_t x2,
+                                          uint32_t x3, int u, int n)
+{
+    if (128 * (k + 1) <= n) {
+        r[4 * k + 0] = x0;
+        r[4 * k + 1] = x1;
+        r[4 * k + 2] = x2;
+        r[4 * k + 3] = x3;
+    } else {
+        r[4 * k + 0] = (u + 0 < n) ? x0 : 0xffffffffu;
+        r[4 * k + 1] = (u + 1 < n) ? x1 : 0xffffffffu;
+        r[4 * k + 2] = (u + 2 < n) ? x2 : 0xffffffffu;
+        r[4 * k + 3] = (u + 3 < n) ? x3 : 0xffffffffu;
+    }
+}
+
 template <int KB>
 __device__ __forceinline__ void unit_words_rk(uint32_t (&r)[4 * KB], const uint32_t* rk, uint64_t draw, int n,
                                               int lane)
@@ -101,11 +122,7 @@ __device__ __forceinline__ void unit_words_rk(uint32_t (&r)[4 * KB], const uint3
         const int j = 32 * k + lane;
         uint32_t x0 = (uint32_t)j, x1 = 0u, x2 = d0, x3 = d1;
         if (4 * j < n) philox4x32_10_rk(x0, x1, x2, x3, rk);
-        const int u = 4 * j;
-        r[4 * k + 0] = (u + 0 < n) ? x0 : 0xffffffffu;
-        r[4 * k + 1] = (u + 1 < n) ? x1 : 0xffffffffu;
-        r[4 * k + 2] = (u + 2 < n) ? x2 : 0xffffffffu;
-        r[4 * k + 3] = (u + 3 < n) ? x3 : 0xffffffffu;
+        pad_block<KB>(r, k, x0, x1, x2, x3, 4 * j, n);
     }
 }
 
@@ -121,11 +138,7 @@ __device__ __forceinline__ void unit_words(uint32_t (&r)[4 * KB], uint64_t seed,
         const int j = 32 * k + lane;
         uint32_t x0 = (uint32_t)j, x1 = 0u, x2 = d0, x3 = d1;
         if (4 * j < n) philox4x32_10(x0, x1, x2, x3, k0, k1);
-        const int u = 4 * j;
-        r[4 * k + 0] = (u + 0 < n) ? x0 : 0xffffffffu;
-        r[4 * k + 1] = (u + 1 < n) ? x1 : 0xffffffffu;
-        r[4 * k + 2] = (u + 2 < n) ? x2 : 0xffffffffu;
-        r[4 * k + 3] = (u + 3 < n) ? x3 : 0xffffffffu;
+        pad_block<KB>(r, k, x0, x1, x2, x3, 4 * j, n);
     }
 }
 
