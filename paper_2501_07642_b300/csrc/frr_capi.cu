@@ -10,6 +10,7 @@
 #include <cstdio>
 
 #include <chrono>
+#include <immintrin.h>
 #include <new>
 #include <vector>
 
@@ -226,10 +227,10 @@ static void release(frr_ctx* ctx)
 
 // Argument checks of frr_init (also applied to every experiment of frr_batch_run).
 // Copies n*d values from X to dst (pinned staging) and checks that they are finite, in one pass.
-frr_status stage_finite(const double* X, int64_t count, double* dst)
+namespace {
+// Copy with the non-finite check (exponent field all ones), one word at a time.
+uint64_t stage_words(const uint64_t* bits, int64_t count, uint64_t* out)
 {
-    const uint64_t* bits = reinterpret_cast<const uint64_t*>(X);
-    uint64_t* out = reinterpret_cast<uint64_t*>(dst);
     const uint64_t em = 0x7ff0000000000000ull;
     uint64_t bad = 0;
     for (int64_t k = 0; k < count; ++k) {
@@ -237,6 +238,39 @@ frr_status stage_finite(const double* X, int64_t count, double* dst)
         out[k] = b;
         bad |= (uint64_t)((b & em) == em);
     }
+    return bad;
+}
+
+// The same with 32-byte loads and non-temporal stores: the staging block is written once and
+// read only by the DMA engine, so the stores bypass the caches (no read for ownership).
+__attribute__((target("avx2"))) uint64_t stage_words_avx2(const uint64_t* bits, int64_t count, uint64_t* out)
+{
+    int64_t k = 0;
+    uint64_t bad = 0;
+    const int64_t head = (int64_t)(((32 - (reinterpret_cast<uintptr_t>(out) & 31)) & 31) / 8);
+    if ((reinterpret_cast<uintptr_t>(out) & 7) != 0 || head >= count) return stage_words(bits, count, out);
+    bad |= stage_words(bits, head, out);
+    k = head;
+    const __m256i em = _mm256_set1_epi64x(0x7ff0000000000000ll);
+    __m256i acc = _mm256_setzero_si256();
+    for (; k + 4 <= count; k += 4) {
+        const __m256i v = _mm256_loadu_si256(reinterpret_cast<const __m256i*>(bits + k));
+        _mm256_stream_si256(reinterpret_cast<__m256i*>(out + k), v);
+        acc = _mm256_or_si256(acc, _mm256_cmpeq_epi64(_mm256_and_si256(v, em), em));
+    }
+    _mm_sfence();
+    if (!_mm256_testz_si256(acc, acc)) bad = 1;
+    return bad | stage_words(bits + k, count - k, out + k);
+}
+
+const bool g_has_avx2 = __builtin_cpu_supports("avx2");
+}  // namespace
+
+frr_status stage_finite(const double* X, int64_t count, double* dst)
+{
+    const uint64_t* bits = reinterpret_cast<const uint64_t*>(X);
+    uint64_t* out = reinterpret_cast<uint64_t*>(dst);
+    const uint64_t bad = g_has_avx2 ? stage_words_avx2(bits, count, out) : stage_words(bits, count, out);
     return bad ? FRR_E_ARG : FRR_OK;
 }
 
@@ -267,6 +301,21 @@ bool all_finite(const double* X, int64_t count)
 // A context for an (n, d, n1) experiment with checked options: streams, events and the fixed
 // arrays allocated, nothing prepared yet. with_aux: also the second stream of the preparation
 // (the batched driver prepares on streams of its own).
+// The per-phase timing events are created when first recorded: a context that never records
+// them (the batched driver turns the timing off) makes no event calls, which contend in the
+// driver when many contexts are created on several threads.
+void record_ev(frr_ctx* ctx, int i)
+{
+    if (!ctx->ev[i] && cudaEventCreate(&ctx->ev[i]) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ev[i] = nullptr;
+        ctx->st.timing = false;  // no event: the phase times of this call are not reported
+        ctx->st.times_pending = false;
+        return;
+    }
+    cudaEventRecord(ctx->ev[i], ctx->stream);
+}
+
 frr_status ctx_create(frr_ctx** out, int64_t n, int64_t d, int64_t n1, const frr_opts& o, bool with_aux)
 {
     *out = nullptr;
@@ -295,7 +344,6 @@ frr_status ctx_create(frr_ctx** out, int64_t n, int64_t d, int64_t n1, const frr
         INIT_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
         ctx->own_stream = true;
     }
-    for (cudaEvent_t& e : ctx->ev) INIT_CUDA(cudaEventCreate(&e));
     if (with_aux) INIT_CUDA(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
     {
         // the fixed per-context arrays in one allocation (each part 256-byte aligned)

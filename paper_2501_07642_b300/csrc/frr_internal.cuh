@@ -200,6 +200,8 @@ frr_status stage_finite(const double* X, int64_t count, double* dst);
 // pinned host blocks pooled by the library (size classes: powers of two up to 16 MiB, then multiples of 16 MiB)
 void* pinned_get(size_t bytes, size_t* cap_out);
 void pinned_put(void* p, size_t cap);
+// records per-phase timing event i on the context's stream (created on first use)
+void record_ev(frr_ctx* ctx, int i);
 frr_status ctx_create(frr_ctx** out, int64_t n, int64_t d, int64_t n1, const frr_opts& o, bool with_aux);
 void ctx_release(frr_ctx* ctx);
 // host_work(arg), when given, runs on the host while the device prepares (after every copy

@@ -1086,7 +1086,7 @@ frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const f
     };
     if (defer) {
         FRR_TRY(select_launch(new_cut));
-        if (st.timing) cudaEventRecord(ctx->ev[2], ctx->stream);
+        if (st.timing) record_ev(ctx, 2);
         st.retained = -1;
         st.retained_bound = std::min<int64_t>(N, cap);
         st.parity = 1 - par;
@@ -1101,7 +1101,7 @@ frr_status stream_select_step(frr_ctx* ctx, uint64_t first, uint64_t bc, const f
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk, &sel->kept, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
         FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hk + 1, ctx->dev_counters + 12, sizeof(int), cudaMemcpyDeviceToHost,
                                           ctx->stream));
-        if (st.timing) cudaEventRecord(ctx->ev[2], ctx->stream);
+        if (st.timing) record_ev(ctx, 2);
         FRR_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         const long long kept = hk[0];
         if (*reinterpret_cast<int*>(hk + 1) != 0) {
@@ -1131,13 +1131,13 @@ frr_status stream_chunk(frr_ctx* ctx, uint64_t first, uint64_t B)
     for (uint64_t off = 0; off < B; off += kChunkMax) {
         const uint64_t bc = std::min<uint64_t>(kChunkMax, B - off);
         FRR_TRY(ensure_device(ctx, reinterpret_cast<void**>(&ctx->Mhat), &ctx->Mhat_bytes, bc * sizeof(float)));
-        if (st.timing) cudaEventRecord(ctx->ev[0], ctx->stream);
+        if (st.timing) record_ev(ctx, 0);
         // the split-BF16 balance kernel also adds the chunk's level-0 counts of the selection
         SelState* sel = static_cast<SelState*>(ctx->sel);
         const bool fused = ctx->opts.precision == FRR_SPLIT_BF16;
         FRR_TRY(balance_launch(ctx, st.seed, st.exact, first + off, bc, ctx->Mhat,
                                fused ? &sel->hist0[st.parity][0] : nullptr));
-        if (st.timing) cudaEventRecord(ctx->ev[1], ctx->stream);
+        if (st.timing) record_ev(ctx, 1);
         FRR_TRY(stream_select_step(ctx, first + off, bc, ctx->Mhat, st.seen + off + bc == st.total, fused));
         if (st.retained < 0) {
             st.times_pending = true;  // nothing was synchronised: read the events in stream_end
@@ -1162,8 +1162,8 @@ frr_status stream_chunk_precomputed(frr_ctx* ctx, uint64_t first, uint64_t B, co
     if (st.seen + B > st.total) return FRR_E_RANGE;
     for (uint64_t off = 0; off < B; off += kChunkMax) {
         const uint64_t bc = std::min<uint64_t>(kChunkMax, B - off);
-        if (st.timing) cudaEventRecord(ctx->ev[0], ctx->stream);  // no balance here: an empty interval
-        if (st.timing) cudaEventRecord(ctx->ev[1], ctx->stream);
+        if (st.timing) record_ev(ctx, 0);  // no balance here: an empty interval
+        if (st.timing) record_ev(ctx, 1);
         FRR_TRY(stream_select_step(ctx, first + off, bc, Mhat + off, st.seen + off + bc == st.total, false));
         if (st.retained < 0) {
             st.times_pending = st.timing;  // nothing was synchronised: read the events in stream_end
@@ -1210,7 +1210,7 @@ frr_status stream_end_enqueue(frr_ctx* ctx, uint64_t* keys_out, double* M64_out,
     st.end_rb = rb;
     st.end_stage_n = stage_n;
     st.end_pinned = used;
-    if (st.timing) cudaEventRecord(ctx->ev[3], ctx->stream);
+    if (st.timing) record_ev(ctx, 3);
     // scratch: M64 (r), M64 out (r), keys out (r), rank (r)
     const size_t need = (size_t)rb * (3 * sizeof(double) + sizeof(int)) + 64;
     FRR_TRY(ensure_device(ctx, &ctx->misc, &ctx->misc_bytes, need));
@@ -1264,7 +1264,7 @@ frr_status stream_end_enqueue(frr_ctx* ctx, uint64_t* keys_out, double* M64_out,
                 FRR_CUDA_TRY(ctx, cudaMemcpyAsync(hm, mout, (size_t)stage_n * 8, cudaMemcpyDeviceToHost, ctx->stream));
         }
     }
-    if (st.timing) cudaEventRecord(ctx->ev[4], ctx->stream);
+    if (st.timing) record_ev(ctx, 4);
     return FRR_OK;
 }
 
