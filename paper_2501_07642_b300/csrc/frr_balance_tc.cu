@@ -67,6 +67,50 @@ __device__ __forceinline__ const TcExp* tile_job(const TcExp* one, const TcExp* 
     return table + lo;
 }
 
+// The tiles of one CTA. Batched launch: global tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// of the table. Single experiment: the CTA owns a contiguous range of D = ceil(B / gridDim.x)
+// draws cut into tiles of 128 with the remainder first, so that the first tile -- whose bit
+// rows must all be generated before the CTA's first MMA -- is the smallest, and every CTA
+// runs the same number of tiles (a draw's M_hat does not depend on the tile it is in).
+struct TileSched {
+    uint64_t lo;         // single experiment: the CTA's first draw
+    uint64_t count;      // tiles of this CTA
+    int first;           // single experiment: draws in the first tile
+};
+
+__device__ __forceinline__ TileSched tile_sched(const TcExp& one, const TcExp* table, unsigned long long tiles)
+{
+    TileSched s{0, 0, 0};
+    if (table != nullptr) {
+        s.count = blockIdx.x < tiles ? (tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+        return s;
+    }
+    const uint64_t D = (one.B + gridDim.x - 1) / gridDim.x;
+    s.lo = (uint64_t)blockIdx.x * D;
+    const uint64_t n = s.lo < one.B ? (one.B - s.lo < D ? one.B - s.lo : D) : 0;
+    s.count = (n + kTileM - 1) / kTileM;
+    s.first = s.count ? (int)(n - (s.count - 1) * kTileM) : 0;
+    return s;
+}
+
+// Tile i of the CTA: its experiment, first draw offset (relative to the experiment's first
+// draw) and number of draws (<= 128).
+__device__ __forceinline__ const TcExp* tile_at(const TileSched& sc, const TcExp* one, const TcExp* table,
+                                                const unsigned long long* prefix, int E, uint64_t i, uint64_t& base,
+                                                int& cnt)
+{
+    if (table == nullptr) {
+        base = sc.lo + (i == 0 ? 0 : (uint64_t)sc.first + (i - 1) * kTileM);
+        cnt = i == 0 ? sc.first : kTileM;
+        return one;
+    }
+    uint64_t tl;
+    const TcExp* x = tile_job(one, table, prefix, E, blockIdx.x + i * gridDim.x, tl);
+    base = tl * kTileM;
+    cnt = x->B - base < (uint64_t)kTileM ? (int)(x->B - base) : kTileM;
+    return x;
+}
+
 // Bit row of one draw for a run-time number of Philox blocks per lane kb <= KBMAX.
 template <int KBMAX>
 __device__ __forceinline__ void draw_bits_kb(int kb, bool exact, uint64_t seed, uint64_t draw, int n, int n1,
@@ -134,6 +178,7 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *sTmem;
+    const TileSched sched = tile_sched(one, table, tiles);
     // limit of every bounded wait (shortened only by the failure-path test, see frr_test_wait_expiry)
     const unsigned long long wlim = one.wait_cycles ? one.wait_cycles : kWaitCycles;
 
@@ -142,9 +187,10 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
         if (lane == 0 && !one.skip_tma) {
             uint32_t bi = 0;
             bool ok = true;
-            for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-                uint64_t tl;
-                const TcExp* x = tile_job(&one, table, prefix, E, t, tl);
+            for (uint64_t i = 0; i < sched.count && ok; ++i) {
+                uint64_t base;
+                int cnt;
+                const TcExp* x = tile_at(sched, &one, table, prefix, E, i, base, cnt);
                 const int nch = x->nchunks, nkb = x->nkb;
                 for (int c = 0; c < nch && ok; ++c)
                     for (int kb = 0; kb < nkb && ok; ++kb)
@@ -171,9 +217,10 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
         if (lane == 0) {
             uint32_t ai = 0, bi = 0, g = 0;
             bool ok = true;
-            for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-                uint64_t tl;
-                const TcExp* x = tile_job(&one, table, prefix, E, t, tl);
+            for (uint64_t i = 0; i < sched.count && ok; ++i) {
+                uint64_t base;
+                int cnt;
+                const TcExp* x = tile_at(sched, &one, table, prefix, E, i, base, cnt);
                 const int nch = x->nchunks, nkb = x->nkb, dd = x->d;
                 for (int c = 0; c < nch && ok; ++c, ++g) {
                     const int buf = g & 1;
@@ -216,9 +263,10 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
         uint32_t ai = 0;
         uint32_t it = 0;
         bool ok = true;
-        for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
-            uint64_t tl;
-            const TcExp* x = tile_job(&one, table, prefix, E, t, tl);
+        for (uint64_t i = 0; i < sched.count && ok; ++i, ++it) {
+            uint64_t base;
+            int cnt;
+            const TcExp* x = tile_at(sched, &one, table, prefix, E, i, base, cnt);
             const int nch = x->nchunks, nkb = x->nkb;
             const int bb = it & 1;
             if (!(ok = wait_bar(&bits_full[bb], (it >> 1) & 1u, sAbort, err, 5, wlim))) break;
@@ -247,31 +295,30 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
         static_assert(NG * 32 >= kTileM, "exact mode gives every row of a tile its own lane");
         uint32_t it = 0;
         bool ok = true;
-        for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
-            uint64_t tl;
-            const TcExp* x = tile_job(&one, table, prefix, E, t, tl);
+        for (uint64_t i = 0; i < sched.count && ok; ++i, ++it) {
+            uint64_t base;
+            int cnt;
+            const TcExp* x = tile_at(sched, &one, table, prefix, E, i, base, cnt);
             const int bb = it & 1;
             if (!(ok = wait_bar(&bits_empty[bb], ((it >> 1) & 1u) ^ 1u, sAbort, err, 7, wlim))) break;
             uint32_t* bits = sBits + bb * kTileM * RS;
             const int kbx = x->kb, nx = x->n, n1x = x->n1, ex = x->exact;
-            const uint64_t sx = x->seed, fx = x->first, Bx = x->B;
+            const uint64_t sx = x->seed, fx = x->first;
             const uint64_t* bx = x->binom;
             if (ex) {
                 // exact enumeration: lane j of this warp unranks row gw + NG j on its own
                 const int r = gw + NG * lane;
                 if (r < kTileM) {
-                    const uint64_t off = tl * kTileM + r;
                     uint32_t* row = bits + r * RS;
-                    if (off < Bx) lane_exact_row(fx + off, nx, n1x, bx, row, 4 * kbx);
+                    if (r < cnt) lane_exact_row(fx + base + r, nx, n1x, bx, row, 4 * kbx);
                     else for (int q = 0; q < 4 * kbx; ++q) row[q] = 0u;
                 }
             } else {
                 for (int r = gw; r < kTileM; r += NG) {
-                    const uint64_t off = tl * kTileM + r;
                     uint32_t* row = bits + r * RS;
-                    if (off < Bx) {
-                        if constexpr (MULTI) draw_bits_kb<KB>(kbx, false, sx, fx + off, nx, n1x, bx, row, lane);
-                        else warp_draw_bits_rk<KB>(one.rk, fx + off, nx, n1x, row, lane);
+                    if (r < cnt) {
+                        if constexpr (MULTI) draw_bits_kb<KB>(kbx, false, sx, fx + base + r, nx, n1x, bx, row, lane);
+                        else warp_draw_bits_rk<KB>(one.rk, fx + base + r, nx, n1x, row, lane);
                     } else {
                         for (int q = lane; q < W; q += 32) row[q] = 0u;
                     }
@@ -285,9 +332,10 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
         const int ew = warp;  // 0..3: TMEM lanes 32 ew .. 32 ew + 31
         uint32_t g = 0;
         bool ok = true;
-        for (uint64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-            uint64_t tl;
-            const TcExp* x = tile_job(&one, table, prefix, E, t, tl);
+        for (uint64_t i = 0; i < sched.count && ok; ++i) {
+            uint64_t base;
+            int cnt;
+            const TcExp* x = tile_at(sched, &one, table, prefix, E, i, base, cnt);
             const int nch = x->nchunks, dd = x->d;
             float sumsq = 0.f;
             for (int c = 0; c < nch; ++c, ++g) {
@@ -312,14 +360,15 @@ k_balance_tc(const __grid_constant__ TcExp one, const TcExp* __restrict__ table,
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acc_empty[buf]);
             }
-            const uint64_t off = tl * kTileM + 32 * ew + lane;
+            const int row = 32 * ew + lane;
+            const uint64_t off = base + row;
             const float mh = x->c_M * sumsq;
-            if (ok && off < x->B) x->Mout[off] = mh;
+            if (ok && row < cnt) x->Mout[off] = mh;
             // level-0 histogram of the streaming selection (bits [31:20] of M_hat), one atomic
             // per distinct bin of the warp
             unsigned* h0 = x->hist0;
             if (h0 != nullptr) {
-                const bool take = ok && off < x->B;
+                const bool take = ok && row < cnt;
                 const unsigned bin = __float_as_uint(mh) >> 20;
                 const unsigned mask = __activemask();
                 const unsigned peers = __match_any_sync(mask, take ? bin : 0xffffffffu);
