@@ -37,7 +37,7 @@ constexpr int kBBytes = kPlanes * kPlaneBytes;     // 32 KiB
 constexpr int kABytes = kM * kKB * 2;              // 16 KiB
 constexpr int kEpiWarps = 16;  // four per TMEM lane quarter, one per 16-column quarter of an item
 constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kParts = 4;      // partial sums per (candidate, column chunk): one per column quarter
+constexpr int kQuarters = 4;   // column quarters of an item (one epilogue thread each per candidate)
 constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1, kExpWarp0 = kEpiWarps + 2;
 constexpr int kThreads = (kExpWarp0 + 4) * 32;
 static_assert(kN == 64 && kPlanes * kN == 256, "16-column epilogue quarters; the four planes in one N = 256 MMA");
@@ -122,7 +122,7 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
     __shared__ long long sQsum[kN];
     __shared__ int sQexp[kN];
     __shared__ int sLast;   // this CTA completed the last column chunk of the item's candidate tile
-    __shared__ double sSum[kParts - 1][kM];  // quarter sums of the M64 partial sums (last CTA)
+    __shared__ double sSum[kQuarters - 1][kM];  // quarter sums: of an item's columns, then of a row's partial sums
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t C = C_dev ? std::min<int64_t>((int64_t)*C_dev, C_host) : C_host;  // within the buffers
@@ -282,39 +282,51 @@ k_recheck_tc(const __grid_constant__ CUtensorMap map_q, const uint32_t* __restri
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty);
-            if (cand < C) part[(cand * ncb + chunk) * kParts + qtr] = psum;
+            // the four quarter sums of the item, added in column order inside this CTA: one
+            // partial sum per (candidate, column chunk), so the tile's last CTA adds ncb of them
+            // per candidate rather than 4 ncb (the FP64 unit is narrow)
+            if (qtr > 0) sSum[qtr - 1][row] = psum;
+            asm volatile("bar.sync 1, %0;" :: "n"(kEpiThreads) : "memory");
+            if (qtr == 0 && cand < C) {
+#pragma unroll
+                for (int q = 0; q < kQuarters - 1; ++q) psum = __dadd_rn(psum, sSum[q][row]);
+                part[cand * ncb + chunk] = psum;
+            }
             // The CTA that completes the last of a tile's ncb column chunks sums each candidate's
-            // 2 ncb partial sums in column order and forms M64 = sum / (n n1 n0): the writers
-            // fence their partial sums before counting, the last one fences after (acquire).
+            // ncb partial sums in column order and forms M64 = sum / (n n1 n0). Thread 0 counts
+            // for the CTA: a fence before the count publishes the CTA's partial sums (written
+            // before the barrier), and in the last CTA a fence after it orders the other CTAs'
+            // partial sums before the loads that follow the second barrier.
             asm volatile("bar.sync 1, %0;" :: "n"(kEpiThreads) : "memory");
             if (tid == 0) {
                 __threadfence();
                 sLast = atomicAdd(&tile_done[item % T], 1) == ncb - 1;
+                if (sLast) __threadfence();
             }
             asm volatile("bar.sync 1, %0;" :: "n"(kEpiThreads) : "memory");
             if (sLast) {
-                // thread (row, quarter qtr) adds partial sums [qtr ncb, (qtr + 1) ncb) of the row's
-                // 4 ncb in column order, sixteen loads in flight; the quarters are then added in
-                // order, and M64 = sum / (n n1 n0)
-                __threadfence();
-                const int nparts = kParts * ncb;
-                const double* pc = part + cand * (int64_t)nparts;
+                // thread (row, quarter qtr) adds the row's partial sums [lo, hi) -- a quarter of its
+                // ncb, one per column chunk -- in column order, sixteen loads in flight; the
+                // quarters are then added in order, and M64 = sum / (n n1 n0)
+                const int per = (ncb + kQuarters - 1) / kQuarters;
+                const int lo = qtr * per, hi = lo + per < ncb ? lo + per : ncb;
+                const double* pc = part + cand * (int64_t)ncb;
                 double s = 0.0;
                 if (cand < C) {
-                    for (int b0 = qtr * ncb; b0 < (qtr + 1) * ncb; b0 += 16) {
+                    for (int b0 = lo; b0 < hi; b0 += 16) {
                         double v[16];
 #pragma unroll
-                        for (int u = 0; u < 16; ++u) v[u] = b0 + u < (qtr + 1) * ncb ? __ldcg(pc + b0 + u) : 0.0;
+                        for (int u = 0; u < 16; ++u) v[u] = b0 + u < hi ? __ldcg(pc + b0 + u) : 0.0;
 #pragma unroll
                         for (int u = 0; u < 16; ++u)
-                            if (b0 + u < (qtr + 1) * ncb) s = __dadd_rn(s, v[u]);
+                            if (b0 + u < hi) s = __dadd_rn(s, v[u]);
                     }
                 }
                 if (qtr > 0) sSum[qtr - 1][row] = s;
                 asm volatile("bar.sync 1, %0;" :: "n"(kEpiThreads) : "memory");
                 if (qtr == 0 && cand < C) {
 #pragma unroll
-                    for (int q = 0; q < kParts - 1; ++q) s = __dadd_rn(s, sSum[q][row]);
+                    for (int q = 0; q < kQuarters - 1; ++q) s = __dadd_rn(s, sSum[q][row]);
                     M64[cand] = __ddiv_rn(__dmul_rn(1.0, s), denom);
                 }
             }
@@ -341,7 +353,7 @@ frr_status recheck_tc_launch(frr_ctx* ctx, uint64_t seed, bool exact, const uint
     const int ncb = ceil_div(ctx->d, kN);
     const int64_t tiles = (count + kM - 1) / kM;
     const size_t rows_bytes = ((size_t)count * W * sizeof(uint32_t) + 255) & ~size_t(255);
-    const size_t part_bytes = ((size_t)count * ncb * kParts * sizeof(double) + 255) & ~size_t(255);
+    const size_t part_bytes = ((size_t)count * ncb * sizeof(double) + 255) & ~size_t(255);
     const size_t ctr_bytes = (size_t)tiles * sizeof(int);
     FRR_TRY(ensure_device(ctx, &ctx->misc2, &ctx->misc2_bytes, rows_bytes + part_bytes + ctr_bytes));
     uint32_t* rows = static_cast<uint32_t*>(ctx->misc2);

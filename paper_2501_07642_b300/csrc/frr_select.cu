@@ -485,6 +485,9 @@ k_finish(const double* __restrict__ m64, const uint64_t* __restrict__ idx, const
     __shared__ int s_viol[32];
     __shared__ unsigned long long s_prefix;
     __shared__ long long s_k, s_ntie;
+    __shared__ unsigned s_cnt;                  // entries in the bin of rank k after a pass
+    __shared__ unsigned long long s_small[32];  // those entries, when there are at most 32
+    __shared__ int s_nsmall;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // a device count above the bound belongs to an overflowed buffer: the host redoes the selection
     const int64_t r = r_dev ? (*r_dev < r_host ? *r_dev : r_host) : r_host;
@@ -610,6 +613,7 @@ k_finish(const double* __restrict__ m64, const uint64_t* __restrict__ idx, const
                         if (run < k && k <= run + (long long)cnt[i]) {
                             s_prefix = (prefix & himask) | ((unsigned long long)(8 * lane + i) << sh);
                             s_k = k - run;
+                            s_cnt = cnt[i];
                         }
                         run += cnt[i];
                     }
@@ -619,6 +623,39 @@ k_finish(const double* __restrict__ m64, const uint64_t* __restrict__ idx, const
             prefix = s_prefix;
             k = s_k;
             if (shift <= 0) break;
+            if (s_cnt <= 32) {
+                // At most 32 entries share the prefix so far: gather them and let one warp find
+                // the k-th smallest of them (each lane counts the keys below and up to its own),
+                // instead of further passes over the remaining low bits.
+                const unsigned long long lmask = ~0ull << sh;
+                if (tid == 0) s_nsmall = 0;
+                __syncthreads();
+#pragma unroll
+                for (int m = 0; m < kFinPer; ++m) {
+                    if (m * kFinThreads >= r) break;  // the same for the whole block
+                    const int c = tid + m * kFinThreads;
+                    if (c < r && (key[m] & lmask) == (prefix & lmask)) s_small[atomicAdd(&s_nsmall, 1)] = key[m];
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    const int nb = s_nsmall;
+                    const unsigned long long v = lane < nb ? s_small[lane] : ~0ull;
+                    int lt = 0, le = 0;
+                    for (int j = 0; j < nb; ++j) {
+                        const unsigned long long u = s_small[j];
+                        lt += u < v ? 1 : 0;
+                        le += u <= v ? 1 : 0;
+                    }
+                    if (lane < nb && lt < k && k <= le) {  // (lanes holding equal keys write the same)
+                        s_prefix = v;
+                        s_k = k - lt;
+                    }
+                }
+                __syncthreads();
+                prefix = s_prefix;
+                k = s_k;
+                break;
+            }
         }
         thr = prefix;  // the K-th smallest key; k of the entries equal to it are accepted
         need = k;
