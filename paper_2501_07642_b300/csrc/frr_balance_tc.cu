@@ -4,7 +4,9 @@
 // W is 0/1, exact in BF16; Zc is split into BF16 parts hi = bf16(Zc), lo = bf16(Zc - hi),
 // and both products accumulate into one FP32 accumulator: s = W.hi + W.lo.
 //
-// One persistent CTA per SM walks tiles of 128 consecutive draws. Warp roles:
+// One persistent CTA per SM walks tiles of up to 128 consecutive draws (a single experiment:
+// a contiguous range of ceil(B / CTAs) draws per CTA with the remainder in its first tile; a
+// batch: the table's tiles dealt round-robin). Warp roles:
 //   warps 0-3   epilogue: tcgen05.ld of the accumulator (TMEM lane = draw), sum of
 //               squares over the covariate chunks, M_hat written per draw;
 //   warp 4      TMA producer: Zc hi / lo tiles (256 covariates x 64 K positions, 128B
