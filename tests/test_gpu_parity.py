@@ -154,6 +154,25 @@ def test_balance_to_device_buffer_matches_host_buffer():
 
 
 # ---------------------------------------------------------------- recheck ----
+@pytest.mark.parametrize("n,d", [(1000, 300), (200, 64)])
+def test_balance_independent_of_the_launch_range(n, d):
+    """A draw's M_hat (Sec. 2.2, 2.3) depends only on its key: computed inside any range of
+    draws -- one draw, fewer than a tile, a CTA count's worth of tiles plus one, an offset
+    start -- it is bit for bit the value the launch over [0, 40000) gives. This covers how a
+    launch splits its draws over CTAs and tiles (contiguous per-CTA ranges, the remainder in a
+    CTA's first tile; CTAs with empty ranges)."""
+    import torch
+    X = ar1_covariates(n, d, 17, 0.4)
+    with _ctx(X, n // 2, "split_bf16", "ridge") as ctx:
+        ref = frr.frr_balance(ctx, 5, 0, 40_000)
+        for first, B in [(0, 1), (5, 127), (1000, 129), (123, 148 * 128 + 1), (7, 20_000), (39_000, 1000),
+                         (2, 148 * 72), (0, 40_000)]:
+            got = torch.empty(B, dtype=torch.float32, device="cuda")
+            frr.frr_balance(ctx, 5, first, B, got)
+            torch.cuda.synchronize()
+            assert np.array_equal(got.cpu().numpy().view(np.uint32), ref[first:first + B].view(np.uint32)), (first, B)
+
+
 @pytest.mark.parametrize("n,d,whiten", [(100, 100, "ridge"), (1000, 1000, "ridge"), (64, 20, "chol")])
 def test_recheck_matches_oracle(n, d, whiten):
     X = ar1_covariates(n, d, 9, 0.5)
