@@ -256,8 +256,7 @@ def run_frr(args):
                     ev0.record(stream)
                 first = draw_base + (i + 1) * B
                 frr.frr_select(ctx, w.philox_seed, first, B, q=q, keys_out=keys, M64_out=m64, cap=K)
-                with torch.cuda.stream(stream):
-                    ev1.record(stream)
+                ev1.record(stream)  # (on the library's stream; no stream switch inside the timed interval)
                 ev1.synchronize()
                 i += 1
                 if i > n_warm:
