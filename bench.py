@@ -165,6 +165,21 @@ def oracle_rate_1t(Zc, n1, seed, target_s: float, first: int = 0):
     return S / (time.perf_counter() - t0), S
 
 
+def oracle_full_mc() -> dict:
+    """The whole n = d = 100 workload (2e5 draws, q = 0.01) through the FP64 oracle on all host
+    cores: preparation, M of every draw and the selection."""
+    from oracle import oracle as O
+    from paper_2501_07642_b300.workloads import workload
+    w = workload("mc_n100_d100")
+    X = w.covariates()
+    t0 = time.perf_counter()
+    Zc, *_ = O.prep(X, w.whiten, 0.1)
+    keys, _ = O.select(Zc, w.n1, w.philox_seed, 0, w.draws, q=w.q)
+    dt = time.perf_counter() - t0
+    return {"value": w.draws / dt, "unit": "draws/s", "s": dt, "draws": w.draws, "K": int(len(keys)),
+            "cores": O.threads(), "workload": "mc_n100_d100 (n = d = 100, q = 0.01), every draw"}
+
+
 def cpu_model() -> str:
     try:
         for line in Path("/proc/cpuinfo").read_text().splitlines():
@@ -349,6 +364,7 @@ def run_frr(args):
         cpu = {"value": rate, "unit": "draws/s", "cores": cores, "kind": "oracle",
                "sample": f"FP64 oracle select (M of every draw + sort) on {S} draws of the {WORKLOAD} workload",
                "single_thread": {"value": rate1, "sample": f"{S1} draws on one thread"},
+               "mc_n100_d100_full": oracle_full_mc(),
                "cpu_model": cpu_model(), "nproc": os.cpu_count()}
     line = {"metric": METRIC, "value": r["value"], "unit": "draws/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
