@@ -140,15 +140,18 @@ def oracle_zc(X):
     return Zc
 
 
-def oracle_rate(Zc, n1, seed, target_s: float, first: int = 0):
-    """Oracle draws/s on a bounded sample sized to take about target_s seconds."""
+def oracle_rate(Zc, n1, seed, target_s: float, first: int = 0, full: int = 200_000):
+    """Oracle draws/s on the first `full` draws, or on a sample sized to take about target_s
+    seconds when they would take longer (a 2048-draw calibration: with fewer, the threads'
+    start-up and the sort dominate the per-draw time)."""
     from oracle import oracle as O
+    cal = min(2048, full)
     t0 = time.perf_counter()
-    O.select(Zc, n1, seed, first, 64, q=1e-3)
-    per = (time.perf_counter() - t0) / 64
-    S = int(max(64, min(200_000, target_s / max(per, 1e-7))))
+    O.select(Zc, n1, seed, first, cal, q=1e-3)
+    per = (time.perf_counter() - t0) / cal
+    S = int(max(64, min(full, target_s / max(per, 1e-7))))
     t0 = time.perf_counter()
-    O.select(Zc, n1, seed, first + 64, S, q=1e-3)
+    O.select(Zc, n1, seed, first + cal, S, q=1e-3)
     dt = time.perf_counter() - t0
     return S / dt, S, O.threads()
 
@@ -198,8 +201,10 @@ def run_reference(args):
     w = workload(WORKLOAD)
     Zc = oracle_zc(w.covariates())
     rates, samples = [], []
+    # per-step sample: at most ref_step_s seconds, and the whole run within about ref_total_s
+    step_s = min(args.ref_step_s, args.ref_total_s / max(1, args.warmup + args.steps))
     for i in range(args.warmup + args.steps):
-        r, S, cores = oracle_rate(Zc, w.n1, w.philox_seed, args.ref_step_s, first=i * 1_000_000)
+        r, S, cores = oracle_rate(Zc, w.n1, w.philox_seed, step_s, first=i * 1_000_000)
         if i >= args.warmup:
             rates.append(r)
             samples.append(S)
@@ -359,10 +364,12 @@ def run_frr(args):
     cpu = None
     if args.cpu_baseline:
         Zc = oracle_zc(X)
-        rate, S, cores = oracle_rate(Zc, n1, w.philox_seed, args.cpu_s)
+        rate, S, cores = oracle_rate(Zc, n1, w.philox_seed, args.cpu_s, full=B)
         rate1, S1 = oracle_rate_1t(Zc, n1, w.philox_seed, args.cpu_s / 4, first=10_000_000)
         cpu = {"value": rate, "unit": "draws/s", "cores": cores, "kind": "oracle",
-               "sample": f"FP64 oracle select (M of every draw + sort) on {S} draws of the {WORKLOAD} workload",
+               "sample": (f"FP64 oracle select (M of every draw + sort) on "
+                          + (f"all {S} draws of one step" if S == B else f"{S} of the {B} draws of a step")
+                          + f" of the {WORKLOAD} workload"),
                "single_thread": {"value": rate1, "sample": f"{S1} draws on one thread"},
                "mc_n100_d100_full": oracle_full_mc(),
                "cpu_model": cpu_model(), "nproc": os.cpu_count()}
@@ -536,8 +543,9 @@ def main():
     ap.add_argument("--impl", choices=("frr", "reference"), default="frr")
     ap.add_argument("--precision", default="split_bf16,f32")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--cpu-s", type=float, default=12.0)
+    ap.add_argument("--cpu-s", type=float, default=20.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)
+    ap.add_argument("--ref-total-s", type=float, default=120.0)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--e2e-steps", type=int, default=7)
     ap.add_argument("--no-distance", dest="distance", action="store_false")
