@@ -12,6 +12,7 @@
 #include <chrono>
 #include <immintrin.h>
 #include <new>
+#include <thread>
 #include <vector>
 
 namespace frr {
@@ -441,21 +442,21 @@ frr_status frr_init(frr_ctx** out, const double* X, int64_t n, int64_t d, int64_
         const frr_status c = ctx_create(&ctx, n, d, n1, o, true);
         if (c != FRR_OK) return all_finite(X, n * d) ? c : FRR_E_ARG;
     }
-    struct Scan {
-        const double* X;
-        int64_t count;
-        bool finite;
-        static void run(void* a)
-        {
-            Scan* sc = static_cast<Scan*>(a);
-            sc->finite = all_finite(sc->X, sc->count);
-        }
-    } scan{X, n * d, true};
-    const frr_status s = prep_run(ctx, X, &Scan::run, &scan);
-    if (s != FRR_OK || !scan.finite) {
+    // The scan runs on its own host thread from before the preparation is enqueued to after it
+    // finished: enqueueing the preparation's launches keeps this thread busy for about as long
+    // as the device needs, so a scan run after the enqueue would add its own time.
+    bool finite = true;
+    std::thread scan_thread;
+    try {
+        scan_thread = std::thread([X, n, d, &finite] { finite = all_finite(X, n * d); });
+    } catch (...) {
+        finite = all_finite(X, n * d);  // no thread: scan before the preparation
+    }
+    const frr_status s = prep_run(ctx, X);
+    if (scan_thread.joinable()) scan_thread.join();
+    if (s != FRR_OK || !finite) {
         release(ctx);
-        // a failed preparation may have returned before running the scan
-        return (scan.finite && all_finite(X, n * d)) ? s : FRR_E_ARG;
+        return finite ? s : FRR_E_ARG;  // a non-finite X is reported before any other error
     }
     ctx->stats.ms_init = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = ctx;

@@ -204,14 +204,14 @@ void pinned_put(void* p, size_t cap);
 void record_ev(frr_ctx* ctx, int i);
 frr_status ctx_create(frr_ctx** out, int64_t n, int64_t d, int64_t n1, const frr_opts& o, bool with_aux);
 void ctx_release(frr_ctx* ctx);
-// host_work(arg), when given, runs on the host while the device prepares (after every copy
-// and launch is enqueued, before the preparation's single synchronisation)
-frr_status prep_run(frr_ctx* ctx, const double* X_host, void (*host_work)(void*) = nullptr, void* arg = nullptr);
+// prepares one context (its arrays allocated) from host covariates X_host, with one
+// synchronisation at the end
+frr_status prep_run(frr_ctx* ctx, const double* X_host);
 // prepares E contexts (created, arrays allocated) together on streams s and aux; st_out[e]
 // receives each one's status (FRR_E_DEGENERATE for a failed pivot, FRR_E_TIMEOUT for an
 // expired bounded wait); the return value is a CUDA failure common to all, else FRR_OK
 frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int E, cudaStream_t s, cudaStream_t aux,
-                          frr_status* st_out, void (*host_work)(void*) = nullptr, void* arg = nullptr);
+                          frr_status* st_out);
 frr_status balance_f32_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
 // hist0 (split BF16 only, may be NULL): 4096 counters that also receive the level-0 histogram
 // of the scored M_hat (bits [31:20] of each value) for the streaming selection

@@ -780,7 +780,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 }  // namespace
 
 frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int E, cudaStream_t s,
-                          cudaStream_t aux, frr_status* st_out, void (*host_work)(void*), void* arg)
+                          cudaStream_t aux, frr_status* st_out)
 {
     if (E < 1) return FRR_OK;
     const int device = ctxs[0]->device;
@@ -956,7 +956,6 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
     for (int e = 0; e < E; ++e)
         PREP_CHECK(cudaMemcpyAsync(h_eps[(size_t)e].data(), jobs[(size_t)e].eps, h_eps[(size_t)e].size() * 8,
                                    cudaMemcpyDeviceToHost, s));
-    if (host_work) host_work(arg);
     PREP_CHECK(cudaStreamSynchronize(s));
     for (int e = 0; e < E; ++e) {
         frr_ctx* c = ctxs[e];
@@ -987,10 +986,10 @@ cleanup:
     return rc;
 }
 
-frr_status prep_run(frr_ctx* ctx, const double* X_host, void (*host_work)(void*), void* arg)
+frr_status prep_run(frr_ctx* ctx, const double* X_host)
 {
     frr_status st = FRR_OK;
-    const frr_status rc = prep_run_batch(&ctx, &X_host, 1, ctx->stream, ctx->aux, &st, host_work, arg);
+    const frr_status rc = prep_run_batch(&ctx, &X_host, 1, ctx->stream, ctx->aux, &st);
     if (rc != FRR_OK) {
         ctx->failed = true;
         return rc;
