@@ -970,15 +970,16 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
 
 cleanup:
 #undef PREP_CHECK
-    for (cudaEvent_t ev : evs)
-        if (ev) cudaEventDestroy(ev);
-    if (ts) cudaStreamDestroy(ts);
-    // after a failure, work may still be in flight on the other streams
+    // after a failure, work may still be in flight on the other streams (synchronised before
+    // the trailing-update stream is destroyed and before the temporaries are released)
     if (rc != FRR_OK) {
         cudaStreamSynchronize(aux);
         if (ts) cudaStreamSynchronize(ts);
         cudaGetLastError();
     }
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
+    if (ts) cudaStreamDestroy(ts);
     // stream-ordered release: no device-wide synchronisation
     if (base) cudaFreeAsync(base, s);
     if (rc != FRR_OK)
