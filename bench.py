@@ -142,10 +142,10 @@ def oracle_zc(X):
 
 def oracle_rate(Zc, n1, seed, target_s: float, first: int = 0, full: int = 200_000):
     """Oracle draws/s on the first `full` draws, or on a sample sized to take about target_s
-    seconds when they would take longer (a 2048-draw calibration: with fewer, the threads'
-    start-up and the sort dominate the per-draw time)."""
+    seconds when they would take longer (an 8192-draw calibration: with fewer, the threads'
+    start-up and the sort inflate the per-draw time)."""
     from oracle import oracle as O
-    cal = min(2048, full)
+    cal = min(8192, full)
     t0 = time.perf_counter()
     O.select(Zc, n1, seed, first, cal, q=1e-3)
     per = (time.perf_counter() - t0) / cal
