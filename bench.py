@@ -200,11 +200,16 @@ def run_reference(args):
     from paper_2501_07642_b300.workloads import workload
     w = workload(WORKLOAD)
     Zc = oracle_zc(w.covariates())
+    from oracle import oracle as O
     rates, samples = [], []
-    # per-step sample: at most ref_step_s seconds, and the whole run within about ref_total_s
+    # per-step sample: at most ref_step_s seconds, and the whole run within about ref_total_s;
+    # its size comes from the first (calibrating) call and is kept for every step
     step_s = min(args.ref_step_s, args.ref_total_s / max(1, args.warmup + args.steps))
+    _, S, cores = oracle_rate(Zc, w.n1, w.philox_seed, step_s, first=0)
     for i in range(args.warmup + args.steps):
-        r, S, cores = oracle_rate(Zc, w.n1, w.philox_seed, step_s, first=i * 1_000_000)
+        t0 = time.perf_counter()
+        O.select(Zc, w.n1, w.philox_seed, (i + 1) * 1_000_000, S, q=1e-3)
+        r = S / (time.perf_counter() - t0)
         if i >= args.warmup:
             rates.append(r)
             samples.append(S)
