@@ -175,8 +175,8 @@ inline cudaError_t set_smem_limit(void (*kernel)(P...), int bytes, int device)
 }
 
 // stream-ordered memory pool of the library for short-lived temporaries on `device`; it keeps
-// up to 2 GiB reserved between calls instead of returning it at every synchronisation (a
-// 256-experiment batch prepares with about 1.2 GB of temporaries)
+// up to 8 GiB reserved between calls instead of returning it at every synchronisation (a
+// 256-experiment batch peaks near 2 GiB)
 cudaMemPool_t temp_pool(int device);
 
 // grow a device buffer to at least `bytes` (old contents are not kept)
