@@ -212,6 +212,31 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host);
 // expired bounded wait); the return value is a CUDA failure common to all, else FRR_OK
 frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int E, cudaStream_t s, cudaStream_t aux,
                           frr_status* st_out);
+// One experiment's covariance from digit products on the tensor cores (frr_cov_tc.cu).
+struct CovJob {
+    int n, d, npad, dpad;       // npad = 64 ceil(n / 64), dpad = 128 ceil(d / 128)
+    const double* Xc;           // centred covariates, n x d row-major
+    int* cexp;                  // d column exponents
+    __nv_bfloat16* G;           // 8 digit planes, dpad x npad each
+    const CUtensorMap* gmap;    // over G (8 dpad rows x npad columns), in device memory
+    long long* acc;             // d x d int64 sums (elements on or above the diagonal)
+    double* S;                  // d x d covariance (output)
+    int* status;                // the preparation's status word (bit 2: a bounded wait expired)
+};
+int cov_tc_npad(int n);
+int cov_tc_dpad(int d);
+size_t cov_tc_plane_bytes(int n, int d);
+// blocks (or work units) per experiment of the four launches of cov_tc_launch
+unsigned cov_tc_exp_blocks(int n, int d);
+unsigned cov_tc_digit_blocks(int n, int d);
+unsigned cov_tc_units(int n, int d);
+unsigned cov_tc_finish_blocks(int n, int d);
+// the tensor map over an experiment's digit planes G (device address)
+bool cov_tc_map(CUtensorMap* m, const __nv_bfloat16* G, int n, int d);
+// column exponents, digit planes, tensor-core sums and S for the experiments of the device
+// table `jobs`; prefix[l] / total[l]: the prefix sums of launch l's blocks over the jobs
+cudaError_t cov_tc_launch(const CovJob* jobs, const unsigned* const prefix[4], const unsigned total[4], int E,
+                          int device, int num_sms, cudaStream_t s);
 frr_status balance_f32_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
 // hist0 (split BF16 only, may be NULL): 4096 counters that also receive the level-0 histogram
 // of the scored M_hat (bits [31:20] of each value) for the streaming selection

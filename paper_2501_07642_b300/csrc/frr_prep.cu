@@ -32,6 +32,7 @@ namespace frr {
 // One experiment's preparation as the kernels see it (device pointers).
 struct PrepJob {
     int n, d, n1, whiten, kpad, dpad32, kused;
+    int cov_tc;  // covariance from digit products on the tensor cores (else the FP64 chain below)
     double ridge;
     // temporaries
     double *X, *xbar, *Xc, *S, *Adiag, *Lm, *ZT, *scal, *eps;
@@ -733,7 +734,11 @@ struct JobBlocks {
     static unsigned colmean(const PrepJob& j) { return (unsigned)ceil_div(j.d, 32); }
     static unsigned cols32(const PrepJob& j) { return (unsigned)ceil_div(j.d, 32); }
     static unsigned center(const PrepJob& j) { return (unsigned)(((size_t)j.n * j.d + 255) / 256); }
-    static unsigned cov(const PrepJob& j) { return (unsigned)(ceil_div(j.d, 32) * ceil_div(j.d, 8)); }
+    static unsigned cov(const PrepJob& j) { return j.cov_tc ? 0u : (unsigned)(ceil_div(j.d, 32) * ceil_div(j.d, 8)); }
+    static unsigned cov_exp(const PrepJob& j) { return j.cov_tc ? cov_tc_exp_blocks(j.n, j.d) : 0u; }
+    static unsigned cov_digits(const PrepJob& j) { return j.cov_tc ? cov_tc_digit_blocks(j.n, j.d) : 0u; }
+    static unsigned cov_units(const PrepJob& j) { return j.cov_tc ? cov_tc_units(j.n, j.d) : 0u; }
+    static unsigned cov_finish(const PrepJob& j) { return j.cov_tc ? cov_tc_finish_blocks(j.n, j.d) : 0u; }
     static unsigned one(const PrepJob&) { return 1u; }
     static unsigned init_L(const PrepJob& j) { return (unsigned)(((size_t)j.d * j.d + 255) / 256); }
     static unsigned chol_diag(const PrepJob& j, int p)
@@ -798,8 +803,15 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         joff[(size_t)e] = bytes;
         bytes += 3 * align256(n * d * 8) + 2 * align256(d * d * 8) + 2 * align256(d * 8) + align256(4 * 8) +
                  align256(2 * d * 8);
+        if (c->opts.covariance == FRR_COV_TENSOR)  // digit planes, exponents, int64 sums
+            bytes += align256(cov_tc_plane_bytes((int)n, (int)d)) + align256(d * 4) + align256(d * d * 8);
         max_panels = std::max(max_panels, ceil_div(c->d, kP));
     }
+    // the covariance jobs and their tensor maps (64-byte aligned)
+    const size_t covjob_off = bytes;
+    bytes += align256((size_t)E * sizeof(CovJob));
+    const size_t maps_off = bytes;
+    bytes += align256((size_t)E * sizeof(CUtensorMap));
     const size_t status_off = bytes;
     bytes += align256((size_t)E * sizeof(int));
     const size_t table_off = bytes;
@@ -824,6 +836,7 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
             PrepJob& J = jobs[(size_t)e];
             J.n = (int)c->n; J.d = (int)c->d; J.n1 = (int)c->n1; J.whiten = c->opts.whiten;
             J.kpad = c->kpad; J.dpad32 = c->dpad32; J.kused = c->kused; J.ridge = c->opts.ridge;
+            J.cov_tc = c->opts.covariance == FRR_COV_TENSOR ? 1 : 0;
             J.Zc64 = c->Zc64; J.Z32 = c->Z32; J.Zhi = c->Zhi; J.Zlo = c->Zlo; J.Zq = c->Zq;
             J.Q = c->Q; J.Qsum = c->Qsum; J.qexp = c->qexp;
         }
@@ -831,6 +844,10 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
     add_launch(JobBlocks::colmean);
     add_launch(JobBlocks::center);
     add_launch(JobBlocks::cov);
+    add_launch(JobBlocks::cov_exp);
+    add_launch(JobBlocks::cov_digits);
+    add_launch(JobBlocks::cov_units);
+    add_launch(JobBlocks::cov_finish);
     add_launch(JobBlocks::one);
     add_launch(JobBlocks::init_L);
     for (int p = 0; p < max_panels; ++p) {
@@ -855,6 +872,8 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
     cudaStream_t ts = nullptr;  // the Cholesky's trailing updates
     std::vector<int> h_status((size_t)E, 0);
     std::vector<std::vector<double>> h_eps((size_t)E);
+    std::vector<CovJob> cjobs((size_t)E);
+    std::vector<CUtensorMap> cmaps((size_t)E);
     auto fail = [&](cudaError_t e) {
         cudaGetLastError();
         rc = (e == cudaErrorMemoryAllocation) ? FRR_E_NOMEM : FRR_E_CUDA;
@@ -871,12 +890,26 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         J.xbar = take(d * 8); J.Adiag = take(d * 8); J.scal = take(4 * 8); J.eps = take(2 * d * 8);
         J.status = reinterpret_cast<int*>(base + status_off) + e;
         h_eps[(size_t)e].resize(2 * d);
+        CovJob& C = cjobs[(size_t)e];
+        C = CovJob{};
+        if (J.cov_tc) {
+            C.n = J.n; C.d = J.d; C.npad = cov_tc_npad(J.n); C.dpad = cov_tc_dpad(J.d);
+            C.Xc = J.Xc; C.S = J.S; C.status = J.status;
+            C.G = reinterpret_cast<__nv_bfloat16*>(take(cov_tc_plane_bytes(J.n, J.d)));
+            C.cexp = reinterpret_cast<int*>(take(d * 4));
+            C.acc = reinterpret_cast<long long*>(take(d * d * 8));
+            C.gmap = reinterpret_cast<const CUtensorMap*>(base + maps_off) + e;
+            if (!cov_tc_map(&cmaps[(size_t)e], C.G, J.n, J.d)) { rc = FRR_E_CUDA; goto cleanup; }
+        }
     }
     PREP_CHECK(cudaMemsetAsync(base + status_off, 0, (size_t)E * sizeof(int), s));
     for (int e = 0; e < E; ++e)
         PREP_CHECK(cudaMemcpyAsync(jobs[(size_t)e].X, X_host[e], (size_t)jobs[(size_t)e].n * jobs[(size_t)e].d * 8,
                                    cudaMemcpyHostToDevice, s));
     PREP_CHECK(cudaMemcpyAsync(base + table_off, jobs.data(), (size_t)E * sizeof(PrepJob), cudaMemcpyHostToDevice, s));
+    PREP_CHECK(cudaMemcpyAsync(base + covjob_off, cjobs.data(), (size_t)E * sizeof(CovJob), cudaMemcpyHostToDevice, s));
+    PREP_CHECK(cudaMemcpyAsync(base + maps_off, cmaps.data(), (size_t)E * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                               s));
     PREP_CHECK(cudaMemcpyAsync(base + pref_off, pref.data(), pref.size() * sizeof(unsigned), cudaMemcpyHostToDevice,
                                s));
     {
@@ -892,6 +925,13 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         ++li;
         if (unsigned g = total(li)) k_cov<<<g, dim3(32, 8), 0, s>>>(dj, P(li), E);
         ++li;
+        {
+            const unsigned* cp[4] = {P(li), P(li + 1), P(li + 2), P(li + 3)};
+            const unsigned ct[4] = {total(li), total(li + 1), total(li + 2), total(li + 3)};
+            PREP_CHECK(cov_tc_launch(reinterpret_cast<const CovJob*>(base + covjob_off), cp, ct, E, device,
+                                     ctxs[0]->num_sms, s));
+            li += 4;
+        }
         if (unsigned g = total(li)) k_diag<<<g, 256, 0, s>>>(dj, P(li), E);
         ++li;
         if (unsigned g = total(li)) k_init_L<<<g, 256, 0, s>>>(dj, P(li), E);

@@ -26,6 +26,8 @@ FRR_CHOL, FRR_RIDGE, FRR_DIAG = 0, 1, 2
 FRR_EXACT_SEED = (1 << 64) - 1
 PRECISION = {"split_bf16": FRR_SPLIT_BF16, "f32": FRR_F32}
 WHITEN = {"chol": FRR_CHOL, "ridge": FRR_RIDGE, "diag": FRR_DIAG}
+FRR_COV_TENSOR, FRR_COV_FP64_CHAIN = 0, 1
+COVARIANCE = {"tensor": FRR_COV_TENSOR, "fp64_chain": FRR_COV_FP64_CHAIN}
 
 
 class FrrError(RuntimeError):
@@ -37,7 +39,8 @@ class FrrError(RuntimeError):
 
 class frr_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("whiten", ctypes.c_int), ("ridge", ctypes.c_double),
-                ("band_safety", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("autotune", ctypes.c_int)]
+                ("band_safety", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("autotune", ctypes.c_int),
+                ("covariance", ctypes.c_int)]
 
 
 class frr_stats(ctypes.Structure):
@@ -182,12 +185,13 @@ class Context:
     """Owns one frr_ctx (frr_init ... frr_destroy)."""
 
     def __init__(self, X, n1: int, precision: str = "split_bf16", whiten: str = "chol", ridge: float = 0.1,
-                 band_safety: float = 2.0, stream=None):
+                 band_safety: float = 2.0, stream=None, covariance: str = "tensor"):
         X = np.ascontiguousarray(X, dtype=np.float64)
         n, d = X.shape
         o = frr_default_opts()
         o.precision = PRECISION[precision]
         o.whiten = WHITEN[whiten]
+        o.covariance = COVARIANCE[covariance]
         o.ridge = float(ridge)
         o.band_safety = float(band_safety)
         o.cuda_stream = None if stream is None else int(getattr(stream, "cuda_stream", stream))
@@ -364,7 +368,7 @@ def frr_test_wait_expiry(ctx: Context, wait_cycles: int) -> int:
 
 
 def frr_batch_run(experiments, precision: str = "split_bf16", band_safety: float = 2.0, stream=None,
-                  autotune: bool = False):
+                  autotune: bool = False, covariance: str = "tensor"):
     """experiments: list of dicts with keys X, n1, seed, B (and optional first_draw, q or
     threshold, whiten, ridge, Y, tau, alpha). Returns (list of result dicts, stats dict).
     Outputs are host numpy arrays. autotune: time the kernel configurations on a probe of
@@ -413,6 +417,7 @@ def frr_batch_run(experiments, precision: str = "split_bf16", band_safety: float
     opts.band_safety = float(band_safety)
     opts.cuda_stream = None if stream is None else int(getattr(stream, "cuda_stream", stream))
     opts.autotune = 1 if autotune else 0
+    opts.covariance = COVARIANCE[covariance]
     st = frr_batch_stats()
     rc = lib().frr_batch_run(ctypes.addressof(arr), E, ctypes.byref(opts), ctypes.byref(st))
     res = []

@@ -27,6 +27,11 @@ def _m_err(got, want, precision, d):
     scale = want if precision == "f32" else np.maximum(want, d)
     return (np.abs(got - want) / scale).max()
 REL_M64 = 1e-11       # exact-sum recheck vs the oracle's FP64 M
+# Whitened covariates from the tensor-core covariance vs the oracle's FP64 chain, relative to
+# each column's largest |Zc|: both covariances are within about n 2^-53 max|Xc_.j| max|Xc_.k|
+# of the exact one, and the whitening multiplies that by the conditioning of S (tens here),
+# so agreement is expected near 1e-15; the bar leaves four orders of magnitude.
+REL_ZC_TC = 1e-11
 PRECISIONS = ["f32", "split_bf16"]
 
 
@@ -37,8 +42,8 @@ def _built():
     O.build()
 
 
-def _ctx(X, n1, precision="f32", whiten="chol", ridge=0.1):
-    return frr.Context(X, n1, precision=precision, whiten=whiten, ridge=ridge)
+def _ctx(X, n1, precision="f32", whiten="chol", ridge=0.1, covariance="tensor"):
+    return frr.Context(X, n1, precision=precision, whiten=whiten, ridge=ridge, covariance=covariance)
 
 
 # ------------------------------------------------------------ assignments ----
@@ -77,7 +82,7 @@ def test_exact_enumeration_all_ranks_n20():
 @pytest.mark.parametrize("n,d,whiten", [(60, 10, "chol"), (100, 100, "ridge"), (40, 7, "diag"), (333, 129, "chol")])
 def test_whitened_covariates_bit_exact(n, d, whiten):
     X = ar1_covariates(n, d, 40 + d, 0.5) * 3.0 + 1.5
-    with _ctx(X, n // 2, whiten=whiten) as ctx:
+    with _ctx(X, n // 2, whiten=whiten, covariance="fp64_chain") as ctx:
         got = frr.frr_whitened(ctx)
     want, *_ = O.prep(X, whiten, 0.1)
     assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
@@ -101,7 +106,7 @@ def test_whitened_covariates_bit_exact_extreme_magnitudes(case):
         X[:, d // 2:] *= 2.0 ** 300
     else:
         X = X * 2.0 ** -500
-    with _ctx(X, n // 2, whiten="ridge") as ctx:
+    with _ctx(X, n // 2, whiten="ridge", covariance="fp64_chain") as ctx:
         got = frr.frr_whitened(ctx)
     want, *_ = O.prep(X, "ridge", 0.1)
     assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
@@ -110,10 +115,57 @@ def test_whitened_covariates_bit_exact_extreme_magnitudes(case):
 def test_whitened_precision_workload_bit_exact():
     w = workload("precision_n1000_d1000")
     X = w.covariates()
-    with _ctx(X, w.n1, whiten="ridge") as ctx:
+    with _ctx(X, w.n1, whiten="ridge", covariance="fp64_chain") as ctx:
         got = frr.frr_whitened(ctx)
     want, *_ = O.prep(X, "ridge", 0.1)
     assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
+def _zc_err(got, want):
+    scale = np.abs(want).max(axis=0)
+    scale = np.where(scale > 0, scale, 1.0)
+    return (np.abs(got - want) / scale).max()
+
+
+@pytest.mark.parametrize("n,d,whiten,kind", [(60, 10, "chol", "ar1"), (100, 100, "ridge", "ar1"),
+                                             (40, 7, "diag", "ar1"), (333, 129, "chol", "ar1"),
+                                             (65, 257, "ridge", "ar1"), (2048, 300, "chol", "mixed"),
+                                             (1000, 1000, "ridge", "mixed")])
+def test_whitened_covariates_tensor_covariance(n, d, whiten, kind):
+    """The default covariance (digit products summed exactly on the tensor cores, rounded once)
+    against the oracle's FP64 chain: ragged tiles (d = 7, 129, 257, 300), one to four exact
+    512-row blocks (n = 40 ... 2048), heavy-tailed columns (the mixed recipe's lognormal quarter)."""
+    X = (ar1_covariates(n, d, 50 + d, 0.5) * 3.0 + 1.5 if kind == "ar1"
+         else mixed_standardised_covariates(n, d, 60 + d))
+    with _ctx(X, n // 2, whiten=whiten) as ctx:
+        got = frr.frr_whitened(ctx)
+    want, *_ = O.prep(X, whiten, 0.1)
+    assert _zc_err(got, want) < REL_ZC_TC
+
+
+@pytest.mark.parametrize("case", ["wide_scales", "zero_column", "tiny_and_huge", "all_tiny"])
+def test_whitened_tensor_covariance_extreme_magnitudes(case):
+    """Per-column power-of-two scales far from 1 (each column's digits are relative to its own
+    largest entry), constant columns (centred to exact zeros: their whitened entries stay exact
+    zeros), and covariates at 2^-500 (products near 2^-1000, still normal)."""
+    n, d = 90, 40
+    X = ar1_covariates(n, d, 77, 0.4)
+    if case == "wide_scales":
+        X = X * np.exp2(np.linspace(-240, 240, d))[None, :]
+    elif case == "zero_column":
+        X[:, 3] = 2.5
+        X[:, 17] = 0.0
+    elif case == "tiny_and_huge":
+        X[:, : d // 2] *= 2.0 ** -300
+        X[:, d // 2:] *= 2.0 ** 300
+    else:
+        X = X * 2.0 ** -500
+    with _ctx(X, n // 2, whiten="ridge") as ctx:
+        got = frr.frr_whitened(ctx)
+    want, *_ = O.prep(X, "ridge", 0.1)
+    assert _zc_err(got, want) < REL_ZC_TC
+    if case == "zero_column":
+        assert np.all(got[:, [3, 17]] == 0.0)
 
 
 # ---------------------------------------------------------------- balance ----
