@@ -79,30 +79,33 @@ __device__ __forceinline__ int job_at(const unsigned* __restrict__ prefix, int E
 }
 
 // Column exponents e_j (|Xc_ij| < 2^e_j; 0 for a zero column) and zeroed sums. Block: 32
-// columns x 8 row groups; the maximum of |Xc_ij| is taken on the bit patterns.
-__global__ void __launch_bounds__(256) k_cov_exp(const CovJob* __restrict__ jobs, const unsigned* __restrict__ prefix,
-                                                 int E)
+// columns x 32 row groups; the maximum of |Xc_ij| is taken on the bit patterns.
+__global__ void __launch_bounds__(1024) k_cov_exp(const CovJob* __restrict__ jobs, const unsigned* __restrict__ prefix,
+                                                  int E)
 {
     unsigned lb;
     const CovJob& J = jobs[job_at(prefix, E, blockIdx.x, lb)];
     const int n = J.n, d = J.d;
     const int j = (int)lb * 32 + threadIdx.x;
-    __shared__ unsigned long long sm[8][32];
+    __shared__ unsigned long long sm[32][33];
     unsigned long long m = 0ull;
     if (j < d)
-        for (int i = threadIdx.y; i < n; i += 8)
+        for (int i = threadIdx.y; i < n; i += 32)
             m = max(m, (unsigned long long)__double_as_longlong(J.Xc[(size_t)i * d + j]) & 0x7FFFFFFFFFFFFFFFull);
     sm[threadIdx.y][threadIdx.x] = m;
     // the sums of columns j of this block (every row), zeroed before the tensor-core kernel adds into them
     if (j < d)
-        for (int r = threadIdx.y; r < d; r += 8) J.acc[(size_t)r * d + j] = 0ll;
+        for (int r = threadIdx.y; r < d; r += 32) J.acc[(size_t)r * d + j] = 0ll;
     __syncthreads();
     if (threadIdx.y == 0 && j < d) {
-        for (int y = 1; y < 8; ++y) m = max(m, sm[y][threadIdx.x]);
+        for (int y = 1; y < 32; ++y) m = max(m, sm[y][threadIdx.x]);
         const int be = (int)(m >> 52);                 // biased exponent of the largest magnitude
         J.cexp[j] = m == 0ull ? 0 : (be == 0 ? -1022 : be - 1022);
     }
 }
+
+// 2^k for -1022 <= k <= 1023
+__device__ __forceinline__ double pow2(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
 
 // Digit planes G[s][j][i] (BF16, dpad x npad per plane, zero padding) of the scaled, rounded
 // columns. Block: a 32 x 32 tile (rows i, columns j), transposed through shared memory.
@@ -120,7 +123,12 @@ __global__ void __launch_bounds__(256) k_cov_digits(const CovJob* __restrict__ j
     for (int r = threadIdx.y; r < 32; r += 8) {
         const int i = i0 + r;
         long long v = 0;
-        if (i < n && j < d) v = __double2ll_rn(scalbn(J.Xc[(size_t)i * d + j], 55 - e));
+        if (i < n && j < d) {
+            // Xc_ij 2^(55 - e_j) in two exact power-of-two steps (55 - e_j lies in [-970, 1077]; a
+            // product that underflows is below 1/2 and rounds to 0 either way)
+            const int a = (55 - e) / 2;
+            v = __double2ll_rn(J.Xc[(size_t)i * d + j] * pow2(a) * pow2(55 - e - a));
+        }
 #pragma unroll
         for (int s = kDig - 1; s > 0; --s) {
             const long long g = ((v + 64) & 127) - 64;
@@ -326,8 +334,8 @@ k_cov_tc(const CovJob* __restrict__ jobs, const unsigned* __restrict__ prefix, i
     }
 }
 
-// S_jk = sum_jk 2^(59 + e_j + e_k - 110) / (n - 1), both halves from the sum of the element
-// on or above the diagonal. One thread per element.
+// S_jk = S_kj = sum_jk 2^(59 + e_j + e_k - 110) / (n - 1) from the sum of the element on or
+// above the diagonal; one thread per element (j, k >= j) writes both halves.
 __global__ void __launch_bounds__(256) k_cov_finish(const CovJob* __restrict__ jobs,
                                                     const unsigned* __restrict__ prefix, int E)
 {
@@ -337,9 +345,11 @@ __global__ void __launch_bounds__(256) k_cov_finish(const CovJob* __restrict__ j
     const size_t idx = (size_t)lb * 256 + threadIdx.x;
     if (idx >= (size_t)d * d) return;
     const int j = (int)(idx / d), k = (int)(idx % d);
-    const int a = min(j, k), b = max(j, k);
-    const double x = __ll2double_rn(J.acc[(size_t)a * d + b]);
-    J.S[idx] = __ddiv_rn(scalbn(x, kShift - 110 + J.cexp[a] + J.cexp[b]), (double)(J.n - 1));
+    if (k < j) return;
+    const double x = __ll2double_rn(J.acc[idx]);
+    const double v = __ddiv_rn(scalbn(x, kShift - 110 + J.cexp[j] + J.cexp[k]), (double)(J.n - 1));
+    J.S[idx] = v;
+    J.S[(size_t)k * d + j] = v;
 }
 
 size_t cov_smem_bytes() { return 1024 + (size_t)kStages * kStageBytes + (2 * kStages + 2 * kAccBufs + 1) * 8 + 16; }
@@ -362,7 +372,7 @@ bool cov_tc_map(CUtensorMap* m, const __nv_bfloat16* G, int n, int d)
 cudaError_t cov_tc_launch(const CovJob* jobs, const unsigned* const prefix[4], const unsigned total[4], int E,
                           int device, int num_sms, cudaStream_t s)
 {
-    if (total[0]) k_cov_exp<<<total[0], dim3(32, 8), 0, s>>>(jobs, prefix[0], E);
+    if (total[0]) k_cov_exp<<<total[0], dim3(32, 32), 0, s>>>(jobs, prefix[0], E);
     if (total[1]) k_cov_digits<<<total[1], dim3(32, 8), 0, s>>>(jobs, prefix[1], E);
     if (total[2]) {
         const size_t smem = cov_smem_bytes();
