@@ -79,14 +79,14 @@ enum { FRR_CHOL = 0,  /* S = L L^T, Zc = Xc L^{-T}: Hotelling T^2 (needs d <= n 
        FRR_DIAG = 2 };/* L = diag(sqrt(S_jj)): sum of squared standardised mean differences */
 
 /* how frr_init forms the covariance S = Xc^T Xc / (n - 1) of the centred covariates (Sec. 2.2) */
-enum { FRR_COV_TENSOR = 0,     /* each centred column rounded to a 56-bit integer relative to its largest
+enum { FRR_PREP_TENSOR = 0,     /* each centred column rounded to a 56-bit integer relative to its largest
                                   entry and cut into eight balanced 7-bit digits; the products of digit
                                   pairs are summed exactly on the tensor cores (integer-valued FP32
                                   accumulators), the sum of those products is formed exactly as an integer
                                   and rounded once to FP64 (the pairs whose weight lies below 2^-56 of the
                                   leading one are left out); S agrees with an FP64 dot product to about
                                   1e-16 of the columns' largest products */
-       FRR_COV_FP64_CHAIN = 1 }; /* one FP64 fused multiply-add per term, rows in ascending order: the
+       FRR_PREP_FP64_CHAIN = 1 }; /* one FP64 fused multiply-add per term, rows in ascending order: the
                                   operation sequence of the FP64 reference, so that Zc is bit-identical
                                   to it; B300's FP64 rate makes it ~1 ms at n = d = 1000 */
 
@@ -100,7 +100,7 @@ typedef struct {
     void* cuda_stream;  /* cudaStream_t to run on; NULL = the context creates its own */
     int autotune;       /* frr_batch_run only: 1 = time the split-BF16 kernel configurations on a
                            probe of the batch before its launch (see frr_autotune); default 0 */
-    int covariance;     /* FRR_COV_TENSOR (default) or FRR_COV_FP64_CHAIN */
+    int prep;           /* FRR_PREP_TENSOR (default) or FRR_PREP_FP64_CHAIN */
 } frr_opts;
 
 typedef struct {
@@ -125,7 +125,7 @@ void frr_default_opts(frr_opts* o);
 
 /* Prepares an experiment (Sec. 2.2: centre, covariance with the n-1 denominator,
  * optional ridge, Cholesky factor, whitening Zc = Xc L^{-T}; FP64 on the GPU, the covariance
- * as opts.covariance says).
+ * as opts.prep says).
  * X: host, n x d row-major FP64 (rows are units). n1: number of treated units.
  * opts: NULL for defaults. On success *out owns device memory; release it with
  * frr_destroy. Supports n <= 2048. */

@@ -284,7 +284,7 @@ frr_status check_init_args(const double* X, int64_t n, int64_t d, int64_t n1, co
     if (o.whiten != FRR_CHOL && o.whiten != FRR_RIDGE && o.whiten != FRR_DIAG) return FRR_E_ARG;
     if (o.whiten == FRR_RIDGE && !(o.ridge > 0.0 && isfinite(o.ridge))) return FRR_E_ARG;
     if (!(o.band_safety >= 1.0 && isfinite(o.band_safety))) return FRR_E_ARG;
-    if (o.covariance != FRR_COV_TENSOR && o.covariance != FRR_COV_FP64_CHAIN) return FRR_E_ARG;
+    if (o.prep != FRR_PREP_TENSOR && o.prep != FRR_PREP_FP64_CHAIN) return FRR_E_ARG;
     if (scan_x && !all_finite(X, n * d)) return FRR_E_ARG;
     if (o.whiten == FRR_CHOL && d >= n - 1) return FRR_E_DEGENERATE;
     return FRR_OK;
@@ -403,7 +403,7 @@ void frr_default_opts(frr_opts* o)
     o->band_safety = 2.0;
     o->cuda_stream = nullptr;
     o->autotune = 0;
-    o->covariance = FRR_COV_TENSOR;
+    o->prep = FRR_PREP_TENSOR;
 }
 
 const char* frr_strerror(frr_status s)

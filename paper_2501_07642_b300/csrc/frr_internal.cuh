@@ -223,6 +223,34 @@ struct CovJob {
     double* S;                  // d x d covariance (output)
     int* status;                // the preparation's status word (bit 2: a bounded wait expired)
 };
+// One experiment's forward-substitution updates across 256-column blocks from digit products
+// on the tensor cores (frr_prep_tc.cu): after block b, rows i of the working Zc and rows
+// 256 (b + 1) + j of L, both over the block's columns, give ZT_i,256(b+1)+j -= their product.
+struct FwdJob {
+    int n, d, npadA, dpadB;     // plane rows: 128 ceil(n / 128), 128 ceil((d - 256) / 128)
+    double* ZT;                 // working Zc, n x d row-major
+    const double* L;            // Cholesky factor, d x d row-major (lower part)
+    int* expA;                  // n row exponents of the Zc block
+    int* expB;                  // d - 256 row exponents of the L rows
+    __nv_bfloat16* GA;          // 8 planes, npadA x 256 each
+    __nv_bfloat16* GB;          // 8 planes, dpadB x 256 each
+    const CUtensorMap* mapA;    // over GA (8 npadA rows x 256 columns), in device memory
+    const CUtensorMap* mapB;    // over GB
+    long long* acc;             // n x d int64 sums, zero between blocks
+    int* status;
+};
+int fwd_tc_npadA(int n);
+int fwd_tc_dpadB(int d);
+size_t fwd_tc_plane_bytes_a(int n);
+size_t fwd_tc_plane_bytes_b(int d);
+// blocks (or work units) per experiment of the three launches after block b (0 when no
+// column follows the block)
+unsigned fwd_tc_digit_blocks(int n, int d, int b);
+unsigned fwd_tc_units(int n, int d, int b);
+unsigned fwd_tc_apply_blocks(int n, int d, int b);
+bool fwd_tc_maps(CUtensorMap* ma, CUtensorMap* mb, const FwdJob& j);
+cudaError_t fwd_tc_launch(const FwdJob* jobs, const unsigned* const prefix[3], const unsigned total[3], int E, int b,
+                          int device, int num_sms, cudaStream_t s);
 int cov_tc_npad(int n);
 int cov_tc_dpad(int d);
 size_t cov_tc_plane_bytes(int n, int d);

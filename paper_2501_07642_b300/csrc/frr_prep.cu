@@ -32,10 +32,12 @@ namespace frr {
 // One experiment's preparation as the kernels see it (device pointers).
 struct PrepJob {
     int n, d, n1, whiten, kpad, dpad32, kused;
-    int cov_tc;  // covariance from digit products on the tensor cores (else the FP64 chain below)
+    int tc;  // covariance and cross-block forward-substitution updates from digit products on the tensor
+             // cores (else the FP64 chains below)
     double ridge;
     // temporaries
     double *X, *xbar, *Xc, *S, *Adiag, *Lm, *ZT, *scal, *eps;
+    long long* facc;  // forward-substitution sums of the tensor-core updates (n x d), or null
     int* status;
     // outputs (the context's arrays)
     double* Zc64;
@@ -112,6 +114,7 @@ __global__ void k_center(PJ_ARGS)
     const double v = __dsub_rn(J.X[idx], J.xbar[idx % J.d]);
     J.Xc[idx] = v;
     J.ZT[idx] = v;  // the forward substitution works in place on a copy of Xc
+    if (J.facc) J.facc[idx] = 0ll;
 }
 
 // S_jk = sum_i Xc_ij Xc_ik / (n - 1) for k >= j, mirrored (the product is commutative,
@@ -495,6 +498,16 @@ __global__ void __launch_bounds__(kP * kPW) k_fwd_panel(PJ_ARGS, int p)
 
 // T_ij -= L_jk z_ik for k in panel p (ascending), j >= k0 + pw. 32 x 32 tiles, local block
 // b = (row tile) * (column tiles) + (column tile).
+// Columns a panel's trailing update reaches: all later ones, or in tensor-core mode those of
+// its own 256-column block (later blocks receive the block's contributions at once, from
+// digit products, after its last panel).
+__host__ __device__ inline int fwd_trailing_end(const PrepJob& j, int k0)
+{
+    if (!j.tc) return j.d;
+    const int e = (k0 / 256 + 1) * 256;
+    return e < j.d ? e : j.d;
+}
+
 __global__ void __launch_bounds__(256) k_fwd_trailing(PJ_ARGS, int p)
 {
     unsigned lb;
@@ -503,19 +516,20 @@ __global__ void __launch_bounds__(256) k_fwd_trailing(PJ_ARGS, int p)
     const int pw = (d - k0) < kP ? (d - k0) : kP;
     const double* __restrict__ L = J.Lm;
     double* __restrict__ T = J.ZT;
-    const unsigned gx = (unsigned)((d - k0 - pw + 31) / 32);
+    const int cend = fwd_trailing_end(J, k0);
+    const unsigned gx = (unsigned)((cend - k0 - pw + 31) / 32);
     __shared__ double Zi[32][kP + 1], Lj[32][kP + 1];
     const int i0 = 32 * (int)(lb / gx), j0 = k0 + pw + 32 * (int)(lb % gx);
     for (int e = threadIdx.x; e < 32 * kP; e += blockDim.x) {
         const int rr = e / kP, kk = e % kP;
         Zi[rr][kk] = (i0 + rr < n && kk < pw) ? T[(size_t)(i0 + rr) * d + k0 + kk] : 0.0;
-        Lj[rr][kk] = (j0 + rr < d && kk < pw) ? L[(size_t)(j0 + rr) * d + k0 + kk] : 0.0;
+        Lj[rr][kk] = (j0 + rr < cend && kk < pw) ? L[(size_t)(j0 + rr) * d + k0 + kk] : 0.0;
     }
     __syncthreads();
     const int jj = threadIdx.x & 31;
     for (int ii = threadIdx.x >> 5; ii < 32; ii += blockDim.x >> 5) {
         const int i = i0 + ii, j = j0 + jj;
-        if (i >= n || j >= d) continue;
+        if (i >= n || j >= cend) continue;
         double v = T[(size_t)i * d + j];
         for (int kk = 0; kk < pw; ++kk) v = __fma_rn(-Lj[jj][kk], Zi[ii][kk], v);
         T[(size_t)i * d + j] = v;
@@ -734,11 +748,11 @@ struct JobBlocks {
     static unsigned colmean(const PrepJob& j) { return (unsigned)ceil_div(j.d, 32); }
     static unsigned cols32(const PrepJob& j) { return (unsigned)ceil_div(j.d, 32); }
     static unsigned center(const PrepJob& j) { return (unsigned)(((size_t)j.n * j.d + 255) / 256); }
-    static unsigned cov(const PrepJob& j) { return j.cov_tc ? 0u : (unsigned)(ceil_div(j.d, 32) * ceil_div(j.d, 8)); }
-    static unsigned cov_exp(const PrepJob& j) { return j.cov_tc ? cov_tc_exp_blocks(j.n, j.d) : 0u; }
-    static unsigned cov_digits(const PrepJob& j) { return j.cov_tc ? cov_tc_digit_blocks(j.n, j.d) : 0u; }
-    static unsigned cov_units(const PrepJob& j) { return j.cov_tc ? cov_tc_units(j.n, j.d) : 0u; }
-    static unsigned cov_finish(const PrepJob& j) { return j.cov_tc ? cov_tc_finish_blocks(j.n, j.d) : 0u; }
+    static unsigned cov(const PrepJob& j) { return j.tc ? 0u : (unsigned)(ceil_div(j.d, 32) * ceil_div(j.d, 8)); }
+    static unsigned cov_exp(const PrepJob& j) { return j.tc ? cov_tc_exp_blocks(j.n, j.d) : 0u; }
+    static unsigned cov_digits(const PrepJob& j) { return j.tc ? cov_tc_digit_blocks(j.n, j.d) : 0u; }
+    static unsigned cov_units(const PrepJob& j) { return j.tc ? cov_tc_units(j.n, j.d) : 0u; }
+    static unsigned cov_finish(const PrepJob& j) { return j.tc ? cov_tc_finish_blocks(j.n, j.d) : 0u; }
     static unsigned one(const PrepJob&) { return 1u; }
     static unsigned init_L(const PrepJob& j) { return (unsigned)(((size_t)j.d * j.d + 255) / 256); }
     static unsigned chol_diag(const PrepJob& j, int p)
@@ -772,9 +786,13 @@ struct JobBlocks {
     {
         const int k0 = kP * p;
         if (k0 >= j.d) return 0u;
-        const int pw = std::min(kP, j.d - k0), below = j.d - k0 - pw;
+        const int pw = std::min(kP, j.d - k0), below = fwd_trailing_end(j, k0) - k0 - pw;
         return below > 0 ? (unsigned)(ceil_div(below, 32) * ceil_div(j.n, 32)) : 0u;
     }
+    // the tensor-core update after the last panel of 256-column block p / 8 (tensor-core mode)
+    static unsigned fwd_xdigits(const PrepJob& j, int p) { return (j.tc && p % 8 == 7) ? fwd_tc_digit_blocks(j.n, j.d, p / 8) : 0u; }
+    static unsigned fwd_xunits(const PrepJob& j, int p) { return (j.tc && p % 8 == 7) ? fwd_tc_units(j.n, j.d, p / 8) : 0u; }
+    static unsigned fwd_xapply(const PrepJob& j, int p) { return (j.tc && p % 8 == 7) ? fwd_tc_apply_blocks(j.n, j.d, p / 8) : 0u; }
     static unsigned derive(const PrepJob& j) { return (unsigned)(((size_t)j.kpad * j.dpad32 + 255) / 256); }
     static unsigned digits(const PrepJob& j) { return (unsigned)(((size_t)j.kpad * j.d + 255) / 256); }
     static unsigned band(const PrepJob& j) { return (unsigned)j.d; }
@@ -803,15 +821,23 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         joff[(size_t)e] = bytes;
         bytes += 3 * align256(n * d * 8) + 2 * align256(d * d * 8) + 2 * align256(d * 8) + align256(4 * 8) +
                  align256(2 * d * 8);
-        if (c->opts.covariance == FRR_COV_TENSOR)  // digit planes, exponents, int64 sums
+        if (c->opts.prep == FRR_PREP_TENSOR) {
+            // covariance: digit planes, exponents, int64 sums; forward substitution (d > 256): the
+            // two plane sets, row exponents, int64 sums
             bytes += align256(cov_tc_plane_bytes((int)n, (int)d)) + align256(d * 4) + align256(d * d * 8);
+            if (d > 256)
+                bytes += align256(fwd_tc_plane_bytes_a((int)n)) + align256(fwd_tc_plane_bytes_b((int)d)) +
+                         align256(n * 4) + align256(d * 4) + align256(n * d * 8);
+        }
         max_panels = std::max(max_panels, ceil_div(c->d, kP));
     }
     // the covariance jobs and their tensor maps (64-byte aligned)
     const size_t covjob_off = bytes;
     bytes += align256((size_t)E * sizeof(CovJob));
-    const size_t maps_off = bytes;
-    bytes += align256((size_t)E * sizeof(CUtensorMap));
+    const size_t fwdjob_off = bytes;
+    bytes += align256((size_t)E * sizeof(FwdJob));
+    const size_t maps_off = bytes;  // per job: the covariance's map, then the forward substitution's two
+    bytes += align256((size_t)E * 3 * sizeof(CUtensorMap));
     const size_t status_off = bytes;
     bytes += align256((size_t)E * sizeof(int));
     const size_t table_off = bytes;
@@ -836,7 +862,7 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
             PrepJob& J = jobs[(size_t)e];
             J.n = (int)c->n; J.d = (int)c->d; J.n1 = (int)c->n1; J.whiten = c->opts.whiten;
             J.kpad = c->kpad; J.dpad32 = c->dpad32; J.kused = c->kused; J.ridge = c->opts.ridge;
-            J.cov_tc = c->opts.covariance == FRR_COV_TENSOR ? 1 : 0;
+            J.tc = c->opts.prep == FRR_PREP_TENSOR ? 1 : 0;
             J.Zc64 = c->Zc64; J.Z32 = c->Z32; J.Zhi = c->Zhi; J.Zlo = c->Zlo; J.Zq = c->Zq;
             J.Q = c->Q; J.Qsum = c->Qsum; J.qexp = c->qexp;
         }
@@ -857,6 +883,9 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         add_launch([p](const PrepJob& j) { return JobBlocks::chol_trailing(j, p); });
         add_launch([p](const PrepJob& j) { return JobBlocks::fwd_trailing(j, p); });
         add_launch([p](const PrepJob& j) { return JobBlocks::chol_lookahead(j, p); });
+        add_launch([p](const PrepJob& j) { return JobBlocks::fwd_xdigits(j, p); });
+        add_launch([p](const PrepJob& j) { return JobBlocks::fwd_xunits(j, p); });
+        add_launch([p](const PrepJob& j) { return JobBlocks::fwd_xapply(j, p); });
     }
     add_launch(JobBlocks::center);  // Zc copy
     add_launch(JobBlocks::cols32);  // qexp
@@ -873,7 +902,8 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
     std::vector<int> h_status((size_t)E, 0);
     std::vector<std::vector<double>> h_eps((size_t)E);
     std::vector<CovJob> cjobs((size_t)E);
-    std::vector<CUtensorMap> cmaps((size_t)E);
+    std::vector<FwdJob> fjobs((size_t)E);
+    std::vector<CUtensorMap> cmaps((size_t)E * 3);
     auto fail = [&](cudaError_t e) {
         cudaGetLastError();
         rc = (e == cudaErrorMemoryAllocation) ? FRR_E_NOMEM : FRR_E_CUDA;
@@ -892,14 +922,30 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         h_eps[(size_t)e].resize(2 * d);
         CovJob& C = cjobs[(size_t)e];
         C = CovJob{};
-        if (J.cov_tc) {
+        if (J.tc) {
             C.n = J.n; C.d = J.d; C.npad = cov_tc_npad(J.n); C.dpad = cov_tc_dpad(J.d);
             C.Xc = J.Xc; C.S = J.S; C.status = J.status;
             C.G = reinterpret_cast<__nv_bfloat16*>(take(cov_tc_plane_bytes(J.n, J.d)));
             C.cexp = reinterpret_cast<int*>(take(d * 4));
             C.acc = reinterpret_cast<long long*>(take(d * d * 8));
-            C.gmap = reinterpret_cast<const CUtensorMap*>(base + maps_off) + e;
-            if (!cov_tc_map(&cmaps[(size_t)e], C.G, J.n, J.d)) { rc = FRR_E_CUDA; goto cleanup; }
+            C.gmap = reinterpret_cast<const CUtensorMap*>(base + maps_off) + 3 * e;
+            if (!cov_tc_map(&cmaps[3 * (size_t)e], C.G, J.n, J.d)) { rc = FRR_E_CUDA; goto cleanup; }
+        }
+        FwdJob& F = fjobs[(size_t)e];
+        F = FwdJob{};
+        J.facc = nullptr;
+        if (J.tc && J.d > 256) {
+            F.n = J.n; F.d = J.d; F.npadA = fwd_tc_npadA(J.n); F.dpadB = fwd_tc_dpadB(J.d);
+            F.ZT = J.ZT; F.L = J.Lm; F.status = J.status;
+            F.GA = reinterpret_cast<__nv_bfloat16*>(take(fwd_tc_plane_bytes_a(J.n)));
+            F.GB = reinterpret_cast<__nv_bfloat16*>(take(fwd_tc_plane_bytes_b(J.d)));
+            F.expA = reinterpret_cast<int*>(take(n * 4));
+            F.expB = reinterpret_cast<int*>(take(d * 4));
+            F.acc = reinterpret_cast<long long*>(take(n * d * 8));
+            J.facc = F.acc;
+            F.mapA = reinterpret_cast<const CUtensorMap*>(base + maps_off) + 3 * e + 1;
+            F.mapB = reinterpret_cast<const CUtensorMap*>(base + maps_off) + 3 * e + 2;
+            if (!fwd_tc_maps(&cmaps[3 * (size_t)e + 1], &cmaps[3 * (size_t)e + 2], F)) { rc = FRR_E_CUDA; goto cleanup; }
         }
     }
     PREP_CHECK(cudaMemsetAsync(base + status_off, 0, (size_t)E * sizeof(int), s));
@@ -908,8 +954,9 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
                                    cudaMemcpyHostToDevice, s));
     PREP_CHECK(cudaMemcpyAsync(base + table_off, jobs.data(), (size_t)E * sizeof(PrepJob), cudaMemcpyHostToDevice, s));
     PREP_CHECK(cudaMemcpyAsync(base + covjob_off, cjobs.data(), (size_t)E * sizeof(CovJob), cudaMemcpyHostToDevice, s));
-    PREP_CHECK(cudaMemcpyAsync(base + maps_off, cmaps.data(), (size_t)E * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
-                               s));
+    PREP_CHECK(cudaMemcpyAsync(base + fwdjob_off, fjobs.data(), (size_t)E * sizeof(FwdJob), cudaMemcpyHostToDevice, s));
+    PREP_CHECK(cudaMemcpyAsync(base + maps_off, cmaps.data(), (size_t)E * 3 * sizeof(CUtensorMap),
+                               cudaMemcpyHostToDevice, s));
     PREP_CHECK(cudaMemcpyAsync(base + pref_off, pref.data(), pref.size() * sizeof(unsigned), cudaMemcpyHostToDevice,
                                s));
     {
@@ -953,8 +1000,8 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         PREP_CHECK(cudaStreamWaitEvent(aux, evs[2], 0));
         PREP_CHECK(cudaStreamWaitEvent(ts, evs[2], 0));
         for (int p = 0; p < max_panels; ++p) {
-            const size_t ld = li, lp = li + 1, lf = li + 2, lt = li + 3, lft = li + 4, la = li + 5;
-            li += 6;
+            const size_t ld = li, lp = li + 1, lf = li + 2, lt = li + 3, lft = li + 4, la = li + 5, lx = li + 6;
+            li += 9;
             if (unsigned g = total(ld)) k_chol_diag<<<g, kP * kPW, 0, s>>>(dj, P(ld), E, p);
             if (p > 0) PREP_CHECK(cudaStreamWaitEvent(s, evs[1], 0));  // trailing rest p - 1
             if (unsigned g = total(lp)) k_chol_below<<<g, kP * kPW, 0, s>>>(dj, P(lp), E, p);
@@ -966,6 +1013,15 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
             if (unsigned g = total(lt)) k_chol_trailing<<<g, 256, 0, ts>>>(dj, P(lt), E, p);
             PREP_CHECK(cudaEventRecord(evs[1], ts));
             if (unsigned g = total(lft)) k_fwd_trailing<<<g, 256, 0, aux>>>(dj, P(lft), E, p);
+            if (p % 8 == 7) {
+                // after the last panel of 256-column block p / 8: the block's contributions to every
+                // later column, from digit products on the tensor cores (tensor-core mode)
+                const unsigned* xp[3] = {P(lx), P(lx + 1), P(lx + 2)};
+                const unsigned xt[3] = {total(lx), total(lx + 1), total(lx + 2)};
+                if (xt[0] || xt[1] || xt[2])
+                    PREP_CHECK(fwd_tc_launch(reinterpret_cast<const FwdJob*>(base + fwdjob_off), xp, xt, E, p / 8,
+                                             device, ctxs[0]->num_sms, aux));
+            }
         }
         PREP_CHECK(cudaEventRecord(evs[2], aux));
         PREP_CHECK(cudaStreamWaitEvent(s, evs[2], 0));

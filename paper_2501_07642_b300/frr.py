@@ -26,8 +26,8 @@ FRR_CHOL, FRR_RIDGE, FRR_DIAG = 0, 1, 2
 FRR_EXACT_SEED = (1 << 64) - 1
 PRECISION = {"split_bf16": FRR_SPLIT_BF16, "f32": FRR_F32}
 WHITEN = {"chol": FRR_CHOL, "ridge": FRR_RIDGE, "diag": FRR_DIAG}
-FRR_COV_TENSOR, FRR_COV_FP64_CHAIN = 0, 1
-COVARIANCE = {"tensor": FRR_COV_TENSOR, "fp64_chain": FRR_COV_FP64_CHAIN}
+FRR_PREP_TENSOR, FRR_PREP_FP64_CHAIN = 0, 1
+PREP = {"tensor": FRR_PREP_TENSOR, "fp64_chain": FRR_PREP_FP64_CHAIN}
 
 
 class FrrError(RuntimeError):
@@ -40,7 +40,7 @@ class FrrError(RuntimeError):
 class frr_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("whiten", ctypes.c_int), ("ridge", ctypes.c_double),
                 ("band_safety", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("autotune", ctypes.c_int),
-                ("covariance", ctypes.c_int)]
+                ("prep", ctypes.c_int)]
 
 
 class frr_stats(ctypes.Structure):
@@ -185,13 +185,13 @@ class Context:
     """Owns one frr_ctx (frr_init ... frr_destroy)."""
 
     def __init__(self, X, n1: int, precision: str = "split_bf16", whiten: str = "chol", ridge: float = 0.1,
-                 band_safety: float = 2.0, stream=None, covariance: str = "tensor"):
+                 band_safety: float = 2.0, stream=None, prep: str = "tensor"):
         X = np.ascontiguousarray(X, dtype=np.float64)
         n, d = X.shape
         o = frr_default_opts()
         o.precision = PRECISION[precision]
         o.whiten = WHITEN[whiten]
-        o.covariance = COVARIANCE[covariance]
+        o.prep = PREP[prep]
         o.ridge = float(ridge)
         o.band_safety = float(band_safety)
         o.cuda_stream = None if stream is None else int(getattr(stream, "cuda_stream", stream))
@@ -368,7 +368,7 @@ def frr_test_wait_expiry(ctx: Context, wait_cycles: int) -> int:
 
 
 def frr_batch_run(experiments, precision: str = "split_bf16", band_safety: float = 2.0, stream=None,
-                  autotune: bool = False, covariance: str = "tensor"):
+                  autotune: bool = False, prep: str = "tensor"):
     """experiments: list of dicts with keys X, n1, seed, B (and optional first_draw, q or
     threshold, whiten, ridge, Y, tau, alpha). Returns (list of result dicts, stats dict).
     Outputs are host numpy arrays. autotune: time the kernel configurations on a probe of
@@ -417,7 +417,7 @@ def frr_batch_run(experiments, precision: str = "split_bf16", band_safety: float
     opts.band_safety = float(band_safety)
     opts.cuda_stream = None if stream is None else int(getattr(stream, "cuda_stream", stream))
     opts.autotune = 1 if autotune else 0
-    opts.covariance = COVARIANCE[covariance]
+    opts.prep = PREP[prep]
     st = frr_batch_stats()
     rc = lib().frr_batch_run(ctypes.addressof(arr), E, ctypes.byref(opts), ctypes.byref(st))
     res = []

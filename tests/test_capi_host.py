@@ -36,7 +36,7 @@ def test_every_declared_entry_point_is_exported(frr):
 def test_defaults_and_strerror(frr):
     o = frr.frr_default_opts()
     assert (o.precision, o.whiten, o.ridge, o.band_safety) == (frr.FRR_SPLIT_BF16, frr.FRR_CHOL, 0.1, 2.0)
-    assert o.covariance == frr.FRR_COV_TENSOR and o.autotune == 0
+    assert o.prep == frr.FRR_PREP_TENSOR and o.autotune == 0
     assert o.cuda_stream is None
     for code in frr.STATUS:
         assert frr.strerror(code)
@@ -71,7 +71,7 @@ def test_init_rejects_bad_arguments_without_a_gpu(frr):
     assert _init_status(frr, X, 10, 3, 5, o) == -1
     o = frr.frr_default_opts(); o.band_safety = 0.5
     assert _init_status(frr, X, 10, 3, 5, o) == -1
-    o = frr.frr_default_opts(); o.covariance = 2
+    o = frr.frr_default_opts(); o.prep = 2
     assert _init_status(frr, X, 10, 3, 5, o) == -1
 
 

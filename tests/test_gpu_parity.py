@@ -42,8 +42,8 @@ def _built():
     O.build()
 
 
-def _ctx(X, n1, precision="f32", whiten="chol", ridge=0.1, covariance="tensor"):
-    return frr.Context(X, n1, precision=precision, whiten=whiten, ridge=ridge, covariance=covariance)
+def _ctx(X, n1, precision="f32", whiten="chol", ridge=0.1, prep="tensor"):
+    return frr.Context(X, n1, precision=precision, whiten=whiten, ridge=ridge, prep=prep)
 
 
 # ------------------------------------------------------------ assignments ----
@@ -82,7 +82,7 @@ def test_exact_enumeration_all_ranks_n20():
 @pytest.mark.parametrize("n,d,whiten", [(60, 10, "chol"), (100, 100, "ridge"), (40, 7, "diag"), (333, 129, "chol")])
 def test_whitened_covariates_bit_exact(n, d, whiten):
     X = ar1_covariates(n, d, 40 + d, 0.5) * 3.0 + 1.5
-    with _ctx(X, n // 2, whiten=whiten, covariance="fp64_chain") as ctx:
+    with _ctx(X, n // 2, whiten=whiten, prep="fp64_chain") as ctx:
         got = frr.frr_whitened(ctx)
     want, *_ = O.prep(X, whiten, 0.1)
     assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
@@ -106,7 +106,7 @@ def test_whitened_covariates_bit_exact_extreme_magnitudes(case):
         X[:, d // 2:] *= 2.0 ** 300
     else:
         X = X * 2.0 ** -500
-    with _ctx(X, n // 2, whiten="ridge", covariance="fp64_chain") as ctx:
+    with _ctx(X, n // 2, whiten="ridge", prep="fp64_chain") as ctx:
         got = frr.frr_whitened(ctx)
     want, *_ = O.prep(X, "ridge", 0.1)
     assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
@@ -115,7 +115,7 @@ def test_whitened_covariates_bit_exact_extreme_magnitudes(case):
 def test_whitened_precision_workload_bit_exact():
     w = workload("precision_n1000_d1000")
     X = w.covariates()
-    with _ctx(X, w.n1, whiten="ridge", covariance="fp64_chain") as ctx:
+    with _ctx(X, w.n1, whiten="ridge", prep="fp64_chain") as ctx:
         got = frr.frr_whitened(ctx)
     want, *_ = O.prep(X, "ridge", 0.1)
     assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
