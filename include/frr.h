@@ -78,17 +78,23 @@ enum { FRR_CHOL = 0,  /* S = L L^T, Zc = Xc L^{-T}: Hotelling T^2 (needs d <= n 
        FRR_RIDGE = 1, /* S + ridge * (tr S / d) I = L L^T (any d; needs ridge > 0) */
        FRR_DIAG = 2 };/* L = diag(sqrt(S_jj)): sum of squared standardised mean differences */
 
-/* how frr_init forms the covariance S = Xc^T Xc / (n - 1) of the centred covariates (Sec. 2.2) */
-enum { FRR_PREP_TENSOR = 0,     /* each centred column rounded to a 56-bit integer relative to its largest
-                                  entry and cut into eight balanced 7-bit digits; the products of digit
-                                  pairs are summed exactly on the tensor cores (integer-valued FP32
-                                  accumulators), the sum of those products is formed exactly as an integer
-                                  and rounded once to FP64 (the pairs whose weight lies below 2^-56 of the
-                                  leading one are left out); S agrees with an FP64 dot product to about
-                                  1e-16 of the columns' largest products */
-       FRR_PREP_FP64_CHAIN = 1 }; /* one FP64 fused multiply-add per term, rows in ascending order: the
-                                  operation sequence of the FP64 reference, so that Zc is bit-identical
-                                  to it; B300's FP64 rate makes it ~1 ms at n = d = 1000 */
+/* how frr_init rounds the sums of its FP64 preparation (Sec. 2.2 defines the covariance
+ * S = Xc^T Xc / (n - 1), its Cholesky factor S = L L^T and Zc = Xc L^{-T}, not their rounding) */
+enum { FRR_PREP_TENSOR = 0,    /* the covariance, and the forward substitution's updates of every column
+                                  from the 256-column blocks before it, as exact integer sums on the tensor
+                                  cores: each vector (a centred column; a row of Zc or of L over one block)
+                                  rounded to a 56-bit integer relative to its largest entry and cut into
+                                  eight balanced 7-bit digits, the products of digit pairs summed exactly
+                                  (integer-valued FP32 accumulators) and the sum rounded once to FP64 (the
+                                  pairs whose weight lies below 2^-56 of the leading one are left out); the
+                                  Cholesky factor and the updates inside a block keep the FP64 chain below.
+                                  Each sum is within about (terms) 2^-53 max|a| max|b| of the exact one, the
+                                  order of an FP64 dot product's own error; Zc agrees with the FP64 chain to
+                                  ~1e-14 of each column's largest entry on the workloads tested. Default. */
+       FRR_PREP_FP64_CHAIN = 1 }; /* every dot-product term added by one FP64 fused multiply-add, terms in
+                                  ascending order: the operation sequence of the FP64 reference, so that Zc
+                                  is bit-identical to it; B300's FP64 rate makes frr_init ~3.8 ms at
+                                  n = d = 1000 (~2.7 ms in FRR_PREP_TENSOR) */
 
 #define FRR_EXACT_SEED UINT64_MAX
 
@@ -124,8 +130,8 @@ typedef struct {
 void frr_default_opts(frr_opts* o);
 
 /* Prepares an experiment (Sec. 2.2: centre, covariance with the n-1 denominator,
- * optional ridge, Cholesky factor, whitening Zc = Xc L^{-T}; FP64 on the GPU, the covariance
- * as opts.prep says).
+ * optional ridge, Cholesky factor, whitening Zc = Xc L^{-T}; FP64 on the GPU, its sums
+ * rounded as opts.prep says).
  * X: host, n x d row-major FP64 (rows are units). n1: number of treated units.
  * opts: NULL for defaults. On success *out owns device memory; release it with
  * frr_destroy. Supports n <= 2048. */
