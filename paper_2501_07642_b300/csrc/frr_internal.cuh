@@ -223,6 +223,9 @@ struct CovJob {
     double* S;                  // d x d covariance (output)
     int* status;                // the preparation's status word (bit 2: a bounded wait expired)
 };
+// Columns per block of the forward substitution's tensor-core updates (a multiple of the
+// panel width, 32, and of the digit kernel's K block, 64).
+constexpr int kFwdBlock = 256;
 // One experiment's forward-substitution updates across 256-column blocks from digit products
 // on the tensor cores (frr_prep_tc.cu): after block b, rows i of the working Zc and rows
 // 256 (b + 1) + j of L, both over the block's columns, give ZT_i,256(b+1)+j -= their product.

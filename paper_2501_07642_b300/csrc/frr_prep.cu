@@ -499,12 +499,12 @@ __global__ void __launch_bounds__(kP * kPW) k_fwd_panel(PJ_ARGS, int p)
 // T_ij -= L_jk z_ik for k in panel p (ascending), j >= k0 + pw. 32 x 32 tiles, local block
 // b = (row tile) * (column tiles) + (column tile).
 // Columns a panel's trailing update reaches: all later ones, or in tensor-core mode those of
-// its own 256-column block (later blocks receive the block's contributions at once, from
+// its own kFwdBlock-column block (later blocks receive the block's contributions at once, from
 // digit products, after its last panel).
 __host__ __device__ inline int fwd_trailing_end(const PrepJob& j, int k0)
 {
     if (!j.tc) return j.d;
-    const int e = (k0 / 256 + 1) * 256;
+    const int e = (k0 / kFwdBlock + 1) * kFwdBlock;
     return e < j.d ? e : j.d;
 }
 
@@ -789,10 +789,10 @@ struct JobBlocks {
         const int pw = std::min(kP, j.d - k0), below = fwd_trailing_end(j, k0) - k0 - pw;
         return below > 0 ? (unsigned)(ceil_div(below, 32) * ceil_div(j.n, 32)) : 0u;
     }
-    // the tensor-core update after the last panel of 256-column block p / 8 (tensor-core mode)
-    static unsigned fwd_xdigits(const PrepJob& j, int p) { return (j.tc && p % 8 == 7) ? fwd_tc_digit_blocks(j.n, j.d, p / 8) : 0u; }
-    static unsigned fwd_xunits(const PrepJob& j, int p) { return (j.tc && p % 8 == 7) ? fwd_tc_units(j.n, j.d, p / 8) : 0u; }
-    static unsigned fwd_xapply(const PrepJob& j, int p) { return (j.tc && p % 8 == 7) ? fwd_tc_apply_blocks(j.n, j.d, p / 8) : 0u; }
+    // the tensor-core update after the last panel of each kFwdBlock-column block (tensor-core mode)
+    static unsigned fwd_xdigits(const PrepJob& j, int p) { return (j.tc && p % (kFwdBlock / kP) == kFwdBlock / kP - 1) ? fwd_tc_digit_blocks(j.n, j.d, p / (kFwdBlock / kP)) : 0u; }
+    static unsigned fwd_xunits(const PrepJob& j, int p) { return (j.tc && p % (kFwdBlock / kP) == kFwdBlock / kP - 1) ? fwd_tc_units(j.n, j.d, p / (kFwdBlock / kP)) : 0u; }
+    static unsigned fwd_xapply(const PrepJob& j, int p) { return (j.tc && p % (kFwdBlock / kP) == kFwdBlock / kP - 1) ? fwd_tc_apply_blocks(j.n, j.d, p / (kFwdBlock / kP)) : 0u; }
     static unsigned derive(const PrepJob& j) { return (unsigned)(((size_t)j.kpad * j.dpad32 + 255) / 256); }
     static unsigned digits(const PrepJob& j) { return (unsigned)(((size_t)j.kpad * j.d + 255) / 256); }
     static unsigned band(const PrepJob& j) { return (unsigned)j.d; }
@@ -822,10 +822,10 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         bytes += 3 * align256(n * d * 8) + 2 * align256(d * d * 8) + 2 * align256(d * 8) + align256(4 * 8) +
                  align256(2 * d * 8);
         if (c->opts.prep == FRR_PREP_TENSOR) {
-            // covariance: digit planes, exponents, int64 sums; forward substitution (d > 256): the
+            // covariance: digit planes, exponents, int64 sums; forward substitution (d > kFwdBlock): the
             // two plane sets, row exponents, int64 sums
             bytes += align256(cov_tc_plane_bytes((int)n, (int)d)) + align256(d * 4) + align256(d * d * 8);
-            if (d > 256)
+            if (d > (size_t)kFwdBlock)
                 bytes += align256(fwd_tc_plane_bytes_a((int)n)) + align256(fwd_tc_plane_bytes_b((int)d)) +
                          align256(n * 4) + align256(d * 4) + align256(n * d * 8);
         }
@@ -934,7 +934,7 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         FwdJob& F = fjobs[(size_t)e];
         F = FwdJob{};
         J.facc = nullptr;
-        if (J.tc && J.d > 256) {
+        if (J.tc && J.d > kFwdBlock) {
             F.n = J.n; F.d = J.d; F.npadA = fwd_tc_npadA(J.n); F.dpadB = fwd_tc_dpadB(J.d);
             F.ZT = J.ZT; F.L = J.Lm; F.status = J.status;
             F.GA = reinterpret_cast<__nv_bfloat16*>(take(fwd_tc_plane_bytes_a(J.n)));
@@ -1013,13 +1013,13 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
             if (unsigned g = total(lt)) k_chol_trailing<<<g, 256, 0, ts>>>(dj, P(lt), E, p);
             PREP_CHECK(cudaEventRecord(evs[1], ts));
             if (unsigned g = total(lft)) k_fwd_trailing<<<g, 256, 0, aux>>>(dj, P(lft), E, p);
-            if (p % 8 == 7) {
-                // after the last panel of 256-column block p / 8: the block's contributions to every
+            if (p % (kFwdBlock / kP) == kFwdBlock / kP - 1) {
+                // after the last panel of a kFwdBlock-column block: the block's contributions to every
                 // later column, from digit products on the tensor cores (tensor-core mode)
                 const unsigned* xp[3] = {P(lx), P(lx + 1), P(lx + 2)};
                 const unsigned xt[3] = {total(lx), total(lx + 1), total(lx + 2)};
                 if (xt[0] || xt[1] || xt[2])
-                    PREP_CHECK(fwd_tc_launch(reinterpret_cast<const FwdJob*>(base + fwdjob_off), xp, xt, E, p / 8,
+                    PREP_CHECK(fwd_tc_launch(reinterpret_cast<const FwdJob*>(base + fwdjob_off), xp, xt, E, p / (kFwdBlock / kP),
                                              device, ctxs[0]->num_sms, aux));
             }
         }

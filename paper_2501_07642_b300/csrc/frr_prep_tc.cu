@@ -4,7 +4,7 @@
 // columns.
 //
 // Digit products. Each operand vector (a centred column of Xc for the covariance; a row of
-// the working Zc or of L over a 256-column block for the forward substitution) is scaled by
+// the working Zc or of L over a kFwdBlock-column block for the forward substitution) is scaled by
 // a power of two, 2^(55 - e) with every entry below 2^e in magnitude, and rounded to
 // integers v (|v| <= 2^55), which are cut into eight balanced base-128 digits, v = sum_{s<8}
 // g_s 128^(7-s), g_1..g_7 in [-64, 63] and |g_0| <= 65; every digit is exact in BF16. For
@@ -53,8 +53,8 @@ constexpr int kEpiWarps = 16;
 constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 constexpr int kThreads = (kEpiWarps + 2) * 32;
 constexpr int kStatusTimeout = 2;  // the preparation's status bit of an expired bounded wait
-constexpr int kFwdBlock = 256;    // columns per block of the forward substitution
 static_assert(kPairs % kGroups == 0, "equal pair groups");
+static_assert(kFwdBlock % 64 == 0 && kFwdBlock <= kChunkKB * 64, "forward blocks of whole K blocks, one exact chunk");
 static_assert(kChunkKB * kKB * 65 * 65 < (1 << 22), "digit-product sums of one chunk stay exact in FP32");
 
 // digit pairs in order of level s + t, then s
@@ -193,7 +193,7 @@ struct CovUnits {
     }
 };
 
-// the forward substitution after 256-column block b: rows i of the working Zc (plane set A)
+// the forward substitution after kFwdBlock-column block b: rows i of the working Zc (plane set A)
 // against rows 256 (b + 1) + j of L (plane set B), both over the block's 256 columns
 struct FwdUnits {
     const FwdJob* jobs;
@@ -412,10 +412,11 @@ __global__ void __launch_bounds__(256) k_fwd_digits(const FwdJob* __restrict__ j
     const int rr = isA ? r : r - J.npadA;
     const bool valid = isA ? rr < J.n : rr < rest;
     const double* src = isA ? J.ZT + (size_t)rr * J.d + kFwdBlock * b : J.L + (size_t)(c_first + rr) * J.d + kFwdBlock * b;
-    double x[8];
+    constexpr int kPer = kFwdBlock / 32;  // entries per lane
+    double x[kPer];
     unsigned long long m = 0ull;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < kPer; ++q) {
         x[q] = valid ? src[lane + 32 * q] : 0.0;
         m = max(m, (unsigned long long)__double_as_longlong(x[q]) & 0x7FFFFFFFFFFFFFFFull);
     }
@@ -433,7 +434,7 @@ __global__ void __launch_bounds__(256) k_fwd_digits(const FwdJob* __restrict__ j
     const int a = (55 - e) / 2;
     const double s1 = pow2(a), s2 = pow2(55 - e - a);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < kPer; ++q) {
         long long v = __double2ll_rn(x[q] * s1 * s2);
         __nv_bfloat16* g = G + (size_t)rr * kFwdBlock + lane + 32 * q;
 #pragma unroll
