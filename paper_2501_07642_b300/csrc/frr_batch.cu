@@ -40,11 +40,17 @@ using namespace frr;
 namespace {
 
 // host threads that check arguments, copy the covariates into the pinned staging block (with
-// the scan for non-finite values: bound by host memory bandwidth) and create contexts; with the
-// 256-experiment workload (226 MB of covariates) 8 of them stage about 6 ms faster than 4. The
-// selection chains are enqueued from one thread: from several, the driver's calls contended
-// (4 threads were 40-60 % slower for that phase)
-constexpr int kWorkers = 8;
+// the scan for non-finite values) and create contexts: one per hardware thread, at most 16;
+// with the 256-experiment workload (226 MB of covariates) on 16 host threads, 16 of them
+// prepare ~2 ms sooner than 8, and 8 about 6 ms sooner than 4. The selection chains are
+// enqueued from one thread: from several, the driver's calls contended (4 threads were
+// 40-60 % slower for that phase)
+constexpr int kMaxWorkers = 16;
+int worker_count()
+{
+    const unsigned hw = std::thread::hardware_concurrency();
+    return hw == 0 ? 8 : (int)std::min<unsigned>(hw, kMaxWorkers);
+}
 // streams of the contexts: the selection and test chains of different experiments overlap
 constexpr int kStreams = 8;
 
@@ -93,7 +99,7 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
     // threads, each with its own stream, so that their small kernels share the SMs (the
     // contexts allocate stream-ordered from a pool, so the threads do not synchronise the
     // device through allocations).
-    const int nw = (int)std::min<int64_t>(kWorkers, E);
+    const int nw = (int)std::min<int64_t>(worker_count(), E);
     // the contexts' streams, assigned round-robin (experiment e runs on ws[e % ns])
     const int ns = (int)std::min<int64_t>(kStreams, E);
     std::vector<cudaStream_t> ws((size_t)ns, nullptr);
