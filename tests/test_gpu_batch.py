@@ -35,15 +35,17 @@ MIX = [  # (n, d, whiten, B, q, seed)
 ]
 
 
-@pytest.mark.parametrize("precision", ["split_bf16", "f32"])
-def test_batch_matches_oracle_and_single_path(precision):
+@pytest.mark.parametrize("precision,prep", [("split_bf16", "tensor"), ("f32", "tensor"), ("split_bf16", "fp64_chain")])
+def test_batch_matches_oracle_and_single_path(precision, prep):
+    """Both preparation modes: the batched preparation covers experiments with and without a
+    256-column block boundary of the forward substitution (d = 257, 299, 500) in one launch set."""
     exps, Xs = [], []
     for k, (n, d, wh, B, q, seed) in enumerate(MIX):
         X = ar1_covariates(n, d, 500 + k, 0.3)
         Xs.append(X)
         exps.append(dict(X=X, n1=n // 2, whiten=wh, ridge=0.1, seed=seed, first_draw=0 if seed == frr.FRR_EXACT_SEED
                          else 1000 * k, B=B, q=q))
-    res, stats = frr.frr_batch_run(exps, precision=precision)
+    res, stats = frr.frr_batch_run(exps, precision=precision, prep=prep)
     assert stats["status"] == 0 and stats["failed"] == 0
     for k, (x, r) in enumerate(zip(exps, res)):
         n, d, wh, B, q, seed = MIX[k]
@@ -54,7 +56,7 @@ def test_batch_matches_oracle_and_single_path(precision):
         wk, wm = O.select_from_M(M, x["first_draw"], q=q)
         assert np.array_equal(r["keys"], wk), f"experiment {k}"
         assert np.allclose(r["m64"], wm, rtol=REL_M64, atol=0)
-        with frr.Context(Xs[k], n // 2, precision=precision, whiten=wh) as ctx:
+        with frr.Context(Xs[k], n // 2, precision=precision, whiten=wh, prep=prep) as ctx:
             sk, sm = frr.frr_select(ctx, seed, x["first_draw"], B, q=q)
         assert np.array_equal(sk, r["keys"]) and np.array_equal(sm, r["m64"])
 
