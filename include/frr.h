@@ -87,14 +87,17 @@ enum { FRR_PREP_TENSOR = 0,    /* the covariance, and the forward substitution's
                                   eight balanced 7-bit digits, the products of digit pairs summed exactly
                                   (integer-valued FP32 accumulators) and the sum rounded once to FP64 (the
                                   pairs whose weight lies below 2^-56 of the leading one are left out); the
-                                  Cholesky factor and the updates inside a block keep the FP64 chain below.
+                                  Cholesky factor and the updates inside a block keep FP64 chains, with each
+                                  pivot and its column from a reciprocal square root (L_ww = a y, L_rw = t y
+                                  with y ~ 1/sqrt(a) to about an ulp) and the row divisions as products with
+                                  the pivot's reciprocal (each within ~2 ulp of the correctly rounded value).
                                   Each sum is within about (terms) 2^-53 max|a| max|b| of the exact one, the
                                   order of an FP64 dot product's own error; Zc agrees with the FP64 chain to
                                   ~1e-14 of each column's largest entry on the workloads tested. Default. */
        FRR_PREP_FP64_CHAIN = 1 }; /* every dot-product term added by one FP64 fused multiply-add, terms in
                                   ascending order: the operation sequence of the FP64 reference, so that Zc
                                   is bit-identical to it; B300's FP64 rate makes frr_init ~3.8 ms at
-                                  n = d = 1000 (~2.7 ms in FRR_PREP_TENSOR) */
+                                  n = d = 1000 (~2.5 ms in FRR_PREP_TENSOR) */
 
 #define FRR_EXACT_SEED UINT64_MAX
 

@@ -262,6 +262,34 @@ __device__ __forceinline__ void publish(PanelSync& ps, int w, int lane, double v
     tc::mbar_arrive(&ps.bar[w]);
 }
 
+// 1/sqrt(a) for a > 0 (normal or subnormal) to about an ulp: a is scaled by an even power of
+// two into [1, 4), an FP32 reciprocal square root gives ~23 bits, and two Newton steps for
+// 1/sqrt (y <- y + y (1/2 - (a/2) y y), each doubling the correct bits) carry it to FP64
+// precision; the result is scaled back by the matching power of two.
+__device__ __forceinline__ double rsqrt_near(double a)
+{
+    long long bits = __double_as_longlong(a);
+    int shift = 0;                      // a = m 2^(2 shift) with m in [1, 4)
+    if ((bits >> 52) == 0) {            // subnormal: make it normal first (exact)
+        a = __dmul_rn(a, 0x1p+64);
+        bits = __double_as_longlong(a);
+        shift -= 32;
+    }
+    const int e = (int)(bits >> 52) - 1023;      // a in [2^e, 2^(e+1))
+    const int h = e >= 0 ? e / 2 : -((1 - e) / 2);  // floor(e / 2)
+    const double m = __longlong_as_double(bits - ((long long)(2 * h) << 52));  // a 2^-2h in [1, 4)
+    shift += h;
+    double y = (double)rsqrtf((float)m);
+    const double hm = __dmul_rn(0.5, m);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const double r = __fma_rn(-__dmul_rn(hm, y), y, 0.5);
+        y = __fma_rn(y, r, y);
+    }
+    // 1/sqrt(a) = y 2^-shift (exact scaling: the exponent of y stays in range)
+    return __longlong_as_double(__double_as_longlong(y) - ((long long)shift << 52));
+}
+
 // RN(a / b) from y = RN(1 / b) by Markstein's method (P. Markstein, IBM J. Res. Dev. 34(1),
 // 1990): from a quotient within one ulp of a / b, q + (a - b q) y rounded once (FMA, with the
 // residual a - b q exact) is the correctly rounded quotient; one correction step from RN(a y)
@@ -295,7 +323,7 @@ __device__ __forceinline__ bool markstein_unsafe(double a, double b)
 template <bool kExact>
 __device__ __forceinline__ double eliminate_col(double t, int w, int lane, const double (*Lc)[kP + 1],
                                                 const double* Ld, const double* Yd, PanelSync& ps, uint32_t parity,
-                                                bool row_ok, bool& unsafe, int* status)
+                                                bool row_ok, bool& unsafe, int* status, bool fast)
 {
     for (int jj = 0; jj < w; ++jj) {
         if (!wait_col(&ps.bar[jj], parity, &ps.abort_flag, status)) break;
@@ -303,6 +331,8 @@ __device__ __forceinline__ double eliminate_col(double t, int w, int lane, const
     }
     if (kExact) {
         t = __ddiv_rn(t, Ld[w]);
+    } else if (fast) {
+        t = __dmul_rn(t, Yd[w]);  // tensor-core mode: times the reciprocal, within 1.5 ulp of the quotient
     } else {
         unsafe |= row_ok && markstein_unsafe(t, Ld[w]);
         t = div_markstein(t, Ld[w], Yd[w]);
@@ -318,13 +348,13 @@ __device__ __forceinline__ double eliminate_col(double t, int w, int lane, const
 // take part in the block-wide vote).
 __device__ __forceinline__ double eliminate_panel_rows(double t0, int pw, int w, int lane, const double (*Lc)[kP + 1],
                                                        const double* Ld, const double* Yd, PanelSync& ps, bool row_ok,
-                                                       int* status)
+                                                       int* status, bool fast)
 {
     bool unsafe = false;
     double t = t0;
-    if (w < pw) t = eliminate_col<false>(t0, w, lane, Lc, Ld, Yd, ps, 0u, row_ok, unsafe, status);
+    if (w < pw) t = eliminate_col<false>(t0, w, lane, Lc, Ld, Yd, ps, 0u, row_ok, unsafe, status, fast);
     if (__syncthreads_or(unsafe) && w < pw)
-        t = eliminate_col<true>(t0, w, lane, Lc, Ld, Yd, ps, 1u, row_ok, unsafe, status);
+        t = eliminate_col<true>(t0, w, lane, Lc, Ld, Yd, ps, 1u, row_ok, unsafe, status, fast);
     return t;
 }
 
@@ -356,14 +386,24 @@ __global__ void __launch_bounds__(kP * kPW) k_chol_diag(PJ_ARGS, int p)
         t = __fma_rn(-ps.Zs[jj][lane], ps.Zs[jj][w], t);
     }
     // pivot on lane w, division below it
-    double piv = 0.0;
+    double piv = 0.0, rpiv = 0.0;
     if (lane == w) {
         if (!(t > tol_abs)) atomicOr(J.status, kStatusPivot);
-        piv = __dsqrt_rn(t > 0.0 ? t : 1.0);
+        const double a = t > 0.0 ? t : 1.0;
+        if (J.tc) {
+            // tensor-core mode: y ~ 1/sqrt(a) to about an ulp, L_ww = a y and L_rw = t_rw y (each
+            // within ~2 ulp of the correctly rounded square root and quotient), a shorter chain
+            // than a square root followed by a division
+            rpiv = rsqrt_near(a);
+            piv = __dmul_rn(a, rpiv);
+        } else {
+            piv = __dsqrt_rn(a);
+        }
     }
     piv = __shfl_sync(0xffffffffu, piv, w);
+    rpiv = __shfl_sync(0xffffffffu, rpiv, w);
     if (lane == w) t = piv;
-    else if (lane > w && lane < pw) t = __ddiv_rn(t, piv);
+    else if (lane > w && lane < pw) t = J.tc ? __dmul_rn(t, rpiv) : __ddiv_rn(t, piv);
     publish(ps, w, lane, (lane >= w && lane < pw) ? t : 0.0);
     if (r < pw && w <= r) A[(size_t)(k0 + r) * d + k0 + w] = t;
 }
@@ -394,7 +434,7 @@ __global__ void __launch_bounds__(kP * kPW) k_chol_below(PJ_ARGS, int p)
     const double t0 = (r < d && w < pw) ? A[(size_t)r * d + k0 + w] : 0.0;
     panel_sync_init(ps);
     __syncthreads();
-    const double t = eliminate_panel_rows(t0, pw, w, lane, Lc, Ld, Yd, ps, r < d, J.status);
+    const double t = eliminate_panel_rows(t0, pw, w, lane, Lc, Ld, Yd, ps, r < d, J.status, J.tc != 0);
     if (r < d && w < pw) A[(size_t)r * d + k0 + w] = t;
 }
 
@@ -492,7 +532,7 @@ __global__ void __launch_bounds__(kP * kPW) k_fwd_panel(PJ_ARGS, int p)
     const double t0 = (i < n && w < pw) ? T[(size_t)i * d + k0 + w] : 0.0;
     panel_sync_init(ps);
     __syncthreads();
-    const double t = eliminate_panel_rows(t0, pw, w, lane, Lc, Ld, Yd, ps, i < n, J.status);
+    const double t = eliminate_panel_rows(t0, pw, w, lane, Lc, Ld, Yd, ps, i < n, J.status, J.tc != 0);
     if (i < n && w < pw) T[(size_t)i * d + k0 + w] = t;
 }
 
