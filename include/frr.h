@@ -90,7 +90,8 @@ enum { FRR_PREP_TENSOR = 0,    /* the covariance, and the forward substitution's
                                   Cholesky factor and the updates inside a block keep FP64 chains, with each
                                   pivot and its column from a reciprocal square root (L_ww = a y, L_rw = t y
                                   with y ~ 1/sqrt(a) to about an ulp) and the row divisions as products with
-                                  the pivot's reciprocal (each within ~2 ulp of the correctly rounded value).
+                                  the pivot's reciprocal (each within ~2 ulp of the correctly rounded value),
+                                  and the column means and the trace as blocked sums.
                                   Each sum is within about (terms) 2^-53 max|a| max|b| of the exact one, the
                                   order of an FP64 dot product's own error; Zc agrees with the FP64 chain to
                                   ~1e-14 of each column's largest entry on the workloads tested. Default. */

@@ -83,6 +83,22 @@ __global__ void __launch_bounds__(256) k_colmean(PJ_ARGS)
     const int j0 = (int)lb * 32;
     __shared__ double tile[2][kCmRows][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (J.tc) {
+        // tensor-core mode (the oracle's chain is not kept): eight row groups sum their rows
+        // (lane = column) and the eight partial sums are added in order, a blocked sum with a
+        // chain of n / 8 additions instead of n
+        double sg = 0.0;
+        if (j0 + lane < d)
+            for (int i = w; i < n; i += 8) sg = __dadd_rn(sg, J.X[(size_t)i * d + j0 + lane]);
+        tile[0][w][lane] = sg;
+        __syncthreads();
+        if (w == 0 && j0 + lane < d) {
+            double t = tile[0][0][lane];
+            for (int g = 1; g < 8; ++g) t = __dadd_rn(t, tile[0][g][lane]);
+            J.xbar[j0 + lane] = __ddiv_rn(t, (double)n);
+        }
+        return;
+    }
     const int ntiles = (n + kCmRows - 1) / kCmRows;
     auto load = [&](int t, int buf) {
         for (int r = w - 1; r < kCmRows; r += 7) {
@@ -160,7 +176,22 @@ __global__ void __launch_bounds__(256) k_diag(PJ_ARGS)
         mx = o > mx ? o : mx;
     }
     if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
-    if (threadIdx.x == 0) {
+    if (J.tc) {
+        // tensor-core mode (the oracle's chain is not kept): the trace as a blocked sum, each
+        // thread's strided terms, then a tree in the warp, then the warps' sums in order
+        __shared__ double s_part[8];
+        double pt = 0.0;
+        for (int j = threadIdx.x; j < d; j += blockDim.x) pt = __dadd_rn(pt, S[(size_t)j * d + j]);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) pt = __dadd_rn(pt, __shfl_xor_sync(kFull, pt, off));
+        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = pt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tr = s_part[0];
+            for (int g = 1; g < (int)(blockDim.x >> 5); ++g) tr = __dadd_rn(tr, s_part[g]);
+            s_tr = tr;
+        }
+    } else if (threadIdx.x == 0) {
         double tr = 0.0;
         int j = 0;
         for (; j + 8 <= d; j += 8) {
