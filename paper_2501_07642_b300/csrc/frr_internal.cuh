@@ -222,6 +222,7 @@ struct CovJob {
     long long* acc;             // d x d int64 sums (elements on or above the diagonal)
     double* S;                  // d x d covariance (output)
     int* status;                // the preparation's status word (bit 2: a bounded wait expired)
+    double rinv;                // RN(1 / (n - 1))
 };
 // Columns per block of the forward substitution's tensor-core updates (a multiple of the
 // panel width, 32, and of the digit kernel's K block, 64).

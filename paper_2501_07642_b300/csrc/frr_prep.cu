@@ -995,7 +995,7 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         C = CovJob{};
         if (J.tc) {
             C.n = J.n; C.d = J.d; C.npad = cov_tc_npad(J.n); C.dpad = cov_tc_dpad(J.d);
-            C.Xc = J.Xc; C.S = J.S; C.status = J.status;
+            C.Xc = J.Xc; C.S = J.S; C.status = J.status; C.rinv = 1.0 / (double)(J.n - 1);
             C.G = reinterpret_cast<__nv_bfloat16*>(take(cov_tc_plane_bytes(J.n, J.d)));
             C.cexp = reinterpret_cast<int*>(take(d * 4));
             C.acc = reinterpret_cast<long long*>(take(d * d * 8));

@@ -388,8 +388,14 @@ __global__ void __launch_bounds__(256) k_cov_finish(const CovJob* __restrict__ j
     if (idx >= (size_t)d * d) return;
     const int j = (int)(idx / d), k = (int)(idx % d);
     if (k < j) return;
+    // the sum's scale 2^(59 + e_j + e_k - 110) in three exact power-of-two steps (each factor
+    // normal and of sc's sign, so no partial product over- or underflows unless the result
+    // does), then the denominator as a product with RN(1/(n - 1)): one rounding more than a
+    // division
     const double x = __ll2double_rn(J.acc[idx]);
-    const double v = __ddiv_rn(scalbn(x, kShift - 110 + J.cexp[j] + J.cexp[k]), (double)(J.n - 1));
+    const int sc = kShift - 110 + J.cexp[j] + J.cexp[k];
+    const int a = sc / 3, b = (sc - a) / 2;
+    const double v = __dmul_rn(__dmul_rn(__dmul_rn(x, pow2(a)), pow2(b)), pow2(sc - a - b)) * J.rinv;
     J.S[idx] = v;
     J.S[(size_t)k * d + j] = v;
 }
@@ -461,7 +467,11 @@ __global__ void __launch_bounds__(256) k_fwd_apply(const FwdJob* __restrict__ jo
     const size_t at = (size_t)i * J.d + c_first + j;
     const double x = __ll2double_rn(J.acc[at]);
     J.acc[at] = 0ll;
-    J.ZT[at] = __dsub_rn(J.ZT[at], scalbn(x, kShift - 110 + J.expA[i] + J.expB[j]));
+    // the scale in three exact power-of-two steps (all of sc's sign, so no partial product over-
+    // or underflows unless the result does)
+    const int sc = kShift - 110 + J.expA[i] + J.expB[j];
+    const int s1 = sc / 3, s2 = (sc - s1) / 2;
+    J.ZT[at] = __dsub_rn(J.ZT[at], __dmul_rn(__dmul_rn(__dmul_rn(x, pow2(s1)), pow2(s2)), pow2(sc - s1 - s2)));
 }
 
 size_t cov_smem_bytes() { return 1024 + (size_t)kStages * kStageBytes + (2 * kStages + 2 * kAccBufs + 1) * 8 + 16; }
