@@ -88,7 +88,7 @@ def test_whitened_covariates_bit_exact(n, d, whiten):
     assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
 
 
-@pytest.mark.parametrize("case", ["wide_scales", "zero_column", "tiny_and_huge", "all_tiny"])
+@pytest.mark.parametrize("case", ["wide_scales", "zero_column", "tiny_and_huge", "all_tiny", "subnormal_cov"])
 def test_whitened_covariates_bit_exact_extreme_magnitudes(case):
     """Bit patterns (signed zeros included) at magnitudes that reach the divisions' safe-range
     edges: columns scaled by powers of two far from 1, an exactly constant column whose
@@ -104,6 +104,8 @@ def test_whitened_covariates_bit_exact_extreme_magnitudes(case):
     elif case == "tiny_and_huge":
         X[:, : d // 2] *= 2.0 ** -300
         X[:, d // 2:] *= 2.0 ** 300
+    elif case == "subnormal_cov":
+        X = X * 2.0 ** -515  # covariances and pivots near 2^-1030: subnormal
     else:
         X = X * 2.0 ** -500
     with _ctx(X, n // 2, whiten="ridge", prep="fp64_chain") as ctx:
@@ -143,11 +145,12 @@ def test_whitened_covariates_tensor_covariance(n, d, whiten, kind):
     assert _zc_err(got, want) < REL_ZC_TC
 
 
-@pytest.mark.parametrize("case", ["wide_scales", "zero_column", "tiny_and_huge", "all_tiny"])
+@pytest.mark.parametrize("case", ["wide_scales", "zero_column", "tiny_and_huge", "all_tiny", "subnormal_cov"])
 def test_whitened_tensor_covariance_extreme_magnitudes(case):
     """Per-column power-of-two scales far from 1 (each column's digits are relative to its own
     largest entry), constant columns (centred to exact zeros: their whitened entries stay exact
-    zeros), and covariates at 2^-500 (products near 2^-1000, still normal)."""
+    zeros), covariates at 2^-500 (products near 2^-1000, still normal) and at 2^-515 (subnormal
+    covariances and pivots)."""
     n, d = 90, 40
     X = ar1_covariates(n, d, 77, 0.4)
     if case == "wide_scales":
@@ -158,6 +161,8 @@ def test_whitened_tensor_covariance_extreme_magnitudes(case):
     elif case == "tiny_and_huge":
         X[:, : d // 2] *= 2.0 ** -300
         X[:, d // 2:] *= 2.0 ** 300
+    elif case == "subnormal_cov":
+        X = X * 2.0 ** -515  # covariances and pivots near 2^-1030: subnormal
     else:
         X = X * 2.0 ** -500
     with _ctx(X, n // 2, whiten="ridge") as ctx:
