@@ -212,7 +212,7 @@ frr_status prep_run(frr_ctx* ctx, const double* X_host);
 // expired bounded wait); the return value is a CUDA failure common to all, else FRR_OK
 frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int E, cudaStream_t s, cudaStream_t aux,
                           frr_status* st_out);
-// One experiment's covariance from digit products on the tensor cores (frr_cov_tc.cu).
+// One experiment's covariance from digit products on the tensor cores (frr_prep_tc.cu).
 struct CovJob {
     int n, d, npad, dpad;       // npad = 64 ceil(n / 64), dpad = 128 ceil(d / 128)
     const double* Xc;           // centred covariates, n x d row-major
