@@ -469,6 +469,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_init(SelState* __restrict__
 constexpr int kFinMax = 4096;
 constexpr int kFinThreads = SNT;
 constexpr int kFinPer = kFinMax / kFinThreads;   // entries per thread
+constexpr int kFinCountMax = 512;  // above this many accepted entries the placement sorts instead of counting
 
 __global__ void __launch_bounds__(kFinThreads, 1)
 k_finish(const double* __restrict__ m64, const uint64_t* __restrict__ idx, const float* __restrict__ mhat, int64_t r_host,
@@ -755,17 +756,52 @@ k_finish(const double* __restrict__ m64, const uint64_t* __restrict__ idx, const
     }
     __syncthreads();
     const int na = s_na;
-    // position = accepted entries with a smaller draw index (one warp per accepted entry)
+    // Ascending draw order. Few accepted entries: each is placed at the number of accepted
+    // entries with a smaller draw index (one warp per entry). Many (the cost of that grows as
+    // na^2): a bitonic sort of the distinct accepted indices, their M64 alongside, over the next
+    // power of two (padding sorts last), O(na log^2 na) with one block barrier per stage.
     unsigned long long best = 0ull;
     bool any = false;
-    for (int a = warp; a < na; a += kFinThreads / 32) {
-        const unsigned long long ic = ai[a];
-        int pos = 0;
-        for (int b = lane; b < na; b += 32) pos += ai[b] < ic ? 1 : 0;
-        pos = (int)__reduce_add_sync(kFull, (unsigned)pos);
-        if (lane == 0) {
-            keys_out[pos] = ic;
-            m_out[pos] = __longlong_as_double((long long)ak[a]);
+    if (na <= kFinCountMax) {
+        for (int a = warp; a < na; a += kFinThreads / 32) {
+            const unsigned long long ic = ai[a];
+            int pos = 0;
+            for (int b = lane; b < na; b += 32) pos += ai[b] < ic ? 1 : 0;
+            pos = (int)__reduce_add_sync(kFull, (unsigned)pos);
+            if (lane == 0) {
+                keys_out[pos] = ic;
+                m_out[pos] = __longlong_as_double((long long)ak[a]);
+                if (!q_mode && (!any || ak[a] > best)) { best = ak[a]; any = true; }
+            }
+        }
+    } else {
+        int np = 1;
+        while (np < na) np <<= 1;
+        for (int i = na + tid; i < np; i += kFinThreads) {
+            ai[i] = ~0ull;
+            ak[i] = 0ull;
+        }
+        __syncthreads();
+        for (int kk = 2; kk <= np; kk <<= 1)
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                for (int i = tid; i < np; i += kFinThreads) {
+                    const int ixj = i ^ jj;
+                    if (ixj > i) {
+                        const unsigned long long x = ai[i], y = ai[ixj];
+                        if ((x > y) == ((i & kk) == 0)) {
+                            ai[i] = y;
+                            ai[ixj] = x;
+                            const unsigned long long t = ak[i];
+                            ak[i] = ak[ixj];
+                            ak[ixj] = t;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int a = tid; a < na; a += kFinThreads) {
+            keys_out[a] = ai[a];
+            m_out[a] = __longlong_as_double((long long)ak[a]);
             if (!q_mode && (!any || ak[a] > best)) { best = ak[a]; any = true; }
         }
     }
@@ -773,7 +809,14 @@ k_finish(const double* __restrict__ m64, const uint64_t* __restrict__ idx, const
         // threshold mode: the largest accepted M64
         __shared__ unsigned long long s_best[32];
         __shared__ int s_any[32];
-        if (lane == 0) { s_best[warp] = best; s_any[warp] = any ? 1 : 0; }
+        // every thread placed entries: the warp's largest first
+        const unsigned am = __ballot_sync(kFull, any);
+        unsigned long long wb = any ? best : 0ull;
+        for (int off = 16; off >= 1; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(kFull, wb, off);
+            wb = o > wb ? o : wb;
+        }
+        if (lane == 0) { s_best[warp] = wb; s_any[warp] = am != 0u ? 1 : 0; }
         __syncthreads();
         if (tid == 0) {
             bool a = false;
