@@ -129,6 +129,19 @@ def _zc_err(got, want):
     return (np.abs(got - want) / scale).max()
 
 
+def _zc_tol(X, whiten, ridge=0.1):
+    """REL_ZC_TC, or for an ill-conditioned covariance (d close to n - 1 under Cholesky
+    whitening) 1e-14 cond(S_lambda): two FP64-accurate whitenings differ by up to about
+    cond(S) u in each column's scale (1e-14 = 45 u). S_lambda from numpy, not the oracle."""
+    if whiten == "diag":
+        return REL_ZC_TC
+    Xc = X - X.mean(axis=0)
+    S = Xc.T @ Xc / (X.shape[0] - 1)
+    if whiten == "ridge":
+        S = S + ridge * np.trace(S) / S.shape[0] * np.eye(S.shape[0])
+    return max(REL_ZC_TC, 1e-14 * np.linalg.cond(S))
+
+
 @pytest.mark.parametrize("n,d,whiten,kind", [(60, 10, "chol", "ar1"), (100, 100, "ridge", "ar1"),
                                              (40, 7, "diag", "ar1"), (333, 129, "chol", "ar1"),
                                              (65, 257, "ridge", "ar1"), (2048, 300, "chol", "mixed"),
@@ -143,6 +156,19 @@ def test_whitened_covariates_tensor_covariance(n, d, whiten, kind):
         got = frr.frr_whitened(ctx)
     want, *_ = O.prep(X, whiten, 0.1)
     assert _zc_err(got, want) < REL_ZC_TC
+
+
+@pytest.mark.parametrize("n,d,whiten", [(3, 1, "chol"), (10, 1, "ridge"), (130, 128, "chol"), (300, 256, "chol"),
+                                         (600, 512, "ridge"), (257, 255, "chol"), (64, 300, "diag")])
+def test_whitened_tensor_mode_edge_shapes(n, d, whiten):
+    """Tensor-core preparation at tile and block edges: one column, one or two exact 128-wide
+    tiles, d = 256 (no forward-substitution block boundary), d = 512 (one boundary whose rest is
+    a whole block), d = n - 2, and diagonal whitening with d > n."""
+    X = ar1_covariates(n, d, 900 + d, 0.3) + 0.25
+    with _ctx(X, n // 2, whiten=whiten) as ctx:
+        got = frr.frr_whitened(ctx)
+    want, *_ = O.prep(X, whiten, 0.1)
+    assert _zc_err(got, want) < _zc_tol(X, whiten)  # d = n - 2: cond(S) ~ 1e5-1e6
 
 
 @pytest.mark.parametrize("case", ["wide_scales", "zero_column", "tiny_and_huge", "all_tiny", "subnormal_cov"])
