@@ -346,7 +346,7 @@ def run_frr(args):
             achieved = flops * B / (res["ms_balance"] / 1e3) / 1e12
             peak = peaks["bf16_tflops"]
             return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": tc_traffic(B), "kernel": "k_balance_tc",
+                    "traffic": tc_traffic(B, WORKLOAD), "kernel": "k_balance_tc",
                     "peak_source": f"bf16_tflops (burst, {peak_kind})", "flop_per_draw": flops}
         # FP32 CUDA-core path: the algorithmic work is n1 * d additions per draw (the treated rows;
         # the kernel executes n * d predicated ones), against the FP32 lane rate measured with a
@@ -522,9 +522,9 @@ def stream_bench() -> dict:
             "note": "wall time of the stream (one read-back per chunk bounds the retained set)"}
 
 
-def tc_traffic(B):
+def tc_traffic(B, workload_name):
     """DRAM bytes per k_balance_tc launch from the committed ncu summary, or None when the
-    kernel's sources changed since the capture or the launch size differs."""
+    kernel's sources changed since the capture, or the workload or launch size differs."""
     md = ROOT / "profiles" / "k_balance_tc_precision_n1000_d1000.md"
     try:
         text = md.read_text()
@@ -532,7 +532,8 @@ def tc_traffic(B):
         h = hashlib.sha256()
         for f in rec["sources"]:
             h.update((ROOT / f).read_bytes())
-        if h.hexdigest() != rec["source_sha256"] or int(rec["draws_per_launch"]) != int(B):
+        if (h.hexdigest() != rec["source_sha256"] or int(rec["draws_per_launch"]) != int(B)
+                or rec.get("workload") != workload_name):
             return None
         return int(rec["dram_bytes_per_launch"])
     except (OSError, ValueError, KeyError):
