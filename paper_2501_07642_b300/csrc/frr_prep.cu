@@ -1100,6 +1100,12 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         PREP_CHECK(cudaStreamWaitEvent(s, evs[2], 0));
         if (unsigned g = total(li)) k_copy_zc<<<g, 256, 0, s>>>(dj, P(li), E);
         ++li;
+        // The band terms read only Zc: they run on the second stream beside the chain that
+        // derives the balance and recheck copies (exponents, copies, sums, digit planes).
+        PREP_CHECK(cudaEventRecord(evs[0], s));
+        PREP_CHECK(cudaStreamWaitEvent(aux, evs[0], 0));
+        if (unsigned g = total(li + 4)) k_band_cols<<<g, 256, 0, aux>>>(dj, P(li + 4), E);
+        PREP_CHECK(cudaEventRecord(evs[1], aux));
         if (unsigned g = total(li)) k_qexp<<<g, dim3(32, kRG), 0, s>>>(dj, P(li), E);
         ++li;
         if (unsigned g = total(li)) k_derive<<<g, 256, 0, s>>>(dj, P(li), E);
@@ -1108,8 +1114,8 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         ++li;
         if (unsigned g = total(li)) k_digits<<<g, 256, 0, s>>>(dj, P(li), E);
         ++li;
-        if (unsigned g = total(li)) k_band_cols<<<g, 256, 0, s>>>(dj, P(li), E);
-        ++li;
+        ++li;  // (k_band_cols, above)
+        PREP_CHECK(cudaStreamWaitEvent(s, evs[1], 0));
         PREP_CHECK(cudaGetLastError());
     }
     // binomial tables for exact enumeration (only shapes that allow it read them); the host
