@@ -553,7 +553,7 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--ref-total-s", type=float, default=120.0)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
-    ap.add_argument("--e2e-steps", type=int, default=7)
+    ap.add_argument("--e2e-steps", type=int, default=15)
     ap.add_argument("--no-distance", dest="distance", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-stream", dest="stream", action="store_false")

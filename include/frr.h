@@ -89,8 +89,9 @@ enum { FRR_PREP_TENSOR = 0,    /* the covariance, and the forward substitution's
                                   pairs whose weight lies below 2^-56 of the leading one are left out); the
                                   Cholesky factor and the updates inside a block keep FP64 chains, with each
                                   pivot and its column from a reciprocal square root (L_ww = a y, L_rw = t y
-                                  with y ~ 1/sqrt(a) to about an ulp) and the row divisions as products with
-                                  the pivot's reciprocal (each within ~2 ulp of the correctly rounded value),
+                                  with y ~ 1/sqrt(a) within about half an ulp) and the row divisions as
+                                  products with the pivot's reciprocal (each within ~1.5 ulp of the
+                                  correctly rounded value),
                                   and the column means and the trace as blocked sums.
                                   Each sum is within about (terms) 2^-53 max|a| max|b| of the exact one, the
                                   order of an FP64 dot product's own error; Zc agrees with the FP64 chain to
@@ -98,7 +99,7 @@ enum { FRR_PREP_TENSOR = 0,    /* the covariance, and the forward substitution's
        FRR_PREP_FP64_CHAIN = 1 }; /* every dot-product term added by one FP64 fused multiply-add, terms in
                                   ascending order: the operation sequence of the FP64 reference, so that Zc
                                   is bit-identical to it; B300's FP64 rate makes frr_init ~3.8 ms at
-                                  n = d = 1000 (~2.5 ms in FRR_PREP_TENSOR) */
+                                  n = d = 1000 (~2.0 ms in FRR_PREP_TENSOR) */
 
 #define FRR_EXACT_SEED UINT64_MAX
 
@@ -138,7 +139,13 @@ void frr_default_opts(frr_opts* o);
  * rounded as opts.prep says).
  * X: host, n x d row-major FP64 (rows are units). n1: number of treated units.
  * opts: NULL for defaults. On success *out owns device memory; release it with
- * frr_destroy. Supports n <= 2048. */
+ * frr_destroy. Supports n <= 2048.
+ * The first call of a shape (n, d, n1, whitening, opts.prep) on a device records the
+ * preparation's launches as a CUDA graph that keeps its own temporary device block (at most
+ * 512 MiB, four shapes per device, least recently used dropped first); later calls of that
+ * shape replay it (~200 dependent launches then follow each other sooner on the device, and
+ * the host enqueues one graph instead of each launch). A call that finds its shape's graph in
+ * use by another thread enqueues the launches itself. */
 frr_status frr_init(frr_ctx** out, const double* X, int64_t n, int64_t d, int64_t n1, const frr_opts* opts);
 
 /* Balance of draws [first_draw, first_draw + B) (Sec. 2.1 batched processing,

@@ -174,6 +174,11 @@ inline cudaError_t set_smem_limit(void (*kernel)(P...), int bytes, int device)
     return set_smem_limit(reinterpret_cast<const void*>(kernel), bytes, device);
 }
 
+// handle of the CUDA context current on the calling thread (null if there is none): it
+// changes when a device's primary context is destroyed (cudaDeviceReset) and created again,
+// which invalidates every device address and graph made in the old one
+void* current_cuda_context();
+
 // stream-ordered memory pool of the library for short-lived temporaries on `device`; it keeps
 // up to 8 GiB reserved between calls instead of returning it at every synchronisation (a
 // 256-experiment batch peaks near 2 GiB)
@@ -269,6 +274,9 @@ bool cov_tc_map(CUtensorMap* m, const __nv_bfloat16* G, int n, int d);
 // table `jobs`; prefix[l] / total[l]: the prefix sums of launch l's blocks over the jobs
 cudaError_t cov_tc_launch(const CovJob* jobs, const unsigned* const prefix[4], const unsigned total[4], int E,
                           int device, int num_sms, cudaStream_t s);
+// the tensor-core sums' shared-memory limits on `device`, set before a launch sequence is
+// captured into a graph (cov_tc_launch and fwd_tc_launch then make no attribute call)
+cudaError_t prep_tc_setup(int device);
 frr_status balance_f32_launch(frr_ctx* ctx, uint64_t seed, bool exact, uint64_t first, uint64_t B, float* Mout_dev);
 // hist0 (split BF16 only, may be NULL): 4096 counters that also receive the level-0 histogram
 // of the scored M_hat (bits [31:20] of each value) for the streaming selection

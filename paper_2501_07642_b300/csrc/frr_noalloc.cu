@@ -100,6 +100,15 @@ bool on_device(const void* p, int device)
 }
 
 }  // namespace
+
+void* current_cuda_context()
+{
+    const CtxGetCurrentFn get_ctx = ctx_get_current();
+    CUcontext c = nullptr;
+    if (!get_ctx || get_ctx(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
+
 }  // namespace frr
 
 extern "C" frr_status frr_recheck_static(frr_ctx* ctx, uint64_t seed, const uint64_t* draws, int64_t count,

@@ -25,6 +25,7 @@
 #include "frr_tc_ptx.cuh"
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 namespace frr {
@@ -293,10 +294,14 @@ __device__ __forceinline__ void publish(PanelSync& ps, int w, int lane, double v
     tc::mbar_arrive(&ps.bar[w]);
 }
 
-// 1/sqrt(a) for a > 0 (normal or subnormal) to about an ulp: a is scaled by an even power of
-// two into [1, 4), an FP32 reciprocal square root gives ~23 bits, and two Newton steps for
-// 1/sqrt (y <- y + y (1/2 - (a/2) y y), each doubling the correct bits) carry it to FP64
-// precision; the result is scaled back by the matching power of two.
+// 1/sqrt(a) for a > 0 (normal or subnormal), within about half an ulp: a = m 4^h with m in
+// [1, 4) (an even power of two split off in the exponent field); an FP32 seed y0 ~ 1/sqrt(m)
+// to ~21 bits (the PTX reciprocal-square-root approximation of m's top 20 fraction bits), then
+// one third-order step from the series (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + ... with
+// e = 1 - m y0^2 (y0^2 is exact: y0 has 24 significant bits), y = y0 + y0 e (1/2 + 3e/8);
+// the truncated terms are below 2^-59 relative. The seed moves between FP64 and FP32 by
+// integer bit operations, not conversion instructions, so the dependent chain holds four
+// FP64 operations (a column of the diagonal panel waits for it).
 __device__ __forceinline__ double rsqrt_near(double a)
 {
     long long bits = __double_as_longlong(a);
@@ -306,17 +311,19 @@ __device__ __forceinline__ double rsqrt_near(double a)
         bits = __double_as_longlong(a);
         shift -= 32;
     }
-    const int e = (int)(bits >> 52) - 1023;      // a in [2^e, 2^(e+1))
-    const int h = e >= 0 ? e / 2 : -((1 - e) / 2);  // floor(e / 2)
-    const double m = __longlong_as_double(bits - ((long long)(2 * h) << 52));  // a 2^-2h in [1, 4)
+    const int h = ((int)(bits >> 52) - 1023) >> 1;  // floor of half the exponent
+    const double m = __longlong_as_double(bits - ((long long)(2 * h) << 52));
     shift += h;
-    double y = (double)rsqrtf((float)m);
-    const double hm = __dmul_rn(0.5, m);
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const double r = __fma_rn(-__dmul_rn(hm, y), y, 0.5);
-        y = __fma_rn(y, r, y);
-    }
+    // exponent field of m: 1023 or 1024 -> FP32 exponent field 127 or 128 (1023 - 127 = 896);
+    // the top 20 fraction bits move along (the 32-bit arithmetic wraps harmlessly)
+    const uint32_t hi = (uint32_t)__double2hiint(m);
+    const float mf = __uint_as_float((hi << 3) - (896u << 23));
+    float y32;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y32) : "f"(mf));
+    const uint32_t fb = __float_as_uint(y32);  // y32 in (1/2, 1]: exact as a double
+    const double y0 = __hiloint2double((int)((fb >> 3) + (896u << 20)), (int)(fb << 29));
+    const double e = __fma_rn(-m, __dmul_rn(y0, y0), 1.0);
+    const double y = __fma_rn(__dmul_rn(y0, e), __fma_rn(e, 0.375, 0.5), y0);
     // 1/sqrt(a) = y 2^-shift (exact scaling: the exponent of y stays in range)
     return __longlong_as_double(__double_as_longlong(y) - ((long long)shift << 52));
 }
@@ -422,19 +429,24 @@ __global__ void __launch_bounds__(kP * kPW) k_chol_diag(PJ_ARGS, int p)
         if (!(t > tol_abs)) atomicOr(J.status, kStatusPivot);
         const double a = t > 0.0 ? t : 1.0;
         if (J.tc) {
-            // tensor-core mode: y ~ 1/sqrt(a) to about an ulp, L_ww = a y and L_rw = t_rw y (each
-            // within ~2 ulp of the correctly rounded square root and quotient), a shorter chain
-            // than a square root followed by a division
+            // tensor-core mode: y ~ 1/sqrt(a) within about half an ulp; L_ww = a y and L_rw = t_rw y
+            // (each within about an ulp of the correctly rounded square root and quotient) come
+            // from one multiplication on every lane, a shorter chain than a square root
+            // followed by a division
             rpiv = rsqrt_near(a);
-            piv = __dmul_rn(a, rpiv);
+            t = a;
         } else {
             piv = __dsqrt_rn(a);
         }
     }
-    piv = __shfl_sync(0xffffffffu, piv, w);
-    rpiv = __shfl_sync(0xffffffffu, rpiv, w);
-    if (lane == w) t = piv;
-    else if (lane > w && lane < pw) t = J.tc ? __dmul_rn(t, rpiv) : __ddiv_rn(t, piv);
+    if (J.tc) {
+        rpiv = __shfl_sync(0xffffffffu, rpiv, w);
+        if (lane >= w && lane < pw) t = __dmul_rn(t, rpiv);
+    } else {
+        piv = __shfl_sync(0xffffffffu, piv, w);
+        if (lane == w) t = piv;
+        else if (lane > w && lane < pw) t = __ddiv_rn(t, piv);
+    }
     publish(ps, w, lane, (lane >= w && lane < pw) ? t : 0.0);
     if (r < pw && w <= r) A[(size_t)(k0 + r) * d + k0 + w] = t;
 }
@@ -871,6 +883,103 @@ struct JobBlocks {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// ---- launch sequences kept as CUDA graphs ----------------------------------------------
+// One experiment's preparation is ~200 dependent launches on three streams, tied together by
+// events. Replayed from a graph they follow each other sooner on the device than when the
+// launches and event records are enqueued one by one (frr_init 2.20 -> 1.99 ms, medians, at
+// n = d = 1000), and the host enqueues one graph instead of ~200 launches (~0.8 ms). The
+// sequence depends only on the shape and the options, and every kernel finds its arrays
+// through the device job table, so the first call of a shape captures it into a graph that
+// keeps its own temporary block, and later calls of that shape replay it (the covariate
+// upload, the job tables and the read-back stay outside the graph). Single experiments
+// only: a batch's launches cover all of its experiments, and its block can be gigabytes. At
+// most kMaxPrepGraphs shapes per device are kept (least recently used first out).
+struct PrepGraph {
+    int key[8];
+    int device;
+    void* owner;           // CUDA context the block and the graph were made in
+    char* base;            // the temporary block (prep_run_batch's layout for this shape)
+    size_t bytes;
+    cudaGraphExec_t exec;  // null until the first call of the shape has been captured
+    bool busy, broken;
+    unsigned long long last_use;
+};
+constexpr int kMaxPrepGraphs = 4;
+constexpr size_t kMaxPrepGraphBytes = (size_t)512 << 20;
+std::mutex g_graph_mutex;
+std::vector<PrepGraph*> g_graphs;
+unsigned long long g_graph_tick = 0;
+
+// The entry of this shape, reserved for the caller until prep_graph_release, or null: its
+// entry is in use by another thread or failed before, the block would be too large, or it
+// cannot be allocated (the caller then takes a block from the pool and enqueues the launches
+// itself). `device` is the current device.
+PrepGraph* prep_graph_acquire(const PrepJob& J, int device, size_t bytes)
+{
+    if (bytes > kMaxPrepGraphBytes) return nullptr;
+    void* owner = current_cuda_context();
+    if (!owner) return nullptr;
+    const int key[8] = {J.n, J.d, J.n1, J.whiten, J.kpad, J.dpad32, J.kused, J.tc};
+    std::lock_guard<std::mutex> lock(g_graph_mutex);
+    // entries made in a context that no longer exists (cudaDeviceReset): their memory and graph
+    // went with it, so they are forgotten, not freed
+    for (size_t i = 0; i < g_graphs.size();) {
+        PrepGraph* g = g_graphs[i];
+        if (g->device == device && g->owner != owner && !g->busy) {
+            delete g;
+            g_graphs.erase(g_graphs.begin() + (long)i);
+        } else {
+            ++i;
+        }
+    }
+    int on_device = 0;
+    for (PrepGraph* g : g_graphs) {
+        if (g->device != device) continue;
+        ++on_device;
+        if (std::equal(key, key + 8, g->key)) {
+            if (g->busy || g->broken || g->bytes != bytes) return nullptr;
+            g->busy = true;
+            g->last_use = ++g_graph_tick;
+            return g;
+        }
+    }
+    if (on_device >= kMaxPrepGraphs) {
+        PrepGraph* lru = nullptr;
+        for (PrepGraph* g : g_graphs)
+            if (g->device == device && !g->busy && (!lru || g->last_use < lru->last_use)) lru = g;
+        if (!lru) return nullptr;
+        if (lru->exec) cudaGraphExecDestroy(lru->exec);
+        cudaFree(lru->base);  // idle: its last call synchronised before releasing it
+        cudaGetLastError();
+        g_graphs.erase(std::find(g_graphs.begin(), g_graphs.end(), lru));
+        delete lru;
+    }
+    char* base = nullptr;
+    if (cudaMalloc(reinterpret_cast<void**>(&base), bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    PrepGraph* g = new PrepGraph{};
+    std::copy(key, key + 8, g->key);
+    g->device = device;
+    g->owner = owner;
+    g->base = base;
+    g->bytes = bytes;
+    g->busy = true;
+    g->last_use = ++g_graph_tick;
+    g_graphs.push_back(g);
+    return g;
+}
+
+// Ends the caller's use of an entry (after its stream has been synchronised). An entry whose
+// call failed is not used again.
+void prep_graph_release(PrepGraph* g, bool ok)
+{
+    std::lock_guard<std::mutex> lock(g_graph_mutex);
+    if (!ok) g->broken = true;
+    g->busy = false;
+}
+
 }  // namespace
 
 frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int E, cudaStream_t s,
@@ -967,6 +1076,8 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
     const size_t pref_off = bytes;
     bytes += align256(pref.size() * sizeof(unsigned));
 
+    PrepGraph* graph = (E == 1) ? prep_graph_acquire(jobs[0], device, bytes) : nullptr;
+    bool capturing = false;  // the launches are being captured into graph
     frr_status rc = FRR_OK;
     std::vector<cudaEvent_t> evs;
     cudaEvent_t up[2] = {nullptr, nullptr};  // the covariate upload on the second stream
@@ -981,7 +1092,10 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         rc = (e == cudaErrorMemoryAllocation) ? FRR_E_NOMEM : FRR_E_CUDA;
     };
 #define PREP_CHECK(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) { fail(_e); goto cleanup; } } while (0)
-    PREP_CHECK(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&base), bytes, pool, s));
+    if (graph)
+        base = graph->base;
+    else
+        PREP_CHECK(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&base), bytes, pool, s));
     for (int e = 0; e < E; ++e) {
         PrepJob& J = jobs[(size_t)e];
         const size_t n = (size_t)J.n, d = (size_t)J.d;
@@ -1053,7 +1167,17 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
                                cudaMemcpyHostToDevice, s));
     PREP_CHECK(cudaMemcpyAsync(base + pref_off, pref.data(), pref.size() * sizeof(unsigned), cudaMemcpyHostToDevice,
                                s));
-    {
+    if (graph && graph->exec) {
+        PREP_CHECK(cudaGraphLaunch(graph->exec, s));
+    } else {
+        evs.assign(3, nullptr);  // [0]: rows below panel p final; [1]: trailing rest p done; [2]: fork / join
+        for (auto& ev : evs) PREP_CHECK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        PREP_CHECK(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
+        if (graph) {
+            PREP_CHECK(prep_tc_setup(device));
+            PREP_CHECK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            capturing = true;
+        }
         const PrepJob* dj = reinterpret_cast<const PrepJob*>(base + table_off);
         const unsigned* dp = reinterpret_cast<const unsigned*>(base + pref_off);
         size_t li = 0;
@@ -1087,9 +1211,6 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         // the rows below panel p + 1 wait for that rest.
         // Three events serve every dependency: each wait is enqueued right after its record,
         // and a wait already enqueued is not affected by a later record of the same event.
-        evs.assign(3, nullptr);  // [0]: rows below panel p final; [1]: trailing rest p done; [2]: fork / join
-        for (auto& ev : evs) PREP_CHECK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        PREP_CHECK(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
         PREP_CHECK(cudaEventRecord(evs[2], s));
         PREP_CHECK(cudaStreamWaitEvent(aux, evs[2], 0));
         PREP_CHECK(cudaStreamWaitEvent(ts, evs[2], 0));
@@ -1140,6 +1261,15 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
         ++li;  // (k_band_cols, above)
         PREP_CHECK(cudaStreamWaitEvent(s, evs[1], 0));
         PREP_CHECK(cudaGetLastError());
+        if (capturing) {
+            cudaGraph_t g = nullptr;
+            capturing = false;
+            PREP_CHECK(cudaStreamEndCapture(s, &g));
+            const cudaError_t e = cudaGraphInstantiate(&graph->exec, g, 0);
+            cudaGraphDestroy(g);
+            PREP_CHECK(e);
+            PREP_CHECK(cudaGraphLaunch(graph->exec, s));
+        }
     }
     // binomial tables for exact enumeration (only shapes that allow it read them); the host
     // table is static, so the copies need no synchronisation
@@ -1166,11 +1296,18 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
 
 cleanup:
 #undef PREP_CHECK
+    if (capturing) {  // failed while capturing: end the capture and keep nothing of it
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+    }
     // after a failure, work may still be in flight on the other streams (synchronised before
     // the trailing-update stream is destroyed and before the temporaries are released)
     if (rc != FRR_OK) {
         cudaStreamSynchronize(aux);
         if (ts) cudaStreamSynchronize(ts);
+        if (graph) cudaStreamSynchronize(s);
         cudaGetLastError();
     }
     for (cudaEvent_t ev : evs)
@@ -1179,7 +1316,8 @@ cleanup:
         if (ev) cudaEventDestroy(ev);
     if (ts) cudaStreamDestroy(ts);
     // stream-ordered release: no device-wide synchronisation
-    if (base) cudaFreeAsync(base, s);
+    if (base && !graph) cudaFreeAsync(base, s);
+    if (graph) prep_graph_release(graph, rc == FRR_OK);
     if (rc != FRR_OK)
         for (int e = 0; e < E; ++e) st_out[e] = rc;
     return rc;

@@ -507,6 +507,14 @@ cudaError_t cov_tc_launch(const CovJob* jobs, const unsigned* const prefix[4], c
     return cudaGetLastError();
 }
 
+cudaError_t prep_tc_setup(int device)
+{
+    const int smem = (int)cov_smem_bytes();
+    cudaError_t e = set_smem_limit(k_digit_gemm<CovUnits>, smem, device);
+    if (e == cudaSuccess) e = set_smem_limit(k_digit_gemm<FwdUnits>, smem, device);
+    return e;
+}
+
 int fwd_tc_npadA(int n) { return (n + kT - 1) / kT * kT; }
 int fwd_tc_dpadB(int d) { return d > kFwdBlock ? (d - kFwdBlock + kT - 1) / kT * kT : 0; }
 size_t fwd_tc_plane_bytes_a(int n) { return (size_t)kDig * fwd_tc_npadA(n) * kFwdBlock * 2; }

@@ -171,6 +171,26 @@ def test_whitened_tensor_mode_edge_shapes(n, d, whiten):
     assert _zc_err(got, want) < _zc_tol(X, whiten)  # d = n - 2: cond(S) ~ 1e5-1e6
 
 
+@pytest.mark.parametrize("prep", ["fp64_chain", "tensor"])
+def test_whitened_repeated_shapes_replay_their_preparation(prep):
+    """A single experiment's preparation is captured into a CUDA graph on the first call of its
+    shape and replayed by later calls of that shape: every call must prepare its own covariates
+    (new values, another ridge, another context's output arrays), also after its shape's
+    graph was evicted by more shapes than are kept, and back again."""
+    shapes = [(60, 20), (70, 33), (90, 40), (64, 64), (130, 100), (600, 300), (60, 20), (90, 40)]
+    for rep in range(2):
+        for i, (n, d) in enumerate(shapes):
+            X = ar1_covariates(n, d, 1000 + 17 * i + rep, 0.3) + 0.5 * rep
+            ridge = 0.1 if (i + rep) % 2 == 0 else 0.35
+            with _ctx(X, n // 2, whiten="ridge", ridge=ridge, prep=prep) as ctx:
+                got = frr.frr_whitened(ctx)
+            want, *_ = O.prep(X, "ridge", ridge)
+            if prep == "fp64_chain":
+                assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), (rep, n, d)
+            else:
+                assert _zc_err(got, want) < _zc_tol(X, "ridge", ridge), (rep, n, d)
+
+
 @pytest.mark.parametrize("case", ["wide_scales", "zero_column", "tiny_and_huge", "all_tiny", "subnormal_cov"])
 def test_whitened_tensor_covariance_extreme_magnitudes(case):
     """Per-column power-of-two scales far from 1 (each column's digits are relative to its own
