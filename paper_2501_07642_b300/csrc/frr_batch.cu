@@ -46,6 +46,7 @@ namespace {
 // enqueued from one thread: from several, the driver's calls contended (4 threads were
 // 40-60 % slower for that phase)
 constexpr int kMaxWorkers = 16;
+constexpr size_t kLendBytes = size_t(4) << 20;  // lent scratch per experiment
 int worker_count()
 {
     const unsigned hw = std::thread::hardware_concurrency();
@@ -192,6 +193,7 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
     for (int64_t e = 0; e < E; ++e)
         if (ctx[e]) live.push_back(e);
     float* mhat = nullptr;
+    char* lend_block = nullptr;  // the experiments' lent scratch (ensure_device)
     TcExp* d_table = nullptr;
     unsigned long long* d_prefix = nullptr;
     int* d_err = nullptr;
@@ -212,6 +214,28 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
         cudaEventCreate(&ea);
         cudaEventCreate(&eb);
         if (cudaMalloc(&mhat, off.back() * sizeof(float)) != cudaSuccess) { cudaGetLastError(); rc = FRR_E_NOMEM; }
+        if (rc == FRR_OK) {
+            // Each experiment's selection chain draws its scratch (retained sets, recheck rows,
+            // test buffers) from a slice of one block instead of ~6 stream-ordered allocations,
+            // which cost the issuing thread ~25 us each while the balance runs (~1500 per
+            // 256-experiment batch: longer than the balance itself on a slower host). A chain
+            // that needs more than its slice takes the rest from the pool.
+            cudaMemPool_t pool = temp_pool(owner->device);
+            if (pool != nullptr &&
+                cudaMallocFromPoolAsync(reinterpret_cast<void**>(&lend_block), live.size() * kLendBytes, pool, stream) ==
+                    cudaSuccess &&
+                cudaStreamSynchronize(stream) == cudaSuccess) {
+                for (size_t k = 0; k < live.size(); ++k) {
+                    frr_ctx* c = ctx[live[k]];
+                    c->lend = lend_block + k * kLendBytes;
+                    c->lend_off = 0;
+                    c->lend_cap = kLendBytes;
+                }
+            } else {
+                cudaGetLastError();
+                lend_block = nullptr;
+            }
+        }
         if (rc == FRR_OK && base.precision == FRR_SPLIT_BF16) {
             // Experiments are grouped by Philox blocks per lane (kb): each group runs in a
             // persistent launch of the kernel configuration compiled (and tuned) for its kb, so
@@ -501,7 +525,8 @@ extern "C" frr_status frr_batch_run(frr_experiment* ex, int64_t E, const frr_opt
     cudaFree(d_table);
     cudaFree(d_prefix);
     cudaFree(d_err);
-    for (frr_ctx* c : ctx) frr_destroy(c);
+    for (frr_ctx* c : ctx) frr_destroy(c);  // (each synchronises its stream first)
+    if (lend_block) cudaFreeAsync(lend_block, stream);
     for (cudaStream_t w : ws)
         if (w != stream) cudaStreamDestroy(w);
     if (own_stream) cudaStreamDestroy(stream);

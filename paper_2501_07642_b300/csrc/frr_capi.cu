@@ -47,13 +47,29 @@ cudaError_t set_smem_limit(const void* fn, int bytes, int device)
     return e;
 }
 
+static bool is_lent(const frr_ctx* ctx, const void* p)
+{
+    const char* c = static_cast<const char*>(p);
+    return ctx->lend != nullptr && c >= ctx->lend && c < ctx->lend + ctx->lend_cap;
+}
+
 frr_status ensure_device(frr_ctx* ctx, void** buf, size_t* cap_bytes, size_t bytes)
 {
     // stream-ordered allocations from the library pool: no device-wide synchronisation
     if (bytes == 0) bytes = 16;
     if (*buf != nullptr && *cap_bytes >= bytes) return FRR_OK;
+    const size_t carve = (bytes + 255) & ~size_t(255);
+    if (ctx->lend != nullptr && ctx->lend_cap - ctx->lend_off >= carve) {
+        // from the lent slice: no allocation call (each costs the issuing thread ~25 us while
+        // the device is busy, and a batch makes ~1500 of them)
+        if (*buf != nullptr && !is_lent(ctx, *buf)) cudaFreeAsync(*buf, ctx->stream);
+        *buf = ctx->lend + ctx->lend_off;
+        ctx->lend_off += carve;
+        *cap_bytes = carve;
+        return FRR_OK;
+    }
     if (*buf != nullptr) {
-        cudaFreeAsync(*buf, ctx->stream);
+        if (!is_lent(ctx, *buf)) cudaFreeAsync(*buf, ctx->stream);
         *buf = nullptr;
         *cap_bytes = 0;
     }
@@ -215,7 +231,7 @@ static void release(frr_ctx* ctx)
     void* bufs[] = {ctx->arena, ctx->Mhat, ctx->ret_idx[0], ctx->ret_idx[1], ctx->ret_m[0], ctx->ret_m[1], ctx->M64,
                     ctx->ukeys, ctx->misc, ctx->misc2, ctx->rt, ctx->sel};
     for (void* b : bufs)
-        if (b) cudaFreeAsync(b, ctx->stream ? ctx->stream : 0);
+        if (b && !is_lent(ctx, b)) cudaFreeAsync(b, ctx->stream ? ctx->stream : 0);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     pinned_put(ctx->host_pinned, ctx->host_pinned_bytes);
     for (cudaEvent_t e : ctx->ev)

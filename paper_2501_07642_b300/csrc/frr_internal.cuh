@@ -110,6 +110,9 @@ struct frr_ctx {
     void* misc = nullptr; size_t misc_bytes = 0;          // replay / randtest scratch
     void* misc2 = nullptr; size_t misc2_bytes = 0;
     void* rt = nullptr; size_t rt_bytes = 0;             // randomization-test scratch
+    // a slice of a block owned by frr_batch_run, lent for the batch's duration: ensure_device
+    // carves scratch from it before it asks the pool, and release() does not free what it carved
+    char* lend = nullptr; size_t lend_off = 0, lend_cap = 0;
     void* sel = nullptr; size_t sel_bytes = 0;           // device state of the running selection
     void* host_pinned = nullptr; size_t host_pinned_bytes = 0;
     cudaEvent_t ev[8] = {};
