@@ -35,6 +35,30 @@ MIX = [  # (n, d, whiten, B, q, seed)
 ]
 
 
+def test_batch_chain_scratch_beyond_its_lent_slice():
+    """Each experiment's selection chain takes its scratch from a slice of one block lent by the
+    batch; an experiment with K = 1e5 of 2e5 draws needs several MiB (retained sets, recheck
+    rows), more than its slice, and takes the rest from the pool. Beside a small experiment,
+    both must match the oracle."""
+    mix = [(100, 20, "chol", 200_000, 0.5, 21), (60, 12, "ridge", 20_000, 0.01, 22)]
+    exps, Xs = [], []
+    for k, (n, d, wh, B, q, seed) in enumerate(mix):
+        X = ar1_covariates(n, d, 700 + k, 0.3)
+        Xs.append(X)
+        exps.append(dict(X=X, n1=n // 2, whiten=wh, ridge=0.1, seed=seed, first_draw=5000 * k, B=B, q=q))
+    res, stats = frr.frr_batch_run(exps, precision="split_bf16")
+    assert stats["status"] == 0 and stats["failed"] == 0
+    for k, (x, r) in enumerate(zip(exps, res)):
+        n, d, wh, B, q, seed = mix[k]
+        assert r["status"] == 0
+        Zc, *_ = O.prep(Xs[k], wh, 0.1)
+        M = O.balance(Zc, n // 2, seed, x["first_draw"], B)
+        wk, wm = O.select_from_M(M, x["first_draw"], q=q)
+        assert len(wk) == math.ceil(q * B - 1e-9 * q * B)
+        assert np.array_equal(r["keys"], wk), f"experiment {k}"
+        assert np.allclose(r["m64"], wm, rtol=REL_M64, atol=0)
+
+
 @pytest.mark.parametrize("precision,prep", [("split_bf16", "tensor"), ("f32", "tensor"), ("split_bf16", "fp64_chain")])
 def test_batch_matches_oracle_and_single_path(precision, prep):
     """Both preparation modes: the batched preparation covers experiments with and without a

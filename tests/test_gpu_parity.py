@@ -191,6 +191,35 @@ def test_whitened_repeated_shapes_replay_their_preparation(prep):
                 assert _zc_err(got, want) < _zc_tol(X, "ridge", ridge), (rep, n, d)
 
 
+def test_whitened_concurrent_preparations_of_one_shape():
+    """Threads preparing experiments of one shape at the same time (the library call releases
+    the interpreter lock): one captures or replays the shape's launch graph, the others find
+    it in use and enqueue their launches themselves; each must get its own covariates'
+    whitening (bit for bit with the FP64 chains)."""
+    import threading
+    n, d, T = 200, 150, 6
+    Xs = [ar1_covariates(n, d, 3000 + i, 0.3) + 0.1 * i for i in range(T)]
+    out, err = [None] * T, [None] * T
+
+    def work(i):
+        try:
+            for _ in range(2):
+                with _ctx(Xs[i], n // 2, whiten="ridge", prep="fp64_chain") as ctx:
+                    out[i] = frr.frr_whitened(ctx)
+        except Exception as e:  # reported below, on the test's thread
+            err[i] = e
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(T)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for i in range(T):
+        assert err[i] is None, err[i]
+        want, *_ = O.prep(Xs[i], "ridge", 0.1)
+        assert np.array_equal(out[i].view(np.uint64), want.view(np.uint64)), i
+
+
 @pytest.mark.parametrize("case", ["wide_scales", "zero_column", "tiny_and_huge", "all_tiny", "subnormal_cov"])
 def test_whitened_tensor_covariance_extreme_magnitudes(case):
     """Per-column power-of-two scales far from 1 (each column's digits are relative to its own
