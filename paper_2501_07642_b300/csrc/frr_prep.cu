@@ -53,8 +53,9 @@ namespace {
 
 #define PJ_ARGS const PrepJob* __restrict__ jobs, const unsigned* __restrict__ prefix, int E
 
-// Status bits of a preparation: 1 = non-positive Cholesky pivot, 2 = a bounded wait expired.
-constexpr int kStatusPivot = 1, kStatusTimeout = 2;
+// Status bits of a preparation: 1 = non-positive Cholesky pivot, 2 = a bounded wait expired,
+// 4 = a non-finite covariate (found where the centring reads X).
+constexpr int kStatusPivot = 1, kStatusTimeout = 2, kStatusNonFinite = 4;
 
 // The job owning this block and the block's index within the job: prefix[e] is the first
 // block of job e (jobs with no blocks have prefix[e] == prefix[e + 1]).
@@ -128,7 +129,11 @@ __global__ void k_center(PJ_ARGS)
     const PrepJob& J = job_of(jobs, prefix, E, lb);
     const size_t idx = (size_t)lb * blockDim.x + threadIdx.x;
     if (idx >= (size_t)J.n * J.d) return;
-    const double v = __dsub_rn(J.X[idx], J.xbar[idx % J.d]);
+    const double x = J.X[idx];
+    // every covariate passes here once: an all-ones exponent field (infinity or NaN) is
+    // reported in the status word (integer instructions; the atomic only when one is found)
+    if ((__double_as_longlong(x) & 0x7ff0000000000000ll) == 0x7ff0000000000000ll) atomicOr(J.status, kStatusNonFinite);
+    const double v = __dsub_rn(x, J.xbar[idx % J.d]);
     J.Xc[idx] = v;
     J.ZT[idx] = v;  // the forward substitution works in place on a copy of Xc
     if (J.facc) J.facc[idx] = 0ll;
@@ -1286,7 +1291,8 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
     for (int e = 0; e < E; ++e) {
         frr_ctx* c = ctxs[e];
         if (h_status[(size_t)e] != 0) {
-            st_out[e] = (h_status[(size_t)e] & kStatusTimeout) ? FRR_E_TIMEOUT : FRR_E_DEGENERATE;
+            const int hs = h_status[(size_t)e];
+            st_out[e] = (hs & kStatusNonFinite) ? FRR_E_ARG : (hs & kStatusTimeout) ? FRR_E_TIMEOUT : FRR_E_DEGENERATE;
             continue;
         }
         c->band32 = band_from_eps(h_eps[(size_t)e].data(), c->c_M, c->d);

@@ -220,6 +220,30 @@ def test_whitened_concurrent_preparations_of_one_shape():
         assert np.array_equal(out[i].view(np.uint64), want.view(np.uint64)), i
 
 
+@pytest.mark.parametrize("prep", ["fp64_chain", "tensor"])
+def test_non_finite_covariates_found_on_the_device(prep):
+    """frr_init finds a non-finite covariate where the device centres X (no host scan when the
+    preparation runs): NaN, +inf or -inf at the first, a middle or the last entry gives
+    FRR_E_ARG, also when the shape's preparation is replayed from its graph, and a finite X of
+    the same shape is prepared correctly afterwards."""
+    n, d = 120, 40
+    X = ar1_covariates(n, d, 4242, 0.3)
+    for bad in (math.nan, math.inf, -math.inf):
+        for at in ((0, 0), (n // 2, d // 3), (n - 1, d - 1)):
+            Xb = X.copy()
+            Xb[at] = bad
+            with pytest.raises(frr.FrrError) as e:
+                _ctx(Xb, n // 2, whiten="ridge", prep=prep)
+            assert e.value.status == -1, (bad, at)
+        with _ctx(X, n // 2, whiten="ridge", prep=prep) as ctx:
+            got = frr.frr_whitened(ctx)
+        want, *_ = O.prep(X, "ridge", 0.1)
+        if prep == "fp64_chain":
+            assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+        else:
+            assert _zc_err(got, want) < _zc_tol(X, "ridge")
+
+
 @pytest.mark.parametrize("case", ["wide_scales", "zero_column", "tiny_and_huge", "all_tiny", "subnormal_cov"])
 def test_whitened_tensor_covariance_extreme_magnitudes(case):
     """Per-column power-of-two scales far from 1 (each column's digits are relative to its own
