@@ -220,6 +220,21 @@ def test_whitened_concurrent_preparations_of_one_shape():
         assert np.array_equal(out[i].view(np.uint64), want.view(np.uint64)), i
 
 
+def test_whitened_at_the_largest_n():
+    """n = 2048, the largest supported, with d = 600 (three 256-column blocks of the forward
+    substitution, the last one partial; 19 panels): both preparation modes against one oracle
+    run, bit for bit with the FP64 chains, within the derived tolerance with the tensor cores."""
+    n, d = 2048, 600
+    X = ar1_covariates(n, d, 2048, 0.3) * 1.5 - 0.25
+    want, *_ = O.prep(X, "ridge", 0.1)
+    with _ctx(X, n // 2, whiten="ridge", prep="fp64_chain") as ctx:
+        got = frr.frr_whitened(ctx)
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+    with _ctx(X, n // 2, whiten="ridge", prep="tensor") as ctx:
+        got = frr.frr_whitened(ctx)
+    assert _zc_err(got, want) < _zc_tol(X, "ridge")
+
+
 @pytest.mark.parametrize("prep", ["fp64_chain", "tensor"])
 def test_non_finite_covariates_found_on_the_device(prep):
     """frr_init finds a non-finite covariate where the device centres X (no host scan when the
