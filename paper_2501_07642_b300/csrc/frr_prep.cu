@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(kP * kPW) k_chol_below(PJ_ARGS, int p)
     __shared__ double Ld[kP], Yd[kP];
     __shared__ PanelSync ps;
     {
-        const int jj = threadIdx.x / kP, kk = threadIdx.x % kP;
+        const int kk = threadIdx.x / kP, jj = threadIdx.x % kP;  // lanes along a row of L: contiguous loads
         Lc[jj][kk] = (kk < pw && kk >= jj) ? A[(size_t)(k0 + kk) * d + k0 + jj] : 0.0;
     }
     if (threadIdx.x < pw) {
@@ -500,15 +500,19 @@ __global__ void __launch_bounds__(32) k_chol_lookahead(PJ_ARGS, int p)
     const int r0 = k0 + pw;
     double* __restrict__ A = J.Lm;
     const int i = r0 + (int)lb, j = r0 + (int)threadIdx.x;
+    // rows r0 .. i of panel p through shared memory, each row read contiguously (lane = k; a
+    // lane per row would touch 32 rows d apart in every load)
+    __shared__ double tile[kP][kP + 1];
+    for (int q = 0; q <= i - r0; ++q)
+        tile[q][threadIdx.x] = (int)threadIdx.x < pw ? A[(size_t)(r0 + q) * d + k0 + threadIdx.x] : 0.0;
+    __syncwarp();
     if (j > i) return;
-    const double* Li = A + (size_t)i * d + k0;
-    const double* Lj = A + (size_t)j * d + k0;
     // every operand is loaded before the chain of dependent FMAs starts
     double li[kP], lj[kP];
 #pragma unroll
     for (int kk = 0; kk < kP; ++kk) {
-        li[kk] = kk < pw ? Li[kk] : 0.0;
-        lj[kk] = kk < pw ? Lj[kk] : 0.0;
+        li[kk] = tile[i - r0][kk];
+        lj[kk] = tile[j - r0][kk];
     }
     double v = A[(size_t)i * d + j];
 #pragma unroll
@@ -567,7 +571,7 @@ __global__ void __launch_bounds__(kP * kPW) k_fwd_panel(PJ_ARGS, int p)
     __shared__ double Ld[kP], Yd[kP];
     __shared__ PanelSync ps;
     {
-        const int jj = threadIdx.x / kP, kk = threadIdx.x % kP;
+        const int kk = threadIdx.x / kP, jj = threadIdx.x % kP;  // lanes along a row of L: contiguous loads
         Lc[jj][kk] = (kk < pw && kk >= jj) ? L[(size_t)(k0 + kk) * d + k0 + jj] : 0.0;
     }
     if (threadIdx.x < pw) {
