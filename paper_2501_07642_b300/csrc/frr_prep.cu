@@ -503,8 +503,14 @@ __global__ void __launch_bounds__(32) k_chol_lookahead(PJ_ARGS, int p)
     // rows r0 .. i of panel p through shared memory, each row read contiguously (lane = k; a
     // lane per row would touch 32 rows d apart in every load)
     __shared__ double tile[kP][kP + 1];
-    for (int q = 0; q <= i - r0; ++q)
-        tile[q][threadIdx.x] = (int)threadIdx.x < pw ? A[(size_t)(r0 + q) * d + k0 + threadIdx.x] : 0.0;
+    {
+        double v[kP];  // all row loads in flight before the first store
+#pragma unroll
+        for (int q = 0; q < kP; ++q)
+            v[q] = (q <= i - r0 && (int)threadIdx.x < pw) ? A[(size_t)(r0 + q) * d + k0 + threadIdx.x] : 0.0;
+#pragma unroll
+        for (int q = 0; q < kP; ++q) tile[q][threadIdx.x] = v[q];
+    }
     __syncwarp();
     if (j > i) return;
     // every operand is loaded before the chain of dependent FMAs starts
