@@ -1280,9 +1280,11 @@ frr_status prep_run_batch(frr_ctx* const* ctxs, const double* const* X_host, int
             cudaGraph_t g = nullptr;
             capturing = false;
             PREP_CHECK(cudaStreamEndCapture(s, &g));
-            const cudaError_t e = cudaGraphInstantiate(&graph->exec, g, 0);
+            cudaGraphExec_t ex = nullptr;  // kept by the entry only once instantiated
+            const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
             cudaGraphDestroy(g);
             PREP_CHECK(e);
+            graph->exec = ex;
             PREP_CHECK(cudaGraphLaunch(graph->exec, s));
         }
     }
